@@ -1,0 +1,210 @@
+/*
+ * mlswe.h -- C ABI of the GB300 multilayer shallow-water AMR library.
+ *
+ * Paper: A. Schwarzschild and K. Mandli, "An Implementation of Adaptive Mesh
+ * Refinement for Shallow Water Equations", arXiv:1803.01450.
+ *
+ * The library advances an M-layer (M = 1 or 2) shallow-water model on a
+ * hierarchy of refinement levels (Sec. 2, Eqs. (1)-(2): dx^{l+1} = dx^l / r^l)
+ * for one or more independent ensemble members, in FP64 on one GPU. Layer 1 is
+ * the top layer (Sec. 2.1). The conserved fields of a cell are, per layer m,
+ * (h_m, h_m u_m, h_m v_m); arrays of a level are stored field-major
+ * [3M][ny][nx] (row-major, x fastest) in the order
+ * (h_1, hu_1, hv_1, h_2, hu_2, hv_2).
+ *
+ * Storage: every level of every member is a dense array over the whole
+ * domain at that level's resolution; patches are index boxes into it. Cells
+ * outside all patches of a level hold ghost values only.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an mlswe_status; nothing throws across the ABI. The
+ *    text of the last error of a hierarchy is returned by mlswe_last_error.
+ *  - Host arrays passed in are copied before the call returns; output
+ *    pointers are owned by the caller. Device memory is owned by the library
+ *    (obtained through the caller's allocator, or cudaMalloc when none is
+ *    given) and released by mlswe_destroy.
+ *  - All GPU work is issued on the stream given at creation. Calls with host
+ *    outputs synchronise that stream before returning.
+ *  - A hierarchy is used by one host thread at a time.
+ *  - Box convention: int32 [i0, j0, i1, j1), half-open, in the cell indices
+ *    of the level the box belongs to.
+ */
+#ifndef MLSWE_H
+#define MLSWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlswe_hier* mlswe_h;
+
+typedef enum {
+  MLSWE_OK = 0,
+  MLSWE_EINVAL = 1,     /* bad argument (sizes, indices, null pointers, unsupported option) */
+  MLSWE_ENOMEM = 2,     /* device or host allocation failed */
+  MLSWE_ECUDA = 3,      /* a CUDA call failed; text in mlswe_last_error */
+  MLSWE_ECFL = 4,       /* a step ran with Courant number above cfl_max (the step is kept) */
+  MLSWE_ENEGDEPTH = 5,  /* a non-finite value was met in the wave-speed reduction */
+  MLSWE_ENESTING = 6,   /* a patch layout violates nesting or overlaps */
+  MLSWE_ETIMEOUT = 7,   /* reserved: a bounded device wait gave up */
+  MLSWE_EHYPERB = 8,    /* warning: edges lost hyperbolicity (eigenvalue guesses used there) */
+  MLSWE_EMISSING = 9    /* the CUDA library or device is not available */
+} mlswe_status;
+
+/* Device allocator callback. alloc returns a device pointer (NULL on failure)
+ * for `bytes` bytes usable on `stream`; free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} mlswe_allocator;
+
+/* Model and AMR configuration.
+ *  M            layers (1 or 2); rho[0..M-1] densities, rho[0] < rho[1].
+ *  g            gravity; dry_tol: layer m is wet where h_m > dry_tol and every
+ *               layer above is wet (top-down rule, Sec. 2.1).
+ *  cfl_desired  target Courant number for the automatic time step;
+ *  cfl_max      steps above it report MLSWE_ECFL.
+ *  order        1 or 2 (second-order wave correction); limiter 0 none,
+ *               1 minmod, 2 MC; eigen 0: eigenvalue guesses + 2 Newton steps,
+ *               1: guesses only.
+ *  max_levels   1..4; ratio[l] refinement ratio from level l to l+1 (2 or 4),
+ *               used in x, y and time (Sec. 2: r_t = max(r_x, r_y)).
+ *  flag_tol     refine where |grad eta_1| > flag_tol.
+ *  regrid_interval  coarse steps between regrids inside mlswe_advance (0: never).
+ *  n_buf        flag dilation in cells; cluster_eff: minimum box efficiency;
+ *  min_side, max_side  patch side bounds in fine cells.
+ */
+typedef struct {
+  int M;
+  double rho[4];
+  double g;
+  double dry_tol;
+  double cfl_desired;
+  double cfl_max;
+  int order;
+  int limiter;
+  int eigen;
+  int max_levels;
+  int ratio[4];
+  double flag_tol;
+  int regrid_interval;
+  int n_buf;
+  double cluster_eff;
+  int min_side;
+  int max_side;
+} mlswe_config;
+
+/* Physical extent [x0,x1] x [y0,y1] and coarse (level 0) cell counts of a member. */
+typedef struct {
+  double x0, y0, x1, y1;
+  int nx0, ny0;
+} mlswe_domain;
+
+/* Creates a hierarchy of n_members independent members. Level 0 of each
+ * member is one patch covering its domain, with walls on all four sides.
+ * alloc may be NULL (cudaMalloc is used). stream is a cudaStream_t (NULL:
+ * legacy default stream). Errors: EINVAL (config or domain), ENOMEM, ECUDA. */
+mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, const mlswe_domain* doms,
+                                    const mlswe_allocator* alloc, void* cuda_stream, mlswe_h* out);
+
+/* Releases all device and host memory of the hierarchy. */
+mlswe_status mlswe_destroy(mlswe_h h);
+
+/* Text of the last error (never NULL; "" when none). Valid until the next call on h. */
+const char* mlswe_last_error(mlswe_h h);
+
+/* Level-0 cell counts of level `level` of `member`: nx, ny (host outputs). */
+mlswe_status mlswe_level_shape(mlswe_h h, int member, int level, int* nx, int* ny);
+
+/* Bathymetry. B_finest: host [ny_f][nx_f] samples at the cell centres of the
+ * finest level (nx_f = nx0 * prod(ratio[0..max_levels-2])). Every level's B is
+ * the recursive r x r mean of the next finer one (the operator of Eq. (11)),
+ * computed on the device. */
+mlswe_status mlswe_set_bathymetry(mlswe_h h, int member, const double* B_finest);
+
+/* Bathymetry of one level (host [ny][nx] output). */
+mlswe_status mlswe_get_bathymetry(mlswe_h h, int member, int level, double* B_out);
+
+/* State of one level: host [3M][ny][nx] on the level's full index space. */
+mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q);
+mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out);
+
+/* Patch layout of level >= 1: n boxes (host int32 [n][4], level-l indices).
+ * Boxes must be disjoint, lie inside the domain, have sides that are
+ * multiples of nothing in particular, and nest inside level l-1 patches with
+ * a margin of two level-(l-1) cells (ENESTING otherwise). Setting the layout
+ * does not touch the data of the level. */
+mlswe_status mlswe_set_patches(mlswe_h h, int member, int level, int n, const int32_t* boxes);
+
+/* Patch layout of a level: *n receives the count; boxes (may be NULL) must
+ * hold 4 * (*n on entry, as capacity) int32. Level 0 returns its single box. */
+mlswe_status mlswe_get_patches(mlswe_h h, int member, int level, int* n, int32_t* boxes);
+
+/* Fixed time step of every member for the next mlswe_step_level of `level`:
+ * dt host [n_members]. */
+mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt);
+
+/* One dimensionally split finite-volume step of every patch of `level` of
+ * every member with the time step set by mlswe_set_dt (or, if dt is not
+ * NULL, with dt host [n_members]). Ghost cells of patches on level >= 1 must
+ * have been filled (mlswe_fill_ghosts). cfl_out (host [n_members], may be
+ * NULL) receives the Courant number of the step: dt * max(sx/dx, sy/dy). */
+mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cfl_out);
+
+/* Fills the ghost ring (2 cells) of every patch of `level` >= 1 that is not
+ * covered by a sibling patch, by the refinement of Sec. 2.1 applied to the
+ * level-(l-1) state interpolated linearly in time, at fraction alpha in
+ * [0,1] between the last two level-(l-1) states. */
+mlswe_status mlswe_fill_ghosts(mlswe_h h, int level, double alpha);
+
+/* Refinement (Sec. 2.1, Eqs. (4), (5), (10), bottom-up over layers): fills
+ * every cell of the level-(coarse_level+1) patches of `member` from the
+ * current level-coarse_level state and the fine bathymetry. */
+mlswe_status mlswe_interp_fine(mlswe_h h, int coarse_level, int member);
+
+/* Coarsening (Sec. 2.2, Eq. (11)): every component of each level-(fine_level-1)
+ * cell covered by a level-fine_level patch becomes the mean of its r x r fine cells. */
+mlswe_status mlswe_average_coarse(mlswe_h h, int fine_level, int member);
+
+/* Refinement flags of `level` from the current state (host uint8 [ny][nx]):
+ * 1 where |grad eta_1|^2 > flag_tol^2 in a wet cell of the level. */
+mlswe_status mlswe_get_flags(mlswe_h h, int member, int level, uint8_t* flags);
+
+/* Rebuilds the patch layouts of levels base_level+1 .. max_levels-1 from flags
+ * (dilated by n_buf, clustered into boxes), top down, and fills newly covered
+ * fine cells by mlswe_interp_fine. */
+mlswe_status mlswe_regrid(mlswe_h h, int base_level);
+
+/* Advances every member by n_coarse_steps level-0 steps of the subcycled
+ * Berger-Oliger scheme (r_t = ratio), with automatic time steps (cfl_desired),
+ * averaging and mass reflux at coarse/fine interfaces, and a regrid every
+ * regrid_interval coarse steps. */
+mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps);
+
+/* Current level-0 time step per member (host [n_members]) and simulated time. */
+mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out);
+
+/* Surface elevations eta_m (Eq. (4)) at n points (host [n][2], physical x, y)
+ * from the finest level whose patch contains each point; eta_out host [n][M]. */
+mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
+
+/* Launch instrumentation (not in the paper). Returns, and resets, the time in
+ * ms and the launch count of each kernel class since the previous call, as
+ * measured by CUDA events recorded around every launch on the hierarchy's
+ * stream while enabled, and the total number of kernels launched (timed or
+ * not). Classes: 0 x sweep, 1 y sweep, 2 ghost fill, 3 refinement, 4 coarsening
+ * (and bathymetry means), 5 flags, 6 reflux, 7 other. n: capacity of ms_out and
+ * launches_out (either may be NULL). enable: timing on (1) or off (0) from now
+ * on. Synchronises the stream. */
+mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long long* launches_out,
+                          long long* total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLSWE_H */

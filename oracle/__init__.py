@@ -1,0 +1,215 @@
+"""FP64 CPU oracle for the multilayer shallow-water AMR hot path.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The CUDA library never
+imports, links or calls it, and it shares no code with the library.
+
+The numerical core is ``mlswe_oracle.cpp`` (plain loops, ``-ffp-contract=off``);
+this module only loads it through ctypes and offers numpy-shaped wrappers. The
+AMR driver built on top of these primitives is in :mod:`oracle.amr`, the
+patch clustering in :mod:`oracle.cluster`.
+
+Paper: arXiv:1803.01450 (Schwarzschild & Mandli). Each wrapper names the
+passage of the paper it follows; the solver step, which the paper does not
+write out, follows the reading stated in ``mlswe_oracle.cpp``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mlswe_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+NG = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++, OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", _LIB_PATH + ".tmp", _SRC]
+        subprocess.check_call(cmd)
+        os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("g", ctypes.c_double), ("r", ctypes.c_double),
+                ("dry_tol", ctypes.c_double), ("order", ctypes.c_int), ("limiter", ctypes.c_int),
+                ("eigen", ctypes.c_int)]
+
+
+def params(M=2, g=9.81, rho=(1000.0, 1025.0), dry_tol=1e-3, order=2, limiter=2, eigen=0) -> Params:
+    r = rho[0] / rho[1] if M == 2 else 1.0
+    return Params(M, g, r, dry_tol, order, limiter, eigen)
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_pp = ctypes.POINTER(Params)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.or_riemann.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _ip]
+        L.or_eigen.argtypes = [_pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip]
+        L.or_sweep_line.argtypes = [_pp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
+        L.or_sweep_line.restype = ctypes.c_double
+        L.or_fill_walls.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int]
+        L.or_step_patch.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
+        L.or_step_patch.restype = ctypes.c_int
+        L.or_step_walled.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _dp, _dp, _dp]
+        L.or_step_walled.restype = ctypes.c_int
+        L.or_interp_fine.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.or_average_coarse.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.or_flags.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _u8p, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, _u8p]
+        L.or_bathy_average.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.or_adjoint_step.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, _dp, _dp, _dp, _dp]
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# --------------------------------------------------------------------------- edge level
+def riemann(P: Params, qL, qR, BL, BR):
+    """Waves, speeds and fluctuations at one edge (normal direction first in each layer).
+
+    Returns (Z[6][6], s[6], amdq[6], apdq[6], info[3]) where info = (wall side of
+    layer 1, wall side of layer 2, hyperbolicity-loss flag)."""
+    qL = _c(np.pad(np.asarray(qL, float), (0, 6 - len(qL))))
+    qR = _c(np.pad(np.asarray(qR, float), (0, 6 - len(qR))))
+    Z = np.zeros((6, 6)); s = np.zeros(6); am = np.zeros(6); ap = np.zeros(6)
+    info = np.zeros(3, dtype=np.int32)
+    lib().or_riemann(ctypes.byref(P), _d(qL), _d(qR), float(BL), float(BR), _d(Z), _d(s), _d(am), _d(ap),
+                     info.ctypes.data_as(_ip))
+    return Z, s, am, ap, info
+
+
+def eigen(P: Params, u1, u2, hb1, hb2):
+    lam = np.zeros(4)
+    lost = ctypes.c_int(0)
+    lib().or_eigen(ctypes.byref(P), float(u1), float(u2), float(hb1), float(hb2), _d(lam), ctypes.byref(lost))
+    return lam, lost.value
+
+
+def sweep_line(P: Params, line, Bline, nu):
+    """1-D sweep of n cells; line is [n+4][3M] (two ghosts per end), Bline [n+4]."""
+    line = _c(line); Bline = _c(Bline)
+    n = line.shape[0] - 4
+    F = 3 * P.M
+    out = np.zeros((n, F))
+    mf = np.zeros((n + 1, P.M))
+    s = lib().or_sweep_line(ctypes.byref(P), n, _d(line), _d(Bline), float(nu), _d(out), _d(mf))
+    return out, s, mf
+
+
+# --------------------------------------------------------------------------- grid level
+def pad(q, B=None):
+    """Dense [F][ny][nx] (and [ny][nx]) -> patch arrays with a zero ghost ring of 2."""
+    qp = np.pad(np.asarray(q, float), ((0, 0), (NG, NG), (NG, NG)))
+    if B is None:
+        return _c(qp)
+    return _c(qp), _c(np.pad(np.asarray(B, float), ((NG, NG), (NG, NG))))
+
+
+def fill_walls(M, qp, Bp=None, sides=15):
+    F, H, W = qp.shape
+    assert F == 3 * M and qp.flags.c_contiguous
+    lib().or_fill_walls(M, W - 2 * NG, H - 2 * NG, _d(qp), _d(Bp) if Bp is not None else None, sides)
+
+
+def step_patch(P: Params, qp, Bp, dx, dy, dt, want_flux=False):
+    """One split step on a patch array with its ghost ring already filled (in place).
+
+    Returns (smax[2], lost, fx, fy) with fx [M][ny][nx+1], fy [M][ny+1][nx] mass fluxes."""
+    assert qp.flags.c_contiguous and Bp.flags.c_contiguous
+    F, H, W = qp.shape
+    nx, ny = W - 2 * NG, H - 2 * NG
+    smax = np.zeros(2)
+    fx = np.zeros((P.M, ny, nx + 1)) if want_flux else None
+    fy = np.zeros((P.M, ny + 1, nx)) if want_flux else None
+    lost = lib().or_step_patch(ctypes.byref(P), nx, ny, float(dx), float(dy), float(dt), _d(qp), _d(Bp),
+                               _d(smax), _d(fx) if want_flux else None, _d(fy) if want_flux else None)
+    return smax, lost, fx, fy
+
+
+def step_walled(P: Params, q, B, dx, dy, dt):
+    """One step of a dense walled grid q [3M][ny][nx]; returns (q_new, smax[2], lost)."""
+    qp, Bp = pad(q, B)
+    fill_walls(P.M, qp, Bp)
+    smax, lost, _, _ = step_patch(P, qp, Bp, dx, dy, dt)
+    return qp[:, NG:-NG, NG:-NG].copy(), smax, lost
+
+
+def interp_fine(P: Params, r, qc_padded, Bc_padded, box, Bf):
+    """Refinement of the coarse cells box = (ci0, cj0, ci1, cj1) (Sec. 2.1).
+
+    qc_padded: coarse patch array with a valid ghost ring. Bf: fine bathymetry of the box."""
+    ci0, cj0, ci1, cj1 = box
+    F, H, W = qc_padded.shape
+    nxc, nyc = W - 2 * NG, H - 2 * NG
+    Bf = _c(Bf)
+    assert Bf.shape == ((cj1 - cj0) * r, (ci1 - ci0) * r)
+    out = np.zeros((F, (cj1 - cj0) * r, (ci1 - ci0) * r))
+    lib().or_interp_fine(ctypes.byref(P), int(r), nxc, nyc, _d(_c(qc_padded)), _d(_c(Bc_padded)),
+                         ci0, cj0, ci1, cj1, _d(Bf), _d(out))
+    return out
+
+
+def average_coarse(qf, r):
+    """Coarsening, Sec. 2.2 Eq. (11): [nf][nyf][nxf] -> [nf][nyf/r][nxf/r]."""
+    qf = _c(qf)
+    squeeze = qf.ndim == 2
+    if squeeze:
+        qf = qf[None]
+    nf, nyf, nxf = qf.shape
+    assert nyf % r == 0 and nxf % r == 0
+    out = np.zeros((nf, nyf // r, nxf // r))
+    lib().or_average_coarse(nf, int(r), nxf, nyf, _d(qf), _d(out))
+    return out[0] if squeeze else out
+
+
+def bathy_average(Bf, r):
+    return average_coarse(Bf, r)
+
+
+def flags(M, q, B, avail, dry_tol, dx, dy, tol):
+    """Gradient flags of eta_1 (dense level arrays); inv_dx etc. computed here once."""
+    q = _c(q); B = _c(B); avail = _c(avail, np.uint8)
+    F, ny, nx = q.shape
+    out = np.zeros((ny, nx), dtype=np.uint8)
+    lib().or_flags(M, nx, ny, _d(q), _d(B), avail.ctypes.data_as(_u8p), float(dry_tol), 1.0 / dx, 1.0 / dy,
+                   float(tol) * float(tol), out.ctypes.data_as(_u8p))
+    return out
+
+
+def adjoint_step(P: Params, qn, B, dx, dy, dt, lam):
+    """Transpose of the first-order step Jacobian applied to lam; returns (lam_n, gB)."""
+    qn = _c(qn); B = _c(B); lam = _c(lam).copy()
+    F, ny, nx = qn.shape
+    gB = np.zeros((ny, nx))
+    lib().or_adjoint_step(ctypes.byref(P), nx, ny, float(dx), float(dy), float(dt), _d(qn), _d(B), _d(lam), _d(gB))
+    return lam, gB

@@ -1,0 +1,931 @@
+// Multilayer shallow-water AMR: FP64 CPU oracle.
+//
+// TEST INFRASTRUCTURE ONLY. This file is the plain, slow reference that the
+// CUDA library is checked against. Only tests/, the smoke check and the CPU
+// baseline leg of bench.py load it. It shares no code with the CUDA library.
+//
+// Paper: Schwarzschild & Mandli, "An Implementation of Adaptive Mesh
+// Refinement for Shallow Water Equations" (arXiv:1803.01450).
+//   Sec. 2, Eqs. (1)-(2)   level spacing  dx^{l+1} = dx^l / r_x^l
+//   Sec. 2.1, Eq. (3)      eta = h + B
+//   Sec. 2.1, Eq. (4)      eta_{m,k} = B_k + h_{M,k} + ... + h_{m,k}
+//   Sec. 2.1, Eq. (5)      effective bathymetry Bhat_{m,k} = sum_{n>m} h_{n,k} + B_k
+//   Sec. 2.1, Eq. (10)     sigma_k = minmod(eta_k - eta_{k-1}, eta_{k+1} - eta_k) / dx
+//   Sec. 2.1 (last para)   bottom-up layer loop of the refinement
+//   Sec. 2.1 (first para)  top-down wet rule: a layer is wet only if all layers above are
+//   Sec. 2.2, Eq. (11)     coarsening: fine cells averaged onto the coarse cell, all components
+//
+// The paper does not write out the per-patch solver (Sec. 1 cites the
+// multilayer GeoClaw solver without equations). The finite-volume step here is
+// this project's reading: an f-wave Riemann solver with the non-conservative
+// layer coupling folded into the momentum flux jump, Godunov dimensional
+// splitting (x sweep, then y sweep), an MC-limited second-order wave
+// correction and a positivity fix. Every choice is listed in the design notes
+// and is shared, as a specification only, with the CUDA path.
+//
+// Parity pins for this file live in tests/test_oracle_*.py.
+//
+// Storage used throughout: a "line" or "patch" array holds 3M conserved fields
+// per cell in the order (h_1, hu_1, hv_1, h_2, hu_2, hv_2); layer 1 is the top
+// layer (Sec. 2.1). Patch arrays carry a ghost ring of NG = 2 cells and are
+// stored field-major: q[f][j + 2][i + 2], row length nx + 4.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+constexpr int NG = 2;
+constexpr int MAXM = 2;
+constexpr int MAXF = 3 * MAXM;
+constexpr int MAXW = 3 * MAXM;
+
+struct Params {
+  int M;          // number of layers, 1 or 2
+  double g;       // gravity
+  double r;       // density ratio rho_1 / rho_2 (M = 2)
+  double dry_tol; // a layer is wet where h > dry_tol (and every layer above is wet)
+  int order;      // 1 or 2
+  int limiter;    // 0 none, 1 minmod, 2 MC
+  int eigen;      // 0: guesses + 2 Newton steps, 1: guesses only
+};
+
+// ---------------------------------------------------------------------------
+// Scalar helpers written for both double and the dual number used by the
+// adjoint check. Comparisons look at values only.
+// ---------------------------------------------------------------------------
+inline double val(double x) { return x; }
+
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+  Dual() : v(0.0) { for (int k = 0; k < N; ++k) d[k] = 0.0; }
+  Dual(double x) : v(x) { for (int k = 0; k < N; ++k) d[k] = 0.0; }
+};
+template <int N> inline double val(const Dual<N>& x) { return x.v; }
+template <int N> inline Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> c; c.v = a.v + b.v; for (int k = 0; k < N; ++k) c.d[k] = a.d[k] + b.d[k]; return c; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> c; c.v = a.v - b.v; for (int k = 0; k < N; ++k) c.d[k] = a.d[k] - b.d[k]; return c; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> c; c.v = -a.v; for (int k = 0; k < N; ++k) c.d[k] = -a.d[k]; return c; }
+template <int N> inline Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> c; c.v = a.v * b.v; for (int k = 0; k < N; ++k) c.d[k] = a.d[k] * b.v + a.v * b.d[k]; return c; }
+template <int N> inline Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> c; c.v = a.v / b.v;
+  for (int k = 0; k < N; ++k) c.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+  return c; }
+template <int N> inline Dual<N> operator+(const Dual<N>& a, double b) { return a + Dual<N>(b); }
+template <int N> inline Dual<N> operator+(double a, const Dual<N>& b) { return Dual<N>(a) + b; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a, double b) { return a - Dual<N>(b); }
+template <int N> inline Dual<N> operator-(double a, const Dual<N>& b) { return Dual<N>(a) - b; }
+template <int N> inline Dual<N> operator*(const Dual<N>& a, double b) { return a * Dual<N>(b); }
+template <int N> inline Dual<N> operator*(double a, const Dual<N>& b) { return Dual<N>(a) * b; }
+template <int N> inline Dual<N> operator/(const Dual<N>& a, double b) { return a / Dual<N>(b); }
+template <int N> inline Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
+template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
+  Dual<N> c; c.v = std::sqrt(a.v);
+  for (int k = 0; k < N; ++k) c.d[k] = a.d[k] / (2.0 * c.v);
+  return c; }
+using std::sqrt;
+
+template <class T> inline T tmin(const T& a, const T& b) { return val(b) < val(a) ? b : a; }
+template <class T> inline T tmax(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
+template <class T> inline T tabs(const T& a) { return val(a) < 0.0 ? -a : a; }
+
+// ---------------------------------------------------------------------------
+// Riemann solver at one edge, normal direction n, transverse direction t.
+// Inputs per side: (h_m, hn_m, ht_m) for each layer, and the bathymetry B.
+// Output: waves Z[p][3M] with speeds s[p]; per-layer wall marks.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Waves {
+  T Z[MAXW][MAXF];
+  T s[MAXW];
+  int nw;
+  int wall_into[MAXM];  // -1 none, 0: the left cell is the dry wall side, 1: the right cell
+  int hyperbolicity_lost;
+};
+
+// Eigenvalue guesses and Newton steps for the coupled two-layer system.
+// The characteristic polynomial of the normal 4x4 system at the Roe state is
+//   P(l) = ((l - u1)^2 - c1)((l - u2)^2 - c2) - r c1 c2,   c_m = g hbar_m.
+// Guesses are the exact roots for u1 = u2 = ubar (mass-weighted mean):
+//   l = ubar -+ sqrt(mu_+-),  mu_+- = ((c1 + c2) +- sqrt((c1 - c2)^2 + 4 r c1 c2)) / 2,
+// ordered (external -, internal -, internal +, external +).
+template <class T>
+void two_layer_eigen(const Params& P, const T& u1, const T& u2, const T& hb1, const T& hb2,
+                     T lam[4], int* lost) {
+  const T c1 = P.g * hb1, c2 = P.g * hb2;
+  const T ubar = (hb1 * u1 + hb2 * u2) / (hb1 + hb2);
+  const T disc = sqrt((c1 - c2) * (c1 - c2) + 4.0 * P.r * c1 * c2);
+  const T mup = 0.5 * ((c1 + c2) + disc);
+  const T mum = 0.5 * ((c1 + c2) - disc);
+  const T sp = sqrt(mup), sm = sqrt(mum);
+  lam[0] = ubar - sp;
+  lam[1] = ubar - sm;
+  lam[2] = ubar + sm;
+  lam[3] = ubar + sp;
+  const T du = u1 - u2;
+  *lost = val(du * du) >= val((1.0 - P.r) * P.g * (hb1 + hb2)) ? 1 : 0;
+  if (*lost || P.eigen == 1) return;
+  for (int p = 0; p < 4; ++p) {
+    T l = lam[p];
+    for (int it = 0; it < 2; ++it) {
+      const T a1 = l - u1, a2 = l - u2;
+      const T f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
+      const T Pl = f1 * f2 - P.r * c1 * c2;
+      const T dP = 2.0 * a1 * f2 + 2.0 * a2 * f1;
+      l = l - Pl / dP;
+    }
+    lam[p] = l;
+  }
+}
+
+// Dense 4x4 solve by Gaussian elimination with partial pivoting (ties: lowest row).
+template <class T>
+void solve4(T A[4][4], T b[4], T x[4]) {
+  int perm[4] = {0, 1, 2, 3};
+  for (int k = 0; k < 4; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < 4; ++i)
+      if (std::fabs(val(A[perm[i]][k])) > std::fabs(val(A[perm[piv]][k]))) piv = i;
+    std::swap(perm[k], perm[piv]);
+    for (int i = k + 1; i < 4; ++i) {
+      const T f = A[perm[i]][k] / A[perm[k]][k];
+      for (int j = k; j < 4; ++j) A[perm[i]][j] = A[perm[i]][j] - f * A[perm[k]][j];
+      b[perm[i]] = b[perm[i]] - f * b[perm[k]];
+    }
+  }
+  for (int k = 3; k >= 0; --k) {
+    T s = b[perm[k]];
+    for (int j = k + 1; j < 4; ++j) s = s - A[perm[k]][j] * x[j];
+    x[k] = s / A[perm[k]][k];
+  }
+}
+
+// Single-layer f-wave split of delta = (d0, d1, d2) on layer m with speeds s1 < s2,
+// transverse velocity vhat and shear speed ushear. Writes waves pa, pb (acoustic) and
+// pshear into W.
+template <class T>
+void single_layer_waves(int m, const T& d0, const T& d1, const T& d2, const T& s1, const T& s2,
+                        const T& vhat, const T& ushear, int pa, int pb, int pshear, Waves<T>& W) {
+  const T b1 = (s2 * d0 - d1) / (s2 - s1);
+  const T b2 = (d1 - s1 * d0) / (s2 - s1);
+  W.Z[pa][3 * m + 0] = b1; W.Z[pa][3 * m + 1] = b1 * s1; W.Z[pa][3 * m + 2] = b1 * vhat;
+  W.Z[pb][3 * m + 0] = b2; W.Z[pb][3 * m + 1] = b2 * s2; W.Z[pb][3 * m + 2] = b2 * vhat;
+  W.s[pa] = s1; W.s[pb] = s2;
+  W.Z[pshear][3 * m + 2] = d2 - vhat * d0;
+  W.s[pshear] = ushear;
+}
+
+template <class T>
+void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR, Waves<T>& W) {
+  const int M = P.M;
+  const double g = P.g;
+  W.nw = 3 * M;
+  W.hyperbolicity_lost = 0;
+  for (int p = 0; p < MAXW; ++p) {
+    W.s[p] = T(0.0);
+    for (int f = 0; f < MAXF; ++f) W.Z[p][f] = T(0.0);
+  }
+  for (int m = 0; m < MAXM; ++m) W.wall_into[m] = -1;
+
+  // Per-side cell quantities.
+  T h[2][MAXM], hn[2][MAXM], ht[2][MAXM], un[2][MAXM], ut[2][MAXM], eta[2][MAXM], Bhat[2][MAXM];
+  bool wet[2][MAXM];
+  for (int sd = 0; sd < 2; ++sd) {
+    const T* q = sd ? qR : qL;
+    const T& B = sd ? BR : BL;
+    for (int m = 0; m < M; ++m) {
+      h[sd][m] = q[3 * m]; hn[sd][m] = q[3 * m + 1]; ht[sd][m] = q[3 * m + 2];
+      // Top-down wet rule (Sec. 2.1): wet only if every layer above is wet.
+      wet[sd][m] = val(h[sd][m]) > P.dry_tol && (m == 0 || wet[sd][m - 1]);
+      if (wet[sd][m]) { un[sd][m] = hn[sd][m] / h[sd][m]; ut[sd][m] = ht[sd][m] / h[sd][m]; }
+      else { un[sd][m] = T(0.0); ut[sd][m] = T(0.0); }
+    }
+    // Eq. (4): eta_m = B + h_M + ... + h_m, summed from the bottom; Eq. (5): Bhat_m = eta_{m+1}.
+    T acc = B;
+    for (int m = M - 1; m >= 0; --m) {
+      Bhat[sd][m] = acc;
+      acc = acc + h[sd][m];
+      eta[sd][m] = acc;
+    }
+  }
+
+  // Flux jumps with the layer coupling folded into the momentum row:
+  //   d1_m = D(hn un) + g hbar_m (D eta_m + sum_{n<m} (rho_n/rho_m) D h_n)
+  // (g hbar D h_m is exactly (g/2) D(h_m^2); the remaining terms are the pressure of
+  // the layers below through D eta_m and of the lighter layers above).
+  T d0[MAXM], d1[MAXM], d2[MAXM], hbar[MAXM];
+  for (int m = 0; m < M; ++m) {
+    hbar[m] = 0.5 * (h[0][m] + h[1][m]);
+    T coup = eta[1][m] - eta[0][m];
+    if (m == 1) coup = coup + P.r * (h[1][0] - h[0][0]);
+    d0[m] = hn[1][m] - hn[0][m];
+    d1[m] = (hn[1][m] * un[1][m] - hn[0][m] * un[0][m]) + g * hbar[m] * coup;
+    d2[m] = hn[1][m] * ut[1][m] - hn[0][m] * ut[0][m];
+  }
+
+  bool all_wet = true;
+  for (int m = 0; m < M; ++m) all_wet = all_wet && wet[0][m] && wet[1][m];
+
+  if (M == 2 && all_wet) {
+    // Coupled branch: 4 acoustic f-waves of the 4x4 normal system, plus 2 shear waves.
+    T uh[2], vh[2], c[2];
+    for (int m = 0; m < 2; ++m) {
+      const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
+      uh[m] = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
+      vh[m] = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
+      c[m] = g * hbar[m];
+    }
+    T lam[4];
+    int lost = 0;
+    two_layer_eigen(P, uh[0], uh[1], hbar[0], hbar[1], lam, &lost);
+    W.hyperbolicity_lost = lost;
+    // Right eigenvectors (1, l, a, a l), a = ((l - u1)^2 - c1) / c1.
+    T alpha[4];
+    for (int p = 0; p < 4; ++p) alpha[p] = ((lam[p] - uh[0]) * (lam[p] - uh[0]) - c[0]) / c[0];
+    T A[4][4], rhs[4], beta[4];
+    for (int p = 0; p < 4; ++p) {
+      A[0][p] = T(1.0); A[1][p] = lam[p]; A[2][p] = alpha[p]; A[3][p] = alpha[p] * lam[p];
+    }
+    rhs[0] = d0[0]; rhs[1] = d1[0]; rhs[2] = d0[1]; rhs[3] = d1[1];
+    solve4(A, rhs, beta);
+    for (int p = 0; p < 4; ++p) {
+      W.Z[p][0] = beta[p];
+      W.Z[p][1] = beta[p] * lam[p];
+      W.Z[p][2] = beta[p] * vh[0];
+      W.Z[p][3] = beta[p] * alpha[p];
+      W.Z[p][4] = beta[p] * alpha[p] * lam[p];
+      W.Z[p][5] = beta[p] * alpha[p] * vh[1];
+      W.s[p] = lam[p];
+    }
+    W.Z[4][2] = d2[0] - vh[0] * d0[0]; W.s[4] = uh[0];
+    W.Z[5][5] = d2[1] - vh[1] * d0[1]; W.s[5] = uh[1];
+    return;
+  }
+
+  // Decoupled branch: every layer on its own. Wave slots: M = 1 -> (left, right, shear);
+  // M = 2 -> layer 1 (0, 3, 4), layer 2 (1, 2, 5).
+  for (int m = 0; m < M; ++m) {
+    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
+    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
+    const int ps = (M == 1) ? 2 : (m == 0 ? 4 : 5);
+    const bool wl = wet[0][m], wr = wet[1][m];
+    if (wl && wr) {
+      const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
+      const T uh = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
+      const T vh = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
+      const T ch = sqrt(g * hbar[m]);
+      single_layer_waves(m, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, pa, pb, ps, W);
+    } else if (!wl && !wr) {
+      // Both sides dry: no waves for this layer.
+    } else {
+      const int w = wl ? 0 : 1, d = 1 - w;
+      if (val(eta[w][m]) < val(Bhat[d][m])) {
+        // Wall for this layer only: the dry side becomes the mirror of the wet side
+        // (same depth, normal momentum negated); the layer coupling is dropped.
+        const T hw = h[w][m], hnw = hn[w][m], htw = ht[w][m], unw = un[w][m], utw = ut[w][m];
+        T hs[2], hns[2], uns[2], uts[2];
+        hs[w] = hw; hns[w] = hnw; uns[w] = unw; uts[w] = utw;
+        hs[d] = hw; hns[d] = -hnw; uns[d] = -unw; uts[d] = utw;
+        (void)htw;
+        const T e0 = hns[1] - hns[0];
+        const T e1 = hns[1] * uns[1] - hns[0] * uns[0];
+        const T e2 = hns[1] * uts[1] - hns[0] * uts[0];
+        const T sq = sqrt(hs[0]);
+        const T uh = (sq * uns[0] + sq * uns[1]) / (sq + sq);
+        const T vh = (sq * uts[0] + sq * uts[1]) / (sq + sq);
+        const T ch = sqrt(g * (0.5 * (hs[0] + hs[1])));
+        single_layer_waves(m, e0, e1, e2, uh - ch, uh + ch, vh, uh, pa, pb, ps, W);
+        W.wall_into[m] = d;
+      } else {
+        // Flow onto a dry cell: real states, dry-front speed bound on the dry side.
+        const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
+        const T uh = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
+        const T vh = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
+        const T ch = sqrt(g * hbar[m]);
+        const T cw = sqrt(g * h[w][m]);
+        T s1, s2;
+        if (d == 1) { s1 = tmin(un[0][m] - cw, uh - ch); s2 = un[0][m] + 2.0 * cw; }
+        else { s1 = un[1][m] - 2.0 * cw; s2 = tmax(un[1][m] + cw, uh + ch); }
+        single_layer_waves(m, d0[m], d1[m], d2[m], s1, s2, vh, uh, pa, pb, ps, W);
+      }
+    }
+  }
+}
+
+// First-order fluctuations: A-dQ gathers left-going waves, A+dQ right-going ones,
+// a wave of speed exactly 0 is split half and half. A wall layer sends nothing into
+// its dry cell.
+template <class T>
+void fluctuations(const Params& P, const Waves<T>& W, T* amdq, T* apdq) {
+  const int F = 3 * P.M;
+  for (int f = 0; f < F; ++f) { amdq[f] = T(0.0); apdq[f] = T(0.0); }
+  for (int p = 0; p < W.nw; ++p) {
+    const double sv = val(W.s[p]);
+    for (int f = 0; f < F; ++f) {
+      if (sv < 0.0) amdq[f] = amdq[f] + W.Z[p][f];
+      else if (sv > 0.0) apdq[f] = apdq[f] + W.Z[p][f];
+      else { amdq[f] = amdq[f] + 0.5 * W.Z[p][f]; apdq[f] = apdq[f] + 0.5 * W.Z[p][f]; }
+    }
+  }
+  for (int m = 0; m < P.M; ++m) {
+    if (W.wall_into[m] == 0) for (int k = 0; k < 3; ++k) amdq[3 * m + k] = T(0.0);
+    if (W.wall_into[m] == 1) for (int k = 0; k < 3; ++k) apdq[3 * m + k] = T(0.0);
+  }
+}
+
+template <class T>
+T limiter_phi(int kind, const T& th) {
+  if (kind == 0) return T(1.0);
+  if (kind == 1) return tmax(T(0.0), tmin(T(1.0), th));
+  // MC: max(0, min((1 + theta)/2, 2, 2 theta))
+  return tmax(T(0.0), tmin(tmin(0.5 * (1.0 + th), T(2.0)), 2.0 * th));
+}
+
+// Second-order correction flux at an edge, from its waves and the waves at the
+// neighbouring edges (wave limiter with the upwind neighbour of each family).
+template <class T>
+void correction(const Params& P, const Waves<T>& W, const Waves<T>& Wleft, const Waves<T>& Wright,
+                double nu, T* ftil) {
+  const int F = 3 * P.M;
+  for (int f = 0; f < F; ++f) ftil[f] = T(0.0);
+  if (P.order < 2) return;
+  for (int p = 0; p < W.nw; ++p) {
+    const double sv = val(W.s[p]);
+    if (sv == 0.0) continue;
+    const Waves<T>& U = sv > 0.0 ? Wleft : Wright;
+    T zz(0.0), zu(0.0);
+    for (int f = 0; f < F; ++f) { zz = zz + W.Z[p][f] * W.Z[p][f]; zu = zu + U.Z[p][f] * W.Z[p][f]; }
+    T th(0.0);
+    if (val(zz) > 0.0) th = zu / zz;
+    const T phi = limiter_phi(P.limiter, th);
+    const T sa = tabs(W.s[p]);
+    const double sg = sv > 0.0 ? 1.0 : -1.0;
+    const T coef = 0.5 * sg * (1.0 - nu * sa) * phi;
+    for (int f = 0; f < F; ++f) ftil[f] = ftil[f] + coef * W.Z[p][f];
+  }
+  for (int m = 0; m < P.M; ++m)
+    if (W.wall_into[m] >= 0) for (int k = 0; k < 3; ++k) ftil[3 * m + k] = T(0.0);
+}
+
+// Positivity fix: negative depths are clipped, momentum of a thin layer is removed.
+template <class T>
+void positivity(const Params& P, T* q) {
+  for (int m = 0; m < P.M; ++m) {
+    if (val(q[3 * m]) < 0.0) q[3 * m] = T(0.0);
+    if (val(q[3 * m]) <= P.dry_tol) { q[3 * m + 1] = T(0.0); q[3 * m + 2] = T(0.0); }
+  }
+}
+
+// One 1-D sweep along a line of n cells with two ghost cells at each end.
+// line[(k)*F + f] for k in [0, n + 4) holds cell k - 2 in (h, hn, ht) order per layer.
+// Writes out[i*F + f] for cells i in [0, n). Returns the largest wave speed at the
+// edges i - 1/2, i in [0, n], and (optionally) the mass flux of every layer there.
+template <class T>
+double sweep_line(const Params& P, int n, const T* line, const T* Bline, double nu, T* out,
+                  T* massflux /*[(n+1)*M] or null*/, int* lost_count) {
+  const int F = 3 * P.M;
+  // Edges e = i - 1/2 for i in [-1, n + 1]: index k = i + 1 in [0, n + 2].
+  std::vector<Waves<T>> W(n + 3);
+  for (int k = 0; k < n + 3; ++k) {
+    const int i = k - 1;  // cells i - 1 and i, stored at i + 1 and i + 2
+    riemann(P, &line[(i + 1) * F], &line[(i + 2) * F], Bline[i + 1], Bline[i + 2], W[k]);
+  }
+  double smax = 0.0;
+  std::vector<T> amdq((n + 1) * F), apdq((n + 1) * F), ftil((n + 1) * F);
+  for (int i = 0; i <= n; ++i) {
+    const int k = i + 1;
+    fluctuations(P, W[k], &amdq[i * F], &apdq[i * F]);
+    correction(P, W[k], W[k - 1], W[k + 1], nu, &ftil[i * F]);
+    for (int p = 0; p < W[k].nw; ++p) smax = std::max(smax, std::fabs(val(W[k].s[p])));
+    if (lost_count) *lost_count += W[k].hyperbolicity_lost;
+    if (massflux) {
+      // Flux through edge i - 1/2 as seen from the left cell i - 1.
+      for (int m = 0; m < P.M; ++m)
+        massflux[i * P.M + m] = line[(i + 1) * F + 3 * m + 1] + amdq[i * F + 3 * m] + ftil[i * F + 3 * m];
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    T q[MAXF];
+    for (int f = 0; f < F; ++f) {
+      q[f] = line[(i + 2) * F + f]
+             - nu * (apdq[i * F + f] + amdq[(i + 1) * F + f])
+             - nu * (ftil[(i + 1) * F + f] - ftil[i * F + f]);
+    }
+    positivity(P, q);
+    for (int f = 0; f < F; ++f) out[i * F + f] = q[f];
+  }
+  return smax;
+}
+
+inline size_t pidx(int nx, int i, int j) { return (size_t)(j + NG) * (nx + 2 * NG) + (i + NG); }
+
+// Wall ghost cells on all four sides: mirror the state, negate the normal momentum of
+// every layer, mirror B. x ghosts of the interior rows first, then full-width y ghost rows
+// (corners therefore carry both negations).
+void fill_walls_impl(int M, int nx, int ny, double* q, double* B, int sides /*bit0 W, bit1 E, bit2 S, bit3 N*/) {
+  const int F = 3 * M;
+  const size_t plane = (size_t)(nx + 2 * NG) * (ny + 2 * NG);
+  for (int j = 0; j < ny; ++j)
+    for (int gI = 1; gI <= NG; ++gI) {
+      if (sides & 1) {
+        const int dst = -gI, src = gI - 1;
+        for (int f = 0; f < F; ++f) {
+          const double sgn = (f % 3 == 1) ? -1.0 : 1.0;
+          q[f * plane + pidx(nx, dst, j)] = sgn * q[f * plane + pidx(nx, src, j)];
+        }
+        if (B) B[pidx(nx, dst, j)] = B[pidx(nx, src, j)];
+      }
+      if (sides & 2) {
+        const int dst = nx - 1 + gI, src = nx - gI;
+        for (int f = 0; f < F; ++f) {
+          const double sgn = (f % 3 == 1) ? -1.0 : 1.0;
+          q[f * plane + pidx(nx, dst, j)] = sgn * q[f * plane + pidx(nx, src, j)];
+        }
+        if (B) B[pidx(nx, dst, j)] = B[pidx(nx, src, j)];
+      }
+    }
+  for (int i = -NG; i < nx + NG; ++i)
+    for (int gJ = 1; gJ <= NG; ++gJ) {
+      if (sides & 4) {
+        const int dst = -gJ, src = gJ - 1;
+        for (int f = 0; f < F; ++f) {
+          const double sgn = (f % 3 == 2) ? -1.0 : 1.0;
+          q[f * plane + pidx(nx, i, dst)] = sgn * q[f * plane + pidx(nx, i, src)];
+        }
+        if (B) B[pidx(nx, i, dst)] = B[pidx(nx, i, src)];
+      }
+      if (sides & 8) {
+        const int dst = ny - 1 + gJ, src = ny - gJ;
+        for (int f = 0; f < F; ++f) {
+          const double sgn = (f % 3 == 2) ? -1.0 : 1.0;
+          q[f * plane + pidx(nx, i, dst)] = sgn * q[f * plane + pidx(nx, i, src)];
+        }
+        if (B) B[pidx(nx, i, dst)] = B[pidx(nx, i, src)];
+      }
+    }
+}
+
+// One dimensionally split step on a patch whose ghost ring is filled.
+// x sweep over every row j in [-2, ny + 2) (ghost rows included, so the y sweep sees
+// swept ghost rows), then y sweep over the interior columns.
+template <class T>
+void step_patch_impl(const Params& P, int nx, int ny, double dx, double dy, double dt,
+                     T* q, const T* B, double* smax, T* fx, T* fy, int* lost) {
+  const int F = 3 * P.M;
+  const int W = nx + 2 * NG, H = ny + 2 * NG;
+  const size_t plane = (size_t)W * H;
+  std::vector<T> qs(q, q + plane * F);  // q* (ghost columns keep Q^n; unused by the y sweep)
+  double sx = 0.0, sy = 0.0;
+  int lost_x = 0, lost_y = 0;
+  #pragma omp parallel for reduction(max : sx) reduction(+ : lost_x) schedule(static)
+  for (int j = -NG; j < ny + NG; ++j) {
+    std::vector<T> line((nx + 4) * F), Bl(nx + 4), out(nx * F), mf((nx + 1) * P.M);
+    for (int i = -NG; i < nx + NG; ++i) {
+      Bl[i + NG] = B[pidx(nx, i, j)];
+      for (int m = 0; m < P.M; ++m) {
+        line[(i + NG) * F + 3 * m + 0] = q[(3 * m + 0) * plane + pidx(nx, i, j)];
+        line[(i + NG) * F + 3 * m + 1] = q[(3 * m + 1) * plane + pidx(nx, i, j)];
+        line[(i + NG) * F + 3 * m + 2] = q[(3 * m + 2) * plane + pidx(nx, i, j)];
+      }
+    }
+    const bool interior = (j >= 0 && j < ny);
+    int lc = 0;
+    const double s = sweep_line(P, nx, line.data(), Bl.data(), dt / dx, out.data(),
+                                (interior && fx) ? mf.data() : nullptr, &lc);
+    if (interior) { sx = std::max(sx, s); lost_x += lc; }
+    for (int i = 0; i < nx; ++i)
+      for (int m = 0; m < P.M; ++m) {
+        qs[(3 * m + 0) * plane + pidx(nx, i, j)] = out[i * F + 3 * m + 0];
+        qs[(3 * m + 1) * plane + pidx(nx, i, j)] = out[i * F + 3 * m + 1];
+        qs[(3 * m + 2) * plane + pidx(nx, i, j)] = out[i * F + 3 * m + 2];
+      }
+    if (interior && fx)
+      for (int i = 0; i <= nx; ++i)
+        for (int m = 0; m < P.M; ++m) fx[((size_t)m * ny + j) * (nx + 1) + i] = mf[i * P.M + m];
+  }
+  #pragma omp parallel for reduction(max : sy) reduction(+ : lost_y) schedule(static)
+  for (int i = 0; i < nx; ++i) {
+    std::vector<T> line((ny + 4) * F), Bl(ny + 4), out(ny * F), mf((ny + 1) * P.M);
+    for (int j = -NG; j < ny + NG; ++j) {
+      Bl[j + NG] = B[pidx(nx, i, j)];
+      for (int m = 0; m < P.M; ++m) {
+        // normal = hv, transverse = hu
+        line[(j + NG) * F + 3 * m + 0] = qs[(3 * m + 0) * plane + pidx(nx, i, j)];
+        line[(j + NG) * F + 3 * m + 1] = qs[(3 * m + 2) * plane + pidx(nx, i, j)];
+        line[(j + NG) * F + 3 * m + 2] = qs[(3 * m + 1) * plane + pidx(nx, i, j)];
+      }
+    }
+    int lc = 0;
+    const double s = sweep_line(P, ny, line.data(), Bl.data(), dt / dy, out.data(),
+                                fy ? mf.data() : nullptr, &lc);
+    sy = std::max(sy, s);
+    lost_y += lc;
+    for (int j = 0; j < ny; ++j)
+      for (int m = 0; m < P.M; ++m) {
+        q[(3 * m + 0) * plane + pidx(nx, i, j)] = out[j * F + 3 * m + 0];
+        q[(3 * m + 2) * plane + pidx(nx, i, j)] = out[j * F + 3 * m + 1];
+        q[(3 * m + 1) * plane + pidx(nx, i, j)] = out[j * F + 3 * m + 2];
+      }
+    if (fy)
+      for (int j = 0; j <= ny; ++j)
+        for (int m = 0; m < P.M; ++m) fy[((size_t)m * (ny + 1) + j) * nx + i] = mf[j * P.M + m];
+  }
+  if (smax) { smax[0] = sx; smax[1] = sy; }
+  if (lost) *lost = lost_x + lost_y;
+}
+
+inline double minmod(double a, double b) {
+  // Sec. 2.1: the argument of smaller modulus, zero when the signs differ.
+  if (a * b <= 0.0) return 0.0;
+  return std::fabs(a) <= std::fabs(b) ? a : b;
+}
+
+}  // namespace
+
+extern "C" {
+
+struct or_params {
+  int M; double g; double r; double dry_tol; int order; int limiter; int eigen;
+};
+
+static Params to_params(const or_params* p) {
+  Params P;
+  P.M = p->M; P.g = p->g; P.r = p->r; P.dry_tol = p->dry_tol;
+  P.order = p->order; P.limiter = p->limiter; P.eigen = p->eigen;
+  return P;
+}
+
+// Waves and fluctuations at one edge (normal direction n): Z[6][6], s[6], amdq[6], apdq[6],
+// info[0..1] wall marks per layer, info[2] hyperbolicity-loss flag.
+void or_riemann(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
+                double* Z, double* s, double* amdq, double* apdq, int* info) {
+  const Params P = to_params(pp);
+  Waves<double> W;
+  riemann(P, qL, qR, BL, BR, W);
+  for (int p = 0; p < MAXW; ++p) {
+    s[p] = W.s[p];
+    for (int f = 0; f < MAXF; ++f) Z[p * MAXF + f] = W.Z[p][f];
+  }
+  fluctuations(P, W, amdq, apdq);
+  info[0] = W.wall_into[0]; info[1] = W.wall_into[1]; info[2] = W.hyperbolicity_lost;
+}
+
+void or_eigen(const or_params* pp, double u1, double u2, double hb1, double hb2, double* lam, int* lost) {
+  const Params P = to_params(pp);
+  two_layer_eigen(P, u1, u2, hb1, hb2, lam, lost);
+}
+
+// 1-D sweep on a line of n cells (plus 2 ghosts per end); test entry.
+double or_sweep_line(const or_params* pp, int n, const double* line, const double* Bline, double nu,
+                     double* out, double* massflux) {
+  const Params P = to_params(pp);
+  int lost = 0;
+  return sweep_line(P, n, line, Bline, nu, out, massflux, &lost);
+}
+
+void or_fill_walls(int M, int nx, int ny, double* q, double* B, int sides) {
+  fill_walls_impl(M, nx, ny, q, B, sides);
+}
+
+// One step on a patch array with a filled ghost ring; q is updated in place (interior).
+// smax[2] receives the largest wave speeds of the x and y sweeps; fx [M][ny][nx+1] and
+// fy [M][ny+1][nx] (either may be null) receive the mass flux of every layer at every
+// interior edge. Returns the number of edges where hyperbolicity was lost.
+int or_step_patch(const or_params* pp, int nx, int ny, double dx, double dy, double dt,
+                  double* q, const double* B, double* smax, double* fx, double* fy) {
+  const Params P = to_params(pp);
+  int lost = 0;
+  step_patch_impl(P, nx, ny, dx, dy, dt, q, B, smax, fx, fy, &lost);
+  return lost;
+}
+
+// Fixed grid with walls on all sides: fill ghosts, then one step.
+int or_step_walled(const or_params* pp, int nx, int ny, double dx, double dy, double dt,
+                   double* q, double* B, double* smax) {
+  fill_walls_impl(pp->M, nx, ny, q, B, 15);
+  return or_step_patch(pp, nx, ny, dx, dy, dt, q, B, smax, nullptr, nullptr);
+}
+
+// Refinement, Sec. 2.1 (Eqs. (4), (5), (10) and the bottom-up layer loop), in 2-D.
+// qc: coarse patch array [3M][nyc+4][nxc+4] with its ghost ring filled (neighbours of
+// every coarse cell in the box must be valid). Box: coarse cells [ci0, ci1) x [cj0, cj1).
+// Bf: fine bathymetry for the fine cells of the box, [(cj1-cj0)*r][(ci1-ci0)*r].
+// out: fine values [3M][(cj1-cj0)*r][(ci1-ci0)*r].
+void or_interp_fine(const or_params* pp, int r, int nxc, int nyc, const double* qc, const double* Bc,
+                    int ci0, int cj0, int ci1, int cj1, const double* Bf, double* out) {
+  const Params P = to_params(pp);
+  const int M = P.M;
+  const size_t plane = (size_t)(nxc + 4) * (nyc + 4);
+  const int nfx = (ci1 - ci0) * r, nfy = (cj1 - cj0) * r;
+  const size_t fplane = (size_t)nfx * nfy;
+  auto Q = [&](int f, int i, int j) { return qc[f * plane + pidx(nxc, i, j)]; };
+  auto wetc = [&](int i, int j, int m) {
+    for (int n = 0; n <= m; ++n) if (!(Q(3 * n, i, j) > P.dry_tol)) return false;
+    return true;
+  };
+  auto etac = [&](int i, int j, int m) {
+    double e = Bc[pidx(nxc, i, j)];
+    for (int n = M - 1; n >= m; --n) e = e + Q(3 * n, i, j);
+    return e;
+  };
+  std::vector<double> off(r);
+  for (int a = 0; a < r; ++a) off[a] = (a + 0.5) / r - 0.5;
+  for (int cj = cj0; cj < cj1; ++cj)
+    for (int ci = ci0; ci < ci1; ++ci) {
+      // Fine depths of the layers below, needed for the effective bathymetry (Eq. (5)).
+      std::vector<double> hf((size_t)M * r * r, 0.0);
+      for (int m = M - 1; m >= 0; --m) {  // bottom layer first (Sec. 2.1, last paragraph)
+        const bool wk = wetc(ci, cj, m);
+        double sx = 0.0, sy = 0.0;
+        if (wk) {
+          const double ek = etac(ci, cj, m);
+          const double aL = wetc(ci - 1, cj, m) ? ek - etac(ci - 1, cj, m) : 0.0;
+          const double aR = wetc(ci + 1, cj, m) ? etac(ci + 1, cj, m) - ek : 0.0;
+          const double aS = wetc(ci, cj - 1, m) ? ek - etac(ci, cj - 1, m) : 0.0;
+          const double aN = wetc(ci, cj + 1, m) ? etac(ci, cj + 1, m) - ek : 0.0;
+          sx = minmod(aL, aR);  // Eq. (10) times dx: the slope in units of one coarse cell
+          sy = minmod(aS, aN);
+        }
+        // Momentum: the same limited linear reconstruction on the conserved variables.
+        double mx[2] = {0, 0}, my[2] = {0, 0}, mc[2] = {0, 0};
+        for (int k = 0; k < 2 && wk; ++k) {
+          const int f = 3 * m + 1 + k;
+          const double c = Q(f, ci, cj);
+          mc[k] = c;
+          const double aL = wetc(ci - 1, cj, m) ? c - Q(f, ci - 1, cj) : 0.0;
+          const double aR = wetc(ci + 1, cj, m) ? Q(f, ci + 1, cj) - c : 0.0;
+          const double aS = wetc(ci, cj - 1, m) ? c - Q(f, ci, cj - 1) : 0.0;
+          const double aN = wetc(ci, cj + 1, m) ? Q(f, ci, cj + 1) - c : 0.0;
+          mx[k] = minmod(aL, aR);
+          my[k] = minmod(aS, aN);
+        }
+        const double ek = wk ? etac(ci, cj, m) : 0.0;
+        for (int b = 0; b < r; ++b)
+          for (int a = 0; a < r; ++a) {
+            const int fi = (ci - ci0) * r + a, fj = (cj - cj0) * r + b;
+            const size_t fo = (size_t)fj * nfx + fi;
+            double h = 0.0, hu = 0.0, hv = 0.0;
+            if (wk) {
+              const double ef = ek + sx * off[a] + sy * off[b];
+              double bh = Bf[fo];
+              for (int n = M - 1; n > m; --n) bh = bh + hf[(size_t)n * r * r + b * r + a];
+              h = std::max(0.0, ef - bh);
+              if (h > P.dry_tol) {
+                hu = mc[0] + mx[0] * off[a] + my[0] * off[b];
+                hv = mc[1] + mx[1] * off[a] + my[1] * off[b];
+              }
+            }
+            hf[(size_t)m * r * r + b * r + a] = h;
+            out[(3 * m + 0) * fplane + fo] = h;
+            out[(3 * m + 1) * fplane + fo] = hu;
+            out[(3 * m + 2) * fplane + fo] = hv;
+          }
+      }
+    }
+}
+
+// Coarsening, Sec. 2.2, Eq. (11) in 2-D: every component of the coarse cell becomes the
+// mean of its r x r fine cells (row-major sum, then times 1/(r r)).
+// qf: [nf][nyf][nxf] (nf components), out: [nf][nyf/r][nxf/r].
+void or_average_coarse(int nf, int r, int nxf, int nyf, const double* qf, double* out) {
+  const int nxc = nxf / r, nyc = nyf / r;
+  const double inv = 1.0 / (double)(r * r);
+  for (int f = 0; f < nf; ++f)
+    for (int j = 0; j < nyc; ++j)
+      for (int i = 0; i < nxc; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < r; ++b)
+          for (int a = 0; a < r; ++a) s = s + qf[((size_t)f * nyf + (size_t)j * r + b) * nxf + (size_t)i * r + a];
+        out[((size_t)f * nyc + j) * nxc + i] = s * inv;
+      }
+}
+
+// Refinement flags from the gradient of the top surface eta_1 (Eq. (4) with m = 1):
+// flag iff gx^2 + gy^2 > tol^2, central differences where both neighbours are usable
+// (inside the domain, inside the level's patches and wet in layer 1), one-sided where
+// only one is. q: [3M][ny][nx] dense level, B: [ny][nx], avail: [ny][nx] (1 = cell of
+// the level). No fused multiply-add anywhere (compiled with -ffp-contract=off).
+void or_flags(int M, int nx, int ny, const double* q, const double* B, const uint8_t* avail,
+              double dry_tol, double inv_dx, double inv_dy, double tol2, uint8_t* flags) {
+  const size_t plane = (size_t)nx * ny;
+  auto usable = [&](int i, int j) {
+    if (i < 0 || j < 0 || i >= nx || j >= ny) return false;
+    const size_t c = (size_t)j * nx + i;
+    return avail[c] != 0 && q[c] > dry_tol;
+  };
+  auto eta1 = [&](int i, int j) {
+    const size_t c = (size_t)j * nx + i;
+    double e = B[c];
+    for (int n = M - 1; n >= 0; --n) e = e + q[(size_t)(3 * n) * plane + c];
+    return e;
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t c = (size_t)j * nx + i;
+      flags[c] = 0;
+      if (!usable(i, j)) continue;
+      const double e = eta1(i, j);
+      const bool l = usable(i - 1, j), rr = usable(i + 1, j), s = usable(i, j - 1), n = usable(i, j + 1);
+      double gx = 0.0, gy = 0.0;
+      if (l && rr) gx = (eta1(i + 1, j) - eta1(i - 1, j)) * (0.5 * inv_dx);
+      else if (rr) gx = (eta1(i + 1, j) - e) * inv_dx;
+      else if (l) gx = (e - eta1(i - 1, j)) * inv_dx;
+      if (s && n) gy = (eta1(i, j + 1) - eta1(i, j - 1)) * (0.5 * inv_dy);
+      else if (n) gy = (eta1(i, j + 1) - e) * inv_dy;
+      else if (s) gy = (e - eta1(i, j - 1)) * inv_dy;
+      const double g2 = gx * gx + gy * gy;
+      flags[c] = g2 > tol2 ? 1 : 0;
+    }
+}
+
+// Bathymetry of a coarser level: mean of the r x r cells of the next finer level
+// (row-major sum, then times 1/(r r)), the same operator as Eq. (11).
+void or_bathy_average(int r, int nxf, int nyf, const double* Bf, double* Bc) {
+  or_average_coarse(1, r, nxf, nyf, Bf, Bc);
+}
+
+// Adjoint of one first-order, fixed-dt step on a walled grid (wet cells only), applied
+// to the cotangent lam (in: d/dQ^{n+1}, out: d/dQ^n, [3M][ny][nx]) and accumulating the
+// bathymetry cotangent into gB [ny][nx]. The local Jacobian of each edge is taken
+// exactly by forward-mode dual numbers; its transpose is applied edge by edge.
+// q: Q^n [3M][ny][nx], B [ny][nx].
+void or_adjoint_step(const or_params* pp, int nx, int ny, double dx, double dy, double dt,
+                     const double* qn, const double* Bd, double* lam, double* gB);
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint (transpose of the step Jacobian) with dual numbers.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int ND = 14;  // 6 + 6 state entries and 2 bathymetry values of one edge
+using D14 = Dual<ND>;
+
+// Jacobian of (A-dQ, A+dQ) of one edge with respect to (qL[6], qR[6], BL, BR):
+// J[out 0..11][in 0..13].
+void edge_jacobian(const Params& P, const double* qL, const double* qR, double BL, double BR,
+                   double J[12][ND], double amdq_v[6], double apdq_v[6]) {
+  const int F = 3 * P.M;
+  D14 L[MAXF], R[MAXF], bl(BL), br(BR);
+  for (int f = 0; f < F; ++f) {
+    L[f] = D14(qL[f]); L[f].d[f] = 1.0;
+    R[f] = D14(qR[f]); R[f].d[6 + f] = 1.0;
+  }
+  bl.d[12] = 1.0; br.d[13] = 1.0;
+  Waves<D14> W;
+  riemann(P, L, R, bl, br, W);
+  D14 am[MAXF], ap[MAXF];
+  fluctuations(P, W, am, ap);
+  for (int o = 0; o < 12; ++o) for (int k = 0; k < ND; ++k) J[o][k] = 0.0;
+  for (int f = 0; f < F; ++f) {
+    amdq_v[f] = am[f].v; apdq_v[f] = ap[f].v;
+    for (int k = 0; k < ND; ++k) { J[f][k] = am[f].d[k]; J[6 + f][k] = ap[f].d[k]; }
+  }
+}
+
+// Map input slot k of an edge (L/R state entry f, or bathymetry) to the array index of the
+// line it belongs to.
+void adjoint_sweep_line(const Params& P, int n, const double* line, const double* Bline, double nu,
+                        const double* lam_out /*[n][F]*/, double* lam_in /*[(n+4)][F]*/,
+                        double* gB_line /*[n+4]*/) {
+  const int F = 3 * P.M;
+  // Q*_i = Q_i - nu (A+dQ_{i-1/2} + A-dQ_{i+1/2}) for i in [0, n).
+  for (int i = 0; i < n; ++i)
+    for (int f = 0; f < F; ++f) lam_in[(i + 2) * F + f] += lam_out[i * F + f];
+  for (int i = 0; i <= n; ++i) {  // edge i - 1/2 between cells i - 1 and i
+    double J[12][ND], am[6], ap[6];
+    edge_jacobian(P, &line[(i + 1) * F], &line[(i + 2) * F], Bline[i + 1], Bline[i + 2], J, am, ap);
+    double cot[12] = {0};
+    // A-dQ at this edge enters cell i - 1, A+dQ enters cell i.
+    if (i - 1 >= 0) for (int f = 0; f < F; ++f) cot[f] = -nu * lam_out[(i - 1) * F + f];
+    if (i < n) for (int f = 0; f < F; ++f) cot[6 + f] = -nu * lam_out[i * F + f];
+    for (int k = 0; k < ND; ++k) {
+      double s = 0.0;
+      for (int o = 0; o < 12; ++o) s += J[o][k] * cot[o];
+      if (k < 6) { if (k < F) lam_in[(i + 1) * F + k] += s; }
+      else if (k < 12) { if (k - 6 < F) lam_in[(i + 2) * F + (k - 6)] += s; }
+      else if (k == 12) gB_line[i + 1] += s;
+      else gB_line[i + 2] += s;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" void or_adjoint_step(const or_params* pp, int nx, int ny, double dx, double dy, double dt,
+                                const double* qn, const double* Bd, double* lam, double* gB) {
+  Params P = to_params(pp);
+  P.order = 1;
+  const int F = 3 * P.M;
+  const size_t plane = (size_t)nx * ny;
+  // Rebuild the forward intermediates: padded Q^n with walls, and Q* with walls.
+  const int W = nx + 4, H = ny + 4;
+  const size_t pplane = (size_t)W * H;
+  std::vector<double> qp(pplane * F), Bp(pplane);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      Bp[pidx(nx, i, j)] = Bd[(size_t)j * nx + i];
+      for (int f = 0; f < F; ++f) qp[f * pplane + pidx(nx, i, j)] = qn[f * plane + (size_t)j * nx + i];
+    }
+  fill_walls_impl(P.M, nx, ny, qp.data(), Bp.data(), 15);
+  std::vector<double> qs = qp;
+  // x sweep (order 1) over all rows, as in the forward step, to rebuild Q*.
+  for (int j = -NG; j < ny + NG; ++j) {
+    std::vector<double> line((nx + 4) * F), Bl(nx + 4), out(nx * F);
+    for (int i = -NG; i < nx + NG; ++i) {
+      Bl[i + NG] = Bp[pidx(nx, i, j)];
+      for (int m = 0; m < P.M; ++m)
+        for (int k = 0; k < 3; ++k) line[(i + NG) * F + 3 * m + k] = qp[(3 * m + k) * pplane + pidx(nx, i, j)];
+    }
+    int lc = 0;
+    sweep_line(P, nx, line.data(), Bl.data(), dt / dx, out.data(), (double*)nullptr, &lc);
+    for (int i = 0; i < nx; ++i)
+      for (int f = 0; f < F; ++f) qs[f * pplane + pidx(nx, i, j)] = out[i * F + f];
+  }
+  // Reverse of the y sweep: lam -> lam* on the padded Q* grid (rows -2..ny+1).
+  std::vector<double> lams(pplane * F, 0.0), gBp(pplane, 0.0);
+  for (int i = 0; i < nx; ++i) {
+    std::vector<double> line((ny + 4) * F), Bl(ny + 4), lo(ny * F), li((ny + 4) * F, 0.0), gl(ny + 4, 0.0);
+    for (int j = -NG; j < ny + NG; ++j) {
+      Bl[j + NG] = Bp[pidx(nx, i, j)];
+      for (int m = 0; m < P.M; ++m) {
+        line[(j + NG) * F + 3 * m + 0] = qs[(3 * m + 0) * pplane + pidx(nx, i, j)];
+        line[(j + NG) * F + 3 * m + 1] = qs[(3 * m + 2) * pplane + pidx(nx, i, j)];
+        line[(j + NG) * F + 3 * m + 2] = qs[(3 * m + 1) * pplane + pidx(nx, i, j)];
+      }
+    }
+    for (int j = 0; j < ny; ++j)
+      for (int m = 0; m < P.M; ++m) {
+        lo[j * F + 3 * m + 0] = lam[(3 * m + 0) * plane + (size_t)j * nx + i];
+        lo[j * F + 3 * m + 1] = lam[(3 * m + 2) * plane + (size_t)j * nx + i];
+        lo[j * F + 3 * m + 2] = lam[(3 * m + 1) * plane + (size_t)j * nx + i];
+      }
+    adjoint_sweep_line(P, ny, line.data(), Bl.data(), dt / dy, lo.data(), li.data(), gl.data());
+    for (int j = -NG; j < ny + NG; ++j) {
+      gBp[pidx(nx, i, j)] += gl[j + NG];
+      for (int m = 0; m < P.M; ++m) {
+        lams[(3 * m + 0) * pplane + pidx(nx, i, j)] += li[(j + NG) * F + 3 * m + 0];
+        lams[(3 * m + 2) * pplane + pidx(nx, i, j)] += li[(j + NG) * F + 3 * m + 1];
+        lams[(3 * m + 1) * pplane + pidx(nx, i, j)] += li[(j + NG) * F + 3 * m + 2];
+      }
+    }
+  }
+  // Reverse of the x sweep on every row: lam* (interior columns) -> cotangent of padded Q^n.
+  std::vector<double> lamp(pplane * F, 0.0);
+  for (int j = -NG; j < ny + NG; ++j) {
+    std::vector<double> line((nx + 4) * F), Bl(nx + 4), lo(nx * F), li((nx + 4) * F, 0.0), gl(nx + 4, 0.0);
+    for (int i = -NG; i < nx + NG; ++i) {
+      Bl[i + NG] = Bp[pidx(nx, i, j)];
+      for (int f = 0; f < F; ++f) line[(i + NG) * F + f] = qp[f * pplane + pidx(nx, i, j)];
+    }
+    for (int i = 0; i < nx; ++i)
+      for (int f = 0; f < F; ++f) lo[i * F + f] = lams[f * pplane + pidx(nx, i, j)];
+    adjoint_sweep_line(P, nx, line.data(), Bl.data(), dt / dx, lo.data(), li.data(), gl.data());
+    for (int i = -NG; i < nx + NG; ++i) {
+      gBp[pidx(nx, i, j)] += gl[i + NG];
+      for (int f = 0; f < F; ++f) lamp[f * pplane + pidx(nx, i, j)] += li[(i + NG) * F + f];
+    }
+  }
+  // Ghost cells of Q^n are mirrors of interior cells (x ghosts of interior rows first,
+  // then y ghost rows over the full width): fold their cotangents back, in reverse order.
+  for (int i = -NG; i < nx + NG; ++i)
+    for (int gJ = NG; gJ >= 1; --gJ) {
+      const int dN = ny - 1 + gJ, sN = ny - gJ, dS = -gJ, sS = gJ - 1;
+      for (int f = 0; f < F; ++f) {
+        const double sgn = (f % 3 == 2) ? -1.0 : 1.0;
+        lamp[f * pplane + pidx(nx, i, sN)] += sgn * lamp[f * pplane + pidx(nx, i, dN)];
+        lamp[f * pplane + pidx(nx, i, dN)] = 0.0;
+        lamp[f * pplane + pidx(nx, i, sS)] += sgn * lamp[f * pplane + pidx(nx, i, dS)];
+        lamp[f * pplane + pidx(nx, i, dS)] = 0.0;
+      }
+      gBp[pidx(nx, i, sN)] += gBp[pidx(nx, i, dN)]; gBp[pidx(nx, i, dN)] = 0.0;
+      gBp[pidx(nx, i, sS)] += gBp[pidx(nx, i, dS)]; gBp[pidx(nx, i, dS)] = 0.0;
+    }
+  for (int j = 0; j < ny; ++j)
+    for (int gI = NG; gI >= 1; --gI) {
+      const int dE = nx - 1 + gI, sE = nx - gI, dW = -gI, sW = gI - 1;
+      for (int f = 0; f < F; ++f) {
+        const double sgn = (f % 3 == 1) ? -1.0 : 1.0;
+        lamp[f * pplane + pidx(nx, sE, j)] += sgn * lamp[f * pplane + pidx(nx, dE, j)];
+        lamp[f * pplane + pidx(nx, dE, j)] = 0.0;
+        lamp[f * pplane + pidx(nx, sW, j)] += sgn * lamp[f * pplane + pidx(nx, dW, j)];
+        lamp[f * pplane + pidx(nx, dW, j)] = 0.0;
+      }
+      gBp[pidx(nx, sE, j)] += gBp[pidx(nx, dE, j)]; gBp[pidx(nx, dE, j)] = 0.0;
+      gBp[pidx(nx, sW, j)] += gBp[pidx(nx, dW, j)]; gBp[pidx(nx, dW, j)] = 0.0;
+    }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      gB[(size_t)j * nx + i] += gBp[pidx(nx, i, j)];
+      for (int f = 0; f < F; ++f) lam[f * plane + (size_t)j * nx + i] = lamp[f * pplane + pidx(nx, i, j)];
+    }
+}

@@ -1,0 +1,325 @@
+"""GB300-native multilayer shallow-water AMR (arXiv:1803.01450), Python binding.
+
+This module only marshals arguments to the C ABI declared in ``include/mlswe.h``
+(``lib/libmlswe.so``, built in tree by :func:`build`). Every step of the hot
+path runs in the library's CUDA kernels; there is no CPU fallback, and every
+entry point raises if the library or a CUDA device is missing.
+
+PyTorch provides device memory (through the allocator callback of the C ABI)
+and the CUDA stream; nothing else.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build_mod
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmlswe.so")
+
+MLSWE_OK = 0
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ECFL", 5: "ENEGDEPTH", 6: "ENESTING",
+                7: "ETIMEOUT", 8: "EHYPERB", 9: "EMISSING"}
+
+
+class MLSWEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mlswe {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("rho", ctypes.c_double * 4), ("g", ctypes.c_double),
+                ("dry_tol", ctypes.c_double), ("cfl_desired", ctypes.c_double), ("cfl_max", ctypes.c_double),
+                ("order", ctypes.c_int), ("limiter", ctypes.c_int), ("eigen", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("ratio", ctypes.c_int * 4), ("flag_tol", ctypes.c_double),
+                ("regrid_interval", ctypes.c_int), ("n_buf", ctypes.c_int), ("cluster_eff", ctypes.c_double),
+                ("min_side", ctypes.c_int), ("max_side", ctypes.c_int)]
+
+
+class _Domain(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y1", ctypes.c_double), ("nx0", ctypes.c_int), ("ny0", ctypes.c_int)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+@dataclasses.dataclass
+class Config:
+    """Mirror of ``mlswe_config`` (see include/mlswe.h)."""
+    M: int = 2
+    rho: Sequence[float] = (1000.0, 1025.0)
+    g: float = 9.81
+    dry_tol: float = 1e-3
+    cfl_desired: float = 0.9
+    cfl_max: float = 1.0
+    order: int = 2
+    limiter: int = 2
+    eigen: int = 0
+    max_levels: int = 1
+    ratio: Sequence[int] = (4, 4, 4)
+    flag_tol: float = 1e-3
+    regrid_interval: int = 4
+    n_buf: int = 2
+    cluster_eff: float = 0.7
+    min_side: int = 16
+    max_side: int = 64
+
+    def to_c(self) -> _Config:
+        c = _Config()
+        c.M = self.M
+        rho = list(self.rho) + [0.0] * (4 - len(self.rho))
+        for k in range(4):
+            c.rho[k] = rho[k]
+        c.g = self.g; c.dry_tol = self.dry_tol; c.cfl_desired = self.cfl_desired; c.cfl_max = self.cfl_max
+        c.order = self.order; c.limiter = self.limiter; c.eigen = self.eigen; c.max_levels = self.max_levels
+        rat = list(self.ratio) + [2] * (4 - len(self.ratio))
+        for k in range(4):
+            c.ratio[k] = rat[k]
+        c.flag_tol = self.flag_tol; c.regrid_interval = self.regrid_interval; c.n_buf = self.n_buf
+        c.cluster_eff = self.cluster_eff; c.min_side = self.min_side; c.max_side = self.max_side
+        return c
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_H = ctypes.c_void_p
+
+# name -> argtypes (restype is mlswe_status unless stated)
+_SIGS = {
+    "mlswe_create_hierarchy": [ctypes.POINTER(_Config), ctypes.c_int, ctypes.POINTER(_Domain),
+                               ctypes.POINTER(_Allocator), ctypes.c_void_p, ctypes.POINTER(_H)],
+    "mlswe_destroy": [_H],
+    "mlswe_level_shape": [_H, ctypes.c_int, ctypes.c_int, _ip, _ip],
+    "mlswe_set_bathymetry": [_H, ctypes.c_int, _dp],
+    "mlswe_get_bathymetry": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_set_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_get_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_set_patches": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p],
+    "mlswe_get_patches": [_H, ctypes.c_int, ctypes.c_int, _ip, _i32p],
+    "mlswe_set_dt": [_H, ctypes.c_int, _dp],
+    "mlswe_step_level": [_H, ctypes.c_int, _dp, _dp],
+    "mlswe_fill_ghosts": [_H, ctypes.c_int, ctypes.c_double],
+    "mlswe_interp_fine": [_H, ctypes.c_int, ctypes.c_int],
+    "mlswe_average_coarse": [_H, ctypes.c_int, ctypes.c_int],
+    "mlswe_get_flags": [_H, ctypes.c_int, ctypes.c_int, _u8p],
+    "mlswe_regrid": [_H, ctypes.c_int],
+    "mlswe_advance": [_H, ctypes.c_int],
+    "mlswe_get_time": [_H, _dp, _dp],
+    "mlswe_read_gauges": [_H, ctypes.c_int, ctypes.c_int, _dp, _dp],
+    "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
+                     ctypes.POINTER(ctypes.c_longlong)],
+}
+
+KERNEL_CLASSES = ["sweep_x", "sweep_y", "ghost_fill", "interp_fine", "average", "flags", "reflux", "other"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (in tree)."""
+    return _build_mod.build(force=force)
+
+
+def lib():
+    """Load the CUDA library; raises if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MLSWEError(9, f"CUDA library not built: {LIB_PATH} (run paper_1803_01450_gb300.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, args in _SIGS.items():
+        fn = getattr(L, name, None)
+        if fn is None:
+            continue
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.mlswe_last_error.argtypes = [_H]
+    L.mlswe_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list:
+    L = lib()
+    return [n for n in list(_SIGS) + ["mlswe_last_error"] if hasattr(L, n)]
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _torch_allocator():
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = _Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+    return a
+
+
+class Hierarchy:
+    """A set of ensemble members, each a hierarchy of refinement levels (C ABI handle)."""
+
+    def __init__(self, cfg: Config, domains: Sequence[tuple], stream: Optional[int] = None,
+                 use_torch_allocator: bool = True):
+        self.cfg = cfg
+        self.L = lib()
+        doms = (_Domain * len(domains))()
+        for k, d in enumerate(domains):
+            x0, y0, x1, y1, nx0, ny0 = d
+            doms[k] = _Domain(x0, y0, x1, y1, nx0, ny0)
+        self._c_cfg = cfg.to_c()
+        self._alloc = None
+        alloc_ptr = None
+        if use_torch_allocator:
+            import torch
+            if not torch.cuda.is_available():
+                raise MLSWEError(9, "no CUDA device")
+            self._alloc = _torch_allocator()
+            alloc_ptr = ctypes.byref(self._alloc)
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = _H()
+        st = self.L.mlswe_create_hierarchy(ctypes.byref(self._c_cfg), len(domains), doms, alloc_ptr,
+                                           ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if st != MLSWE_OK:
+            raise MLSWEError(st, "mlswe_create_hierarchy failed")
+        self.h = h
+        self.n_members = len(domains)
+        self.M = cfg.M
+
+    def _check(self, st: int, what: str, ok=(MLSWE_OK,)):
+        if st not in ok:
+            raise MLSWEError(st, f"{what}: {self.L.mlswe_last_error(self.h).decode()}")
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mlswe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, member: int, level: int):
+        nx, ny = ctypes.c_int(), ctypes.c_int()
+        self._check(self.L.mlswe_level_shape(self.h, member, level, ctypes.byref(nx), ctypes.byref(ny)), "level_shape")
+        return ny.value, nx.value
+
+    def set_bathymetry(self, member: int, B_finest: np.ndarray):
+        B = np.ascontiguousarray(B_finest, dtype=np.float64)
+        self._check(self.L.mlswe_set_bathymetry(self.h, member, _d(B)), "set_bathymetry")
+
+    def get_bathymetry(self, member: int, level: int) -> np.ndarray:
+        ny, nx = self.shape(member, level)
+        out = np.zeros((ny, nx))
+        self._check(self.L.mlswe_get_bathymetry(self.h, member, level, _d(out)), "get_bathymetry")
+        return out
+
+    def set_state(self, member: int, level: int, q: np.ndarray):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        ny, nx = self.shape(member, level)
+        assert q.shape == (3 * self.M, ny, nx), q.shape
+        self._check(self.L.mlswe_set_state(self.h, member, level, _d(q)), "set_state")
+
+    def get_state(self, member: int, level: int) -> np.ndarray:
+        ny, nx = self.shape(member, level)
+        out = np.zeros((3 * self.M, ny, nx))
+        self._check(self.L.mlswe_get_state(self.h, member, level, _d(out)), "get_state")
+        return out
+
+    def set_patches(self, member: int, level: int, boxes):
+        b = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 4))
+        return self._check(self.L.mlswe_set_patches(self.h, member, level, len(b), b.ctypes.data_as(_i32p)),
+                           "set_patches")
+
+    def get_patches(self, member: int, level: int) -> np.ndarray:
+        n = ctypes.c_int(0)
+        self._check(self.L.mlswe_get_patches(self.h, member, level, ctypes.byref(n), None), "get_patches")
+        out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+        cap = ctypes.c_int(n.value)
+        self._check(self.L.mlswe_get_patches(self.h, member, level, ctypes.byref(cap), out.ctypes.data_as(_i32p)),
+                    "get_patches")
+        return out[: n.value]
+
+    def set_dt(self, level: int, dt):
+        dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, float), (self.n_members,)))
+        self._check(self.L.mlswe_set_dt(self.h, level, _d(dt)), "set_dt")
+
+    def step_level(self, level: int, dt=None, want_cfl: bool = False, allow=(MLSWE_OK,)):
+        dtp = None
+        if dt is not None:
+            dta = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, float), (self.n_members,)))
+            dtp = _d(dta)
+        cfl = np.zeros(self.n_members) if want_cfl else None
+        self._check(self.L.mlswe_step_level(self.h, level, dtp, _d(cfl) if want_cfl else None), "step_level", allow)
+        return cfl
+
+    def fill_ghosts(self, level: int, alpha: float):
+        self._check(self.L.mlswe_fill_ghosts(self.h, level, float(alpha)), "fill_ghosts")
+
+    def interp_fine(self, coarse_level: int, member: int):
+        self._check(self.L.mlswe_interp_fine(self.h, coarse_level, member), "interp_fine")
+
+    def average_coarse(self, fine_level: int, member: int):
+        self._check(self.L.mlswe_average_coarse(self.h, fine_level, member), "average_coarse")
+
+    def get_flags(self, member: int, level: int) -> np.ndarray:
+        ny, nx = self.shape(member, level)
+        out = np.zeros((ny, nx), dtype=np.uint8)
+        self._check(self.L.mlswe_get_flags(self.h, member, level, out.ctypes.data_as(_u8p)), "get_flags")
+        return out
+
+    def regrid(self, base_level: int = 0):
+        self._check(self.L.mlswe_regrid(self.h, base_level), "regrid")
+
+    def advance(self, n_coarse_steps: int, allow=(MLSWE_OK,)):
+        return self._check(self.L.mlswe_advance(self.h, n_coarse_steps), "advance", allow)
+
+    def get_time(self):
+        t = ctypes.c_double()
+        dt = np.zeros(self.n_members)
+        self._check(self.L.mlswe_get_time(self.h, ctypes.byref(t), _d(dt)), "get_time")
+        return t.value, dt
+
+    def timing(self, enable: bool = True):
+        """Per-kernel-class device time (ms) and launches since the last call; resets them."""
+        n = len(KERNEL_CLASSES)
+        ms = np.zeros(n)
+        cnt = (ctypes.c_longlong * n)()
+        tot = ctypes.c_longlong(0)
+        self._check(self.L.mlswe_timing(self.h, int(enable), n, _d(ms), cnt, ctypes.byref(tot)), "timing")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}, int(tot.value)
+
+    def read_gauges(self, member: int, xy: np.ndarray) -> np.ndarray:
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        out = np.zeros((len(xy), self.M))
+        self._check(self.L.mlswe_read_gauges(self.h, member, len(xy), _d(xy), _d(out)), "read_gauges")
+        return out

@@ -1,0 +1,291 @@
+// Device-side data structures and the per-edge multilayer Riemann solver.
+//
+// Paper: arXiv:1803.01450. The paper cites GeoClaw's multilayer solver (Sec. 1)
+// without writing it out; the solver below is this library's reading of it:
+//  * surfaces eta_m = B + h_M + ... + h_m (Sec. 2.1, Eq. (4)), effective
+//    bathymetry Bhat_m = eta_{m+1} (Eq. (5)), top-down wet rule (Sec. 2.1);
+//  * f-waves of the flux jump with the layer coupling folded into the
+//    momentum row: d1_m = D(hn un) + g hbar_m (D eta_m + sum_{n<m} r D h_n);
+//  * all layers wet on both sides (M = 2): 4 acoustic waves of the coupled
+//    normal system, eigenvalues from the closed-form guesses for equal layer
+//    velocities refined by 2 Newton steps on the characteristic quartic, wave
+//    strengths from R beta = delta with eigenvectors (1, l, a, a l),
+//    a = ((l - u1)^2 - g hbar_1) / (g hbar_1), plus one shear wave per layer;
+//  * otherwise every layer alone (Roe speeds), a dry layer whose wet
+//    neighbour's surface lies below the dry cell's effective bathymetry
+//    becomes a reflecting wall for that layer only.
+//
+// GPU specifics (not in the paper): FP64 is the bound on GB300 (about 1/66 of
+// the FP32 rate), so every per-cell quantity (velocities, sqrt(h), surfaces,
+// wet bits) is computed once per cell and staged in shared memory, divisions
+// are reciprocal-and-multiply, and the 4x4 wave-strength system is solved in
+// closed form through its Vandermonde structure instead of by elimination.
+#pragma once
+#include <cstdint>
+
+namespace mlswe {
+
+constexpr int kNG = 2;          // ghost cells per side
+constexpr int kMaxEdges = 256;  // edges per tile (one thread each)
+constexpr int kMaxCells = 288;  // cells per tile (edges + lines, lines <= 32)
+constexpr int kThreads = 256;
+
+struct DevParams {
+  int M;
+  double g;
+  double r;        // rho_1 / rho_2
+  double dry_tol;
+  int order;
+  int limiter;
+  int eigen;
+};
+
+// One (member, level) of the hierarchy: dense arrays over the whole level.
+struct LevelDesc {
+  double* q[2];        // state double buffer [3M][NY][P]
+  double* qs;          // state after the x sweep [3M][NY][P]
+  double* B;           // bathymetry [NY][P]
+  const uint8_t* in_patch;   // [NY][NX] 1 inside a patch of this level (null on level 0)
+  const uint8_t* covered;    // [NY][NX] 1 where a finer patch covers the cell (null if none)
+  double* fxc;         // interface mass flux of this (coarse) level, x edges [M][NY][NX+1]
+  double* fyc;         // y edges [M][NY+1][NX]
+  double* fxf;         // boundary mass flux accumulators of this (fine) level, x edges
+  double* fyf;         // y edges
+  const double* dt;    // device scalar: time step of this member on this level
+  int NX, NY, P;
+  double inv_dx, inv_dy;
+};
+
+// One tile of a sweep: `nlines` lines of `len` cells, along x (x sweep: rows
+// j0.., cells i0..) or along y (y sweep: columns i0.., cells j0..).
+struct SweepItem {
+  int desc;
+  int i0, j0;
+  int len;
+  int nlines;
+  int flags;  // bit 0: interior lines (count CFL, record interface fluxes)
+};
+
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// ----------------------------------------------------------------------------
+// Cell record staged in shared memory (fields already permuted to normal /
+// transverse for the sweep direction).
+// ----------------------------------------------------------------------------
+template <int M>
+struct Rec {
+  static constexpr int H = 0;             // h_m at 3m, hn_m at 3m+1, ht_m at 3m+2
+  static constexpr int UN = 3 * M;        // un_m at UN + 2m, ut_m at UN + 2m + 1
+  static constexpr int SQ = 5 * M;        // sqrt(h_m)
+  static constexpr int ETA = 6 * M;       // eta_m
+  static constexpr int BB = 7 * M;        // B
+  static constexpr int N = 7 * M + 1;
+};
+
+// Compressed waves of one edge: acoustic wave p is
+//   Z_p = (a_p, a_p s_p, a_p vh_1 | b_p, b_p s_p, b_p vh_2),
+// shear wave of layer m is (0, 0, z_m) on layer m with speed us_m.
+template <int M>
+struct EdgeW {
+  static constexpr int NA = 2 * M;
+  double a[NA], b[NA], s[NA];
+  double z[M], us[M], vh[M];
+  int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
+};
+
+template <int M>
+struct WRec {  // shared-memory layout of EdgeW
+  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, N = 9 * M;
+};
+
+// Layer of acoustic slot p in the per-layer (decoupled) branch.
+template <int M>
+__device__ __forceinline__ int layer_of_slot(int p) {
+  return (M == 1) ? 0 : ((p == 0 || p == 3) ? 0 : 1);
+}
+
+// Single-layer f-wave split of (d0, d1, d2) with speeds s1 < s2.
+template <int M>
+__device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, double d1, double d2,
+                                             double s1, double s2, double vh, double us, EdgeW<M>& W) {
+  const double inv = rcp(s2 - s1);
+  const double b1 = (s2 * d0 - d1) * inv;
+  const double b2 = (d1 - s1 * d0) * inv;
+  if (m == 0) { W.a[pa] = b1; W.a[pb] = b2; }
+  else { W.b[pa] = b1; W.b[pb] = b2; }
+  W.s[pa] = s1; W.s[pb] = s2;
+  W.z[m] = d2 - vh * d0;
+  W.us[m] = us;
+  W.vh[m] = vh;
+}
+
+// Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
+template <int M>
+__device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL, const double* cR,
+                                           int wL, int wR, EdgeW<M>& W, int& lost) {
+  using R = Rec<M>;
+  const double g = P.g;
+#pragma unroll
+  for (int p = 0; p < 2 * M; ++p) { W.a[p] = 0.0; W.b[p] = 0.0; W.s[p] = 0.0; }
+#pragma unroll
+  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; }
+  W.wall = 0;
+
+  double d0[M], d1[M], d2[M], hb[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const double hL = cL[3 * m], hR = cR[3 * m];
+    const double hnL = cL[3 * m + 1], hnR = cR[3 * m + 1];
+    hb[m] = 0.5 * (hL + hR);
+    double coup = cR[R::ETA + m] - cL[R::ETA + m];
+    if (m == 1) coup += P.r * (cR[0] - cL[0]);
+    d0[m] = hnR - hnL;
+    d1[m] = (hnR * cR[R::UN + 2 * m] - hnL * cL[R::UN + 2 * m]) + g * hb[m] * coup;
+    d2[m] = hnR * cR[R::UN + 2 * m + 1] - hnL * cL[R::UN + 2 * m + 1];
+  }
+  const int full = (1 << M) - 1;
+  if (M == 2 && wL == full && wR == full) {
+    // ---- coupled two-layer branch ----
+    double uh[2], vh[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+      const double inv = rcp(sl + sr);
+      uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+      vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+    }
+    const double c1 = g * hb[0], c2 = g * hb[1];
+    const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * rcp(hb[0] + hb[1]);
+    const double dc = c1 - c2;
+    const double disc = sqrt(dc * dc + 4.0 * P.r * c1 * c2);
+    const double csum = c1 + c2;
+    const double sp = sqrt(0.5 * (csum + disc)), sm = sqrt(0.5 * (csum - disc));
+    double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+    const double du = uh[0] - uh[1];
+    const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
+    lost += lst ? 1 : 0;
+    if (!lst && P.eigen == 0) {
+      const double rc = P.r * c1 * c2;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        double Pl[4], dP[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
+          const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
+          Pl[p] = f1 * f2 - rc;
+          dP[p] = 2.0 * (a1 * f2 + a2 * f1);
+        }
+        // One reciprocal for the four Newton quotients.
+        const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
+        const double inv = rcp(p01 * p23);
+        const double i01 = inv * p23, i23 = inv * p01;
+        lam[0] -= Pl[0] * (i01 * dP[1]);
+        lam[1] -= Pl[1] * (i01 * dP[0]);
+        lam[2] -= Pl[2] * (i23 * dP[3]);
+        lam[3] -= Pl[3] * (i23 * dP[2]);
+      }
+    }
+    // Wave strengths. With a(l) = (l^2 + p1 l + p0) / c1 (p1 = -2 u1, p0 = u1^2 - c1) the rows
+    // of R beta = delta give the power moments m_k = sum_p beta_p l_p^k, k = 0..3, and
+    // beta_p follows from the Lagrange basis of the four eigenvalues.
+    const double p1 = -2.0 * uh[0], p0 = uh[0] * uh[0] - c1;
+    const double m0 = d0[0], m1 = d1[0];
+    const double m2 = c1 * d0[1] - p1 * m1 - p0 * m0;
+    const double m3 = c1 * d1[1] - p1 * m2 - p0 * m1;
+    const double ic1 = rcp(c1);
+    const double l01 = lam[0] - lam[1], l02 = lam[0] - lam[2], l03 = lam[0] - lam[3];
+    const double l12 = lam[1] - lam[2], l13 = lam[1] - lam[3], l23 = lam[2] - lam[3];
+    double den[4];
+    den[0] = l01 * l02 * l03;
+    den[1] = -l01 * l12 * l13;
+    den[2] = l02 * l12 * l23;
+    den[3] = -l03 * l13 * l23;
+    const double q01 = den[0] * den[1], q23 = den[2] * den[3];
+    const double iall = rcp(q01 * q23);
+    double iden[4];
+    iden[0] = iall * q23 * den[1];
+    iden[1] = iall * q23 * den[0];
+    iden[2] = iall * q01 * den[3];
+    iden[3] = iall * q01 * den[2];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int qa = (p + 1) & 3, qb = (p + 2) & 3, qc = (p + 3) & 3;
+      const double e1 = lam[qa] + lam[qb] + lam[qc];
+      const double e2 = lam[qa] * lam[qb] + lam[qa] * lam[qc] + lam[qb] * lam[qc];
+      const double e3 = lam[qa] * lam[qb] * lam[qc];
+      const double num = m3 - e1 * m2 + e2 * m1 - e3 * m0;
+      const double beta = num * iden[p];
+      const double al = lam[p] - uh[0];
+      const double alpha = (al * al - c1) * ic1;
+      W.a[p] = beta;
+      W.b[p] = beta * alpha;
+      W.s[p] = lam[p];
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      W.z[m] = d2[m] - vh[m] * d0[m];
+      W.us[m] = uh[m];
+      W.vh[m] = vh[m];
+    }
+    return;
+  }
+  // ---- per-layer branch ----
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
+    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
+    const bool wl = (wL >> m) & 1, wr = (wR >> m) & 1;
+    const double hL = cL[3 * m], hR = cR[3 * m];
+    if (wl && wr) {
+      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+      const double inv = rcp(sl + sr);
+      const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+      const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+      const double ch = sqrt(g * hb[m]);
+      split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W);
+    } else if (wl || wr) {
+      const double* cw = wl ? cL : cR;
+      const double* cd = wl ? cR : cL;
+      const double bhat_d = (m == M - 1) ? cd[R::BB] : cd[R::ETA + m + 1];
+      if (cw[R::ETA + m] < bhat_d) {
+        // Wall for this layer: mirror of the wet side, coupling dropped.
+        const double hw = cw[3 * m], hnw = cw[3 * m + 1];
+        const double unw = cw[R::UN + 2 * m], utw = cw[R::UN + 2 * m + 1];
+        // Oriented left -> right: wet left gives (hn, -hn), wet right gives (-hn, hn).
+        const double sgn = wl ? 1.0 : -1.0;
+        const double e0 = -2.0 * sgn * hnw;
+        const double e1 = 0.0 * hnw * unw;
+        const double e2 = -2.0 * sgn * hnw * utw;
+        const double ch = sqrt(g * hw);
+        split_single<M>(m, pa, pb, e0, e1, e2, -ch, ch, utw, 0.0, W);
+        W.wall |= 1 << (2 * m + (wl ? 1 : 0));
+      } else {
+        const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+        const double inv = rcp(sl + sr);
+        const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+        const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+        const double ch = sqrt(g * hb[m]);
+        double s1, s2;
+        if (wl) {
+          const double c = sqrt(g * hL), u = cL[R::UN + 2 * m];
+          s1 = fmin(u - c, uh - ch);
+          s2 = u + 2.0 * c;
+        } else {
+          const double c = sqrt(g * hR), u = cR[R::UN + 2 * m];
+          s1 = u - 2.0 * c;
+          s2 = fmax(u + c, uh + ch);
+        }
+        split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], s1, s2, vh, uh, W);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double limiter_phi(int kind, double th) {
+  if (kind == 0) return 1.0;
+  if (kind == 1) return fmax(0.0, fmin(1.0, th));
+  return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
+}
+
+}  // namespace mlswe

@@ -1,0 +1,457 @@
+// Hierarchy management and the C ABI (see include/mlswe.h).
+//
+// Every level of every member is one dense device array over the whole
+// domain at that level's resolution (GB300's 288 GB of HBM make this cheap
+// for the workloads here); patches are index boxes into it. Sibling patches
+// therefore share their ghost cells in place, and the solver kernels need no
+// patch-to-patch indirection.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include "mlswe_internal.h"
+
+namespace mlswe {
+
+static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
+  if (H) H->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(H, call)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((H), MLSWE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dev_alloc(Hier* H, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (H->own_alloc) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  } else {
+    p = H->alloc.alloc(bytes, (void*)H->st, H->alloc.ctx);
+  }
+  if (p) H->allocations.push_back(p);
+  return p;
+}
+
+void dev_free(Hier* H, void* p) {
+  if (!p) return;
+  auto it = std::find(H->allocations.begin(), H->allocations.end(), p);
+  if (it != H->allocations.end()) H->allocations.erase(it);
+  if (H->own_alloc) cudaFree(p);
+  else H->alloc.free(p, (void*)H->st, H->alloc.ctx);
+}
+
+void timer_begin(Hier* H, int kc, int* token) {
+  H->kernel_launches++;
+  *token = -1;
+  LaunchTimer& T = H->timer;
+  if (!T.on) return;
+  if (T.next + 2 > T.pool.size()) {
+    for (int k = 0; k < 256; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      T.pool.push_back(e);
+    }
+  }
+  const int e0 = (int)T.next++, e1 = (int)T.next++;
+  cudaEventRecord(T.pool[e0], H->st);
+  T.recs.push_back({kc, e0, e1});
+  *token = (int)T.recs.size() - 1;
+}
+
+void timer_end(Hier* H, int token) {
+  if (token < 0) return;
+  LaunchTimer& T = H->timer;
+  cudaEventRecord(T.pool[T.recs[token].e1], H->st);
+}
+
+// Folds recorded events into the per-class totals (synchronises the stream).
+static void timer_collect(Hier* H) {
+  LaunchTimer& T = H->timer;
+  if (T.recs.empty()) return;
+  cudaStreamSynchronize(H->st);
+  for (const auto& r : T.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, T.pool[r.e0], T.pool[r.e1]) == cudaSuccess) {
+      T.ms[r.kc] += ms;
+      T.launches[r.kc] += 1;
+    }
+  }
+  T.recs.clear();
+  T.next = 0;
+}
+
+static mlswe_status upload_desc(Hier* H) {
+  std::vector<LevelDesc> d(H->n_members * H->L);
+  for (int m = 0; m < H->n_members; ++m)
+    for (int l = 0; l < H->L; ++l) {
+      const Level& V = H->mem[m].lev[l];
+      LevelDesc& D = d[H->desc_index(m, l)];
+      D.q[0] = V.q[0]; D.q[1] = V.q[1]; D.qs = V.qs; D.B = V.B;
+      D.in_patch = V.in_patch; D.covered = V.covered;
+      D.fxc = V.fxc; D.fyc = V.fyc; D.fxf = V.fxf; D.fyf = V.fyf;
+      D.dt = H->d_dt + H->desc_index(m, l);
+      D.NX = V.NX; D.NY = V.NY; D.P = V.P;
+      D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
+    }
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_desc, d.data(), d.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  return MLSWE_OK;
+}
+
+static bool valid_member_level(Hier* H, int member, int level) {
+  return H && member >= 0 && member < H->n_members && level >= 0 && level < H->L;
+}
+
+// Sweep work list of one level: tiles over every patch of every member.
+static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out) {
+  out.clear();
+  const TileShape ts = H->shape[dir];
+  for (int m = 0; m < H->n_members; ++m) {
+    const Level& V = H->mem[m].lev[level];
+    const int desc = H->desc_index(m, level);
+    for (const Box& b : V.patches) {
+      if (dir == 0) {
+        // Rows of the patch, plus (refined levels) the two ghost rows on each side that
+        // lie in the domain: the y sweep reads Q* there.
+        const int g = level > 0 ? kNG : 0;
+        const int jlo = std::max(0, b.j0 - g), jhi = std::min(V.NY, b.j1 + g);
+        int j = jlo;
+        while (j < jhi) {
+          const bool inter = j >= b.j0 && j < b.j1;
+          int jend = inter ? b.j1 : (j < b.j0 ? b.j0 : jhi);
+          jend = std::min(jend, jhi);
+          for (int jj = j; jj < jend; jj += ts.lines) {
+            const int nl = std::min(ts.lines, jend - jj);
+            for (int i = b.i0; i < b.i1; i += ts.len) {
+              SweepItem it;
+              it.desc = desc; it.i0 = i; it.j0 = jj; it.len = std::min(ts.len, b.i1 - i);
+              it.nlines = nl; it.flags = inter ? 1 : 0;
+              out.push_back(it);
+            }
+          }
+          j = jend;
+        }
+      } else {
+        for (int i = b.i0; i < b.i1; i += ts.lines) {
+          const int nl = std::min(ts.lines, b.i1 - i);
+          for (int j = b.j0; j < b.j1; j += ts.len) {
+            SweepItem it;
+            it.desc = desc; it.i0 = i; it.j0 = j; it.len = std::min(ts.len, b.j1 - j);
+            it.nlines = nl; it.flags = 1;
+            out.push_back(it);
+          }
+        }
+      }
+    }
+  }
+}
+
+static mlswe_status ensure_worklist(Hier* H, int level, int dir) {
+  Hier::WorkList& W = H->wl[level * 2 + dir];
+  if (!W.dirty) return MLSWE_OK;
+  std::vector<SweepItem> items;
+  build_items(H, level, dir, items);
+  if ((int)items.size() > W.capacity) {
+    if (W.d_items) dev_free(H, W.d_items);
+    const int cap = std::max<int>(1024, (int)items.size() * 5 / 4);
+    W.d_items = (SweepItem*)dev_alloc(H, cap * sizeof(SweepItem));
+    if (!W.d_items) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
+    W.capacity = cap;
+  }
+  if (!W.d_count) {
+    W.d_count = (int*)dev_alloc(H, sizeof(int));
+    if (!W.d_count) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
+  }
+  W.count = (int)items.size();
+  if (!items.empty())
+    CUDA_TRY(H, cudaMemcpyAsync(W.d_items, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(W.d_count, &W.count, sizeof(int), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  W.dirty = false;
+  return MLSWE_OK;
+}
+
+// Launch the two sweeps of one level step (device work only, no host sync).
+mlswe_status enqueue_level_step(Hier* H, int level) {
+  for (int dir = 0; dir < 2; ++dir) {
+    mlswe_status s = ensure_worklist(H, level, dir);
+    if (s != MLSWE_OK) return s;
+  }
+  const int par = H->parity[level];
+  for (int dir = 0; dir < 2; ++dir) {
+    Hier::WorkList& W = H->wl[level * 2 + dir];
+    const int grid = std::min(W.count, H->blocks_per_sm * H->num_sms);
+    if (grid <= 0) continue;
+    int tok;
+    timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
+    CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, grid, par, H->d_smax, H->d_lost, H->st));
+    timer_end(H, tok);
+  }
+  H->parity[level] ^= 1;
+  return MLSWE_OK;
+}
+
+static mlswe_status level_cfl(Hier* H, int level, double* cfl_out, bool* nan_seen) {
+  std::vector<unsigned long long> bits(H->n_members * H->L * 2);
+  CUDA_TRY(H, cudaMemcpyAsync(bits.data(), H->d_smax, bits.size() * 8, cudaMemcpyDeviceToHost, H->st));
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  *nan_seen = false;
+  for (int m = 0; m < H->n_members; ++m) {
+    const int d = H->desc_index(m, level);
+    double sx, sy;
+    std::memcpy(&sx, &bits[2 * d], 8);
+    std::memcpy(&sy, &bits[2 * d + 1], 8);
+    if (std::isnan(sx) || std::isnan(sy)) *nan_seen = true;
+    const Level& V = H->mem[m].lev[level];
+    const double dt = H->h_dt[d];
+    if (cfl_out) cfl_out[m] = dt * std::max(sx / V.dx, sy / V.dy);
+  }
+  return MLSWE_OK;
+}
+
+}  // namespace mlswe
+
+using namespace mlswe;
+
+struct mlswe_hier : public Hier {};
+
+extern "C" {
+
+const char* mlswe_last_error(mlswe_h h) { return h ? h->err.c_str() : "null handle"; }
+
+mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, const mlswe_domain* doms,
+                                    const mlswe_allocator* alloc, void* cuda_stream, mlswe_h* out) {
+  if (!cfg || !doms || !out || n_members <= 0) return MLSWE_EINVAL;
+  *out = nullptr;
+  if (cfg->M < 1 || cfg->M > 2 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
+  if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
+  if (cfg->M == 2 && !(cfg->rho[0] > 0.0 && cfg->rho[0] < cfg->rho[1])) return MLSWE_EINVAL;
+  for (int l = 0; l + 1 < cfg->max_levels; ++l)
+    if (cfg->ratio[l] != 2 && cfg->ratio[l] != 4) return MLSWE_EINVAL;
+  for (int m = 0; m < n_members; ++m)
+    if (doms[m].nx0 < 4 || doms[m].ny0 < 4 || !(doms[m].x1 > doms[m].x0) || !(doms[m].y1 > doms[m].y0))
+      return MLSWE_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MLSWE_EMISSING;
+  mlswe_hier* H = new (std::nothrow) mlswe_hier();
+  if (!H) return MLSWE_ENOMEM;
+  H->cfg = *cfg;
+  H->n_members = n_members;
+  H->L = cfg->max_levels;
+  H->st = (cudaStream_t)cuda_stream;
+  if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
+  H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
+  cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  H->parity.assign(H->L, 0);
+  H->wl.resize(H->L * 2);
+  H->mem.resize(n_members);
+  const int F = 3 * cfg->M;
+  for (int m = 0; m < n_members; ++m) {
+    Member& Mb = H->mem[m];
+    Mb.dom = doms[m];
+    Mb.lev.resize(H->L);
+    int nx = doms[m].nx0, ny = doms[m].ny0;
+    for (int l = 0; l < H->L; ++l) {
+      Level& V = Mb.lev[l];
+      V.NX = nx; V.NY = ny; V.P = (nx + 7) / 8 * 8;
+      V.dx = (doms[m].x1 - doms[m].x0) / nx;
+      V.dy = (doms[m].y1 - doms[m].y0) / ny;
+      const size_t plane = (size_t)V.NY * V.P;
+      V.q[0] = (double*)dev_alloc(H, plane * F * 8);
+      V.q[1] = (double*)dev_alloc(H, plane * F * 8);
+      V.qs = (double*)dev_alloc(H, plane * F * 8);
+      V.B = (double*)dev_alloc(H, plane * 8);
+      if (!V.q[0] || !V.q[1] || !V.qs || !V.B) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+      cudaMemsetAsync(V.q[0], 0, plane * F * 8, H->st);
+      cudaMemsetAsync(V.q[1], 0, plane * F * 8, H->st);
+      cudaMemsetAsync(V.qs, 0, plane * F * 8, H->st);
+      cudaMemsetAsync(V.B, 0, plane * 8, H->st);
+      if (l == 0) V.patches.push_back(Box{0, 0, nx, ny});
+      if (l + 1 < H->L) { nx *= cfg->ratio[l]; ny *= cfg->ratio[l]; }
+    }
+  }
+  const int nd = n_members * H->L;
+  H->d_desc = (LevelDesc*)dev_alloc(H, nd * sizeof(LevelDesc));
+  H->d_dt = (double*)dev_alloc(H, nd * sizeof(double));
+  H->d_smax = (unsigned long long*)dev_alloc(H, nd * 2 * 8);
+  H->d_lost = (unsigned int*)dev_alloc(H, 8);
+  if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_lost) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+  H->h_dt.assign(nd, 0.0);
+  cudaMemsetAsync(H->d_dt, 0, nd * 8, H->st);
+  cudaMemsetAsync(H->d_smax, 0, nd * 16, H->st);
+  cudaMemsetAsync(H->d_lost, 0, 8, H->st);
+  if (upload_desc(H) != MLSWE_OK) { mlswe_destroy(H); return MLSWE_ECUDA; }
+  // Tile shapes: x sweep 61 cells x 4 rows (256 edges), y sweep 8 columns x 29 cells.
+  H->shape[0].len = 61; H->shape[0].lines = 4;
+  H->shape[1].len = 29; H->shape[1].lines = 8;
+  H->blocks_per_sm = 1;
+  *out = H;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_destroy(mlswe_h h) {
+  if (!h) return MLSWE_EINVAL;
+  cudaStreamSynchronize(h->st);
+  for (cudaEvent_t e : h->timer.pool) cudaEventDestroy(e);
+  std::vector<void*> all = h->allocations;
+  for (void* p : all) dev_free(h, p);
+  delete h;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_level_shape(mlswe_h h, int member, int level, int* nx, int* ny) {
+  if (!valid_member_level(h, member, level) || !nx || !ny) return fail(h, MLSWE_EINVAL, "level_shape: bad argument");
+  *nx = h->mem[member].lev[level].NX;
+  *ny = h->mem[member].lev[level].NY;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q) {
+  if (!valid_member_level(h, member, level) || !q) return fail(h, MLSWE_EINVAL, "set_state: bad argument");
+  Level& V = h->mem[member].lev[level];
+  const int F = 3 * h->cfg.M;
+  double* dst = V.q[h->parity[level]];
+  for (int f = 0; f < F; ++f)
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst + (size_t)f * V.NY * V.P, V.P * 8, q + (size_t)f * V.NY * V.NX, V.NX * 8,
+                                  V.NX * 8, V.NY, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out) {
+  if (!valid_member_level(h, member, level) || !q_out) return fail(h, MLSWE_EINVAL, "get_state: bad argument");
+  Level& V = h->mem[member].lev[level];
+  const int F = 3 * h->cfg.M;
+  const double* src = V.q[h->parity[level]];
+  for (int f = 0; f < F; ++f)
+    CUDA_TRY(h, cudaMemcpy2DAsync(q_out + (size_t)f * V.NY * V.NX, V.NX * 8, src + (size_t)f * V.NY * V.P, V.P * 8,
+                                  V.NX * 8, V.NY, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt) {
+  if (!h || level < 0 || level >= h->L || !dt) return fail(h, MLSWE_EINVAL, "set_dt: bad argument");
+  for (int m = 0; m < h->n_members; ++m) h->h_dt[h->desc_index(m, level)] = dt[m];
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_dt, h->h_dt.data(), h->h_dt.size() * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cfl_out) {
+  if (!h || level < 0 || level >= h->L) return fail(h, MLSWE_EINVAL, "step_level: bad argument");
+  if (dt) {
+    mlswe_status s = mlswe_set_dt(h, level, dt);
+    if (s != MLSWE_OK) return s;
+  }
+  CUDA_TRY(h, cudaMemsetAsync(h->d_smax, 0, (size_t)h->n_members * h->L * 16, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_lost, 0, 4, h->st));
+  mlswe_status s = enqueue_level_step(h, level);
+  if (s != MLSWE_OK) return s;
+  if (cfl_out) {
+    bool nan_seen = false;
+    s = level_cfl(h, level, cfl_out, &nan_seen);
+    if (s != MLSWE_OK) return s;
+    if (nan_seen) return fail(h, MLSWE_ENEGDEPTH, "non-finite wave speed in step");
+    for (int m = 0; m < h->n_members; ++m)
+      if (cfl_out[m] > h->cfg.cfl_max) return fail(h, MLSWE_ECFL, "Courant number above cfl_max");
+  }
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long long* launches_out,
+                          long long* total_launches) {
+  if (!h) return MLSWE_EINVAL;
+  timer_collect(h);
+  if (ms_out) for (int k = 0; k < n && k < KC_COUNT; ++k) ms_out[k] = h->timer.ms[k];
+  if (launches_out) for (int k = 0; k < n && k < KC_COUNT; ++k) launches_out[k] = h->timer.launches[k];
+  if (total_launches) *total_launches = h->kernel_launches;
+  for (int k = 0; k < KC_COUNT; ++k) { h->timer.ms[k] = 0.0; h->timer.launches[k] = 0; }
+  h->kernel_launches = 0;
+  h->timer.on = enable != 0;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out) {
+  if (!valid_member_level(h, member, 0) || n < 0 || (n > 0 && (!xy || !eta_out)))
+    return fail(h, MLSWE_EINVAL, "read_gauges: bad argument");
+  if (n == 0) return MLSWE_OK;
+  const Member& Mb = h->mem[member];
+  const int M = h->cfg.M;
+  // Host: finest level whose patch holds each point, and its cell.
+  std::vector<int> cells(3 * n), par(h->n_members * h->L);
+  for (int k = 0; k < (int)par.size(); ++k) par[k] = h->parity[k % h->L];
+  for (int k = 0; k < n; ++k) {
+    const double x = xy[2 * k], y = xy[2 * k + 1];
+    if (!(x >= Mb.dom.x0 && x <= Mb.dom.x1 && y >= Mb.dom.y0 && y <= Mb.dom.y1))
+      return fail(h, MLSWE_EINVAL, "read_gauges: point outside the domain");
+    int best = 0, bi = 0, bj = 0;
+    for (int l = 0; l < h->L; ++l) {
+      const Level& V = Mb.lev[l];
+      const int i = std::min(V.NX - 1, (int)std::floor((x - Mb.dom.x0) / V.dx));
+      const int j = std::min(V.NY - 1, (int)std::floor((y - Mb.dom.y0) / V.dy));
+      bool inside = false;
+      for (const Box& b : V.patches)
+        if (i >= b.i0 && i < b.i1 && j >= b.j0 && j < b.j1) { inside = true; break; }
+      if (inside) { best = l; bi = i; bj = j; }
+    }
+    cells[3 * k] = h->desc_index(member, best);
+    cells[3 * k + 1] = bi;
+    cells[3 * k + 2] = bj;
+  }
+  const size_t need = cells.size() * 4 + par.size() * 4 + (size_t)n * M * 8 + 64;
+  if (need > h->scratch_bytes) {
+    if (h->scratch) dev_free(h, h->scratch);
+    h->scratch = dev_alloc(h, need * 2);
+    if (!h->scratch) return fail(h, MLSWE_ENOMEM, "gauge scratch allocation failed");
+    h->scratch_bytes = need * 2;
+  }
+  char* base = (char*)h->scratch;
+  double* d_out = (double*)base;
+  int* d_cells = (int*)(base + (size_t)n * M * 8);
+  int* d_par = d_cells + cells.size();
+  CUDA_TRY(h, cudaMemcpyAsync(d_cells, cells.data(), cells.size() * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_par, par.data(), par.size() * 4, cudaMemcpyHostToDevice, h->st));
+  int tok;
+  timer_begin(h, KC_OTHER, &tok);
+  CUDA_TRY(h, launch_gauges(M, h->d_desc, d_par, d_cells, n, d_out, h->st));
+  timer_end(h, tok);
+  CUDA_TRY(h, cudaMemcpyAsync(eta_out, d_out, (size_t)n * M * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_bathymetry(mlswe_h h, int member, const double* B_finest) {
+  if (!valid_member_level(h, member, 0) || !B_finest) return fail(h, MLSWE_EINVAL, "set_bathymetry: bad argument");
+  Member& Mb = h->mem[member];
+  Level& Fv = Mb.lev[h->L - 1];
+  CUDA_TRY(h, cudaMemcpy2DAsync(Fv.B, Fv.P * 8, B_finest, Fv.NX * 8, Fv.NX * 8, Fv.NY, cudaMemcpyHostToDevice, h->st));
+  for (int l = h->L - 2; l >= 0; --l) {
+    Level& C = Mb.lev[l];
+    Level& Fn = Mb.lev[l + 1];
+    int tok;
+    timer_begin(h, KC_AVERAGE, &tok);
+    CUDA_TRY(h, launch_average(1, h->cfg.ratio[l], Fn.B, Fn.P, (size_t)Fn.NY * Fn.P, C.B, C.P, (size_t)C.NY * C.P, 0, 0,
+                               C.NX, C.NY, nullptr, 0, h->st));
+    timer_end(h, tok);
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_get_bathymetry(mlswe_h h, int member, int level, double* B_out) {
+  if (!valid_member_level(h, member, level) || !B_out) return fail(h, MLSWE_EINVAL, "get_bathymetry: bad argument");
+  Level& V = h->mem[member].lev[level];
+  CUDA_TRY(h, cudaMemcpy2DAsync(B_out, V.NX * 8, V.B, V.P * 8, V.NX * 8, V.NY, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+}  // extern "C"

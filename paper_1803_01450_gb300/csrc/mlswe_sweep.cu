@@ -1,0 +1,353 @@
+// Dimensionally split finite-volume sweeps over tiles of patches.
+//
+// One sweep (x or y) of the step: for every edge of a line, the Riemann solve
+// of mlswe_device.cuh, then first-order fluctuations plus the second-order
+// wave correction (MC-limited, upwind neighbour of each wave family), then the
+// update of every cell of the line and the positivity fix
+//   Q_i <- Q_i - (dt/dx) (A+dQ_{i-1/2} + A-dQ_{i+1/2}) - (dt/dx)(F_{i+1/2} - F_{i-1/2}).
+// The x sweep writes Q* for the patch rows (and, on refined levels, the two
+// ghost rows on each side); the y sweep reads Q* and writes Q^{n+1}.
+//
+// Layout of one work tile in shared memory: a cell record of Rec<M>::N doubles
+// per cell (structure of arrays), then the compressed waves of every edge,
+// then (reusing the wave space) the left/right cell contributions of every
+// edge. Every thread owns one edge; no CTA ever waits on another.
+#include <cuda_runtime.h>
+#include "mlswe_device.cuh"
+
+namespace mlswe {
+
+template <int DIR>
+__device__ __forceinline__ int cslot(int l, int k, int len, int nl) {
+  return DIR == 0 ? l * (len + 4) + k : k * nl + l;
+}
+template <int DIR>
+__device__ __forceinline__ int eslot(int l, int e, int len, int nl) {
+  return DIR == 0 ? l * (len + 3) + e : e * nl + l;
+}
+template <int DIR>
+__device__ __forceinline__ int gslot(int l, int e, int len, int nl) {
+  return DIR == 0 ? l * (len + 1) + e : e * nl + l;
+}
+
+// Largest |s| of a tile, then one atomicMax on the bit pattern (non-negative doubles order
+// like their unsigned 64-bit patterns).
+__device__ __forceinline__ void block_max_atomic(double v, unsigned long long* dst, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = red[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
+    if (!(m >= 0.0)) m = __longlong_as_double(0x7ff0000000000001ll);  // NaN marker: set all bits high
+    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+  }
+  __syncthreads();
+}
+
+template <int M, int DIR>
+__global__ void __launch_bounds__(kThreads, 1)
+sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
+             const int* __restrict__ n_items_dev, int parity, unsigned long long* smax_bits,
+             unsigned int* lost_count) {
+  using R = Rec<M>;
+  using WR = WRec<M>;
+  constexpr int F = 3 * M;
+  extern __shared__ double smem[];
+  double* cell = smem;                                  // [R::N][kMaxCells]
+  double* wav = cell + R::N * kMaxCells;                // [WR::N][kMaxEdges], reused for contributions
+  int* wallb = reinterpret_cast<int*>(wav + WR::N * kMaxEdges);   // [kMaxEdges]
+  unsigned char* wetb = reinterpret_cast<unsigned char*>(wallb + kMaxEdges);  // [kMaxCells]
+  __shared__ double red[kThreads / 32];
+
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const SweepItem item = items[it];
+    const LevelDesc& D = descs[item.desc];
+    const int len = item.len, nl = item.nlines;
+    const int NX = D.NX, NY = D.NY, Pt = D.P;
+    const size_t plane = (size_t)NY * Pt;
+    const double* __restrict__ qin = DIR == 0 ? D.q[parity] : D.qs;
+    double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
+    const double dt = *D.dt;
+    const double nu = dt * (DIR == 0 ? D.inv_dx : D.inv_dy);
+    const bool interior = item.flags & 1;
+
+    // ---- phase 1: load cells (mirror at walls) and compute the per-cell record ----
+    const int ncell = nl * (len + 4);
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+      int l, k;
+      if (DIR == 0) { l = t / (len + 4); k = t - l * (len + 4); }
+      else { k = t / nl; l = t - k * nl; }
+      int i, j;
+      if (DIR == 0) { i = item.i0 - kNG + k; j = item.j0 + l; }
+      else { i = item.i0 + l; j = item.j0 - kNG + k; }
+      double sgn = 1.0;
+      if (DIR == 0) {
+        if (i < 0) { i = -1 - i; sgn = -1.0; }
+        else if (i >= NX) { i = 2 * NX - 1 - i; sgn = -1.0; }
+      } else {
+        if (j < 0) { j = -1 - j; sgn = -1.0; }
+        else if (j >= NY) { j = 2 * NY - 1 - j; sgn = -1.0; }
+      }
+      const size_t o = (size_t)j * Pt + i;
+      const int c = cslot<DIR>(l, k, len, nl);
+      double rec[R::N];
+      const double Bv = D.B[o];
+      rec[R::BB] = Bv;
+      int wet = 0;
+      bool above = true;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double h = qin[(3 * m) * plane + o];
+        const double hu = qin[(3 * m + 1) * plane + o];
+        const double hv = qin[(3 * m + 2) * plane + o];
+        const double hn = (DIR == 0 ? hu : hv) * sgn;
+        const double ht = DIR == 0 ? hv : hu;
+        rec[3 * m] = h; rec[3 * m + 1] = hn; rec[3 * m + 2] = ht;
+        const bool w = above && (h > P.dry_tol);
+        above = w;
+        wet |= w ? (1 << m) : 0;
+        double un = 0.0, ut = 0.0;
+        if (w) { const double ih = rcp(h); un = hn * ih; ut = ht * ih; }
+        rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
+        rec[R::SQ + m] = sqrt(fmax(h, 0.0));
+      }
+      double acc = Bv;
+#pragma unroll
+      for (int m = M - 1; m >= 0; --m) { acc = acc + rec[3 * m]; rec[R::ETA + m] = acc; }
+#pragma unroll
+      for (int f = 0; f < R::N; ++f) cell[f * kMaxCells + c] = rec[f];
+      wetb[c] = (unsigned char)wet;
+    }
+    __syncthreads();
+
+    // ---- phase 2: Riemann solve at every edge of the tile ----
+    const int nedge = nl * (len + 3);
+    double smax = 0.0;
+    int lost = 0;
+    for (int t = threadIdx.x; t < nedge; t += blockDim.x) {
+      int l, e;
+      if (DIR == 0) { l = t / (len + 3); e = t - l * (len + 3); }
+      else { e = t / nl; l = t - e * nl; }
+      const int cl = cslot<DIR>(l, e, len, nl), cr = cslot<DIR>(l, e + 1, len, nl);
+      double cL[R::N], cR[R::N];
+#pragma unroll
+      for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
+      EdgeW<M> W;
+      int lst = 0;
+      solve_edge<M>(P, cL, cR, wetb[cl], wetb[cr], W, lst);
+      const int es = eslot<DIR>(l, e, len, nl);
+#pragma unroll
+      for (int p = 0; p < 2 * M; ++p) {
+        wav[(WR::A + p) * kMaxEdges + es] = W.a[p];
+        wav[(WR::B + p) * kMaxEdges + es] = W.b[p];
+        wav[(WR::S + p) * kMaxEdges + es] = W.s[p];
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        wav[(WR::Z + m) * kMaxEdges + es] = W.z[m];
+        wav[(WR::US + m) * kMaxEdges + es] = W.us[m];
+        wav[(WR::VH + m) * kMaxEdges + es] = W.vh[m];
+      }
+      wallb[es] = W.wall;
+      if (interior && e >= 1 && e <= len + 1) {
+        double sm = 0.0;
+#pragma unroll
+        for (int p = 0; p < 2 * M; ++p) sm = fmax(sm, fabs(W.s[p]));
+#pragma unroll
+        for (int m = 0; m < M; ++m) sm = fmax(sm, fabs(W.us[m]));
+        smax = fmax(smax, sm);
+        lost += lst;
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 3: fluctuations + limited correction -> left/right cell contributions ----
+    const int ng = nl * (len + 1);
+    double Lc[F], Rc[F];
+    int gl = -1, ge = -1;
+    if (threadIdx.x < ng) {
+      const int t = threadIdx.x;
+      int l, e1;
+      if (DIR == 0) { l = t / (len + 1); e1 = t - l * (len + 1); }
+      else { e1 = t / nl; l = t - e1 * nl; }
+      gl = l; ge = e1;
+      const int e = e1 + 1;
+      const int es = eslot<DIR>(l, e, len, nl);
+      const int esl = eslot<DIR>(l, e - 1, len, nl), esr = eslot<DIR>(l, e + 1, len, nl);
+      const int wall = wallb[es];
+      double vh[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) vh[m] = wav[(WR::VH + m) * kMaxEdges + es];
+      double La = 0, Lsa = 0, Lb = 0, Lsb = 0, Ra = 0, Rsa = 0, Rb = 0, Rsb = 0;
+#pragma unroll
+      for (int p = 0; p < 2 * M; ++p) {
+        const double a = wav[(WR::A + p) * kMaxEdges + es];
+        const double b = wav[(WR::B + p) * kMaxEdges + es];
+        const double s = wav[(WR::S + p) * kMaxEdges + es];
+        double corr = 0.0;
+        const int lay = layer_of_slot<M>(p);
+        const bool walled = (wall >> (2 * lay)) & 3;
+        if (P.order >= 2 && s != 0.0 && !walled) {
+          const int eu = s > 0.0 ? esl : esr;
+          const double au = wav[(WR::A + p) * kMaxEdges + eu];
+          const double bu = wav[(WR::B + p) * kMaxEdges + eu];
+          const double su = wav[(WR::S + p) * kMaxEdges + eu];
+          const double vu0 = wav[(WR::VH + 0) * kMaxEdges + eu];
+          const double ss = 1.0 + s * s, su1 = 1.0 + s * su;
+          double zz = a * a * (ss + vh[0] * vh[0]);
+          double zu = a * au * (su1 + vh[0] * vu0);
+          if (M == 2) {
+            const double vu1 = wav[(WR::VH + (M - 1)) * kMaxEdges + eu];
+            zz += b * b * (ss + vh[M - 1] * vh[M - 1]);
+            zu += b * bu * (su1 + vh[M - 1] * vu1);
+          }
+          const double th = zz > 0.0 ? zu * rcp(zz) : 0.0;
+          const double phi = limiter_phi(P.limiter, th);
+          corr = 0.5 * (s > 0.0 ? 1.0 : -1.0) * (1.0 - nu * fabs(s)) * phi;
+        }
+        const double cl = (s < 0.0 ? 1.0 : (s > 0.0 ? 0.0 : 0.5)) + corr;
+        const double cr = 1.0 - cl;
+        const double ca = cl * a, cb = cl * b, ra = cr * a, rb = cr * b;
+        La += ca; Lsa += ca * s; Lb += cb; Lsb += cb * s;
+        Ra += ra; Rsa += ra * s; Rb += rb; Rsb += rb * s;
+      }
+      double Lz[M], Rz[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double z = wav[(WR::Z + m) * kMaxEdges + es];
+        const double us = wav[(WR::US + m) * kMaxEdges + es];
+        double corr = 0.0;
+        const bool walled = (wall >> (2 * m)) & 3;
+        if (P.order >= 2 && us != 0.0 && !walled) {
+          const int eu = us > 0.0 ? esl : esr;
+          const double zu = wav[(WR::Z + m) * kMaxEdges + eu];
+          const double zz = z * z;
+          const double th = zz > 0.0 ? (zu * z) * rcp(zz) : 0.0;
+          const double phi = limiter_phi(P.limiter, th);
+          corr = 0.5 * (us > 0.0 ? 1.0 : -1.0) * (1.0 - nu * fabs(us)) * phi;
+        }
+        const double cl = (us < 0.0 ? 1.0 : (us > 0.0 ? 0.0 : 0.5)) + corr;
+        Lz[m] = cl * z;
+        Rz[m] = (1.0 - cl) * z;
+      }
+      Lc[0] = La; Lc[1] = Lsa; Lc[2] = vh[0] * La + Lz[0];
+      Rc[0] = Ra; Rc[1] = Rsa; Rc[2] = vh[0] * Ra + Rz[0];
+      if (M == 2) {
+        Lc[3] = Lb; Lc[4] = Lsb; Lc[5] = vh[M - 1] * Lb + Lz[M - 1];
+        Rc[3] = Rb; Rc[4] = Rsb; Rc[5] = vh[M - 1] * Rb + Rz[M - 1];
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        if ((wall >> (2 * m)) & 1) { Lc[3 * m] = 0.0; Lc[3 * m + 1] = 0.0; Lc[3 * m + 2] = 0.0; }
+        if ((wall >> (2 * m + 1)) & 1) { Rc[3 * m] = 0.0; Rc[3 * m + 1] = 0.0; Rc[3 * m + 2] = 0.0; }
+      }
+    }
+    __syncthreads();  // every neighbour read of the waves is done: reuse the space
+    if (gl >= 0) {
+      const int g = gslot<DIR>(gl, ge, len, nl);
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        wav[f * kMaxEdges + g] = Lc[f];
+        wav[(F + f) * kMaxEdges + g] = Rc[f];
+      }
+      // Mass flux of every layer through this edge, seen from the left cell:
+      // hn_L + (A-dQ + F)_h. Recorded at coarse/fine interfaces of this level (for the
+      // reflux of the coarser level) and accumulated, times dt, at the patch boundaries of a
+      // refined level (for the reflux of its parent level).
+      if (interior && (D.covered != nullptr || D.in_patch != nullptr)) {
+        const int a = (DIR == 0 ? item.i0 : item.j0) + ge;  // edge a - 1/2 between cells a-1 and a
+        const int line = DIR == 0 ? item.j0 + gl : item.i0 + gl;
+        const int NA = DIR == 0 ? NX : NY;
+        if (a >= 1 && a <= NA - 1) {
+          const size_t cA = DIR == 0 ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
+          const size_t cB = DIR == 0 ? cA + 1 : cA + NX;
+          const int clft = cslot<DIR>(gl, ge + 1, len, nl);
+          const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
+          const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
+          if (iface || bnd) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              const double fm = cell[(3 * m + 1) * kMaxCells + clft] + Lc[3 * m];
+              const size_t fo = DIR == 0 ? ((size_t)m * NY + line) * (NX + 1) + a
+                                         : ((size_t)m * (NY + 1) + a) * NX + line;
+              if (iface) (DIR == 0 ? D.fxc : D.fyc)[fo] = fm;
+              if (bnd) (DIR == 0 ? D.fxf : D.fyf)[fo] += dt * fm;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 4: update the cells of the tile ----
+    const int nupd = nl * len;
+    for (int t = threadIdx.x; t < nupd; t += blockDim.x) {
+      int l, k;
+      if (DIR == 0) { l = t / len; k = t - l * len; }
+      else { k = t / nl; l = t - k * nl; }
+      const int c = cslot<DIR>(l, k + 2, len, nl);
+      const int gL = gslot<DIR>(l, k, len, nl), gR = gslot<DIR>(l, k + 1, len, nl);
+      double qn[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+        qn[f] = cell[f * kMaxCells + c] - nu * (wav[(F + f) * kMaxEdges + gL] + wav[f * kMaxEdges + gR]);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        if (qn[3 * m] < 0.0) qn[3 * m] = 0.0;
+        if (qn[3 * m] <= P.dry_tol) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
+      }
+      int i, j;
+      if (DIR == 0) { i = item.i0 + k; j = item.j0 + l; }
+      else { i = item.i0 + l; j = item.j0 + k; }
+      const size_t o = (size_t)j * Pt + i;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        qout[(3 * m) * plane + o] = qn[3 * m];
+        qout[(3 * m + 1) * plane + o] = DIR == 0 ? qn[3 * m + 1] : qn[3 * m + 2];
+        qout[(3 * m + 2) * plane + o] = DIR == 0 ? qn[3 * m + 2] : qn[3 * m + 1];
+      }
+    }
+    if (interior) block_max_atomic(smax, &smax_bits[item.desc * 2 + DIR], red);
+    if (lost_count) {
+      for (int o = 16; o > 0; o >>= 1) lost += __shfl_xor_sync(0xffffffffu, lost, o);
+      if ((threadIdx.x & 31) == 0 && lost) atomicAdd(lost_count, (unsigned)lost);
+    }
+    __syncthreads();
+  }
+}
+
+size_t sweep_smem_bytes(int M) {
+  const int rn = 7 * M + 1, wn = 9 * M;
+  return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
+}
+
+template <int M, int DIR>
+static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                                  const int* n_items_dev, int grid, int parity, unsigned long long* smax_bits,
+                                  unsigned int* lost_count, cudaStream_t st) {
+  const size_t sm = sweep_smem_bytes(M);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, smax_bits, lost_count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                         const int* n_items_dev, int grid, int parity, unsigned long long* smax_bits,
+                         unsigned int* lost_count, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  if (P.M == 1)
+    return dir == 0 ? launch_sweep_t<1, 0>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st)
+                    : launch_sweep_t<1, 1>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st);
+  return dir == 0 ? launch_sweep_t<2, 0>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st)
+                  : launch_sweep_t<2, 1>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st);
+}
+
+}  // namespace mlswe
