@@ -1,0 +1,399 @@
+// AMR transfer kernels: refinement of Sec. 2.1 (new fine cells and fine ghost
+// cells), coarsening of Sec. 2.2, refinement flags, patch masks, mass reflux,
+// initial wave speeds. One thread per output cell; work items are boxes.
+#include <cuda_runtime.h>
+#include "mlswe_internal.h"
+
+namespace mlswe {
+
+// ---------------------------------------------------------------------------
+// Refinement, Sec. 2.1 in 2-D. For a fine cell (I, J) of level l+1 inside
+// coarse cell k = (I / r, J / r), for every layer from the bottom up (Sec. 2.1,
+// last paragraph):
+//   eta_m at k and its 4 face neighbours (Eq. (4), summed from the bottom),
+//   slope numerators minmod(eta_k - eta_{k-1}, eta_{k+1} - eta_k) per direction
+//   (Eq. (10) times dx; a neighbour dry in layer m gives a zero difference),
+//   eta_f = eta_k + sx ((a + 1/2)/r - 1/2) + sy ((b + 1/2)/r - 1/2),
+//   Bhat_f = B_f + h_{M,f} + ... + h_{m+1,f} (Eq. (5), fine layers below),
+//   h_{m,f} = max(0, eta_f - Bhat_f);
+// the momenta take the same limited linear reconstruction of the conserved
+// variables and are zero where h_{m,f} <= dry_tol. A layer not wet in k (top-down
+// rule) gives zero depth and momentum. The coarse state is (1-alpha) Q^n + alpha Q^{n+1}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double minmod_d(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) <= fabs(b) ? a : b;
+}
+
+template <int M>
+__device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* qn, double alpha, int i, int j,
+                            double* q /*[3M]*/, double& B) {
+  double sx = 1.0, sy = 1.0;
+  if (i < 0) { i = -1 - i; sx = -1.0; } else if (i >= C.NX) { i = 2 * C.NX - 1 - i; sx = -1.0; }
+  if (j < 0) { j = -1 - j; sy = -1.0; } else if (j >= C.NY) { j = 2 * C.NY - 1 - j; sy = -1.0; }
+  const size_t o = (size_t)j * C.P + i, plane = (size_t)C.NY * C.P;
+  const double a1 = 1.0 - alpha;
+#pragma unroll
+  for (int f = 0; f < 3 * M; ++f) q[f] = a1 * qo[f * plane + o] + alpha * qn[f * plane + o];
+#pragma unroll
+  for (int m = 0; m < M; ++m) { q[3 * m + 1] *= sx; q[3 * m + 2] *= sy; }
+  B = C.B[o];
+}
+
+// mode 0: write every cell of the item box; mode 1: only in-domain cells outside every
+// patch of the fine level (ghost cells).
+template <int M>
+__global__ void interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+                              int n_items, int r, int par_c, int par_f, double alpha, int mode) {
+  constexpr int F = 3 * M;
+  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+    const InterpItem item = items[it];
+    const LevelDesc& C = descs[item.desc_c];
+    const LevelDesc& Fd = descs[item.desc_f];
+    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
+    const long long total = (long long)w * h;
+    const double* qo = C.q[par_c ^ 1];
+    const double* qn = C.q[par_c];
+    double* qf = Fd.q[par_f];
+    const size_t fplane = (size_t)Fd.NY * Fd.P;
+    const double inv_r = 1.0 / (double)r;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int I = item.i0 + (int)(t % w), J = item.j0 + (int)(t / w);
+      if (I < 0 || J < 0 || I >= Fd.NX || J >= Fd.NY) continue;
+      const size_t fo = (size_t)J * Fd.P + I;
+      if (mode == 1 && Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
+      const int ic = I / r, jc = J / r, a = I - ic * r, b = J - jc * r;
+      const double offx = (a + 0.5) * inv_r - 0.5, offy = (b + 0.5) * inv_r - 0.5;
+      // coarse cell k and its face neighbours: 0 = k, 1 = west, 2 = east, 3 = south, 4 = north
+      double q[5][F], Bc[5];
+      coarse_cell<M>(C, qo, qn, alpha, ic, jc, q[0], Bc[0]);
+      coarse_cell<M>(C, qo, qn, alpha, ic - 1, jc, q[1], Bc[1]);
+      coarse_cell<M>(C, qo, qn, alpha, ic + 1, jc, q[2], Bc[2]);
+      coarse_cell<M>(C, qo, qn, alpha, ic, jc - 1, q[3], Bc[3]);
+      coarse_cell<M>(C, qo, qn, alpha, ic, jc + 1, q[4], Bc[4]);
+      const double Bf = Fd.B[fo];
+      double hf[M];
+      double out[F];
+#pragma unroll
+      for (int m = M - 1; m >= 0; --m) {
+        bool wet[5];
+        double eta[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+          bool wt = true;
+#pragma unroll
+          for (int n = 0; n <= m; ++n) wt = wt && (q[c][3 * n] > P.dry_tol);
+          wet[c] = wt;
+          double e = Bc[c];
+#pragma unroll
+          for (int n = M - 1; n >= m; --n) e = e + q[c][3 * n];
+          eta[c] = e;
+        }
+        double hv = 0.0, huv = 0.0, hvv = 0.0;
+        if (wet[0]) {
+          const double sx = minmod_d(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
+          const double sy = minmod_d(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
+          const double ef = eta[0] + sx * offx + sy * offy;
+          double bh = Bf;
+#pragma unroll
+          for (int n = M - 1; n > m; --n) bh = bh + hf[n];
+          hv = fmax(0.0, ef - bh);
+          if (hv > P.dry_tol) {
+            double mom[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              const int f = 3 * m + 1 + k;
+              const double c0 = q[0][f];
+              const double mx = minmod_d(wet[1] ? c0 - q[1][f] : 0.0, wet[2] ? q[2][f] - c0 : 0.0);
+              const double my = minmod_d(wet[3] ? c0 - q[3][f] : 0.0, wet[4] ? q[4][f] - c0 : 0.0);
+              mom[k] = c0 + mx * offx + my * offy;
+            }
+            huv = mom[0];
+            hvv = mom[1];
+          }
+        }
+        hf[m] = hv;
+        out[3 * m] = hv;
+        out[3 * m + 1] = huv;
+        out[3 * m + 2] = hvv;
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) qf[f * fplane + fo] = out[f];
+    }
+  }
+}
+
+cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
+                          long long max_cells, int r, int par_c, int par_f, double alpha, int mode, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
+            (unsigned)std::min(n_items, 65535));
+  if (M == 1) interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items, r, par_c, par_f, alpha, mode);
+  else interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items, r, par_c, par_f, alpha, mode);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Coarsening, Sec. 2.2, Eq. (11) in 2-D: coarse cells under a fine patch take the
+// mean of their r x r fine cells (row-major sum, then times 1/(r r)), every component.
+// Items: (desc_c, desc_f, coarse box).
+// ---------------------------------------------------------------------------
+__global__ void average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+                                     int n_items, int r, int par_c, int par_f) {
+  const double inv = 1.0 / (double)(r * r);
+  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+    const InterpItem item = items[it];
+    const LevelDesc& C = descs[item.desc_c];
+    const LevelDesc& Fd = descs[item.desc_f];
+    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
+    const long long total = (long long)w * h;
+    const double* qf = Fd.q[par_f];
+    double* qc = C.q[par_c];
+    const size_t fplane = (size_t)Fd.NY * Fd.P, cplane = (size_t)C.NY * C.P;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+      for (int f = 0; f < F; ++f) {
+        double s = 0.0;
+        for (int b = 0; b < r; ++b)
+          for (int a = 0; a < r; ++a) s += qf[f * fplane + (size_t)(j * r + b) * Fd.P + (i * r + a)];
+        qc[f * cplane + (size_t)j * C.P + i] = s * inv;
+      }
+    }
+  }
+}
+
+cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
+                                 int r, int par_c, int par_f, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
+            (unsigned)std::min(n_items, 65535));
+  average_items_kernel<<<grid, 256, 0, st>>>(F, descs, items, n_items, r, par_c, par_f);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Refinement flags from the gradient of eta_1 = B + h_M + ... + h_1 (Eq. (4)):
+// flag = gx^2 + gy^2 > tol^2, central differences where both neighbours are usable
+// (in the domain, in a patch of the level, layer 1 wet), one-sided where only one is.
+// Every operation is an explicitly rounded FP64 op (no contraction into FMA), so that
+// the flags are bit-identical to a plain sequential evaluation.
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ double eta1_at(const double* q, size_t plane, const double* B, size_t o) {
+  double e = B[o];
+#pragma unroll
+  for (int n = M - 1; n >= 0; --n) e = __dadd_rn(e, q[(3 * n) * plane + o]);
+  return e;
+}
+
+template <int M>
+__global__ void flags_kernel(const LevelDesc* __restrict__ descs, int desc, int par, double dry_tol, double inv_dx,
+                             double inv_dy, double tol2, uint8_t* __restrict__ flags) {
+  const LevelDesc& D = descs[desc];
+  const long long total = (long long)D.NX * D.NY;
+  const double* q = D.q[par];
+  const size_t plane = (size_t)D.NY * D.P;
+  const double hx = __dmul_rn(0.5, inv_dx), hy = __dmul_rn(0.5, inv_dy);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % D.NX), j = (int)(t / D.NX);
+    auto usable = [&](int ii, int jj) -> bool {
+      if (ii < 0 || jj < 0 || ii >= D.NX || jj >= D.NY) return false;
+      if (D.in_patch && !D.in_patch[(size_t)jj * D.NX + ii]) return false;
+      return q[(size_t)jj * D.P + ii] > dry_tol;
+    };
+    uint8_t fl = 0;
+    if (usable(i, j)) {
+      const size_t o = (size_t)j * D.P + i;
+      const double e = eta1_at<M>(q, plane, D.B, o);
+      const bool l = usable(i - 1, j), rr = usable(i + 1, j), s = usable(i, j - 1), n = usable(i, j + 1);
+      double gx = 0.0, gy = 0.0;
+      if (l && rr) gx = __dmul_rn(__dsub_rn(eta1_at<M>(q, plane, D.B, o + 1), eta1_at<M>(q, plane, D.B, o - 1)), hx);
+      else if (rr) gx = __dmul_rn(__dsub_rn(eta1_at<M>(q, plane, D.B, o + 1), e), inv_dx);
+      else if (l) gx = __dmul_rn(__dsub_rn(e, eta1_at<M>(q, plane, D.B, o - 1)), inv_dx);
+      if (s && n) gy = __dmul_rn(__dsub_rn(eta1_at<M>(q, plane, D.B, o + D.P), eta1_at<M>(q, plane, D.B, o - D.P)), hy);
+      else if (n) gy = __dmul_rn(__dsub_rn(eta1_at<M>(q, plane, D.B, o + D.P), e), inv_dy);
+      else if (s) gy = __dmul_rn(__dsub_rn(e, eta1_at<M>(q, plane, D.B, o - D.P)), inv_dy);
+      const double g2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
+      fl = g2 > tol2 ? 1 : 0;
+    }
+    flags[t] = fl;
+  }
+}
+
+cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long long cells, double dry_tol,
+                         double inv_dx, double inv_dy, double tol2, uint8_t* flags, cudaStream_t st) {
+  const int grid = (int)std::max<long long>(1, std::min<long long>((cells + 255) / 256, 4096));
+  if (M == 1) flags_kernel<1><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
+  else flags_kernel<2><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Masks: set mask cells of every box (level indices, scaled by `scale` division).
+// ---------------------------------------------------------------------------
+__global__ void mask_boxes_kernel(uint8_t* __restrict__ mask, int NX, const int* __restrict__ boxes, int n, int div) {
+  for (int b = blockIdx.y; b < n; b += gridDim.y) {
+    const int i0 = boxes[4 * b] / div, j0 = boxes[4 * b + 1] / div, i1 = boxes[4 * b + 2] / div, j1 = boxes[4 * b + 3] / div;
+    const int w = i1 - i0;
+    const long long total = (long long)w * (j1 - j0);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int i = i0 + (int)(t % w), j = j0 + (int)(t / w);
+      mask[(size_t)j * NX + i] = 1;
+    }
+  }
+}
+
+cudaError_t launch_mask_boxes(uint8_t* mask, int NX, const int* boxes, int n, int div, long long max_cells,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 256)),
+            (unsigned)std::min(n, 65535));
+  mask_boxes_kernel<<<grid, 256, 0, st>>>(mask, NX, boxes, n, div);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Mass reflux of a coarse level: for every uncovered cell of the level next to a
+// covered one, the coarse mass flux recorded at that edge during the coarse step is
+// replaced by the time and space mean of the fine mass fluxes accumulated there:
+//   h_C += +-(dt_c F_c - (1/r) sum_k acc_k) / dx_c.
+// The consumed fine accumulators are zeroed. Items: (desc_c, desc_f, coarse box to scan).
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items, int n_items,
+                              int r, int par_c) {
+  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+    const InterpItem item = items[it];
+    const LevelDesc& C = descs[item.desc_c];
+    const LevelDesc& Fd = descs[item.desc_f];
+    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
+    const long long total = (long long)w * h;
+    double* qc = C.q[par_c];
+    const size_t cplane = (size_t)C.NY * C.P;
+    const double dt_c = *C.dt;
+    const double inv_r = 1.0 / (double)r;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+      const size_t c = (size_t)j * C.NX + i;
+      if (C.covered[c]) continue;
+      if (C.in_patch && !C.in_patch[c]) continue;
+      double dh[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) dh[m] = 0.0;
+      // west edge (i - 1/2): neighbour i-1 covered, this cell on the right: h -= corr
+      if (i > 0 && C.covered[c - 1]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double fine = 0.0;
+          for (int k = 0; k < r; ++k) {
+            const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)i * r;
+            fine += Fd.fxf[fo];
+            Fd.fxf[fo] = 0.0;
+          }
+          const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i];
+          dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dx;
+        }
+      }
+      // east edge (i + 1/2): neighbour i+1 covered, this cell on the left: h += corr
+      if (i + 1 < C.NX && C.covered[c + 1]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double fine = 0.0;
+          for (int k = 0; k < r; ++k) {
+            const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)(i + 1) * r;
+            fine += Fd.fxf[fo];
+            Fd.fxf[fo] = 0.0;
+          }
+          const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i + 1];
+          dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dx;
+        }
+      }
+      if (j > 0 && C.covered[c - C.NX]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double fine = 0.0;
+          for (int k = 0; k < r; ++k) {
+            const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)j * r) * Fd.NX + (size_t)i * r + k;
+            fine += Fd.fyf[fo];
+            Fd.fyf[fo] = 0.0;
+          }
+          const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j) * C.NX + i];
+          dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dy;
+        }
+      }
+      if (j + 1 < C.NY && C.covered[c + C.NX]) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double fine = 0.0;
+          for (int k = 0; k < r; ++k) {
+            const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)(j + 1) * r) * Fd.NX + (size_t)i * r + k;
+            fine += Fd.fyf[fo];
+            Fd.fyf[fo] = 0.0;
+          }
+          const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j + 1) * C.NX + i];
+          dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dy;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m)
+        if (dh[m] != 0.0) qc[(3 * m) * cplane + (size_t)j * C.P + i] += dh[m];
+    }
+  }
+}
+
+cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
+                          int r, int par_c, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
+            (unsigned)std::min(n_items, 65535));
+  if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, items, n_items, r, par_c);
+  else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, items, n_items, r, par_c);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Initial wave speed of every (member, level): max over patch cells of
+// max_m max(|u_m|, |v_m|) + sqrt(g sum_m h_m). Items: (desc, -, patch box).
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void speed_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+                             int n_items, const int* __restrict__ par_of_desc, unsigned long long* __restrict__ out) {
+  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+    const InterpItem item = items[it];
+    const LevelDesc& D = descs[item.desc_c];
+    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
+    const long long total = (long long)w * h;
+    const double* q = D.q[par_of_desc[item.desc_c]];
+    const size_t plane = (size_t)D.NY * D.P;
+    double best = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+      const size_t o = (size_t)j * D.P + i;
+      double htot = 0.0, umax = 0.0;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double hm = q[(3 * m) * plane + o];
+        htot += hm;
+        if (hm > P.dry_tol) {
+          const double u = fabs(q[(3 * m + 1) * plane + o]) / hm, v = fabs(q[(3 * m + 2) * plane + o]) / hm;
+          umax = fmax(umax, fmax(u, v));
+        }
+      }
+      best = fmax(best, umax + sqrt(P.g * fmax(htot, 0.0)));
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&out[item.desc_c], (unsigned long long)__double_as_longlong(best));
+  }
+}
+
+cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
+                         long long max_cells, const int* par_of_desc, unsigned long long* out, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 256)),
+            (unsigned)std::min(n_items, 65535));
+  if (M == 1) speed_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items, par_of_desc, out);
+  else speed_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items, par_of_desc, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mlswe

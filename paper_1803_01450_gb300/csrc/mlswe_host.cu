@@ -219,8 +219,6 @@ static mlswe_status level_cfl(Hier* H, int level, double* cfl_out, bool* nan_see
 
 using namespace mlswe;
 
-struct mlswe_hier : public Hier {};
-
 extern "C" {
 
 const char* mlswe_last_error(mlswe_h h) { return h ? h->err.c_str() : "null handle"; }
@@ -274,6 +272,28 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
       cudaMemsetAsync(V.qs, 0, plane * F * 8, H->st);
       cudaMemsetAsync(V.B, 0, plane * 8, H->st);
       if (l == 0) V.patches.push_back(Box{0, 0, nx, ny});
+      if (H->L > 1) {
+        const int M = cfg->M;
+        const size_t ex = (size_t)M * V.NY * (V.NX + 1) * 8, ey = (size_t)M * (V.NY + 1) * V.NX * 8;
+        if (l > 0) {
+          V.in_patch = (uint8_t*)dev_alloc(H, (size_t)V.NX * V.NY);
+          V.fxf = (double*)dev_alloc(H, ex);
+          V.fyf = (double*)dev_alloc(H, ey);
+          if (!V.in_patch || !V.fxf || !V.fyf) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+          cudaMemsetAsync(V.in_patch, 0, (size_t)V.NX * V.NY, H->st);
+          cudaMemsetAsync(V.fxf, 0, ex, H->st);
+          cudaMemsetAsync(V.fyf, 0, ey, H->st);
+        }
+        if (l + 1 < H->L) {
+          V.covered = (uint8_t*)dev_alloc(H, (size_t)V.NX * V.NY);
+          V.fxc = (double*)dev_alloc(H, ex);
+          V.fyc = (double*)dev_alloc(H, ey);
+          if (!V.covered || !V.fxc || !V.fyc) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+          cudaMemsetAsync(V.covered, 0, (size_t)V.NX * V.NY, H->st);
+          cudaMemsetAsync(V.fxc, 0, ex, H->st);
+          cudaMemsetAsync(V.fyc, 0, ey, H->st);
+        }
+      }
       if (l + 1 < H->L) { nx *= cfg->ratio[l]; ny *= cfg->ratio[l]; }
     }
   }

@@ -15,6 +15,13 @@ struct Box {
   int h() const { return j1 - j0; }
 };
 
+// Work item of the level-transfer kernels: a box of cells of one level (the fine level
+// for refinement, the coarse level for coarsening and reflux) and the two levels involved.
+struct InterpItem {
+  int desc_c, desc_f;
+  int i0, j0, i1, j1;
+};
+
 struct Level {
   int NX = 0, NY = 0, P = 0;
   double dx = 0, dy = 0;
@@ -89,8 +96,13 @@ struct Hier {
   long long coarse_steps = 0;
   LaunchTimer timer;
   long long kernel_launches = 0;   // every kernel this hierarchy launched
-  void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
+  void* scratch = nullptr;         // small per-call device scratch (gauges)
   size_t scratch_bytes = 0;
+  void* stage = nullptr;           // staging of per-launch item tables (AMR kernels)
+  size_t stage_bytes = 0;
+  bool have_rates = false;         // wave-speed rates of the last coarse step are known
+  std::vector<double> last_rates;  // [member * L + level]: max(sx/dx, sy/dy)
+  std::vector<double> last_dt0;    // [member]: last level-0 step
 
   int desc_index(int member, int level) const { return member * L + level; }
 };
@@ -115,3 +127,5 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
                          unsigned int* lost_count, cudaStream_t st);
 
 }  // namespace mlswe
+
+struct mlswe_hier : public mlswe::Hier {};

@@ -1,0 +1,246 @@
+"""Pins of the oracle's AMR pieces against what the paper and the mathematics fix.
+
+Refinement (Sec. 2.1): interpolating eta_m (not h_m) with minmod slopes keeps the
+mean of every coarse cell (so mass away from the shore), creates no new extrema,
+reproduces linear surfaces exactly and reduces to the one-layer scheme. Coarsening
+(Sec. 2.2, Eq. (11)) is the mean of the fine cells of every component. Flags are the
+gradient test of the top surface; clustering boxes cover every buffered flag, are
+disjoint, nested and within the side bounds. The composite AMR solution conserves
+layer masses on walled wet domains and keeps a lake at rest.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import cluster as C
+from oracle.amr import OracleAMR
+from paper_1803_01450_gb300 import inputs as I
+
+
+def _coarse_setup(seed, M=2, n=12, r=4, wet=True):
+    rng = np.random.default_rng(seed)
+    Bf = -10.0 + 0.3 * rng.standard_normal((n * r, n * r))
+    Bc = O.bathy_average(Bf, r)
+    eta2 = -4.0 + 0.2 * rng.standard_normal((n, n))
+    eta1 = 0.0 + 0.2 * rng.standard_normal((n, n))
+    q = np.zeros((3 * M, n, n))
+    if M == 2:
+        q[3] = eta2 - Bc
+        q[0] = eta1 - eta2
+    else:
+        q[0] = eta1 - Bc
+    for m in range(M):
+        q[3 * m + 1] = 0.3 * rng.standard_normal((n, n)) * q[3 * m]
+        q[3 * m + 2] = 0.3 * rng.standard_normal((n, n)) * q[3 * m]
+    return q, Bc, Bf
+
+
+def _interp_all(P, q, Bc, Bf, r):
+    qp, Bp = O.pad(q, Bc)
+    O.fill_walls(P.M, qp, Bp)
+    n = q.shape[1]
+    return O.interp_fine(P, r, qp, Bp, (0, 0, n, n), Bf)
+
+
+@pytest.mark.parametrize("M", [1, 2])
+@pytest.mark.parametrize("r", [2, 4])
+def test_refinement_preserves_cell_means(M, r):
+    """Sec. 2.1: the offsets (a + 1/2)/r - 1/2 sum to zero, so the fine surfaces average to
+    the coarse surface; with B averaged by the same operator and no clipping, the fine
+    depths average to the coarse depth (mass is conserved away from the shore)."""
+    P = O.params(M=M, dry_tol=1e-6)
+    q, Bc, Bf = _coarse_setup(1, M=M, r=r)
+    fine = _interp_all(P, q, Bc, Bf, r)
+    for m in range(M):
+        avg = O.average_coarse(fine[3 * m], r)
+        assert np.abs(avg - q[3 * m]).max() <= 1e-13 * np.abs(q[3 * m]).max()
+        for k in (1, 2):
+            avg = O.average_coarse(fine[3 * m + k], r)
+            assert np.abs(avg - q[3 * m + k]).max() <= 1e-13 * np.abs(q[3 * m + k]).max()
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_refinement_no_new_extrema(r):
+    """Sec. 2.1 (minmod, Eq. (10)): every fine surface value lies within the range of the
+    coarse cell and its face neighbours."""
+    P = O.params(M=2, dry_tol=1e-6)
+    q, Bc, Bf = _coarse_setup(2, r=r)
+    fine = _interp_all(P, q, Bc, Bf, r)
+    n = q.shape[1]
+    eta_c = [Bc + q[3] + q[0], Bc + q[3]]
+    Bf_eta = [Bf + fine[3] + fine[0], Bf + fine[3]]
+    for m in range(2):
+        e = np.pad(eta_c[m], 1, mode="edge")
+        lo = np.minimum.reduce([e[1:-1, 1:-1], e[1:-1, :-2], e[1:-1, 2:], e[:-2, 1:-1], e[2:, 1:-1]])
+        hi = np.maximum.reduce([e[1:-1, 1:-1], e[1:-1, :-2], e[1:-1, 2:], e[:-2, 1:-1], e[2:, 1:-1]])
+        ef = Bf_eta[m].reshape(n, r, n, r)
+        tol = 1e-12 * np.abs(eta_c[m]).max()
+        assert np.all(ef >= lo[:, None, :, None] - tol)
+        assert np.all(ef <= hi[:, None, :, None] + tol)
+
+
+@pytest.mark.parametrize("r", [2, 4])
+def test_refinement_reproduces_linear_surfaces(r):
+    """minmod of two equal differences is that difference: linear surfaces are refined
+    exactly (the offsets are exact binary fractions for r = 2, 4)."""
+    P = O.params(M=2, dry_tol=1e-6)
+    n = 10
+    x = np.arange(n) + 0.5
+    X, Y = np.meshgrid(x, x)
+    Bc = -20.0 * np.ones((n, n))
+    Bf = -20.0 * np.ones((n * r, n * r))
+    eta2 = -8.0 + 0.25 * X - 0.125 * Y
+    eta1 = 0.5 + 0.0625 * X + 0.5 * Y
+    q = np.zeros((6, n, n))
+    q[3] = eta2 - Bc
+    q[0] = eta1 - eta2
+    fine = _interp_all(P, q, Bc, Bf, r)
+    xf = (np.arange(n * r) + 0.5) / r
+    XF, YF = np.meshgrid(xf, xf)
+    sl = slice(r, -r)  # interior coarse cells (the walls flatten the boundary slopes)
+    assert np.abs((Bf + fine[3])[sl, sl] - (-8.0 + 0.25 * XF - 0.125 * YF)[sl, sl]).max() <= 1e-13
+    assert np.abs((Bf + fine[3] + fine[0])[sl, sl] - (0.5 + 0.0625 * XF + 0.5 * YF)[sl, sl]).max() <= 1e-13
+
+
+def test_refinement_two_layers_reduce_to_one():
+    """With the lower layer absent (h_2 = 0), refining two layers equals refining one."""
+    P1, P2 = O.params(M=1, dry_tol=1e-6), O.params(M=2, dry_tol=1e-6)
+    q1, Bc, Bf = _coarse_setup(3, M=1)
+    q2 = np.zeros((6,) + q1.shape[1:])
+    q2[:3] = q1
+    f1 = _interp_all(P1, q1, Bc, Bf, 4)
+    f2 = _interp_all(P2, q2, Bc, Bf, 4)
+    assert np.array_equal(f1, f2[:3])
+    assert not f2[3:].any()
+
+
+def test_coarsening_is_block_mean_and_round_trip():
+    """Sec. 2.2, Eq. (11) in 2-D: the block mean of every component (numpy reshape mean
+    as the reference); coarsening a refinement returns the coarse state."""
+    rng = np.random.default_rng(5)
+    qf = rng.standard_normal((6, 24, 36))
+    avg = O.average_coarse(qf, 4)
+    ref = qf.reshape(6, 6, 4, 9, 4).mean(axis=(2, 4))
+    assert np.abs(avg - ref).max() <= 1e-15 * np.abs(ref).max() * 16
+    P = O.params(M=2, dry_tol=1e-6)
+    q, Bc, Bf = _coarse_setup(6, r=4)
+    back = O.average_coarse(_interp_all(P, q, Bc, Bf, 4), 4)
+    assert np.abs(back - q).max(axis=(1, 2)).max() <= 1e-13 * np.abs(q).max()
+
+
+def test_bathymetry_levels_are_block_means():
+    rng = np.random.default_rng(9)
+    Bf = rng.standard_normal((32, 48))
+    assert np.allclose(O.bathy_average(Bf, 4), Bf.reshape(8, 4, 12, 4).mean(axis=(1, 3)), rtol=1e-14, atol=1e-15)
+
+
+def test_flags_match_numpy_gradient():
+    """Flags of |grad eta_1| > tol on a fully wet level equal numpy.gradient's central /
+    one-sided differences (evaluated with a margin around the threshold)."""
+    w = I.small(50)
+    q, B = w["q"], w["B"]
+    dx = w["dx"]
+    tol = 1e-3
+    fl = O.flags(2, q, B, np.ones((50, 50), np.uint8), 1e-6, dx, dx, tol)
+    eta = B + q[3] + q[0]
+    gy, gx = np.gradient(eta, dx, dx)
+    g2 = gx * gx + gy * gy
+    clear = np.abs(g2 - tol * tol) > 1e-9 * tol * tol
+    assert np.array_equal(fl[clear].astype(bool), (g2 > tol * tol)[clear])
+    assert fl.sum() > 50
+
+
+def _check_boxes(flags, level, patches, r, n_buf, eff, min_side, max_side, boxes, n_nest=2):
+    ny, nx = flags.shape
+    F = C.dilate(flags, n_buf)
+    regs = C.regions(level, nx, ny, patches, n_nest)
+    allowed = np.zeros_like(F)
+    for (i0, j0, i1, j1) in regs:
+        allowed[j0:j1, i0:i1] = True
+    need = F & allowed
+    cov = np.zeros((ny, nx), int)
+    for (a, b, c, d) in boxes:
+        assert a % r == 0 and b % r == 0 and c % r == 0 and d % r == 0
+        ci0, cj0, ci1, cj1 = a // r, b // r, c // r, d // r
+        assert ci1 - ci0 <= max_side // r and cj1 - cj0 <= max_side // r
+        assert any(ci0 >= R[0] and cj0 >= R[1] and ci1 <= R[2] and cj1 <= R[3] for R in regs)
+        cov[cj0:cj1, ci0:ci1] += 1
+    assert cov.max() <= 1, "boxes overlap"
+    assert np.all(cov[need] == 1), "a buffered flag is not covered"
+
+
+def test_dilation_brute_force():
+    rng = np.random.default_rng(11)
+    f = rng.random((9, 11)) < 0.1
+    d = C.dilate(f, 2)
+    for j, i in itertools.product(range(9), range(11)):
+        ref = f[max(0, j - 2):j + 3, max(0, i - 2):i + 3].any()
+        assert d[j, i] == ref
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_clustering_invariants_random(seed):
+    rng = np.random.default_rng(seed)
+    nx, ny = int(rng.integers(20, 70)), int(rng.integers(20, 70))
+    flags = np.zeros((ny, nx), bool)
+    for _ in range(int(rng.integers(1, 5))):
+        cx, cy, rad = rng.integers(0, nx), rng.integers(0, ny), rng.integers(2, 9)
+        Y, X = np.mgrid[0:ny, 0:nx]
+        flags |= (X - cx) ** 2 + (Y - cy) ** 2 < rad ** 2
+    flags &= rng.random((ny, nx)) < 0.8
+    boxes = C.cluster(flags, 0, [(0, 0, nx, ny)], 4, 2, 0.7, 16, 64)
+    _check_boxes(flags, 0, [(0, 0, nx, ny)], 4, 2, 0.7, 16, 64, boxes)
+    # refined level: regions are shrunk patches
+    patches = [(0, 0, nx // 2, ny), (nx // 2, 0, nx, ny // 2)]
+    boxes = C.cluster(flags, 1, patches, 4, 2, 0.7, 16, 64)
+    _check_boxes(flags, 1, patches, 4, 2, 0.7, 16, 64, boxes)
+
+
+def test_clustering_tiny_exhaustive():
+    """Every 4x4 flag pattern (65536 of them) on an 8x8 region with r = 2, min side 2 fine
+    cells: covering, disjoint, inside, efficiency or unsplittable."""
+    nx = ny = 8
+    for bits in range(0, 1 << 16, 7):
+        f = np.zeros((ny, nx), bool)
+        sub = np.array([(bits >> k) & 1 for k in range(16)], bool).reshape(4, 4)
+        f[2:6, 2:6] = sub
+        boxes = C.cluster(f, 0, [(0, 0, nx, ny)], 2, 0, 0.7, 2, 16)
+        _check_boxes(f, 0, [(0, 0, nx, ny)], 2, 0, 0.7, 2, 16, boxes)
+
+
+# ------------------------------------------------------------------ composite AMR
+def test_amr_mass_conservation_with_reflux():
+    """Walled, wet, flat-bottom two-layer AMR run: the composite mass of each layer is
+    constant to rounding (the reflux makes the coarse/fine edges conservative)."""
+    w = I.small(50)
+    P = O.params(M=2, dry_tol=1e-6)
+    A = OracleAMR(P, (0, 0, 1, 1), 50, 50, 2, [2], -np.ones((100, 100)), min_side=16, max_side=64)
+    A.set_state(0, w["q"])
+    m0 = A.mass()
+    A.advance(12, regrid_interval=4)
+    m1 = A.mass()
+    assert len(A.lev[1].patches) > 0
+    assert np.all(np.abs(m1 - m0) <= 1e-13 * m0)
+
+
+def test_amr_lake_at_rest_on_shelf():
+    """Three levels over a shelf at rest: surfaces stay flat, momenta stay zero."""
+    n0, r = 16, [2, 2]
+    nf = n0 * 4
+    Bf = I.shelf_B(np.meshgrid(I.centers(0, 1e5, nf), I.centers(0, 1e5, nf))[0])
+    P = O.params(M=2, dry_tol=1e-3)
+    A = OracleAMR(P, (0, 0, 1e5, 1e5), n0, n0, 3, r, Bf, min_side=8, max_side=32)
+    q0 = I.layered_state(A.lev[0].B, np.zeros_like(A.lev[0].B), -200.0 * np.ones_like(A.lev[0].B))
+    A.set_state(0, q0)
+    A.set_patches(1, [(8, 8, 24, 24)])
+    A.interp_into(0, A.lev[0].q, A.lev[1].in_patch_mask())
+    A.set_patches(2, [(24, 24, 40, 40)])
+    A.interp_into(1, A.lev[1].q, A.lev[2].in_patch_mask())
+    A.advance(4, dt=2.0)
+    for l, V in enumerate(A.lev):
+        m = V.in_patch_mask() if l else np.ones((V.ny, V.nx), bool)
+        eta1 = V.B + V.q[3] + V.q[0]
+        assert np.abs(eta1[m]).max() <= 1e-13 * 4000
+        assert np.abs(V.q[[1, 2, 4, 5]][:, m]).max() <= 1e-13 * 4000
