@@ -106,8 +106,10 @@ typedef struct {
 
 /* Creates a hierarchy of n_members independent members. Level 0 of each
  * member is one patch covering its domain, with walls on all four sides.
- * alloc may be NULL (cudaMalloc is used). stream is a cudaStream_t (NULL:
- * legacy default stream). Errors: EINVAL (config or domain), ENOMEM, ECUDA. */
+ * alloc may be NULL (cudaMalloc is used). stream is a cudaStream_t; NULL makes
+ * the library create (and destroy with the hierarchy) a non-blocking stream of
+ * its own, since the legacy default stream cannot be captured into a CUDA graph.
+ * Errors: EINVAL (config or domain), ENOMEM, ECUDA. */
 mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, const mlswe_domain* doms,
                                     const mlswe_allocator* alloc, void* cuda_stream, mlswe_h* out);
 
@@ -185,12 +187,33 @@ mlswe_status mlswe_regrid(mlswe_h h, int base_level);
  * regrid_interval coarse steps. */
 mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps);
 
-/* Current level-0 time step per member (host [n_members]) and simulated time. */
+/* Simulated time of every member (t_out, host [n_members]) and the level-0 time
+ * step of its next coarse step (dt_out, host [n_members]); either may be NULL. */
 mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out);
+
+/* Execution form of mlswe_advance (not in the paper). use_graphs: capture one
+ * coarse step per level-0 parity as a CUDA graph and replay it (kernels read
+ * their work lists and time steps from device memory, so a regrid needs no
+ * recapture). per_patch_launches: launch the sweeps once per patch instead of
+ * once per level for all patches of all members (the unbatched form, kept for
+ * comparison; disables graphs). */
+mlswe_status mlswe_set_execution(mlswe_h h, int use_graphs, int per_patch_launches);
+
+/* Tile autotuner (not in the paper): times the candidate sweep tiles on the
+ * current patches of `level` (iters launches each, CUDA events, the state is not
+ * advanced) and keeps the fastest per sweep direction. chosen (host int[4], may
+ * be NULL): x len, x lines, y len, y lines. */
+mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
 
 /* Surface elevations eta_m (Eq. (4)) at n points (host [n][2], physical x, y)
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
+
+/* Launch configuration of the sweep kernels (not in the paper): tile of `len`
+ * cells along the sweep direction times `lines` lines (x sweep dir = 0: rows;
+ * y sweep dir = 1: columns), with lines * (len + 3) <= 256 and len >= 4, and
+ * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range. */
+mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm);
 
 /* Launch instrumentation (not in the paper). Returns, and resets, the time in
  * ms and the launch count of each kernel class since the previous call, as

@@ -121,6 +121,9 @@ _SIGS = {
     "mlswe_advance": [_H, ctypes.c_int],
     "mlswe_get_time": [_H, _dp, _dp],
     "mlswe_read_gauges": [_H, ctypes.c_int, ctypes.c_int, _dp, _dp],
+    "mlswe_set_tiles": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
+    "mlswe_set_execution": [_H, ctypes.c_int, ctypes.c_int],
+    "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
     "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
                      ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -304,10 +307,22 @@ class Hierarchy:
         return self._check(self.L.mlswe_advance(self.h, n_coarse_steps), "advance", allow)
 
     def get_time(self):
-        t = ctypes.c_double()
+        """(simulated time per member, next level-0 time step per member)."""
+        t = np.zeros(self.n_members)
         dt = np.zeros(self.n_members)
-        self._check(self.L.mlswe_get_time(self.h, ctypes.byref(t), _d(dt)), "get_time")
-        return t.value, dt
+        self._check(self.L.mlswe_get_time(self.h, _d(t), _d(dt)), "get_time")
+        return t, dt
+
+    def set_execution(self, use_graphs: bool = True, per_patch_launches: bool = False):
+        self._check(self.L.mlswe_set_execution(self.h, int(use_graphs), int(per_patch_launches)), "set_execution")
+
+    def autotune(self, level: int, iters: int = 5):
+        out = (ctypes.c_int * 4)()
+        self._check(self.L.mlswe_autotune(self.h, level, iters, out), "autotune")
+        return tuple(out)
+
+    def set_tiles(self, dir: int, length: int, lines: int, ctas_per_sm: int = 1):
+        self._check(self.L.mlswe_set_tiles(self.h, dir, length, lines, ctas_per_sm), "set_tiles")
 
     def timing(self, enable: bool = True):
         """Per-kernel-class device time (ms) and launches since the last call; resets them."""

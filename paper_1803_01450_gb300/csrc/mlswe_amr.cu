@@ -1,6 +1,11 @@
 // AMR transfer kernels: refinement of Sec. 2.1 (new fine cells and fine ghost
 // cells), coarsening of Sec. 2.2, refinement flags, patch masks, mass reflux,
-// initial wave speeds. One thread per output cell; work items are boxes.
+// wave speeds and the device-side time step.
+//
+// All box kernels are persistent: a fixed grid loops over a device-resident
+// item table whose length is read from device memory, so a captured CUDA
+// graph stays valid when a regrid rewrites the tables. One CTA works on one
+// item (a box of at most 64 x 64 cells) at a time, one thread per cell.
 #include <cuda_runtime.h>
 #include "mlswe_internal.h"
 
@@ -41,24 +46,26 @@ __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* 
 }
 
 // mode 0: write every cell of the item box; mode 1: only in-domain cells outside every
-// patch of the fine level (ghost cells).
+// patch of the fine level (ghost cells). alpha < 0: read alpha from alpha_dev.
 template <int M>
-__global__ void interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-                              int n_items, int r, int par_c, int par_f, double alpha, int mode) {
+__global__ void __launch_bounds__(256)
+interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha, int mode) {
   constexpr int F = 3 * M;
-  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+  const int n_items = *n_items_dev;
+  const double inv_r = 1.0 / (double)r;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const long long total = (long long)w * h;
+    const int total = w * h;
     const double* qo = C.q[par_c ^ 1];
     const double* qn = C.q[par_c];
     double* qf = Fd.q[par_f];
     const size_t fplane = (size_t)Fd.NY * Fd.P;
-    const double inv_r = 1.0 / (double)r;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-      const int I = item.i0 + (int)(t % w), J = item.j0 + (int)(t / w);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int I = item.i0 + t % w, J = item.j0 + t / w;
       if (I < 0 || J < 0 || I >= Fd.NX || J >= Fd.NY) continue;
       const size_t fo = (size_t)J * Fd.P + I;
       if (mode == 1 && Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
@@ -123,13 +130,11 @@ __global__ void interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, 
   }
 }
 
-cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
-                          long long max_cells, int r, int par_c, int par_f, double alpha, int mode, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
-            (unsigned)std::min(n_items, 65535));
-  if (M == 1) interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items, r, par_c, par_f, alpha, mode);
-  else interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items, r, par_c, par_f, alpha, mode);
+cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
+                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
+                          cudaStream_t st) {
+  if (M == 1) interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
+  else interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
   return cudaGetLastError();
 }
 
@@ -138,20 +143,22 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
 // mean of their r x r fine cells (row-major sum, then times 1/(r r)), every component.
 // Items: (desc_c, desc_f, coarse box).
 // ---------------------------------------------------------------------------
-__global__ void average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-                                     int n_items, int r, int par_c, int par_f) {
+__global__ void __launch_bounds__(256)
+average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+                     const int* __restrict__ n_items_dev, int r, int par_c, int par_f) {
   const double inv = 1.0 / (double)(r * r);
-  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const long long total = (long long)w * h;
+    const int total = w * h;
     const double* qf = Fd.q[par_f];
     double* qc = C.q[par_c];
     const size_t fplane = (size_t)Fd.NY * Fd.P, cplane = (size_t)C.NY * C.P;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = item.i0 + t % w, j = item.j0 + t / w;
       for (int f = 0; f < F; ++f) {
         double s = 0.0;
         for (int b = 0; b < r; ++b)
@@ -162,12 +169,9 @@ __global__ void average_items_kernel(int F, const LevelDesc* __restrict__ descs,
   }
 }
 
-cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
-                                 int r, int par_c, int par_f, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
-            (unsigned)std::min(n_items, 65535));
-  average_items_kernel<<<grid, 256, 0, st>>>(F, descs, items, n_items, r, par_c, par_f);
+cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
+                                 int grid, int r, int par_c, int par_f, cudaStream_t st) {
+  average_items_kernel<<<grid, 256, 0, st>>>(F, descs, items, n_items_dev, r, par_c, par_f);
   return cudaGetLastError();
 }
 
@@ -229,7 +233,7 @@ cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long 
 }
 
 // ---------------------------------------------------------------------------
-// Masks: set mask cells of every box (level indices, scaled by `scale` division).
+// Masks: set mask cells of every box (level indices divided by `div`).
 // ---------------------------------------------------------------------------
 __global__ void mask_boxes_kernel(uint8_t* __restrict__ mask, int NX, const int* __restrict__ boxes, int n, int div) {
   for (int b = blockIdx.y; b < n; b += gridDim.y) {
@@ -260,20 +264,22 @@ cudaError_t launch_mask_boxes(uint8_t* mask, int NX, const int* boxes, int n, in
 // The consumed fine accumulators are zeroed. Items: (desc_c, desc_f, coarse box to scan).
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items, int n_items,
-                              int r, int par_c) {
-  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+__global__ void __launch_bounds__(256)
+reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+              const int* __restrict__ n_items_dev, int r, int par_c) {
+  const int n_items = *n_items_dev;
+  const double inv_r = 1.0 / (double)r;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const long long total = (long long)w * h;
+    const int total = w * h;
     double* qc = C.q[par_c];
     const size_t cplane = (size_t)C.NY * C.P;
     const double dt_c = *C.dt;
-    const double inv_r = 1.0 / (double)r;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = item.i0 + t % w, j = item.j0 + t / w;
       const size_t c = (size_t)j * C.NX + i;
       if (C.covered[c]) continue;
       if (C.in_patch && !C.in_patch[c]) continue;
@@ -341,33 +347,34 @@ __global__ void reflux_kernel(const LevelDesc* __restrict__ descs, const InterpI
   }
 }
 
-cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
+cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev, int grid,
                           int r, int par_c, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 1024)),
-            (unsigned)std::min(n_items, 65535));
-  if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, items, n_items, r, par_c);
-  else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, items, n_items, r, par_c);
+  if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
+  else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Initial wave speed of every (member, level): max over patch cells of
-// max_m max(|u_m|, |v_m|) + sqrt(g sum_m h_m). Items: (desc, -, patch box).
+// Wave speed of the state of every (member, level) before its first step:
+// max over patch cells of max_m max(|u_m|, |v_m|) + sqrt(g sum_m h_m).
+// Items: (desc, -, box); the level's parity of each desc in par_of_desc.
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void speed_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-                             int n_items, const int* __restrict__ par_of_desc, unsigned long long* __restrict__ out) {
-  for (int it = blockIdx.y; it < n_items; it += gridDim.y) {
+__global__ void __launch_bounds__(256)
+speed_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+             const int* __restrict__ n_items_dev, const int* __restrict__ par_of_desc,
+             unsigned long long* __restrict__ out) {
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const InterpItem item = items[it];
     const LevelDesc& D = descs[item.desc_c];
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const long long total = (long long)w * h;
+    const int total = w * h;
     const double* q = D.q[par_of_desc[item.desc_c]];
     const size_t plane = (size_t)D.NY * D.P;
     double best = 0.0;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-      const int i = item.i0 + (int)(t % w), j = item.j0 + (int)(t / w);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int i = item.i0 + t % w, j = item.j0 + t / w;
       const size_t o = (size_t)j * D.P + i;
       double htot = 0.0, umax = 0.0;
 #pragma unroll
@@ -386,13 +393,91 @@ __global__ void speed_kernel(DevParams P, const LevelDesc* __restrict__ descs, c
   }
 }
 
-cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
-                         long long max_cells, const int* par_of_desc, unsigned long long* out, cudaStream_t st) {
-  if (n_items <= 0) return cudaSuccess;
-  dim3 grid((unsigned)std::max<long long>(1, std::min<long long>((max_cells + 255) / 256, 256)),
-            (unsigned)std::min(n_items, 65535));
-  if (M == 1) speed_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items, par_of_desc, out);
-  else speed_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items, par_of_desc, out);
+cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
+                         const int* n_items_dev, int grid, const int* par_of_desc, unsigned long long* out,
+                         cudaStream_t st) {
+  if (M == 1) speed_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
+  else speed_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Device-side time step, one thread per member, at the start of every coarse step.
+// From the largest wave speeds of the previous coarse step (smax bits [desc][x, y])
+// or, right after the state was set, from the speeds of the state (init_bits [desc],
+// selected by *init_flag, which is then cleared):
+//   rate_l = max(sx/dx_l, sy/dy_l)        (state speeds: s * max(1/dx_l, 1/dy_l))
+//   dt_0   = cfl * min_l (prod_{k<l} r_k) / rate_l   over levels that have patches now,
+//   dt_l   = dt_0 / prod_{k<l} r_k.
+// The speed slots are then cleared for the step.
+// ---------------------------------------------------------------------------
+__global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const unsigned long long* init_bits,
+                                int* init_flag, double* dt) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool initial = *init_flag != 0;
+  __syncthreads();
+  if (m < A.n_members) {
+    double best = INFINITY, fac = 1.0;
+    for (int l = 0; l < A.L; ++l) {
+      if (l > 0) fac *= A.ratio[l - 1];
+      const int d = m * A.L + l;
+      if (!A.has_patches[d]) continue;
+      double rate;
+      if (initial) {
+        const double s = __longlong_as_double((long long)init_bits[d]);
+        rate = s * fmax(A.inv_dx[d], A.inv_dy[d]);
+      } else {
+        const double sx = __longlong_as_double((long long)smax_bits[2 * d]);
+        const double sy = __longlong_as_double((long long)smax_bits[2 * d + 1]);
+        rate = fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]);
+      }
+      if (rate > 0.0) best = fmin(best, fac / rate);
+    }
+    const double dt0 = isfinite(best) ? A.cfl * best : 0.0;
+    double dl = dt0;
+    for (int l = 0; l < A.L; ++l) {
+      if (l > 0) dl /= A.ratio[l - 1];
+      dt[m * A.L + l] = dl;
+      smax_bits[2 * (m * A.L + l)] = 0ull;
+      smax_bits[2 * (m * A.L + l) + 1] = 0ull;
+    }
+  }
+}
+
+// End of a coarse step: Courant number reached by every member (status bit 0 when
+// above cfl_max, bit 1 when a wave speed was not finite) and the member's time.
+__global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, const double* dt, double* t_member,
+                                double* cfl_reached, unsigned int* status) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= A.n_members) return;
+  double reached = 0.0;
+  bool bad = false;
+  for (int l = 0; l < A.L; ++l) {
+    const int d = m * A.L + l;
+    const double sx = __longlong_as_double((long long)smax_bits[2 * d]);
+    const double sy = __longlong_as_double((long long)smax_bits[2 * d + 1]);
+    if (!(sx >= 0.0) || !(sy >= 0.0)) bad = true;
+    reached = fmax(reached, dt[d] * fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]));
+  }
+  cfl_reached[m] = reached;
+  if (reached > A.cfl_max) atomicOr(status, 1u);
+  if (bad) atomicOr(status, 2u);
+  t_member[m] += dt[m * A.L];
+}
+
+cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
+                            int* init_flag, double* dt, cudaStream_t st) {
+  // a single CTA reads the flag, then its thread 0 clears it after everyone has read it
+  if (A.n_members > 1024) return cudaErrorInvalidValue;
+  dt_begin_kernel<<<1, ((A.n_members + 31) / 32) * 32, 0, st>>>(A, smax_bits, init_bits, init_flag, dt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(init_flag, 0, sizeof(int), st);
+}
+
+cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
+                            double* cfl_reached, unsigned int* status, cudaStream_t st) {
+  step_end_kernel<<<(A.n_members + 127) / 128, 128, 0, st>>>(A, smax_bits, dt, t_member, cfl_reached, status);
   return cudaGetLastError();
 }
 

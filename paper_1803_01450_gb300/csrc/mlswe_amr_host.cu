@@ -1,5 +1,6 @@
-// Host side of the AMR: patch layouts and masks, ghost fill, refinement,
-// coarsening, reflux, regridding and the subcycled Berger-Oliger driver.
+// Host side of the AMR: patch layouts and masks, work-item tables of the level
+// transfer kernels, the subcycled Berger-Oliger coarse step (captured once per
+// level-0 parity as a CUDA graph and replayed), regridding and the tile autotuner.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -7,24 +8,27 @@
 
 namespace mlswe {
 
-cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
-                          long long max_cells, int r, int par_c, int par_f, double alpha, int mode, cudaStream_t st);
-cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
-                                 int r, int par_c, int par_f, cudaStream_t st);
+cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
+                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
+                          cudaStream_t st);
+cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
+                                 int grid, int r, int par_c, int par_f, cudaStream_t st);
 cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long long cells, double dry_tol,
                          double inv_dx, double inv_dy, double tol2, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_mask_boxes(uint8_t* mask, int NX, const int* boxes, int n, int div, long long max_cells,
                               cudaStream_t st);
-cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, int n_items, long long max_cells,
+cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev, int grid,
                           int r, int par_c, cudaStream_t st);
-cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items, int n_items,
-                         long long max_cells, const int* par_of_desc, unsigned long long* out, cudaStream_t st);
+cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
+                         const int* n_items_dev, int grid, const int* par_of_desc, unsigned long long* out,
+                         cudaStream_t st);
 std::vector<Box> cluster_flags(const uint8_t* flags, int nx, int ny, int level, const std::vector<Box>& patches,
                                int r, int n_buf, double eff, int min_side, int max_side, int n_nest);
 std::vector<Box> box_difference(const Box& a, const std::vector<Box>& sub);
-mlswe_status enqueue_level_step(Hier* H, int level);
+void set_level_shape(Hier* H, int level, int dir, int len, int lines);
 
-constexpr int kNest = 2;  // nesting margin in coarse cells
+constexpr int kNest = 2;    // nesting margin in coarse cells
+constexpr int kChunk = 64;  // largest side of a level-transfer work item
 
 static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
   if (H) H->err = msg;
@@ -38,35 +42,76 @@ static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
       return fail((H), MLSWE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-// Device staging buffer for small per-launch tables (items, boxes), grown on demand.
-static void* staging(Hier* H, size_t bytes) {
-  if (bytes > H->stage_bytes) {
-    if (H->stage) dev_free(H, H->stage);
-    H->stage_bytes = std::max<size_t>(bytes * 2, 1 << 16);
-    H->stage = dev_alloc(H, H->stage_bytes);
-    if (!H->stage) H->stage_bytes = 0;
-  }
-  return H->stage;
+static int grid_full(Hier* H) { return 2 * H->num_sms; }
+
+// Appends the chunks (sides <= kChunk) of box b as items.
+static void push_chunks(std::vector<InterpItem>& v, int dc, int df, Box b) {
+  for (int j = b.j0; j < b.j1; j += kChunk)
+    for (int i = b.i0; i < b.i1; i += kChunk)
+      v.push_back(InterpItem{dc, df, i, j, std::min(i + kChunk, b.i1), std::min(j + kChunk, b.j1)});
 }
 
-template <class T>
-static mlswe_status upload_items(Hier* H, const std::vector<T>& v, T** dptr) {
-  *dptr = nullptr;
-  if (v.empty()) return MLSWE_OK;
-  // Several tables may be in flight on the stream: copy into a fresh region each time
-  // is avoided by synchronising before reuse of the staging buffer.
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  void* p = staging(H, v.size() * sizeof(T));
-  if (!p) return fail(H, MLSWE_ENOMEM, "staging allocation failed");
-  CUDA_TRY(H, cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, H->st));
-  *dptr = (T*)p;
+static mlswe_status upload_table(Hier* H, DevTable<InterpItem>& T, const std::vector<InterpItem>& v) {
+  if ((int)v.size() > T.cap || !T.d) {
+    if (T.d) dev_free(H, T.d);
+    T.cap = std::max<int>(256, (int)v.size() * 3 / 2);
+    T.d = (InterpItem*)dev_alloc(H, T.cap * sizeof(InterpItem));
+    if (!T.d) return fail(H, MLSWE_ENOMEM, "item table allocation failed");
+    invalidate_graphs(H);
+  }
+  if (!T.d_count) {
+    T.d_count = (int*)dev_alloc(H, sizeof(int));
+    if (!T.d_count) return fail(H, MLSWE_ENOMEM, "item table allocation failed");
+  }
+  T.count = (int)v.size();
+  if (!v.empty())
+    CUDA_TRY(H, cudaMemcpyAsync(T.d, v.data(), v.size() * sizeof(InterpItem), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(T.d_count, &T.count, sizeof(int), cudaMemcpyHostToDevice, H->st));
   return MLSWE_OK;
 }
 
-static long long max_cells_of(const std::vector<InterpItem>& v) {
-  long long m = 0;
-  for (const auto& it : v) m = std::max<long long>(m, (long long)(it.i1 - it.i0) * (it.j1 - it.j0));
-  return m;
+// Rebuilds every level-transfer table from the current patch layouts (host -> device,
+// synchronous). Graphs stay valid unless a table had to grow.
+static mlswe_status build_tables(Hier* H) {
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  std::vector<int> has(H->n_members * H->L, 0);
+  std::vector<InterpItem> speed;
+  for (int l = 0; l < H->L; ++l) {
+    std::vector<InterpItem> ghost, avg, refl;
+    for (int m = 0; m < H->n_members; ++m) {
+      const Level& V = H->mem[m].lev[l];
+      const int d = H->desc_index(m, l);
+      has[d] = V.patches.empty() ? 0 : 1;
+      for (const Box& b : V.patches) push_chunks(speed, d, d, b);
+      if (l > 0) {
+        const int dc = H->desc_index(m, l - 1);
+        const int r = H->cfg.ratio[l - 1];
+        for (const Box& b : V.patches) {
+          // ghost ring as four strips, clipped to the domain
+          const int gi0 = std::max(0, b.i0 - kNG), gi1 = std::min(V.NX, b.i1 + kNG);
+          const Box strips[4] = {Box{gi0, std::max(0, b.j0 - kNG), gi1, b.j0},
+                                 Box{gi0, b.j1, gi1, std::min(V.NY, b.j1 + kNG)},
+                                 Box{gi0, b.j0, b.i0, b.j1},
+                                 Box{b.i1, b.j0, gi1, b.j1}};
+          for (const Box& s : strips)
+            if (s.i1 > s.i0 && s.j1 > s.j0) push_chunks(ghost, dc, d, s);
+          push_chunks(avg, dc, d, Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
+        }
+      }
+      if (l + 1 < H->L && !H->mem[m].lev[l + 1].patches.empty())
+        for (const Box& b : V.patches) push_chunks(refl, d, H->desc_index(m, l + 1), b);
+    }
+    mlswe_status s = upload_table(H, H->t_ghost[l], ghost);
+    if (s == MLSWE_OK) s = upload_table(H, H->t_avg[l], avg);
+    if (s == MLSWE_OK) s = upload_table(H, H->t_reflux[l], refl);
+    if (s != MLSWE_OK) return s;
+  }
+  mlswe_status s = upload_table(H, H->t_speed, speed);
+  if (s != MLSWE_OK) return s;
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_has, has.data(), has.size() * 4, cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  H->tables_dirty = false;
+  return MLSWE_OK;
 }
 
 // Rebuilds in_patch of (member, level) and covered of (member, level - 1).
@@ -78,9 +123,10 @@ static mlswe_status rebuild_masks(Hier* H, int member, int level) {
   CUDA_TRY(H, cudaMemsetAsync(V.in_patch, 0, (size_t)V.NX * V.NY, H->st));
   CUDA_TRY(H, cudaMemsetAsync(C.covered, 0, (size_t)C.NX * C.NY, H->st));
   if (!b.empty()) {
-    int* d = nullptr;
-    mlswe_status s = upload_items(H, b, &d);
-    if (s != MLSWE_OK) return s;
+    int* d = (int*)scratch_buffer(H, b.size() * 4);
+    if (!d) return fail(H, MLSWE_ENOMEM, "scratch allocation failed");
+    CUDA_TRY(H, cudaStreamSynchronize(H->st));
+    CUDA_TRY(H, cudaMemcpyAsync(d, b.data(), b.size() * 4, cudaMemcpyHostToDevice, H->st));
     long long mc = 0;
     for (const Box& x : V.patches) mc = std::max<long long>(mc, (long long)x.w() * x.h());
     int tok;
@@ -90,10 +136,11 @@ static mlswe_status rebuild_masks(Hier* H, int member, int level) {
     timer_begin(H, KC_OTHER, &tok);
     CUDA_TRY(H, launch_mask_boxes(C.covered, C.NX, d, (int)V.patches.size(), H->cfg.ratio[level - 1], mc, H->st));
     timer_end(H, tok);
-    CUDA_TRY(H, cudaStreamSynchronize(H->st));
   }
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
   H->wl[level * 2].dirty = H->wl[level * 2 + 1].dirty = true;
   H->wl[(level - 1) * 2].dirty = H->wl[(level - 1) * 2 + 1].dirty = true;
+  H->tables_dirty = true;
   return MLSWE_OK;
 }
 
@@ -129,38 +176,35 @@ static mlswe_status check_layout(Hier* H, int member, int level, const std::vect
   return MLSWE_OK;
 }
 
-mlswe_status set_patches_internal(Hier* H, int member, int level, const std::vector<Box>& boxes) {
+static mlswe_status set_patches_internal(Hier* H, int member, int level, const std::vector<Box>& boxes) {
   mlswe_status s = check_layout(H, member, level, boxes);
   if (s != MLSWE_OK) return s;
   H->mem[member].lev[level].patches = boxes;
   return rebuild_masks(H, member, level);
 }
 
-static int parity_c(Hier* H, int level) { return H->parity[level]; }
-
-// Ghost cells of every patch of `level` (all members) at time fraction alpha.
-mlswe_status fill_ghosts_internal(Hier* H, int level, double alpha) {
-  std::vector<InterpItem> items;
-  for (int m = 0; m < H->n_members; ++m) {
-    const Level& V = H->mem[m].lev[level];
-    for (const Box& b : V.patches) {
-      InterpItem it;
-      it.desc_c = H->desc_index(m, level - 1);
-      it.desc_f = H->desc_index(m, level);
-      it.i0 = std::max(0, b.i0 - kNG); it.j0 = std::max(0, b.j0 - kNG);
-      it.i1 = std::min(V.NX, b.i1 + kNG); it.j1 = std::min(V.NY, b.j1 + kNG);
-      items.push_back(it);
-    }
-  }
+// ---- one-shot (synchronous) level transfers used by the API and by regridding ----
+static mlswe_status run_items(Hier* H, int kc, const std::vector<InterpItem>& items, int kind, int r, int par_c,
+                              int par_f, double alpha, int mode) {
   if (items.empty()) return MLSWE_OK;
-  InterpItem* d;
-  mlswe_status s = upload_items(H, items, &d);
-  if (s != MLSWE_OK) return s;
+  const size_t bytes = items.size() * sizeof(InterpItem) + 64;
+  char* base = (char*)scratch_buffer(H, bytes);
+  if (!base) return fail(H, MLSWE_ENOMEM, "scratch allocation failed");
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  int* d_count = (int*)base;
+  InterpItem* d_items = (InterpItem*)(base + 64);
+  const int n = (int)items.size();
+  CUDA_TRY(H, cudaMemcpyAsync(d_count, &n, sizeof(int), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(InterpItem), cudaMemcpyHostToDevice, H->st));
   int tok;
-  timer_begin(H, KC_GHOST, &tok);
-  CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, d, (int)items.size(), max_cells_of(items),
-                            H->cfg.ratio[level - 1], parity_c(H, level - 1), H->parity[level], alpha, 1, H->st));
+  timer_begin(H, kc, &tok);
+  if (kind == 0)
+    CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, d_items, d_count, grid_full(H), r, par_c, par_f, alpha, mode,
+                              H->st));
+  else
+    CUDA_TRY(H, launch_average_items(3 * H->cfg.M, H->d_desc, d_items, d_count, grid_full(H), r, par_c, par_f, H->st));
   timer_end(H, tok);
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
   return MLSWE_OK;
 }
 
@@ -169,174 +213,127 @@ mlswe_status fill_ghosts_internal(Hier* H, int level, double alpha) {
 static mlswe_status interp_boxes(Hier* H, int member, int coarse_level, const std::vector<Box>& boxes) {
   std::vector<InterpItem> items;
   for (const Box& b : boxes)
-    items.push_back(InterpItem{H->desc_index(member, coarse_level), H->desc_index(member, coarse_level + 1), b.i0, b.j0,
-                               b.i1, b.j1});
-  if (items.empty()) return MLSWE_OK;
-  InterpItem* d;
-  mlswe_status s = upload_items(H, items, &d);
-  if (s != MLSWE_OK) return s;
+    push_chunks(items, H->desc_index(member, coarse_level), H->desc_index(member, coarse_level + 1), b);
+  return run_items(H, KC_INTERP, items, 0, H->cfg.ratio[coarse_level], H->parity[coarse_level],
+                   H->parity[coarse_level + 1], 1.0, 0);
+}
+
+// ---- the subcycled coarse step (graph-capturable: no host syncs, tables on device) ----
+static mlswe_status enqueue_level_tree(Hier* H, int level, double alpha) {
   int tok;
-  timer_begin(H, KC_INTERP, &tok);
-  CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, d, (int)items.size(), max_cells_of(items),
-                            H->cfg.ratio[coarse_level], parity_c(H, coarse_level), H->parity[coarse_level + 1], 1.0, 0,
-                            H->st));
-  timer_end(H, tok);
-  return MLSWE_OK;
-}
-
-// Coarsening of every member's level `fine_level` onto fine_level - 1 (members: -1 = all).
-mlswe_status average_internal(Hier* H, int fine_level, int member) {
-  std::vector<InterpItem> items;
-  const int r = H->cfg.ratio[fine_level - 1];
-  for (int m = 0; m < H->n_members; ++m) {
-    if (member >= 0 && m != member) continue;
-    for (const Box& b : H->mem[m].lev[fine_level].patches)
-      items.push_back(InterpItem{H->desc_index(m, fine_level - 1), H->desc_index(m, fine_level), b.i0 / r, b.j0 / r,
-                                 b.i1 / r, b.j1 / r});
-  }
-  if (items.empty()) return MLSWE_OK;
-  InterpItem* d;
-  mlswe_status s = upload_items(H, items, &d);
-  if (s != MLSWE_OK) return s;
-  int tok;
-  timer_begin(H, KC_AVERAGE, &tok);
-  CUDA_TRY(H, launch_average_items(3 * H->cfg.M, H->d_desc, d, (int)items.size(), max_cells_of(items), r,
-                                   H->parity[fine_level - 1], H->parity[fine_level], H->st));
-  timer_end(H, tok);
-  return MLSWE_OK;
-}
-
-static mlswe_status reflux_internal(Hier* H, int level) {
-  std::vector<InterpItem> items;
-  for (int m = 0; m < H->n_members; ++m) {
-    if (H->mem[m].lev[level + 1].patches.empty()) continue;
-    for (const Box& b : H->mem[m].lev[level].patches)
-      items.push_back(InterpItem{H->desc_index(m, level), H->desc_index(m, level + 1), b.i0, b.j0, b.i1, b.j1});
-  }
-  if (items.empty()) return MLSWE_OK;
-  InterpItem* d;
-  mlswe_status s = upload_items(H, items, &d);
-  if (s != MLSWE_OK) return s;
-  int tok;
-  timer_begin(H, KC_REFLUX, &tok);
-  CUDA_TRY(H, launch_reflux(H->cfg.M, H->d_desc, d, (int)items.size(), max_cells_of(items), H->cfg.ratio[level],
-                            H->parity[level], H->st));
-  timer_end(H, tok);
-  return MLSWE_OK;
-}
-
-static bool level_has_patches(Hier* H, int level) {
-  for (int m = 0; m < H->n_members; ++m)
-    if (!H->mem[m].lev[level].patches.empty()) return true;
-  return false;
-}
-
-static mlswe_status advance_level(Hier* H, int level, double alpha) {
-  mlswe_status s;
   if (level > 0) {
-    s = fill_ghosts_internal(H, level, alpha);
-    if (s != MLSWE_OK) return s;
+    timer_begin(H, KC_GHOST, &tok);
+    CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, H->t_ghost[level].d, H->t_ghost[level].d_count, grid_full(H),
+                              H->cfg.ratio[level - 1], H->parity[level - 1], H->parity[level], alpha, 1, H->st));
+    timer_end(H, tok);
   }
-  s = enqueue_level_step(H, level);
+  mlswe_status s = enqueue_level_step(H, level, 1);
   if (s != MLSWE_OK) return s;
-  if (level + 1 < H->L && level_has_patches(H, level + 1)) {
+  if (level + 1 < H->L) {
     const int rt = H->cfg.ratio[level];
     for (int k = 0; k < rt; ++k) {
-      s = advance_level(H, level + 1, (double)k / rt);
+      s = enqueue_level_tree(H, level + 1, (double)k / rt);
       if (s != MLSWE_OK) return s;
     }
-    s = average_internal(H, level + 1, -1);
-    if (s != MLSWE_OK) return s;
-    s = reflux_internal(H, level);
-    if (s != MLSWE_OK) return s;
+    timer_begin(H, KC_AVERAGE, &tok);
+    CUDA_TRY(H, launch_average_items(3 * H->cfg.M, H->d_desc, H->t_avg[level + 1].d, H->t_avg[level + 1].d_count,
+                                     grid_full(H), rt, H->parity[level], H->parity[level + 1], H->st));
+    timer_end(H, tok);
+    timer_begin(H, KC_REFLUX, &tok);
+    CUDA_TRY(H, launch_reflux(H->cfg.M, H->d_desc, H->t_reflux[level].d, H->t_reflux[level].d_count, grid_full(H), rt,
+                              H->parity[level], H->st));
+    timer_end(H, tok);
   }
   return MLSWE_OK;
 }
 
-// Per-member level-0 step from wave speeds: dt_0 = cfl * min_l (prod_{k<l} r_k) / rate_l.
-static void dt_from_rates(Hier* H, const std::vector<double>& rate /*[member*L + l]*/, std::vector<double>& dt0) {
-  dt0.assign(H->n_members, 0.0);
-  for (int m = 0; m < H->n_members; ++m) {
-    double best = INFINITY, fac = 1.0;
-    for (int l = 0; l < H->L; ++l) {
-      if (l > 0) fac *= H->cfg.ratio[l - 1];
-      if (H->mem[m].lev[l].patches.empty()) continue;
-      const double rt = rate[H->desc_index(m, l)];
-      if (rt > 0.0) best = std::min(best, fac / rt);
-    }
-    dt0[m] = std::isfinite(best) ? H->cfg.cfl_desired * best : 0.0;
-  }
+static DtArgs dt_args(Hier* H) {
+  DtArgs A;
+  A.L = H->L;
+  A.n_members = H->n_members;
+  for (int k = 0; k < 4; ++k) A.ratio[k] = H->cfg.ratio[k];
+  A.cfl = H->cfg.cfl_desired;
+  A.cfl_max = H->cfg.cfl_max;
+  A.has_patches = H->d_has;
+  A.inv_dx = H->d_invdx;
+  A.inv_dy = H->d_invdy;
+  return A;
 }
 
-static mlswe_status initial_rates(Hier* H, std::vector<double>& rate) {
-  std::vector<InterpItem> items;
-  for (int m = 0; m < H->n_members; ++m)
-    for (int l = 0; l < H->L; ++l)
-      for (const Box& b : H->mem[m].lev[l].patches)
-        items.push_back(InterpItem{H->desc_index(m, l), 0, b.i0, b.j0, b.i1, b.j1});
+// One coarse step: time step on the device, the level tree, the Courant check.
+static mlswe_status enqueue_coarse_step(Hier* H) {
+  int tok;
+  timer_begin(H, KC_OTHER, &tok);
+  CUDA_TRY(H, launch_dt_begin(dt_args(H), H->d_smax, H->d_init, H->d_init_flag, H->d_dt, H->st));
+  timer_end(H, tok);
+  mlswe_status s = enqueue_level_tree(H, 0, 0.0);
+  if (s != MLSWE_OK) return s;
+  timer_begin(H, KC_OTHER, &tok);
+  CUDA_TRY(H, launch_step_end(dt_args(H), H->d_smax, H->d_dt, H->d_t, H->d_cfl, H->d_status, H->st));
+  timer_end(H, tok);
+  return MLSWE_OK;
+}
+
+// Wave speeds of the current state; the next coarse step takes its dt from them.
+static mlswe_status initial_dt(Hier* H) {
   const int nd = H->n_members * H->L;
   std::vector<int> par(nd);
   for (int k = 0; k < nd; ++k) par[k] = H->parity[k % H->L];
-  // layout in staging: items | parity | speeds
-  const size_t ib = items.size() * sizeof(InterpItem), pb = nd * sizeof(int);
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  char* base = (char*)staging(H, ib + pb + nd * 8 + 64);
-  if (!base) return fail(H, MLSWE_ENOMEM, "staging allocation failed");
-  InterpItem* d_items = (InterpItem*)base;
-  int* d_par = (int*)(base + ib);
-  unsigned long long* d_sp = (unsigned long long*)(base + ((ib + pb + 7) / 8) * 8);
-  CUDA_TRY(H, cudaMemcpyAsync(d_items, items.data(), ib, cudaMemcpyHostToDevice, H->st));
-  CUDA_TRY(H, cudaMemcpyAsync(d_par, par.data(), pb, cudaMemcpyHostToDevice, H->st));
-  CUDA_TRY(H, cudaMemsetAsync(d_sp, 0, nd * 8, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_par, par.data(), nd * 4, cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemsetAsync(H->d_init, 0, nd * 8, H->st));
   int tok;
   timer_begin(H, KC_OTHER, &tok);
-  CUDA_TRY(H, launch_speed(H->cfg.M, H->dp, H->d_desc, d_items, (int)items.size(), max_cells_of(items), d_par, d_sp,
-                           H->st));
+  CUDA_TRY(H, launch_speed(H->cfg.M, H->dp, H->d_desc, H->t_speed.d, H->t_speed.d_count, grid_full(H), H->d_par,
+                           H->d_init, H->st));
   timer_end(H, tok);
-  std::vector<unsigned long long> bits(nd);
-  CUDA_TRY(H, cudaMemcpyAsync(bits.data(), d_sp, nd * 8, cudaMemcpyDeviceToHost, H->st));
+  static const int one = 1;
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_init_flag, &one, sizeof(int), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  rate.assign(nd, 0.0);
-  for (int k = 0; k < nd; ++k) {
-    double s;
-    std::memcpy(&s, &bits[k], 8);
-    const Level& V = H->mem[k / H->L].lev[k % H->L];
-    rate[k] = s / std::min(V.dx, V.dy);
-  }
+  H->dt_ready = true;
   return MLSWE_OK;
 }
 
-static mlswe_status step_rates(Hier* H, std::vector<double>& rate, bool* nan_seen) {
-  const int nd = H->n_members * H->L;
-  std::vector<unsigned long long> bits(nd * 2);
-  CUDA_TRY(H, cudaMemcpyAsync(bits.data(), H->d_smax, nd * 16, cudaMemcpyDeviceToHost, H->st));
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  rate.assign(nd, 0.0);
-  *nan_seen = false;
-  for (int k = 0; k < nd; ++k) {
-    double sx, sy;
-    std::memcpy(&sx, &bits[2 * k], 8);
-    std::memcpy(&sy, &bits[2 * k + 1], 8);
-    if (std::isnan(sx) || std::isnan(sy)) *nan_seen = true;
-    const Level& V = H->mem[k / H->L].lev[k % H->L];
-    rate[k] = std::max(sx / V.dx, sy / V.dy);
-  }
-  return MLSWE_OK;
-}
-
-static mlswe_status set_level_dts(Hier* H, const std::vector<double>& dt0) {
-  for (int m = 0; m < H->n_members; ++m) {
-    double dt = dt0[m];
-    for (int l = 0; l < H->L; ++l) {
-      if (l > 0) dt /= H->cfg.ratio[l - 1];
-      H->h_dt[H->desc_index(m, l)] = dt;
+// One coarse step: replay of the captured graph for the current level-0 parity, or
+// direct launches (per-patch form, timing on, or graphs disabled).
+static mlswe_status coarse_step(Hier* H) {
+  const bool graphs = H->use_graphs && !H->per_patch_launch && !H->timer.on;
+  if (!graphs) return enqueue_coarse_step(H);
+  for (int l = 0; l < H->L; ++l)
+    for (int dir = 0; dir < 2; ++dir) {
+      mlswe_status s = ensure_worklist(H, l, dir);
+      if (s != MLSWE_OK) return s;
     }
+  const int p = H->parity[0];
+  if (!H->graph_valid[p]) {
+    const std::vector<int> par0 = H->parity;
+    const long long k0 = H->kernel_launches;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(H, cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
+    mlswe_status s = enqueue_coarse_step(H);
+    cudaError_t e = cudaStreamEndCapture(H->st, &g);
+    if (s != MLSWE_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return fail(H, MLSWE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    if (H->graph[p]) cudaGraphExecDestroy(H->graph[p]);
+    e = cudaGraphInstantiate(&H->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(H, MLSWE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    H->graph_valid[p] = true;
+    H->graph_launches[p] = H->kernel_launches - k0;
+    H->kernel_launches = k0;
+    H->parity = par0;  // the capture did not run anything
   }
-  CUDA_TRY(H, cudaMemcpyAsync(H->d_dt, H->h_dt.data(), H->h_dt.size() * 8, cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaGraphLaunch(H->graph[p], H->st));
+  H->kernel_launches += H->graph_launches[p];
+  // Parities after one coarse step: level l steps prod_{k<l} r_k times.
+  long long steps = 1;
+  for (int l = 0; l < H->L; ++l) {
+    if (l > 0) steps *= H->cfg.ratio[l - 1];
+    if (steps & 1) H->parity[l] ^= 1;
+  }
   return MLSWE_OK;
 }
 
-mlswe_status regrid_internal(Hier* H, int base) {
+static mlswe_status regrid_internal(Hier* H, int base) {
   for (int m = 0; m < H->n_members; ++m) {
     for (int l = base; l + 1 < H->L; ++l) {
       Level& V = H->mem[m].lev[l];
@@ -344,9 +341,9 @@ mlswe_status regrid_internal(Hier* H, int base) {
       std::vector<Box> boxes;
       if (l == 0 || !V.patches.empty()) {
         const size_t cells = (size_t)V.NX * V.NY;
+        uint8_t* d_flags = (uint8_t*)scratch_buffer(H, cells);
+        if (!d_flags) return fail(H, MLSWE_ENOMEM, "scratch allocation failed");
         CUDA_TRY(H, cudaStreamSynchronize(H->st));
-        uint8_t* d_flags = (uint8_t*)staging(H, cells);
-        if (!d_flags) return fail(H, MLSWE_ENOMEM, "staging allocation failed");
         int tok;
         timer_begin(H, KC_FLAGS, &tok);
         CUDA_TRY(H, launch_flags(H->cfg.M, H->d_desc, H->desc_index(m, l), H->parity[l], (long long)cells,
@@ -374,6 +371,46 @@ mlswe_status regrid_internal(Hier* H, int base) {
   return MLSWE_OK;
 }
 
+// Autotuner of the sweep tiles of one level: times every candidate shape on the level's
+// current patch layout (CUDA events, sweeps run without recording, the state is not
+// advanced) and keeps the fastest per direction.
+static mlswe_status autotune_level(Hier* H, int level, int iters, int* chosen) {
+  static const int cand[][2] = {{13, 16}, {29, 8}, {61, 4}, {125, 2}, {253, 1}};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(H, cudaEventCreate(&e0));
+  CUDA_TRY(H, cudaEventCreate(&e1));
+  const int full = H->blocks_per_sm * H->num_sms;
+  for (int dir = 0; dir < 2; ++dir) {
+    float best = 1e30f;
+    int bl = H->shape[level * 2 + dir].len, bn = H->shape[level * 2 + dir].lines;
+    for (const auto& c : cand) {
+      set_level_shape(H, level, dir, c[0], c[1]);
+      mlswe_status s = ensure_worklist(H, level, dir);
+      if (s != MLSWE_OK) return s;
+      Hier::WorkList& W = H->wl[level * 2 + dir];
+      if (W.count == 0) continue;
+      const int par = H->parity[level];
+      CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr, H->st));
+      CUDA_TRY(H, cudaEventRecord(e0, H->st));
+      for (int k = 0; k < iters; ++k)
+        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr, H->st));
+      CUDA_TRY(H, cudaEventRecord(e1, H->st));
+      CUDA_TRY(H, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CUDA_TRY(H, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bl = c[0]; bn = c[1]; }
+    }
+    set_level_shape(H, level, dir, bl, bn);
+    mlswe_status s = ensure_worklist(H, level, dir);
+    if (s != MLSWE_OK) return s;
+    if (chosen) { chosen[2 * dir] = bl; chosen[2 * dir + 1] = bn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  invalidate_graphs(H);
+  return MLSWE_OK;
+}
+
 }  // namespace mlswe
 
 using namespace mlswe;
@@ -381,23 +418,23 @@ using namespace mlswe;
 extern "C" {
 
 mlswe_status mlswe_set_patches(mlswe_h h, int member, int level, int n, const int32_t* boxes) {
-  Hier* H = h;
-  if (!H || member < 0 || member >= H->n_members || level < 1 || level >= H->L || n < 0 || (n > 0 && !boxes))
-    return fail(H, MLSWE_EINVAL, "set_patches: bad argument");
+  if (!h || member < 0 || member >= h->n_members || level < 1 || level >= h->L || n < 0 || (n > 0 && !boxes))
+    return fail(h, MLSWE_EINVAL, "set_patches: bad argument");
   std::vector<Box> b(n);
   for (int k = 0; k < n; ++k) b[k] = Box{boxes[4 * k], boxes[4 * k + 1], boxes[4 * k + 2], boxes[4 * k + 3]};
-  return set_patches_internal(H, member, level, b);
+  mlswe_status s = set_patches_internal(h, member, level, b);
+  if (s == MLSWE_OK) h->dt_ready = false;
+  return s;
 }
 
 mlswe_status mlswe_get_patches(mlswe_h h, int member, int level, int* n, int32_t* boxes) {
-  Hier* H = h;
-  if (!H || member < 0 || member >= H->n_members || level < 0 || level >= H->L || !n)
-    return fail(H, MLSWE_EINVAL, "get_patches: bad argument");
-  const std::vector<Box>& P = H->mem[member].lev[level].patches;
+  if (!h || member < 0 || member >= h->n_members || level < 0 || level >= h->L || !n)
+    return fail(h, MLSWE_EINVAL, "get_patches: bad argument");
+  const std::vector<Box>& P = h->mem[member].lev[level].patches;
   const int cap = *n;
   *n = (int)P.size();
   if (boxes) {
-    if (cap < (int)P.size()) return fail(H, MLSWE_EINVAL, "get_patches: capacity too small");
+    if (cap < (int)P.size()) return fail(h, MLSWE_EINVAL, "get_patches: capacity too small");
     for (size_t k = 0; k < P.size(); ++k) {
       boxes[4 * k] = P[k].i0; boxes[4 * k + 1] = P[k].j0; boxes[4 * k + 2] = P[k].i1; boxes[4 * k + 3] = P[k].j1;
     }
@@ -406,113 +443,118 @@ mlswe_status mlswe_get_patches(mlswe_h h, int member, int level, int* n, int32_t
 }
 
 mlswe_status mlswe_fill_ghosts(mlswe_h h, int level, double alpha) {
-  Hier* H = h;
-  if (!H || level < 1 || level >= H->L || !(alpha >= 0.0 && alpha <= 1.0))
-    return fail(H, MLSWE_EINVAL, "fill_ghosts: bad argument");
-  mlswe_status s = fill_ghosts_internal(H, level, alpha);
-  if (s != MLSWE_OK) return s;
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  if (!h || level < 1 || level >= h->L || !(alpha >= 0.0 && alpha <= 1.0))
+    return fail(h, MLSWE_EINVAL, "fill_ghosts: bad argument");
+  if (h->tables_dirty) {
+    mlswe_status s = build_tables(h);
+    if (s != MLSWE_OK) return s;
+  }
+  int tok;
+  timer_begin(h, KC_GHOST, &tok);
+  CUDA_TRY(h, launch_interp(h->cfg.M, h->dp, h->d_desc, h->t_ghost[level].d, h->t_ghost[level].d_count, grid_full(h),
+                            h->cfg.ratio[level - 1], h->parity[level - 1], h->parity[level], alpha, 1, h->st));
+  timer_end(h, tok);
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
 }
 
 mlswe_status mlswe_interp_fine(mlswe_h h, int coarse_level, int member) {
-  Hier* H = h;
-  if (!H || member < 0 || member >= H->n_members || coarse_level < 0 || coarse_level + 1 >= H->L)
-    return fail(H, MLSWE_EINVAL, "interp_fine: bad argument");
-  mlswe_status s = interp_boxes(H, member, coarse_level, H->mem[member].lev[coarse_level + 1].patches);
-  if (s != MLSWE_OK) return s;
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  return MLSWE_OK;
+  if (!h || member < 0 || member >= h->n_members || coarse_level < 0 || coarse_level + 1 >= h->L)
+    return fail(h, MLSWE_EINVAL, "interp_fine: bad argument");
+  h->dt_ready = false;
+  return interp_boxes(h, member, coarse_level, h->mem[member].lev[coarse_level + 1].patches);
 }
 
 mlswe_status mlswe_average_coarse(mlswe_h h, int fine_level, int member) {
-  Hier* H = h;
-  if (!H || member < 0 || member >= H->n_members || fine_level < 1 || fine_level >= H->L)
-    return fail(H, MLSWE_EINVAL, "average_coarse: bad argument");
-  mlswe_status s = average_internal(H, fine_level, member);
-  if (s != MLSWE_OK) return s;
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  return MLSWE_OK;
+  if (!h || member < 0 || member >= h->n_members || fine_level < 1 || fine_level >= h->L)
+    return fail(h, MLSWE_EINVAL, "average_coarse: bad argument");
+  std::vector<InterpItem> items;
+  const int r = h->cfg.ratio[fine_level - 1];
+  for (const Box& b : h->mem[member].lev[fine_level].patches)
+    push_chunks(items, h->desc_index(member, fine_level - 1), h->desc_index(member, fine_level),
+                Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
+  h->dt_ready = false;
+  return run_items(h, KC_AVERAGE, items, 1, r, h->parity[fine_level - 1], h->parity[fine_level], 1.0, 0);
 }
 
 mlswe_status mlswe_get_flags(mlswe_h h, int member, int level, uint8_t* flags) {
-  Hier* H = h;
-  if (!H || member < 0 || member >= H->n_members || level < 0 || level >= H->L || !flags)
-    return fail(H, MLSWE_EINVAL, "get_flags: bad argument");
-  const Level& V = H->mem[member].lev[level];
+  if (!h || member < 0 || member >= h->n_members || level < 0 || level >= h->L || !flags)
+    return fail(h, MLSWE_EINVAL, "get_flags: bad argument");
+  const Level& V = h->mem[member].lev[level];
   const size_t cells = (size_t)V.NX * V.NY;
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
-  uint8_t* d = (uint8_t*)staging(H, cells);
-  if (!d) return fail(H, MLSWE_ENOMEM, "staging allocation failed");
+  uint8_t* d = (uint8_t*)scratch_buffer(h, cells);
+  if (!d) return fail(h, MLSWE_ENOMEM, "scratch allocation failed");
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   int tok;
-  timer_begin(H, KC_FLAGS, &tok);
-  CUDA_TRY(H, launch_flags(H->cfg.M, H->d_desc, H->desc_index(member, level), H->parity[level], (long long)cells,
-                           H->cfg.dry_tol, 1.0 / V.dx, 1.0 / V.dy, H->cfg.flag_tol * H->cfg.flag_tol, d, H->st));
-  timer_end(H, tok);
-  CUDA_TRY(H, cudaMemcpyAsync(flags, d, cells, cudaMemcpyDeviceToHost, H->st));
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  timer_begin(h, KC_FLAGS, &tok);
+  CUDA_TRY(h, launch_flags(h->cfg.M, h->d_desc, h->desc_index(member, level), h->parity[level], (long long)cells,
+                           h->cfg.dry_tol, 1.0 / V.dx, 1.0 / V.dy, h->cfg.flag_tol * h->cfg.flag_tol, d, h->st));
+  timer_end(h, tok);
+  CUDA_TRY(h, cudaMemcpyAsync(flags, d, cells, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
 }
 
 mlswe_status mlswe_regrid(mlswe_h h, int base_level) {
-  Hier* H = h;
-  if (!H || base_level < 0 || base_level >= H->L) return fail(H, MLSWE_EINVAL, "regrid: bad argument");
-  mlswe_status s = regrid_internal(H, base_level);
+  if (!h || base_level < 0 || base_level >= h->L) return fail(h, MLSWE_EINVAL, "regrid: bad argument");
+  mlswe_status s = regrid_internal(h, base_level);
   if (s != MLSWE_OK) return s;
-  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  h->dt_ready = false;
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
 }
 
 mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
-  Hier* H = h;
-  if (!H || n_coarse_steps < 0) return fail(H, MLSWE_EINVAL, "advance: bad argument");
-  mlswe_status warn = MLSWE_OK;
+  if (!h || n_coarse_steps < 0) return fail(h, MLSWE_EINVAL, "advance: bad argument");
+  CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
   for (int k = 0; k < n_coarse_steps; ++k) {
     mlswe_status s;
-    if (H->cfg.regrid_interval > 0 && H->L > 1 && H->coarse_steps % H->cfg.regrid_interval == 0) {
-      s = regrid_internal(H, 0);
+    if (h->cfg.regrid_interval > 0 && h->L > 1 && h->coarse_steps % h->cfg.regrid_interval == 0) {
+      s = regrid_internal(h, 0);
       if (s != MLSWE_OK) return s;
     }
-    std::vector<double> rate, dt0;
-    if (!H->have_rates) {
-      s = initial_rates(H, rate);
+    if (h->tables_dirty) {
+      s = build_tables(h);
       if (s != MLSWE_OK) return s;
-    } else {
-      rate = H->last_rates;
     }
-    dt_from_rates(H, rate, dt0);
-    s = set_level_dts(H, dt0);
-    if (s != MLSWE_OK) return s;
-    CUDA_TRY(H, cudaMemsetAsync(H->d_smax, 0, (size_t)H->n_members * H->L * 16, H->st));
-    s = advance_level(H, 0, 0.0);
-    if (s != MLSWE_OK) return s;
-    bool nan_seen = false;
-    s = step_rates(H, H->last_rates, &nan_seen);
-    if (s != MLSWE_OK) return s;
-    if (nan_seen) return fail(H, MLSWE_ENEGDEPTH, "non-finite wave speed in step");
-    H->have_rates = true;
-    for (int m = 0; m < H->n_members; ++m) {
-      double dt = dt0[m];
-      for (int l = 0; l < H->L; ++l) {
-        if (l > 0) dt /= H->cfg.ratio[l - 1];
-        if (dt * H->last_rates[H->desc_index(m, l)] > H->cfg.cfl_max) warn = MLSWE_ECFL;
-      }
+    if (!h->dt_ready) {
+      s = initial_dt(h);
+      if (s != MLSWE_OK) return s;
     }
-    H->t += dt0[0];
-    H->last_dt0 = dt0;
-    H->coarse_steps++;
+    s = coarse_step(h);
+    if (s != MLSWE_OK) return s;
+    h->coarse_steps++;
   }
-  if (warn != MLSWE_OK) return fail(H, warn, "Courant number above cfl_max in a step");
+  unsigned int status = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (status & 2u) return fail(h, MLSWE_ENEGDEPTH, "non-finite wave speed in a step");
+  if (status & 1u) return fail(h, MLSWE_ECFL, "Courant number above cfl_max in a step");
   return MLSWE_OK;
 }
 
 mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out) {
-  Hier* H = h;
-  if (!H) return MLSWE_EINVAL;
-  if (t_out) *t_out = H->t;
-  if (dt_out)
-    for (int m = 0; m < H->n_members; ++m) dt_out[m] = H->last_dt0.empty() ? 0.0 : H->last_dt0[m];
+  if (!h) return MLSWE_EINVAL;
+  std::vector<double> t(h->n_members), dt(h->n_members * h->L);
+  CUDA_TRY(h, cudaMemcpyAsync(t.data(), h->d_t, t.size() * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(dt.data(), h->d_dt, dt.size() * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (t_out) for (int m = 0; m < h->n_members; ++m) t_out[m] = t[m];
+  if (dt_out) for (int m = 0; m < h->n_members; ++m) dt_out[m] = dt[m * h->L];
   return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_execution(mlswe_h h, int use_graphs, int per_patch_launches) {
+  if (!h) return MLSWE_EINVAL;
+  h->use_graphs = use_graphs != 0;
+  h->per_patch_launch = per_patch_launches != 0;
+  invalidate_graphs(h);
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen) {
+  if (!h || level < 0 || level >= h->L || iters < 1) return fail(h, MLSWE_EINVAL, "autotune: bad argument");
+  return autotune_level(h, level, iters, chosen);
 }
 
 }  // extern "C"

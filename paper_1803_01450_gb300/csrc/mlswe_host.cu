@@ -46,6 +46,26 @@ void dev_free(Hier* H, void* p) {
   else H->alloc.free(p, (void*)H->st, H->alloc.ctx);
 }
 
+// Per-call device scratch (gauges, flags); the stream is synchronised before reuse.
+void* scratch_buffer(Hier* H, size_t bytes) {
+  if (bytes > H->scratch_bytes) {
+    cudaStreamSynchronize(H->st);
+    if (H->scratch) dev_free(H, H->scratch);
+    H->scratch_bytes = std::max<size_t>(bytes * 2, 1 << 16);
+    H->scratch = dev_alloc(H, H->scratch_bytes);
+    if (!H->scratch) H->scratch_bytes = 0;
+  }
+  return H->scratch;
+}
+
+void invalidate_graphs(Hier* H) {
+  for (int p = 0; p < 2; ++p) {
+    if (H->graph[p]) cudaGraphExecDestroy(H->graph[p]);
+    H->graph[p] = nullptr;
+    H->graph_valid[p] = false;
+  }
+}
+
 void timer_begin(Hier* H, int kc, int* token) {
   H->kernel_launches++;
   *token = -1;
@@ -87,19 +107,25 @@ static void timer_collect(Hier* H) {
 }
 
 static mlswe_status upload_desc(Hier* H) {
-  std::vector<LevelDesc> d(H->n_members * H->L);
+  const int nd = H->n_members * H->L;
+  std::vector<LevelDesc> d(nd);
+  std::vector<double> idx(nd), idy(nd);
   for (int m = 0; m < H->n_members; ++m)
     for (int l = 0; l < H->L; ++l) {
       const Level& V = H->mem[m].lev[l];
-      LevelDesc& D = d[H->desc_index(m, l)];
+      const int k = H->desc_index(m, l);
+      LevelDesc& D = d[k];
       D.q[0] = V.q[0]; D.q[1] = V.q[1]; D.qs = V.qs; D.B = V.B;
       D.in_patch = V.in_patch; D.covered = V.covered;
       D.fxc = V.fxc; D.fyc = V.fyc; D.fxf = V.fxf; D.fyf = V.fyf;
-      D.dt = H->d_dt + H->desc_index(m, l);
+      D.dt = H->d_dt + k;
       D.NX = V.NX; D.NY = V.NY; D.P = V.P;
       D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
+      idx[k] = D.inv_dx; idy[k] = D.inv_dy;
     }
   CUDA_TRY(H, cudaMemcpyAsync(H->d_desc, d.data(), d.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_invdx, idx.data(), nd * 8, cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_invdy, idy.data(), nd * 8, cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   return MLSWE_OK;
 }
@@ -108,14 +134,16 @@ static bool valid_member_level(Hier* H, int member, int level) {
   return H && member >= 0 && member < H->n_members && level >= 0 && level < H->L;
 }
 
-// Sweep work list of one level: tiles over every patch of every member.
-static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out) {
+// Sweep work list of one level: tiles over every patch of every member, grouped by patch.
+static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out, std::vector<int>& patch_off) {
   out.clear();
-  const TileShape ts = H->shape[dir];
+  patch_off.clear();
+  const TileShape ts = H->shape[level * 2 + dir];
   for (int m = 0; m < H->n_members; ++m) {
     const Level& V = H->mem[m].lev[level];
     const int desc = H->desc_index(m, level);
     for (const Box& b : V.patches) {
+      patch_off.push_back((int)out.size());
       if (dir == 0) {
         // Rows of the patch, plus (refined levels) the two ghost rows on each side that
         // lie in the domain: the y sweep reads Q* there.
@@ -150,48 +178,78 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
       }
     }
   }
+  patch_off.push_back((int)out.size());
 }
 
-static mlswe_status ensure_worklist(Hier* H, int level, int dir) {
+mlswe_status ensure_worklist(Hier* H, int level, int dir) {
   Hier::WorkList& W = H->wl[level * 2 + dir];
   if (!W.dirty) return MLSWE_OK;
   std::vector<SweepItem> items;
-  build_items(H, level, dir, items);
+  build_items(H, level, dir, items, W.patch_off);
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
   if ((int)items.size() > W.capacity) {
     if (W.d_items) dev_free(H, W.d_items);
-    const int cap = std::max<int>(1024, (int)items.size() * 5 / 4);
+    const int cap = std::max<int>(1024, (int)items.size() * 3 / 2);
     W.d_items = (SweepItem*)dev_alloc(H, cap * sizeof(SweepItem));
     if (!W.d_items) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
     W.capacity = cap;
+    invalidate_graphs(H);
+  }
+  const int np = (int)W.patch_off.size() - 1;
+  if (np + 1 > W.patch_cap) {
+    if (W.d_patch_count) dev_free(H, W.d_patch_count);
+    W.patch_cap = std::max(64, (np + 1) * 3 / 2);
+    W.d_patch_count = (int*)dev_alloc(H, W.patch_cap * sizeof(int));
+    if (!W.d_patch_count) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
   }
   if (!W.d_count) {
     W.d_count = (int*)dev_alloc(H, sizeof(int));
     if (!W.d_count) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
   }
+  std::vector<int> pc(std::max(np, 1), 0);
+  for (int p = 0; p < np; ++p) pc[p] = W.patch_off[p + 1] - W.patch_off[p];
   W.count = (int)items.size();
   if (!items.empty())
     CUDA_TRY(H, cudaMemcpyAsync(W.d_items, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaMemcpyAsync(W.d_count, &W.count, sizeof(int), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(W.d_patch_count, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   W.dirty = false;
   return MLSWE_OK;
 }
 
 // Launch the two sweeps of one level step (device work only, no host sync).
-mlswe_status enqueue_level_step(Hier* H, int level) {
+// Batched form: one persistent launch per sweep over the tiles of every patch of every
+// member. Per-patch form (comparison only): one launch per patch and sweep.
+mlswe_status enqueue_level_step(Hier* H, int level, int record) {
   for (int dir = 0; dir < 2; ++dir) {
     mlswe_status s = ensure_worklist(H, level, dir);
     if (s != MLSWE_OK) return s;
   }
   const int par = H->parity[level];
+  const int full = H->blocks_per_sm * H->num_sms;
   for (int dir = 0; dir < 2; ++dir) {
     Hier::WorkList& W = H->wl[level * 2 + dir];
-    const int grid = std::min(W.count, H->blocks_per_sm * H->num_sms);
-    if (grid <= 0) continue;
-    int tok;
-    timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
-    CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, grid, par, H->d_smax, H->d_lost, H->st));
-    timer_end(H, tok);
+    if (!H->per_patch_launch) {
+      // Always launched (also with no items): a captured graph must hold the node for
+      // when a later regrid fills the work list.
+      int tok;
+      timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
+      CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, record, H->d_smax,
+                               H->d_lost, H->st));
+      timer_end(H, tok);
+    } else {
+      const int np = (int)W.patch_off.size() - 1;
+      for (int p = 0; p < np; ++p) {
+        const int cnt = W.patch_off[p + 1] - W.patch_off[p];
+        if (cnt == 0) continue;
+        int tok;
+        timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
+        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p,
+                                 std::min(cnt, full), par, record, H->d_smax, H->d_lost, H->st));
+        timer_end(H, tok);
+      }
+    }
   }
   H->parity[level] ^= 1;
   return MLSWE_OK;
@@ -215,6 +273,16 @@ static mlswe_status level_cfl(Hier* H, int level, double* cfl_out, bool* nan_see
   return MLSWE_OK;
 }
 
+static bool shape_ok(int len, int lines) {
+  return len >= 4 && lines >= 1 && lines <= 32 && lines * (len + 3) <= kMaxEdges && lines * (len + 4) <= kMaxCells;
+}
+
+void set_level_shape(Hier* H, int level, int dir, int len, int lines) {
+  H->shape[level * 2 + dir].len = len;
+  H->shape[level * 2 + dir].lines = lines;
+  H->wl[level * 2 + dir].dirty = true;
+}
+
 }  // namespace mlswe
 
 using namespace mlswe;
@@ -229,9 +297,11 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   *out = nullptr;
   if (cfg->M < 1 || cfg->M > 2 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
   if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
+  if (cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->dry_tol >= 0.0) || !(cfg->g > 0.0)) return MLSWE_EINVAL;
   if (cfg->M == 2 && !(cfg->rho[0] > 0.0 && cfg->rho[0] < cfg->rho[1])) return MLSWE_EINVAL;
   for (int l = 0; l + 1 < cfg->max_levels; ++l)
     if (cfg->ratio[l] != 2 && cfg->ratio[l] != 4) return MLSWE_EINVAL;
+  if (cfg->max_levels > 1 && (cfg->min_side < 1 || cfg->max_side < 2 * cfg->min_side)) return MLSWE_EINVAL;
   for (int m = 0; m < n_members; ++m)
     if (doms[m].nx0 < 4 || doms[m].ny0 < 4 || !(doms[m].x1 > doms[m].x0) || !(doms[m].y1 > doms[m].y0))
       return MLSWE_EINVAL;
@@ -243,12 +313,26 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->n_members = n_members;
   H->L = cfg->max_levels;
   H->st = (cudaStream_t)cuda_stream;
+  if (!H->st) {
+    // The legacy default stream cannot be captured into a graph: own a stream instead.
+    if (cudaStreamCreateWithFlags(&H->st, cudaStreamNonBlocking) != cudaSuccess) { delete H; return MLSWE_ECUDA; }
+    H->own_stream = true;
+  }
   if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
   H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
   H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
   cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
   H->parity.assign(H->L, 0);
   H->wl.resize(H->L * 2);
+  H->shape.resize(H->L * 2);
+  for (int l = 0; l < H->L; ++l) {
+    // Default tiles: 125-cell rows x 2 (x sweep), 125-cell columns x 2 (y sweep); 256 edges.
+    H->shape[l * 2] = TileShape{125, 2};
+    H->shape[l * 2 + 1] = TileShape{125, 2};
+  }
+  H->t_ghost.resize(H->L);
+  H->t_avg.resize(H->L);
+  H->t_reflux.resize(H->L);
   H->mem.resize(n_members);
   const int F = 3 * cfg->M;
   for (int m = 0; m < n_members; ++m) {
@@ -301,16 +385,32 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->d_desc = (LevelDesc*)dev_alloc(H, nd * sizeof(LevelDesc));
   H->d_dt = (double*)dev_alloc(H, nd * sizeof(double));
   H->d_smax = (unsigned long long*)dev_alloc(H, nd * 2 * 8);
+  H->d_init = (unsigned long long*)dev_alloc(H, nd * 8);
   H->d_lost = (unsigned int*)dev_alloc(H, 8);
-  if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_lost) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+  H->d_status = (unsigned int*)dev_alloc(H, 8);
+  H->d_t = (double*)dev_alloc(H, n_members * 8);
+  H->d_cfl = (double*)dev_alloc(H, n_members * 8);
+  H->d_has = (int*)dev_alloc(H, nd * 4);
+  H->d_invdx = (double*)dev_alloc(H, nd * 8);
+  H->d_invdy = (double*)dev_alloc(H, nd * 8);
+  H->d_par = (int*)dev_alloc(H, nd * 4);
+  H->d_init_flag = (int*)dev_alloc(H, 8);
+  if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_init || !H->d_lost || !H->d_status || !H->d_t || !H->d_cfl ||
+      !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag) {
+    mlswe_destroy(H);
+    return MLSWE_ENOMEM;
+  }
   H->h_dt.assign(nd, 0.0);
   cudaMemsetAsync(H->d_dt, 0, nd * 8, H->st);
   cudaMemsetAsync(H->d_smax, 0, nd * 16, H->st);
+  cudaMemsetAsync(H->d_init, 0, nd * 8, H->st);
   cudaMemsetAsync(H->d_lost, 0, 8, H->st);
+  cudaMemsetAsync(H->d_status, 0, 8, H->st);
+  cudaMemsetAsync(H->d_t, 0, n_members * 8, H->st);
+  cudaMemsetAsync(H->d_cfl, 0, n_members * 8, H->st);
+  cudaMemsetAsync(H->d_has, 0, nd * 4, H->st);
+  cudaMemsetAsync(H->d_init_flag, 0, 8, H->st);
   if (upload_desc(H) != MLSWE_OK) { mlswe_destroy(H); return MLSWE_ECUDA; }
-  // Tile shapes: x sweep 61 cells x 4 rows (256 edges), y sweep 8 columns x 29 cells.
-  H->shape[0].len = 61; H->shape[0].lines = 4;
-  H->shape[1].len = 29; H->shape[1].lines = 8;
   H->blocks_per_sm = 1;
   *out = H;
   return MLSWE_OK;
@@ -319,9 +419,11 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
 mlswe_status mlswe_destroy(mlswe_h h) {
   if (!h) return MLSWE_EINVAL;
   cudaStreamSynchronize(h->st);
+  invalidate_graphs(h);
   for (cudaEvent_t e : h->timer.pool) cudaEventDestroy(e);
   std::vector<void*> all = h->allocations;
   for (void* p : all) dev_free(h, p);
+  if (h->own_stream) cudaStreamDestroy(h->st);
   delete h;
   return MLSWE_OK;
 }
@@ -342,6 +444,7 @@ mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q) 
     CUDA_TRY(h, cudaMemcpy2DAsync(dst + (size_t)f * V.NY * V.P, V.P * 8, q + (size_t)f * V.NY * V.NX, V.NX * 8,
                                   V.NX * 8, V.NY, cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->dt_ready = false;  // the next automatic step starts from this state's wave speeds
   return MLSWE_OK;
 }
 
@@ -359,9 +462,13 @@ mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out) {
 
 mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt) {
   if (!h || level < 0 || level >= h->L || !dt) return fail(h, MLSWE_EINVAL, "set_dt: bad argument");
-  for (int m = 0; m < h->n_members; ++m) h->h_dt[h->desc_index(m, level)] = dt[m];
+  for (int m = 0; m < h->n_members; ++m) {
+    if (!(dt[m] >= 0.0)) return fail(h, MLSWE_EINVAL, "set_dt: negative or non-finite dt");
+    h->h_dt[h->desc_index(m, level)] = dt[m];
+  }
   CUDA_TRY(h, cudaMemcpyAsync(h->d_dt, h->h_dt.data(), h->h_dt.size() * 8, cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->dt_ready = false;
   return MLSWE_OK;
 }
 
@@ -373,8 +480,9 @@ mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cf
   }
   CUDA_TRY(h, cudaMemsetAsync(h->d_smax, 0, (size_t)h->n_members * h->L * 16, h->st));
   CUDA_TRY(h, cudaMemsetAsync(h->d_lost, 0, 4, h->st));
-  mlswe_status s = enqueue_level_step(h, level);
+  mlswe_status s = enqueue_level_step(h, level, 1);
   if (s != MLSWE_OK) return s;
+  h->dt_ready = false;
   if (cfl_out) {
     bool nan_seen = false;
     s = level_cfl(h, level, cfl_out, &nan_seen);
@@ -383,6 +491,15 @@ mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cf
     for (int m = 0; m < h->n_members; ++m)
       if (cfl_out[m] > h->cfg.cfl_max) return fail(h, MLSWE_ECFL, "Courant number above cfl_max");
   }
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm) {
+  if (!h || dir < 0 || dir > 1 || !shape_ok(len, lines) || ctas_per_sm < 1 || ctas_per_sm > 2)
+    return fail(h, MLSWE_EINVAL, "set_tiles: shape out of range");
+  for (int l = 0; l < h->L; ++l) set_level_shape(h, l, dir, len, lines);
+  h->blocks_per_sm = ctas_per_sm;
+  invalidate_graphs(h);
   return MLSWE_OK;
 }
 
@@ -427,13 +544,9 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
     cells[3 * k + 2] = bj;
   }
   const size_t need = cells.size() * 4 + par.size() * 4 + (size_t)n * M * 8 + 64;
-  if (need > h->scratch_bytes) {
-    if (h->scratch) dev_free(h, h->scratch);
-    h->scratch = dev_alloc(h, need * 2);
-    if (!h->scratch) return fail(h, MLSWE_ENOMEM, "gauge scratch allocation failed");
-    h->scratch_bytes = need * 2;
-  }
-  char* base = (char*)h->scratch;
+  char* base = (char*)scratch_buffer(h, need);
+  if (!base) return fail(h, MLSWE_ENOMEM, "gauge scratch allocation failed");
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   double* d_out = (double*)base;
   int* d_cells = (int*)(base + (size_t)n * M * 8);
   int* d_par = d_cells + cells.size();

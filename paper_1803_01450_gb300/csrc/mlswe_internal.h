@@ -61,6 +61,16 @@ struct LaunchTimer {
   long long launches[KC_COUNT] = {0};
 };
 
+// Device-resident table of work items with a device-resident count (a captured graph
+// reads both at replay time, so tables can be rewritten without recapture).
+template <class T>
+struct DevTable {
+  T* d = nullptr;
+  int* d_count = nullptr;
+  int cap = 0;
+  int count = 0;
+};
+
 struct Hier {
   mlswe_config cfg;
   DevParams dp;
@@ -71,6 +81,7 @@ struct Hier {
   mlswe_allocator alloc{};
   bool own_alloc = true;
   cudaStream_t st = nullptr;
+  bool own_stream = false;
   std::string err;
   std::vector<void*> allocations;
 
@@ -78,34 +89,68 @@ struct Hier {
   LevelDesc* d_desc = nullptr;        // [n_members * L]
   double* d_dt = nullptr;             // [n_members * L]
   unsigned long long* d_smax = nullptr;  // [n_members * L * 2]
+  unsigned long long* d_init = nullptr;  // [n_members * L] initial wave speeds
   unsigned int* d_lost = nullptr;     // [1]
+  unsigned int* d_status = nullptr;   // [1] bit 0: Courant above cfl_max, bit 1: non-finite speed
+  double* d_t = nullptr;              // [n_members] simulated time
+  double* d_cfl = nullptr;            // [n_members] Courant number of the last coarse step
+  int* d_has = nullptr;               // [n_members * L] level has patches
+  double* d_invdx = nullptr;          // [n_members * L]
+  double* d_invdy = nullptr;
+  int* d_par = nullptr;               // [n_members * L] parity of the desc's level (speed kernel)
+  int* d_init_flag = nullptr;         // [1] 1: the next step's dt comes from d_init
   std::vector<double> h_dt;           // host copy of dt per (member, level)
-  // Sweep work lists per level and direction.
+  // Sweep work lists per level and direction, with per-patch ranges for the
+  // one-launch-per-patch form.
   struct WorkList {
     SweepItem* d_items = nullptr;
     int* d_count = nullptr;
     int capacity = 0;
     int count = 0;
     bool dirty = true;
+    std::vector<int> patch_off;     // item offset of every (member, patch)
+    int* d_patch_count = nullptr;   // item count of every (member, patch)
+    int patch_cap = 0;
   };
   std::vector<WorkList> wl;  // [L * 2]
-  TileShape shape[2];
+  std::vector<TileShape> shape;  // [L * 2]
   int blocks_per_sm = 1;
   int num_sms = 0;
-  double t = 0.0;
+  bool per_patch_launch = false;
+  bool use_graphs = true;
+  // Level-transfer tables per level (ghost strips of level l, coarsening of l onto l-1,
+  // reflux scan of l, wave-speed boxes of all levels).
+  std::vector<DevTable<InterpItem>> t_ghost, t_avg, t_reflux;
+  DevTable<InterpItem> t_speed;
+  bool tables_dirty = true;
+  bool dt_ready = false;           // device dt holds the next coarse step
+  // Graphs of one coarse step, per level-0 parity.
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_valid[2] = {false, false};
+  long long graph_launches[2] = {0, 0};  // kernels inside each graph
   long long coarse_steps = 0;
   LaunchTimer timer;
   long long kernel_launches = 0;   // every kernel this hierarchy launched
-  void* scratch = nullptr;         // small per-call device scratch (gauges)
+  void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
   size_t scratch_bytes = 0;
-  void* stage = nullptr;           // staging of per-launch item tables (AMR kernels)
-  size_t stage_bytes = 0;
-  bool have_rates = false;         // wave-speed rates of the last coarse step are known
-  std::vector<double> last_rates;  // [member * L + level]: max(sx/dx, sy/dy)
-  std::vector<double> last_dt0;    // [member]: last level-0 step
 
   int desc_index(int member, int level) const { return member * L + level; }
 };
+
+// Arguments of the device-side time-step kernels.
+struct DtArgs {
+  int L;
+  int n_members;
+  int ratio[4];
+  double cfl, cfl_max;
+  const int* has_patches;   // [member * L + l]
+  const double* inv_dx;     // [member * L + l]
+  const double* inv_dy;
+};
+cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
+                            int* init_flag, double* dt, cudaStream_t st);
+cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
+                            double* cfl_reached, unsigned int* status, cudaStream_t st);
 
 // Optional per-kernel-class timing with CUDA events on the hierarchy's stream.
 void timer_begin(Hier* H, int kc, int* token);
@@ -114,6 +159,8 @@ void timer_end(Hier* H, int token);
 // Memory helpers (implemented in mlswe_host.cu).
 void* dev_alloc(Hier* H, size_t bytes);
 void dev_free(Hier* H, void* p);
+void* scratch_buffer(Hier* H, size_t bytes);
+void invalidate_graphs(Hier* H);
 
 // Kernel launchers.
 size_t sweep_smem_bytes(int M);
@@ -123,8 +170,11 @@ cudaError_t launch_average(int nf, int r, const double* fine, int fP, size_t fpl
 cudaError_t launch_gauges(int M, const LevelDesc* descs, const int* parity_of_desc, const int* cells, int n,
                           double* out, cudaStream_t st);
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                         const int* n_items_dev, int grid, int parity, unsigned long long* smax_bits,
+                         const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
                          unsigned int* lost_count, cudaStream_t st);
+
+mlswe_status enqueue_level_step(Hier* H, int level, int record);
+mlswe_status ensure_worklist(Hier* H, int level, int dir);
 
 }  // namespace mlswe
 

@@ -49,7 +49,7 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* d
 template <int M, int DIR>
 __global__ void __launch_bounds__(kThreads, 1)
 sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
-             const int* __restrict__ n_items_dev, int parity, unsigned long long* smax_bits,
+             const int* __restrict__ n_items_dev, int parity, int record, unsigned long long* smax_bits,
              unsigned int* lost_count) {
   using R = Rec<M>;
   using WR = WRec<M>;
@@ -72,7 +72,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
     const double dt = *D.dt;
     const double nu = dt * (DIR == 0 ? D.inv_dx : D.inv_dy);
-    const bool interior = item.flags & 1;
+    // interior lines of a recorded step count toward the CFL reduction and the reflux fluxes
+    const bool interior = (item.flags & 1) && record;
 
     // ---- phase 1: load cells (mirror at walls) and compute the per-cell record ----
     const int ncell = nl * (len + 4);
@@ -326,8 +327,8 @@ size_t sweep_smem_bytes(int M) {
 
 template <int M, int DIR>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                                  const int* n_items_dev, int grid, int parity, unsigned long long* smax_bits,
-                                  unsigned int* lost_count, cudaStream_t st) {
+                                  const int* n_items_dev, int grid, int parity, int record,
+                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st) {
   const size_t sm = sweep_smem_bytes(M);
   static bool attr_set = false;
   if (!attr_set) {
@@ -335,19 +336,19 @@ static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, co
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, smax_bits, lost_count);
+  sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record, smax_bits, lost_count);
   return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                         const int* n_items_dev, int grid, int parity, unsigned long long* smax_bits,
+                         const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
                          unsigned int* lost_count, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   if (P.M == 1)
-    return dir == 0 ? launch_sweep_t<1, 0>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st)
-                    : launch_sweep_t<1, 1>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st);
-  return dir == 0 ? launch_sweep_t<2, 0>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st)
-                  : launch_sweep_t<2, 1>(P, descs, items, n_items_dev, grid, parity, smax_bits, lost_count, st);
+    return dir == 0 ? launch_sweep_t<1, 0>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
+                    : launch_sweep_t<1, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
+  return dir == 0 ? launch_sweep_t<2, 0>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
+                  : launch_sweep_t<2, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
 }
 
 }  // namespace mlswe

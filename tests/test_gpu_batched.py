@@ -1,0 +1,118 @@
+"""Batched execution: every patch of a level of every ensemble member in one persistent
+launch, whole coarse steps replayed from CUDA graphs, per-member device time steps, and the
+tile autotuner. The execution form must not change any result: graph replay, direct
+launches and one launch per patch give bit-identical states; the ensemble matches the
+oracle member by member."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.amr import OracleAMR
+from paper_1803_01450_gb300 import inputs as I
+from conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+def _ensemble(pkg, members, levels=2, r=4, regrid=4):
+    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=levels, ratio=[r, r], flag_tol=2e-5, regrid_interval=regrid,
+                     n_buf=2, cluster_eff=0.7, min_side=16, max_side=64)
+    doms = [(0.0, 0.0, m["L"], m["L"], m["n"], m["n"]) for m in members]
+    H = pkg.Hierarchy(cfg, doms)
+    states = []
+    for k, m in enumerate(members):
+        nf = m["n"] * r ** (levels - 1)
+        _, Bf = I.ensemble_state(m, nf)  # bathymetry sampled at the finest cell centres
+        H.set_bathymetry(k, Bf)
+        B0 = H.get_bathymetry(k, 0)
+        q0 = I.layered_state(B0, _eta1(m, m["n"]), -200.0 * np.ones_like(B0))
+        H.set_state(k, 0, q0)
+        states.append((q0, Bf))
+    return H, states
+
+
+def _eta1(member, n):
+    x = I.centers(0.0, member["L"], n)
+    X, Y = np.meshgrid(x, x)
+    return I.hump_field(X, Y, *member["humps"])
+
+
+def _members(k_list, n_min=48, n_max=80):
+    return [I.ensemble_member(k, n_min=n_min, n_max=n_max) for k in k_list]
+
+
+def test_graph_direct_and_per_patch_are_bit_identical(mlswe_lib):
+    members = _members(range(3))
+    outs = []
+    for mode in ("graph", "direct", "per_patch"):
+        H, _ = _ensemble(mlswe_lib, members)
+        if mode == "direct":
+            H.set_execution(use_graphs=False)
+        elif mode == "per_patch":
+            H.set_execution(use_graphs=False, per_patch_launches=True)
+        H.advance(9)
+        outs.append([(H.get_state(k, 0), H.get_state(k, 1), H.get_patches(k, 1)) for k in range(len(members))])
+        H.close()
+    for k in range(len(members)):
+        for mode in (1, 2):
+            assert np.array_equal(outs[0][k][2], outs[mode][k][2])
+            assert np.array_equal(outs[0][k][0], outs[mode][k][0])
+            assert np.array_equal(outs[0][k][1], outs[mode][k][1])
+
+
+def test_graph_replay_is_deterministic(mlswe_lib):
+    members = _members(range(2))
+    res = []
+    for _ in range(2):
+        H, _ = _ensemble(mlswe_lib, members)
+        H.advance(6)
+        res.append(H.get_state(1, 1))
+        H.close()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_ensemble_members_match_oracle(mlswe_lib):
+    """Every member of a 3-member ensemble (different grids, bathymetry, humps and time
+    steps) advanced together matches its own oracle run."""
+    members = _members(range(3))
+    H, states = _ensemble(mlswe_lib, members)
+    H.advance(8)
+    t, dt = H.get_time()
+    for k, m in enumerate(members):
+        q0, Bf = states[k]
+        P = O.params(M=2, dry_tol=1e-3)
+        A = OracleAMR(P, (0, 0, m["L"], m["L"]), m["n"], m["n"], 2, [4], Bf, flag_tol=2e-5, min_side=16, max_side=64)
+        A.set_state(0, q0)
+        A.advance(8, regrid_interval=4)
+        assert [tuple(b) for b in H.get_patches(k, 1).tolist()] == [tuple(b) for b in A.lev[1].patches]
+        assert abs(t[k] - A.t) <= 1e-12 * A.t
+        # Deep water: momentum near rest is rounding noise of eta - B, so the bound is the
+        # larger of 1e-11 and 10x the oracle's own change under a one-ulp input perturbation.
+        A2 = OracleAMR(P, (0, 0, m["L"], m["L"]), m["n"], m["n"], 2, [4], Bf, flag_tol=2e-5, min_side=16, max_side=64)
+        rng = np.random.default_rng(k)
+        A2.set_state(0, q0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=q0.shape)))
+        A2.advance(8, regrid_interval=4)
+        sens = rel_err(A2.lev[0].q, A.lev[0].q)
+        err = rel_err(H.get_state(k, 0), A.lev[0].q)
+        assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (k, err, sens)
+        assert err[[0, 3]].max() <= TOL
+    assert len(set(np.round(dt, 12))) == len(members)  # per-member time steps differ
+    H.close()
+
+
+def test_autotune_keeps_state_and_results(mlswe_lib):
+    members = _members(range(2))
+    H1, _ = _ensemble(mlswe_lib, members)
+    H1.advance(4)
+    q_before = H1.get_state(0, 1)
+    chosen = H1.autotune(1, iters=2)
+    assert np.array_equal(H1.get_state(0, 1), q_before)
+    assert chosen[0] >= 4 and chosen[2] >= 4
+    H1.advance(4)
+    H2, _ = _ensemble(mlswe_lib, members)
+    H2.advance(8)
+    for k in range(2):
+        assert np.array_equal(H1.get_state(k, 1), H2.get_state(k, 1))
+    H1.close()
+    H2.close()
