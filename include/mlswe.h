@@ -215,6 +215,26 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
  * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range. */
 mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm);
 
+/* One dimensionally split step of a single grid with walls on all sides that
+ * allocates no memory. The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory while they step the model
+ * (for example a solver run inside a callback of a framework that owns the
+ * device memory pool, or a service under a no-allocation-after-start-up rule).
+ * The caller passes its own device buffers: q_in and q_out [3M][ny][nx]
+ * (distinct), B [ny][nx]. The solver's working memory (state after the x sweep,
+ * tile lists, descriptor, time step, wave-speed slots) lives in one static
+ * device array of about 16 MB that every GPU loading the library holds until
+ * the process exits; grids up to nx * ny <= 512 * 512 cells (nx, ny >= 4) fit,
+ * larger ones return MLSWE_EINVAL. The first call on a device looks up that
+ * array's device address, so make it before any stream capture. All calls
+ * share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller. Uses the model settings of cfg (M, rho, g, dry_tol, order,
+ * limiter, eigen); work is issued on cuda_stream. cfl_out (host, may be NULL)
+ * receives the Courant number and then synchronises the stream. */
+mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx, int ny, double dx, double dy, double dt,
+                                      const double* q_in, const double* B, double* q_out, void* cuda_stream,
+                                      double* cfl_out);
+
 /* Launch instrumentation (not in the paper). Returns, and resets, the time in
  * ms and the launch count of each kernel class since the previous call, as
  * measured by CUDA events recorded around every launch on the hierarchy's
