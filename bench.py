@@ -1,15 +1,22 @@
-"""Benchmark: layer-cell-updates per second of the two-layer shallow-water step on GB300.
+"""Benchmark: layer-cell-updates per second of the two-layer shallow-water AMR hot path on GB300.
 
-Workload (default): the 2048 x 2048 fixed-grid shelf problem, two layers, FP64,
-second order with the MC limiter, walls on all sides; one benchmark step is one
-full time step of the level (x sweep + y sweep, all cells). Inputs are larger
-than L2 (201 MB of state per buffer), so no flush is needed between steps.
+Headline workload (``value``): the 2048 x 2048 fixed-grid shelf problem (two layers, FP64,
+second order with the MC limiter, walls on all sides); one benchmark step is one full time
+step of the level (x sweep + y sweep over every cell). The state (201 MB per buffer) is
+larger than L2, so no flush is needed between steps.
+
+Also reported on the same line:
+  * ``batched_amr``: three levels (512^2 coarse, ratios 4 and 4) over the shore bathymetry
+    with 1000 level-1 and 3000 level-2 patches of sides 16..64 (seeded synthetic layout),
+    whole subcycled coarse steps; all patches of a level in one persistent launch replayed
+    from a CUDA graph versus one launch per patch;
+  * ``ensemble``: 64 members of sizes U{128..512}^2 with a refined level (ratio 4), all
+    members stepped together with per-member time steps, batched versus per-patch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlswe|reference]
 
-``--impl reference`` times the FP64 CPU oracle (the plain reference
-implementation) on the host cores for the same workload and metric.
-Prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle (the plain reference implementation) on the
+host cores for the headline workload and metric. Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -33,18 +40,14 @@ UNIT = "LCU/s"
 N_CELLS = 2048
 M_LAYERS = 2
 
-# FP64 operations per cell update of the step kernels (x sweep + y sweep), counted by ncu
-# on the scale workload (2 * dfma + dadd + dmul instructions, thread level), with the
-# halo edges of each tile removed. See profiles/ for the capture.
-FP64_FLOP_PER_CELL_UPDATE = None
-
-
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except Exception:
-        return {}
+# FP64 operations per cell update of the method (x sweep + y sweep, order 2, MC limiter,
+# eigenvalue guesses + 2 Newton steps), counted by the oracle's counting scalar on the
+# headline workload: `python -m oracle.count_flops`. Half of it belongs to each sweep.
+FP64_FLOP_PER_CELL_UPDATE = 1293.25
+# FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
+SWEEP_X_DRAM_BYTES = None
 
 
 class ClockSampler:
@@ -93,13 +96,15 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    return rank, ws
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def _workload_name():
+    return "scale: 2048x2048 fixed grid, 2 layers, shelf bathymetry, 8 humps, order 2 MC, walls"
 
 
 def run_reference(args):
-    """The FP64 CPU oracle on the host cores, same workload and metric."""
+    """The FP64 CPU oracle on the host cores, same workload and metric (rank 0 only)."""
     rank, ws = _dist()
     if rank != 0:
         return
@@ -115,22 +120,21 @@ def run_reference(args):
     for _ in range(args.steps):
         q, _, _ = oracle.step_walled(P, q, B, w["dx"], w["dy"], dt)
     el = time.perf_counter() - t0
-    lcu = N_CELLS * N_CELLS * M_LAYERS * args.steps
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    v = lcu / el
+    v = N_CELLS * N_CELLS * M_LAYERS * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "scale: 2048x2048 fixed grid, 2 layers, shelf bathymetry, 8 humps, order 2 MC",
-                       "cells": N_CELLS * N_CELLS, "layers": M_LAYERS},
+            "config": {"workload": _workload_name(), "cells": N_CELLS * N_CELLS, "layers": M_LAYERS},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full steps of the 2048^2 workload after {args.warmup} warm-up"},
+                             "sample": f"{args.steps} full time steps of the 2048^2 workload after "
+                                       f"{args.warmup} warm-up steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline(seconds_budget=15.0):
-    """Oracle throughput on the host cores over a bounded sample of the same workload."""
+    """Oracle throughput on the host cores over a bounded sample of the headline workload."""
     import oracle
     oracle.build()
     w = I.scale(N_CELLS)
@@ -147,7 +151,108 @@ def cpu_baseline(seconds_budget=15.0):
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": N_CELLS * N_CELLS * M_LAYERS * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} full time steps of the 2048^2 scale workload ({el:.1f} s)"}
+            "sample": f"{n} full time steps of the 2048^2 headline workload ({el:.1f} s)"}
+
+
+def _interior_updates(H, member_count, levels, ratios):
+    """Cell updates of one coarse step (patch cells x time steps of each level)."""
+    tot = 0
+    for m in range(member_count):
+        steps = 1
+        for l in range(levels):
+            if l > 0:
+                steps *= ratios[l - 1]
+            boxes = H.get_patches(m, l)
+            tot += steps * int(sum((b[2] - b[0]) * (b[3] - b[1]) for b in boxes))
+    return tot
+
+
+def _time_advance(torch, H, stream, n_steps):
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.advance(n_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def bench_batched_amr(pkg, torch, stream, steps=3):
+    """Three-level AMR over the shore bathymetry, 1000 + 3000 synthetic patches."""
+    n0, r = 512, 4
+    nf = n0 * r * r
+    L = 1e5
+    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)], stream=stream.cuda_stream)
+    xf = I.centers(0.0, L, nf)
+    Bf = np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf)))
+    H.set_bathymetry(0, Bf)
+    del Bf
+    B0 = H.get_bathymetry(0, 0)
+    x0 = I.centers(0.0, L, n0)
+    X, Y = np.meshgrid(x0, x0)
+    eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
+    H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
+    l1 = I.random_layout(3100, n0 * r, n0 * r, 1000, r)
+    l2 = I.random_layout(3200, nf, nf, 3000, r, parents=l1, margin=2)
+    H.set_patches(0, 1, l1)
+    H.interp_fine(0, 0)
+    H.set_patches(0, 2, l2)
+    H.interp_fine(1, 0)
+    chosen = [H.autotune(l, iters=2) for l in range(3)]
+    upd = _interior_updates(H, 1, 3, [r, r])
+    H.advance(1)
+    ms_b = _time_advance(torch, H, stream, steps)
+    H.set_execution(use_graphs=False, per_patch_launches=True)
+    H.advance(1)
+    ms_p = _time_advance(torch, H, stream, max(1, steps // 2))
+    H.close()
+    lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
+    lp = upd * M_LAYERS * max(1, steps // 2) / (ms_p * 1e-3)
+    return {"workload": "3 levels, 512^2 coarse, ratios 4,4, shore bathymetry, 8 humps; seeded layout of "
+                        f"{len(l1)} level-1 and {len(l2)} level-2 patches (sides 16..64)",
+            "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
+            "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
+            "ms_per_coarse_step_batched": ms_b / steps, "ms_per_coarse_step_per_patch": ms_p / max(1, steps // 2),
+            "autotuned_tiles": chosen}
+
+
+def bench_ensemble(pkg, torch, stream, n_members=64, steps=3):
+    """Ensemble of independent members, U{128..512}^2 coarse grids, one refined level."""
+    r = 4
+    members = [I.ensemble_member(k) for k in range(n_members)]
+    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=2, ratio=[r], regrid_interval=0, min_side=16, max_side=64)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, m["L"], m["L"], m["n"], m["n"]) for m in members], stream=stream.cuda_stream)
+    for k, m in enumerate(members):
+        nf = m["n"] * r
+        xf = I.centers(0.0, m["L"], nf)
+        Bf = np.ascontiguousarray(np.broadcast_to(I.shelf_B(xf, depth=m["depth"], shelf_x=m["shelf_x"])[None, :],
+                                                  (nf, nf)))
+        H.set_bathymetry(k, Bf)
+        B0 = H.get_bathymetry(k, 0)
+        x0 = I.centers(0.0, m["L"], m["n"])
+        X, Y = np.meshgrid(x0, x0)
+        H.set_state(k, 0, I.layered_state(B0, I.hump_field(X, Y, *m["humps"]), -200.0 * np.ones_like(B0)))
+        lay = I.random_layout(5100 + k, m["n"] * r, m["n"] * r, max(4, m["n"] // 16), r)
+        H.set_patches(k, 1, lay)
+        H.interp_fine(0, k)
+    chosen = [H.autotune(l, iters=2) for l in range(2)]
+    upd = _interior_updates(H, n_members, 2, [r])
+    H.advance(1)
+    ms_b = _time_advance(torch, H, stream, steps)
+    H.set_execution(use_graphs=False, per_patch_launches=True)
+    H.advance(1)
+    ms_p = _time_advance(torch, H, stream, steps)
+    t, dt = H.get_time()
+    H.close()
+    lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
+    lp = upd * M_LAYERS * steps / (ms_p * 1e-3)
+    return {"workload": f"{n_members} members, coarse U{{128..512}}^2, seeded shelf depth/position and 1-4 humps, "
+                        "1 refined level (ratio 4, seeded patches)",
+            "members": n_members, "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
+            "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
+            "distinct_member_dt": int(len(set(np.round(dt, 12)))), "autotuned_tiles": chosen}
 
 
 def run_gpu(args):
@@ -164,12 +269,14 @@ def run_gpu(args):
     torch.cuda.set_device(dev)
     pkg.build()
 
+    # Each rank advances its own replica of the headline workload (independent problems).
     w = I.scale(N_CELLS, seed=1000 + rank)
     cfg = pkg.Config(M=2, dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
     stream = torch.cuda.Stream(device=dev)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, N_CELLS, N_CELLS)], stream=stream.cuda_stream)
     H.set_bathymetry(0, w["B"])
     H.set_state(0, 0, w["q"])
+    tiles = H.autotune(0, iters=3)
     dt = 0.9 * w["dx"] / 205.0
     H.set_dt(0, dt)
     for _ in range(args.warmup):
@@ -196,9 +303,8 @@ def run_gpu(args):
     clocks = clk.stop()
     per_kernel, total_launches = H.timing(enable=False)
 
-    # ---- end-to-end through the public API with host buffers ----
-    import torch as _t
-    qh = _t.empty(w["q"].shape, dtype=_t.float64, pin_memory=True).numpy()
+    # ---- end to end through the public API with pinned host buffers ----
+    qh = torch.empty(w["q"].shape, dtype=torch.float64, pin_memory=True).numpy()
     qh[...] = w["q"]
     xy = np.stack([np.linspace(1e4, 9e4, 32), np.linspace(2e4, 8e4, 32)], axis=1)
     e2e_steps = max(3, min(args.steps, 10))
@@ -209,7 +315,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         H.set_state(0, 0, qh)
         H.step_level(0)
-        g = H.read_gauges(0, xy) if hasattr(H, "read_gauges") else None
+        H.read_gauges(0, xy)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     H.close()
@@ -222,22 +328,23 @@ def run_gpu(args):
         tmax = float(tt.item())
     value = lcu_per_step * args.steps * ws / (tmax * 1e-3)
 
-    peaks = _peaks()
     sx_ms, sx_n = per_kernel["sweep_x"]
     sy_ms, sy_n = per_kernel["sweep_y"]
-    roof = None
-    if FP64_FLOP_PER_CELL_UPDATE:
-        step_ms = (sx_ms + sy_ms) / max(1, sx_n)
-        ach = FP64_FLOP_PER_CELL_UPDATE * N_CELLS * N_CELLS / (step_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": 1.012, "unit": "TFLOP/s", "frac": ach / 1.012,
-                "traffic": None}
+    x_launch_ms = sx_ms / max(1, sx_n)
+    ach = 0.5 * FP64_FLOP_PER_CELL_UPDATE * N_CELLS * N_CELLS / (x_launch_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "sweep_kernel<2,0> (x sweep)", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": SWEEP_X_DRAM_BYTES,
+            "flop_per_launch": 0.5 * FP64_FLOP_PER_CELL_UPDATE * N_CELLS * N_CELLS,
+            "launch_ms": x_launch_ms, "y_sweep_launch_ms": sy_ms / max(1, sy_n),
+            "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; a DFMA-chain microbenchmark "
+                         "reaches 1.012 TFLOP/s on this part"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "scale: 2048x2048 fixed grid, 2 layers, shelf bathymetry, 8 humps, order 2 MC",
-                   "cells": N_CELLS * N_CELLS, "layers": M_LAYERS, "l2": "inputs larger than L2 (201 MB state)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "config": {"workload": _workload_name(), "cells": N_CELLS * N_CELLS, "layers": M_LAYERS,
+                   "l2": "inputs larger than L2 (201 MB state per buffer), no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "tiles": tiles},
         "clocks": clocks,
         "gpu_launches": total_launches,
         "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in per_kernel.items() if v[1]},
@@ -245,6 +352,9 @@ def run_gpu(args):
         "e2e": {"value": lcu_per_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(w["q"].nbytes + xy.nbytes), "d2h_bytes_per_step": 32 * M_LAYERS * 8},
     }
+    if rank == 0 and not args.no_amr:
+        line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
+        line["ensemble"] = bench_ensemble(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -260,6 +370,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR and ensemble figures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

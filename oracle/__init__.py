@@ -80,6 +80,7 @@ def lib():
         L.or_flags.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _u8p, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _u8p]
         L.or_bathy_average.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.or_count_sweep.argtypes = [_pp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
         L.or_adjoint_step.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, _dp, _dp, _dp, _dp]
     return _lib
@@ -124,6 +125,45 @@ def sweep_line(P: Params, line, Bline, nu):
     mf = np.zeros((n + 1, P.M))
     s = lib().or_sweep_line(ctypes.byref(P), n, _d(line), _d(Bline), float(nu), _d(out), _d(mf))
     return out, s, mf
+
+
+def count_sweep(P: Params, line, Bline, nu):
+    """(additions, multiplications, divisions, square roots) of one 1-D sweep of the method
+    over a line of n cells (two ghosts per end), counted by the oracle's counting scalar."""
+    line = _c(line); Bline = _c(Bline)
+    out = (ctypes.c_longlong * 4)()
+    lib().or_count_sweep(ctypes.byref(P), line.shape[0] - 4, _d(line), _d(Bline), float(nu), out)
+    return tuple(int(v) for v in out)
+
+
+def flops_per_cell_update(P: Params, q, B, dx, dy, dt, rows, cols):
+    """FP64 operations of the method per cell update (x sweep + y sweep, one flop per +, -,
+    *, / and sqrt), averaged over the given interior rows (x sweep) and columns (y sweep)
+    of a dense state q [3M][ny][nx]; the halo edges of a line are charged to the line."""
+    F = 3 * P.M
+    ny, nx = B.shape
+    tot, cells = 0, 0
+    for j in rows:
+        line = np.zeros((nx + 4, F))
+        line[2:-2] = q[:, j, :].T
+        line[:2] = line[2:4][::-1]; line[-2:] = line[-4:-2][::-1]
+        for m in range(P.M):
+            line[:2, 3 * m + 1] *= -1; line[-2:, 3 * m + 1] *= -1
+        Bl = np.concatenate([B[j, :2][::-1], B[j], B[j, -2:][::-1]])
+        tot += sum(count_sweep(P, line, Bl, dt / dx)); cells += nx
+    for i in cols:
+        line = np.zeros((ny + 4, F))
+        for m in range(P.M):
+            line[2:-2, 3 * m] = q[3 * m, :, i]
+            line[2:-2, 3 * m + 1] = q[3 * m + 2, :, i]
+            line[2:-2, 3 * m + 2] = q[3 * m + 1, :, i]
+        line[:2] = line[2:4][::-1]; line[-2:] = line[-4:-2][::-1]
+        for m in range(P.M):
+            line[:2, 3 * m + 1] *= -1; line[-2:, 3 * m + 1] *= -1
+        Bl = np.concatenate([B[:2, i][::-1], B[:, i], B[-2:, i][::-1]])
+        tot += sum(count_sweep(P, line, Bl, dt / dy)); cells += ny
+    # one x sweep and one y sweep per cell update
+    return 2.0 * tot / cells
 
 
 # --------------------------------------------------------------------------- grid level

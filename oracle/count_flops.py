@@ -1,0 +1,27 @@
+"""Prints the algorithmic FP64 operation count per cell update of the method (one x sweep
+plus one y sweep, second order with the MC limiter, eigenvalue guesses plus two Newton
+steps), counted by the oracle's counting scalar on interior rows and columns of the
+2048 x 2048 shelf workload. Run: python -m oracle.count_flops
+
+TEST/MEASUREMENT INFRASTRUCTURE: the constant in bench.py comes from this script."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import oracle as O  # noqa: E402
+from paper_1803_01450_gb300 import inputs as I  # noqa: E402
+
+
+def main():
+    w = I.scale(2048)
+    dt = 0.9 * w["dx"] / 205.0
+    for order, eigen in ((2, 0), (1, 0)):
+        P = O.params(M=2, dry_tol=1e-3, order=order, eigen=eigen)
+        f = O.flops_per_cell_update(P, w["q"], w["B"], w["dx"], w["dy"], dt, rows=[100, 1024, 1900],
+                                    cols=[100, 1024, 1900])
+        print(f"order={order} eigen={eigen}: {f:.2f} FP64 operations per cell update")
+
+
+if __name__ == "__main__":
+    main()

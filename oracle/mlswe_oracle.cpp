@@ -93,6 +93,31 @@ template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
   return c; }
 using std::sqrt;
 
+// Operation-counting scalar: every +, -, *, / and sqrt on it increments a global counter
+// (used only to count the floating-point work of the method per cell update).
+struct OpCount { long long add = 0, mul = 0, div = 0, sqrt = 0; };
+static OpCount g_ops;
+struct Cnt {
+  double v;
+  Cnt() : v(0.0) {}
+  Cnt(double x) : v(x) {}
+};
+inline double val(const Cnt& x) { return x.v; }
+inline Cnt operator+(const Cnt& a, const Cnt& b) { g_ops.add++; return Cnt(a.v + b.v); }
+inline Cnt operator-(const Cnt& a, const Cnt& b) { g_ops.add++; return Cnt(a.v - b.v); }
+inline Cnt operator-(const Cnt& a) { return Cnt(-a.v); }
+inline Cnt operator*(const Cnt& a, const Cnt& b) { g_ops.mul++; return Cnt(a.v * b.v); }
+inline Cnt operator/(const Cnt& a, const Cnt& b) { g_ops.div++; return Cnt(a.v / b.v); }
+inline Cnt operator+(const Cnt& a, double b) { return a + Cnt(b); }
+inline Cnt operator+(double a, const Cnt& b) { return Cnt(a) + b; }
+inline Cnt operator-(const Cnt& a, double b) { return a - Cnt(b); }
+inline Cnt operator-(double a, const Cnt& b) { return Cnt(a) - b; }
+inline Cnt operator*(const Cnt& a, double b) { return a * Cnt(b); }
+inline Cnt operator*(double a, const Cnt& b) { return Cnt(a) * b; }
+inline Cnt operator/(const Cnt& a, double b) { return a / Cnt(b); }
+inline Cnt operator/(double a, const Cnt& b) { return Cnt(a) / b; }
+inline Cnt sqrt(const Cnt& a) { g_ops.sqrt++; return Cnt(std::sqrt(a.v)); }
+
 template <class T> inline T tmin(const T& a, const T& b) { return val(b) < val(a) ? b : a; }
 template <class T> inline T tmax(const T& a, const T& b) { return val(b) > val(a) ? b : a; }
 template <class T> inline T tabs(const T& a) { return val(a) < 0.0 ? -a : a; }
@@ -589,6 +614,21 @@ double or_sweep_line(const or_params* pp, int n, const double* line, const doubl
   const Params P = to_params(pp);
   int lost = 0;
   return sweep_line(P, n, line, Bline, nu, out, massflux, &lost);
+}
+
+// Floating-point operations of one 1-D sweep over a line of n cells (two ghosts per end),
+// counted with the counting scalar: out[0..3] = additions/subtractions, multiplications,
+// divisions, square roots.
+void or_count_sweep(const or_params* pp, int n, const double* line, const double* Bline, double nu, long long* out) {
+  const Params P = to_params(pp);
+  const int F = 3 * P.M;
+  std::vector<Cnt> l((n + 4) * F), b(n + 4), o(n * F);
+  for (int k = 0; k < (n + 4) * F; ++k) l[k] = Cnt(line[k]);
+  for (int k = 0; k < n + 4; ++k) b[k] = Cnt(Bline[k]);
+  g_ops = OpCount();
+  int lost = 0;
+  sweep_line(P, n, l.data(), b.data(), nu, o.data(), (Cnt*)nullptr, &lost);
+  out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt;
 }
 
 void or_fill_walls(int M, int nx, int ny, double* q, double* B, int sides) {

@@ -167,6 +167,47 @@ def ensemble_state(member: dict, n: int):
     return q, B
 
 
+def random_layout(seed: int, nx: int, ny: int, n_boxes: int, r: int, side=(16, 64), parents=None,
+                  margin: int = 2, max_tries: int = 200000):
+    """Seeded random non-overlapping patch boxes of one refined level (fine indices,
+    half-open (i0, j0, i1, j1)), sides drawn from U{side} rounded to multiples of r, corners
+    on multiples of r. With `parents` (boxes of the coarser level, its indices) every box
+    lies inside one parent shrunk by `margin` coarse cells (not at the domain boundary).
+    Stands in for the patch layouts of a regridded level; returns fewer boxes than asked
+    when no more fit."""
+    g = rng(seed)
+    occ = np.zeros((ny // r, nx // r), dtype=bool)
+    boxes = []
+    regions = [(0, 0, nx // r, ny // r)]
+    if parents is not None:
+        NXc, NYc = nx // r, ny // r
+        regions = []
+        for (i0, j0, i1, j1) in parents:
+            a0 = i0 if i0 == 0 else i0 + margin
+            b0 = j0 if j0 == 0 else j0 + margin
+            a1 = i1 if i1 == NXc else i1 - margin
+            b1 = j1 if j1 == NYc else j1 - margin
+            if a1 > a0 and b1 > b0:
+                regions.append((a0, b0, a1, b1))
+    tries = 0
+    while len(boxes) < n_boxes and tries < max_tries:
+        tries += 1
+        a0, b0, a1, b1 = regions[int(g.integers(0, len(regions)))]
+        w = max(1, int(g.integers(side[0], side[1] + 1)) // r)
+        h = max(1, int(g.integers(side[0], side[1] + 1)) // r)
+        w, h = min(w, a1 - a0), min(h, b1 - b0)
+        if w <= 0 or h <= 0:
+            continue
+        i0 = int(g.integers(a0, a1 - w + 1))
+        j0 = int(g.integers(b0, b1 - h + 1))
+        if occ[j0:j0 + h, i0:i0 + w].any():
+            continue
+        occ[j0:j0 + h, i0:i0 + w] = True
+        boxes.append((i0 * r, j0 * r, (i0 + w) * r, (j0 + h) * r))
+    boxes.sort(key=lambda b: (b[1], b[0]))
+    return boxes
+
+
 def gaussian_random_state(seed: int, M: int, nx: int, ny: int, depth=(1.0, 0.5), amp=0.05, vel=0.05):
     """Random smooth-ish wet state for parity tests: positive depths with perturbations
     and small velocities; bathymetry with gentle variation."""
