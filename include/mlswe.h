@@ -215,6 +215,27 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
  * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range. */
 mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm);
 
+/* Discrete adjoint of the fixed-grid step (not written out in the paper; the
+ * forward step is the per-patch solver the paper's AMR drives, Sec. 1-2).
+ * Gauge misfit J = sum_{n=1..n_steps} sum_g (eta_1(cell_g, Q^n) - obs[n-1][g])^2
+ * with eta_1 = B + h_M + ... + h_1 (Eq. (4)). Requires a hierarchy with one
+ * member, one level and order 1, a fixed time step (mlswe_set_dt) and a wet
+ * state (every layer wet on both sides of every edge; EINVAL otherwise).
+ * gauge_ij: host int32 [n_gauges][2] cell indices (i, j); obs: host
+ * [n_steps][n_gauges]. The forward pass keeps a state every ckpt_every steps;
+ * the backward pass recomputes each segment from it. */
+mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_gauges, const int32_t* gauge_ij,
+                                 const double* obs);
+
+/* Runs n_steps first-order steps from the current level-0 state (advancing it)
+ * and returns J in *loss (host). */
+mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss);
+
+/* Gradient of J of the last mlswe_fixed_forward: dL_dq0 receives dJ/dQ^0
+ * (device, dense [3M][ny][nx], caller-owned) and dL_dB receives dJ/dB (device,
+ * dense [ny][nx]; B enters every step's flux jumps and every gauge's eta_1). */
+mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB);
+
 /* One dimensionally split step of a single grid with walls on all sides that
  * allocates no memory. The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory while they step the model
@@ -240,7 +261,8 @@ mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx, int ny, d
  * measured by CUDA events recorded around every launch on the hierarchy's
  * stream while enabled, and the total number of kernels launched (timed or
  * not). Classes: 0 x sweep, 1 y sweep, 2 ghost fill, 3 refinement, 4 coarsening
- * (and bathymetry means), 5 flags, 6 reflux, 7 other. n: capacity of ms_out and
+ * (and bathymetry means), 5 flags, 6 reflux, 7 other, 8 adjoint (the transposed
+ * sweeps and the recomputed x sweeps of the backward pass). n: capacity of ms_out and
  * launches_out (either may be NULL). enable: timing on (1) or off (0) from now
  * on. Synchronises the stream. */
 mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long long* launches_out,

@@ -861,6 +861,17 @@ void adjoint_sweep_line(const Params& P, int n, const double* line, const double
 
 }  // namespace
 
+// Jacobian of the first-order fluctuations of one edge, J[12][14]: rows A-dQ (6), A+dQ (6);
+// columns qL (6), qR (6), BL, BR (dual numbers).
+extern "C" void or_edge_jacobian(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
+                                 double* J) {
+  const Params P = to_params(pp);
+  double Jm[12][ND], am[6], ap[6];
+  edge_jacobian(P, qL, qR, BL, BR, Jm, am, ap);
+  for (int o = 0; o < 12; ++o)
+    for (int k = 0; k < ND; ++k) J[o * ND + k] = Jm[o][k];
+}
+
 extern "C" void or_adjoint_step(const or_params* pp, int nx, int ny, double dx, double dy, double dt,
                                 const double* qn, const double* Bd, double* lam, double* gB) {
   Params P = to_params(pp);

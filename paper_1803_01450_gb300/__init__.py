@@ -123,12 +123,16 @@ _SIGS = {
     "mlswe_read_gauges": [_H, ctypes.c_int, ctypes.c_int, _dp, _dp],
     "mlswe_set_tiles": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "mlswe_set_execution": [_H, ctypes.c_int, ctypes.c_int],
+    "mlswe_adjoint_setup": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _dp],
+    "mlswe_fixed_forward": [_H, _dp],
+    "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
     "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
                      ctypes.POINTER(ctypes.c_longlong)],
 }
 
-KERNEL_CLASSES = ["sweep_x", "sweep_y", "ghost_fill", "interp_fine", "average", "flags", "reflux", "other"]
+KERNEL_CLASSES = ["sweep_x", "sweep_y", "ghost_fill", "interp_fine", "average", "flags", "reflux", "other",
+                  "adjoint"]
 
 
 def build(force: bool = False) -> str:
@@ -323,6 +327,22 @@ class Hierarchy:
 
     def set_tiles(self, dir: int, length: int, lines: int, ctas_per_sm: int = 1):
         self._check(self.L.mlswe_set_tiles(self.h, dir, length, lines, ctas_per_sm), "set_tiles")
+
+    def adjoint_setup(self, n_steps: int, ckpt_every: int, gauge_ij: np.ndarray, obs: np.ndarray):
+        g = np.ascontiguousarray(np.asarray(gauge_ij, dtype=np.int32).reshape(-1, 2))
+        o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
+        self._check(self.L.mlswe_adjoint_setup(self.h, n_steps, ckpt_every, len(g), g.ctypes.data_as(_i32p), _d(o)),
+                    "adjoint_setup")
+
+    def fixed_forward(self) -> float:
+        loss = ctypes.c_double(0.0)
+        self._check(self.L.mlswe_fixed_forward(self.h, ctypes.byref(loss)), "fixed_forward")
+        return loss.value
+
+    def fixed_backward(self, dq0_ptr: int, dB_ptr: int):
+        """Writes dJ/dQ^0 ([3M][ny][nx]) and dJ/dB ([ny][nx]) into caller-owned device buffers."""
+        self._check(self.L.mlswe_fixed_backward(self.h, ctypes.c_void_p(dq0_ptr), ctypes.c_void_p(dB_ptr)),
+                    "fixed_backward")
 
     def timing(self, enable: bool = True):
         """Per-kernel-class device time (ms) and launches since the last call; resets them."""

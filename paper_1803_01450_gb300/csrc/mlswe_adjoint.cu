@@ -1,0 +1,446 @@
+// Discrete adjoint of the fixed-grid, first-order, fixed-dt step on a walled
+// single-level grid (wet states only), for gradients of a gauge misfit
+//   J = sum_{n=1..N} sum_g (eta_1(cell_g, Q^n) - obs_{n,g})^2,   eta_1 = B + h_2 + h_1 (Eq. (4)),
+// with respect to the initial state and the bathymetry. The forward pass keeps a
+// checkpoint every `ckpt_every` steps; the backward pass recomputes each segment
+// from its checkpoint and applies the transposed step in reverse:
+//   lambda_n = (dQ^{n+1}/dQ^n)^T lambda_{n+1} + dJ_n/dQ^n,
+//   dJ/dB   += (dQ^{n+1}/dB)^T lambda_{n+1} + dJ_n/dB.
+// The transposed split step runs the y sweep's adjoint on the recomputed state
+// after the x sweep, then the x sweep's adjoint; each edge's contribution is the
+// hand-written vector-Jacobian product of mlswe_adjoint.cuh. Wall ghost cells are
+// mirrors of interior cells, so their cotangents fold back into those cells.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cstring>
+#include "mlswe_adjoint.cuh"
+#include "mlswe_internal.h"
+
+namespace mlswe {
+
+template <int DIR>
+__device__ __forceinline__ int acslot(int l, int k, int len, int nl) {  // k in [0, len + 2): cells -1 .. len
+  return DIR == 0 ? l * (len + 2) + k : k * nl + l;
+}
+template <int DIR>
+__device__ __forceinline__ int aeslot(int l, int e, int len, int nl) {  // e in [0, len + 1): edges -1/2 .. len-1/2
+  return DIR == 0 ? l * (len + 1) + e : e * nl + l;
+}
+
+// Adjoint of one first-order sweep over the tiles of the level. state: input of the
+// forward sweep (pitched like the level); lam_out: cotangent of its output; lam_in:
+// cotangent of its input (written); gB: bathymetry cotangent (accumulated).
+template <int M, int DIR>
+__global__ void __launch_bounds__(kThreads, 1)
+adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
+                     const int* __restrict__ n_items_dev, const double* __restrict__ state,
+                     const double* __restrict__ lam_out, double* __restrict__ lam_in, double* __restrict__ gB,
+                     unsigned int* __restrict__ status) {
+  using R = Rec<M>;
+  constexpr int F = 3 * M;
+  constexpr int NE = 2 * F + 2;  // edge outputs: qL_b, qR_b, BL_b, BR_b
+  extern __shared__ double smem[];
+  double* cell = smem;                       // [R::N][kMaxCells]
+  double* lamo = cell + R::N * kMaxCells;    // [F][kMaxCells] (normal frame)
+  double* eout = lamo + F * kMaxCells;       // [NE][kMaxEdges]
+  unsigned char* wetb = reinterpret_cast<unsigned char*>(eout + NE * kMaxEdges);
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const SweepItem item = items[it];
+    const LevelDesc& D = descs[item.desc];
+    const int len = item.len, nl = item.nlines;
+    const int NX = D.NX, NY = D.NY, Pt = D.P;
+    const size_t plane = (size_t)NY * Pt;
+    const double nu = (*D.dt) * (DIR == 0 ? D.inv_dx : D.inv_dy);
+    // ---- load cells -1 .. len of every line (mirrored at walls), and their output cotangents
+    const int ncell = nl * (len + 2);
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+      int l, k;
+      if (DIR == 0) { l = t / (len + 2); k = t - l * (len + 2); }
+      else { k = t / nl; l = t - k * nl; }
+      int i, j;
+      if (DIR == 0) { i = item.i0 - 1 + k; j = item.j0 + l; }
+      else { i = item.i0 + l; j = item.j0 - 1 + k; }
+      double sgn = 1.0;
+      bool ghost = false;
+      if (DIR == 0) {
+        if (i < 0) { i = -1 - i; sgn = -1.0; ghost = true; }
+        else if (i >= NX) { i = 2 * NX - 1 - i; sgn = -1.0; ghost = true; }
+      } else {
+        if (j < 0) { j = -1 - j; sgn = -1.0; ghost = true; }
+        else if (j >= NY) { j = 2 * NY - 1 - j; sgn = -1.0; ghost = true; }
+      }
+      const size_t o = (size_t)j * Pt + i;
+      const int c = acslot<DIR>(l, k, len, nl);
+      double rec[R::N];
+      rec[R::BB] = D.B[o];
+      int wet = 0;
+      bool above = true;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double h = state[(3 * m) * plane + o];
+        const double hu = state[(3 * m + 1) * plane + o];
+        const double hv = state[(3 * m + 2) * plane + o];
+        const double hn = (DIR == 0 ? hu : hv) * sgn;
+        const double ht = DIR == 0 ? hv : hu;
+        rec[3 * m] = h; rec[3 * m + 1] = hn; rec[3 * m + 2] = ht;
+        const bool w = above && (h > P.dry_tol);
+        above = w;
+        wet |= w ? (1 << m) : 0;
+        double un = 0.0, ut = 0.0;
+        if (w) { const double ih = rcp(h); un = hn * ih; ut = ht * ih; }
+        rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
+        rec[R::SQ + m] = sqrt(fmax(h, 0.0));
+        // cotangent of the sweep output at this cell (zero for a wall ghost: not an output)
+        const double lh = ghost ? 0.0 : lam_out[(3 * m) * plane + o];
+        const double lu = ghost ? 0.0 : lam_out[(3 * m + 1) * plane + o];
+        const double lv = ghost ? 0.0 : lam_out[(3 * m + 2) * plane + o];
+        lamo[(3 * m) * kMaxCells + c] = lh;
+        lamo[(3 * m + 1) * kMaxCells + c] = DIR == 0 ? lu : lv;
+        lamo[(3 * m + 2) * kMaxCells + c] = DIR == 0 ? lv : lu;
+      }
+      double acc = rec[R::BB];
+#pragma unroll
+      for (int m = M - 1; m >= 0; --m) { acc = acc + rec[3 * m]; rec[R::ETA + m] = acc; }
+#pragma unroll
+      for (int f = 0; f < R::N; ++f) cell[f * kMaxCells + c] = rec[f];
+      wetb[c] = (unsigned char)wet;
+    }
+    __syncthreads();
+    // ---- edge VJPs: edge e between cells e-1 and e (e = 0 .. len)
+    const int nedge = nl * (len + 1);
+    for (int t = threadIdx.x; t < nedge; t += blockDim.x) {
+      int l, e;
+      if (DIR == 0) { l = t / (len + 1); e = t - l * (len + 1); }
+      else { e = t / nl; l = t - e * nl; }
+      const int cl = acslot<DIR>(l, e, len, nl), cr = acslot<DIR>(l, e + 1, len, nl);
+      double cL[R::N], cR[R::N], amb[6], apb[6];
+#pragma unroll
+      for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
+#pragma unroll
+      for (int f = 0; f < 6; ++f) { amb[f] = 0.0; apb[f] = 0.0; }
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        amb[f] = -nu * lamo[f * kMaxCells + cl];  // A-dQ of this edge updates the left cell
+        apb[f] = -nu * lamo[f * kMaxCells + cr];  // A+dQ updates the right cell
+      }
+      double qLb[6] = {0, 0, 0, 0, 0, 0}, qRb[6] = {0, 0, 0, 0, 0, 0}, BLb = 0.0, BRb = 0.0;
+      const bool ok = (M == 2) ? edge_vjp_2(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb)
+                               : edge_vjp_1(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb);
+      if (!ok) atomicOr(status, 4u);
+      const int es = aeslot<DIR>(l, e, len, nl);
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        eout[f * kMaxEdges + es] = qLb[f];
+        eout[(F + f) * kMaxEdges + es] = qRb[f];
+      }
+      eout[(2 * F) * kMaxEdges + es] = BLb;
+      eout[(2 * F + 1) * kMaxEdges + es] = BRb;
+    }
+    __syncthreads();
+    // ---- gather per cell: lam_in = lam_out + right side of edge k + left side of edge k+1,
+    // plus the ghost cotangents folded back at walls
+    const int ncl = nl * len;
+    for (int t = threadIdx.x; t < ncl; t += blockDim.x) {
+      int l, k;
+      if (DIR == 0) { l = t / len; k = t - l * len; }
+      else { k = t / nl; l = t - k * nl; }
+      const int c = acslot<DIR>(l, k + 1, len, nl);
+      const int ew = aeslot<DIR>(l, k, len, nl), ee = aeslot<DIR>(l, k + 1, len, nl);
+      int i, j;
+      if (DIR == 0) { i = item.i0 + k; j = item.j0 + l; }
+      else { i = item.i0 + l; j = item.j0 + k; }
+      const int a = DIR == 0 ? i : j, NA = DIR == 0 ? NX : NY;
+      double v[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+        v[f] = lamo[f * kMaxCells + c] + eout[(F + f) * kMaxEdges + ew] + eout[f * kMaxEdges + ee];
+      double bb = eout[(2 * F + 1) * kMaxEdges + ew] + eout[(2 * F) * kMaxEdges + ee];
+      if (a == 0) {  // ghost -1 = mirror of this cell: its cotangent (left side of edge 0)
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[f] += (f % 3 == 1 ? -1.0 : 1.0) * eout[f * kMaxEdges + ew];
+        bb += eout[(2 * F) * kMaxEdges + ew];
+      }
+      if (a == NA - 1) {  // ghost NA = mirror of this cell (right side of edge NA)
+#pragma unroll
+        for (int f = 0; f < F; ++f) v[f] += (f % 3 == 1 ? -1.0 : 1.0) * eout[(F + f) * kMaxEdges + ee];
+        bb += eout[(2 * F + 1) * kMaxEdges + ee];
+      }
+      const size_t o = (size_t)j * Pt + i;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        lam_in[(3 * m) * plane + o] = v[3 * m];
+        lam_in[(3 * m + 1) * plane + o] = DIR == 0 ? v[3 * m + 1] : v[3 * m + 2];
+        lam_in[(3 * m + 2) * plane + o] = DIR == 0 ? v[3 * m + 2] : v[3 * m + 1];
+      }
+      gB[o] += bb;
+    }
+    __syncthreads();
+  }
+}
+
+static size_t adjoint_smem_bytes(int M) {
+  const int rn = 7 * M + 1, F = 3 * M, ne = 2 * F + 2;
+  return (size_t)rn * kMaxCells * 8 + (size_t)F * kMaxCells * 8 + (size_t)ne * kMaxEdges * 8 + kMaxCells;
+}
+
+template <int M, int DIR>
+static cudaError_t launch_adjoint_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items, const int* n,
+                                    int grid, const double* state, const double* lam_out, double* lam_in, double* gB,
+                                    unsigned int* status, cudaStream_t st) {
+  const size_t sm = adjoint_smem_bytes(M);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e =
+        cudaFuncSetAttribute(adjoint_sweep_kernel<M, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  adjoint_sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in, gB, status);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_adjoint_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                                        const int* n, int grid, const double* state, const double* lam_out,
+                                        double* lam_in, double* gB, unsigned int* status, cudaStream_t st) {
+  if (P.M == 1)
+    return dir == 0 ? launch_adjoint_t<1, 0>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st)
+                    : launch_adjoint_t<1, 1>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st);
+  return dir == 0 ? launch_adjoint_t<2, 0>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st)
+                  : launch_adjoint_t<2, 1>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st);
+}
+
+// Gauge misfit of one state: loss += sum_g (eta_1 - obs_g)^2, summed in gauge order by one
+// thread (deterministic); with lam != null also adds its gradient 2 (eta_1 - obs_g) to the
+// cotangents of h_1, ..., h_M and of B at the gauge cells.
+__global__ void gauge_misfit_kernel(int M, const LevelDesc* __restrict__ descs, const double* __restrict__ q,
+                                    const int* __restrict__ gij, int ng, const double* __restrict__ obs,
+                                    double* loss, double* lam, double* gB) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const LevelDesc& D = descs[0];
+  const size_t plane = (size_t)D.NY * D.P;
+  double s = 0.0;
+  for (int g = 0; g < ng; ++g) {
+    const size_t o = (size_t)gij[2 * g + 1] * D.P + gij[2 * g];
+    double eta = D.B[o];
+    for (int m = M - 1; m >= 0; --m) eta = eta + q[(3 * m) * plane + o];
+    const double r = eta - obs[g];
+    s += r * r;
+    if (lam) {
+      for (int m = 0; m < M; ++m) lam[(3 * m) * plane + o] += 2.0 * r;
+      gB[o] += 2.0 * r;
+    }
+  }
+  if (loss) *loss += s;
+}
+
+}  // namespace mlswe
+
+using namespace mlswe;
+
+namespace {
+
+struct Adjoint {
+  int n_steps = 0, ckpt = 0, ng = 0;
+  size_t state_bytes = 0;
+  std::vector<double*> ckpts;  // [n_steps / ckpt + 1]
+  std::vector<double*> slots;  // [ckpt + 1]
+  double* lam = nullptr;
+  double* lam2 = nullptr;
+  double* gB = nullptr;
+  double* qs = nullptr;
+  int* gij = nullptr;
+  double* obs = nullptr;
+  double* loss = nullptr;
+  LevelDesc* desc = nullptr;  // [1] level-0 descriptor with q[] re-pointed per recomputed step
+  bool forward_done = false;
+};
+
+}  // namespace
+
+// The adjoint buffers hang off the hierarchy (device memory is in its allocation list
+// and is released with it; the host record is deleted by adjoint_release).
+static Adjoint* adj_of(mlswe_hier* h, bool create) {
+  if (!h->adj && create) h->adj = new Adjoint();
+  return (Adjoint*)h->adj;
+}
+
+namespace mlswe {
+void adjoint_release(Hier* H) {
+  delete (Adjoint*)H->adj;
+  H->adj = nullptr;
+}
+}  // namespace mlswe
+
+static mlswe_status afail(mlswe_hier* h, mlswe_status s, const char* msg) {
+  h->err = msg;
+  return s;
+}
+
+#define ACUDA(h, call)                                                                \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+      return MLSWE_ECUDA;                                                             \
+    }                                                                                 \
+  } while (0)
+
+// Copies a pitched level state.
+static cudaError_t copy_state(Hier* H, double* dst, const double* src) {
+  const Level& V = H->mem[0].lev[0];
+  return cudaMemcpyAsync(dst, src, (size_t)3 * H->cfg.M * V.NY * V.P * 8, cudaMemcpyDeviceToDevice, H->st);
+}
+
+// One forward first-order step from `in` to `out` (or only its x sweep, into the Q* buffer)
+// through a private copy of the level descriptor whose state pointers are re-aimed. The
+// descriptor copy is stream-ordered behind the kernels that read the previous one.
+static mlswe_status adj_forward_step(Hier* H, Adjoint* A, const double* in, double* out, bool x_only) {
+  const Level& V = H->mem[0].lev[0];
+  LevelDesc D{};
+  D.q[0] = const_cast<double*>(in);
+  D.q[1] = out;
+  D.qs = A->qs;
+  D.B = V.B;
+  D.dt = H->d_dt;
+  D.NX = V.NX; D.NY = V.NY; D.P = V.P;
+  D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
+  ACUDA(H, cudaMemcpyAsync(A->desc, &D, sizeof(D), cudaMemcpyHostToDevice, H->st));
+  const int grid = H->blocks_per_sm * H->num_sms;
+  for (int dir = 0; dir < (x_only ? 1 : 2); ++dir) {
+    Hier::WorkList& W = H->wl[dir];
+    int tok;
+    timer_begin(H, KC_ADJOINT, &tok);
+    ACUDA(H, launch_sweep(dir, H->dp, A->desc, W.d_items, W.d_count, grid, 0, 0, H->d_smax, nullptr, H->st));
+    timer_end(H, tok);
+  }
+  return MLSWE_OK;
+}
+
+extern "C" {
+
+mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_gauges, const int32_t* gauge_ij,
+                                 const double* obs) {
+  if (!h || n_steps < 1 || ckpt_every < 1 || n_gauges < 0 || (n_gauges > 0 && (!gauge_ij || !obs)))
+    return h ? afail(h, MLSWE_EINVAL, "adjoint_setup: bad argument") : MLSWE_EINVAL;
+  if (h->n_members != 1 || h->L != 1 || h->cfg.order != 1)
+    return afail(h, MLSWE_EINVAL, "adjoint_setup: needs one member, one level and order 1");
+  const Level& V = h->mem[0].lev[0];
+  for (int g = 0; g < n_gauges; ++g)
+    if (gauge_ij[2 * g] < 0 || gauge_ij[2 * g] >= V.NX || gauge_ij[2 * g + 1] < 0 || gauge_ij[2 * g + 1] >= V.NY)
+      return afail(h, MLSWE_EINVAL, "adjoint_setup: gauge cell outside the grid");
+  Adjoint* A = adj_of(h, true);
+  A->n_steps = n_steps;
+  A->ckpt = ckpt_every;
+  A->ng = n_gauges;
+  A->state_bytes = (size_t)3 * h->cfg.M * V.NY * V.P * 8;
+  const int nck = n_steps / ckpt_every + 1;
+  auto grab = [&](size_t bytes) { return (double*)dev_alloc(h, bytes); };
+  while ((int)A->ckpts.size() < nck) A->ckpts.push_back(grab(A->state_bytes));
+  while ((int)A->slots.size() < ckpt_every + 1) A->slots.push_back(grab(A->state_bytes));
+  if (!A->lam) A->lam = grab(A->state_bytes);
+  if (!A->lam2) A->lam2 = grab(A->state_bytes);
+  if (!A->qs) A->qs = grab(A->state_bytes);
+  if (!A->gB) A->gB = grab((size_t)V.NY * V.P * 8);
+  if (!A->loss) A->loss = grab(64);
+  if (!A->desc) A->desc = (LevelDesc*)dev_alloc(h, sizeof(LevelDesc));
+  if (A->gij) dev_free(h, A->gij);
+  if (A->obs) dev_free(h, A->obs);
+  A->gij = (int*)dev_alloc(h, std::max(1, 2 * n_gauges) * sizeof(int));
+  A->obs = grab(std::max<size_t>(1, (size_t)n_steps * n_gauges) * 8);
+  for (double* p : A->ckpts) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+  for (double* p : A->slots) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+  if (!A->lam || !A->lam2 || !A->qs || !A->gB || !A->loss || !A->desc || !A->gij || !A->obs)
+    return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+  if (n_gauges > 0) {
+    ACUDA(h, cudaMemcpyAsync(A->gij, gauge_ij, 2 * n_gauges * sizeof(int), cudaMemcpyHostToDevice, h->st));
+    ACUDA(h, cudaMemcpyAsync(A->obs, obs, (size_t)n_steps * n_gauges * 8, cudaMemcpyHostToDevice, h->st));
+  }
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  A->forward_done = false;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss) {
+  if (!h) return MLSWE_EINVAL;
+  Adjoint* A = adj_of(h, false);
+  if (!A || A->n_steps < 1) return afail(h, MLSWE_EINVAL, "fixed_forward: call mlswe_adjoint_setup first");
+  for (int dir = 0; dir < 2; ++dir) {
+    mlswe_status s = ensure_worklist(h, 0, dir);
+    if (s != MLSWE_OK) return s;
+  }
+  ACUDA(h, cudaMemsetAsync(A->loss, 0, 8, h->st));
+  ACUDA(h, copy_state(h, A->ckpts[0], h->mem[0].lev[0].q[h->parity[0]]));
+  for (int n = 1; n <= A->n_steps; ++n) {
+    mlswe_status s = enqueue_level_step(h, 0, 1);
+    if (s != MLSWE_OK) return s;
+    int tok;
+    timer_begin(h, KC_OTHER, &tok);
+    gauge_misfit_kernel<<<1, 32, 0, h->st>>>(h->cfg.M, h->d_desc, h->mem[0].lev[0].q[h->parity[0]], A->gij, A->ng,
+                                             A->obs + (size_t)(n - 1) * A->ng, A->loss, nullptr, nullptr);
+    ACUDA(h, cudaGetLastError());
+    timer_end(h, tok);
+    if (n % A->ckpt == 0 && n / A->ckpt < (int)A->ckpts.size())
+      ACUDA(h, copy_state(h, A->ckpts[n / A->ckpt], h->mem[0].lev[0].q[h->parity[0]]));
+  }
+  double l = 0.0;
+  ACUDA(h, cudaMemcpyAsync(&l, A->loss, 8, cudaMemcpyDeviceToHost, h->st));
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  if (loss) *loss = l;
+  A->forward_done = true;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
+  if (!h || !dL_dq0 || !dL_dB) return h ? afail(h, MLSWE_EINVAL, "fixed_backward: bad argument") : MLSWE_EINVAL;
+  Adjoint* A = adj_of(h, false);
+  if (!A || !A->forward_done) return afail(h, MLSWE_EINVAL, "fixed_backward: run mlswe_fixed_forward first");
+  const Level& V = h->mem[0].lev[0];
+  const int M = h->cfg.M, F = 3 * M;
+  const size_t plane = (size_t)V.NY * V.P;
+  const int grid = h->blocks_per_sm * h->num_sms;
+  ACUDA(h, cudaMemsetAsync(A->lam, 0, A->state_bytes, h->st));
+  ACUDA(h, cudaMemsetAsync(A->gB, 0, plane * 8, h->st));
+  ACUDA(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
+  const int N = A->n_steps, C = A->ckpt;
+  const int nseg = (N + C - 1) / C;
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int k0 = seg * C, k1 = std::min(N, k0 + C);
+    // recompute Q^{k0} .. Q^{k1} into the slots
+    ACUDA(h, copy_state(h, A->slots[0], A->ckpts[seg]));
+    for (int n = k0; n < k1; ++n) {
+      mlswe_status s = adj_forward_step(h, A, A->slots[n - k0], A->slots[n - k0 + 1], false);
+      if (s != MLSWE_OK) return s;
+    }
+    for (int n = k1 - 1; n >= k0; --n) {
+      // gauge term of J at Q^{n+1}
+      int tok;
+      timer_begin(h, KC_OTHER, &tok);
+      gauge_misfit_kernel<<<1, 32, 0, h->st>>>(M, h->d_desc, A->slots[n + 1 - k0], A->gij, A->ng,
+                                               A->obs + (size_t)n * A->ng, nullptr, A->lam, A->gB);
+      ACUDA(h, cudaGetLastError());
+      timer_end(h, tok);
+      // Q* of step n, then the transposed y sweep and x sweep
+      mlswe_status s = adj_forward_step(h, A, A->slots[n - k0], A->slots[n + 1 - k0], true);
+      if (s != MLSWE_OK) return s;
+      timer_begin(h, KC_ADJOINT, &tok);
+      ACUDA(h, launch_adjoint_sweep(1, h->dp, A->desc, h->wl[1].d_items, h->wl[1].d_count, grid, A->qs, A->lam,
+                                    A->lam2, A->gB, h->d_status, h->st));
+      timer_end(h, tok);
+      timer_begin(h, KC_ADJOINT, &tok);
+      ACUDA(h, launch_adjoint_sweep(0, h->dp, A->desc, h->wl[0].d_items, h->wl[0].d_count, grid, A->slots[n - k0],
+                                    A->lam2, A->lam, A->gB, h->d_status, h->st));
+      timer_end(h, tok);
+    }
+  }
+  ACUDA(h, cudaMemcpy2DAsync(dL_dq0, V.NX * 8, A->lam, V.P * 8, V.NX * 8, (size_t)F * V.NY, cudaMemcpyDeviceToDevice,
+                             h->st));
+  ACUDA(h, cudaMemcpy2DAsync(dL_dB, V.NX * 8, A->gB, V.P * 8, V.NX * 8, V.NY, cudaMemcpyDeviceToDevice, h->st));
+  unsigned int status = 0;
+  ACUDA(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  if (status & 4u) return afail(h, MLSWE_EINVAL, "fixed_backward: a layer was not wet on both sides of an edge");
+  return MLSWE_OK;
+}
+
+}  // extern "C"

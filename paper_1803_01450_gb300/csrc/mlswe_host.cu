@@ -424,6 +424,7 @@ mlswe_status mlswe_destroy(mlswe_h h) {
   std::vector<void*> all = h->allocations;
   for (void* p : all) dev_free(h, p);
   if (h->own_stream) cudaStreamDestroy(h->st);
+  adjoint_release(h);
   delete h;
   return MLSWE_OK;
 }

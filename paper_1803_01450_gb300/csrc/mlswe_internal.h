@@ -49,7 +49,9 @@ struct TileShape {
 };
 
 // Kernel classes timed by the optional launch timer.
-enum KernelClass { KC_SWEEP_X = 0, KC_SWEEP_Y, KC_GHOST, KC_INTERP, KC_AVERAGE, KC_FLAGS, KC_REFLUX, KC_OTHER, KC_COUNT };
+enum KernelClass {
+  KC_SWEEP_X = 0, KC_SWEEP_Y, KC_GHOST, KC_INTERP, KC_AVERAGE, KC_FLAGS, KC_REFLUX, KC_OTHER, KC_ADJOINT, KC_COUNT
+};
 
 struct LaunchTimer {
   bool on = false;
@@ -133,6 +135,7 @@ struct Hier {
   long long kernel_launches = 0;   // every kernel this hierarchy launched
   void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
   size_t scratch_bytes = 0;
+  void* adj = nullptr;             // buffers of the fixed-grid adjoint (mlswe_adjoint.cu)
 
   int desc_index(int member, int level) const { return member * L + level; }
 };
@@ -174,6 +177,7 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
                          unsigned int* lost_count, cudaStream_t st);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
+void adjoint_release(Hier* H);
 mlswe_status ensure_worklist(Hier* H, int level, int dir);
 
 }  // namespace mlswe
