@@ -47,7 +47,7 @@ FP64_FLOP_PER_CELL_UPDATE = 1293.25
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
-SWEEP_X_DRAM_BYTES = None
+SWEEP_X_DRAM_BYTES = 396.4e6
 
 
 class ClockSampler:
@@ -255,6 +255,45 @@ def bench_ensemble(pkg, torch, stream, n_members=64, steps=3):
             "distinct_member_dt": int(len(set(np.round(dt, 12)))), "autotuned_tiles": chosen}
 
 
+def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
+    """Gauge-misfit gradient on the 512^2 adjoint workload: forward (200 first-order steps,
+    loss) versus backward (segment recomputation from checkpoints + transposed steps)."""
+    from paper_1803_01450_gb300.adjoint import FixedGridProblem
+    L = 1e5
+    B = I.adjoint_bathymetry(n, L)
+    eta1 = I.adjoint_eta1(n, seed=4000, L=L)
+    gauges = I.gauge_cells(n, n_g, seed=4100)
+    dt = 0.5 * (L / n) / 205.0
+    obs = np.zeros((steps, n_g))  # the cost does not depend on the observed values
+    prob = FixedGridProblem(n, n, L, dt, steps, ckpt, gauges, obs, stream=stream.cuda_stream)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prob.forward(eta1, B)
+    prob.backward(dev)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    prob.H.set_state(0, 0, prob.initial_state(eta1, B))
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    loss = prob.H.fixed_forward()
+    e[1].record(stream)
+    dq0 = torch.empty((6, n, n), dtype=torch.float64, device=dev)
+    dB = torch.empty((n, n), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    e[1].synchronize()
+    t_b0 = torch.cuda.Event(enable_timing=True)
+    t_b0.record(stream)
+    prob.H.fixed_backward(dq0.data_ptr(), dB.data_ptr())
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1])
+    bwd = t_b0.elapsed_time(e[2])
+    prob.close()
+    return {"workload": f"{n}^2 fixed grid, 2 layers, B = -4000 + 500 sin cos, 8 humps, order 1, fixed dt, "
+                        f"{steps} steps, {n_g} gauges, checkpoint every {ckpt}",
+            "forward_ms": fwd, "backward_ms": bwd, "adjoint_over_forward": bwd / fwd,
+            "forward_lcups": n * n * M_LAYERS * steps / (fwd * 1e-3), "loss": loss}
+
+
 def run_gpu(args):
     import torch
     import paper_1803_01450_gb300 as pkg
@@ -355,6 +394,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_amr:
         line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
         line["ensemble"] = bench_ensemble(pkg, torch, stream)
+        line["adjoint"] = bench_adjoint(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
