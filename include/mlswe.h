@@ -201,8 +201,9 @@ mlswe_status mlswe_set_execution(mlswe_h h, int use_graphs, int per_patch_launch
 
 /* Tile autotuner (not in the paper): times the candidate sweep tiles on the
  * current patches of `level` (iters launches each, CUDA events, the state is not
- * advanced) and keeps the fastest per sweep direction. chosen (host int[4], may
- * be NULL): x len, x lines, y len, y lines. */
+ * advanced) and keeps the fastest per sweep direction, over 5 tile shapes and
+ * 1 or 2 resident CTAs per SM. chosen (host int[6], may be NULL): x len, x lines,
+ * x CTAs per SM, y len, y lines, y CTAs per SM. */
 mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
 
 /* Surface elevations eta_m (Eq. (4)) at n points (host [n][2], physical x, y)

@@ -321,7 +321,7 @@ class Hierarchy:
         self._check(self.L.mlswe_set_execution(self.h, int(use_graphs), int(per_patch_launches)), "set_execution")
 
     def autotune(self, level: int, iters: int = 5):
-        out = (ctypes.c_int * 4)()
+        out = (ctypes.c_int * 6)()
         self._check(self.L.mlswe_autotune(self.h, level, iters, out), "autotune")
         return tuple(out)
 

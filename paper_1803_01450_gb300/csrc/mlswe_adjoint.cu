@@ -306,12 +306,13 @@ static mlswe_status adj_forward_step(Hier* H, Adjoint* A, const double* in, doub
   D.NX = V.NX; D.NY = V.NY; D.P = V.P;
   D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
   ACUDA(H, cudaMemcpyAsync(A->desc, &D, sizeof(D), cudaMemcpyHostToDevice, H->st));
-  const int grid = H->blocks_per_sm * H->num_sms;
   for (int dir = 0; dir < (x_only ? 1 : 2); ++dir) {
     Hier::WorkList& W = H->wl[dir];
+    const int ctas = H->shape[dir].ctas;
     int tok;
     timer_begin(H, KC_ADJOINT, &tok);
-    ACUDA(H, launch_sweep(dir, H->dp, A->desc, W.d_items, W.d_count, grid, 0, 0, H->d_smax, nullptr, H->st));
+    ACUDA(H, launch_sweep(dir, H->dp, A->desc, W.d_items, W.d_count, ctas * H->num_sms, 0, 0, H->d_smax, nullptr,
+                          H->st, ctas));
     timer_end(H, tok);
   }
   return MLSWE_OK;

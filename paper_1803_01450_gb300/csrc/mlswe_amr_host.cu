@@ -25,7 +25,7 @@ cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, cons
 std::vector<Box> cluster_flags(const uint8_t* flags, int nx, int ny, int level, const std::vector<Box>& patches,
                                int r, int n_buf, double eff, int min_side, int max_side, int n_nest);
 std::vector<Box> box_difference(const Box& a, const std::vector<Box>& sub);
-void set_level_shape(Hier* H, int level, int dir, int len, int lines);
+void set_level_shape(Hier* H, int level, int dir, int len, int lines, int ctas);
 
 constexpr int kNest = 2;    // nesting margin in coarse cells
 constexpr int kChunk = 64;  // largest side of a level-transfer work item
@@ -379,31 +379,35 @@ static mlswe_status autotune_level(Hier* H, int level, int iters, int* chosen) {
   cudaEvent_t e0, e1;
   CUDA_TRY(H, cudaEventCreate(&e0));
   CUDA_TRY(H, cudaEventCreate(&e1));
-  const int full = H->blocks_per_sm * H->num_sms;
   for (int dir = 0; dir < 2; ++dir) {
     float best = 1e30f;
-    int bl = H->shape[level * 2 + dir].len, bn = H->shape[level * 2 + dir].lines;
-    for (const auto& c : cand) {
-      set_level_shape(H, level, dir, c[0], c[1]);
-      mlswe_status s = ensure_worklist(H, level, dir);
-      if (s != MLSWE_OK) return s;
-      Hier::WorkList& W = H->wl[level * 2 + dir];
-      if (W.count == 0) continue;
-      const int par = H->parity[level];
-      CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr, H->st));
-      CUDA_TRY(H, cudaEventRecord(e0, H->st));
-      for (int k = 0; k < iters; ++k)
-        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr, H->st));
-      CUDA_TRY(H, cudaEventRecord(e1, H->st));
-      CUDA_TRY(H, cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CUDA_TRY(H, cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; bl = c[0]; bn = c[1]; }
-    }
-    set_level_shape(H, level, dir, bl, bn);
+    const TileShape cur = H->shape[level * 2 + dir];
+    int bl = cur.len, bn = cur.lines, bc = cur.ctas;
+    for (int ctas = 1; ctas <= 2; ++ctas)
+      for (const auto& c : cand) {
+        set_level_shape(H, level, dir, c[0], c[1], ctas);
+        mlswe_status s = ensure_worklist(H, level, dir);
+        if (s != MLSWE_OK) return s;
+        Hier::WorkList& W = H->wl[level * 2 + dir];
+        if (W.count == 0) continue;
+        const int par = H->parity[level];
+        const int full = ctas * H->num_sms;
+        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr,
+                                 H->st, ctas));
+        CUDA_TRY(H, cudaEventRecord(e0, H->st));
+        for (int k = 0; k < iters; ++k)
+          CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr,
+                                   H->st, ctas));
+        CUDA_TRY(H, cudaEventRecord(e1, H->st));
+        CUDA_TRY(H, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(H, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bl = c[0]; bn = c[1]; bc = ctas; }
+      }
+    set_level_shape(H, level, dir, bl, bn, bc);
     mlswe_status s = ensure_worklist(H, level, dir);
     if (s != MLSWE_OK) return s;
-    if (chosen) { chosen[2 * dir] = bl; chosen[2 * dir + 1] = bn; }
+    if (chosen) { chosen[3 * dir] = bl; chosen[3 * dir + 1] = bn; chosen[3 * dir + 2] = bc; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -174,11 +174,11 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
           const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
           const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
           Pl[p] = f1 * f2 - rc;
-          dP[p] = 2.0 * (a1 * f2 + a2 * f1);
+          dP[p] = a1 * f2 + a2 * f1;  // P'(l) / 2
         }
-        // One reciprocal for the four Newton quotients.
+        // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
         const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
-        const double inv = rcp(p01 * p23);
+        const double inv = 0.5 * rcp(p01 * p23);
         const double i01 = inv * p23, i23 = inv * p01;
         lam[0] -= Pl[0] * (i01 * dP[1]);
         lam[1] -= Pl[1] * (i01 * dP[0]);
@@ -286,6 +286,60 @@ __device__ __forceinline__ double limiter_phi(int kind, double th) {
   if (kind == 0) return 1.0;
   if (kind == 1) return fmax(0.0, fmin(1.0, th));
   return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
+}
+
+// ---- helpers that keep comparisons off the FP64 pipe (integer work is nearly free) ----
+
+// -1, 0, +1 for s < 0, s == 0 (either sign of zero), s > 0 (finite or infinite s).
+__device__ __forceinline__ int sign_class(double s) {
+  const long long b = __double_as_longlong(s);
+  if ((b << 1) == 0) return 0;
+  return b < 0 ? -1 : 1;
+}
+
+// Bit pattern of |s|; for non-negative doubles the unsigned order is the numeric order.
+__device__ __forceinline__ unsigned long long abs_bits(double s) {
+  return (unsigned long long)__double_as_longlong(s) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+
+__device__ __forceinline__ double pos_min(double a, double b) {  // both > 0
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x < y ? x : y);
+}
+
+// Same values as limiter_phi: theta <= 0 gives 0; the minima of positive numbers are taken
+// on their bit patterns.
+__device__ __forceinline__ double limiter_phi_fast(int kind, double th) {
+  if (kind == 0) return 1.0;
+  if (__double_as_longlong(th) <= 0) return 0.0;  // th <= +0 or negative
+  if (kind == 1) return pos_min(1.0, th);
+  return pos_min(pos_min(fma(0.5, th, 0.5), 2.0), th + th);
+}
+
+// Reciprocals of N positive numbers with one division when their product stays well inside
+// the FP64 range: 1/x_p = (1/prod x) * prod_{q != p} x_q.
+template <int N>
+__device__ __forceinline__ void batched_reciprocal(const double* x, double* inv) {
+  double pre[N], suf[N];
+  pre[0] = 1.0;
+#pragma unroll
+  for (int p = 1; p < N; ++p) pre[p] = pre[p - 1] * x[p - 1];
+  suf[N - 1] = 1.0;
+#pragma unroll
+  for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
+  const double prod = pre[N - 1] * x[N - 1];
+  if (prod > 1e-280 && prod < 1e280) {
+    const double ip = rcp(prod);
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = ip * (pre[p] * suf[p]);
+  } else {
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = rcp(x[p]);
+  }
 }
 
 }  // namespace mlswe

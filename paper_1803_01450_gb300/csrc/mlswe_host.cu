@@ -227,16 +227,17 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
     if (s != MLSWE_OK) return s;
   }
   const int par = H->parity[level];
-  const int full = H->blocks_per_sm * H->num_sms;
   for (int dir = 0; dir < 2; ++dir) {
     Hier::WorkList& W = H->wl[level * 2 + dir];
+    const int ctas = H->shape[level * 2 + dir].ctas;
+    const int full = ctas * H->num_sms;
     if (!H->per_patch_launch) {
       // Always launched (also with no items): a captured graph must hold the node for
       // when a later regrid fills the work list.
       int tok;
       timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
       CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, record, H->d_smax,
-                               H->d_lost, H->st));
+                               H->d_lost, H->st, ctas));
       timer_end(H, tok);
     } else {
       const int np = (int)W.patch_off.size() - 1;
@@ -246,7 +247,7 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
         int tok;
         timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
         CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p,
-                                 std::min(cnt, full), par, record, H->d_smax, H->d_lost, H->st));
+                                 std::min(cnt, full), par, record, H->d_smax, H->d_lost, H->st, ctas));
         timer_end(H, tok);
       }
     }
@@ -277,9 +278,10 @@ static bool shape_ok(int len, int lines) {
   return len >= 4 && lines >= 1 && lines <= 32 && lines * (len + 3) <= kMaxEdges && lines * (len + 4) <= kMaxCells;
 }
 
-void set_level_shape(Hier* H, int level, int dir, int len, int lines) {
+void set_level_shape(Hier* H, int level, int dir, int len, int lines, int ctas) {
   H->shape[level * 2 + dir].len = len;
   H->shape[level * 2 + dir].lines = lines;
+  H->shape[level * 2 + dir].ctas = ctas;
   H->wl[level * 2 + dir].dirty = true;
 }
 
@@ -498,8 +500,7 @@ mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cf
 mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm) {
   if (!h || dir < 0 || dir > 1 || !shape_ok(len, lines) || ctas_per_sm < 1 || ctas_per_sm > 2)
     return fail(h, MLSWE_EINVAL, "set_tiles: shape out of range");
-  for (int l = 0; l < h->L; ++l) set_level_shape(h, l, dir, len, lines);
-  h->blocks_per_sm = ctas_per_sm;
+  for (int l = 0; l < h->L; ++l) set_level_shape(h, l, dir, len, lines, ctas_per_sm);
   invalidate_graphs(h);
   return MLSWE_OK;
 }

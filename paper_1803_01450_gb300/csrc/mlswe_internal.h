@@ -46,6 +46,7 @@ struct Member {
 struct TileShape {
   int len = 61;
   int lines = 4;
+  int ctas = 1;  // resident CTAs per SM of the persistent grid (kernel variant)
 };
 
 // Kernel classes timed by the optional launch timer.
@@ -174,7 +175,7 @@ cudaError_t launch_gauges(int M, const LevelDesc* descs, const int* parity_of_de
                           double* out, cudaStream_t st);
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                          const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st);
+                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm = 1);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
 void adjoint_release(Hier* H);

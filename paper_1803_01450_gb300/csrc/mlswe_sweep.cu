@@ -46,8 +46,10 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* d
   __syncthreads();
 }
 
-template <int M, int DIR>
-__global__ void __launch_bounds__(kThreads, 1)
+// MINB: CTAs resident per SM the build targets (1: up to 255 registers per thread; 2: at
+// most 128, 16 warps per SM to hide FP64 latency). The autotuner picks per level.
+template <int M, int DIR, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
              const int* __restrict__ n_items_dev, int parity, int record, unsigned long long* smax_bits,
              unsigned int* lost_count) {
@@ -110,10 +112,12 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const bool w = above && (h > P.dry_tol);
         above = w;
         wet |= w ? (1 << m) : 0;
+        // one reciprocal square root gives both sqrt(h) = h t and 1/h = t t
+        const double t = h > 0.0 ? rsqrt(h) : 0.0;
         double un = 0.0, ut = 0.0;
-        if (w) { const double ih = rcp(h); un = hn * ih; ut = ht * ih; }
+        if (w) { const double ih = t * t; un = hn * ih; ut = ht * ih; }
         rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
-        rec[R::SQ + m] = sqrt(fmax(h, 0.0));
+        rec[R::SQ + m] = h * t;
       }
       double acc = Bv;
 #pragma unroll
@@ -154,12 +158,13 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       }
       wallb[es] = W.wall;
       if (interior && e >= 1 && e <= len + 1) {
-        double sm = 0.0;
+        // |s| as bit patterns: non-negative doubles order like unsigned integers (NaN above all)
+        unsigned long long sm = __double_as_longlong(smax);
 #pragma unroll
-        for (int p = 0; p < 2 * M; ++p) sm = fmax(sm, fabs(W.s[p]));
+        for (int p = 0; p < 2 * M; ++p) sm = umax64(sm, abs_bits(W.s[p]));
 #pragma unroll
-        for (int m = 0; m < M; ++m) sm = fmax(sm, fabs(W.us[m]));
-        smax = fmax(smax, sm);
+        for (int m = 0; m < M; ++m) sm = umax64(sm, abs_bits(W.us[m]));
+        smax = __longlong_as_double((long long)sm);
         lost += lst;
       }
     }
@@ -183,16 +188,26 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 #pragma unroll
       for (int m = 0; m < M; ++m) vh[m] = wav[(WR::VH + m) * kMaxEdges + es];
       double La = 0, Lsa = 0, Lb = 0, Lsb = 0, Ra = 0, Rsa = 0, Rb = 0, Rsb = 0;
+      // Wave limiter of the acoustic waves: theta_p = zu_p / zz_p with one reciprocal for
+      // all of them (1/zz_p = (1/prod zz) * prod_{q != p} zz), falling back to one
+      // reciprocal each when the product leaves the safe exponent range.
+      constexpr int NA = 2 * M;
+      double zzv[NA], zuv[NA];
+      int sc[NA];
+      bool act[NA];
 #pragma unroll
-      for (int p = 0; p < 2 * M; ++p) {
+      for (int p = 0; p < NA; ++p) {
         const double a = wav[(WR::A + p) * kMaxEdges + es];
         const double b = wav[(WR::B + p) * kMaxEdges + es];
         const double s = wav[(WR::S + p) * kMaxEdges + es];
-        double corr = 0.0;
+        sc[p] = sign_class(s);
         const int lay = layer_of_slot<M>(p);
         const bool walled = (wall >> (2 * lay)) & 3;
-        if (P.order >= 2 && s != 0.0 && !walled) {
-          const int eu = s > 0.0 ? esl : esr;
+        act[p] = P.order >= 2 && sc[p] != 0 && !walled;
+        zzv[p] = 1.0;
+        zuv[p] = 0.0;
+        if (act[p]) {
+          const int eu = sc[p] > 0 ? esl : esr;
           const double au = wav[(WR::A + p) * kMaxEdges + eu];
           const double bu = wav[(WR::B + p) * kMaxEdges + eu];
           const double su = wav[(WR::S + p) * kMaxEdges + eu];
@@ -205,11 +220,22 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
             zz += b * b * (ss + vh[M - 1] * vh[M - 1]);
             zu += b * bu * (su1 + vh[M - 1] * vu1);
           }
-          const double th = zz > 0.0 ? zu * rcp(zz) : 0.0;
-          const double phi = limiter_phi(P.limiter, th);
-          corr = 0.5 * (s > 0.0 ? 1.0 : -1.0) * (1.0 - nu * fabs(s)) * phi;
+          if (zz > 0.0) { zzv[p] = zz; zuv[p] = zu; }
         }
-        const double cl = (s < 0.0 ? 1.0 : (s > 0.0 ? 0.0 : 0.5)) + corr;
+      }
+      double izz[NA];
+      batched_reciprocal<NA>(zzv, izz);
+#pragma unroll
+      for (int p = 0; p < NA; ++p) {
+        const double a = wav[(WR::A + p) * kMaxEdges + es];
+        const double b = wav[(WR::B + p) * kMaxEdges + es];
+        const double s = wav[(WR::S + p) * kMaxEdges + es];
+        double corr = 0.0;
+        if (act[p]) {
+          const double phi = limiter_phi_fast(P.limiter, zuv[p] * izz[p]);
+          corr = (sc[p] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(s), 1.0) * phi;
+        }
+        const double cl = (sc[p] < 0 ? 1.0 : (sc[p] > 0 ? 0.0 : 0.5)) + corr;
         const double cr = 1.0 - cl;
         const double ca = cl * a, cb = cl * b, ra = cr * a, rb = cr * b;
         La += ca; Lsa += ca * s; Lb += cb; Lsb += cb * s;
@@ -222,15 +248,16 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const double us = wav[(WR::US + m) * kMaxEdges + es];
         double corr = 0.0;
         const bool walled = (wall >> (2 * m)) & 3;
-        if (P.order >= 2 && us != 0.0 && !walled) {
-          const int eu = us > 0.0 ? esl : esr;
+        const int su = sign_class(us);
+        if (P.order >= 2 && su != 0 && !walled) {
+          const int eu = su > 0 ? esl : esr;
           const double zu = wav[(WR::Z + m) * kMaxEdges + eu];
           const double zz = z * z;
           const double th = zz > 0.0 ? (zu * z) * rcp(zz) : 0.0;
-          const double phi = limiter_phi(P.limiter, th);
-          corr = 0.5 * (us > 0.0 ? 1.0 : -1.0) * (1.0 - nu * fabs(us)) * phi;
+          const double phi = limiter_phi_fast(P.limiter, th);
+          corr = (su > 0 ? 0.5 : -0.5) * fma(-nu, fabs(us), 1.0) * phi;
         }
-        const double cl = (us < 0.0 ? 1.0 : (us > 0.0 ? 0.0 : 0.5)) + corr;
+        const double cl = (su < 0 ? 1.0 : (su > 0 ? 0.0 : 0.5)) + corr;
         Lz[m] = cl * z;
         Rz[m] = (1.0 - cl) * z;
       }
@@ -325,30 +352,45 @@ size_t sweep_smem_bytes(int M) {
   return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
 }
 
-template <int M, int DIR>
+template <int M, int DIR, int MINB>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                   const int* n_items_dev, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st) {
   const size_t sm = sweep_smem_bytes(M);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e =
+        cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record, smax_bits, lost_count);
+  sweep_kernel<M, DIR, MINB><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record, smax_bits,
+                                                         lost_count);
   return cudaGetLastError();
+}
+
+template <int M, int DIR>
+static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                                  const int* n_items_dev, int grid, int parity, int record,
+                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st) {
+  return ctas >= 2 ? launch_sweep_t<M, DIR, 2>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                               lost_count, st)
+                   : launch_sweep_t<M, DIR, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                               lost_count, st);
 }
 
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                          const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st) {
+                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm) {
   if (grid <= 0) return cudaSuccess;
+  const int c = ctas_per_sm;
   if (P.M == 1)
-    return dir == 0 ? launch_sweep_t<1, 0>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
-                    : launch_sweep_t<1, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
-  return dir == 0 ? launch_sweep_t<2, 0>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
-                  : launch_sweep_t<2, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
+    return dir == 0
+               ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
+               : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
+  return dir == 0
+             ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
+             : launch_sweep_m<2, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
 }
 
 }  // namespace mlswe
