@@ -244,15 +244,15 @@ struct Adjoint {
   int n_steps = 0, ckpt = 0, ng = 0;
   size_t state_bytes = 0;
   std::vector<double*> ckpts;  // [n_steps / ckpt + 1]
-  std::vector<double*> slots;  // [ckpt + 1]
+  std::vector<double*> slots;  // [ckpt + 1] recomputed states of a segment
+  std::vector<double*> qstar;  // [ckpt] their states after the x sweep
   double* lam = nullptr;
   double* lam2 = nullptr;
   double* gB = nullptr;
-  double* qs = nullptr;
   int* gij = nullptr;
   double* obs = nullptr;
   double* loss = nullptr;
-  LevelDesc* desc = nullptr;  // [1] level-0 descriptor with q[] re-pointed per recomputed step
+  LevelDesc* descs = nullptr;  // [ckpt] level-0 descriptors: step a reads slots[a], writes slots[a+1], qstar[a]
   bool forward_done = false;
 };
 
@@ -292,27 +292,36 @@ static cudaError_t copy_state(Hier* H, double* dst, const double* src) {
   return cudaMemcpyAsync(dst, src, (size_t)3 * H->cfg.M * V.NY * V.P * 8, cudaMemcpyDeviceToDevice, H->st);
 }
 
-// One forward first-order step from `in` to `out` (or only its x sweep, into the Q* buffer)
-// through a private copy of the level descriptor whose state pointers are re-aimed. The
-// descriptor copy is stream-ordered behind the kernels that read the previous one.
-static mlswe_status adj_forward_step(Hier* H, Adjoint* A, const double* in, double* out, bool x_only) {
+// Descriptors of the recomputation slots (built once per setup): step a of a segment reads
+// slots[a], keeps its x-sweep result in qstar[a] and writes slots[a + 1].
+static mlswe_status adj_build_descs(Hier* H, Adjoint* A) {
   const Level& V = H->mem[0].lev[0];
-  LevelDesc D{};
-  D.q[0] = const_cast<double*>(in);
-  D.q[1] = out;
-  D.qs = A->qs;
-  D.B = V.B;
-  D.dt = H->d_dt;
-  D.NX = V.NX; D.NY = V.NY; D.P = V.P;
-  D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
-  ACUDA(H, cudaMemcpyAsync(A->desc, &D, sizeof(D), cudaMemcpyHostToDevice, H->st));
-  for (int dir = 0; dir < (x_only ? 1 : 2); ++dir) {
+  std::vector<LevelDesc> d(A->ckpt);
+  for (int a = 0; a < A->ckpt; ++a) {
+    LevelDesc& D = d[a];
+    D = LevelDesc{};
+    D.q[0] = A->slots[a];
+    D.q[1] = A->slots[a + 1];
+    D.qs = A->qstar[a];
+    D.B = V.B;
+    D.dt = H->d_dt;
+    D.NX = V.NX; D.NY = V.NY; D.P = V.P;
+    D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
+  }
+  ACUDA(H, cudaMemcpyAsync(A->descs, d.data(), d.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice, H->st));
+  ACUDA(H, cudaStreamSynchronize(H->st));
+  return MLSWE_OK;
+}
+
+// Step a of the segment being recomputed (both sweeps, nothing recorded).
+static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
+  for (int dir = 0; dir < 2; ++dir) {
     Hier::WorkList& W = H->wl[dir];
     const int ctas = H->shape[dir].ctas;
     int tok;
     timer_begin(H, KC_ADJOINT, &tok);
-    ACUDA(H, launch_sweep(dir, H->dp, A->desc, W.d_items, W.d_count, ctas * H->num_sms, 0, 0, H->d_smax, nullptr,
-                          H->st, ctas));
+    ACUDA(H, launch_sweep(dir, H->dp, A->descs + a, W.d_items, W.d_count, ctas * H->num_sms, 0, 0, H->d_smax,
+                          nullptr, H->st, ctas));
     timer_end(H, tok);
   }
   return MLSWE_OK;
@@ -339,25 +348,28 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
   auto grab = [&](size_t bytes) { return (double*)dev_alloc(h, bytes); };
   while ((int)A->ckpts.size() < nck) A->ckpts.push_back(grab(A->state_bytes));
   while ((int)A->slots.size() < ckpt_every + 1) A->slots.push_back(grab(A->state_bytes));
+  while ((int)A->qstar.size() < ckpt_every) A->qstar.push_back(grab(A->state_bytes));
   if (!A->lam) A->lam = grab(A->state_bytes);
   if (!A->lam2) A->lam2 = grab(A->state_bytes);
-  if (!A->qs) A->qs = grab(A->state_bytes);
   if (!A->gB) A->gB = grab((size_t)V.NY * V.P * 8);
   if (!A->loss) A->loss = grab(64);
-  if (!A->desc) A->desc = (LevelDesc*)dev_alloc(h, sizeof(LevelDesc));
+  if (A->descs) dev_free(h, A->descs);
+  A->descs = (LevelDesc*)dev_alloc(h, ckpt_every * sizeof(LevelDesc));
   if (A->gij) dev_free(h, A->gij);
   if (A->obs) dev_free(h, A->obs);
   A->gij = (int*)dev_alloc(h, std::max(1, 2 * n_gauges) * sizeof(int));
   A->obs = grab(std::max<size_t>(1, (size_t)n_steps * n_gauges) * 8);
   for (double* p : A->ckpts) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
   for (double* p : A->slots) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
-  if (!A->lam || !A->lam2 || !A->qs || !A->gB || !A->loss || !A->desc || !A->gij || !A->obs)
+  for (double* p : A->qstar) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+  if (!A->lam || !A->lam2 || !A->gB || !A->loss || !A->descs || !A->gij || !A->obs)
     return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
   if (n_gauges > 0) {
     ACUDA(h, cudaMemcpyAsync(A->gij, gauge_ij, 2 * n_gauges * sizeof(int), cudaMemcpyHostToDevice, h->st));
     ACUDA(h, cudaMemcpyAsync(A->obs, obs, (size_t)n_steps * n_gauges * 8, cudaMemcpyHostToDevice, h->st));
   }
-  ACUDA(h, cudaStreamSynchronize(h->st));
+  mlswe_status s = adj_build_descs(h, A);
+  if (s != MLSWE_OK) return s;
   A->forward_done = false;
   return MLSWE_OK;
 }
@@ -399,7 +411,7 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
   const Level& V = h->mem[0].lev[0];
   const int M = h->cfg.M, F = 3 * M;
   const size_t plane = (size_t)V.NY * V.P;
-  const int grid = h->blocks_per_sm * h->num_sms;
+  const int grid = h->num_sms;
   ACUDA(h, cudaMemsetAsync(A->lam, 0, A->state_bytes, h->st));
   ACUDA(h, cudaMemsetAsync(A->gB, 0, plane * 8, h->st));
   ACUDA(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
@@ -407,29 +419,28 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
   const int nseg = (N + C - 1) / C;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int k0 = seg * C, k1 = std::min(N, k0 + C);
-    // recompute Q^{k0} .. Q^{k1} into the slots
+    // recompute Q^{k0} .. Q^{k1} into the slots, keeping every step's Q*
     ACUDA(h, copy_state(h, A->slots[0], A->ckpts[seg]));
     for (int n = k0; n < k1; ++n) {
-      mlswe_status s = adj_forward_step(h, A, A->slots[n - k0], A->slots[n - k0 + 1], false);
+      mlswe_status s = adj_forward_step(h, A, n - k0);
       if (s != MLSWE_OK) return s;
     }
     for (int n = k1 - 1; n >= k0; --n) {
+      const int a = n - k0;
       // gauge term of J at Q^{n+1}
       int tok;
       timer_begin(h, KC_OTHER, &tok);
-      gauge_misfit_kernel<<<1, 32, 0, h->st>>>(M, h->d_desc, A->slots[n + 1 - k0], A->gij, A->ng,
+      gauge_misfit_kernel<<<1, 32, 0, h->st>>>(M, h->d_desc, A->slots[a + 1], A->gij, A->ng,
                                                A->obs + (size_t)n * A->ng, nullptr, A->lam, A->gB);
       ACUDA(h, cudaGetLastError());
       timer_end(h, tok);
-      // Q* of step n, then the transposed y sweep and x sweep
-      mlswe_status s = adj_forward_step(h, A, A->slots[n - k0], A->slots[n + 1 - k0], true);
-      if (s != MLSWE_OK) return s;
+      // transposed y sweep (on Q* of step n), then transposed x sweep (on Q^n)
       timer_begin(h, KC_ADJOINT, &tok);
-      ACUDA(h, launch_adjoint_sweep(1, h->dp, A->desc, h->wl[1].d_items, h->wl[1].d_count, grid, A->qs, A->lam,
-                                    A->lam2, A->gB, h->d_status, h->st));
+      ACUDA(h, launch_adjoint_sweep(1, h->dp, A->descs + a, h->wl[1].d_items, h->wl[1].d_count, grid, A->qstar[a],
+                                    A->lam, A->lam2, A->gB, h->d_status, h->st));
       timer_end(h, tok);
       timer_begin(h, KC_ADJOINT, &tok);
-      ACUDA(h, launch_adjoint_sweep(0, h->dp, A->desc, h->wl[0].d_items, h->wl[0].d_count, grid, A->slots[n - k0],
+      ACUDA(h, launch_adjoint_sweep(0, h->dp, A->descs + a, h->wl[0].d_items, h->wl[0].d_count, grid, A->slots[a],
                                     A->lam2, A->lam, A->gB, h->d_status, h->st));
       timer_end(h, tok);
     }

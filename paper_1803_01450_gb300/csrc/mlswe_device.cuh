@@ -68,226 +68,6 @@ struct SweepItem {
 
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
-// ----------------------------------------------------------------------------
-// Cell record staged in shared memory (fields already permuted to normal /
-// transverse for the sweep direction).
-// ----------------------------------------------------------------------------
-template <int M>
-struct Rec {
-  static constexpr int H = 0;             // h_m at 3m, hn_m at 3m+1, ht_m at 3m+2
-  static constexpr int UN = 3 * M;        // un_m at UN + 2m, ut_m at UN + 2m + 1
-  static constexpr int SQ = 5 * M;        // sqrt(h_m)
-  static constexpr int ETA = 6 * M;       // eta_m
-  static constexpr int BB = 7 * M;        // B
-  static constexpr int N = 7 * M + 1;
-};
-
-// Compressed waves of one edge: acoustic wave p is
-//   Z_p = (a_p, a_p s_p, a_p vh_1 | b_p, b_p s_p, b_p vh_2),
-// shear wave of layer m is (0, 0, z_m) on layer m with speed us_m.
-template <int M>
-struct EdgeW {
-  static constexpr int NA = 2 * M;
-  double a[NA], b[NA], s[NA];
-  double z[M], us[M], vh[M];
-  int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
-};
-
-template <int M>
-struct WRec {  // shared-memory layout of EdgeW
-  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, N = 9 * M;
-};
-
-// Layer of acoustic slot p in the per-layer (decoupled) branch.
-template <int M>
-__device__ __forceinline__ int layer_of_slot(int p) {
-  return (M == 1) ? 0 : ((p == 0 || p == 3) ? 0 : 1);
-}
-
-// Single-layer f-wave split of (d0, d1, d2) with speeds s1 < s2.
-template <int M>
-__device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, double d1, double d2,
-                                             double s1, double s2, double vh, double us, EdgeW<M>& W) {
-  const double inv = rcp(s2 - s1);
-  const double b1 = (s2 * d0 - d1) * inv;
-  const double b2 = (d1 - s1 * d0) * inv;
-  if (m == 0) { W.a[pa] = b1; W.a[pb] = b2; }
-  else { W.b[pa] = b1; W.b[pb] = b2; }
-  W.s[pa] = s1; W.s[pb] = s2;
-  W.z[m] = d2 - vh * d0;
-  W.us[m] = us;
-  W.vh[m] = vh;
-}
-
-// Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
-template <int M>
-__device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL, const double* cR,
-                                           int wL, int wR, EdgeW<M>& W, int& lost) {
-  using R = Rec<M>;
-  const double g = P.g;
-#pragma unroll
-  for (int p = 0; p < 2 * M; ++p) { W.a[p] = 0.0; W.b[p] = 0.0; W.s[p] = 0.0; }
-#pragma unroll
-  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; }
-  W.wall = 0;
-
-  double d0[M], d1[M], d2[M], hb[M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const double hL = cL[3 * m], hR = cR[3 * m];
-    const double hnL = cL[3 * m + 1], hnR = cR[3 * m + 1];
-    hb[m] = 0.5 * (hL + hR);
-    double coup = cR[R::ETA + m] - cL[R::ETA + m];
-    if (m == 1) coup += P.r * (cR[0] - cL[0]);
-    d0[m] = hnR - hnL;
-    d1[m] = (hnR * cR[R::UN + 2 * m] - hnL * cL[R::UN + 2 * m]) + g * hb[m] * coup;
-    d2[m] = hnR * cR[R::UN + 2 * m + 1] - hnL * cL[R::UN + 2 * m + 1];
-  }
-  const int full = (1 << M) - 1;
-  if (M == 2 && wL == full && wR == full) {
-    // ---- coupled two-layer branch ----
-    double uh[2], vh[2];
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-      const double inv = rcp(sl + sr);
-      uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-      vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
-    }
-    const double c1 = g * hb[0], c2 = g * hb[1];
-    const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * rcp(hb[0] + hb[1]);
-    const double dc = c1 - c2;
-    const double disc = sqrt(dc * dc + 4.0 * P.r * c1 * c2);
-    const double csum = c1 + c2;
-    const double sp = sqrt(0.5 * (csum + disc)), sm = sqrt(0.5 * (csum - disc));
-    double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
-    const double du = uh[0] - uh[1];
-    const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
-    lost += lst ? 1 : 0;
-    if (!lst && P.eigen == 0) {
-      const double rc = P.r * c1 * c2;
-#pragma unroll
-      for (int it = 0; it < 2; ++it) {
-        double Pl[4], dP[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
-          const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
-          Pl[p] = f1 * f2 - rc;
-          dP[p] = a1 * f2 + a2 * f1;  // P'(l) / 2
-        }
-        // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
-        const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
-        const double inv = 0.5 * rcp(p01 * p23);
-        const double i01 = inv * p23, i23 = inv * p01;
-        lam[0] -= Pl[0] * (i01 * dP[1]);
-        lam[1] -= Pl[1] * (i01 * dP[0]);
-        lam[2] -= Pl[2] * (i23 * dP[3]);
-        lam[3] -= Pl[3] * (i23 * dP[2]);
-      }
-    }
-    // Wave strengths. With a(l) = (l^2 + p1 l + p0) / c1 (p1 = -2 u1, p0 = u1^2 - c1) the rows
-    // of R beta = delta give the power moments m_k = sum_p beta_p l_p^k, k = 0..3, and
-    // beta_p follows from the Lagrange basis of the four eigenvalues.
-    const double p1 = -2.0 * uh[0], p0 = uh[0] * uh[0] - c1;
-    const double m0 = d0[0], m1 = d1[0];
-    const double m2 = c1 * d0[1] - p1 * m1 - p0 * m0;
-    const double m3 = c1 * d1[1] - p1 * m2 - p0 * m1;
-    const double ic1 = rcp(c1);
-    const double l01 = lam[0] - lam[1], l02 = lam[0] - lam[2], l03 = lam[0] - lam[3];
-    const double l12 = lam[1] - lam[2], l13 = lam[1] - lam[3], l23 = lam[2] - lam[3];
-    double den[4];
-    den[0] = l01 * l02 * l03;
-    den[1] = -l01 * l12 * l13;
-    den[2] = l02 * l12 * l23;
-    den[3] = -l03 * l13 * l23;
-    const double q01 = den[0] * den[1], q23 = den[2] * den[3];
-    const double iall = rcp(q01 * q23);
-    double iden[4];
-    iden[0] = iall * q23 * den[1];
-    iden[1] = iall * q23 * den[0];
-    iden[2] = iall * q01 * den[3];
-    iden[3] = iall * q01 * den[2];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const int qa = (p + 1) & 3, qb = (p + 2) & 3, qc = (p + 3) & 3;
-      const double e1 = lam[qa] + lam[qb] + lam[qc];
-      const double e2 = lam[qa] * lam[qb] + lam[qa] * lam[qc] + lam[qb] * lam[qc];
-      const double e3 = lam[qa] * lam[qb] * lam[qc];
-      const double num = m3 - e1 * m2 + e2 * m1 - e3 * m0;
-      const double beta = num * iden[p];
-      const double al = lam[p] - uh[0];
-      const double alpha = (al * al - c1) * ic1;
-      W.a[p] = beta;
-      W.b[p] = beta * alpha;
-      W.s[p] = lam[p];
-    }
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      W.z[m] = d2[m] - vh[m] * d0[m];
-      W.us[m] = uh[m];
-      W.vh[m] = vh[m];
-    }
-    return;
-  }
-  // ---- per-layer branch ----
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
-    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
-    const bool wl = (wL >> m) & 1, wr = (wR >> m) & 1;
-    const double hL = cL[3 * m], hR = cR[3 * m];
-    if (wl && wr) {
-      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-      const double inv = rcp(sl + sr);
-      const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-      const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
-      const double ch = sqrt(g * hb[m]);
-      split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W);
-    } else if (wl || wr) {
-      const double* cw = wl ? cL : cR;
-      const double* cd = wl ? cR : cL;
-      const double bhat_d = (m == M - 1) ? cd[R::BB] : cd[R::ETA + m + 1];
-      if (cw[R::ETA + m] < bhat_d) {
-        // Wall for this layer: mirror of the wet side, coupling dropped.
-        const double hw = cw[3 * m], hnw = cw[3 * m + 1];
-        const double unw = cw[R::UN + 2 * m], utw = cw[R::UN + 2 * m + 1];
-        // Oriented left -> right: wet left gives (hn, -hn), wet right gives (-hn, hn).
-        const double sgn = wl ? 1.0 : -1.0;
-        const double e0 = -2.0 * sgn * hnw;
-        const double e1 = 0.0 * hnw * unw;
-        const double e2 = -2.0 * sgn * hnw * utw;
-        const double ch = sqrt(g * hw);
-        split_single<M>(m, pa, pb, e0, e1, e2, -ch, ch, utw, 0.0, W);
-        W.wall |= 1 << (2 * m + (wl ? 1 : 0));
-      } else {
-        const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-        const double inv = rcp(sl + sr);
-        const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-        const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
-        const double ch = sqrt(g * hb[m]);
-        double s1, s2;
-        if (wl) {
-          const double c = sqrt(g * hL), u = cL[R::UN + 2 * m];
-          s1 = fmin(u - c, uh - ch);
-          s2 = u + 2.0 * c;
-        } else {
-          const double c = sqrt(g * hR), u = cR[R::UN + 2 * m];
-          s1 = u - 2.0 * c;
-          s2 = fmax(u + c, uh + ch);
-        }
-        split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], s1, s2, vh, uh, W);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ double limiter_phi(int kind, double th) {
-  if (kind == 0) return 1.0;
-  if (kind == 1) return fmax(0.0, fmin(1.0, th));
-  return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
-}
-
 // ---- helpers that keep comparisons off the FP64 pipe (integer work is nearly free) ----
 
 // -1, 0, +1 for s < 0, s == 0 (either sign of zero), s > 0 (finite or infinite s).
@@ -340,6 +120,244 @@ __device__ __forceinline__ void batched_reciprocal(const double* x, double* inv)
 #pragma unroll
     for (int p = 0; p < N; ++p) inv[p] = rcp(x[p]);
   }
+}
+
+
+// ----------------------------------------------------------------------------
+// Cell record staged in shared memory (fields already permuted to normal /
+// transverse for the sweep direction).
+// ----------------------------------------------------------------------------
+template <int M>
+struct Rec {
+  static constexpr int H = 0;             // h_m at 3m, hn_m at 3m+1, ht_m at 3m+2
+  static constexpr int UN = 3 * M;        // un_m at UN + 2m, ut_m at UN + 2m + 1
+  static constexpr int SQ = 5 * M;        // sqrt(h_m)
+  static constexpr int ETA = 6 * M;       // eta_m
+  static constexpr int BB = 7 * M;        // B
+  static constexpr int N = 7 * M + 1;
+};
+
+// Compressed waves of one edge: acoustic wave p is
+//   Z_p = (a_p, a_p s_p, a_p vh_1 | b_p, b_p s_p, b_p vh_2),
+// shear wave of layer m is (0, 0, z_m) on layer m with speed us_m.
+template <int M>
+struct EdgeW {
+  static constexpr int NA = 2 * M;
+  double a[NA], b[NA], s[NA];
+  double z[M], us[M], vh[M];
+  int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
+};
+
+template <int M>
+struct WRec {  // shared-memory layout of EdgeW
+  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, N = 9 * M;
+};
+
+// Layer of acoustic slot p in the per-layer (decoupled) branch.
+template <int M>
+__device__ __forceinline__ int layer_of_slot(int p) {
+  return (M == 1) ? 0 : ((p == 0 || p == 3) ? 0 : 1);
+}
+
+// Single-layer f-wave split of (d0, d1, d2) with speeds s1 < s2 (inv_ds: 1/(s2 - s1) when
+// known, else 0).
+template <int M>
+__device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, double d1, double d2,
+                                             double s1, double s2, double vh, double us, EdgeW<M>& W,
+                                             double inv_ds = 0.0) {
+  const double inv = inv_ds != 0.0 ? inv_ds : rcp(s2 - s1);
+  const double b1 = (s2 * d0 - d1) * inv;
+  const double b2 = (d1 - s1 * d0) * inv;
+  if (m == 0) { W.a[pa] = b1; W.a[pb] = b2; }
+  else { W.b[pa] = b1; W.b[pb] = b2; }
+  W.s[pa] = s1; W.s[pb] = s2;
+  W.z[m] = d2 - vh * d0;
+  W.us[m] = us;
+  W.vh[m] = vh;
+}
+
+// Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
+template <int M>
+__device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL, const double* cR,
+                                           int wL, int wR, EdgeW<M>& W, int& lost) {
+  using R = Rec<M>;
+  const double g = P.g;
+#pragma unroll
+  for (int p = 0; p < 2 * M; ++p) { W.a[p] = 0.0; W.b[p] = 0.0; W.s[p] = 0.0; }
+#pragma unroll
+  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; }
+  W.wall = 0;
+
+  double d0[M], d1[M], d2[M], hb[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const double hL = cL[3 * m], hR = cR[3 * m];
+    const double hnL = cL[3 * m + 1], hnR = cR[3 * m + 1];
+    hb[m] = 0.5 * (hL + hR);
+    double coup = cR[R::ETA + m] - cL[R::ETA + m];
+    if (m == 1) coup += P.r * (cR[0] - cL[0]);
+    d0[m] = hnR - hnL;
+    d1[m] = (hnR * cR[R::UN + 2 * m] - hnL * cL[R::UN + 2 * m]) + g * hb[m] * coup;
+    d2[m] = hnR * cR[R::UN + 2 * m + 1] - hnL * cL[R::UN + 2 * m + 1];
+  }
+  const int full = (1 << M) - 1;
+  if (M == 2 && wL == full && wR == full) {
+    // ---- coupled two-layer branch ----
+    const double c1 = g * hb[0], c2 = g * hb[1];
+    // one reciprocal for the Roe weights of both layers, the depth sum and c1
+    double den4[4] = {cL[R::SQ] + cR[R::SQ], cL[R::SQ + 1] + cR[R::SQ + 1], hb[0] + hb[1], c1}, inv4[4];
+    batched_reciprocal<4>(den4, inv4);
+    double uh[2], vh[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+      uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv4[m];
+      vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv4[m];
+    }
+    const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * inv4[2];
+    const double dc = c1 - c2;
+    const double X = dc * dc + 4.0 * P.r * c1 * c2;
+    const double disc = X * rsqrt(X);
+    const double csum = c1 + c2;
+    // mu_+ mu_- = (1 - r) c1 c2: mu_- without the cancellation of (csum - disc)/2
+    const double mup = 0.5 * (csum + disc);
+    const double tp = rsqrt(mup);
+    const double sp = mup * tp;
+    const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
+    const double sm = mum * rsqrt(mum);
+    double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+    const double du = uh[0] - uh[1];
+    const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
+    lost += lst ? 1 : 0;
+    if (!lst && P.eigen == 0) {
+      const double rc = P.r * c1 * c2;
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        double Pl[4], dP[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
+          const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
+          Pl[p] = f1 * f2 - rc;
+          dP[p] = a1 * f2 + a2 * f1;  // P'(l) / 2
+        }
+        // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
+        const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
+        const double inv = 0.5 * rcp(p01 * p23);
+        const double i01 = inv * p23, i23 = inv * p01;
+        lam[0] -= Pl[0] * (i01 * dP[1]);
+        lam[1] -= Pl[1] * (i01 * dP[0]);
+        lam[2] -= Pl[2] * (i23 * dP[3]);
+        lam[3] -= Pl[3] * (i23 * dP[2]);
+      }
+    }
+    // Wave strengths. With a(l) = (l^2 + p1 l + p0) / c1 (p1 = -2 u1, p0 = u1^2 - c1) the rows
+    // of R beta = delta give the power moments m_k = sum_p beta_p l_p^k, k = 0..3, and
+    // beta_p follows from the Lagrange basis of the four eigenvalues.
+    const double p1 = -2.0 * uh[0], p0 = uh[0] * uh[0] - c1;
+    const double m0 = d0[0], m1 = d1[0];
+    const double m2 = c1 * d0[1] - p1 * m1 - p0 * m0;
+    const double m3 = c1 * d1[1] - p1 * m2 - p0 * m1;
+    const double ic1 = inv4[3];
+    const double l01 = lam[0] - lam[1], l02 = lam[0] - lam[2], l03 = lam[0] - lam[3];
+    const double l12 = lam[1] - lam[2], l13 = lam[1] - lam[3], l23 = lam[2] - lam[3];
+    double den[4];
+    den[0] = l01 * l02 * l03;
+    den[1] = -l01 * l12 * l13;
+    den[2] = l02 * l12 * l23;
+    den[3] = -l03 * l13 * l23;
+    const double q01 = den[0] * den[1], q23 = den[2] * den[3];
+    const double iall = rcp(q01 * q23);
+    double iden[4];
+    iden[0] = iall * q23 * den[1];
+    iden[1] = iall * q23 * den[0];
+    iden[2] = iall * q01 * den[3];
+    iden[3] = iall * q01 * den[2];
+    // Numerators: prod_{q != p}(x - l_q) = Q(x)/(x - l_p), Q(x) = x^4 - S1 x^3 + S2 x^2 - S3 x + S4,
+    // by synthetic division: coefficients 1, l_p - S1, S2 + l_p (l_p - S1), l_p (...) - S3.
+    const double s01 = lam[0] + lam[1], s23 = lam[2] + lam[3];
+    const double q0 = lam[0] * lam[1], q1 = lam[2] * lam[3];
+    const double S1 = s01 + s23, S2 = q0 + q1 + s01 * s23, S3 = q0 * s23 + q1 * s01;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const double k2 = lam[p] - S1;
+      const double k1 = S2 + lam[p] * k2;
+      const double k0 = lam[p] * k1 - S3;
+      const double num = m3 + k2 * m2 + k1 * m1 + k0 * m0;
+      const double beta = num * iden[p];
+      const double al = lam[p] - uh[0];
+      const double alpha = (al * al - c1) * ic1;
+      W.a[p] = beta;
+      W.b[p] = beta * alpha;
+      W.s[p] = lam[p];
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      W.z[m] = d2[m] - vh[m] * d0[m];
+      W.us[m] = uh[m];
+      W.vh[m] = vh[m];
+    }
+    return;
+  }
+  // ---- per-layer branch ----
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
+    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
+    const bool wl = (wL >> m) & 1, wr = (wR >> m) & 1;
+    const double hL = cL[3 * m], hR = cR[3 * m];
+    if (wl && wr) {
+      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+      const double inv = rcp(sl + sr);
+      const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+      const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+      // one reciprocal square root gives c = sqrt(g hbar) and 1/(s2 - s1) = 1/(2c)
+      const double gh = g * hb[m];
+      const double tc = rsqrt(gh);
+      const double ch = gh * tc;
+      split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W, 0.5 * tc);
+    } else if (wl || wr) {
+      const double* cw = wl ? cL : cR;
+      const double* cd = wl ? cR : cL;
+      const double bhat_d = (m == M - 1) ? cd[R::BB] : cd[R::ETA + m + 1];
+      if (cw[R::ETA + m] < bhat_d) {
+        // Wall for this layer: mirror of the wet side, coupling dropped.
+        const double hw = cw[3 * m], hnw = cw[3 * m + 1];
+        const double unw = cw[R::UN + 2 * m], utw = cw[R::UN + 2 * m + 1];
+        // Oriented left -> right: wet left gives (hn, -hn), wet right gives (-hn, hn).
+        const double sgn = wl ? 1.0 : -1.0;
+        const double e0 = -2.0 * sgn * hnw;
+        const double e1 = 0.0 * hnw * unw;
+        const double e2 = -2.0 * sgn * hnw * utw;
+        const double ch = sqrt(g * hw);
+        split_single<M>(m, pa, pb, e0, e1, e2, -ch, ch, utw, 0.0, W);
+        W.wall |= 1 << (2 * m + (wl ? 1 : 0));
+      } else {
+        const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+        const double inv = rcp(sl + sr);
+        const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+        const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+        const double ch = sqrt(g * hb[m]);
+        double s1, s2;
+        if (wl) {
+          const double c = sqrt(g * hL), u = cL[R::UN + 2 * m];
+          s1 = fmin(u - c, uh - ch);
+          s2 = u + 2.0 * c;
+        } else {
+          const double c = sqrt(g * hR), u = cR[R::UN + 2 * m];
+          s1 = u - 2.0 * c;
+          s2 = fmax(u + c, uh + ch);
+        }
+        split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], s1, s2, vh, uh, W);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ double limiter_phi(int kind, double th) {
+  if (kind == 0) return 1.0;
+  if (kind == 1) return fmax(0.0, fmin(1.0, th));
+  return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
 }
 
 }  // namespace mlswe
