@@ -37,11 +37,12 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
                      const double* __restrict__ lam_out, double* __restrict__ lam_in, double* __restrict__ gB,
                      unsigned int* __restrict__ status) {
   using R = Rec<M>;
+  constexpr int RN = ARec<M>::N;
   constexpr int F = 3 * M;
   constexpr int NE = 2 * F + 2;  // edge outputs: qL_b, qR_b, BL_b, BR_b
   extern __shared__ double smem[];
-  double* cell = smem;                       // [R::N][kMaxCells]
-  double* lamo = cell + R::N * kMaxCells;    // [F][kMaxCells] (normal frame)
+  double* cell = smem;                       // [RN][kMaxCells]
+  double* lamo = cell + RN * kMaxCells;      // [F][kMaxCells] (normal frame)
   double* eout = lamo + F * kMaxCells;       // [NE][kMaxEdges]
   unsigned char* wetb = reinterpret_cast<unsigned char*>(eout + NE * kMaxEdges);
   const int n_items = *n_items_dev;
@@ -72,7 +73,7 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
       }
       const size_t o = (size_t)j * Pt + i;
       const int c = acslot<DIR>(l, k, len, nl);
-      double rec[R::N];
+      double rec[RN];
       rec[R::BB] = D.B[o];
       int wet = 0;
       bool above = true;
@@ -87,10 +88,18 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
         const bool w = above && (h > P.dry_tol);
         above = w;
         wet |= w ? (1 << m) : 0;
-        double un = 0.0, ut = 0.0;
-        if (w) { const double ih = rcp(h); un = hn * ih; ut = ht * ih; }
+        double un = 0.0, ut = 0.0, is = 0.0, sq;
+        if (w) {  // 1/sqrt(h) once; 1/h and sqrt(h) from it
+          is = rsqrt(h);
+          const double ih = is * is;
+          un = hn * ih; ut = ht * ih;
+          sq = h * is;
+        } else {
+          sq = sqrt(fmax(h, 0.0));
+        }
         rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
-        rec[R::SQ + m] = sqrt(fmax(h, 0.0));
+        rec[R::SQ + m] = sq;
+        rec[ARec<M>::IS + m] = is;
         // cotangent of the sweep output at this cell (zero for a wall ghost: not an output)
         const double lh = ghost ? 0.0 : lam_out[(3 * m) * plane + o];
         const double lu = ghost ? 0.0 : lam_out[(3 * m + 1) * plane + o];
@@ -103,7 +112,7 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
 #pragma unroll
       for (int m = M - 1; m >= 0; --m) { acc = acc + rec[3 * m]; rec[R::ETA + m] = acc; }
 #pragma unroll
-      for (int f = 0; f < R::N; ++f) cell[f * kMaxCells + c] = rec[f];
+      for (int f = 0; f < RN; ++f) cell[f * kMaxCells + c] = rec[f];
       wetb[c] = (unsigned char)wet;
     }
     __syncthreads();
@@ -114,15 +123,17 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
       if (DIR == 0) { l = t / (len + 1); e = t - l * (len + 1); }
       else { e = t / nl; l = t - e * nl; }
       const int cl = acslot<DIR>(l, e, len, nl), cr = acslot<DIR>(l, e + 1, len, nl);
-      double cL[R::N], cR[R::N], amb[6], apb[6];
+      double cL[RN], cR[RN], amb[6], apb[6];
 #pragma unroll
-      for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
+      for (int f = 0; f < RN; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
 #pragma unroll
       for (int f = 0; f < 6; ++f) { amb[f] = 0.0; apb[f] = 0.0; }
+      // A-dQ of this edge updates the left cell, A+dQ the right one, both scaled by -nu; the
+      // VJP is linear in these cotangents, so the factor -nu is applied per cell in the gather.
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        amb[f] = -nu * lamo[f * kMaxCells + cl];  // A-dQ of this edge updates the left cell
-        apb[f] = -nu * lamo[f * kMaxCells + cr];  // A+dQ updates the right cell
+        amb[f] = lamo[f * kMaxCells + cl];
+        apb[f] = lamo[f * kMaxCells + cr];
       }
       double qLb[6] = {0, 0, 0, 0, 0, 0}, qRb[6] = {0, 0, 0, 0, 0, 0}, BLb = 0.0, BRb = 0.0;
       const bool ok = (M == 2) ? edge_vjp_2(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb)
@@ -153,8 +164,7 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
       const int a = DIR == 0 ? i : j, NA = DIR == 0 ? NX : NY;
       double v[F];
 #pragma unroll
-      for (int f = 0; f < F; ++f)
-        v[f] = lamo[f * kMaxCells + c] + eout[(F + f) * kMaxEdges + ew] + eout[f * kMaxEdges + ee];
+      for (int f = 0; f < F; ++f) v[f] = eout[(F + f) * kMaxEdges + ew] + eout[f * kMaxEdges + ee];
       double bb = eout[(2 * F + 1) * kMaxEdges + ew] + eout[(2 * F) * kMaxEdges + ee];
       if (a == 0) {  // ghost -1 = mirror of this cell: its cotangent (left side of edge 0)
 #pragma unroll
@@ -168,6 +178,9 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
       }
       const size_t o = (size_t)j * Pt + i;
 #pragma unroll
+      for (int f = 0; f < F; ++f) v[f] = lamo[f * kMaxCells + c] - nu * v[f];
+      bb = -nu * bb;
+#pragma unroll
       for (int m = 0; m < M; ++m) {
         lam_in[(3 * m) * plane + o] = v[3 * m];
         lam_in[(3 * m + 1) * plane + o] = DIR == 0 ? v[3 * m + 1] : v[3 * m + 2];
@@ -180,7 +193,7 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
 }
 
 static size_t adjoint_smem_bytes(int M) {
-  const int rn = 7 * M + 1, F = 3 * M, ne = 2 * F + 2;
+  const int rn = 8 * M + 1, F = 3 * M, ne = 2 * F + 2;
   return (size_t)rn * kMaxCells * 8 + (size_t)F * kMaxCells * 8 + (size_t)ne * kMaxEdges * 8 + kMaxCells;
 }
 
@@ -254,6 +267,7 @@ struct Adjoint {
   double* loss = nullptr;
   LevelDesc* descs = nullptr;  // [ckpt] level-0 descriptors: step a reads slots[a], writes slots[a+1], qstar[a]
   bool forward_done = false;
+  bool last_kept = false;      // the slots hold the last segment as the forward pass left it
 };
 
 }  // namespace
@@ -371,6 +385,7 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
   mlswe_status s = adj_build_descs(h, A);
   if (s != MLSWE_OK) return s;
   A->forward_done = false;
+  A->last_kept = false;
   return MLSWE_OK;
 }
 
@@ -384,18 +399,34 @@ mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss) {
   }
   ACUDA(h, cudaMemsetAsync(A->loss, 0, 8, h->st));
   ACUDA(h, copy_state(h, A->ckpts[0], h->mem[0].lev[0].q[h->parity[0]]));
-  for (int n = 1; n <= A->n_steps; ++n) {
-    mlswe_status s = enqueue_level_step(h, 0, 1);
-    if (s != MLSWE_OK) return s;
+  // Steps of the last segment run in the recomputation slots (same kernels, same dt), so
+  // the backward pass starts from them without recomputing that segment.
+  const int C = A->ckpt, N = A->n_steps;
+  const int k_last = ((N + C - 1) / C - 1) * C;
+  for (int n = 1; n <= N; ++n) {
+    const double* qn;
+    if (n - 1 >= k_last) {
+      const int a = n - 1 - k_last;
+      if (a == 0) ACUDA(h, copy_state(h, A->slots[0], h->mem[0].lev[0].q[h->parity[0]]));
+      mlswe_status s = adj_forward_step(h, A, a);
+      if (s != MLSWE_OK) return s;
+      qn = A->slots[a + 1];
+    } else {
+      mlswe_status s = enqueue_level_step(h, 0, 1);
+      if (s != MLSWE_OK) return s;
+      qn = h->mem[0].lev[0].q[h->parity[0]];
+    }
     int tok;
     timer_begin(h, KC_OTHER, &tok);
-    gauge_misfit_kernel<<<1, 32, 0, h->st>>>(h->cfg.M, h->d_desc, h->mem[0].lev[0].q[h->parity[0]], A->gij, A->ng,
+    gauge_misfit_kernel<<<1, 32, 0, h->st>>>(h->cfg.M, h->d_desc, qn, A->gij, A->ng,
                                              A->obs + (size_t)(n - 1) * A->ng, A->loss, nullptr, nullptr);
     ACUDA(h, cudaGetLastError());
     timer_end(h, tok);
-    if (n % A->ckpt == 0 && n / A->ckpt < (int)A->ckpts.size())
-      ACUDA(h, copy_state(h, A->ckpts[n / A->ckpt], h->mem[0].lev[0].q[h->parity[0]]));
+    if (n % C == 0 && n / C < (int)A->ckpts.size()) ACUDA(h, copy_state(h, A->ckpts[n / C], qn));
   }
+  // the hierarchy's state is Q^N, as after N plain steps
+  ACUDA(h, copy_state(h, h->mem[0].lev[0].q[h->parity[0]], A->slots[N - k_last]));
+  A->last_kept = true;
   double l = 0.0;
   ACUDA(h, cudaMemcpyAsync(&l, A->loss, 8, cudaMemcpyDeviceToHost, h->st));
   ACUDA(h, cudaStreamSynchronize(h->st));
@@ -419,12 +450,16 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
   const int nseg = (N + C - 1) / C;
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int k0 = seg * C, k1 = std::min(N, k0 + C);
-    // recompute Q^{k0} .. Q^{k1} into the slots, keeping every step's Q*
-    ACUDA(h, copy_state(h, A->slots[0], A->ckpts[seg]));
-    for (int n = k0; n < k1; ++n) {
-      mlswe_status s = adj_forward_step(h, A, n - k0);
-      if (s != MLSWE_OK) return s;
+    // recompute Q^{k0} .. Q^{k1} into the slots, keeping every step's Q* (the last segment
+    // is still there from the forward pass unless an earlier backward pass reused the slots)
+    if (!(seg == nseg - 1 && A->last_kept)) {
+      ACUDA(h, copy_state(h, A->slots[0], A->ckpts[seg]));
+      for (int n = k0; n < k1; ++n) {
+        mlswe_status s = adj_forward_step(h, A, n - k0);
+        if (s != MLSWE_OK) return s;
+      }
     }
+    if (seg < nseg - 1) A->last_kept = false;
     for (int n = k1 - 1; n >= k0; --n) {
       const int a = n - k0;
       // gauge term of J at Q^{n+1}

@@ -6,9 +6,13 @@
 // reverse order. Signs of the wave speeds select fluctuations and are treated
 // as constant (the derivative of the selection is zero almost everywhere).
 //
-// Cell records are the same as the forward sweep's (Rec<M>: h, hn, ht per
-// layer, un, ut, sqrt(h), eta, B); bathymetry enters through eta.
+// Cell records are the forward sweep's (Rec<M>: h, hn, ht per layer, un, ut,
+// sqrt(h), eta, B) followed by 1/sqrt(h) per layer (ARec<M>); bathymetry
+// enters through eta. Reciprocals that share an edge are taken in batches of
+// four with one division.
 #pragma once
+#include <cmath>
+#include <cstring>
 #include "mlswe_device.cuh"
 
 namespace mlswe {
@@ -27,10 +31,74 @@ MLSWE_HD double adj_rcp(double x) {
 #endif
 }
 
-// Selection weights of a wave of speed s into (A-dQ, A+dQ).
-MLSWE_HD void adj_side_weights(double s, double& wl, double& wr) {
-  wl = s < 0.0 ? 1.0 : (s > 0.0 ? 0.0 : 0.5);
-  wr = 1.0 - wl;
+MLSWE_HD double adj_rsqrt(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / std::sqrt(x);
+#endif
+}
+
+MLSWE_HD long long adj_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return __double_as_longlong(x);
+#else
+  long long b;
+  std::memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+
+// Sign of a wave speed from its bits (integer unit, not the FP64 pipe): -1, +1, or 0 for +-0.
+MLSWE_HD int adj_sign(double s) {
+  const long long b = adj_bits(s);
+  return (b << 1) == 0 ? 0 : (b < 0 ? -1 : 1);
+}
+
+// |x| in [2^-199, 2^200), read from the exponent field.
+MLSWE_HD bool adj_moderate(double x) {
+  const unsigned e = (unsigned)((adj_bits(x) >> 52) & 0x7ff);
+  return e - 824u <= 398u;
+}
+
+// Reciprocals of N <= 4 nonzero numbers with one division: 1/x_p = (1/prod x) * prod_{q != p} x_q.
+// Used when every |x_p| lies in [2^-199, 2^200) (every partial product stays a normal FP64
+// number); otherwise one division each.
+template <int N>
+MLSWE_HD void adj_batched_rcp(const double* x, double* inv) {
+  bool safe = true;
+  for (int p = 0; p < N; ++p) safe = safe && adj_moderate(x[p]);
+  if (!safe) {
+    for (int p = 0; p < N; ++p) inv[p] = adj_rcp(x[p]);
+    return;
+  }
+  double pre[N], suf[N];
+  pre[0] = 1.0;
+  for (int p = 1; p < N; ++p) pre[p] = pre[p - 1] * x[p - 1];
+  suf[N - 1] = 1.0;
+  for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
+  const double ip = adj_rcp(pre[N - 1] * x[N - 1]);
+  for (int p = 0; p < N; ++p) inv[p] = ip * (pre[p] * suf[p]);
+}
+
+// Cell record of the adjoint sweep: the forward record Rec<M> followed by 1/sqrt(h_m)
+// (zero where layer m is not wet).
+template <int M>
+struct ARec {
+  static constexpr int IS = Rec<M>::N;
+  static constexpr int N = Rec<M>::N + M;
+};
+
+// Cotangent seen by a wave of speed s: a wave with s < 0 goes into A-dQ, s > 0 into A+dQ,
+// s = 0 half into each.
+template <int N>
+MLSWE_HD void adj_pick(double s, const double* am_b, const double* ap_b, double* z) {
+  const int sg = adj_sign(s);
+  if (sg != 0) {
+    for (int f = 0; f < N; ++f) z[f] = sg < 0 ? am_b[f] : ap_b[f];
+  } else {
+    for (int f = 0; f < N; ++f) z[f] = 0.5 * (am_b[f] + ap_b[f]);
+  }
 }
 
 // Coupled two-layer edge. cL, cR: cell records (Rec<2>). am_b, ap_b: cotangents of A-dQ and
@@ -43,48 +111,61 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
   if (wL != 3 || wR != 3) return false;
   const double g = P.g, r = P.r;
   // ---------------- forward recompute ----------------
-  double hb[2], coup[2], d0[2], d1[2], d2[2], S[2], iS[2], uh[2], vh[2];
+  double hb[2], coup[2], d0[2], d1[2], uh[2], vh[2];
   for (int m = 0; m < 2; ++m) {
     hb[m] = 0.5 * (cL[3 * m] + cR[3 * m]);
     coup[m] = cR[R::ETA + m] - cL[R::ETA + m];
     if (m == 1) coup[m] += r * (cR[0] - cL[0]);
     d0[m] = cR[3 * m + 1] - cL[3 * m + 1];
     d1[m] = (cR[3 * m + 1] * cR[R::UN + 2 * m] - cL[3 * m + 1] * cL[R::UN + 2 * m]) + g * hb[m] * coup[m];
-    d2[m] = cR[3 * m + 1] * cR[R::UN + 2 * m + 1] - cL[3 * m + 1] * cL[R::UN + 2 * m + 1];
-    S[m] = cL[R::SQ + m] + cR[R::SQ + m];
-    iS[m] = adj_rcp(S[m]);
+  }
+  const double c1 = g * hb[0], c2 = g * hb[1];
+  const double Hs = hb[0] + hb[1];
+  // 1/(sqrt hL + sqrt hR) per layer, 1/(hbar_1 + hbar_2), 1/c1 in one division
+  double iS[2], iH, ic1;
+  {
+    const double den[4] = {cL[R::SQ] + cR[R::SQ], cL[R::SQ + 1] + cR[R::SQ + 1], Hs, c1};
+    double inv[4];
+    adj_batched_rcp<4>(den, inv);
+    iS[0] = inv[0]; iS[1] = inv[1]; iH = inv[2]; ic1 = inv[3];
+  }
+  for (int m = 0; m < 2; ++m) {
     uh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m] + cR[R::SQ + m] * cR[R::UN + 2 * m]) * iS[m];
     vh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m + 1] + cR[R::SQ + m] * cR[R::UN + 2 * m + 1]) * iS[m];
   }
-  const double c1 = g * hb[0], c2 = g * hb[1];
-  const double Hs = hb[0] + hb[1], iH = adj_rcp(Hs);
   const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * iH;
   const double dc = c1 - c2;
-  const double disc = sqrt(dc * dc + 4.0 * r * c1 * c2);
+  const double X = dc * dc + 4.0 * r * c1 * c2;
+  const double idisc = adj_rsqrt(X), disc = X * idisc;
   const double csum = c1 + c2;
-  const double sp = sqrt(0.5 * (csum + disc)), sm = sqrt(0.5 * (csum - disc));
+  // mu_+ = (csum + disc)/2; mu_- from mu_+ mu_- = (1 - r) c1 c2 (no cancellation)
+  const double mup = 0.5 * (csum + disc);
+  const double isp = adj_rsqrt(mup), sp = mup * isp;
+  const double mum = ((1.0 - r) * c1 * c2) * (isp * isp);
+  const double ism = adj_rsqrt(mum), sm = mum * ism;
   double lam0[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
   const double du = uh[0] - uh[1];
   const bool newton = !(du * du >= (1.0 - r) * g * (hb[0] + hb[1])) && P.eigen == 0;
   double lam1[4], lam[4];
+  double iD[2][4];  // 1/P'(lambda) at each Newton step, reused in reverse
   const double rc = r * c1 * c2;
-  for (int p = 0; p < 4; ++p) {
-    double l = lam0[p];
-    if (newton) {
-      for (int it = 0; it < 2; ++it) {
-        if (it == 1) lam1[p] = l;
-        const double a1 = l - uh[0], a2 = l - uh[1];
+  for (int p = 0; p < 4; ++p) lam[p] = lam0[p];
+  if (newton) {
+    for (int it = 0; it < 2; ++it) {
+      double Pl[4], D[4];
+      for (int p = 0; p < 4; ++p) {
+        if (it == 1) lam1[p] = lam[p];
+        const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
         const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
-        const double Pl = f1 * f2 - rc;
-        const double D = 2.0 * (a1 * f2 + a2 * f1);
-        l = l - Pl * adj_rcp(D);
+        Pl[p] = f1 * f2 - rc;
+        D[p] = 2.0 * (a1 * f2 + a2 * f1);
       }
-    } else {
-      lam1[p] = l;
+      adj_batched_rcp<4>(D, iD[it]);
+      for (int p = 0; p < 4; ++p) lam[p] = lam[p] - Pl[p] * iD[it][p];
     }
-    lam[p] = l;
+  } else {
+    for (int p = 0; p < 4; ++p) lam1[p] = lam[p];
   }
-  const double ic1 = adj_rcp(c1);
   double al[4], tt[4];
   for (int p = 0; p < 4; ++p) { tt[p] = lam[p] - uh[0]; al[p] = (tt[p] * tt[p] - c1) * ic1; }
   // wave strengths: Vandermonde form (see mlswe_device.cuh)
@@ -93,24 +174,25 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
   const double m2 = c1 * d0[1] - p1 * m1 - p0 * m0;
   const double m3 = c1 * d1[1] - p1 * m2 - p0 * m1;
   double e1[4], e2[4], e3[4], iden[4], beta[4];
-  for (int p = 0; p < 4; ++p) {
-    const int qa = (p + 1) & 3, qb = (p + 2) & 3, qc = (p + 3) & 3;
-    e1[p] = lam[qa] + lam[qb] + lam[qc];
-    e2[p] = lam[qa] * lam[qb] + lam[qa] * lam[qc] + lam[qb] * lam[qc];
-    e3[p] = lam[qa] * lam[qb] * lam[qc];
-    const double den = (lam[p] - lam[qa]) * (lam[p] - lam[qb]) * (lam[p] - lam[qc]);
-    iden[p] = adj_rcp(den);
-    beta[p] = (m3 - e1[p] * m2 + e2[p] * m1 - e3[p] * m0) * iden[p];
+  {
+    double den[4];
+    for (int p = 0; p < 4; ++p) {
+      const int qa = (p + 1) & 3, qb = (p + 2) & 3, qc = (p + 3) & 3;
+      e1[p] = lam[qa] + lam[qb] + lam[qc];
+      e2[p] = lam[qa] * lam[qb] + lam[qa] * lam[qc] + lam[qb] * lam[qc];
+      e3[p] = lam[qa] * lam[qb] * lam[qc];
+      den[p] = (lam[p] - lam[qa]) * (lam[p] - lam[qb]) * (lam[p] - lam[qc]);
+    }
+    adj_batched_rcp<4>(den, iden);
   }
+  for (int p = 0; p < 4; ++p) beta[p] = (m3 - e1[p] * m2 + e2[p] * m1 - e3[p] * m0) * iden[p];
   // ---------------- reverse ----------------
   double lamb[4] = {0, 0, 0, 0}, alb[4] = {0, 0, 0, 0}, betab[4];
   double vhb[2] = {0, 0}, uhb[2] = {0, 0}, d0b[2] = {0, 0}, d1b[2] = {0, 0}, d2b[2] = {0, 0};
   double c1b = 0.0, c2b = 0.0;
   for (int p = 0; p < 4; ++p) {
-    double wl, wr;
-    adj_side_weights(lam[p], wl, wr);
     double Zb[6];
-    for (int f = 0; f < 6; ++f) Zb[f] = wl * am_b[f] + wr * ap_b[f];
+    adj_pick<6>(lam[p], am_b, ap_b, Zb);
     betab[p] = Zb[0] + lam[p] * Zb[1] + vh[0] * Zb[2] + al[p] * (Zb[3] + lam[p] * Zb[4] + vh[1] * Zb[5]);
     lamb[p] += beta[p] * (Zb[1] + al[p] * Zb[4]);
     vhb[0] += beta[p] * Zb[2];
@@ -118,9 +200,8 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
     vhb[1] += beta[p] * al[p] * Zb[5];
   }
   for (int m = 0; m < 2; ++m) {
-    double wl, wr;
-    adj_side_weights(uh[m], wl, wr);
-    const double zb = wl * am_b[3 * m + 2] + wr * ap_b[3 * m + 2];
+    double zb;
+    adj_pick<1>(uh[m], am_b + 3 * m + 2, ap_b + 3 * m + 2, &zb);
     d2b[m] += zb;
     vhb[m] -= d0[m] * zb;
     d0b[m] -= vh[m] * zb;
@@ -147,36 +228,41 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
     uhb[0] -= g2;
     c1b -= alb[p] * tt[p] * tt[p] * ic1 * ic1;
   }
-  // Newton steps in reverse
+  // Newton steps in reverse. A step is l' = l - P/D with P(l) = f1 f2 - r c1 c2,
+  // f_m = (l - u_m)^2 - c_m, D = dP/dl. For a parameter x, dl'/dx = -(P_x D - P D_x)/D^2 and
+  // dl'/dl = P D_l / D^2. With w = lb/D and v = w P/D the cotangent of x is -(w P_x - v D_x);
+  // P_u1 = -D - P_u2 and D_u1 = -D_l - D_u2 give the second velocity from the first.
   if (newton) {
+    const double rc1 = r * c1, rc2 = r * c2;
     for (int it = 1; it >= 0; --it) {
       for (int p = 0; p < 4; ++p) {
         const double l = it == 1 ? lam1[p] : lam0[p];
         const double a1 = l - uh[0], a2 = l - uh[1];
+        const double a12 = a1 * a2;
         const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
         const double Pl = f1 * f2 - rc;
-        const double D = 2.0 * (a1 * f2 + a2 * f1);
-        const double iD = adj_rcp(D), iD2 = iD * iD;
-        const double Dl = 2.0 * (f1 + f2 + 4.0 * a1 * a2);
-        const double Pu0 = -2.0 * a1 * f2, Du0 = -2.0 * (f2 + 2.0 * a1 * a2);
-        const double Pu1 = -2.0 * a2 * f1, Du1 = -2.0 * (f1 + 2.0 * a1 * a2);
-        const double Pc1 = -f2 - r * c2, Dc1 = -2.0 * a2;
-        const double Pc2 = -f1 - r * c1, Dc2 = -2.0 * a1;
+        const double Dl = 2.0 * ((f1 + f2) + 4.0 * a12);
         const double lb = lamb[p];
-        uhb[0] -= lb * (Pu0 * D - Pl * Du0) * iD2;
-        uhb[1] -= lb * (Pu1 * D - Pl * Du1) * iD2;
-        c1b -= lb * (Pc1 * D - Pl * Dc1) * iD2;
-        c2b -= lb * (Pc2 * D - Pl * Dc2) * iD2;
-        lamb[p] = lb * Pl * Dl * iD2;
+        const double w = lb * iD[it][p];
+        const double v = (w * Pl) * iD[it][p];
+        const double lnew = v * Dl;
+        // P_u1 = -2 a1 f2, D_u1 = -2 (f2 + 2 a1 a2); P_c1 = -(f2 + r c2), D_c1 = -2 a2; P_c2, D_c2 alike
+        const double gu0 = 2.0 * (v * (f2 + 2.0 * a12) - (w * a1) * f2);
+        const double gc1 = 2.0 * v * a2 - w * (f2 + rc2);
+        const double gc2 = 2.0 * v * a1 - w * (f1 + rc1);
+        uhb[0] -= gu0;
+        uhb[1] += (lb - lnew) + gu0;
+        c1b -= gc1;
+        c2b -= gc2;
+        lamb[p] = lnew;
       }
     }
   }
   // guesses lam0 = ubar -+ sqrt(mu_+-)
   const double ubarb = lamb[0] + lamb[1] + lamb[2] + lamb[3];
   const double spb = lamb[3] - lamb[0], smb = lamb[2] - lamb[1];
-  const double mupb = spb * 0.5 * adj_rcp(sp), mumb = smb * 0.5 * adj_rcp(sm);
+  const double mupb = spb * 0.5 * isp, mumb = smb * 0.5 * ism;
   const double csumb = 0.5 * (mupb + mumb), discb = 0.5 * (mupb - mumb);
-  const double idisc = adj_rcp(disc);
   c1b += csumb + discb * (dc + 2.0 * r * c2) * idisc;
   c2b += csumb + discb * (-dc + 2.0 * r * c1) * idisc;
   double hbb[2];
@@ -219,9 +305,9 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
     double hbs[2] = {hbar_b[s][0] + etab[s][0], hbar_b[s][1] + e2b};
     Bb += e2b;
     for (int m = 0; m < 2; ++m) {
-      const double h = c[3 * m], ih = adj_rcp(h);
+      const double is = c[ARec<2>::IS + m], ih = is * is;  // 1/sqrt(h), 1/h
       const double un = c[R::UN + 2 * m], ut = c[R::UN + 2 * m + 1];
-      hbs[m] += -(unb[s][m] * un + utb[s][m] * ut) * ih + sqb[s][m] * 0.5 * adj_rcp(c[R::SQ + m]);
+      hbs[m] += -(unb[s][m] * un + utb[s][m] * ut) * ih + sqb[s][m] * 0.5 * is;
       qb[3 * m] += hbs[m];
       qb[3 * m + 1] += hnb[s][m] + unb[s][m] * ih;
       qb[3 * m + 2] += utb[s][m] * ih;
@@ -243,21 +329,17 @@ MLSWE_HD bool edge_vjp_1(const DevParams& P, const double* cL, const double* cR,
   const double coup = cR[R::ETA] - cL[R::ETA];
   const double d0 = hnR - hnL;
   const double d1 = (hnR * unR - hnL * unL) + g * hb * coup;
-  const double d2 = hnR * utR - hnL * utL;
   const double iS = adj_rcp(sL + sR);
   const double uh = (sL * unL + sR * unR) * iS, vh = (sL * utL + sR * utR) * iS;
-  const double ch = sqrt(g * hb);
+  const double ghb = g * hb, ich = adj_rsqrt(ghb), ch = ghb * ich;
   const double s1 = uh - ch, s2 = uh + ch;
-  const double inv = adj_rcp(s2 - s1);
+  const double inv = 0.5 * ich;  // 1/(s2 - s1)
   const double b1 = (s2 * d0 - d1) * inv, b2 = (d1 - s1 * d0) * inv;
   // reverse
-  double w1l, w1r, w2l, w2r, wsl, wsr;
-  adj_side_weights(s1, w1l, w1r);
-  adj_side_weights(s2, w2l, w2r);
-  adj_side_weights(uh, wsl, wsr);
-  double Z1b[3], Z2b[3];
-  for (int f = 0; f < 3; ++f) { Z1b[f] = w1l * am_b[f] + w1r * ap_b[f]; Z2b[f] = w2l * am_b[f] + w2r * ap_b[f]; }
-  const double zb = wsl * am_b[2] + wsr * ap_b[2];
+  double Z1b[3], Z2b[3], zb;
+  adj_pick<3>(s1, am_b, ap_b, Z1b);
+  adj_pick<3>(s2, am_b, ap_b, Z2b);
+  adj_pick<1>(uh, am_b + 2, ap_b + 2, &zb);
   // Z1 = b1 (1, s1, vh), Z2 = b2 (1, s2, vh), shear = d2 - vh d0
   const double b1b = Z1b[0] + s1 * Z1b[1] + vh * Z1b[2];
   const double b2b = Z2b[0] + s2 * Z2b[1] + vh * Z2b[2];
@@ -272,7 +354,7 @@ MLSWE_HD bool edge_vjp_1(const DevParams& P, const double* cL, const double* cR,
   // s1 = uh - ch, s2 = uh + ch, ch = sqrt(g hb)
   const double uhb = s1b + s2b;
   const double chb = s2b - s1b;
-  double hbb = chb * g * 0.5 * adj_rcp(ch);
+  double hbb = chb * g * 0.5 * ich;
   double unb[2], utb[2], sqb[2], hnb[2] = {0, 0};
   unb[0] = uhb * sL * iS; unb[1] = uhb * sR * iS;
   utb[0] = vhb * sL * iS; utb[1] = vhb * sR * iS;
@@ -287,9 +369,8 @@ MLSWE_HD bool edge_vjp_1(const DevParams& P, const double* cL, const double* cR,
   double* qb[2] = {qLb, qRb};
   double etab[2] = {-coupb, coupb};
   for (int s = 0; s < 2; ++s) {
-    const double h = c[s][0], ih = adj_rcp(h);
-    double hsb = 0.5 * hbb + etab[s] - (unb[s] * c[s][R::UN] + utb[s] * c[s][R::UN + 1]) * ih +
-                 sqb[s] * 0.5 * adj_rcp(c[s][R::SQ]);
+    const double is = c[s][ARec<1>::IS], ih = is * is;  // 1/sqrt(h), 1/h
+    double hsb = 0.5 * hbb + etab[s] - (unb[s] * c[s][R::UN] + utb[s] * c[s][R::UN + 1]) * ih + sqb[s] * 0.5 * is;
     qb[s][0] += hsb;
     qb[s][1] += hnb[s] + unb[s] * ih;
     qb[s][2] += utb[s] * ih;
