@@ -10,8 +10,10 @@ Also reported on the same line:
     with 1000 level-1 and 3000 level-2 patches of sides 16..64 (seeded synthetic layout),
     whole subcycled coarse steps; all patches of a level in one persistent launch replayed
     from a CUDA graph versus one launch per patch;
-  * ``ensemble``: 64 members of sizes U{128..512}^2 with a refined level (ratio 4), all
-    members stepped together with per-member time steps, batched versus per-patch.
+  * ``ensemble``: 256 members of sizes U{128..512}^2 with a refined level (ratio 4), all
+    members stepped together with per-member time steps, batched versus per-patch;
+  * ``adjoint``: gauge-misfit gradient on a 512^2 grid over 200 first-order steps with a
+    checkpoint every 20 steps: backward (recomputation + transposed steps) over forward.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlswe|reference]
 
@@ -97,6 +99,27 @@ class ClockSampler:
 
 def _dist():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the headline replica a rank advances (independent problems, one per rank)."""
+    return 1000 + rank
+
+
+def max_over_ranks(ms: float, ws: int, device=None) -> float:
+    """Longest timed-region duration over all ranks (every rank receives it)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step_per_rank: float, steps: int, ws: int, tmax_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_step_per_rank * steps * ws / (tmax_ms * 1e-3)
 
 
 def _workload_name():
@@ -218,7 +241,7 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
             "autotuned_tiles": chosen}
 
 
-def bench_ensemble(pkg, torch, stream, n_members=64, steps=3):
+def bench_ensemble(pkg, torch, stream, n_members=256, steps=3):
     """Ensemble of independent members, U{128..512}^2 coarse grids, one refined level."""
     r = 4
     members = [I.ensemble_member(k) for k in range(n_members)]
@@ -245,6 +268,7 @@ def bench_ensemble(pkg, torch, stream, n_members=64, steps=3):
     H.advance(1)
     ms_p = _time_advance(torch, H, stream, steps)
     t, dt = H.get_time()
+    dev_gb = torch.cuda.max_memory_allocated() / 1e9
     H.close()
     lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
     lp = upd * M_LAYERS * steps / (ms_p * 1e-3)
@@ -252,7 +276,8 @@ def bench_ensemble(pkg, torch, stream, n_members=64, steps=3):
                         "1 refined level (ratio 4, seeded patches)",
             "members": n_members, "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
             "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
-            "distinct_member_dt": int(len(set(np.round(dt, 12)))), "autotuned_tiles": chosen}
+            "distinct_member_dt": int(len(set(np.round(dt, 12)))), "autotuned_tiles": chosen,
+            "peak_device_gb": dev_gb}
 
 
 def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
@@ -309,7 +334,7 @@ def run_gpu(args):
     pkg.build()
 
     # Each rank advances its own replica of the headline workload (independent problems).
-    w = I.scale(N_CELLS, seed=1000 + rank)
+    w = I.scale(N_CELLS, seed=replica_seed(rank))
     cfg = pkg.Config(M=2, dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
     stream = torch.cuda.Stream(device=dev)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, N_CELLS, N_CELLS)], stream=stream.cuda_stream)
@@ -360,12 +385,8 @@ def run_gpu(args):
     H.close()
 
     lcu_per_step = N_CELLS * N_CELLS * M_LAYERS
-    tmax = ms
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        tmax = float(tt.item())
-    value = lcu_per_step * args.steps * ws / (tmax * 1e-3)
+    tmax = max_over_ranks(ms, ws, dev)
+    value = job_value(lcu_per_step, args.steps, ws, tmax)
 
     sx_ms, sx_n = per_kernel["sweep_x"]
     sy_ms, sy_n = per_kernel["sweep_y"]
