@@ -49,7 +49,7 @@ FP64_FLOP_PER_CELL_UPDATE = 1293.25
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
-SWEEP_X_DRAM_BYTES = 396.4e6
+SWEEP_X_DRAM_BYTES = 397.6e6
 
 
 class ClockSampler:
@@ -319,6 +319,14 @@ def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
             "forward_lcups": n * n * M_LAYERS * steps / (fwd * 1e-3), "loss": loss}
 
 
+def run_adjoint_only():
+    import torch
+    import paper_1803_01450_gb300 as pkg
+    pkg.build()
+    stream = torch.cuda.Stream()
+    print(json.dumps({"adjoint": bench_adjoint(pkg, torch, stream)}), flush=True)
+
+
 def run_gpu(args):
     import torch
     import paper_1803_01450_gb300 as pkg
@@ -431,9 +439,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR and ensemble figures")
+    ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="print only the adjoint figure (a short command for profiling the adjoint kernels)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.adjoint_only:
+        run_adjoint_only()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
