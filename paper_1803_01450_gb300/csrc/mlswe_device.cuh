@@ -100,20 +100,30 @@ __device__ __forceinline__ double limiter_phi_fast(int kind, double th) {
   return pos_min(pos_min(fma(0.5, th, 0.5), 2.0), th + th);
 }
 
-// Reciprocals of N positive numbers with one division when their product stays well inside
-// the FP64 range: 1/x_p = (1/prod x) * prod_{q != p} x_q.
+// |x| in [2^-160, 2^160), read from the exponent field (integer unit, not the FP64 pipe).
+__device__ __forceinline__ bool moderate(double x) {
+  const unsigned e = (unsigned)(__double_as_longlong(x) >> 52) & 0x7ffu;
+  return e - 863u <= 320u;
+}
+
+// Reciprocals of N <= 6 nonzero numbers with one division:
+// 1/x_p = (1/prod x) * prod_{q != p} x_q, used when every |x_p| lies in [2^-160, 2^160) (so
+// every partial product stays a normal FP64 number); otherwise one division each.
 template <int N>
 __device__ __forceinline__ void batched_reciprocal(const double* x, double* inv) {
-  double pre[N], suf[N];
-  pre[0] = 1.0;
+  static_assert(N <= 6, "partial products must stay in range");
+  bool safe = true;
 #pragma unroll
-  for (int p = 1; p < N; ++p) pre[p] = pre[p - 1] * x[p - 1];
-  suf[N - 1] = 1.0;
+  for (int p = 0; p < N; ++p) safe = safe && moderate(x[p]);
+  if (safe) {
+    double pre[N], suf[N];
+    pre[0] = 1.0;
 #pragma unroll
-  for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
-  const double prod = pre[N - 1] * x[N - 1];
-  if (prod > 1e-280 && prod < 1e280) {
-    const double ip = rcp(prod);
+    for (int p = 1; p < N; ++p) pre[p] = pre[p - 1] * x[p - 1];
+    suf[N - 1] = 1.0;
+#pragma unroll
+    for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
+    const double ip = rcp(pre[N - 1] * x[N - 1]);
 #pragma unroll
     for (int p = 0; p < N; ++p) inv[p] = ip * (pre[p] * suf[p]);
   } else {
@@ -145,12 +155,16 @@ struct EdgeW {
   static constexpr int NA = 2 * M;
   double a[NA], b[NA], s[NA];
   double z[M], us[M], vh[M];
+  // What the acoustic waves of layer m sum to: its mass and normal-momentum flux jumps
+  // (sum_p Z_p = jump exactly for the f-wave split, up to rounding).
+  double t0[M], t1[M];
   int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
 };
 
 template <int M>
 struct WRec {  // shared-memory layout of EdgeW
-  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, N = 9 * M;
+  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, T0 = 9 * M, T1 = 10 * M,
+                       N = 11 * M;
 };
 
 // Layer of acoustic slot p in the per-layer (decoupled) branch.
@@ -174,6 +188,8 @@ __device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, d
   W.z[m] = d2 - vh * d0;
   W.us[m] = us;
   W.vh[m] = vh;
+  W.t0[m] = d0;
+  W.t1[m] = d1;
 }
 
 // Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
@@ -185,7 +201,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
 #pragma unroll
   for (int p = 0; p < 2 * M; ++p) { W.a[p] = 0.0; W.b[p] = 0.0; W.s[p] = 0.0; }
 #pragma unroll
-  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; }
+  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; }
   W.wall = 0;
 
   double d0[M], d1[M], d2[M], hb[M];
@@ -296,6 +312,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       W.z[m] = d2[m] - vh[m] * d0[m];
       W.us[m] = uh[m];
       W.vh[m] = vh[m];
+      W.t0[m] = d0[m];
+      W.t1[m] = d1[m];
     }
     return;
   }

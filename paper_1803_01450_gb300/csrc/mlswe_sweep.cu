@@ -155,6 +155,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         wav[(WR::Z + m) * kMaxEdges + es] = W.z[m];
         wav[(WR::US + m) * kMaxEdges + es] = W.us[m];
         wav[(WR::VH + m) * kMaxEdges + es] = W.vh[m];
+        wav[(WR::T0 + m) * kMaxEdges + es] = W.t0[m];
+        wav[(WR::T1 + m) * kMaxEdges + es] = W.t1[m];
       }
       wallb[es] = W.wall;
       if (interior && e >= 1 && e <= len + 1) {
@@ -187,14 +189,16 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       double vh[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) vh[m] = wav[(WR::VH + m) * kMaxEdges + es];
-      double La = 0, Lsa = 0, Lb = 0, Lsb = 0, Ra = 0, Rsa = 0, Rb = 0, Rsb = 0;
-      // Wave limiter of the acoustic waves: theta_p = zu_p / zz_p with one reciprocal for
-      // all of them (1/zz_p = (1/prod zz) * prod_{q != p} zz), falling back to one
-      // reciprocal each when the product leaves the safe exponent range.
-      constexpr int NA = 2 * M;
-      double zzv[NA], zuv[NA];
-      int sc[NA];
-      bool act[NA];
+      // Left-going parts L (A-dQ minus the correction flux); the right-going parts follow as
+      // R = T - L, since the waves of a layer sum to its flux jump T (mass, normal momentum)
+      // and the transverse row to vh T_mass + z.
+      double La = 0, Lsa = 0, Lb = 0, Lsb = 0;
+      // Wave limiter: theta_p = zu_p / zz_p for the acoustic waves and zu_m / z_m for the shear
+      // waves ((z_up z)/(z z) with z != 0), with one reciprocal for all of them.
+      constexpr int NA = 2 * M, NR = 2 * M + M;
+      double den[NR], num[NR];
+      int sc[NR];
+      bool act[NR];
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
         const double a = wav[(WR::A + p) * kMaxEdges + es];
@@ -204,8 +208,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const int lay = layer_of_slot<M>(p);
         const bool walled = (wall >> (2 * lay)) & 3;
         act[p] = P.order >= 2 && sc[p] != 0 && !walled;
-        zzv[p] = 1.0;
-        zuv[p] = 0.0;
+        den[p] = 1.0;
+        num[p] = 0.0;
         if (act[p]) {
           const int eu = sc[p] > 0 ? esl : esr;
           const double au = wav[(WR::A + p) * kMaxEdges + eu];
@@ -220,11 +224,27 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
             zz += b * b * (ss + vh[M - 1] * vh[M - 1]);
             zu += b * bu * (su1 + vh[M - 1] * vu1);
           }
-          if (zz > 0.0) { zzv[p] = zz; zuv[p] = zu; }
+          if (zz > 0.0) { den[p] = zz; num[p] = zu; }
+          else act[p] = false;
         }
       }
-      double izz[NA];
-      batched_reciprocal<NA>(zzv, izz);
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double z = wav[(WR::Z + m) * kMaxEdges + es];
+        const double us = wav[(WR::US + m) * kMaxEdges + es];
+        const bool walled = (wall >> (2 * m)) & 3;
+        const int q = NA + m;
+        sc[q] = sign_class(us);
+        act[q] = P.order >= 2 && sc[q] != 0 && !walled && ((__double_as_longlong(z) << 1) != 0);
+        den[q] = 1.0;
+        num[q] = 0.0;
+        if (act[q]) {
+          den[q] = z;
+          num[q] = wav[(WR::Z + m) * kMaxEdges + (sc[q] > 0 ? esl : esr)];
+        }
+      }
+      double iden[NR];
+      batched_reciprocal<NR>(den, iden);
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
         const double a = wav[(WR::A + p) * kMaxEdges + es];
@@ -232,40 +252,35 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const double s = wav[(WR::S + p) * kMaxEdges + es];
         double corr = 0.0;
         if (act[p]) {
-          const double phi = limiter_phi_fast(P.limiter, zuv[p] * izz[p]);
+          const double phi = limiter_phi_fast(P.limiter, num[p] * iden[p]);
           corr = (sc[p] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(s), 1.0) * phi;
         }
         const double cl = (sc[p] < 0 ? 1.0 : (sc[p] > 0 ? 0.0 : 0.5)) + corr;
-        const double cr = 1.0 - cl;
-        const double ca = cl * a, cb = cl * b, ra = cr * a, rb = cr * b;
+        const double ca = cl * a, cb = cl * b;
         La += ca; Lsa += ca * s; Lb += cb; Lsb += cb * s;
-        Ra += ra; Rsa += ra * s; Rb += rb; Rsb += rb * s;
       }
       double Lz[M], Rz[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) {
+        const int q = NA + m;
         const double z = wav[(WR::Z + m) * kMaxEdges + es];
         const double us = wav[(WR::US + m) * kMaxEdges + es];
         double corr = 0.0;
-        const bool walled = (wall >> (2 * m)) & 3;
-        const int su = sign_class(us);
-        if (P.order >= 2 && su != 0 && !walled) {
-          const int eu = su > 0 ? esl : esr;
-          const double zu = wav[(WR::Z + m) * kMaxEdges + eu];
-          const double zz = z * z;
-          const double th = zz > 0.0 ? (zu * z) * rcp(zz) : 0.0;
-          const double phi = limiter_phi_fast(P.limiter, th);
-          corr = (su > 0 ? 0.5 : -0.5) * fma(-nu, fabs(us), 1.0) * phi;
+        if (act[q]) {
+          const double phi = limiter_phi_fast(P.limiter, num[q] * iden[q]);
+          corr = (sc[q] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(us), 1.0) * phi;
         }
-        const double cl = (su < 0 ? 1.0 : (su > 0 ? 0.0 : 0.5)) + corr;
+        const double cl = (sc[q] < 0 ? 1.0 : (sc[q] > 0 ? 0.0 : 0.5)) + corr;
         Lz[m] = cl * z;
-        Rz[m] = (1.0 - cl) * z;
+        Rz[m] = z - Lz[m];
       }
+      const double T0a = wav[(WR::T0 + 0) * kMaxEdges + es], T1a = wav[(WR::T1 + 0) * kMaxEdges + es];
       Lc[0] = La; Lc[1] = Lsa; Lc[2] = vh[0] * La + Lz[0];
-      Rc[0] = Ra; Rc[1] = Rsa; Rc[2] = vh[0] * Ra + Rz[0];
+      Rc[0] = T0a - La; Rc[1] = T1a - Lsa; Rc[2] = vh[0] * Rc[0] + Rz[0];
       if (M == 2) {
+        const double T0b = wav[(WR::T0 + M - 1) * kMaxEdges + es], T1b = wav[(WR::T1 + M - 1) * kMaxEdges + es];
         Lc[3] = Lb; Lc[4] = Lsb; Lc[5] = vh[M - 1] * Lb + Lz[M - 1];
-        Rc[3] = Rb; Rc[4] = Rsb; Rc[5] = vh[M - 1] * Rb + Rz[M - 1];
+        Rc[3] = T0b - Lb; Rc[4] = T1b - Lsb; Rc[5] = vh[M - 1] * Rc[3] + Rz[M - 1];
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) {
@@ -348,7 +363,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 }
 
 size_t sweep_smem_bytes(int M) {
-  const int rn = 7 * M + 1, wn = 9 * M;
+  const int rn = 7 * M + 1, wn = 11 * M;
   return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
 }
 
