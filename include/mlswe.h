@@ -213,7 +213,8 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
 /* Launch configuration of the sweep kernels (not in the paper): tile of `len`
  * cells along the sweep direction times `lines` lines (x sweep dir = 0: rows;
  * y sweep dir = 1: columns), with lines * (len + 3) <= 256 and len >= 4, and
- * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range. */
+ * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range.
+ * Default: 125 x 2 with 2 CTAs per SM in both directions. */
 mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm);
 
 /* Discrete adjoint of the fixed-grid step (not written out in the paper; the
@@ -224,7 +225,10 @@ mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_pe
  * state (every layer wet on both sides of every edge; EINVAL otherwise).
  * gauge_ij: host int32 [n_gauges][2] cell indices (i, j); obs: host
  * [n_steps][n_gauges]. The forward pass keeps a state every ckpt_every steps;
- * the backward pass recomputes each segment from it. */
+ * the backward pass recomputes each segment from it. Setup also times three
+ * tile shapes of the transposed sweeps on the current state (CUDA events) and
+ * keeps the fastest per direction (the timings are representative when it
+ * follows mlswe_set_dt and mlswe_set_state; results never depend on the shape). */
 mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_gauges, const int32_t* gauge_ij,
                                  const double* obs);
 

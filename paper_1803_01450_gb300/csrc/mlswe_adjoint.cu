@@ -27,11 +27,16 @@ __device__ __forceinline__ int aeslot(int l, int e, int len, int nl) {  // e in 
   return DIR == 0 ? l * (len + 1) + e : e * nl + l;
 }
 
+// Threads per CTA of the adjoint sweep: two CTAs per SM fit the 255 registers the edge VJP
+// takes, so one CTA's load and gather phases overlap the other's FP64 work; tiles have at
+// most kAdjThreads edges.
+constexpr int kAdjThreads = 128;
+
 // Adjoint of one first-order sweep over the tiles of the level. state: input of the
 // forward sweep (pitched like the level); lam_out: cotangent of its output; lam_in:
 // cotangent of its input (written); gB: bathymetry cotangent (accumulated).
 template <int M, int DIR>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kAdjThreads, 2)
 adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
                      const int* __restrict__ n_items_dev, const double* __restrict__ state,
                      const double* __restrict__ lam_out, double* __restrict__ lam_in, double* __restrict__ gB,
@@ -209,7 +214,7 @@ static cudaError_t launch_adjoint_t(const DevParams& P, const LevelDesc* descs, 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  adjoint_sweep_kernel<M, DIR><<<grid, kThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in, gB, status);
+  adjoint_sweep_kernel<M, DIR><<<grid, kAdjThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in, gB, status);
   return cudaGetLastError();
 }
 
@@ -266,6 +271,10 @@ struct Adjoint {
   double* obs = nullptr;
   double* loss = nullptr;
   LevelDesc* descs = nullptr;  // [ckpt] level-0 descriptors: step a reads slots[a], writes slots[a+1], qstar[a]
+  SweepItem* items[2] = {nullptr, nullptr};  // tiles of the transposed sweeps, per direction
+  int* n_items[2] = {nullptr, nullptr};
+  int item_cap[2] = {0, 0};
+  int tile[2][2] = {{0, 0}, {0, 0}};         // chosen (len, lines) per direction
   bool forward_done = false;
   bool last_kept = false;      // the slots hold the last segment as the forward pass left it
 };
@@ -327,6 +336,80 @@ static mlswe_status adj_build_descs(Hier* H, Adjoint* A) {
   return MLSWE_OK;
 }
 
+// Tiles of len x lines cells over the whole level for the transposed sweep in direction dir
+// (along x: rows j, cells i; along y: columns i, cells j).
+static mlswe_status adj_build_items(mlswe_hier* H, Adjoint* A, int dir, int len, int lines) {
+  const Level& V = H->mem[0].lev[0];
+  const int NA = dir == 0 ? V.NX : V.NY, NL = dir == 0 ? V.NY : V.NX;
+  std::vector<SweepItem> it;
+  for (int l = 0; l < NL; l += lines)
+    for (int a = 0; a < NA; a += len) {
+      SweepItem s;
+      s.desc = 0;
+      s.i0 = dir == 0 ? a : l;
+      s.j0 = dir == 0 ? l : a;
+      s.len = std::min(len, NA - a);
+      s.nlines = std::min(lines, NL - l);
+      s.flags = 1;
+      it.push_back(s);
+    }
+  if ((int)it.size() > A->item_cap[dir]) {
+    if (A->items[dir]) dev_free(H, A->items[dir]);
+    A->items[dir] = (SweepItem*)dev_alloc(H, it.size() * sizeof(SweepItem));
+    if (!A->items[dir]) return afail(H, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+    A->item_cap[dir] = (int)it.size();
+  }
+  if (!A->n_items[dir]) {
+    A->n_items[dir] = (int*)dev_alloc(H, sizeof(int));
+    if (!A->n_items[dir]) return afail(H, MLSWE_ENOMEM, "adjoint_setup: out of memory");
+  }
+  const int n = (int)it.size();
+  ACUDA(H, cudaMemcpyAsync(A->items[dir], it.data(), it.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, H->st));
+  ACUDA(H, cudaMemcpyAsync(A->n_items[dir], &n, sizeof(int), cudaMemcpyHostToDevice, H->st));
+  ACUDA(H, cudaStreamSynchronize(H->st));
+  A->tile[dir][0] = len;
+  A->tile[dir][1] = lines;
+  return MLSWE_OK;
+}
+
+// Picks the tile shape of each transposed sweep by timing it (CUDA events) on the level's
+// current state with zero cotangents; candidates have at most kAdjThreads edges per tile.
+// Leaves lam, lam2 and gB with scratch values (the backward pass clears them).
+static mlswe_status adj_autotune(mlswe_hier* H, Adjoint* A) {
+  static const int cand[][2] = {{125, 1}, {61, 2}, {29, 4}};
+  const Level& V = H->mem[0].lev[0];
+  const double* q = V.q[H->parity[0]];
+  ACUDA(H, cudaMemsetAsync(A->lam, 0, A->state_bytes, H->st));
+  cudaEvent_t e0, e1;
+  ACUDA(H, cudaEventCreate(&e0));
+  ACUDA(H, cudaEventCreate(&e1));
+  const int grid = 2 * H->num_sms;
+  for (int dir = 0; dir < 2; ++dir) {
+    float best = 1e30f;
+    int bl = cand[0][0], bn = cand[0][1];
+    for (const auto& c : cand) {
+      mlswe_status s = adj_build_items(H, A, dir, c[0], c[1]);
+      if (s != MLSWE_OK) return s;
+      ACUDA(H, launch_adjoint_sweep(dir, H->dp, H->d_desc, A->items[dir], A->n_items[dir], grid, q, A->lam, A->lam2,
+                                    A->gB, H->d_status, H->st));
+      ACUDA(H, cudaEventRecord(e0, H->st));
+      for (int k = 0; k < 3; ++k)
+        ACUDA(H, launch_adjoint_sweep(dir, H->dp, H->d_desc, A->items[dir], A->n_items[dir], grid, q, A->lam,
+                                      A->lam2, A->gB, H->d_status, H->st));
+      ACUDA(H, cudaEventRecord(e1, H->st));
+      ACUDA(H, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      ACUDA(H, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bl = c[0]; bn = c[1]; }
+    }
+    mlswe_status s = adj_build_items(H, A, dir, bl, bn);
+    if (s != MLSWE_OK) return s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return MLSWE_OK;
+}
+
 // Step a of the segment being recomputed (both sweeps, nothing recorded).
 static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
   for (int dir = 0; dir < 2; ++dir) {
@@ -383,6 +466,8 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
     ACUDA(h, cudaMemcpyAsync(A->obs, obs, (size_t)n_steps * n_gauges * 8, cudaMemcpyHostToDevice, h->st));
   }
   mlswe_status s = adj_build_descs(h, A);
+  if (s != MLSWE_OK) return s;
+  s = adj_autotune(h, A);
   if (s != MLSWE_OK) return s;
   A->forward_done = false;
   A->last_kept = false;
@@ -442,7 +527,7 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
   const Level& V = h->mem[0].lev[0];
   const int M = h->cfg.M, F = 3 * M;
   const size_t plane = (size_t)V.NY * V.P;
-  const int grid = h->num_sms;
+  const int grid = 2 * h->num_sms;
   ACUDA(h, cudaMemsetAsync(A->lam, 0, A->state_bytes, h->st));
   ACUDA(h, cudaMemsetAsync(A->gB, 0, plane * 8, h->st));
   ACUDA(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
@@ -471,12 +556,12 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
       timer_end(h, tok);
       // transposed y sweep (on Q* of step n), then transposed x sweep (on Q^n)
       timer_begin(h, KC_ADJOINT, &tok);
-      ACUDA(h, launch_adjoint_sweep(1, h->dp, A->descs + a, h->wl[1].d_items, h->wl[1].d_count, grid, A->qstar[a],
-                                    A->lam, A->lam2, A->gB, h->d_status, h->st));
+      ACUDA(h, launch_adjoint_sweep(1, h->dp, A->descs + a, A->items[1], A->n_items[1], grid, A->qstar[a], A->lam,
+                                    A->lam2, A->gB, h->d_status, h->st));
       timer_end(h, tok);
       timer_begin(h, KC_ADJOINT, &tok);
-      ACUDA(h, launch_adjoint_sweep(0, h->dp, A->descs + a, h->wl[0].d_items, h->wl[0].d_count, grid, A->slots[a],
-                                    A->lam2, A->lam, A->gB, h->d_status, h->st));
+      ACUDA(h, launch_adjoint_sweep(0, h->dp, A->descs + a, A->items[0], A->n_items[0], grid, A->slots[a], A->lam2,
+                                    A->lam, A->gB, h->d_status, h->st));
       timer_end(h, tok);
     }
   }

@@ -328,9 +328,10 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->wl.resize(H->L * 2);
   H->shape.resize(H->L * 2);
   for (int l = 0; l < H->L; ++l) {
-    // Default tiles: 125-cell rows x 2 (x sweep), 125-cell columns x 2 (y sweep); 256 edges.
-    H->shape[l * 2] = TileShape{125, 2};
-    H->shape[l * 2 + 1] = TileShape{125, 2};
+    // Default tiles: 125-cell rows x 2 (x sweep), 125-cell columns x 2 (y sweep); 256 edges;
+    // 2 CTAs per SM (the autotuner's choice on every workload measured).
+    H->shape[l * 2] = TileShape{125, 2, 2};
+    H->shape[l * 2 + 1] = TileShape{125, 2, 2};
   }
   H->t_ghost.resize(H->L);
   H->t_avg.resize(H->L);

@@ -74,6 +74,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
     const double dt = *D.dt;
     const double nu = dt * (DIR == 0 ? D.inv_dx : D.inv_dy);
+    const long long tol_bits = __double_as_longlong(P.dry_tol);
     // interior lines of a recorded step count toward the CFL reduction and the reflux fluxes
     const bool interior = (item.flags & 1) && record;
 
@@ -109,11 +110,14 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const double hn = (DIR == 0 ? hu : hv) * sgn;
         const double ht = DIR == 0 ? hv : hu;
         rec[3 * m] = h; rec[3 * m + 1] = hn; rec[3 * m + 2] = ht;
-        const bool w = above && (h > P.dry_tol);
+        // comparisons on bit patterns (integer unit): for a bound b >= +0 and any non-NaN
+        // x, x > b exactly when bits(x) > bits(b) as signed 64-bit integers
+        const long long hbits = __double_as_longlong(h);
+        const bool w = above && (hbits > tol_bits);
         above = w;
         wet |= w ? (1 << m) : 0;
         // one reciprocal square root gives both sqrt(h) = h t and 1/h = t t
-        const double t = h > 0.0 ? rsqrt(h) : 0.0;
+        const double t = hbits > 0 ? rsqrt(h) : 0.0;
         double un = 0.0, ut = 0.0;
         if (w) { const double ih = t * t; un = hn * ih; ut = ht * ih; }
         rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
@@ -224,7 +228,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
             zz += b * b * (ss + vh[M - 1] * vh[M - 1]);
             zu += b * bu * (su1 + vh[M - 1] * vu1);
           }
-          if (zz > 0.0) { den[p] = zz; num[p] = zu; }
+          if (__double_as_longlong(zz) > 0) { den[p] = zz; num[p] = zu; }
           else act[p] = false;
         }
       }
@@ -339,8 +343,9 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         qn[f] = cell[f * kMaxCells + c] - nu * (wav[(F + f) * kMaxEdges + gL] + wav[f * kMaxEdges + gR]);
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        if (qn[3 * m] < 0.0) qn[3 * m] = 0.0;
-        if (qn[3 * m] <= P.dry_tol) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
+        // h < 0 (or -0) -> +0; h <= dry_tol -> momenta 0 (bit-pattern comparisons as above)
+        if (__double_as_longlong(qn[3 * m]) < 0) qn[3 * m] = 0.0;
+        if (__double_as_longlong(qn[3 * m]) <= tol_bits) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
       }
       int i, j;
       if (DIR == 0) { i = item.i0 + k; j = item.j0 + l; }
