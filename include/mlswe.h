@@ -232,6 +232,18 @@ mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_pe
 mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_gauges, const int32_t* gauge_ij,
                                  const double* obs);
 
+/* Whether the adjoint keeps, for every step of the segment being recomputed, the
+ * forward record of each coupled two-layer edge (eigenvalue guesses and Newton
+ * iterates, the reciprocals of the Newton steps, of the Roe weights and of the
+ * Vandermonde denominators, the wave strengths: 36 doubles per edge and sweep,
+ * ckpt_every steps of them, about 2 * 36 * 8 * (nx + 1) * (ny + 1) * ckpt_every
+ * bytes) so the transposed sweeps read it instead of rebuilding it. enable = 1
+ * (the default) or 0; takes effect at the next mlswe_adjoint_setup, which keeps
+ * the rebuilding path when the memory cannot be allocated. Results agree to
+ * rounding either way. Not in the paper (a memory-for-arithmetic trade on a
+ * device whose FP64 rate bounds the adjoint). */
+mlswe_status mlswe_adjoint_keep_edge_data(mlswe_h h, int enable);
+
 /* Runs n_steps first-order steps from the current level-0 state (advancing it)
  * and returns J in *loss (host). */
 mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss);

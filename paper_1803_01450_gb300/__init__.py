@@ -124,6 +124,7 @@ _SIGS = {
     "mlswe_set_tiles": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int],
     "mlswe_set_execution": [_H, ctypes.c_int, ctypes.c_int],
     "mlswe_adjoint_setup": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _dp],
+    "mlswe_adjoint_keep_edge_data": [_H, ctypes.c_int],
     "mlswe_fixed_forward": [_H, _dp],
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
@@ -333,6 +334,11 @@ class Hierarchy:
         o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
         self._check(self.L.mlswe_adjoint_setup(self.h, n_steps, ckpt_every, len(g), g.ctypes.data_as(_i32p), _d(o)),
                     "adjoint_setup")
+
+    def adjoint_keep_edge_data(self, enable: bool = True):
+        """Keep per-edge forward records of the recomputed steps (default) or rebuild them in
+        the transposed sweeps; takes effect at the next adjoint_setup."""
+        self._check(self.L.mlswe_adjoint_keep_edge_data(self.h, 1 if enable else 0), "adjoint_keep_edge_data")
 
     def fixed_forward(self) -> float:
         loss = ctypes.c_double(0.0)

@@ -20,7 +20,7 @@ class FixedGridProblem:
     """One walled grid, a fixed time step, gauges and observations."""
 
     def __init__(self, nx, ny, L, dt, n_steps, ckpt_every, gauge_ij, obs, eta2=-200.0, dry_tol=1e-3,
-                 stream=None):
+                 stream=None, keep_edge_data=True):
         self.nx, self.ny, self.L, self.dt = nx, ny, L, dt
         self.n_steps, self.ckpt_every = n_steps, ckpt_every
         self.gauge_ij = np.asarray(gauge_ij, dtype=np.int32)
@@ -28,6 +28,7 @@ class FixedGridProblem:
         self.eta2 = eta2
         cfg = _pkg.Config(M=2, dry_tol=dry_tol, order=1, max_levels=1)
         self.H = _pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, nx, ny)], stream=stream)
+        self.H.adjoint_keep_edge_data(keep_edge_data)
 
     def initial_state(self, eta1, B):
         h2 = self.eta2 - B

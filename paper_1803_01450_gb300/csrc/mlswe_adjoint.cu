@@ -35,12 +35,15 @@ constexpr int kAdjThreads = 128;
 // Adjoint of one first-order sweep over the tiles of the level. state: input of the
 // forward sweep (pitched like the level); lam_out: cotangent of its output; lam_in:
 // cotangent of its input (written); gB: bathymetry cotangent (accumulated).
-template <int M, int DIR>
+// LOADED (M = 2): the forward records of the coupled edges (FwdRec, one plane of eplane
+// doubles per field, indexed like the sweep kernel's STORE output) are read from est instead
+// of being rebuilt.
+template <int M, int DIR, bool LOADED>
 __global__ void __launch_bounds__(kAdjThreads, 2)
 adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
                      const int* __restrict__ n_items_dev, const double* __restrict__ state,
                      const double* __restrict__ lam_out, double* __restrict__ lam_in, double* __restrict__ gB,
-                     unsigned int* __restrict__ status) {
+                     unsigned int* __restrict__ status, const double* __restrict__ est, long long eplane) {
   using R = Rec<M>;
   constexpr int RN = ARec<M>::N;
   constexpr int F = 3 * M;
@@ -141,8 +144,22 @@ adjoint_sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Swe
         apb[f] = lamo[f * kMaxCells + cr];
       }
       double qLb[6] = {0, 0, 0, 0, 0, 0}, qRb[6] = {0, 0, 0, 0, 0, 0}, BLb = 0.0, BRb = 0.0;
-      const bool ok = (M == 2) ? edge_vjp_2(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb)
-                               : edge_vjp_1(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb);
+      bool ok;
+      if constexpr (LOADED && M == 2) {
+        ok = wetb[cl] == 3 && wetb[cr] == 3;
+        if (ok) {
+          // edge e of the tile lies left of (below) cell i0 + e (j0 + e) of its line
+          const size_t gi = DIR == 0 ? (size_t)(item.j0 + l) * (NX + 1) + (item.i0 + e)
+                                     : (size_t)(item.j0 + e) * NX + (item.i0 + l);
+          double Fr[FwdRec::N];
+#pragma unroll
+          for (int k = 0; k < FwdRec::N; ++k) Fr[k] = est[(size_t)k * eplane + gi];
+          edge_rev_2(P, cL, cR, Fr, amb, apb, qLb, qRb, BLb, BRb);
+        }
+      } else {
+        ok = (M == 2) ? edge_vjp_2(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb)
+                      : edge_vjp_1(P, cL, cR, wetb[cl], wetb[cr], amb, apb, qLb, qRb, BLb, BRb);
+      }
       if (!ok) atomicOr(status, 4u);
       const int es = aeslot<DIR>(l, e, len, nl);
 #pragma unroll
@@ -202,30 +219,42 @@ static size_t adjoint_smem_bytes(int M) {
   return (size_t)rn * kMaxCells * 8 + (size_t)F * kMaxCells * 8 + (size_t)ne * kMaxEdges * 8 + kMaxCells;
 }
 
-template <int M, int DIR>
+template <int M, int DIR, bool LOADED>
 static cudaError_t launch_adjoint_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items, const int* n,
                                     int grid, const double* state, const double* lam_out, double* lam_in, double* gB,
-                                    unsigned int* status, cudaStream_t st) {
+                                    unsigned int* status, cudaStream_t st, const double* est, long long eplane) {
   const size_t sm = adjoint_smem_bytes(M);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(adjoint_sweep_kernel<M, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(adjoint_sweep_kernel<M, DIR, LOADED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  adjoint_sweep_kernel<M, DIR><<<grid, kAdjThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in, gB, status);
+  adjoint_sweep_kernel<M, DIR, LOADED><<<grid, kAdjThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in,
+                                                                       gB, status, est, eplane);
   return cudaGetLastError();
 }
 
+// est: forward records of the swept step (M = 2 only), or null to rebuild them per edge.
 static cudaError_t launch_adjoint_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                         const int* n, int grid, const double* state, const double* lam_out,
-                                        double* lam_in, double* gB, unsigned int* status, cudaStream_t st) {
+                                        double* lam_in, double* gB, unsigned int* status, cudaStream_t st,
+                                        const double* est = nullptr, long long eplane = 0) {
   if (P.M == 1)
-    return dir == 0 ? launch_adjoint_t<1, 0>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st)
-                    : launch_adjoint_t<1, 1>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st);
-  return dir == 0 ? launch_adjoint_t<2, 0>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st)
-                  : launch_adjoint_t<2, 1>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st);
+    return dir == 0 ? launch_adjoint_t<1, 0, false>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                    nullptr, 0)
+                    : launch_adjoint_t<1, 1, false>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                    nullptr, 0);
+  if (est != nullptr)
+    return dir == 0 ? launch_adjoint_t<2, 0, true>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                   est, eplane)
+                    : launch_adjoint_t<2, 1, true>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                   est, eplane);
+  return dir == 0 ? launch_adjoint_t<2, 0, false>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                  nullptr, 0)
+                  : launch_adjoint_t<2, 1, false>(P, descs, items, n, grid, state, lam_out, lam_in, gB, status, st,
+                                                  nullptr, 0);
 }
 
 // Gauge misfit of one state: loss += sum_g (eta_1 - obs_g)^2, summed in gauge order by one
@@ -277,6 +306,11 @@ struct Adjoint {
   int tile[2][2] = {{0, 0}, {0, 0}};         // chosen (len, lines) per direction
   bool forward_done = false;
   bool last_kept = false;      // the slots hold the last segment as the forward pass left it
+  // Per-edge forward records (FwdRec) of every recomputed step, M = 2: [ckpt][2 sweeps][N]
+  // planes of eplane doubles; null when switched off or when the memory was not available.
+  bool keep_edges = true;
+  double* estore = nullptr;
+  long long eplane = 0;
 };
 
 }  // namespace
@@ -410,7 +444,14 @@ static mlswe_status adj_autotune(mlswe_hier* H, Adjoint* A) {
   return MLSWE_OK;
 }
 
-// Step a of the segment being recomputed (both sweeps, nothing recorded).
+// Forward records of sweep dir of step a of a segment, or null.
+static double* adj_edge_records(Adjoint* A, int a, int dir) {
+  if (!A->estore) return nullptr;
+  return A->estore + ((size_t)(2 * a + dir) * FwdRec::N) * (size_t)A->eplane;
+}
+
+// Step a of the segment being recomputed (both sweeps, no fluxes recorded; the per-edge
+// forward records are kept when the store is on).
 static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
   for (int dir = 0; dir < 2; ++dir) {
     Hier::WorkList& W = H->wl[dir];
@@ -418,7 +459,7 @@ static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
     int tok;
     timer_begin(H, KC_ADJOINT, &tok);
     ACUDA(H, launch_sweep(dir, H->dp, A->descs + a, W.d_items, W.d_count, ctas * H->num_sms, 0, 0, H->d_smax,
-                          nullptr, H->st, ctas));
+                          nullptr, H->st, ctas, adj_edge_records(A, a, dir), A->eplane));
     timer_end(H, tok);
   }
   return MLSWE_OK;
@@ -456,6 +497,18 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
   if (A->obs) dev_free(h, A->obs);
   A->gij = (int*)dev_alloc(h, std::max(1, 2 * n_gauges) * sizeof(int));
   A->obs = grab(std::max<size_t>(1, (size_t)n_steps * n_gauges) * 8);
+  // per-edge forward records of a segment (two-layer only); without the memory the
+  // transposed sweeps rebuild them
+  if (A->estore) dev_free(h, A->estore);
+  A->estore = nullptr;
+  A->eplane = 0;
+  if (A->keep_edges && h->cfg.M == 2) {
+    // one spare slot per plane takes the records of tile-halo edges (see sweep_kernel)
+    const long long plane = ((long long)(V.NX + 1) * (V.NY + 1) + 1 + 31) / 32 * 32;
+    A->estore = grab((size_t)ckpt_every * 2 * FwdRec::N * (size_t)plane * 8);
+    if (A->estore) A->eplane = plane;
+    cudaGetLastError();  // an allocation failure here is not an error of the call
+  }
   for (double* p : A->ckpts) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
   for (double* p : A->slots) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
   for (double* p : A->qstar) if (!p) return afail(h, MLSWE_ENOMEM, "adjoint_setup: out of memory");
@@ -471,6 +524,15 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
   if (s != MLSWE_OK) return s;
   A->forward_done = false;
   A->last_kept = false;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_adjoint_keep_edge_data(mlswe_h h, int enable) {
+  if (!h) return MLSWE_EINVAL;
+  Adjoint* A = adj_of(h, true);
+  A->keep_edges = enable != 0;
+  A->n_steps = 0;  // takes effect at the next mlswe_adjoint_setup
+  A->forward_done = false;
   return MLSWE_OK;
 }
 
@@ -557,11 +619,11 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
       // transposed y sweep (on Q* of step n), then transposed x sweep (on Q^n)
       timer_begin(h, KC_ADJOINT, &tok);
       ACUDA(h, launch_adjoint_sweep(1, h->dp, A->descs + a, A->items[1], A->n_items[1], grid, A->qstar[a], A->lam,
-                                    A->lam2, A->gB, h->d_status, h->st));
+                                    A->lam2, A->gB, h->d_status, h->st, adj_edge_records(A, a, 1), A->eplane));
       timer_end(h, tok);
       timer_begin(h, KC_ADJOINT, &tok);
       ACUDA(h, launch_adjoint_sweep(0, h->dp, A->descs + a, A->items[0], A->n_items[0], grid, A->slots[a], A->lam2,
-                                    A->lam, A->gB, h->d_status, h->st));
+                                    A->lam, A->gB, h->d_status, h->st, adj_edge_records(A, a, 0), A->eplane));
       timer_end(h, tok);
     }
   }

@@ -101,17 +101,15 @@ MLSWE_HD void adj_pick(double s, const double* am_b, const double* ap_b, double*
   }
 }
 
-// Coupled two-layer edge. cL, cR: cell records (Rec<2>). am_b, ap_b: cotangents of A-dQ and
-// A+dQ (6 each, (h, hn, ht) per layer). Outputs (accumulated, +=): cotangents of the left and
-// right conserved states qLb[6], qRb[6] and of BL, BR. Returns false if the states are not
-// in the coupled branch (some layer not wet on some side).
-MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR, int wL, int wR,
-                         const double* am_b, const double* ap_b, double* qLb, double* qRb, double& BLb, double& BRb) {
+// Forward part of a coupled two-layer edge (M = 2, both layers wet on both sides): fills the
+// record F (layout FwdRec) with what the reverse part needs. Returns false if the states are
+// not in the coupled branch.
+MLSWE_HD bool edge_fwd_2(const DevParams& P, const double* cL, const double* cR, int wL, int wR, double* F) {
   using R = Rec<2>;
+  using FR = FwdRec;
   if (wL != 3 || wR != 3) return false;
   const double g = P.g, r = P.r;
-  // ---------------- forward recompute ----------------
-  double hb[2], coup[2], d0[2], d1[2], uh[2], vh[2];
+  double hb[2], coup[2], d0[2], d1[2], uh[2];
   for (int m = 0; m < 2; ++m) {
     hb[m] = 0.5 * (cL[3 * m] + cR[3 * m]);
     coup[m] = cR[R::ETA + m] - cL[R::ETA + m];
@@ -120,60 +118,59 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
     d1[m] = (cR[3 * m + 1] * cR[R::UN + 2 * m] - cL[3 * m + 1] * cL[R::UN + 2 * m]) + g * hb[m] * coup[m];
   }
   const double c1 = g * hb[0], c2 = g * hb[1];
-  const double Hs = hb[0] + hb[1];
   // 1/(sqrt hL + sqrt hR) per layer, 1/(hbar_1 + hbar_2), 1/c1 in one division
-  double iS[2], iH, ic1;
   {
-    const double den[4] = {cL[R::SQ] + cR[R::SQ], cL[R::SQ + 1] + cR[R::SQ + 1], Hs, c1};
-    double inv[4];
-    adj_batched_rcp<4>(den, inv);
-    iS[0] = inv[0]; iS[1] = inv[1]; iH = inv[2]; ic1 = inv[3];
+    const double den[4] = {cL[R::SQ] + cR[R::SQ], cL[R::SQ + 1] + cR[R::SQ + 1], hb[0] + hb[1], c1};
+    adj_batched_rcp<4>(den, F + FR::IS0);
   }
-  for (int m = 0; m < 2; ++m) {
-    uh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m] + cR[R::SQ + m] * cR[R::UN + 2 * m]) * iS[m];
-    vh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m + 1] + cR[R::SQ + m] * cR[R::UN + 2 * m + 1]) * iS[m];
-  }
-  const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * iH;
+  for (int m = 0; m < 2; ++m)
+    uh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m] + cR[R::SQ + m] * cR[R::UN + 2 * m]) * F[FR::IS0 + m];
+  const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * F[FR::IH];
   const double dc = c1 - c2;
   const double X = dc * dc + 4.0 * r * c1 * c2;
-  const double idisc = adj_rsqrt(X), disc = X * idisc;
-  const double csum = c1 + c2;
+  F[FR::IDISC] = adj_rsqrt(X);
+  const double disc = X * F[FR::IDISC];
   // mu_+ = (csum + disc)/2; mu_- from mu_+ mu_- = (1 - r) c1 c2 (no cancellation)
-  const double mup = 0.5 * (csum + disc);
+  const double mup = 0.5 * ((c1 + c2) + disc);
   const double isp = adj_rsqrt(mup), sp = mup * isp;
   const double mum = ((1.0 - r) * c1 * c2) * (isp * isp);
   const double ism = adj_rsqrt(mum), sm = mum * ism;
-  double lam0[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+  F[FR::ISP] = isp;
+  F[FR::ISM] = ism;
+  double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+  for (int p = 0; p < 4; ++p) F[FR::LAM0 + p] = lam[p];
   const double du = uh[0] - uh[1];
   const bool newton = !(du * du >= (1.0 - r) * g * (hb[0] + hb[1])) && P.eigen == 0;
-  double lam1[4], lam[4];
-  double iD[2][4];  // 1/P'(lambda) at each Newton step, reused in reverse
+  F[FR::NEWTON] = newton ? 1.0 : 0.0;
   const double rc = r * c1 * c2;
-  for (int p = 0; p < 4; ++p) lam[p] = lam0[p];
   if (newton) {
     for (int it = 0; it < 2; ++it) {
       double Pl[4], D[4];
       for (int p = 0; p < 4; ++p) {
-        if (it == 1) lam1[p] = lam[p];
+        if (it == 1) F[FR::LAM1 + p] = lam[p];
         const double a1 = lam[p] - uh[0], a2 = lam[p] - uh[1];
         const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
         Pl[p] = f1 * f2 - rc;
         D[p] = 2.0 * (a1 * f2 + a2 * f1);
       }
-      adj_batched_rcp<4>(D, iD[it]);
-      for (int p = 0; p < 4; ++p) lam[p] = lam[p] - Pl[p] * iD[it][p];
+      double* iD = F + (it == 0 ? FR::ID0 : FR::ID1);
+      adj_batched_rcp<4>(D, iD);
+      for (int p = 0; p < 4; ++p) lam[p] = lam[p] - Pl[p] * iD[p];
     }
   } else {
-    for (int p = 0; p < 4; ++p) lam1[p] = lam[p];
+    for (int p = 0; p < 4; ++p) {
+      F[FR::LAM1 + p] = lam[p];
+      F[FR::ID0 + p] = 0.0;
+      F[FR::ID1 + p] = 0.0;
+    }
   }
-  double al[4], tt[4];
-  for (int p = 0; p < 4; ++p) { tt[p] = lam[p] - uh[0]; al[p] = (tt[p] * tt[p] - c1) * ic1; }
+  for (int p = 0; p < 4; ++p) F[FR::LAM + p] = lam[p];
   // wave strengths: Vandermonde form (see mlswe_device.cuh)
   const double p1 = -2.0 * uh[0], p0 = uh[0] * uh[0] - c1;
   const double m0 = d0[0], m1 = d1[0];
   const double m2 = c1 * d0[1] - p1 * m1 - p0 * m0;
   const double m3 = c1 * d1[1] - p1 * m2 - p0 * m1;
-  double e1[4], e2[4], e3[4], iden[4], beta[4];
+  double e1[4], e2[4], e3[4];
   {
     double den[4];
     for (int p = 0; p < 4; ++p) {
@@ -183,9 +180,62 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
       e3[p] = lam[qa] * lam[qb] * lam[qc];
       den[p] = (lam[p] - lam[qa]) * (lam[p] - lam[qb]) * (lam[p] - lam[qc]);
     }
-    adj_batched_rcp<4>(den, iden);
+    adj_batched_rcp<4>(den, F + FR::IDEN);
   }
-  for (int p = 0; p < 4; ++p) beta[p] = (m3 - e1[p] * m2 + e2[p] * m1 - e3[p] * m0) * iden[p];
+  for (int p = 0; p < 4; ++p)
+    F[FR::BETA + p] = (m3 - e1[p] * m2 + e2[p] * m1 - e3[p] * m0) * F[FR::IDEN + p];
+  return true;
+}
+
+// Reverse part of a coupled two-layer edge from its forward record F (filled by edge_fwd_2,
+// or by the sweep kernel while it recomputed the step). cL, cR: cell records (ARec<2>).
+// am_b, ap_b: cotangents of A-dQ and A+dQ (6 each, (h, hn, ht) per layer). Outputs
+// (accumulated, +=): cotangents of the left and right conserved states qLb[6], qRb[6] and
+// of BL, BR. The cheap forward quantities (Roe averages, flux jumps, alpha_p, the elementary
+// symmetric polynomials of the other three eigenvalues) are rebuilt here.
+MLSWE_HD void edge_rev_2(const DevParams& P, const double* cL, const double* cR, const double* F,
+                         const double* am_b, const double* ap_b, double* qLb, double* qRb, double& BLb,
+                         double& BRb) {
+  using R = Rec<2>;
+  using FR = FwdRec;
+  const double g = P.g, r = P.r;
+  double hb[2], coup[2], d0[2], uh[2], vh[2], iS[2];
+  for (int m = 0; m < 2; ++m) {
+    hb[m] = 0.5 * (cL[3 * m] + cR[3 * m]);
+    coup[m] = cR[R::ETA + m] - cL[R::ETA + m];
+    if (m == 1) coup[m] += r * (cR[0] - cL[0]);
+    d0[m] = cR[3 * m + 1] - cL[3 * m + 1];
+    iS[m] = F[FR::IS0 + m];
+    uh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m] + cR[R::SQ + m] * cR[R::UN + 2 * m]) * iS[m];
+    vh[m] = (cL[R::SQ + m] * cL[R::UN + 2 * m + 1] + cR[R::SQ + m] * cR[R::UN + 2 * m + 1]) * iS[m];
+  }
+  const double c1 = g * hb[0], c2 = g * hb[1];
+  const double iH = F[FR::IH], ic1 = F[FR::IC1], idisc = F[FR::IDISC], isp = F[FR::ISP], ism = F[FR::ISM];
+  const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * iH;
+  const double dc = c1 - c2;
+  const bool newton = F[FR::NEWTON] != 0.0;
+  const double rc = r * c1 * c2;
+  double lam[4], beta[4], iden[4], al[4], tt[4], e1[4], e2[4], e3[4];
+  for (int p = 0; p < 4; ++p) {
+    lam[p] = F[FR::LAM + p];
+    beta[p] = F[FR::BETA + p];
+    iden[p] = F[FR::IDEN + p];
+    tt[p] = lam[p] - uh[0];
+    al[p] = (tt[p] * tt[p] - c1) * ic1;
+  }
+  // elementary symmetric polynomials of the three eigenvalues other than lam_p, from those of
+  // all four: e1 = S1 - l, e2 = S2 - l e1, e3 = S3 - l e2
+  {
+    const double s01 = lam[0] + lam[1], s23 = lam[2] + lam[3];
+    const double q01 = lam[0] * lam[1], q23 = lam[2] * lam[3];
+    const double S1 = s01 + s23, S2 = q01 + q23 + s01 * s23, S3 = q01 * s23 + q23 * s01;
+    for (int p = 0; p < 4; ++p) {
+      e1[p] = S1 - lam[p];
+      e2[p] = S2 - lam[p] * e1[p];
+      e3[p] = S3 - lam[p] * e2[p];
+    }
+  }
+  const double p1 = -2.0 * uh[0], p0 = uh[0] * uh[0] - c1;
   // ---------------- reverse ----------------
   double lamb[4] = {0, 0, 0, 0}, alb[4] = {0, 0, 0, 0}, betab[4];
   double vhb[2] = {0, 0}, uhb[2] = {0, 0}, d0b[2] = {0, 0}, d1b[2] = {0, 0}, d2b[2] = {0, 0};
@@ -236,15 +286,16 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
     const double rc1 = r * c1, rc2 = r * c2;
     for (int it = 1; it >= 0; --it) {
       for (int p = 0; p < 4; ++p) {
-        const double l = it == 1 ? lam1[p] : lam0[p];
+        const double l = F[(it == 1 ? FR::LAM1 : FR::LAM0) + p];
         const double a1 = l - uh[0], a2 = l - uh[1];
         const double a12 = a1 * a2;
         const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
         const double Pl = f1 * f2 - rc;
         const double Dl = 2.0 * ((f1 + f2) + 4.0 * a12);
         const double lb = lamb[p];
-        const double w = lb * iD[it][p];
-        const double v = (w * Pl) * iD[it][p];
+        const double iD = F[(it == 1 ? FR::ID1 : FR::ID0) + p];
+        const double w = lb * iD;
+        const double v = (w * Pl) * iD;
         const double lnew = v * Dl;
         // P_u1 = -2 a1 f2, D_u1 = -2 (f2 + 2 a1 a2); P_c1 = -(f2 + r c2), D_c1 = -2 a2; P_c2, D_c2 alike
         const double gu0 = 2.0 * (v * (f2 + 2.0 * a12) - (w * a1) * f2);
@@ -313,6 +364,15 @@ MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR,
       qb[3 * m + 2] += utb[s][m] * ih;
     }
   }
+}
+
+// Coupled two-layer edge, forward and reverse in one call. Returns false if the states are
+// not in the coupled branch (some layer not wet on some side).
+MLSWE_HD bool edge_vjp_2(const DevParams& P, const double* cL, const double* cR, int wL, int wR,
+                         const double* am_b, const double* ap_b, double* qLb, double* qRb, double& BLb, double& BRb) {
+  double F[FwdRec::N];
+  if (!edge_fwd_2(P, cL, cR, wL, wR, F)) return false;
+  edge_rev_2(P, cL, cR, F, am_b, ap_b, qLb, qRb, BLb, BRb);
   return true;
 }
 

@@ -167,6 +167,18 @@ struct WRec {  // shared-memory layout of EdgeW
                        N = 11 * M;
 };
 
+// Per-edge record of a coupled two-layer edge that the adjoint's reverse pass reads instead
+// of rebuilding it (field offsets; each field is one plane over the edges of a sweep):
+// reciprocals of the Roe weights (sqrt hL + sqrt hR per layer), of hbar_1 + hbar_2 and of
+// c1 = g hbar_1; reciprocal square roots of the discriminant and of mu_+, mu_-; the
+// eigenvalue guesses, the iterate after the first Newton step and the final eigenvalues;
+// 1/P'(lambda) of both Newton steps; reciprocals of prod_{q != p}(lambda_p - lambda_q); the
+// wave strengths beta_p; 1.0 if the Newton steps ran, else 0.0.
+struct FwdRec {
+  static constexpr int IS0 = 0, IS1 = 1, IH = 2, IC1 = 3, IDISC = 4, ISP = 5, ISM = 6, LAM0 = 7, LAM1 = 11,
+                       LAM = 15, ID0 = 19, ID1 = 23, IDEN = 27, BETA = 31, NEWTON = 35, N = 36;
+};
+
 // Layer of acoustic slot p in the per-layer (decoupled) branch.
 template <int M>
 __device__ __forceinline__ int layer_of_slot(int p) {
@@ -193,9 +205,16 @@ __device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, d
 }
 
 // Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
-template <int M>
+// STORE: a coupled two-layer edge also writes its FwdRec record to st (field k at
+// st[k * sstride]). The stores are unconditional (st must be valid), so the arithmetic is
+// compiled in the same basic blocks, and therefore rounds the same, as without STORE.
+template <int M, bool STORE = false>
 __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL, const double* cR,
-                                           int wL, int wR, EdgeW<M>& W, int& lost) {
+                                           int wL, int wR, EdgeW<M>& W, int& lost, double* st = nullptr,
+                                           long long sstride = 0) {
+  auto put = [&](int k, double v) {
+    if constexpr (STORE) st[(long long)k * sstride] = v;
+  };
   using R = Rec<M>;
   const double g = P.g;
 #pragma unroll
@@ -223,6 +242,10 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     // one reciprocal for the Roe weights of both layers, the depth sum and c1
     double den4[4] = {cL[R::SQ] + cR[R::SQ], cL[R::SQ + 1] + cR[R::SQ + 1], hb[0] + hb[1], c1}, inv4[4];
     batched_reciprocal<4>(den4, inv4);
+    put(FwdRec::IS0, inv4[0]);
+    put(FwdRec::IS1, inv4[1]);
+    put(FwdRec::IH, inv4[2]);
+    put(FwdRec::IC1, inv4[3]);
     double uh[2], vh[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
@@ -233,22 +256,35 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * inv4[2];
     const double dc = c1 - c2;
     const double X = dc * dc + 4.0 * P.r * c1 * c2;
-    const double disc = X * rsqrt(X);
+    const double rX = rsqrt(X);
+    const double disc = X * rX;
     const double csum = c1 + c2;
     // mu_+ mu_- = (1 - r) c1 c2: mu_- without the cancellation of (csum - disc)/2
     const double mup = 0.5 * (csum + disc);
     const double tp = rsqrt(mup);
     const double sp = mup * tp;
     const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
-    const double sm = mum * rsqrt(mum);
+    const double rmum = rsqrt(mum);
+    const double sm = mum * rmum;
     double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+    put(FwdRec::IDISC, rX);
+    put(FwdRec::ISP, tp);
+    put(FwdRec::ISM, rmum);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) put(FwdRec::LAM0 + p, lam[p]);
     const double du = uh[0] - uh[1];
     const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
     lost += lst ? 1 : 0;
-    if (!lst && P.eigen == 0) {
+    const bool newton = !lst && P.eigen == 0;
+    put(FwdRec::NEWTON, newton ? 1.0 : 0.0);
+    if (newton) {
       const double rc = P.r * c1 * c2;
 #pragma unroll
       for (int it = 0; it < 2; ++it) {
+        if (it == 1) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) put(FwdRec::LAM1 + p, lam[p]);
+        }
         double Pl[4], dP[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -261,12 +297,23 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
         const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
         const double inv = 0.5 * rcp(p01 * p23);
         const double i01 = inv * p23, i23 = inv * p01;
-        lam[0] -= Pl[0] * (i01 * dP[1]);
-        lam[1] -= Pl[1] * (i01 * dP[0]);
-        lam[2] -= Pl[2] * (i23 * dP[3]);
-        lam[3] -= Pl[3] * (i23 * dP[2]);
+        const double q[4] = {i01 * dP[1], i01 * dP[0], i23 * dP[3], i23 * dP[2]};  // 1/P'(lambda_p)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          lam[p] -= Pl[p] * q[p];
+          put((it == 0 ? FwdRec::ID0 : FwdRec::ID1) + p, q[p]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        put(FwdRec::LAM1 + p, lam[p]);
+        put(FwdRec::ID0 + p, 0.0);
+        put(FwdRec::ID1 + p, 0.0);
       }
     }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) put(FwdRec::LAM + p, lam[p]);
     // Wave strengths. With a(l) = (l^2 + p1 l + p0) / c1 (p1 = -2 u1, p0 = u1^2 - c1) the rows
     // of R beta = delta give the power moments m_k = sum_p beta_p l_p^k, k = 0..3, and
     // beta_p follows from the Lagrange basis of the four eigenvalues.
@@ -301,6 +348,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       const double k0 = lam[p] * k1 - S3;
       const double num = m3 + k2 * m2 + k1 * m1 + k0 * m0;
       const double beta = num * iden[p];
+      put(FwdRec::IDEN + p, iden[p]);
+      put(FwdRec::BETA + p, beta);
       const double al = lam[p] - uh[0];
       const double alpha = (al * al - c1) * ic1;
       W.a[p] = beta;

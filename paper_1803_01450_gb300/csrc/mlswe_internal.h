@@ -175,7 +175,8 @@ cudaError_t launch_gauges(int M, const LevelDesc* descs, const int* parity_of_de
                           double* out, cudaStream_t st);
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                          const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm = 1);
+                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm = 1, double* est = nullptr,
+                         long long eplane = 0);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
 void adjoint_release(Hier* H);

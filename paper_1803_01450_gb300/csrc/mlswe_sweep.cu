@@ -48,11 +48,16 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* d
 
 // MINB: CTAs resident per SM the build targets (1: up to 255 registers per thread; 2: at
 // most 128, 16 warps per SM to hide FP64 latency). The autotuner picks per level.
-template <int M, int DIR, int MINB>
+// STORE (M = 2, for the adjoint's recomputation): every coupled edge between the cells of a
+// tile and their first neighbours also writes its FwdRec record to est, one plane of
+// eplane doubles per field, at the edge's index on the level (x edges: j (NX + 1) + i for
+// the edge left of cell i; y edges: j NX + i for the edge below cell j); the other coupled
+// edges of the tile write to slot eplane - 1, which eplane > (NX + 1) (NY + 1) keeps spare.
+template <int M, int DIR, int MINB, bool STORE>
 __global__ void __launch_bounds__(kThreads, MINB)
 sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
              const int* __restrict__ n_items_dev, int parity, int record, unsigned long long* smax_bits,
-             unsigned int* lost_count) {
+             unsigned int* lost_count, double* __restrict__ est, long long eplane) {
   using R = Rec<M>;
   using WR = WRec<M>;
   constexpr int F = 3 * M;
@@ -146,7 +151,15 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
       EdgeW<M> W;
       int lst = 0;
-      solve_edge<M>(P, cL, cR, wetb[cl], wetb[cr], W, lst);
+      // halo edges write their record to the spare last slot of each plane
+      double* st = nullptr;
+      if (STORE) {
+        st = est + (eplane - 1);
+        if (e >= 1 && e <= len + 1)
+          st = DIR == 0 ? est + (size_t)(item.j0 + l) * (NX + 1) + (item.i0 - 1 + e)
+                        : est + (size_t)(item.j0 - 1 + e) * NX + (item.i0 + l);
+      }
+      solve_edge<M, STORE>(P, cL, cR, wetb[cl], wetb[cr], W, lst, st, eplane);
       const int es = eslot<DIR>(l, e, len, nl);
 #pragma unroll
       for (int p = 0; p < 2 * M; ++p) {
@@ -372,45 +385,56 @@ size_t sweep_smem_bytes(int M) {
   return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
 }
 
-template <int M, int DIR, int MINB>
+template <int M, int DIR, int MINB, bool STORE>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                   const int* n_items_dev, int grid, int parity, int record,
-                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st) {
+                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
+                                  double* est, long long eplane) {
   const size_t sm = sweep_smem_bytes(M);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sweep_kernel<M, DIR, MINB><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record, smax_bits,
-                                                         lost_count);
+  sweep_kernel<M, DIR, MINB, STORE><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record,
+                                                                smax_bits, lost_count, est, eplane);
   return cudaGetLastError();
 }
 
 template <int M, int DIR>
 static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                   const int* n_items_dev, int grid, int parity, int record,
-                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st) {
-  return ctas >= 2 ? launch_sweep_t<M, DIR, 2>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
-                                               lost_count, st)
-                   : launch_sweep_t<M, DIR, 1>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
-                                               lost_count, st);
+                                  unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
+                                  double* est, long long eplane) {
+  if constexpr (M == 2) {
+    if (est != nullptr)
+      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, true>(P, descs, items, n_items_dev, grid, parity, record,
+                                                          smax_bits, lost_count, st, est, eplane)
+                       : launch_sweep_t<M, DIR, 1, true>(P, descs, items, n_items_dev, grid, parity, record,
+                                                          smax_bits, lost_count, st, est, eplane);
+  }
+  return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                       smax_bits, lost_count, st, nullptr, 0)
+                   : launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                       smax_bits, lost_count, st, nullptr, 0);
 }
 
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                          const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm) {
+                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm, double* est, long long eplane) {
   if (grid <= 0) return cudaSuccess;
   const int c = ctas_per_sm;
   if (P.M == 1)
-    return dir == 0
-               ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
-               : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
-  return dir == 0
-             ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st)
-             : launch_sweep_m<2, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits, lost_count, st);
+    return dir == 0 ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0)
+                    : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0);
+  return dir == 0 ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                         lost_count, st, est, eplane)
+                  : launch_sweep_m<2, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                         lost_count, st, est, eplane);
 }
 
 }  // namespace mlswe

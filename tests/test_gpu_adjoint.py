@@ -25,10 +25,11 @@ def _setup(n=48, steps=12, n_g=8, seed=3):
     return dict(n=n, L=L, B=B, eta1=eta1, gauges=gauges, dx=dx, dt=dt, P=P, steps=steps, obs=obs)
 
 
-def _gpu_grad(pkg, s, ckpt):
+def _gpu_grad(pkg, s, ckpt, keep_edge_data=True):
     import torch
     from paper_1803_01450_gb300.adjoint import FixedGridProblem
-    prob = FixedGridProblem(s["n"], s["n"], s["L"], s["dt"], s["steps"], ckpt, s["gauges"], s["obs"])
+    prob = FixedGridProblem(s["n"], s["n"], s["L"], s["dt"], s["steps"], ckpt, s["gauges"], s["obs"],
+                            keep_edge_data=keep_edge_data)
     J = prob.forward(s["eta1"], s["B"])
     dq0, dB = prob.backward(torch.device("cuda", 0))
     out = (J, dq0.cpu().numpy(), dB.cpu().numpy())
@@ -36,9 +37,12 @@ def _gpu_grad(pkg, s, ckpt):
     return out
 
 
-def test_gradient_matches_oracle_adjoint(mlswe_lib):
+@pytest.mark.parametrize("keep_edge_data", [True, False])
+def test_gradient_matches_oracle_adjoint(mlswe_lib, keep_edge_data):
+    """Both forms of the transposed sweep: reading the per-edge forward records the
+    recomputation kept, and rebuilding them per edge."""
     s = _setup()
-    J, dq0, dB = _gpu_grad(mlswe_lib, s, ckpt=5)
+    J, dq0, dB = _gpu_grad(mlswe_lib, s, ckpt=5, keep_edge_data=keep_edge_data)
     q0 = OA.initial_state(s["eta1"], s["B"])
     Jo, dq0o, dBo = OA.gradient(s["P"], q0, s["B"], s["dx"], s["dx"], s["dt"], s["steps"], s["gauges"], s["obs"])
     assert abs(J - Jo) <= 1e-12 * Jo
@@ -46,6 +50,19 @@ def test_gradient_matches_oracle_adjoint(mlswe_lib):
         sc = max(np.abs(dq0o[f]).max(), 1e-300)
         assert np.abs(dq0[f] - dq0o[f]).max() <= 1e-10 * sc, (f, np.abs(dq0[f] - dq0o[f]).max() / sc)
     assert np.abs(dB - dBo).max() <= 1e-10 * np.abs(dBo).max()
+
+
+def test_kept_and_rebuilt_edge_records_agree(mlswe_lib):
+    """The two forms differ only in where the forward quantities are computed (the sweep
+    kernel's arithmetic or the VJP's), so the gradients agree to rounding."""
+    s = _setup(n=40, steps=8)
+    a = _gpu_grad(mlswe_lib, s, ckpt=4, keep_edge_data=True)
+    b = _gpu_grad(mlswe_lib, s, ckpt=4, keep_edge_data=False)
+    assert a[0] == b[0]  # the forward pass is the same
+    for f in range(6):
+        sc = max(np.abs(b[1][f]).max(), 1e-300)
+        assert np.abs(a[1][f] - b[1][f]).max() <= 1e-12 * sc
+    assert np.abs(a[2] - b[2]).max() <= 1e-12 * np.abs(b[2]).max()
 
 
 def test_checkpoint_spacing_does_not_change_gradient(mlswe_lib):
@@ -81,3 +98,25 @@ def test_gradient_matches_central_fd_of_gpu_forward(mlswe_lib):
         ad = float(np.sum(ge * de) + np.sum(gB * dB))
         assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
     prob.close()
+
+
+def test_recording_sweep_reproduces_plain_steps(mlswe_lib):
+    """With the per-edge records kept, the forward pass steps its last segment with the
+    recording form of the sweep kernel; its state must equal plain level steps bit for bit
+    (the recorded steps are the ones the backward pass differentiates)."""
+    s = _setup(n=32, steps=6)
+    from paper_1803_01450_gb300.adjoint import FixedGridProblem
+    prob = FixedGridProblem(s["n"], s["n"], s["L"], s["dt"], s["steps"], s["steps"], s["gauges"], s["obs"],
+                            keep_edge_data=True)
+    prob.forward(s["eta1"], s["B"])
+    q_rec = prob.H.get_state(0, 0)
+    prob.close()
+    cfg = mlswe_lib.Config(M=2, dry_tol=1e-3, order=1, max_levels=1)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, s["L"], s["L"], s["n"], s["n"])])
+    H.set_bathymetry(0, s["B"])
+    H.set_state(0, 0, OA.initial_state(s["eta1"], s["B"]))
+    H.set_dt(0, s["dt"])
+    for _ in range(s["steps"]):
+        H.step_level(0)
+    assert np.array_equal(H.get_state(0, 0), q_rec)
+    H.close()
