@@ -319,12 +319,14 @@ def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
             "forward_lcups": n * n * M_LAYERS * steps / (fwd * 1e-3), "loss": loss}
 
 
-def run_adjoint_only():
+def run_only(name):
     import torch
     import paper_1803_01450_gb300 as pkg
     pkg.build()
     stream = torch.cuda.Stream()
-    print(json.dumps({"adjoint": bench_adjoint(pkg, torch, stream)}), flush=True)
+    fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint}[name]
+    key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint"}[name]
+    print(json.dumps({key: fn(pkg, torch, stream)}), flush=True)
 
 
 def run_gpu(args):
@@ -440,11 +442,11 @@ def main():
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
-    ap.add_argument("--adjoint-only", action="store_true",
-                    help="print only the adjoint figure (a short command for profiling the adjoint kernels)")
+    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint"],
+                    help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()
-    if args.adjoint_only:
-        run_adjoint_only()
+    if args.only:
+        run_only(args.only)
     elif args.impl == "reference":
         run_reference(args)
     else:

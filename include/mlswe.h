@@ -210,11 +210,13 @@ mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
 
-/* Launch configuration of the sweep kernels (not in the paper): tile of `len`
- * cells along the sweep direction times `lines` lines (x sweep dir = 0: rows;
- * y sweep dir = 1: columns), with lines * (len + 3) <= 256 and len >= 4, and
- * CTAs per SM of the persistent grid (1 or 2). EINVAL for shapes out of range.
- * Default: 125 x 2 with 2 CTAs per SM in both directions. */
+/* Launch configuration of the sweep kernels (not in the paper): tiles of at
+ * most `len` cells along the sweep direction (each patch's extent is split into
+ * equal parts) times at least `lines` lines (x sweep dir = 0: rows; y sweep
+ * dir = 1: columns; a tile takes as many lines, up to 32, as fill 256 edges,
+ * lines * (len + 3) <= 256), with len >= 4, and CTAs per SM of the persistent
+ * grid (1 or 2). EINVAL for shapes out of range. Results do not depend on the
+ * tiles. Default: 125 x 2 with 2 CTAs per SM in both directions. */
 mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_per_sm);
 
 /* Discrete adjoint of the fixed-grid step (not written out in the paper; the

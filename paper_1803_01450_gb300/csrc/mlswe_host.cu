@@ -134,6 +134,20 @@ static bool valid_member_level(Hier* H, int member, int level) {
   return H && member >= 0 && member < H->n_members && level >= 0 && level < H->L;
 }
 
+// Tile of a patch for the sweeps: `len` cells along the sweep times as many lines as fill
+// kMaxEdges edges (at least ts.lines, at most 32), so narrow patches still give every thread
+// an edge. len is ts.len on patches at least twice that long (a shorter last tile), else the
+// patch extent split into equal parts of at most ts.len cells.
+static void tile_dims(const TileShape& ts, int extent, int* len, int* lines) {
+  if (extent >= 2 * ts.len) {
+    *len = ts.len;
+  } else {
+    const int parts = (extent + ts.len - 1) / ts.len;
+    *len = (extent + parts - 1) / parts;
+  }
+  *lines = std::max(ts.lines, std::min(32, kMaxEdges / (*len + 3)));
+}
+
 // Sweep work list of one level: tiles over every patch of every member, grouped by patch.
 static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out, std::vector<int>& patch_off) {
   out.clear();
@@ -144,6 +158,8 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
     const int desc = H->desc_index(m, level);
     for (const Box& b : V.patches) {
       patch_off.push_back((int)out.size());
+      int tl, tn;
+      tile_dims(ts, dir == 0 ? b.i1 - b.i0 : b.j1 - b.j0, &tl, &tn);
       if (dir == 0) {
         // Rows of the patch, plus (refined levels) the two ghost rows on each side that
         // lie in the domain: the y sweep reads Q* there.
@@ -154,11 +170,11 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
           const bool inter = j >= b.j0 && j < b.j1;
           int jend = inter ? b.j1 : (j < b.j0 ? b.j0 : jhi);
           jend = std::min(jend, jhi);
-          for (int jj = j; jj < jend; jj += ts.lines) {
-            const int nl = std::min(ts.lines, jend - jj);
-            for (int i = b.i0; i < b.i1; i += ts.len) {
+          for (int jj = j; jj < jend; jj += tn) {
+            const int nl = std::min(tn, jend - jj);
+            for (int i = b.i0; i < b.i1; i += tl) {
               SweepItem it;
-              it.desc = desc; it.i0 = i; it.j0 = jj; it.len = std::min(ts.len, b.i1 - i);
+              it.desc = desc; it.i0 = i; it.j0 = jj; it.len = std::min(tl, b.i1 - i);
               it.nlines = nl; it.flags = inter ? 1 : 0;
               out.push_back(it);
             }
@@ -166,11 +182,11 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
           j = jend;
         }
       } else {
-        for (int i = b.i0; i < b.i1; i += ts.lines) {
-          const int nl = std::min(ts.lines, b.i1 - i);
-          for (int j = b.j0; j < b.j1; j += ts.len) {
+        for (int i = b.i0; i < b.i1; i += tn) {
+          const int nl = std::min(tn, b.i1 - i);
+          for (int j = b.j0; j < b.j1; j += tl) {
             SweepItem it;
-            it.desc = desc; it.i0 = i; it.j0 = j; it.len = std::min(ts.len, b.j1 - j);
+            it.desc = desc; it.i0 = i; it.j0 = j; it.len = std::min(tl, b.j1 - j);
             it.nlines = nl; it.flags = 1;
             out.push_back(it);
           }
