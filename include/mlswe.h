@@ -50,7 +50,8 @@ typedef enum {
   MLSWE_ENEGDEPTH = 5,  /* a non-finite value was met in the wave-speed reduction */
   MLSWE_ENESTING = 6,   /* a patch layout violates nesting or overlaps */
   MLSWE_ETIMEOUT = 7,   /* reserved: a bounded device wait gave up */
-  MLSWE_EHYPERB = 8,    /* warning: edges lost hyperbolicity (eigenvalue guesses used there) */
+  MLSWE_EHYPERB = 8,    /* reserved: edges that lost hyperbolicity are counted, not failed
+                           (mlswe_hyperbolicity_losses) */
   MLSWE_EMISSING = 9    /* the CUDA library or device is not available */
 } mlswe_status;
 
@@ -209,6 +210,15 @@ mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
 /* Surface elevations eta_m (Eq. (4)) at n points (host [n][2], physical x, y)
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
+
+/* Number of edges (counted once each, over the interior lines of every sweep
+ * of every level step since the last reset) whose two-layer Roe state had
+ * (u1 - u2)^2 >= (1 - r) g (hbar_1 + hbar_2), where the eigenvalue guesses
+ * were used without the Newton steps (GeoClaw's treatment of a loss of
+ * hyperbolicity, read for the solver the paper cites in Sec. 1). *count
+ * (host) receives the count modulo 2^32; reset = 1 sets it back to zero.
+ * Synchronises the stream. */
+mlswe_status mlswe_hyperbolicity_losses(mlswe_h h, long long* count, int reset);
 
 /* Launch configuration of the sweep kernels (not in the paper): tiles of at
  * most `len` cells along the sweep direction (each patch's extent is split into

@@ -125,6 +125,7 @@ _SIGS = {
     "mlswe_set_execution": [_H, ctypes.c_int, ctypes.c_int],
     "mlswe_adjoint_setup": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _dp],
     "mlswe_adjoint_keep_edge_data": [_H, ctypes.c_int],
+    "mlswe_hyperbolicity_losses": [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
     "mlswe_fixed_forward": [_H, _dp],
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
@@ -334,6 +335,13 @@ class Hierarchy:
         o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
         self._check(self.L.mlswe_adjoint_setup(self.h, n_steps, ckpt_every, len(g), g.ctypes.data_as(_i32p), _d(o)),
                     "adjoint_setup")
+
+    def hyperbolicity_losses(self, reset: bool = True) -> int:
+        """Edges that used the eigenvalue guesses (loss of hyperbolicity) since the last reset."""
+        c = ctypes.c_longlong(0)
+        self._check(self.L.mlswe_hyperbolicity_losses(self.h, ctypes.byref(c), 1 if reset else 0),
+                    "hyperbolicity_losses")
+        return c.value
 
     def adjoint_keep_edge_data(self, enable: bool = True):
         """Keep per-edge forward records of the recomputed steps (default) or rebuild them in

@@ -63,7 +63,8 @@ struct SweepItem {
   int i0, j0;
   int len;
   int nlines;
-  int flags;  // bit 0: interior lines (count CFL, record interface fluxes)
+  int flags;  // bit 0: interior lines (count CFL, record interface fluxes); bit 1: the tile
+              // ends its patch line (its last edge is the patch boundary)
 };
 
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }

@@ -175,7 +175,7 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
             for (int i = b.i0; i < b.i1; i += tl) {
               SweepItem it;
               it.desc = desc; it.i0 = i; it.j0 = jj; it.len = std::min(tl, b.i1 - i);
-              it.nlines = nl; it.flags = inter ? 1 : 0;
+              it.nlines = nl; it.flags = (inter ? 1 : 0) | (i + it.len == b.i1 ? 2 : 0);
               out.push_back(it);
             }
           }
@@ -187,7 +187,7 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
           for (int j = b.j0; j < b.j1; j += tl) {
             SweepItem it;
             it.desc = desc; it.i0 = i; it.j0 = j; it.len = std::min(tl, b.j1 - j);
-            it.nlines = nl; it.flags = 1;
+            it.nlines = nl; it.flags = 1 | (j + it.len == b.j1 ? 2 : 0);
             out.push_back(it);
           }
         }
@@ -499,7 +499,6 @@ mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cf
     if (s != MLSWE_OK) return s;
   }
   CUDA_TRY(h, cudaMemsetAsync(h->d_smax, 0, (size_t)h->n_members * h->L * 16, h->st));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_lost, 0, 4, h->st));
   mlswe_status s = enqueue_level_step(h, level, 1);
   if (s != MLSWE_OK) return s;
   h->dt_ready = false;
@@ -519,6 +518,16 @@ mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_pe
     return fail(h, MLSWE_EINVAL, "set_tiles: shape out of range");
   for (int l = 0; l < h->L; ++l) set_level_shape(h, l, dir, len, lines, ctas_per_sm);
   invalidate_graphs(h);
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_hyperbolicity_losses(mlswe_h h, long long* count, int reset) {
+  if (!h || !count) return fail(h, MLSWE_EINVAL, "hyperbolicity_losses: bad argument");
+  unsigned int c = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&c, h->d_lost, 4, cudaMemcpyDeviceToHost, h->st));
+  if (reset) CUDA_TRY(h, cudaMemsetAsync(h->d_lost, 0, 4, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  *count = (long long)c;
   return MLSWE_OK;
 }
 

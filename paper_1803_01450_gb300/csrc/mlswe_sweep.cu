@@ -184,7 +184,9 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 #pragma unroll
         for (int m = 0; m < M; ++m) sm = umax64(sm, abs_bits(W.us[m]));
         smax = __longlong_as_double((long long)sm);
-        lost += lst;
+        // each edge counted once: the edge after the tile's last cell belongs to the next
+        // tile unless the tile ends the patch line (flag bit 1)
+        if (e <= len || (item.flags & 2)) lost += lst;
       }
     }
     __syncthreads();

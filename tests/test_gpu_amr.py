@@ -301,3 +301,20 @@ def test_gauges_read_finest_level(mlswe_lib):
             h1, h2, B = q[0, j, i], q[3, j, i], Bc[j, i]
         assert eta[k, 1] == B + h2 and eta[k, 0] == (B + h2) + h1
     H.close()
+
+
+def test_empty_refined_level_changes_nothing(mlswe_lib):
+    """A refined level without patches (the batched launches run with empty work lists):
+    coarse steps, time steps and the level-0 state equal those of a one-level hierarchy
+    bit for bit."""
+    w = I.small(50)
+    H2 = _small_amr(mlswe_lib, regrid=0)
+    H1 = _small_amr(mlswe_lib, levels=1, ratios=(), regrid=0)
+    for H in (H1, H2):
+        H.set_state(0, 0, w["q"])
+        H.advance(6)
+    assert H2.get_patches(0, 1).shape[0] == 0
+    assert np.array_equal(H1.get_time()[0], H2.get_time()[0])
+    assert np.array_equal(H1.get_state(0, 0), H2.get_state(0, 0))
+    H1.close()
+    H2.close()

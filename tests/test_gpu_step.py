@@ -150,3 +150,35 @@ def test_full_size_sampled(mlswe_lib, orc):
         sens = np.abs(pert[:, 4, 4] - ref) / np.maximum(scale, 1e-300)
         assert np.all(err < np.maximum(TOL, 10.0 * sens)), (j, i, err, sens)
         assert err[[0, 3]].max() < TOL, (j, i, err)
+
+
+def test_hyperbolicity_loss_branch(mlswe_lib, orc):
+    """A band where the layers shear past each other ((u1 - u2)^2 = 1 above (1 - r) g (h1 + h2)
+    = 0.36) takes the guesses-only branch at its edges: the state matches the oracle and the
+    count of such edges equals the oracle's, each edge counted once."""
+    nx, ny = 48, 40
+    q, B = I.gaussian_random_state(21, 2, nx, ny)
+    band = slice(15, 25)
+    q[1, band] = 0.5 * q[0, band]
+    q[4, band] = -0.5 * q[3, band]
+    dx, dy = 1.0 / nx, 1.0 / ny
+    dts = [0.2 * min(dx, dy) / 4.0] * 3
+    H = _hier(mlswe_lib, 2, nx, ny, (0.0, 0.0, 1.0, 1.0), dry_tol=1e-6)
+    H.set_bathymetry(0, B)
+    H.set_state(0, 0, q)
+    H.hyperbolicity_losses(reset=True)
+    P = orc.params(M=2, dry_tol=1e-6)
+    qo, lost_o = q.copy(), 0
+    for dt in dts:
+        H.step_level(0, dt=dt)
+        qo, _, lost = orc.step_walled(P, qo, B, dx, dy, dt)
+        lost_o += lost
+    lost_g = H.hyperbolicity_losses()
+    assert lost_o > 0 and lost_g == lost_o, (lost_g, lost_o)
+    err = rel_err(H.get_state(0, 0), qo)
+    assert err.max() < TOL, err
+    # no shear, no loss
+    H.set_state(0, 0, I.gaussian_random_state(22, 2, nx, ny)[0])
+    H.step_level(0, dt=dts[0])
+    assert H.hyperbolicity_losses() == 0
+    H.close()
