@@ -211,6 +211,18 @@ mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
 
+/* Time-stepping state of the hierarchy, for checkpoint and resume (not in the
+ * paper): member times, the wave speeds from which the next coarse step takes
+ * its time step (or the pending speeds of a new state), whether that time step
+ * is ready, and the coarse-step counter that schedules regrids, as
+ * n_doubles = n_members * (1 + 3 * max_levels) + 3 doubles (host; speeds are
+ * stored as their bit patterns). EINVAL for another n_doubles. A hierarchy
+ * created with the same configuration and domains, given the same bathymetry,
+ * then the patch layouts and states of every level (mlswe_set_patches,
+ * mlswe_set_state) and last this clock, continues a run bit for bit. */
+mlswe_status mlswe_get_clock(mlswe_h h, double* buf, int n_doubles);
+mlswe_status mlswe_set_clock(mlswe_h h, const double* buf, int n_doubles);
+
 /* Number of edges (counted once each, over the interior lines of every sweep
  * of every level step since the last reset) whose two-layer Roe state had
  * (u1 - u2)^2 >= (1 - r) g (hbar_1 + hbar_2), where the eigenvalue guesses

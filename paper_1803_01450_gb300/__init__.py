@@ -126,6 +126,8 @@ _SIGS = {
     "mlswe_adjoint_setup": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _dp],
     "mlswe_adjoint_keep_edge_data": [_H, ctypes.c_int],
     "mlswe_hyperbolicity_losses": [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
+    "mlswe_get_clock": [_H, _dp, ctypes.c_int],
+    "mlswe_set_clock": [_H, _dp, ctypes.c_int],
     "mlswe_fixed_forward": [_H, _dp],
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
@@ -171,6 +173,22 @@ def _d(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
+def _python_allocator(alloc, free):
+    """Allocator callback from two Python callables: alloc(nbytes) -> device pointer (int;
+    0 or None on failure) and free(pointer)."""
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes)) or None
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        free(ptr)
+
+    return _Allocator(_ALLOC_FN(_alloc), _FREE_FN(_free), None)
+
+
 def _torch_allocator():
     import torch
 
@@ -193,7 +211,9 @@ class Hierarchy:
     """A set of ensemble members, each a hierarchy of refinement levels (C ABI handle)."""
 
     def __init__(self, cfg: Config, domains: Sequence[tuple], stream: Optional[int] = None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, allocator=None):
+        """allocator: optional (alloc, free) pair of callables (alloc(nbytes) -> device pointer
+        or 0, free(pointer)) used instead of torch's caching allocator."""
         self.cfg = cfg
         self.L = lib()
         doms = (_Domain * len(domains))()
@@ -203,7 +223,10 @@ class Hierarchy:
         self._c_cfg = cfg.to_c()
         self._alloc = None
         alloc_ptr = None
-        if use_torch_allocator:
+        if allocator is not None:
+            self._alloc = _python_allocator(*allocator)
+            alloc_ptr = ctypes.byref(self._alloc)
+        elif use_torch_allocator:
             import torch
             if not torch.cuda.is_available():
                 raise MLSWEError(9, "no CUDA device")
@@ -335,6 +358,20 @@ class Hierarchy:
         o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
         self._check(self.L.mlswe_adjoint_setup(self.h, n_steps, ckpt_every, len(g), g.ctypes.data_as(_i32p), _d(o)),
                     "adjoint_setup")
+
+    def clock_size(self) -> int:
+        return self.n_members * (1 + 3 * self.cfg.max_levels) + 3
+
+    def get_clock(self) -> np.ndarray:
+        """Time-stepping state (member times, next-step wave speeds, step counter) for resume."""
+        buf = np.zeros(self.clock_size())
+        self._check(self.L.mlswe_get_clock(self.h, _d(buf), len(buf)), "get_clock")
+        return buf
+
+    def set_clock(self, buf: np.ndarray):
+        """Restores get_clock()'s record; call it after the last set_state."""
+        b = np.ascontiguousarray(buf, dtype=np.float64)
+        self._check(self.L.mlswe_set_clock(self.h, _d(b), len(b)), "set_clock")
 
     def hyperbolicity_losses(self, reset: bool = True) -> int:
         """Edges that used the eigenvalue guesses (loss of hyperbolicity) since the last reset."""

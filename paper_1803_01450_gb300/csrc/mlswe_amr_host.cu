@@ -537,6 +537,37 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
   return MLSWE_OK;
 }
 
+static int clock_doubles(mlswe_h h) { return h->n_members * (1 + 3 * h->L) + 3; }
+
+mlswe_status mlswe_get_clock(mlswe_h h, double* buf, int n_doubles) {
+  if (!h || !buf || n_doubles != clock_doubles(h)) return fail(h, MLSWE_EINVAL, "get_clock: bad argument");
+  const int n = h->n_members, nd = n * h->L;
+  CUDA_TRY(h, cudaMemcpyAsync(buf, h->d_t, n * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(buf + n, h->d_smax, (size_t)2 * nd * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(buf + n + 2 * nd, h->d_init, (size_t)nd * 8, cudaMemcpyDeviceToHost, h->st));
+  int flag = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&flag, h->d_init_flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  buf[n + 3 * nd] = flag;
+  buf[n + 3 * nd + 1] = h->dt_ready ? 1.0 : 0.0;
+  buf[n + 3 * nd + 2] = (double)h->coarse_steps;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_clock(mlswe_h h, const double* buf, int n_doubles) {
+  if (!h || !buf || n_doubles != clock_doubles(h)) return fail(h, MLSWE_EINVAL, "set_clock: bad argument");
+  const int n = h->n_members, nd = n * h->L;
+  const int flag = buf[n + 3 * nd] != 0.0 ? 1 : 0;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_t, buf, n * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_smax, buf + n, (size_t)2 * nd * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_init, buf + n + 2 * nd, (size_t)nd * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_init_flag, &flag, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->dt_ready = buf[n + 3 * nd + 1] != 0.0;
+  h->coarse_steps = (long long)buf[n + 3 * nd + 2];
+  return MLSWE_OK;
+}
+
 mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out) {
   if (!h) return MLSWE_EINVAL;
   std::vector<double> t(h->n_members), dt(h->n_members * h->L);

@@ -30,18 +30,21 @@ __device__ __forceinline__ int gslot(int l, int e, int len, int nl) {
   return DIR == 0 ? l * (len + 1) + e : e * nl + l;
 }
 
-// Largest |s| of a tile, then one atomicMax on the bit pattern (non-negative doubles order
-// like their unsigned 64-bit patterns).
+// Largest |s| of a tile, then one atomicMax on the bit pattern. v holds |s| as a bit pattern
+// with the sign cleared, so non-negative doubles order like their unsigned 64-bit patterns
+// and a NaN (exponent all ones, mantissa not zero) lies above +inf: reducing the patterns
+// with an integer max keeps a non-finite speed visible to the host (fmax would drop it).
 __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* dst, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  for (int o = 16; o > 0; o >>= 1) b = umax64(b, __shfl_xor_sync(0xffffffffu, b, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
+  if (l == 0) red[w] = __longlong_as_double((long long)b);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double m = red[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, red[k]);
-    if (!(m >= 0.0)) m = __longlong_as_double(0x7ff0000000000001ll);  // NaN marker: set all bits high
-    atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+    unsigned long long m = (unsigned long long)__double_as_longlong(red[0]);
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      m = umax64(m, (unsigned long long)__double_as_longlong(red[k]));
+    atomicMax(dst, m);
   }
   __syncthreads();
 }
