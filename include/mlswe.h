@@ -211,6 +211,27 @@ mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
 
+/* Run counters (not in the paper; its own report counts cell updates and time,
+ * Sec. 3). level_steps[l]: steps taken on level l (subcycles of mlswe_advance
+ * and mlswe_step_level calls); cell_updates[l]: cells inside the patches of
+ * level l times those steps, summed over members (multiply by M for
+ * layer-cell updates); patches[l]: current patch count of level l over
+ * members; regrids: regrids run; coarse_steps: coarse steps of mlswe_advance;
+ * cfl_exceeded: member coarse steps whose Courant number exceeded cfl_max;
+ * last_cfl: largest Courant number of the last coarse step over the members.
+ * Levels beyond max_levels read 0. Synchronises the stream. */
+typedef struct {
+  long long coarse_steps;
+  long long regrids;
+  long long level_steps[4];
+  long long cell_updates[4];
+  int patches[4];
+  long long cfl_exceeded;
+  double last_cfl;
+} mlswe_stats;
+
+mlswe_status mlswe_get_stats(mlswe_h h, mlswe_stats* out);
+
 /* Time-stepping state of the hierarchy, for checkpoint and resume (not in the
  * paper): member times, the wave speeds from which the next coarse step takes
  * its time step (or the pending speeds of a new state), whether that time step

@@ -127,6 +127,7 @@ _SIGS = {
     "mlswe_adjoint_keep_edge_data": [_H, ctypes.c_int],
     "mlswe_hyperbolicity_losses": [_H, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
     "mlswe_get_clock": [_H, _dp, ctypes.c_int],
+    "mlswe_get_stats": [_H, ctypes.c_void_p],
     "mlswe_set_clock": [_H, _dp, ctypes.c_int],
     "mlswe_fixed_forward": [_H, _dp],
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
@@ -171,6 +172,12 @@ def exported_symbols() -> list:
 
 def _d(a: np.ndarray):
     return a.ctypes.data_as(_dp)
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("coarse_steps", ctypes.c_longlong), ("regrids", ctypes.c_longlong),
+                ("level_steps", ctypes.c_longlong * 4), ("cell_updates", ctypes.c_longlong * 4),
+                ("patches", ctypes.c_int * 4), ("cfl_exceeded", ctypes.c_longlong), ("last_cfl", ctypes.c_double)]
 
 
 def _python_allocator(alloc, free):
@@ -358,6 +365,16 @@ class Hierarchy:
         o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
         self._check(self.L.mlswe_adjoint_setup(self.h, n_steps, ckpt_every, len(g), g.ctypes.data_as(_i32p), _d(o)),
                     "adjoint_setup")
+
+    def get_stats(self) -> dict:
+        """Run counters: coarse steps, regrids, per-level steps, cell updates and patch counts,
+        member coarse steps above cfl_max, the last Courant number."""
+        st = _Stats()
+        self._check(self.L.mlswe_get_stats(self.h, ctypes.cast(ctypes.byref(st), ctypes.c_void_p)), "get_stats")
+        L = self.cfg.max_levels
+        return {"coarse_steps": st.coarse_steps, "regrids": st.regrids,
+                "level_steps": list(st.level_steps)[:L], "cell_updates": list(st.cell_updates)[:L],
+                "patches": list(st.patches)[:L], "cfl_exceeded": st.cfl_exceeded, "last_cfl": st.last_cfl}
 
     def clock_size(self) -> int:
         return self.n_members * (1 + 3 * self.cfg.max_levels) + 3

@@ -540,6 +540,7 @@ mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss) {
   if (!h) return MLSWE_EINVAL;
   Adjoint* A = adj_of(h, false);
   if (!A || A->n_steps < 1) return afail(h, MLSWE_EINVAL, "fixed_forward: call mlswe_adjoint_setup first");
+  NvtxRange range("mlswe_fixed_forward");
   for (int dir = 0; dir < 2; ++dir) {
     mlswe_status s = ensure_worklist(h, 0, dir);
     if (s != MLSWE_OK) return s;
@@ -586,6 +587,7 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
   if (!h || !dL_dq0 || !dL_dB) return h ? afail(h, MLSWE_EINVAL, "fixed_backward: bad argument") : MLSWE_EINVAL;
   Adjoint* A = adj_of(h, false);
   if (!A || !A->forward_done) return afail(h, MLSWE_EINVAL, "fixed_backward: run mlswe_fixed_forward first");
+  NvtxRange range("mlswe_fixed_backward");
   const Level& V = h->mem[0].lev[0];
   const int M = h->cfg.M, F = 3 * M;
   const size_t plane = (size_t)V.NY * V.P;

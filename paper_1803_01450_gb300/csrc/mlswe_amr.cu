@@ -447,7 +447,7 @@ __global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const u
 // End of a coarse step: Courant number reached by every member (status bit 0 when
 // above cfl_max, bit 1 when a wave speed was not finite) and the member's time.
 __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, const double* dt, double* t_member,
-                                double* cfl_reached, unsigned int* status) {
+                                double* cfl_reached, unsigned int* status, unsigned long long* cfl_count) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= A.n_members) return;
   double reached = 0.0;
@@ -460,7 +460,10 @@ __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, c
     reached = fmax(reached, dt[d] * fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]));
   }
   cfl_reached[m] = reached;
-  if (reached > A.cfl_max) atomicOr(status, 1u);
+  if (reached > A.cfl_max) {
+    atomicOr(status, 1u);
+    atomicAdd(cfl_count, 1ull);
+  }
   if (bad) atomicOr(status, 2u);
   t_member[m] += dt[m * A.L];
 }
@@ -476,8 +479,10 @@ cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, cons
 }
 
 cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
-                            double* cfl_reached, unsigned int* status, cudaStream_t st) {
-  step_end_kernel<<<(A.n_members + 127) / 128, 128, 0, st>>>(A, smax_bits, dt, t_member, cfl_reached, status);
+                            double* cfl_reached, unsigned int* status, unsigned long long* cfl_count,
+                            cudaStream_t st) {
+  step_end_kernel<<<(A.n_members + 127) / 128, 128, 0, st>>>(A, smax_bits, dt, t_member, cfl_reached, status,
+                                                              cfl_count);
   return cudaGetLastError();
 }
 

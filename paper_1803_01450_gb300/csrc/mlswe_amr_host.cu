@@ -269,7 +269,8 @@ static mlswe_status enqueue_coarse_step(Hier* H) {
   mlswe_status s = enqueue_level_tree(H, 0, 0.0);
   if (s != MLSWE_OK) return s;
   timer_begin(H, KC_OTHER, &tok);
-  CUDA_TRY(H, launch_step_end(dt_args(H), H->d_smax, H->d_dt, H->d_t, H->d_cfl, H->d_status, H->st));
+  CUDA_TRY(H, launch_step_end(dt_args(H), H->d_smax, H->d_dt, H->d_t, H->d_cfl, H->d_status, H->d_cfl_count,
+                              H->st));
   timer_end(H, tok);
   return MLSWE_OK;
 }
@@ -334,6 +335,8 @@ static mlswe_status coarse_step(Hier* H) {
 }
 
 static mlswe_status regrid_internal(Hier* H, int base) {
+  NvtxRange range("mlswe_regrid");
+  H->regrids++;
   for (int m = 0; m < H->n_members; ++m) {
     for (int l = base; l + 1 < H->L; ++l) {
       Level& V = H->mem[m].lev[l];
@@ -375,6 +378,7 @@ static mlswe_status regrid_internal(Hier* H, int base) {
 // current patch layout (CUDA events, sweeps run without recording, the state is not
 // advanced) and keeps the fastest per direction.
 static mlswe_status autotune_level(Hier* H, int level, int iters, int* chosen) {
+  NvtxRange range("mlswe_autotune");
   static const int cand[][2] = {{13, 16}, {29, 8}, {61, 4}, {125, 2}, {253, 1}};
   cudaEvent_t e0, e1;
   CUDA_TRY(H, cudaEventCreate(&e0));
@@ -510,6 +514,7 @@ mlswe_status mlswe_regrid(mlswe_h h, int base_level) {
 
 mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
   if (!h || n_coarse_steps < 0) return fail(h, MLSWE_EINVAL, "advance: bad argument");
+  NvtxRange range("mlswe_advance");
   CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
   for (int k = 0; k < n_coarse_steps; ++k) {
     mlswe_status s;
@@ -525,9 +530,18 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
       s = initial_dt(h);
       if (s != MLSWE_OK) return s;
     }
-    s = coarse_step(h);
+    {
+      NvtxRange step_range("mlswe_coarse_step");
+      s = coarse_step(h);
+    }
     if (s != MLSWE_OK) return s;
     h->coarse_steps++;
+    long long steps = 1;
+    for (int l = 0; l < h->L; ++l) {
+      if (l > 0) steps *= h->cfg.ratio[l - 1];
+      h->level_steps[l] += steps;
+      h->cell_updates[l] += steps * patch_cells(h, l);
+    }
   }
   unsigned int status = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));

@@ -148,6 +148,13 @@ static void tile_dims(const TileShape& ts, int extent, int* len, int* lines) {
   *lines = std::max(ts.lines, std::min(32, kMaxEdges / (*len + 3)));
 }
 
+long long patch_cells(const Hier* H, int level) {
+  long long c = 0;
+  for (int m = 0; m < H->n_members; ++m)
+    for (const Box& b : H->mem[m].lev[level].patches) c += (long long)(b.i1 - b.i0) * (b.j1 - b.j0);
+  return c;
+}
+
 // Sweep work list of one level: tiles over every patch of every member, grouped by patch.
 static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out, std::vector<int>& patch_off) {
   out.clear();
@@ -414,8 +421,9 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->d_invdy = (double*)dev_alloc(H, nd * 8);
   H->d_par = (int*)dev_alloc(H, nd * 4);
   H->d_init_flag = (int*)dev_alloc(H, 8);
+  H->d_cfl_count = (unsigned long long*)dev_alloc(H, 8);
   if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_init || !H->d_lost || !H->d_status || !H->d_t || !H->d_cfl ||
-      !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag) {
+      !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag || !H->d_cfl_count) {
     mlswe_destroy(H);
     return MLSWE_ENOMEM;
   }
@@ -429,6 +437,9 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   cudaMemsetAsync(H->d_cfl, 0, n_members * 8, H->st);
   cudaMemsetAsync(H->d_has, 0, nd * 4, H->st);
   cudaMemsetAsync(H->d_init_flag, 0, 8, H->st);
+  cudaMemsetAsync(H->d_cfl_count, 0, 8, H->st);
+  H->level_steps.assign(H->L, 0);
+  H->cell_updates.assign(H->L, 0);
   if (upload_desc(H) != MLSWE_OK) { mlswe_destroy(H); return MLSWE_ECUDA; }
   H->blocks_per_sm = 1;
   *out = H;
@@ -494,6 +505,9 @@ mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt) {
 
 mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cfl_out) {
   if (!h || level < 0 || level >= h->L) return fail(h, MLSWE_EINVAL, "step_level: bad argument");
+  NvtxRange range("mlswe_step_level");
+  h->level_steps[level] += 1;
+  h->cell_updates[level] += patch_cells(h, level);
   if (dt) {
     mlswe_status s = mlswe_set_dt(h, level, dt);
     if (s != MLSWE_OK) return s;
@@ -518,6 +532,30 @@ mlswe_status mlswe_set_tiles(mlswe_h h, int dir, int len, int lines, int ctas_pe
     return fail(h, MLSWE_EINVAL, "set_tiles: shape out of range");
   for (int l = 0; l < h->L; ++l) set_level_shape(h, l, dir, len, lines, ctas_per_sm);
   invalidate_graphs(h);
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_get_stats(mlswe_h h, mlswe_stats* out) {
+  if (!h || !out) return fail(h, MLSWE_EINVAL, "get_stats: bad argument");
+  std::memset(out, 0, sizeof(*out));
+  unsigned long long exceeded = 0;
+  std::vector<double> cfl(h->n_members);
+  CUDA_TRY(h, cudaMemcpyAsync(&exceeded, h->d_cfl_count, 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(cfl.data(), h->d_cfl, cfl.size() * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  out->coarse_steps = h->coarse_steps;
+  out->regrids = h->regrids;
+  for (int l = 0; l < h->L && l < 4; ++l) {
+    out->level_steps[l] = h->level_steps[l];
+    out->cell_updates[l] = h->cell_updates[l];
+    int np = 0;
+    for (int m = 0; m < h->n_members; ++m) np += (int)h->mem[m].lev[l].patches.size();
+    out->patches[l] = np;
+  }
+  out->cfl_exceeded = (long long)exceeded;
+  double mx = 0.0;
+  for (double c : cfl) mx = std::max(mx, c);
+  out->last_cfl = mx;
   return MLSWE_OK;
 }
 

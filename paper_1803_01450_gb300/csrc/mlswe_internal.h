@@ -1,6 +1,7 @@
 // Host-side internals of the library (not part of the C ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -132,6 +133,10 @@ struct Hier {
   bool graph_valid[2] = {false, false};
   long long graph_launches[2] = {0, 0};  // kernels inside each graph
   long long coarse_steps = 0;
+  long long regrids = 0;                 // regrids run (automatic and mlswe_regrid)
+  std::vector<long long> level_steps;    // [L] steps taken per level
+  std::vector<long long> cell_updates;   // [L] patch cells x steps per level, all members
+  unsigned long long* d_cfl_count = nullptr;  // [1] member coarse steps above cfl_max
   LaunchTimer timer;
   long long kernel_launches = 0;   // every kernel this hierarchy launched
   void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
@@ -154,7 +159,20 @@ struct DtArgs {
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
                             int* init_flag, double* dt, cudaStream_t st);
 cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
-                            double* cfl_reached, unsigned int* status, cudaStream_t st);
+                            double* cfl_reached, unsigned int* status, unsigned long long* cfl_count,
+                            cudaStream_t st);
+
+// Cells inside the patches of `level`, summed over the members.
+long long patch_cells(const Hier* H, int level);
+
+// NVTX range for the duration of a scope (shows host phases in a timeline profiler; costs
+// nothing measurable when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Optional per-kernel-class timing with CUDA events on the hierarchy's stream.
 void timer_begin(Hier* H, int kc, int* token);

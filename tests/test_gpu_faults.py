@@ -3,7 +3,7 @@ reports what went wrong through its status code and leaves the hierarchy usable 
 released. Cases: a non-finite state, a time step above the Courant limit, patch tables that
 break nesting, allocation failures in the allocator callback, and a state with negative
 depths (repaired by the positivity rule, not an error). Also: checkpoint and resume of a
-subcycled AMR run through the public calls, bit for bit."""
+subcycled AMR run through the public calls, bit for bit, and the run counters."""
 import numpy as np
 import pytest
 
@@ -60,6 +60,8 @@ def test_courant_number_above_limit_is_reported(mlswe_lib):
     H = _small(mlswe_lib, cfl_desired=1.5, cfl_max=1.0)
     H.set_state(0, 0, w["q"])
     _raises(mlswe_lib, ECFL, H.advance, 2)
+    st = H.get_stats()
+    assert st["cfl_exceeded"] >= 1 and st["last_cfl"] > 1.0
     H.close()
 
 
@@ -172,3 +174,21 @@ def test_checkpoint_and_resume_bit_for_bit(mlswe_lib):
     assert np.array_equal(A.get_state(0, 1)[:, m], B.get_state(0, 1)[:, m])
     A.close()
     B.close()
+
+
+def test_run_counters(mlswe_lib):
+    w = I.small(50)
+    H = _small(mlswe_lib, levels=2, regrid=4, min_side=16)
+    H.set_state(0, 0, w["q"])
+    H.advance(8)
+    st = H.get_stats()
+    assert st["coarse_steps"] == 8 and st["regrids"] == 2  # before coarse steps 0 and 4
+    assert st["level_steps"] == [8, 16]  # ratio 2 subcycling
+    assert st["cell_updates"][0] == 8 * 50 * 50
+    assert st["cell_updates"][1] > 0 and st["cell_updates"][1] % 2 == 0
+    assert st["patches"] == [1, H.get_patches(0, 1).shape[0]]
+    assert st["cfl_exceeded"] == 0 and 0.5 < st["last_cfl"] < 1.0
+    H.step_level(0, dt=1e-4)
+    st2 = H.get_stats()
+    assert st2["level_steps"] == [9, 16] and st2["cell_updates"][0] == 9 * 50 * 50
+    H.close()
