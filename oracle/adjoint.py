@@ -62,3 +62,25 @@ def control_gradient(P, eta1_0, B, dx, dy, dt, n_steps, gauge_ij, obs, eta2=-200
     q0 = initial_state(eta1_0, B, eta2)
     J, dq0, gB = gradient(P, q0, B, dx, dy, dt, n_steps, gauge_ij, obs)
     return J, dq0[0], gB - dq0[3]
+
+
+def tangent(P, q0, B, dx, dy, dt, n_steps, gauge_ij, obs, dq0, dB):
+    """(J, dJ along (dq0, dB)) by forward-mode dual numbers through every step
+    (or_tangent_loss): the exact directional derivative the adjoint's gradient must match
+    in a dot product."""
+    import ctypes
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    dq0 = np.ascontiguousarray(dq0, dtype=np.float64)
+    dB = np.ascontiguousarray(dB, dtype=np.float64)
+    g = np.ascontiguousarray(np.asarray(gauge_ij, dtype=np.int32).reshape(-1, 2))
+    o = np.ascontiguousarray(np.asarray(obs, dtype=np.float64).reshape(n_steps, len(g)))
+    ny, nx = B.shape
+    J = ctypes.c_double(0.0)
+    dJ = ctypes.c_double(0.0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    O.lib().or_tangent_loss(ctypes.byref(P), nx, ny, ctypes.c_double(dx), ctypes.c_double(dy), ctypes.c_double(dt),
+                            n_steps, q0.ctypes.data_as(dp), B.ctypes.data_as(dp), dq0.ctypes.data_as(dp),
+                            dB.ctypes.data_as(dp), len(g), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                            o.ctypes.data_as(dp), ctypes.byref(J), ctypes.byref(dJ))
+    return J.value, dJ.value

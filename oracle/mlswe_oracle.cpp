@@ -455,7 +455,8 @@ inline size_t pidx(int nx, int i, int j) { return (size_t)(j + NG) * (nx + 2 * N
 // Wall ghost cells on all four sides: mirror the state, negate the normal momentum of
 // every layer, mirror B. x ghosts of the interior rows first, then full-width y ghost rows
 // (corners therefore carry both negations).
-void fill_walls_impl(int M, int nx, int ny, double* q, double* B, int sides /*bit0 W, bit1 E, bit2 S, bit3 N*/) {
+template <class T>
+void fill_walls_t(int M, int nx, int ny, T* q, T* B, int sides /*bit0 W, bit1 E, bit2 S, bit3 N*/) {
   const int F = 3 * M;
   const size_t plane = (size_t)(nx + 2 * NG) * (ny + 2 * NG);
   for (int j = 0; j < ny; ++j)
@@ -496,6 +497,10 @@ void fill_walls_impl(int M, int nx, int ny, double* q, double* B, int sides /*bi
         if (B) B[pidx(nx, i, dst)] = B[pidx(nx, i, src)];
       }
     }
+}
+
+void fill_walls_impl(int M, int nx, int ny, double* q, double* B, int sides) {
+  fill_walls_t<double>(M, nx, ny, q, B, sides);
 }
 
 // One dimensionally split step on a patch whose ghost ring is filled.
@@ -979,4 +984,44 @@ extern "C" void or_adjoint_step(const or_params* pp, int nx, int ny, double dx, 
       gB[(size_t)j * nx + i] += gBp[pidx(nx, i, j)];
       for (int f = 0; f < F; ++f) lam[f * plane + (size_t)j * nx + i] = lamp[f * pplane + pidx(nx, i, j)];
     }
+}
+
+// Tangent-linear run of the gauge misfit (forward-mode dual numbers through every step):
+// J = sum_{n=1..N} sum_g (eta_1(cell_g, Q^n) - obs[n-1][g])^2 with eta_1 = (B + h_2) + h_1
+// (Eq. (4)) for N walled, fixed-dt steps from Q^0, and its directional derivative along
+// (dq0, dB). q0, dq0: [3M][ny][nx]; B, dB: [ny][nx]; gij: [n_g][2] (i, j); obs: [N][n_g].
+extern "C" void or_tangent_loss(const or_params* pp, int nx, int ny, double dx, double dy, double dt, int n_steps,
+                                const double* q0, const double* B, const double* dq0, const double* dB, int n_g,
+                                const int* gij, const double* obs, double* J, double* dJ) {
+  using D1 = Dual<1>;
+  const Params P = to_params(pp);
+  const int F = 3 * P.M;
+  const int W = nx + 2 * NG, H = ny + 2 * NG;
+  const size_t pplane = (size_t)W * H, plane = (size_t)nx * ny;
+  std::vector<D1> q(pplane * F), Bp(pplane);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t o = (size_t)j * nx + i;
+      Bp[pidx(nx, i, j)] = D1(B[o]);
+      Bp[pidx(nx, i, j)].d[0] = dB[o];
+      for (int f = 0; f < F; ++f) {
+        q[f * pplane + pidx(nx, i, j)] = D1(q0[f * plane + o]);
+        q[f * pplane + pidx(nx, i, j)].d[0] = dq0[f * plane + o];
+      }
+    }
+  double j_val = 0.0, j_dot = 0.0;
+  for (int n = 1; n <= n_steps; ++n) {
+    fill_walls_t<D1>(P.M, nx, ny, q.data(), Bp.data(), 15);
+    step_patch_impl<D1>(P, nx, ny, dx, dy, dt, q.data(), Bp.data(), nullptr, nullptr, nullptr, nullptr);
+    for (int g = 0; g < n_g; ++g) {
+      const int i = gij[2 * g], jj = gij[2 * g + 1];
+      D1 eta = Bp[pidx(nx, i, jj)];
+      for (int m = P.M - 1; m >= 0; --m) eta = eta + q[(3 * m) * pplane + pidx(nx, i, jj)];
+      const D1 r = eta - obs[(size_t)(n - 1) * n_g + g];
+      j_val += r.v * r.v;
+      j_dot += 2.0 * r.v * r.d[0];
+    }
+  }
+  *J = j_val;
+  *dJ = j_dot;
 }

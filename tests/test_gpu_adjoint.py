@@ -48,8 +48,26 @@ def test_gradient_matches_oracle_adjoint(mlswe_lib, keep_edge_data):
     assert abs(J - Jo) <= 1e-12 * Jo
     for f in range(6):
         sc = max(np.abs(dq0o[f]).max(), 1e-300)
-        assert np.abs(dq0[f] - dq0o[f]).max() <= 1e-10 * sc, (f, np.abs(dq0[f] - dq0o[f]).max() / sc)
-    assert np.abs(dB - dBo).max() <= 1e-10 * np.abs(dBo).max()
+        assert np.abs(dq0[f] - dq0o[f]).max() <= 1e-11 * sc, (f, np.abs(dq0[f] - dq0o[f]).max() / sc)
+    assert np.abs(dB - dBo).max() <= 1e-11 * np.abs(dBo).max()
+
+
+def test_gradient_dot_product_with_oracle_tangent(mlswe_lib):
+    """<GPU gradient, v> equals the oracle's forward-mode (dual-number) directional
+    derivative of the loss along v, for random directions through every state field and
+    the bathymetry."""
+    s = _setup()
+    J, dq0, dB = _gpu_grad(mlswe_lib, s, ckpt=5)
+    q0 = OA.initial_state(s["eta1"], s["B"])
+    rng = np.random.default_rng(11)
+    scale = np.array([1e-2, 1.0, 1.0, 1e-2, 1.0, 1.0])[:, None, None]
+    for _ in range(4):
+        vq = rng.standard_normal(q0.shape) * scale
+        vB = 1e-2 * rng.standard_normal(s["B"].shape)
+        Jt, dJ = OA.tangent(s["P"], q0, s["B"], s["dx"], s["dx"], s["dt"], s["steps"], s["gauges"], s["obs"], vq, vB)
+        assert abs(Jt - J) <= 1e-12 * Jt
+        ad = float(np.sum(dq0 * vq) + np.sum(dB * vB))
+        assert abs(ad - dJ) <= 1e-11 * abs(dJ), (ad, dJ)
 
 
 def test_kept_and_rebuilt_edge_records_agree(mlswe_lib):
@@ -74,7 +92,7 @@ def test_checkpoint_spacing_does_not_change_gradient(mlswe_lib):
 
 
 def test_gradient_matches_central_fd_of_gpu_forward(mlswe_lib):
-    """Directional derivatives along seeded Gaussian directions mixing both controls."""
+    """Directional derivatives along 64 seeded Gaussian directions mixing both controls."""
     import torch
     from paper_1803_01450_gb300.adjoint import FixedGridProblem, gauge_misfit
     s = _setup(n=64, steps=20, n_g=16)
@@ -87,7 +105,7 @@ def test_gradient_matches_central_fd_of_gpu_forward(mlswe_lib):
     ge, gB = e.grad.cpu().numpy(), Bt.grad.cpu().numpy()
     rng = np.random.default_rng(9)
     x_norm = np.sqrt(np.sum(s["eta1"] ** 2) + np.sum(s["B"] ** 2))
-    for _ in range(8):
+    for _ in range(64):
         de = rng.standard_normal(ge.shape)
         dB = rng.standard_normal(gB.shape)
         d_norm = np.sqrt(np.sum(de ** 2) + np.sum(dB ** 2))

@@ -72,3 +72,24 @@ def test_gauge_misfit_gradient_matches_central_fd():
         fd = (Jp - Jm) / (2 * eps)
         ad = float(np.sum(g_eta * de) + np.sum(g_B * dB))
         assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
+
+
+def test_adjoint_dot_product_with_dual_number_tangent():
+    """<gradient, v> of the reverse-mode adjoint equals the forward-mode (dual-number)
+    directional derivative of the same loss along v, for random directions through every
+    state field and the bathymetry: two exact derivatives, independent code, equal to
+    rounding."""
+    P, eta1, B, dx, dt, steps, gauges, obs = _problem()
+    q0 = A.initial_state(eta1, B)
+    rng = np.random.default_rng(7)
+    q0[1] = 0.2 * rng.standard_normal(q0[1].shape) * q0[0] / 200.0  # some motion in both layers
+    q0[5] = 0.2 * rng.standard_normal(q0[5].shape) * q0[3] / 3000.0
+    J, dq0, gB = A.gradient(P, q0, B, dx, dx, dt, steps, gauges, obs)
+    scale = np.array([1e-2, 1.0, 1.0, 1e-2, 1.0, 1.0])[:, None, None]
+    for _ in range(4):
+        vq = rng.standard_normal(q0.shape) * scale
+        vB = 1e-2 * rng.standard_normal(B.shape)
+        Jt, dJ = A.tangent(P, q0, B, dx, dx, dt, steps, gauges, obs, vq, vB)
+        assert abs(Jt - J) <= 1e-14 * J
+        ad = float(np.sum(dq0 * vq) + np.sum(gB * vB))
+        assert abs(ad - dJ) <= 1e-13 * abs(dJ), (ad, dJ, abs(ad - dJ) / abs(dJ))
