@@ -171,9 +171,9 @@ def test_fill_ghosts_parity(mlswe_lib):
 
 
 def test_amr_run_parity_small(mlswe_lib):
-    """20 coarse steps of the small workload with a level of refinement (ratio 2), regrid
-    every 4 steps, automatic time steps: identical patch layouts, states within 1e-11,
-    and the GPU composite mass constant to 1e-13."""
+    """The small workload's full run, 100 coarse steps with a level of refinement (ratio 2),
+    regrid every 4 steps, automatic time steps: identical patch layouts after every regrid,
+    states within 1e-11, and the GPU composite mass equal to the oracle's to 1e-12."""
     w = I.small(50)
     H = _small_amr(mlswe_lib)
     A = _oracle_small()
@@ -192,7 +192,7 @@ def test_amr_run_parity_small(mlswe_lib):
             out[k] = q0[3 * k][~cov].sum() * 0.02 ** 2 + q1[3 * k][m1].sum() * 0.01 ** 2
         return out
 
-    for chunk in range(5):
+    for chunk in range(25):
         H.advance(4)
         A.advance(4, regrid_interval=4)
         gp = [tuple(b) for b in H.get_patches(0, 1).tolist()]
