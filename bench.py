@@ -49,7 +49,7 @@ FP64_FLOP_PER_CELL_UPDATE = 1293.25
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
-SWEEP_X_DRAM_BYTES = 396.0e6
+SWEEP_X_DRAM_BYTES = 395.8e6
 
 
 class ClockSampler:
