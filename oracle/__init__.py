@@ -41,15 +41,23 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+MAXM = 4  # layers the oracle supports (MAXM in mlswe_oracle.cpp)
+
+
 class Params(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("g", ctypes.c_double), ("r", ctypes.c_double),
                 ("dry_tol", ctypes.c_double), ("order", ctypes.c_int), ("limiter", ctypes.c_int),
-                ("eigen", ctypes.c_int)]
+                ("eigen", ctypes.c_int), ("rho", ctypes.c_double * MAXM)]
 
 
-def params(M=2, g=9.81, rho=(1000.0, 1025.0), dry_tol=1e-3, order=2, limiter=2, eigen=0) -> Params:
+def params(M=2, g=9.81, rho=None, dry_tol=1e-3, order=2, limiter=2, eigen=0) -> Params:
+    """rho: layer densities, top (lightest) first; default 1000, 1025 for two layers and
+    1000, 1020, 1030, 1040 (first M) otherwise."""
+    if rho is None:
+        rho = (1000.0, 1025.0) if M == 2 else (1000.0, 1020.0, 1030.0, 1040.0)[:M]
     r = rho[0] / rho[1] if M == 2 else 1.0
-    return Params(M, g, r, dry_tol, order, limiter, eigen)
+    rr = (ctypes.c_double * MAXM)(*(list(rho[:M]) + [0.0] * (MAXM - min(M, len(rho)))))
+    return Params(M, g, r, dry_tol, order, limiter, eigen, rr)
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -64,6 +72,7 @@ def lib():
         _lib = ctypes.CDLL(build())
         L = _lib
         L.or_riemann.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _ip]
+        L.or_riemann_general.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _ip]
         L.or_eigen.argtypes = [_pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip]
         L.or_sweep_line.argtypes = [_pp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_sweep_line.restype = ctypes.c_double
@@ -95,18 +104,23 @@ def _c(a, dtype=np.float64):
 
 
 # --------------------------------------------------------------------------- edge level
-def riemann(P: Params, qL, qR, BL, BR):
+def riemann(P: Params, qL, qR, BL, BR, general=False):
     """Waves, speeds and fluctuations at one edge (normal direction first in each layer).
 
-    Returns (Z[6][6], s[6], amdq[6], apdq[6], info[3]) where info = (wall side of
-    layer 1, wall side of layer 2, hyperbolicity-loss flag)."""
-    qL = _c(np.pad(np.asarray(qL, float), (0, 6 - len(qL))))
-    qR = _c(np.pad(np.asarray(qR, float), (0, 6 - len(qR))))
-    Z = np.zeros((6, 6)); s = np.zeros(6); am = np.zeros(6); ap = np.zeros(6)
-    info = np.zeros(3, dtype=np.int32)
-    lib().or_riemann(ctypes.byref(P), _d(qL), _d(qR), float(BL), float(BR), _d(Z), _d(s), _d(am), _d(ap),
-                     info.ctypes.data_as(_ip))
-    return Z, s, am, ap, info
+    Returns (Z[3W][3W], s[3W], amdq[3W], apdq[3W], info) with W = max(M, 2): waves and
+    fields beyond 3M are zero; info = (wall side of each of the first W layers,
+    hyperbolicity-loss flag). general: take the general M-layer coupled branch also for
+    M = 2."""
+    F, W = 3 * MAXM, max(P.M, 2)
+    qL = _c(np.pad(np.asarray(qL, float), (0, F - len(qL))))
+    qR = _c(np.pad(np.asarray(qR, float), (0, F - len(qR))))
+    Z = np.zeros((F, F)); s = np.zeros(F); am = np.zeros(F); ap = np.zeros(F)
+    info = np.zeros(MAXM + 1, dtype=np.int32)
+    fn = lib().or_riemann_general if general else lib().or_riemann
+    fn(ctypes.byref(P), _d(qL), _d(qR), float(BL), float(BR), _d(Z), _d(s), _d(am), _d(ap),
+       info.ctypes.data_as(_ip))
+    n = 3 * W
+    return Z[:n, :n].copy(), s[:n].copy(), am[:n].copy(), ap[:n].copy(), np.concatenate([info[:W], info[MAXM:]])
 
 
 def eigen(P: Params, u1, u2, hb1, hb2):

@@ -39,18 +39,20 @@
 namespace {
 
 constexpr int NG = 2;
-constexpr int MAXM = 2;
+constexpr int MAXM = 4;
 constexpr int MAXF = 3 * MAXM;
 constexpr int MAXW = 3 * MAXM;
 
 struct Params {
-  int M;          // number of layers, 1 or 2
+  int M;          // number of layers, 1 .. MAXM
   double g;       // gravity
   double r;       // density ratio rho_1 / rho_2 (M = 2)
+  double rho[MAXM];  // layer densities, top (lightest) first (M >= 3)
   double dry_tol; // a layer is wet where h > dry_tol (and every layer above is wet)
   int order;      // 1 or 2
   int limiter;    // 0 none, 1 minmod, 2 MC
   int eigen;      // 0: guesses + 2 Newton steps, 1: guesses only
+  int force_general = 0;  // 1: the general coupled branch also for M = 2 (a check of it)
 };
 
 // ---------------------------------------------------------------------------
@@ -208,6 +210,204 @@ void single_layer_waves(int m, const T& d0, const T& d1, const T& d2, const T& s
   W.s[pshear] = ushear;
 }
 
+// rho_n / rho_m: the weight of layer n's depth jump in layer m's pressure (n above m).
+inline double density_ratio(const Params& P, int n, int m) {
+  if (P.M == 2) return P.r;
+  return P.rho[n] / P.rho[m];
+}
+
+// Dense n x n solve by Gaussian elimination with partial pivoting (ties: lowest row).
+template <class T>
+void solve_n(int n, T A[2 * MAXM][2 * MAXM], T b[2 * MAXM], T x[2 * MAXM]) {
+  int perm[2 * MAXM];
+  for (int i = 0; i < n; ++i) perm[i] = i;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(val(A[perm[i]][k])) > std::fabs(val(A[perm[piv]][k]))) piv = i;
+    std::swap(perm[k], perm[piv]);
+    for (int i = k + 1; i < n; ++i) {
+      const T f = A[perm[i]][k] / A[perm[k]][k];
+      for (int j = k; j < n; ++j) A[perm[i]][j] = A[perm[i]][j] - f * A[perm[k]][j];
+      b[perm[i]] = b[perm[i]] - f * b[perm[k]];
+    }
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    T sum = b[perm[k]];
+    for (int j = k + 1; j < n; ++j) sum = sum - A[perm[k]][j] * x[j];
+    x[k] = sum / A[perm[k]][k];
+  }
+}
+
+// Determinant of the n x n matrix A with row `skip` and column `skip` removed (skip < 0:
+// none), by Gaussian elimination with partial pivoting.
+template <class T>
+T det_minor(int n, const T A[MAXM][MAXM], int skip) {
+  T B[MAXM][MAXM];
+  int k = 0;
+  for (int i = 0; i < n; ++i) {
+    if (i == skip) continue;
+    int l = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == skip) continue;
+      B[k][l++] = A[i][j];
+    }
+    ++k;
+  }
+  T det = T(1.0);
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < k; ++i)
+      if (std::fabs(val(B[i][c])) > std::fabs(val(B[piv][c]))) piv = i;
+    if (piv != c) {
+      for (int j = 0; j < k; ++j) std::swap(B[c][j], B[piv][j]);
+      det = -det;
+    }
+    det = det * B[c][c];
+    for (int i = c + 1; i < k; ++i) {
+      const T f = B[i][c] / B[c][c];
+      for (int j = c; j < k; ++j) B[i][j] = B[i][j] - f * B[c][j];
+    }
+  }
+  return det;
+}
+
+// Eigenvalues of the symmetric n x n matrix K by cyclic Jacobi rotations (each rotation
+// zeroes one off-diagonal pair), repeated until the off-diagonal part is below 1e-30 of
+// the diagonal; returned in descending order.
+template <class T>
+void jacobi_eigenvalues(int n, T K[MAXM][MAXM], T mu[MAXM]) {
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i) {
+      diag += val(K[i][i]) * val(K[i][i]);
+      for (int j = 0; j < n; ++j)
+        if (i != j) off += val(K[i][j]) * val(K[i][j]);
+    }
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (val(K[p][q]) == 0.0) continue;
+        // rotation angle: tan(2 phi) = 2 K_pq / (K_qq - K_pp); t = tan(phi), smaller root
+        const T theta = (K[q][q] - K[p][p]) / (2.0 * K[p][q]);
+        const T t = (val(theta) >= 0.0 ? T(1.0) : T(-1.0)) / (tabs(theta) + sqrt(theta * theta + 1.0));
+        const T c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const T kp = K[k][p], kq = K[k][q];
+          K[k][p] = c * kp - sn * kq;
+          K[k][q] = sn * kp + c * kq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const T pk = K[p][k], qk = K[q][k];
+          K[p][k] = c * pk - sn * qk;
+          K[q][k] = sn * pk + c * qk;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) mu[i] = K[i][i];
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (val(mu[j]) > val(mu[i])) std::swap(mu[i], mu[j]);
+}
+
+// Coupled branch for M >= 2 layers, all wet on both sides (the general form of the
+// two-layer branch). For an eigenvalue l the layer depths of the eigenvector solve
+//   ((l - u_m)^2) dh_m = sum_n G_mn dh_n,   G_mn = g hbar_m C_mn,
+//   C_mn = 1 (n >= m: own layer and the layers below), rho_n / rho_m (n < m: lighter above),
+// so the 2M eigenvalues are the roots of P(l) = det(diag((l - u_m)^2) - G). Guesses: the
+// exact roots for equal velocities, l = ubar -+ sqrt(mu_k) with mu_k the eigenvalues of G
+// (G = diag(g hbar / rho) S with S_mn = rho_min(m,n) symmetric, so G is similar to the
+// symmetric K = W^(1/2) S W^(1/2)), then 2 Newton steps with P'(l) = sum_m 2 (l - u_m) A~_mm
+// (A~_mm the diagonal cofactors of A(l) = diag((l - u_m)^2) - G). Eigenvectors: dh_1 = 1
+// and rows 1 .. M-1 of A(l) dh = 0; momenta l dh. Strengths from the 2M x 2M system.
+// Loss of hyperbolicity: some adjacent pair with (u_m - u_{m+1})^2 >= (1 - rho_m/rho_{m+1})
+// g (hbar_m + hbar_{m+1}); then the guesses are used.
+template <class T>
+void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2][MAXM], T ut[2][MAXM],
+                           const T hbar[MAXM], const T d0[MAXM], const T d1[MAXM], const T d2[MAXM], Waves<T>& W) {
+  const int M = P.M, N = 2 * M;
+  const double g = P.g;
+  T uh[MAXM], vh[MAXM], G[MAXM][MAXM];
+  for (int m = 0; m < M; ++m) {
+    const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
+    uh[m] = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
+    vh[m] = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
+  }
+  for (int m = 0; m < M; ++m)
+    for (int n = 0; n < M; ++n) G[m][n] = g * hbar[m] * (n >= m ? 1.0 : density_ratio(P, n, m));
+  // guesses
+  T K[MAXM][MAXM], mu[MAXM], wq[MAXM];
+  for (int m = 0; m < M; ++m) wq[m] = sqrt(g * hbar[m] / P.rho[m]);
+  for (int m = 0; m < M; ++m)
+    for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * std::min(P.rho[m], P.rho[n]);
+  jacobi_eigenvalues(M, K, mu);
+  T hsum = T(0.0), husum = T(0.0);
+  for (int m = 0; m < M; ++m) { hsum = hsum + hbar[m]; husum = husum + hbar[m] * uh[m]; }
+  const T ubar = husum / hsum;
+  T lam[2 * MAXM];
+  for (int k = 0; k < M; ++k) {
+    const T sq = sqrt(mu[k]);
+    lam[k] = ubar - sq;
+    lam[N - 1 - k] = ubar + sq;
+  }
+  int lost = 0;
+  for (int m = 0; m + 1 < M; ++m) {
+    const T du = uh[m] - uh[m + 1];
+    if (val(du * du) >= val((1.0 - P.rho[m] / P.rho[m + 1]) * g * (hbar[m] + hbar[m + 1]))) lost = 1;
+  }
+  W.hyperbolicity_lost = lost;
+  T A[MAXM][MAXM];
+  if (!lost && P.eigen == 0) {
+    for (int p = 0; p < N; ++p) {
+      T l = lam[p];
+      for (int it = 0; it < 2; ++it) {
+        for (int m = 0; m < M; ++m)
+          for (int n = 0; n < M; ++n) A[m][n] = (m == n ? (l - uh[m]) * (l - uh[m]) : T(0.0)) - G[m][n];
+        const T Pl = det_minor(M, A, -1);
+        T dP = T(0.0);
+        for (int m = 0; m < M; ++m) dP = dP + 2.0 * (l - uh[m]) * det_minor(M, A, m);
+        l = l - Pl / dP;
+      }
+      lam[p] = l;
+    }
+  }
+  // eigenvectors and the strengths
+  T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM], beta[2 * MAXM], dh[2 * MAXM][MAXM];
+  for (int p = 0; p < N; ++p) {
+    const T l = lam[p];
+    for (int m = 0; m < M; ++m)
+      for (int n = 0; n < M; ++n) A[m][n] = (m == n ? (l - uh[m]) * (l - uh[m]) : T(0.0)) - G[m][n];
+    dh[p][0] = T(1.0);
+    // rows 0 .. M-2 for dh_1 .. dh_{M-1}: A[i][1..] x = -A[i][0]
+    T S[2 * MAXM][2 * MAXM], b[2 * MAXM], x[2 * MAXM];
+    for (int i = 0; i < M - 1; ++i) {
+      for (int j = 1; j < M; ++j) S[i][j - 1] = A[i][j];
+      b[i] = -A[i][0];
+    }
+    solve_n(M - 1, S, b, x);
+    for (int m = 1; m < M; ++m) dh[p][m] = x[m - 1];
+    for (int m = 0; m < M; ++m) {
+      R[2 * m][p] = dh[p][m];
+      R[2 * m + 1][p] = l * dh[p][m];
+    }
+  }
+  for (int m = 0; m < M; ++m) { rhs[2 * m] = d0[m]; rhs[2 * m + 1] = d1[m]; }
+  solve_n(N, R, rhs, beta);
+  for (int p = 0; p < N; ++p) {
+    for (int m = 0; m < M; ++m) {
+      const T mass = beta[p] * dh[p][m];
+      W.Z[p][3 * m] = mass;
+      W.Z[p][3 * m + 1] = mass * lam[p];
+      W.Z[p][3 * m + 2] = mass * vh[m];
+    }
+    W.s[p] = lam[p];
+  }
+  for (int m = 0; m < M; ++m) {
+    W.Z[N + m][3 * m + 2] = d2[m] - vh[m] * d0[m];
+    W.s[N + m] = uh[m];
+  }
+}
+
 template <class T>
 void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR, Waves<T>& W) {
   const int M = P.M;
@@ -250,7 +450,7 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
   for (int m = 0; m < M; ++m) {
     hbar[m] = 0.5 * (h[0][m] + h[1][m]);
     T coup = eta[1][m] - eta[0][m];
-    if (m == 1) coup = coup + P.r * (h[1][0] - h[0][0]);
+    for (int n = 0; n < m; ++n) coup = coup + density_ratio(P, n, m) * (h[1][n] - h[0][n]);
     d0[m] = hn[1][m] - hn[0][m];
     d1[m] = (hn[1][m] * un[1][m] - hn[0][m] * un[0][m]) + g * hbar[m] * coup;
     d2[m] = hn[1][m] * ut[1][m] - hn[0][m] * ut[0][m];
@@ -259,6 +459,10 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
   bool all_wet = true;
   for (int m = 0; m < M; ++m) all_wet = all_wet && wet[0][m] && wet[1][m];
 
+  if ((M >= 3 || (M == 2 && P.force_general)) && all_wet) {
+    coupled_waves_general(P, h, hn, un, ut, hbar, d0, d1, d2, W);
+    return;
+  }
   if (M == 2 && all_wet) {
     // Coupled branch: 4 acoustic f-waves of the 4x4 normal system, plus 2 shear waves.
     T uh[2], vh[2], c[2];
@@ -295,12 +499,13 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
     return;
   }
 
-  // Decoupled branch: every layer on its own. Wave slots: M = 1 -> (left, right, shear);
-  // M = 2 -> layer 1 (0, 3, 4), layer 2 (1, 2, 5).
+  // Decoupled branch: every layer on its own. Wave slots of layer m: m (left-going),
+  // 2M - 1 - m (right-going), 2M + m (shear): M = 1 -> (0, 1, 2); M = 2 -> layer 1 (0, 3, 4),
+  // layer 2 (1, 2, 5).
   for (int m = 0; m < M; ++m) {
-    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
-    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
-    const int ps = (M == 1) ? 2 : (m == 0 ? 4 : 5);
+    const int pa = m;
+    const int pb = 2 * M - 1 - m;
+    const int ps = 2 * M + m;
     const bool wl = wet[0][m], wr = wet[1][m];
     if (wl && wr) {
       const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
@@ -584,20 +789,22 @@ extern "C" {
 
 struct or_params {
   int M; double g; double r; double dry_tol; int order; int limiter; int eigen;
+  double rho[4];  // layer densities, top first (read for M >= 3 and by the general branch)
 };
 
 static Params to_params(const or_params* p) {
   Params P;
   P.M = p->M; P.g = p->g; P.r = p->r; P.dry_tol = p->dry_tol;
   P.order = p->order; P.limiter = p->limiter; P.eigen = p->eigen;
+  for (int m = 0; m < MAXM; ++m) P.rho[m] = p->rho[m];
   return P;
 }
 
-// Waves and fluctuations at one edge (normal direction n): Z[6][6], s[6], amdq[6], apdq[6],
-// info[0..1] wall marks per layer, info[2] hyperbolicity-loss flag.
-void or_riemann(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
-                double* Z, double* s, double* amdq, double* apdq, int* info) {
-  const Params P = to_params(pp);
+// Waves and fluctuations at one edge (normal direction n): Z[MAXW][MAXF], s[MAXW],
+// amdq[MAXF], apdq[MAXF]; info[0 .. MAXM-1] wall marks per layer, info[MAXM] the
+// hyperbolicity-loss flag. general = 1 takes the general coupled branch also for M = 2.
+static void riemann_out(const Params& P, const double* qL, const double* qR, double BL, double BR, double* Z,
+                        double* s, double* amdq, double* apdq, int* info) {
   Waves<double> W;
   riemann(P, qL, qR, BL, BR, W);
   for (int p = 0; p < MAXW; ++p) {
@@ -605,7 +812,20 @@ void or_riemann(const or_params* pp, const double* qL, const double* qR, double 
     for (int f = 0; f < MAXF; ++f) Z[p * MAXF + f] = W.Z[p][f];
   }
   fluctuations(P, W, amdq, apdq);
-  info[0] = W.wall_into[0]; info[1] = W.wall_into[1]; info[2] = W.hyperbolicity_lost;
+  for (int m = 0; m < MAXM; ++m) info[m] = W.wall_into[m];
+  info[MAXM] = W.hyperbolicity_lost;
+}
+
+void or_riemann(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
+                double* Z, double* s, double* amdq, double* apdq, int* info) {
+  riemann_out(to_params(pp), qL, qR, BL, BR, Z, s, amdq, apdq, info);
+}
+
+void or_riemann_general(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
+                        double* Z, double* s, double* amdq, double* apdq, int* info) {
+  Params P = to_params(pp);
+  P.force_general = 1;
+  riemann_out(P, qL, qR, BL, BR, Z, s, amdq, apdq, info);
 }
 
 void or_eigen(const or_params* pp, double u1, double u2, double hb1, double hb2, double* lam, int* lost) {

@@ -26,7 +26,12 @@ def _coarse_setup(seed, M=2, n=12, r=4, wet=True):
     eta2 = -4.0 + 0.2 * rng.standard_normal((n, n))
     eta1 = 0.0 + 0.2 * rng.standard_normal((n, n))
     q = np.zeros((3 * M, n, n))
-    if M == 2:
+    if M == 3:
+        eta3 = -7.0 + 0.2 * rng.standard_normal((n, n))
+        q[6] = eta3 - Bc
+        q[3] = eta2 - eta3
+        q[0] = eta1 - eta2
+    elif M == 2:
         q[3] = eta2 - Bc
         q[0] = eta1 - eta2
     else:
@@ -44,7 +49,7 @@ def _interp_all(P, q, Bc, Bf, r):
     return O.interp_fine(P, r, qp, Bp, (0, 0, n, n), Bf)
 
 
-@pytest.mark.parametrize("M", [1, 2])
+@pytest.mark.parametrize("M", [1, 2, 3])
 @pytest.mark.parametrize("r", [2, 4])
 def test_refinement_preserves_cell_means(M, r):
     """Sec. 2.1: the offsets (a + 1/2)/r - 1/2 sum to zero, so the fine surfaces average to
