@@ -134,6 +134,7 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
                           const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
                           cudaStream_t st) {
   if (M == 1) interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
+  else if (M == 3) interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
   else interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
   return cudaGetLastError();
 }
@@ -228,6 +229,7 @@ cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long 
                          double inv_dx, double inv_dy, double tol2, uint8_t* flags, cudaStream_t st) {
   const int grid = (int)std::max<long long>(1, std::min<long long>((cells + 255) / 256, 4096));
   if (M == 1) flags_kernel<1><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
+  else if (M == 3) flags_kernel<3><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
   else flags_kernel<2><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
   return cudaGetLastError();
 }
@@ -350,6 +352,7 @@ reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict_
 cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev, int grid,
                           int r, int par_c, cudaStream_t st) {
   if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
+  else if (M == 3) reflux_kernel<3><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
   else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
   return cudaGetLastError();
 }
@@ -397,6 +400,7 @@ cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, cons
                          const int* n_items_dev, int grid, const int* par_of_desc, unsigned long long* out,
                          cudaStream_t st) {
   if (M == 1) speed_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
+  else if (M == 3) speed_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
   else speed_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
   return cudaGetLastError();
 }

@@ -387,7 +387,7 @@ static mlswe_status autotune_level(Hier* H, int level, int iters, int* chosen) {
     float best = 1e30f;
     const TileShape cur = H->shape[level * 2 + dir];
     int bl = cur.len, bn = cur.lines, bc = cur.ctas;
-    for (int ctas = 1; ctas <= 2; ++ctas)
+    for (int ctas = 1; ctas <= (H->cfg.M >= 3 ? 1 : 2); ++ctas)
       for (const auto& c : cand) {
         set_level_shape(H, level, dir, c[0], c[1], ctas);
         mlswe_status s = ensure_worklist(H, level, dir);

@@ -33,7 +33,8 @@ constexpr int kThreads = 256;
 struct DevParams {
   int M;
   double g;
-  double r;        // rho_1 / rho_2
+  double r;        // rho_1 / rho_2 (M = 2)
+  double rho[4];   // layer densities, top (lightest) first
   double dry_tol;
   int order;
   int limiter;
@@ -134,6 +135,17 @@ __device__ __forceinline__ void batched_reciprocal(const double* x, double* inv)
 }
 
 
+// batched_reciprocal for any N, in groups of at most six.
+template <int N>
+__device__ __forceinline__ void batched_reciprocal_groups(const double* x, double* inv) {
+  if constexpr (N <= 6) {
+    batched_reciprocal<N>(x, inv);
+  } else {
+    batched_reciprocal<6>(x, inv);
+    batched_reciprocal_groups<N - 6>(x + 6, inv + 6);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Cell record staged in shared memory (fields already permuted to normal /
 // transverse for the sweep direction).
@@ -148,13 +160,13 @@ struct Rec {
   static constexpr int N = 7 * M + 1;
 };
 
-// Compressed waves of one edge: acoustic wave p is
-//   Z_p = (a_p, a_p s_p, a_p vh_1 | b_p, b_p s_p, b_p vh_2),
+// Compressed waves of one edge: acoustic wave p carries in layer m the mass mass[m][p], so
+//   Z_p = (mass[m][p], mass[m][p] s_p, mass[m][p] vh_m) for m = 1 .. M,
 // shear wave of layer m is (0, 0, z_m) on layer m with speed us_m.
 template <int M>
 struct EdgeW {
   static constexpr int NA = 2 * M;
-  double a[NA], b[NA], s[NA];
+  double mass[M][NA], s[NA];
   double z[M], us[M], vh[M];
   // What the acoustic waves of layer m sum to: its mass and normal-momentum flux jumps
   // (sum_p Z_p = jump exactly for the f-wave split, up to rounding).
@@ -163,9 +175,9 @@ struct EdgeW {
 };
 
 template <int M>
-struct WRec {  // shared-memory layout of EdgeW
-  static constexpr int A = 0, B = 2 * M, S = 4 * M, Z = 6 * M, US = 7 * M, VH = 8 * M, T0 = 9 * M, T1 = 10 * M,
-                       N = 11 * M;
+struct WRec {  // shared-memory layout of EdgeW: mass of layer m, wave p at A + 2M m + p
+  static constexpr int A = 0, S = 2 * M * M, Z = S + 2 * M, US = Z + M, VH = US + M, T0 = VH + M, T1 = T0 + M,
+                       N = T1 + M;
 };
 
 // Per-edge record of a coupled two-layer edge that the adjoint's reverse pass reads instead
@@ -180,10 +192,18 @@ struct FwdRec {
                        LAM = 15, ID0 = 19, ID1 = 23, IDEN = 27, BETA = 31, NEWTON = 35, N = 36;
 };
 
-// Layer of acoustic slot p in the per-layer (decoupled) branch.
+// Layer of acoustic slot p in the per-layer (decoupled) branch: layer m owns slots m
+// (left-going) and 2M - 1 - m (right-going).
 template <int M>
 __device__ __forceinline__ int layer_of_slot(int p) {
-  return (M == 1) ? 0 : ((p == 0 || p == 3) ? 0 : 1);
+  return p < M ? p : 2 * M - 1 - p;
+}
+
+// rho_n / rho_m: weight of the depth jump of the lighter layer n above in layer m's pressure.
+template <int M>
+__device__ __forceinline__ double density_ratio(const DevParams& P, int n, int m) {
+  if constexpr (M == 2) return P.r;
+  return P.rho[n] * rcp(P.rho[m]);
 }
 
 // Single-layer f-wave split of (d0, d1, d2) with speeds s1 < s2 (inv_ds: 1/(s2 - s1) when
@@ -195,14 +215,227 @@ __device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, d
   const double inv = inv_ds != 0.0 ? inv_ds : rcp(s2 - s1);
   const double b1 = (s2 * d0 - d1) * inv;
   const double b2 = (d1 - s1 * d0) * inv;
-  if (m == 0) { W.a[pa] = b1; W.a[pb] = b2; }
-  else { W.b[pa] = b1; W.b[pb] = b2; }
+  W.mass[m][pa] = b1;
+  W.mass[m][pb] = b2;
   W.s[pa] = s1; W.s[pb] = s2;
   W.z[m] = d2 - vh * d0;
   W.us[m] = us;
   W.vh[m] = vh;
   W.t0[m] = d0;
   W.t1[m] = d1;
+}
+
+// ---- general coupled branch (M >= 3 layers, all wet on both sides) ----
+
+// Eigenvalues of the symmetric M x M matrix K by cyclic Jacobi rotations (each rotation
+// zeroes one off-diagonal pair: tan phi = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
+// theta = (K_qq - K_pp) / (2 K_pq)), until the off-diagonal part is below 1e-32 of the
+// diagonal or 10 sweeps; mu in descending order.
+template <int M>
+__device__ __forceinline__ void jacobi_eigenvalues(double K[M][M], double mu[M]) {
+  for (int sweep = 0; sweep < 10; ++sweep) {
+    double off = 0.0, dg = 0.0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      dg = fma(K[i][i], K[i][i], dg);
+#pragma unroll
+      for (int j = i + 1; j < M; ++j) off = fma(K[i][j], K[i][j], off);
+    }
+    if (off <= 1e-32 * dg) break;
+#pragma unroll
+    for (int p = 0; p < M - 1; ++p)
+#pragma unroll
+      for (int q = p + 1; q < M; ++q) {
+        const double kpq = K[p][q];
+        if (kpq == 0.0) continue;
+        const double theta = (K[q][q] - K[p][p]) * (0.5 * rcp(kpq));
+        const double t = copysign(rcp(fabs(theta) + sqrt(fma(theta, theta, 1.0))), theta);
+        const double c = rsqrt(fma(t, t, 1.0)), sn = t * c;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const double kp = K[k][p], kq = K[k][q];
+          K[k][p] = c * kp - sn * kq;
+          K[k][q] = sn * kp + c * kq;
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const double pk = K[p][k], qk = K[q][k];
+          K[p][k] = c * pk - sn * qk;
+          K[q][k] = sn * pk + c * qk;
+        }
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < M; ++i) mu[i] = K[i][i];
+#pragma unroll
+  for (int i = 0; i < M; ++i)
+#pragma unroll
+    for (int j = i + 1; j < M; ++j) {
+      const double a = mu[i], b = mu[j];
+      mu[i] = fmax(a, b);
+      mu[j] = fmin(a, b);
+    }
+}
+
+// Solve A x = b (N x N) by Gaussian elimination with partial pivoting; every index is a
+// compile-time constant (row exchanges are selects), so A stays in registers.
+template <int N>
+__device__ __forceinline__ void gauss_solve(double A[N][N], double b[N], double x[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    int piv = k;
+    unsigned long long best = abs_bits(A[k][k]);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) {
+      const unsigned long long v = abs_bits(A[i][k]);
+      if (v > best) { best = v; piv = i; }
+    }
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) {
+      const bool sw = i == piv;
+#pragma unroll
+      for (int j = k; j < N; ++j) {
+        const double t = A[k][j];
+        A[k][j] = sw ? A[i][j] : t;
+        A[i][j] = sw ? t : A[i][j];
+      }
+      const double tb = b[k];
+      b[k] = sw ? b[i] : tb;
+      b[i] = sw ? tb : b[i];
+    }
+    const double ip = rcp(A[k][k]);
+#pragma unroll
+    for (int i = k + 1; i < N; ++i) {
+      const double f = A[i][k] * ip;
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) A[i][j] = fma(-f, A[k][j], A[i][j]);
+      b[i] = fma(-f, b[k], b[i]);
+    }
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    double sum = b[k];
+#pragma unroll
+    for (int j = k + 1; j < N; ++j) sum = fma(-A[k][j], x[j], sum);
+    x[k] = sum * rcp(A[k][k]);
+  }
+}
+
+// Coupled branch for M = 3 layers. The eigenvalues of the normal system at the Roe state are
+// the roots of P(l) = det(A(l)), A(l) = diag((l - u_m)^2) - G, G_mn = g hbar_m C_mn with
+// C_mn = 1 for n >= m and rho_n / rho_m for the lighter layers n < m. Guesses: the roots for
+// equal velocities, ubar -+ sqrt(mu_k), mu_k the eigenvalues of G (similar to the symmetric
+// K_mn = sqrt(w_m w_n) rho_min(m,n), w_m = g hbar_m / rho_m); then 2 Newton steps with
+// P' = sum_m 2 (l - u_m) cof_mm(A). Eigenvectors: dh_1 = 1 and the first two rows of
+// A(l) dh = 0 (Cramer); momenta l dh; strengths from the 6 x 6 system of the flux jumps.
+// Loss of hyperbolicity: some adjacent pair with (u_m - u_{m+1})^2 >= (1 - rho_m/rho_{m+1})
+// g (hbar_m + hbar_{m+1}); the guesses are used then (and for P.eigen = 1).
+template <int M>
+__device__ __forceinline__ void coupled_general(const DevParams& P, const double* cL, const double* cR,
+                                                const double* hb, const double* d0, const double* d1,
+                                                const double* d2, EdgeW<M>& W, int& lost) {
+  static_assert(M == 3, "general coupled branch written for three layers");
+  using R = Rec<M>;
+  constexpr int N = 2 * M;
+  const double g = P.g;
+  double uh[M], vh[M], G[M][M], K[M][M], wq[M], mu[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
+    const double inv = rcp(sl + sr);
+    uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
+    vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+    wq[m] = sqrt(g * hb[m] * rcp(P.rho[m]));
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int n = 0; n < M; ++n) {
+      G[m][n] = g * hb[m] * (n >= m ? 1.0 : density_ratio<M>(P, n, m));
+      K[m][n] = wq[m] * wq[n] * fmin(P.rho[m], P.rho[n]);
+    }
+  jacobi_eigenvalues<M>(K, mu);
+  double hs = 0.0, hus = 0.0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) { hs += hb[m]; hus = fma(hb[m], uh[m], hus); }
+  const double ubar = hus * rcp(hs);
+  double lam[N];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const double sq = sqrt(mu[k]);
+    lam[k] = ubar - sq;
+    lam[N - 1 - k] = ubar + sq;
+  }
+  bool lst = false;
+#pragma unroll
+  for (int m = 0; m + 1 < M; ++m) {
+    const double du = uh[m] - uh[m + 1];
+    lst = lst || (du * du >= (1.0 - P.rho[m] * rcp(P.rho[m + 1])) * g * (hb[m] + hb[m + 1]));
+  }
+  lost += lst ? 1 : 0;
+  auto build_A = [&](double l, double A[M][M]) {
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int n = 0; n < M; ++n) {
+        const double am = l - uh[m];
+        A[m][n] = (m == n ? am * am : 0.0) - G[m][n];
+      }
+  };
+  if (!lst && P.eigen == 0) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      double Pl[N], dP[N], idP[N];
+#pragma unroll
+      for (int p = 0; p < N; ++p) {
+        double A[M][M];
+        build_A(lam[p], A);
+        const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+        const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+        const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        Pl[p] = A[0][0] * c00 - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        dP[p] = 2.0 * ((lam[p] - uh[0]) * c00 + (lam[p] - uh[1]) * c11 + (lam[p] - uh[2]) * c22);
+      }
+      batched_reciprocal<N>(dP, idP);
+#pragma unroll
+      for (int p = 0; p < N; ++p) lam[p] -= Pl[p] * idP[p];
+    }
+  }
+  // eigenvectors (dh_1 = 1) and the strengths
+  double Rm[N][N], rhs[N], beta[N], dh[N][M];
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    double A[M][M];
+    build_A(lam[p], A);
+    const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    const double id2 = rcp(det2);
+    dh[p][0] = 1.0;
+    dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
+    dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      Rm[2 * m][p] = dh[p][m];
+      Rm[2 * m + 1][p] = lam[p] * dh[p][m];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) { rhs[2 * m] = d0[m]; rhs[2 * m + 1] = d1[m]; }
+  gauss_solve<N>(Rm, rhs, beta);
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) W.mass[m][p] = beta[p] * dh[p][m];
+    W.s[p] = lam[p];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    W.z[m] = d2[m] - vh[m] * d0[m];
+    W.us[m] = uh[m];
+    W.vh[m] = vh[m];
+    W.t0[m] = d0[m];
+    W.t1[m] = d1[m];
+  }
 }
 
 // Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
@@ -219,7 +452,11 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
   using R = Rec<M>;
   const double g = P.g;
 #pragma unroll
-  for (int p = 0; p < 2 * M; ++p) { W.a[p] = 0.0; W.b[p] = 0.0; W.s[p] = 0.0; }
+  for (int p = 0; p < 2 * M; ++p) {
+    W.s[p] = 0.0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) W.mass[m][p] = 0.0;
+  }
 #pragma unroll
   for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; }
   W.wall = 0;
@@ -231,13 +468,14 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     const double hnL = cL[3 * m + 1], hnR = cR[3 * m + 1];
     hb[m] = 0.5 * (hL + hR);
     double coup = cR[R::ETA + m] - cL[R::ETA + m];
-    if (m == 1) coup += P.r * (cR[0] - cL[0]);
+#pragma unroll
+    for (int n = 0; n < m; ++n) coup += density_ratio<M>(P, n, m) * (cR[3 * n] - cL[3 * n]);
     d0[m] = hnR - hnL;
     d1[m] = (hnR * cR[R::UN + 2 * m] - hnL * cL[R::UN + 2 * m]) + g * hb[m] * coup;
     d2[m] = hnR * cR[R::UN + 2 * m + 1] - hnL * cL[R::UN + 2 * m + 1];
   }
   const int full = (1 << M) - 1;
-  if (M == 2 && wL == full && wR == full) {
+  if constexpr (M == 2) if (wL == full && wR == full) {
     // ---- coupled two-layer branch ----
     const double c1 = g * hb[0], c2 = g * hb[1];
     // one reciprocal for the Roe weights of both layers, the depth sum and c1
@@ -353,8 +591,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       put(FwdRec::BETA + p, beta);
       const double al = lam[p] - uh[0];
       const double alpha = (al * al - c1) * ic1;
-      W.a[p] = beta;
-      W.b[p] = beta * alpha;
+      W.mass[0][p] = beta;
+      W.mass[M - 1][p] = beta * alpha;
       W.s[p] = lam[p];
     }
 #pragma unroll
@@ -367,11 +605,17 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     }
     return;
   }
+  if constexpr (M >= 3) {
+    if (wL == full && wR == full) {
+      coupled_general<M>(P, cL, cR, hb, d0, d1, d2, W, lost);
+      return;
+    }
+  }
   // ---- per-layer branch ----
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const int pa = (M == 1) ? 0 : (m == 0 ? 0 : 1);
-    const int pb = (M == 1) ? 1 : (m == 0 ? 3 : 2);
+    const int pa = m;
+    const int pb = 2 * M - 1 - m;
     const bool wl = (wL >> m) & 1, wr = (wR >> m) & 1;
     const double hL = cL[3 * m], hR = cR[3 * m];
     if (wl && wr) {

@@ -320,10 +320,12 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
                                     const mlswe_allocator* alloc, void* cuda_stream, mlswe_h* out) {
   if (!cfg || !doms || !out || n_members <= 0) return MLSWE_EINVAL;
   *out = nullptr;
-  if (cfg->M < 1 || cfg->M > 2 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
+  if (cfg->M < 1 || cfg->M > 3 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
   if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
   if (cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->dry_tol >= 0.0) || !(cfg->g > 0.0)) return MLSWE_EINVAL;
-  if (cfg->M == 2 && !(cfg->rho[0] > 0.0 && cfg->rho[0] < cfg->rho[1])) return MLSWE_EINVAL;
+  if (cfg->M >= 2 && !(cfg->rho[0] > 0.0)) return MLSWE_EINVAL;
+  for (int m = 0; m + 1 < cfg->M; ++m)  // densities increase downwards (stable stratification)
+    if (!(cfg->rho[m] < cfg->rho[m + 1])) return MLSWE_EINVAL;
   for (int l = 0; l + 1 < cfg->max_levels; ++l)
     if (cfg->ratio[l] != 2 && cfg->ratio[l] != 4) return MLSWE_EINVAL;
   if (cfg->max_levels > 1 && (cfg->min_side < 1 || cfg->max_side < 2 * cfg->min_side)) return MLSWE_EINVAL;
@@ -345,6 +347,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   }
   if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
   H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  for (int m = 0; m < 4; ++m) H->dp.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
   cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
   H->parity.assign(H->L, 0);
@@ -352,9 +355,11 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->shape.resize(H->L * 2);
   for (int l = 0; l < H->L; ++l) {
     // Default tiles: 125-cell rows x 2 (x sweep), 125-cell columns x 2 (y sweep); 256 edges;
-    // 2 CTAs per SM (the autotuner's choice on every workload measured).
-    H->shape[l * 2] = TileShape{125, 2, 2};
-    H->shape[l * 2 + 1] = TileShape{125, 2, 2};
+    // 2 CTAs per SM (the autotuner's choice on every workload measured); one for three layers,
+    // whose sweep needs the whole register file and most of the shared memory.
+    const int ctas = cfg->M >= 3 ? 1 : 2;
+    H->shape[l * 2] = TileShape{125, 2, ctas};
+    H->shape[l * 2 + 1] = TileShape{125, 2, ctas};
   }
   H->t_ghost.resize(H->L);
   H->t_avg.resize(H->L);

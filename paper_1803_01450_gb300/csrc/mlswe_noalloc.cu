@@ -115,6 +115,7 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
   const int counts[2] = {(int)items[0].size(), (int)items[1].size()};
   DevParams P;
   P.M = cfg->M; P.g = cfg->g; P.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  for (int m = 0; m < 4; ++m) P.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   P.dry_tol = cfg->dry_tol; P.order = cfg->order; P.limiter = cfg->limiter; P.eigen = cfg->eigen;
 
   if (cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess) return MLSWE_ECUDA;

@@ -166,8 +166,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       const int es = eslot<DIR>(l, e, len, nl);
 #pragma unroll
       for (int p = 0; p < 2 * M; ++p) {
-        wav[(WR::A + p) * kMaxEdges + es] = W.a[p];
-        wav[(WR::B + p) * kMaxEdges + es] = W.b[p];
+#pragma unroll
+        for (int m = 0; m < M; ++m) wav[(WR::A + 2 * M * m + p) * kMaxEdges + es] = W.mass[m][p];
         wav[(WR::S + p) * kMaxEdges + es] = W.s[p];
       }
 #pragma unroll
@@ -214,7 +214,9 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       // Left-going parts L (A-dQ minus the correction flux); the right-going parts follow as
       // R = T - L, since the waves of a layer sum to its flux jump T (mass, normal momentum)
       // and the transverse row to vh T_mass + z.
-      double La = 0, Lsa = 0, Lb = 0, Lsb = 0;
+      double Lm[M], Lsm[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) { Lm[m] = 0.0; Lsm[m] = 0.0; }
       // Wave limiter: theta_p = zu_p / zz_p for the acoustic waves and zu_m / z_m for the shear
       // waves ((z_up z)/(z z) with z != 0), with one reciprocal for all of them.
       constexpr int NA = 2 * M, NR = 2 * M + M;
@@ -223,8 +225,9 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       bool act[NR];
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
-        const double a = wav[(WR::A + p) * kMaxEdges + es];
-        const double b = wav[(WR::B + p) * kMaxEdges + es];
+        double mp[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) mp[m] = wav[(WR::A + NA * m + p) * kMaxEdges + es];
         const double s = wav[(WR::S + p) * kMaxEdges + es];
         sc[p] = sign_class(s);
         const int lay = layer_of_slot<M>(p);
@@ -234,17 +237,21 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         num[p] = 0.0;
         if (act[p]) {
           const int eu = sc[p] > 0 ? esl : esr;
-          const double au = wav[(WR::A + p) * kMaxEdges + eu];
-          const double bu = wav[(WR::B + p) * kMaxEdges + eu];
           const double su = wav[(WR::S + p) * kMaxEdges + eu];
-          const double vu0 = wav[(WR::VH + 0) * kMaxEdges + eu];
           const double ss = 1.0 + s * s, su1 = 1.0 + s * su;
-          double zz = a * a * (ss + vh[0] * vh[0]);
-          double zu = a * au * (su1 + vh[0] * vu0);
-          if (M == 2) {
-            const double vu1 = wav[(WR::VH + (M - 1)) * kMaxEdges + eu];
-            zz += b * b * (ss + vh[M - 1] * vh[M - 1]);
-            zu += b * bu * (su1 + vh[M - 1] * vu1);
+          // Z_p . Z_p and Z_up . Z_p, layer by layer
+          double zz = 0.0, zu = 0.0;
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            const double mu_m = wav[(WR::A + NA * m + p) * kMaxEdges + eu];
+            const double vu = wav[(WR::VH + m) * kMaxEdges + eu];
+            if (m == 0) {
+              zz = mp[0] * mp[0] * (ss + vh[0] * vh[0]);
+              zu = mp[0] * mu_m * (su1 + vh[0] * vu);
+            } else {
+              zz += mp[m] * mp[m] * (ss + vh[m] * vh[m]);
+              zu += mp[m] * mu_m * (su1 + vh[m] * vu);
+            }
           }
           if (__double_as_longlong(zz) > 0) { den[p] = zz; num[p] = zu; }
           else act[p] = false;
@@ -266,11 +273,9 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         }
       }
       double iden[NR];
-      batched_reciprocal<NR>(den, iden);
+      batched_reciprocal_groups<NR>(den, iden);
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
-        const double a = wav[(WR::A + p) * kMaxEdges + es];
-        const double b = wav[(WR::B + p) * kMaxEdges + es];
         const double s = wav[(WR::S + p) * kMaxEdges + es];
         double corr = 0.0;
         if (act[p]) {
@@ -278,8 +283,12 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
           corr = (sc[p] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(s), 1.0) * phi;
         }
         const double cl = (sc[p] < 0 ? 1.0 : (sc[p] > 0 ? 0.0 : 0.5)) + corr;
-        const double ca = cl * a, cb = cl * b;
-        La += ca; Lsa += ca * s; Lb += cb; Lsb += cb * s;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const double cm = cl * wav[(WR::A + NA * m + p) * kMaxEdges + es];
+          Lm[m] += cm;
+          Lsm[m] += cm * s;
+        }
       }
       double Lz[M], Rz[M];
 #pragma unroll
@@ -296,13 +305,11 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         Lz[m] = cl * z;
         Rz[m] = z - Lz[m];
       }
-      const double T0a = wav[(WR::T0 + 0) * kMaxEdges + es], T1a = wav[(WR::T1 + 0) * kMaxEdges + es];
-      Lc[0] = La; Lc[1] = Lsa; Lc[2] = vh[0] * La + Lz[0];
-      Rc[0] = T0a - La; Rc[1] = T1a - Lsa; Rc[2] = vh[0] * Rc[0] + Rz[0];
-      if (M == 2) {
-        const double T0b = wav[(WR::T0 + M - 1) * kMaxEdges + es], T1b = wav[(WR::T1 + M - 1) * kMaxEdges + es];
-        Lc[3] = Lb; Lc[4] = Lsb; Lc[5] = vh[M - 1] * Lb + Lz[M - 1];
-        Rc[3] = T0b - Lb; Rc[4] = T1b - Lsb; Rc[5] = vh[M - 1] * Rc[3] + Rz[M - 1];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const double T0 = wav[(WR::T0 + m) * kMaxEdges + es], T1 = wav[(WR::T1 + m) * kMaxEdges + es];
+        Lc[3 * m] = Lm[m]; Lc[3 * m + 1] = Lsm[m]; Lc[3 * m + 2] = vh[m] * Lm[m] + Lz[m];
+        Rc[3 * m] = T0 - Lm[m]; Rc[3 * m + 1] = T1 - Lsm[m]; Rc[3 * m + 2] = vh[m] * Rc[3 * m] + Rz[m];
       }
 #pragma unroll
       for (int m = 0; m < M; ++m) {
@@ -386,7 +393,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 }
 
 size_t sweep_smem_bytes(int M) {
-  const int rn = 7 * M + 1, wn = 11 * M;
+  const int rn = 7 * M + 1, wn = 2 * M * M + 7 * M;
   return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
 }
 
@@ -420,10 +427,15 @@ static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc*
                        : launch_sweep_t<M, DIR, 1, true>(P, descs, items, n_items_dev, grid, parity, record,
                                                           smax_bits, lost_count, st, est, eplane);
   }
-  return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false>(P, descs, items, n_items_dev, grid, parity, record,
-                                                       smax_bits, lost_count, st, nullptr, 0)
-                   : launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record,
-                                                       smax_bits, lost_count, st, nullptr, 0);
+  if constexpr (M >= 3) {  // three layers fill the register file and shared memory: one CTA per SM
+    return launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                            lost_count, st, nullptr, 0);
+  } else {
+    return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                         smax_bits, lost_count, st, nullptr, 0)
+                     : launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                         smax_bits, lost_count, st, nullptr, 0);
+  }
 }
 
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
@@ -435,6 +447,11 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
     return dir == 0 ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0)
                     : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0);
+  if (P.M == 3)
+    return dir == 0 ? launch_sweep_m<3, 0>(1, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0)
+                    : launch_sweep_m<3, 1>(1, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0);
   return dir == 0 ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
                                          lost_count, st, est, eplane)

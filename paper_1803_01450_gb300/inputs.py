@@ -82,6 +82,32 @@ def layered_state(B, eta1, eta2):
     return np.stack([h1, z, z.copy(), h2, z.copy(), z.copy()])
 
 
+def stacked_state(B, etas):
+    """Conserved fields [3M][ny][nx] of M layers at rest whose upper surfaces are etas (top
+    layer first) above the ground B. A layer absent where the ground or the layers below
+    reach above its surface gets depth 0."""
+    M = len(etas)
+    q = np.zeros((3 * M,) + np.shape(B))
+    lower = np.asarray(B, dtype=float)
+    for m in range(M - 1, -1, -1):
+        top = np.maximum(np.broadcast_to(etas[m], lower.shape), lower)
+        q[3 * m] = top - lower
+        lower = top
+    return q
+
+
+def shore3(n: int, seed: int = 3000, L: float = 1e5, n_humps: int = 8):
+    """Three-layer shore workload on an n x n grid: surfaces humps / -50 m / -200 m over the
+    shore bathymetry, so both lower layers meet the rising ground before the top one."""
+    x = centers(0.0, L, n)
+    X, Y = np.meshgrid(x, x)
+    B = shore_B(X)
+    A, w, xc, yc = humps(seed, n_humps, L)
+    eta1 = hump_field(X, Y, A, w, xc, yc)
+    q = stacked_state(B, (eta1, -50.0 + 0.0 * X, -200.0 + 0.0 * X))
+    return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
+
+
 def small(n: int = 50):
     x = centers(0.0, 1.0, n)
     X, Y = np.meshgrid(x, x)

@@ -60,7 +60,16 @@ static double family(JacFn jac, int eigen, double d1, double d2, double spread, 
                      double shear, int trials, unsigned seed) {
   const double g = 9.81, r = M == 2 ? 1025.0 / 1028.0 : 1.0;
   OrParams op{M, g, r, 1e-6, 1, 2, eigen, {1025.0, 1028.0, 0.0, 0.0}};
-  DevParams P{M, g, r, 1e-6, 1, 2, eigen};
+  DevParams P{};
+  P.M = M;
+  P.g = g;
+  P.r = r;
+  P.rho[0] = 1025.0;
+  P.rho[1] = 1028.0;
+  P.dry_tol = 1e-6;
+  P.order = 1;
+  P.limiter = 2;
+  P.eigen = eigen;
   std::mt19937_64 rng(seed);
   std::normal_distribution<double> N01(0.0, 1.0);
   double worst = 0.0;
