@@ -13,7 +13,8 @@ Also reported on the same line:
   * ``ensemble``: 256 members of sizes U{128..512}^2 with a refined level (ratio 4), all
     members stepped together with per-member time steps, batched versus per-patch;
   * ``adjoint``: gauge-misfit gradient on a 512^2 grid over 200 first-order steps with a
-    checkpoint every 20 steps: backward (recomputation + transposed steps) over forward.
+    checkpoint every 20 steps: backward (recomputation + transposed steps) over forward;
+  * ``three_layers``: the headline workload with three layers (general M-layer solver).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlswe|reference]
 
@@ -46,6 +47,8 @@ M_LAYERS = 2
 # eigenvalue guesses + 2 Newton steps), counted by the oracle's counting scalar on the
 # headline workload: `python -m oracle.count_flops`. Half of it belongs to each sweep.
 FP64_FLOP_PER_CELL_UPDATE = 1293.25
+# The same count for the three-layer version of the workload (inputs.scale3).
+FP64_FLOP_PER_CELL_UPDATE_3 = 4134.82
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
@@ -319,13 +322,48 @@ def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
             "forward_lcups": n * n * M_LAYERS * steps / (fwd * 1e-3), "loss": loss}
 
 
+def bench_three_layers(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
+    """The headline workload with three layers (surfaces humps / -100 m / -600 m over the same
+    shelf, densities 1000 / 1020 / 1030): the general M-layer coupled branch in deep water, the
+    per-layer branch on the shelf where the bottom layer ends."""
+    w = I.scale3(n, seed=1000)
+    cfg = pkg.Config(M=3, rho=(1000.0, 1020.0, 1030.0), dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)], stream=stream.cuda_stream)
+    H.set_bathymetry(0, w["B"])
+    H.set_state(0, 0, w["q"])
+    tiles = H.autotune(0, iters=2)
+    H.set_dt(0, 0.9 * w["dx"] / 205.0)
+    for _ in range(warmup):
+        H.step_level(0)
+    torch.cuda.synchronize()
+    H.timing(enable=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        H.step_level(0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    per_kernel, _ = H.timing(enable=False)
+    H.close()
+    sx_ms, sx_n = per_kernel["sweep_x"]
+    x_ms = sx_ms / max(1, sx_n)
+    ach = 0.5 * FP64_FLOP_PER_CELL_UPDATE_3 * n * n / (x_ms * 1e-3) / 1e12
+    return {"workload": f"{n}^2 shelf, 3 layers (humps / -100 m / -600 m), order 2 MC, walls",
+            "lcups": n * n * 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "sweep_x_ms": x_ms,
+            "flop_per_cell_update": FP64_FLOP_PER_CELL_UPDATE_3, "achieved_tflops": ach,
+            "frac_of_fp64_peak": ach / FP64_PEAK_TFLOPS, "tiles": tiles}
+
+
 def run_only(name):
     import torch
     import paper_1803_01450_gb300 as pkg
     pkg.build()
     stream = torch.cuda.Stream()
-    fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint}[name]
-    key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint"}[name]
+    fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint,
+          "three": bench_three_layers}[name]
+    key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint", "three": "three_layers"}[name]
     print(json.dumps({key: fn(pkg, torch, stream)}), flush=True)
 
 
@@ -426,6 +464,7 @@ def run_gpu(args):
         line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
         line["ensemble"] = bench_ensemble(pkg, torch, stream)
         line["adjoint"] = bench_adjoint(pkg, torch, stream)
+        line["three_layers"] = bench_three_layers(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -442,7 +481,7 @@ def main():
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
-    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint"],
+    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three"],
                     help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()
     if args.only:

@@ -1,7 +1,8 @@
 """Prints the algorithmic FP64 operation count per cell update of the method (one x sweep
 plus one y sweep, second order with the MC limiter, eigenvalue guesses plus two Newton
 steps), counted by the oracle's counting scalar on interior rows and columns of the
-2048 x 2048 shelf workload. Run: python -m oracle.count_flops
+2048 x 2048 shelf workload (two layers; and its three-layer version). Run:
+python -m oracle.count_flops
 
 TEST/MEASUREMENT INFRASTRUCTURE: the constant in bench.py comes from this script."""
 import os
@@ -21,6 +22,11 @@ def main():
         f = O.flops_per_cell_update(P, w["q"], w["B"], w["dx"], w["dy"], dt, rows=[100, 1024, 1900],
                                     cols=[100, 1024, 1900])
         print(f"order={order} eigen={eigen}: {f:.2f} FP64 operations per cell update")
+    w3 = I.scale3(2048)
+    P3 = O.params(M=3, dry_tol=1e-3, order=2, rho=(1000.0, 1020.0, 1030.0))
+    f3 = O.flops_per_cell_update(P3, w3["q"], w3["B"], w3["dx"], w3["dy"], dt, rows=[100, 1024, 1900],
+                                 cols=[100, 1024, 1900])
+    print(f"three layers (scale3 workload), order=2 eigen=0: {f3:.2f} FP64 operations per cell update")
 
 
 if __name__ == "__main__":

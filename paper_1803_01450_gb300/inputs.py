@@ -131,6 +131,18 @@ def scale(n: int = 2048, seed: int = 1000, L: float = 1e5):
     return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
 
 
+def scale3(n: int = 2048, seed: int = 1000, L: float = 1e5):
+    """Three-layer version of the scale workload: the same shelf and humps, surfaces
+    humps / -100 m / -600 m (the bottom layer ends where the shelf rises above -600 m)."""
+    x = centers(0.0, L, n)
+    X, Y = np.meshgrid(x, x)
+    B = shelf_B(X)
+    A, w, xc, yc = humps(seed, 8, L)
+    eta1 = hump_field(X, Y, A, w, xc, yc)
+    q = stacked_state(B, (eta1, -100.0 + 0.0 * X, -600.0 + 0.0 * X))
+    return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
+
+
 def shore_bathymetry(nx: int, ny: int, L: float = 1e5):
     x = centers(0.0, L, nx)
     y = centers(0.0, L, ny)
