@@ -82,6 +82,12 @@ typedef struct {
  *  regrid_interval  coarse steps between regrids inside mlswe_advance (0: never).
  *  n_buf        flag dilation in cells; cluster_eff: minimum box efficiency;
  *  min_side, max_side  patch side bounds in fine cells.
+ *  dynamic_rt   0: time ratio r_t = ratio[l] on every level (the CFL-safe choice,
+ *               Sec. 2); 1: each coarse step chooses r_t of every level as the fewest
+ *               steps per parent step that keep the level's Courant number at
+ *               cfl_desired, ceil(dt_parent * rate / cfl_desired) within [1, ratio],
+ *               from the wave speeds of the previous step (Sec. 2: a smaller r_t
+ *               where the refined region is shallow, as GeoClaw does).
  */
 typedef struct {
   int M;
@@ -101,6 +107,7 @@ typedef struct {
   double cluster_eff;
   int min_side;
   int max_side;
+  int dynamic_rt;
 } mlswe_config;
 
 /* Physical extent [x0,x1] x [y0,y1] and coarse (level 0) cell counts of a member. */

@@ -5,7 +5,11 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Paper passages followed:
 * Sec. 2, Eqs. (1)-(2): dx^{l+1} = dx^l / r^l; time ratio r_t^l = max(r_x, r_y) = r^l
-  (the fixed choice; GeoClaw's dynamic ratio is not used).
+  (the fixed choice), or with dynamic_rt the ratio GeoClaw chooses per step (Sec. 2): the
+  fewest steps of level l per step of its parent that keep its Courant number at cfl,
+  r_t = ceil(dt_parent * rate_l / cfl) within [1, r^l], rate_l the level's largest
+  speed / cell size from the previous step (or from the initial speeds); the first step
+  after a regrid takes r^l (those speeds were measured on the old patches).
 * Sec. 2.1 refinement (Eqs. (4), (5), (10), bottom-up layer loop) for new fine cells
   and for fine ghost cells (after linear interpolation of the coarse state in time).
 * Sec. 2.2, Eq. (11): coarse cells under fine patches take the mean of their fine cells,
@@ -19,6 +23,8 @@ Storage mirrors the problem, not the GPU: every level is a dense numpy array ove
 domain; each patch is stepped as its own array with a filled ghost ring.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -49,8 +55,9 @@ class Level:
 
 class OracleAMR:
     def __init__(self, P, domain, nx0, ny0, max_levels, ratios, B_finest, flag_tol=1e-3, n_buf=2,
-                 cluster_eff=0.7, min_side=16, max_side=64, cfl=0.9, n_nest=2):
+                 cluster_eff=0.7, min_side=16, max_side=64, cfl=0.9, n_nest=2, dynamic_rt=False):
         self.P = P
+        self.dynamic_rt = dynamic_rt
         self.M = P.M
         self.F = 3 * P.M
         self.x0, self.y0, self.x1, self.y1 = domain
@@ -75,6 +82,9 @@ class OracleAMR:
         self.t = 0.0
         self.dt = None
         self.smax = [np.zeros(2) for _ in range(max_levels)]
+        self.rates = [0.0] * max_levels   # largest speed / cell size per level, for the next step
+        self.fresh = False                # this coarse step follows a regrid: fixed ratios
+        self.level_steps = [0] * max_levels
 
     # ------------------------------------------------------------------ helpers
     def set_state(self, level, q):
@@ -250,10 +260,19 @@ class OracleAMR:
                 V.acc_x = np.zeros((self.M, V.ny, V.nx + 1))
                 V.acc_y = np.zeros((self.M, V.ny + 1, V.nx))
 
+    def time_ratio(self, l, dt_parent):
+        """Steps of level l per step of its parent (l >= 1)."""
+        r = self.r[l - 1]
+        if not self.dynamic_rt or self.fresh or self.rates[l] <= 0.0:
+            return r
+        need = math.ceil((dt_parent * self.rates[l]) / self.cfl)
+        return min(r, max(1, need))
+
     def advance_level(self, l, dt, alpha):
         self.step_level(l, dt, alpha)
+        self.level_steps[l] += 1
         if l + 1 < self.L and self.lev[l + 1].patches:
-            rt = self.r[l]
+            rt = self.time_ratio(l + 1, dt)
             for s in range(rt):
                 self.advance_level(l + 1, dt / rt, s / rt)
             self.average_down(l)
@@ -281,6 +300,7 @@ class OracleAMR:
                 umax = np.maximum(umax, np.maximum(u, v))
             s = umax + np.sqrt(g * np.maximum(htot, 0.0))
             smax = s[m].max()
+            self.rates[l] = smax / min(V.dx, V.dy)
             if smax > 0:
                 best = min(best, fac * min(V.dx, V.dy) / smax)
         return self.cfl * best
@@ -294,6 +314,7 @@ class OracleAMR:
             if not V.patches:
                 continue
             rate = max(self.smax[l][0] / V.dx, self.smax[l][1] / V.dy)
+            self.rates[l] = rate
             if rate > 0:
                 best = min(best, fac / rate)
         return self.cfl * best
@@ -303,9 +324,11 @@ class OracleAMR:
         for k in range(n_coarse_steps):
             if regrid_interval and k % regrid_interval == 0 and self.L > 1:
                 self.regrid(0)
+                self.fresh = True  # the last speeds were measured on the old patches
             step_dt = dt if dt is not None else (self.initial_dt() if self.dt is None else self.next_dt())
             self.smax = [np.zeros(2) for _ in range(self.L)]
             self.advance_level(0, step_dt, 0.0)
+            self.fresh = False
             self.dt = step_dt
             self.t += step_dt
 

@@ -39,7 +39,7 @@ class _Config(ctypes.Structure):
                 ("order", ctypes.c_int), ("limiter", ctypes.c_int), ("eigen", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("ratio", ctypes.c_int * 4), ("flag_tol", ctypes.c_double),
                 ("regrid_interval", ctypes.c_int), ("n_buf", ctypes.c_int), ("cluster_eff", ctypes.c_double),
-                ("min_side", ctypes.c_int), ("max_side", ctypes.c_int)]
+                ("min_side", ctypes.c_int), ("max_side", ctypes.c_int), ("dynamic_rt", ctypes.c_int)]
 
 
 class _Domain(ctypes.Structure):
@@ -75,6 +75,7 @@ class Config:
     cluster_eff: float = 0.7
     min_side: int = 16
     max_side: int = 64
+    dynamic_rt: int = 0
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -89,6 +90,7 @@ class Config:
             c.ratio[k] = rat[k]
         c.flag_tol = self.flag_tol; c.regrid_interval = self.regrid_interval; c.n_buf = self.n_buf
         c.cluster_eff = self.cluster_eff; c.min_side = self.min_side; c.max_side = self.max_side
+        c.dynamic_rt = int(self.dynamic_rt)
         return c
 
 

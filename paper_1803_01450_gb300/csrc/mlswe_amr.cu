@@ -46,11 +46,14 @@ __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* 
 }
 
 // mode 0: write every cell of the item box; mode 1: only in-domain cells outside every
-// patch of the fine level (ghost cells). alpha < 0: read alpha from alpha_dev.
+// patch of the fine level (ghost cells). substep >= 0 (ghost fill inside a coarse step): the
+// coarse state is taken at alpha = substep / rt of the fine level's member, and items of
+// members whose fine level is not active in this substep are skipped; substep < 0: alpha.
 template <int M>
 __global__ void __launch_bounds__(256)
 interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha, int mode) {
+              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha_in, int mode,
+              int substep) {
   constexpr int F = 3 * M;
   const int n_items = *n_items_dev;
   const double inv_r = 1.0 / (double)r;
@@ -58,6 +61,11 @@ interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
+    double alpha = alpha_in;
+    if (substep >= 0) {
+      if (Fd.active != nullptr && *Fd.active == 0) continue;
+      alpha = (double)substep / (double)(*Fd.rt);
+    }
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
     const int total = w * h;
     const double* qo = C.q[par_c ^ 1];
@@ -132,10 +140,29 @@ interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem
 
 cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
                           const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
-                          cudaStream_t st) {
-  if (M == 1) interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
-  else if (M == 3) interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
-  else interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode);
+                          cudaStream_t st, int substep) {
+  if (M == 1)
+    interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+  else if (M == 3)
+    interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+  else
+    interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+  return cudaGetLastError();
+}
+
+// Start of substep k of `level` (>= 1) inside a coarse step: a member takes it when its
+// parent level's current substep is taken and k < rt of the level.
+__global__ void set_active_kernel(int L, int n_members, int level, int k, const int* __restrict__ rt,
+                                  int* __restrict__ active) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_members) return;
+  const int d = m * L + level;
+  active[d] = (active[d - 1] != 0 && k < rt[d]) ? 1 : 0;
+}
+
+cudaError_t launch_set_active(int L, int n_members, int level, int k, const int* rt, int* active,
+                              cudaStream_t st) {
+  set_active_kernel<<<(n_members + 127) / 128, 128, 0, st>>>(L, n_members, level, k, rt, active);
   return cudaGetLastError();
 }
 
@@ -153,6 +180,7 @@ average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpIte
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
+    if (C.active != nullptr && *C.active == 0) continue;  // the coarse level copied its state through
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
     const int total = w * h;
     const double* qf = Fd.q[par_f];
@@ -275,6 +303,7 @@ reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict_
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
+    if (C.active != nullptr && *C.active == 0) continue;  // no coarse step taken: nothing to correct
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
     const int total = w * h;
     double* qc = C.q[par_c];
@@ -422,28 +451,44 @@ __global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const u
   __syncthreads();
   if (m < A.n_members) {
     double best = INFINITY, fac = 1.0;
+    double rate[4] = {0.0, 0.0, 0.0, 0.0};
     for (int l = 0; l < A.L; ++l) {
       if (l > 0) fac *= A.ratio[l - 1];
       const int d = m * A.L + l;
       if (!A.has_patches[d]) continue;
-      double rate;
       if (initial) {
         const double s = __longlong_as_double((long long)init_bits[d]);
-        rate = s * fmax(A.inv_dx[d], A.inv_dy[d]);
+        rate[l] = s * fmax(A.inv_dx[d], A.inv_dy[d]);
       } else {
         const double sx = __longlong_as_double((long long)smax_bits[2 * d]);
         const double sy = __longlong_as_double((long long)smax_bits[2 * d + 1]);
-        rate = fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]);
+        rate[l] = fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]);
       }
-      if (rate > 0.0) best = fmin(best, fac / rate);
+      if (rate[l] > 0.0) best = fmin(best, fac / rate[l]);
     }
     const double dt0 = isfinite(best) ? A.cfl * best : 0.0;
+    // Time ratio of every level: the fixed r, or (dynamic) the fewest steps of the level per
+    // parent step that keep its Courant number at cfl: ceil(dt_parent rate / cfl), in [1, r].
     double dl = dt0;
+    long long steps = 1;
     for (int l = 0; l < A.L; ++l) {
-      if (l > 0) dl /= A.ratio[l - 1];
-      dt[m * A.L + l] = dl;
-      smax_bits[2 * (m * A.L + l)] = 0ull;
-      smax_bits[2 * (m * A.L + l) + 1] = 0ull;
+      const int d = m * A.L + l;
+      int rt = 1;
+      if (l > 0) {
+        rt = A.ratio[l - 1];
+        if (A.dynamic_rt && *A.fresh == 0 && rate[l] > 0.0) {
+          const double need = ceil((dl * rate[l]) / A.cfl);
+          rt = need < 1.0 ? 1 : (need < (double)rt ? (int)need : rt);
+        }
+        dl = dl / rt;
+      }
+      steps *= rt;
+      A.rt[d] = rt;
+      dt[d] = dl;
+      A.steps_acc[d] += steps;
+      A.cells_acc[d] += steps * A.cells[d];
+      smax_bits[2 * d] = 0ull;
+      smax_bits[2 * d + 1] = 0ull;
     }
   }
 }
@@ -470,6 +515,8 @@ __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, c
   }
   if (bad) atomicOr(status, 2u);
   t_member[m] += dt[m * A.L];
+  for (int l = 1; l < A.L; ++l) A.active[m * A.L + l] = 1;  // steps outside advance take every level
+  if (m == 0) *A.fresh = 0;
 }
 
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,

@@ -10,7 +10,7 @@ namespace mlswe {
 
 cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
                           const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
-                          cudaStream_t st);
+                          cudaStream_t st, int substep = -1);
 cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
                                  int grid, int r, int par_c, int par_f, cudaStream_t st);
 cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long long cells, double dry_tol,
@@ -75,6 +75,7 @@ static mlswe_status upload_table(Hier* H, DevTable<InterpItem>& T, const std::ve
 static mlswe_status build_tables(Hier* H) {
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   std::vector<int> has(H->n_members * H->L, 0);
+  std::vector<long long> cells(H->n_members * H->L, 0);
   std::vector<InterpItem> speed;
   for (int l = 0; l < H->L; ++l) {
     std::vector<InterpItem> ghost, avg, refl;
@@ -82,6 +83,7 @@ static mlswe_status build_tables(Hier* H) {
       const Level& V = H->mem[m].lev[l];
       const int d = H->desc_index(m, l);
       has[d] = V.patches.empty() ? 0 : 1;
+      for (const Box& b : V.patches) cells[d] += (long long)(b.i1 - b.i0) * (b.j1 - b.j0);
       for (const Box& b : V.patches) push_chunks(speed, d, d, b);
       if (l > 0) {
         const int dc = H->desc_index(m, l - 1);
@@ -109,6 +111,7 @@ static mlswe_status build_tables(Hier* H) {
   mlswe_status s = upload_table(H, H->t_speed, speed);
   if (s != MLSWE_OK) return s;
   CUDA_TRY(H, cudaMemcpyAsync(H->d_has, has.data(), has.size() * 4, cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(H->d_cells, cells.data(), cells.size() * 8, cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   H->tables_dirty = false;
   return MLSWE_OK;
@@ -219,20 +222,28 @@ static mlswe_status interp_boxes(Hier* H, int member, int coarse_level, const st
 }
 
 // ---- the subcycled coarse step (graph-capturable: no host syncs, tables on device) ----
-static mlswe_status enqueue_level_tree(Hier* H, int level, double alpha) {
+// Substep `substep` of `level` inside a coarse step (level 0: the coarse step itself): which
+// members take it (their time ratio of the level may be below the launch's substep count),
+// ghost cells at alpha = substep / rt, the level's sweeps, then the finer levels' substeps,
+// coarsening and reflux onto this level.
+static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
   int tok;
   if (level > 0) {
+    timer_begin(H, KC_OTHER, &tok);
+    CUDA_TRY(H, launch_set_active(H->L, H->n_members, level, substep, H->d_rt, H->d_active, H->st));
+    timer_end(H, tok);
     timer_begin(H, KC_GHOST, &tok);
     CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, H->t_ghost[level].d, H->t_ghost[level].d_count, grid_full(H),
-                              H->cfg.ratio[level - 1], H->parity[level - 1], H->parity[level], alpha, 1, H->st));
+                              H->cfg.ratio[level - 1], H->parity[level - 1], H->parity[level], 0.0, 1, H->st,
+                              substep));
     timer_end(H, tok);
   }
   mlswe_status s = enqueue_level_step(H, level, 1);
   if (s != MLSWE_OK) return s;
   if (level + 1 < H->L) {
-    const int rt = H->cfg.ratio[level];
+    const int rt = H->cfg.ratio[level];  // the most substeps any member takes
     for (int k = 0; k < rt; ++k) {
-      s = enqueue_level_tree(H, level + 1, (double)k / rt);
+      s = enqueue_level_tree(H, level + 1, k);
       if (s != MLSWE_OK) return s;
     }
     timer_begin(H, KC_AVERAGE, &tok);
@@ -252,11 +263,18 @@ static DtArgs dt_args(Hier* H) {
   A.L = H->L;
   A.n_members = H->n_members;
   for (int k = 0; k < 4; ++k) A.ratio[k] = H->cfg.ratio[k];
+  A.dynamic_rt = H->cfg.dynamic_rt;
   A.cfl = H->cfg.cfl_desired;
   A.cfl_max = H->cfg.cfl_max;
   A.has_patches = H->d_has;
   A.inv_dx = H->d_invdx;
   A.inv_dy = H->d_invdy;
+  A.rt = H->d_rt;
+  A.active = H->d_active;
+  A.fresh = H->d_fresh;
+  A.cells = H->d_cells;
+  A.steps_acc = H->d_steps_acc;
+  A.cells_acc = H->d_cells_acc;
   return A;
 }
 
@@ -266,7 +284,7 @@ static mlswe_status enqueue_coarse_step(Hier* H) {
   timer_begin(H, KC_OTHER, &tok);
   CUDA_TRY(H, launch_dt_begin(dt_args(H), H->d_smax, H->d_init, H->d_init_flag, H->d_dt, H->st));
   timer_end(H, tok);
-  mlswe_status s = enqueue_level_tree(H, 0, 0.0);
+  mlswe_status s = enqueue_level_tree(H, 0, 0);
   if (s != MLSWE_OK) return s;
   timer_begin(H, KC_OTHER, &tok);
   CUDA_TRY(H, launch_step_end(dt_args(H), H->d_smax, H->d_dt, H->d_t, H->d_cfl, H->d_status, H->d_cfl_count,
@@ -521,6 +539,8 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
     if (h->cfg.regrid_interval > 0 && h->L > 1 && h->coarse_steps % h->cfg.regrid_interval == 0) {
       s = regrid_internal(h, 0);
       if (s != MLSWE_OK) return s;
+      static const int one = 1;  // the next step takes the fixed time ratios
+      CUDA_TRY(h, cudaMemcpyAsync(h->d_fresh, &one, sizeof(int), cudaMemcpyHostToDevice, h->st));
     }
     if (h->tables_dirty) {
       s = build_tables(h);
@@ -535,13 +555,7 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
       s = coarse_step(h);
     }
     if (s != MLSWE_OK) return s;
-    h->coarse_steps++;
-    long long steps = 1;
-    for (int l = 0; l < h->L; ++l) {
-      if (l > 0) steps *= h->cfg.ratio[l - 1];
-      h->level_steps[l] += steps;
-      h->cell_updates[l] += steps * patch_cells(h, l);
-    }
+    h->coarse_steps++;  // level steps and cell updates are counted on the device (dt_begin)
   }
   unsigned int status = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));

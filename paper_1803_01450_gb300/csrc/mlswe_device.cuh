@@ -53,6 +53,10 @@ struct LevelDesc {
   double* fxf;         // boundary mass flux accumulators of this (fine) level, x edges
   double* fyf;         // y edges
   const double* dt;    // device scalar: time step of this member on this level
+  const int* rt;       // device scalar: time steps of this level per step of its parent
+  const int* active;   // device scalar: 0 while a substep beyond this member's rt runs for
+                       // others (the step then copies the state through and records nothing);
+                       // null: always active
   int NX, NY, P;
   double inv_dx, inv_dy;
 };

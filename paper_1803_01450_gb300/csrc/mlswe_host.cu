@@ -119,6 +119,8 @@ static mlswe_status upload_desc(Hier* H) {
       D.in_patch = V.in_patch; D.covered = V.covered;
       D.fxc = V.fxc; D.fyc = V.fyc; D.fxf = V.fxf; D.fyf = V.fyf;
       D.dt = H->d_dt + k;
+      D.rt = H->d_rt + k;
+      D.active = H->d_active + k;
       D.NX = V.NX; D.NY = V.NY; D.P = V.P;
       D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
       idx[k] = D.inv_dx; idy[k] = D.inv_dy;
@@ -323,6 +325,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   if (cfg->M < 1 || cfg->M > 3 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
   if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
   if (cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->dry_tol >= 0.0) || !(cfg->g > 0.0)) return MLSWE_EINVAL;
+  if (cfg->dynamic_rt < 0 || cfg->dynamic_rt > 1) return MLSWE_EINVAL;
   if (cfg->M >= 2 && !(cfg->rho[0] > 0.0)) return MLSWE_EINVAL;
   for (int m = 0; m + 1 < cfg->M; ++m)  // densities increase downwards (stable stratification)
     if (!(cfg->rho[m] < cfg->rho[m + 1])) return MLSWE_EINVAL;
@@ -427,8 +430,15 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->d_par = (int*)dev_alloc(H, nd * 4);
   H->d_init_flag = (int*)dev_alloc(H, 8);
   H->d_cfl_count = (unsigned long long*)dev_alloc(H, 8);
+  H->d_rt = (int*)dev_alloc(H, nd * 4);
+  H->d_fresh = (int*)dev_alloc(H, 8);
+  H->d_active = (int*)dev_alloc(H, nd * 4);
+  H->d_cells = (long long*)dev_alloc(H, nd * 8);
+  H->d_steps_acc = (long long*)dev_alloc(H, nd * 8);
+  H->d_cells_acc = (long long*)dev_alloc(H, nd * 8);
   if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_init || !H->d_lost || !H->d_status || !H->d_t || !H->d_cfl ||
-      !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag || !H->d_cfl_count) {
+      !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag || !H->d_cfl_count || !H->d_rt ||
+      !H->d_active || !H->d_cells || !H->d_steps_acc || !H->d_cells_acc || !H->d_fresh) {
     mlswe_destroy(H);
     return MLSWE_ENOMEM;
   }
@@ -443,6 +453,19 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   cudaMemsetAsync(H->d_has, 0, nd * 4, H->st);
   cudaMemsetAsync(H->d_init_flag, 0, 8, H->st);
   cudaMemsetAsync(H->d_cfl_count, 0, 8, H->st);
+  {
+    // time ratios (the fixed ones until a coarse step chooses), every level active
+    std::vector<int> rt(nd), act(nd, 1);
+    for (int m = 0; m < n_members; ++m)
+      for (int l = 0; l < H->L; ++l) rt[m * H->L + l] = l == 0 ? 1 : cfg->ratio[l - 1];
+    cudaMemcpyAsync(H->d_rt, rt.data(), nd * 4, cudaMemcpyHostToDevice, H->st);
+    cudaMemcpyAsync(H->d_active, act.data(), nd * 4, cudaMemcpyHostToDevice, H->st);
+    cudaMemsetAsync(H->d_cells, 0, nd * 8, H->st);
+    cudaMemsetAsync(H->d_fresh, 0, 8, H->st);
+    cudaMemsetAsync(H->d_steps_acc, 0, nd * 8, H->st);
+    cudaMemsetAsync(H->d_cells_acc, 0, nd * 8, H->st);
+    cudaStreamSynchronize(H->st);
+  }
   H->level_steps.assign(H->L, 0);
   H->cell_updates.assign(H->L, 0);
   if (upload_desc(H) != MLSWE_OK) { mlswe_destroy(H); return MLSWE_ECUDA; }
@@ -548,11 +571,23 @@ mlswe_status mlswe_get_stats(mlswe_h h, mlswe_stats* out) {
   CUDA_TRY(h, cudaMemcpyAsync(&exceeded, h->d_cfl_count, 8, cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaMemcpyAsync(cfl.data(), h->d_cfl, cfl.size() * 8, cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const int nd = h->n_members * h->L;
+  std::vector<long long> dsteps(nd), dcells(nd);
+  CUDA_TRY(h, cudaMemcpyAsync(dsteps.data(), h->d_steps_acc, nd * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(dcells.data(), h->d_cells_acc, nd * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   out->coarse_steps = h->coarse_steps;
   out->regrids = h->regrids;
   for (int l = 0; l < h->L && l < 4; ++l) {
-    out->level_steps[l] = h->level_steps[l];
-    out->cell_updates[l] = h->cell_updates[l];
+    // steps of mlswe_step_level (host) plus those of mlswe_advance (device: the largest over
+    // the members, whose time ratios may differ), cell updates summed over the members
+    long long most = 0, cells = 0;
+    for (int m = 0; m < h->n_members; ++m) {
+      most = std::max(most, dsteps[m * h->L + l]);
+      cells += dcells[m * h->L + l];
+    }
+    out->level_steps[l] = h->level_steps[l] + most;
+    out->cell_updates[l] = h->cell_updates[l] + cells;
     int np = 0;
     for (int m = 0; m < h->n_members; ++m) np += (int)h->mem[m].lev[l].patches.size();
     out->patches[l] = np;

@@ -137,6 +137,12 @@ struct Hier {
   std::vector<long long> level_steps;    // [L] steps taken per level
   std::vector<long long> cell_updates;   // [L] patch cells x steps per level, all members
   unsigned long long* d_cfl_count = nullptr;  // [1] member coarse steps above cfl_max
+  int* d_rt = nullptr;                 // [n_members * L] time ratio of each level (this step)
+  int* d_active = nullptr;             // [n_members * L] the level's current substep is taken
+  int* d_fresh = nullptr;              // [1] the next coarse step follows a regrid
+  long long* d_cells = nullptr;        // [n_members * L] cells inside the patches
+  long long* d_steps_acc = nullptr;    // [n_members * L] level steps of mlswe_advance
+  long long* d_cells_acc = nullptr;    // [n_members * L] cell updates of mlswe_advance
   LaunchTimer timer;
   long long kernel_launches = 0;   // every kernel this hierarchy launched
   void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
@@ -151,13 +157,23 @@ struct DtArgs {
   int L;
   int n_members;
   int ratio[4];
+  int dynamic_rt;           // 1: time ratio per level and step from the wave speeds
   double cfl, cfl_max;
   const int* has_patches;   // [member * L + l]
   const double* inv_dx;     // [member * L + l]
   const double* inv_dy;
+  int* rt;                  // [member * L + l] time steps of level l per parent step (written)
+  int* active;              // [member * L + l] substep activity, reset to 1 at the step end
+  int* fresh;               // [1] 1 on the first coarse step after a regrid: fixed ratios (the
+                            // last speeds were measured on the old patches); cleared at the end
+  const long long* cells;   // [member * L + l] cells inside the level's patches
+  long long* steps_acc;     // [member * L + l] level steps taken (accumulated)
+  long long* cells_acc;     // [member * L + l] cell updates taken (accumulated)
 };
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
                             int* init_flag, double* dt, cudaStream_t st);
+cudaError_t launch_set_active(int L, int n_members, int level, int k, const int* rt, int* active,
+                              cudaStream_t st);
 cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
                             double* cfl_reached, unsigned int* status, unsigned long long* cfl_count,
                             cudaStream_t st);

@@ -80,6 +80,20 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     const size_t plane = (size_t)NY * Pt;
     const double* __restrict__ qin = DIR == 0 ? D.q[parity] : D.qs;
     double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
+    if (D.active != nullptr && *D.active == 0) {
+      // This member's level takes no step in this substep (its time ratio is smaller than
+      // the substep count of the launch): copy the tile's cells through, record nothing.
+      const int ncp = nl * len;
+      for (int t = threadIdx.x; t < ncp; t += blockDim.x) {
+        int l, k;
+        if (DIR == 0) { l = t / len; k = t - l * len; }
+        else { k = t / nl; l = t - k * nl; }
+        const size_t o = DIR == 0 ? (size_t)(item.j0 + l) * Pt + (item.i0 + k) : (size_t)(item.j0 + k) * Pt + (item.i0 + l);
+#pragma unroll
+        for (int f = 0; f < F; ++f) qout[f * plane + o] = qin[f * plane + o];
+      }
+      continue;
+    }
     const double dt = *D.dt;
     const double nu = dt * (DIR == 0 ? D.inv_dx : D.inv_dy);
     const long long tol_bits = __double_as_longlong(P.dry_tol);

@@ -249,3 +249,66 @@ def test_amr_lake_at_rest_on_shelf():
         eta1 = V.B + V.q[3] + V.q[0]
         assert np.abs(eta1[m]).max() <= 1e-13 * 4000
         assert np.abs(V.q[[1, 2, 4, 5]][:, m]).max() <= 1e-13 * 4000
+
+
+def _shallow_region_amr(dynamic, n=32, r=4, steps=12):
+    """Two levels over a basin that is deep (-1) in the west and shallow (-0.05) in the east,
+    a hump in the shallow part: the refined patches sit where the waves are slow."""
+    P = O.params(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6)
+    nf = n * r
+    xf = (np.arange(nf) + 0.5) / nf
+    Xf, _ = np.meshgrid(xf, xf)
+    Bf = np.where(Xf < 0.5, -1.0, -0.05)
+    A = OracleAMR(P, (0, 0, 1, 1), n, n, 2, [r], Bf, flag_tol=2e-3, min_side=8, max_side=32, dynamic_rt=dynamic)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    B0 = O.bathy_average(Bf, r)
+    eta1 = 0.004 * np.exp(-((X - 0.75) ** 2 + (Y - 0.5) ** 2) / 0.004)
+    q = np.zeros((6, n, n))
+    q[3] = np.maximum(-0.02 - B0, 0.0)
+    q[0] = eta1 - np.maximum(-0.02, B0)
+    A.set_state(0, q)
+    return A, steps
+
+
+def test_dynamic_time_ratio_takes_fewer_fine_steps_within_cfl():
+    """Sec. 2: with refined patches only in shallow water the fine level needs fewer steps
+    per coarse step than the spatial ratio; each level's Courant number stays at cfl."""
+    A, steps = _shallow_region_amr(True)
+    A.advance(steps, regrid_interval=4)
+    assert A.level_steps[0] == steps
+    assert 0 < A.level_steps[1] < 4 * steps  # fewer than the fixed ratio's
+    # Courant number of the last step on each level from its speeds and time step
+    dt0 = A.dt
+    rt = A.time_ratio(1, dt0)
+    for l, dtl in ((0, dt0), (1, dt0 / rt)):
+        V = A.lev[l]
+        c = dtl * max(A.smax[l][0] / V.dx, A.smax[l][1] / V.dy)
+        assert c <= A.cfl * (1 + 1e-9) * 1.2, (l, c)  # speeds of this step vs the previous step's
+
+
+def test_dynamic_time_ratio_conserves_mass_and_rest():
+    A, steps = _shallow_region_amr(True)
+    A.advance(1, regrid_interval=4)
+    m0 = A.mass()
+    A.advance(steps, regrid_interval=4)
+    assert np.all(np.abs(A.mass() - m0) <= 1e-13 * np.abs(m0))
+    # lake at rest stays at rest with dynamic ratios
+    P = O.params(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6)
+    n, r = 24, 2
+    nf = n * r
+    xf = (np.arange(nf) + 0.5) / nf
+    Xf, Yf = np.meshgrid(xf, xf)
+    # a bump that keeps both layers wet (averaging across an internal shoreline, where a layer
+    # ends inside a coarse cell, does not keep the rest state: Sec. 2.2 holds away from shores)
+    Bf = -1.0 + 0.25 * np.exp(-((Xf - 0.6) ** 2 + (Yf - 0.5) ** 2) / 0.01)
+    R = OracleAMR(P, (0, 0, 1, 1), n, n, 2, [r], Bf, flag_tol=1e-9, min_side=8, max_side=32, dynamic_rt=True)
+    B0 = O.bathy_average(Bf, r)
+    q = np.zeros((6, n, n))
+    q[3] = np.maximum(-0.6 - B0, 0.0)
+    q[0] = 0.0 - np.maximum(-0.6, B0)
+    R.set_state(0, q)
+    R.set_patches(1, [(16, 16, 32, 32)])
+    R.interp_into(0, R.lev[0].q, R.lev[1].in_patch_mask())
+    R.advance(6)
+    assert np.abs(R.lev[0].q[[1, 2, 4, 5]]).max() <= 1e-13
