@@ -244,6 +244,57 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
             "autotuned_tiles": chosen}
 
 
+def bench_dynamic_rt(pkg, torch, stream, steps=6):
+    """Three levels refined on the coastal strip of the shore bathymetry (x in 86..99 km, 340 m
+    deep at most against 4000 m offshore), advanced with the fixed time ratios and with the
+    dynamic ones (fewest substeps that keep each level at the Courant target): simulated time
+    per wall second, level steps and cell updates per coarse step for both."""
+    n0, r = 512, 4
+    nf = n0 * r * r
+    L = 1e5
+    xf = I.centers(0.0, L, nf)
+    Bf = np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf)))
+    x0 = I.centers(0.0, L, n0)
+    X, Y = np.meshgrid(x0, x0)
+    eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
+    strip = [(int(8.6e4 / L * n0), 0, int(9.9e4 / L * n0), n0)]  # coarse cells over the coastal strip
+    l1 = I.random_layout(3300, n0 * r, n0 * r, 600, r, parents=strip, margin=2)
+    l2 = I.random_layout(3400, nf, nf, 2000, r, parents=l1, margin=2)
+    out = {"workload": "3 levels, 512^2 coarse, ratios 4,4, shore bathymetry, 8 humps; seeded layout of "
+                       f"{len(l1)} level-1 and {len(l2)} level-2 patches on the coastal strip (x 86..99 km, 30..340 m deep)",
+           "coarse_steps": steps}
+    for dyn in (0, 1):
+        cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16,
+                         max_side=64, dynamic_rt=dyn)
+        H = pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)], stream=stream.cuda_stream)
+        H.set_bathymetry(0, Bf)
+        B0 = H.get_bathymetry(0, 0)
+        H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
+        H.set_patches(0, 1, l1)
+        H.interp_fine(0, 0)
+        H.set_patches(0, 2, l2)
+        H.interp_fine(1, 0)
+        for l in range(3):
+            H.autotune(l, iters=2)
+        H.advance(1)
+        s0 = H.get_stats()
+        t0 = H.get_time()[0][0]
+        ms = _time_advance(torch, H, stream, steps)
+        s1 = H.get_stats()
+        t1 = H.get_time()[0][0]
+        H.close()
+        upd = sum(s1["cell_updates"]) - sum(s0["cell_updates"])
+        key = "dynamic" if dyn else "fixed"
+        out[key] = {"ms_per_coarse_step": ms / steps, "sim_seconds_per_wall_second": (t1 - t0) / (ms * 1e-3),
+                    "level_steps_per_coarse_step": [(b - a) / steps for a, b in
+                                                    zip(s0["level_steps"], s1["level_steps"])],
+                    "cell_updates_per_coarse_step": upd / steps,
+                    "lcups": upd * M_LAYERS / (ms * 1e-3), "last_cfl": s1["last_cfl"]}
+    out["dynamic_over_fixed_sim_rate"] = (out["dynamic"]["sim_seconds_per_wall_second"]
+                                          / out["fixed"]["sim_seconds_per_wall_second"])
+    return out
+
+
 def bench_ensemble(pkg, torch, stream, n_members=256, steps=3):
     """Ensemble of independent members, U{128..512}^2 coarse grids, one refined level."""
     r = 4
@@ -362,8 +413,9 @@ def run_only(name):
     pkg.build()
     stream = torch.cuda.Stream()
     fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint,
-          "three": bench_three_layers}[name]
-    key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint", "three": "three_layers"}[name]
+          "three": bench_three_layers, "dynrt": bench_dynamic_rt}[name]
+    key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint", "three": "three_layers",
+           "dynrt": "dynamic_time_ratio"}[name]
     print(json.dumps({key: fn(pkg, torch, stream)}), flush=True)
 
 
@@ -465,6 +517,7 @@ def run_gpu(args):
         line["ensemble"] = bench_ensemble(pkg, torch, stream)
         line["adjoint"] = bench_adjoint(pkg, torch, stream)
         line["three_layers"] = bench_three_layers(pkg, torch, stream)
+        line["dynamic_time_ratio"] = bench_dynamic_rt(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -481,7 +534,7 @@ def main():
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
-    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three"],
+    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "dynrt"],
                     help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()
     if args.only:

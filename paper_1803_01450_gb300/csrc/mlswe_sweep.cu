@@ -82,7 +82,10 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
     if (D.active != nullptr && *D.active == 0) {
       // This member's level takes no step in this substep (its time ratio is smaller than
-      // the substep count of the launch): copy the tile's cells through, record nothing.
+      // the substep count of the launch): the y sweep copies the tile's cells from the step's
+      // input to its output (the x sweep's scratch is skipped), nothing is recorded.
+      if (DIR == 0) continue;
+      const double* __restrict__ qsrc = D.q[parity];
       const int ncp = nl * len;
       for (int t = threadIdx.x; t < ncp; t += blockDim.x) {
         int l, k;
@@ -90,7 +93,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         else { k = t / nl; l = t - k * nl; }
         const size_t o = DIR == 0 ? (size_t)(item.j0 + l) * Pt + (item.i0 + k) : (size_t)(item.j0 + k) * Pt + (item.i0 + l);
 #pragma unroll
-        for (int f = 0; f < F; ++f) qout[f * plane + o] = qin[f * plane + o];
+        for (int f = 0; f < F; ++f) qout[f * plane + o] = qsrc[f * plane + o];
       }
       continue;
     }

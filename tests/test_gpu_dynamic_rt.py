@@ -15,6 +15,7 @@ TOL = 1e-11
 
 
 def _basin(n, r, shallow_east=True):
+    """Basin on n x n coarse cells, bathymetry at n * r per side (r: the product of the ratios)."""
     nf = n * r
     xf = (np.arange(nf) + 0.5) / nf
     Xf, _ = np.meshgrid(xf, xf)
@@ -33,7 +34,8 @@ def _basin(n, r, shallow_east=True):
 
 
 def _gpu(pkg, members, n, r, dynamic):
-    cfg = pkg.Config(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6, max_levels=2, ratio=[r], flag_tol=2e-3,
+    ratios = list(r) if isinstance(r, (list, tuple)) else [r]
+    cfg = pkg.Config(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6, max_levels=len(ratios) + 1, ratio=ratios, flag_tol=2e-3,
                      regrid_interval=4, n_buf=2, cluster_eff=0.7, min_side=8, max_side=32, dynamic_rt=dynamic)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, n, n)] * len(members))
     for k, (Bf, q) in enumerate(members):
@@ -43,18 +45,20 @@ def _gpu(pkg, members, n, r, dynamic):
 
 
 def _oracle(Bf, q, n, r, dynamic):
-    A = OracleAMR(O.params(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6), (0, 0, 1, 1), n, n, 2, [r], Bf,
+    ratios = list(r) if isinstance(r, (list, tuple)) else [r]
+    A = OracleAMR(O.params(M=2, rho=(1000.0, 1025.0), dry_tol=1e-6), (0, 0, 1, 1), n, n, len(ratios) + 1, ratios, Bf,
                   flag_tol=2e-3, min_side=8, max_side=32, dynamic_rt=dynamic)
     A.set_state(0, q)
     return A
 
 
 def _compare(H, k, A):
-    assert [tuple(b) for b in H.get_patches(k, 1).tolist()] == [tuple(b) for b in A.lev[1].patches]
     assert rel_err(H.get_state(k, 0), A.lev[0].q).max() < TOL
-    m = A.lev[1].in_patch_mask()
-    if m.any():
-        assert rel_err(H.get_state(k, 1)[:, m], A.lev[1].q[:, m]).max() < TOL
+    for l in range(1, A.L):
+        assert [tuple(b) for b in H.get_patches(k, l).tolist()] == [tuple(b) for b in A.lev[l].patches]
+        m = A.lev[l].in_patch_mask()
+        if m.any():
+            assert rel_err(H.get_state(k, l)[:, m], A.lev[l].q[:, m]).max() < TOL
 
 
 def test_dynamic_time_ratio_matches_oracle(mlswe_lib):
@@ -71,6 +75,22 @@ def test_dynamic_time_ratio_matches_oracle(mlswe_lib):
     st = H.get_stats()
     assert st["level_steps"] == A.level_steps, (st["level_steps"], A.level_steps)
     assert st["level_steps"][1] < r * steps  # the shallow fine level took fewer steps
+    H.close()
+
+
+def test_three_levels_dynamic_time_ratio_matches_oracle(mlswe_lib):
+    """Both refined levels choose their ratio (level 2 within each level-1 substep)."""
+    n, r, steps = 24, (2, 2), 8
+    Bf, q = _basin(n, 4)
+    H = _gpu(mlswe_lib, [(Bf, q)], n, r, 1)
+    A = _oracle(Bf, q, n, r, True)
+    for _ in range(steps // 4):
+        H.advance(4)
+        A.advance(4, regrid_interval=4)
+        _compare(H, 0, A)
+    assert H.get_stats()["level_steps"] == A.level_steps, (H.get_stats()["level_steps"], A.level_steps)
+    assert A.lev[2].patches and A.level_steps[2] < 4 * steps
+    assert abs(H.get_time()[0][0] - A.t) <= 1e-12 * A.t
     H.close()
 
 
