@@ -47,17 +47,19 @@ MAXM = 4  # layers the oracle supports (MAXM in mlswe_oracle.cpp)
 class Params(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("g", ctypes.c_double), ("r", ctypes.c_double),
                 ("dry_tol", ctypes.c_double), ("order", ctypes.c_int), ("limiter", ctypes.c_int),
-                ("eigen", ctypes.c_int), ("rho", ctypes.c_double * MAXM)]
+                ("eigen", ctypes.c_int), ("rho", ctypes.c_double * MAXM), ("unsplit", ctypes.c_int)]
 
 
-def params(M=2, g=9.81, rho=None, dry_tol=1e-3, order=2, limiter=2, eigen=0) -> Params:
+def params(M=2, g=9.81, rho=None, dry_tol=1e-3, order=2, limiter=2, eigen=0, unsplit=0) -> Params:
     """rho: layer densities, top (lightest) first; default 1000, 1025 for two layers and
-    1000, 1020, 1030, 1040 (first M) otherwise."""
+    1000, 1020, 1030, 1040 (first M) otherwise. unsplit: 1 for the unsplit step with
+    transverse Riemann solves (wave propagation in corner-transport form), 0 for
+    dimensional splitting."""
     if rho is None:
         rho = (1000.0, 1025.0) if M == 2 else (1000.0, 1020.0, 1030.0, 1040.0)[:M]
     r = rho[0] / rho[1] if M == 2 else 1.0
     rr = (ctypes.c_double * MAXM)(*(list(rho[:M]) + [0.0] * (MAXM - min(M, len(rho)))))
-    return Params(M, g, r, dry_tol, order, limiter, eigen, rr)
+    return Params(M, g, r, dry_tol, order, limiter, eigen, rr, unsplit)
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -73,6 +75,7 @@ def lib():
         L = _lib
         L.or_riemann.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _ip]
         L.or_riemann_general.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _ip]
+        L.or_transverse.argtypes = [_pp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]
         L.or_eigen.argtypes = [_pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip]
         L.or_sweep_line.argtypes = [_pp, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_sweep_line.restype = ctypes.c_double
@@ -121,6 +124,18 @@ def riemann(P: Params, qL, qR, BL, BR, general=False):
        info.ctypes.data_as(_ip))
     n = 3 * W
     return Z[:n, :n].copy(), s[:n].copy(), am[:n].copy(), ap[:n].copy(), np.concatenate([info[:W], info[MAXM:]])
+
+
+def transverse(P: Params, qL, qR, BL, BR, dq, general=False):
+    """Transverse split of the fluctuation dq (3M, normal-frame order (h, hn, ht) per layer)
+    at the edge (qL, qR, BL, BR): returns (bp, bm), the parts carried towards +t and -t."""
+    F = 3 * MAXM
+    pad = lambda v: _c(np.pad(np.asarray(v, float), (0, F - len(v))))
+    bp = np.zeros(F); bm = np.zeros(F)
+    lib().or_transverse(ctypes.byref(P), _d(pad(qL)), _d(pad(qR)), float(BL), float(BR), _d(pad(dq)), _d(bp),
+                        _d(bm), int(general))
+    n = 3 * P.M
+    return bp[:n].copy(), bm[:n].copy()
 
 
 def eigen(P: Params, u1, u2, hb1, hb2):
@@ -196,7 +211,8 @@ def fill_walls(M, qp, Bp=None, sides=15):
 
 
 def step_patch(P: Params, qp, Bp, dx, dy, dt, want_flux=False):
-    """One split step on a patch array with its ghost ring already filled (in place).
+    """One step (split, or unsplit with P.unsplit) on a patch array with its ghost ring
+    already filled (in place).
 
     Returns (smax[2], lost, fx, fy) with fx [M][ny][nx+1], fy [M][ny+1][nx] mass fluxes."""
     assert qp.flags.c_contiguous and Bp.flags.c_contiguous

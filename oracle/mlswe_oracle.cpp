@@ -53,6 +53,7 @@ struct Params {
   int limiter;    // 0 none, 1 minmod, 2 MC
   int eigen;      // 0: guesses + 2 Newton steps, 1: guesses only
   int force_general = 0;  // 1: the general coupled branch also for M = 2 (a check of it)
+  int unsplit = 0;        // 1: unsplit step with transverse Riemann solves (else split)
 };
 
 // ---------------------------------------------------------------------------
@@ -136,6 +137,12 @@ struct Waves {
   int nw;
   int wall_into[MAXM];  // -1 none, 0: the left cell is the dry wall side, 1: the right cell
   int hyperbolicity_lost;
+  // State of the edge that the transverse solve decomposes in (per layer): the depth whose
+  // gravity speed it takes, the normal and the transverse velocity; whether the layers were
+  // solved together, and which layers had a wet side.
+  T hbt[MAXM], unt[MAXM], utt[MAXM];
+  int coupled;
+  int active[MAXM];
 };
 
 // Eigenvalue guesses and Newton steps for the coupled two-layer system.
@@ -322,17 +329,15 @@ void jacobi_eigenvalues(int n, T K[MAXM][MAXM], T mu[MAXM]) {
 // and rows 1 .. M-1 of A(l) dh = 0; momenta l dh. Strengths from the 2M x 2M system.
 // Loss of hyperbolicity: some adjacent pair with (u_m - u_{m+1})^2 >= (1 - rho_m/rho_{m+1})
 // g (hbar_m + hbar_{m+1}); then the guesses are used.
+// Eigenvalues lam[0 .. 2M-1] (ascending guesses order) and eigenvector depths dh[p][m]
+// (dh_1 = 1) of the coupled M-layer system with velocities uh and mean depths hbar, as
+// described above; returns 1 when hyperbolicity is lost (the guesses are kept).
 template <class T>
-void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2][MAXM], T ut[2][MAXM],
-                           const T hbar[MAXM], const T d0[MAXM], const T d1[MAXM], const T d2[MAXM], Waves<T>& W) {
+int general_eigen(const Params& P, const T uh[MAXM], const T hbar[MAXM], T lam[2 * MAXM],
+                  T dh[2 * MAXM][MAXM]) {
   const int M = P.M, N = 2 * M;
   const double g = P.g;
-  T uh[MAXM], vh[MAXM], G[MAXM][MAXM];
-  for (int m = 0; m < M; ++m) {
-    const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
-    uh[m] = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
-    vh[m] = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
-  }
+  T G[MAXM][MAXM];
   for (int m = 0; m < M; ++m)
     for (int n = 0; n < M; ++n) G[m][n] = g * hbar[m] * (n >= m ? 1.0 : density_ratio(P, n, m));
   // guesses
@@ -344,7 +349,6 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
   T hsum = T(0.0), husum = T(0.0);
   for (int m = 0; m < M; ++m) { hsum = hsum + hbar[m]; husum = husum + hbar[m] * uh[m]; }
   const T ubar = husum / hsum;
-  T lam[2 * MAXM];
   for (int k = 0; k < M; ++k) {
     const T sq = sqrt(mu[k]);
     lam[k] = ubar - sq;
@@ -355,7 +359,6 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
     const T du = uh[m] - uh[m + 1];
     if (val(du * du) >= val((1.0 - P.rho[m] / P.rho[m + 1]) * g * (hbar[m] + hbar[m + 1]))) lost = 1;
   }
-  W.hyperbolicity_lost = lost;
   T A[MAXM][MAXM];
   if (!lost && P.eigen == 0) {
     for (int p = 0; p < N; ++p) {
@@ -371,8 +374,7 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
       lam[p] = l;
     }
   }
-  // eigenvectors and the strengths
-  T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM], beta[2 * MAXM], dh[2 * MAXM][MAXM];
+  // eigenvectors
   for (int p = 0; p < N; ++p) {
     const T l = lam[p];
     for (int m = 0; m < M; ++m)
@@ -386,11 +388,29 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
     }
     solve_n(M - 1, S, b, x);
     for (int m = 1; m < M; ++m) dh[p][m] = x[m - 1];
+  }
+  return lost;
+}
+
+template <class T>
+void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2][MAXM], T ut[2][MAXM],
+                           const T hbar[MAXM], const T d0[MAXM], const T d1[MAXM], const T d2[MAXM], Waves<T>& W) {
+  const int M = P.M, N = 2 * M;
+  T uh[MAXM], vh[MAXM];
+  for (int m = 0; m < M; ++m) {
+    const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
+    uh[m] = (sl * un[0][m] + sr * un[1][m]) / (sl + sr);
+    vh[m] = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
+  }
+  T lam[2 * MAXM], dh[2 * MAXM][MAXM];
+  W.hyperbolicity_lost = general_eigen(P, uh, hbar, lam, dh);
+  // the strengths
+  T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM], beta[2 * MAXM];
+  for (int p = 0; p < N; ++p)
     for (int m = 0; m < M; ++m) {
       R[2 * m][p] = dh[p][m];
-      R[2 * m + 1][p] = l * dh[p][m];
+      R[2 * m + 1][p] = lam[p] * dh[p][m];
     }
-  }
   for (int m = 0; m < M; ++m) { rhs[2 * m] = d0[m]; rhs[2 * m + 1] = d1[m]; }
   solve_n(N, R, rhs, beta);
   for (int p = 0; p < N; ++p) {
@@ -406,6 +426,8 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
     W.Z[N + m][3 * m + 2] = d2[m] - vh[m] * d0[m];
     W.s[N + m] = uh[m];
   }
+  W.coupled = 1;
+  for (int m = 0; m < M; ++m) { W.hbt[m] = hbar[m]; W.unt[m] = uh[m]; W.utt[m] = vh[m]; W.active[m] = 1; }
 }
 
 template <class T>
@@ -418,7 +440,12 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
     W.s[p] = T(0.0);
     for (int f = 0; f < MAXF; ++f) W.Z[p][f] = T(0.0);
   }
-  for (int m = 0; m < MAXM; ++m) W.wall_into[m] = -1;
+  for (int m = 0; m < MAXM; ++m) {
+    W.wall_into[m] = -1;
+    W.hbt[m] = T(0.0); W.unt[m] = T(0.0); W.utt[m] = T(0.0);
+    W.active[m] = 0;
+  }
+  W.coupled = 0;
 
   // Per-side cell quantities.
   T h[2][MAXM], hn[2][MAXM], ht[2][MAXM], un[2][MAXM], ut[2][MAXM], eta[2][MAXM], Bhat[2][MAXM];
@@ -496,6 +523,8 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
     }
     W.Z[4][2] = d2[0] - vh[0] * d0[0]; W.s[4] = uh[0];
     W.Z[5][5] = d2[1] - vh[1] * d0[1]; W.s[5] = uh[1];
+    W.coupled = 1;
+    for (int m = 0; m < 2; ++m) { W.hbt[m] = hbar[m]; W.unt[m] = uh[m]; W.utt[m] = vh[m]; W.active[m] = 1; }
     return;
   }
 
@@ -513,6 +542,7 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
       const T vh = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
       const T ch = sqrt(g * hbar[m]);
       single_layer_waves(m, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, pa, pb, ps, W);
+      W.hbt[m] = hbar[m]; W.unt[m] = uh; W.utt[m] = vh; W.active[m] = 1;
     } else if (!wl && !wr) {
       // Both sides dry: no waves for this layer.
     } else {
@@ -534,6 +564,7 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
         const T ch = sqrt(g * (0.5 * (hs[0] + hs[1])));
         single_layer_waves(m, e0, e1, e2, uh - ch, uh + ch, vh, uh, pa, pb, ps, W);
         W.wall_into[m] = d;
+        W.hbt[m] = 0.5 * (hs[0] + hs[1]); W.unt[m] = uh; W.utt[m] = vh; W.active[m] = 1;
       } else {
         // Flow onto a dry cell: real states, dry-front speed bound on the dry side.
         const T sl = sqrt(h[0][m]), sr = sqrt(h[1][m]);
@@ -545,6 +576,7 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
         if (d == 1) { s1 = tmin(un[0][m] - cw, uh - ch); s2 = un[0][m] + 2.0 * cw; }
         else { s1 = un[1][m] - 2.0 * cw; s2 = tmax(un[1][m] + cw, uh + ch); }
         single_layer_waves(m, d0[m], d1[m], d2[m], s1, s2, vh, uh, pa, pb, ps, W);
+        W.hbt[m] = hbar[m]; W.unt[m] = uh; W.utt[m] = vh; W.active[m] = 1;
       }
     }
   }
@@ -611,6 +643,74 @@ void positivity(const Params& P, T* q) {
   for (int m = 0; m < P.M; ++m) {
     if (val(q[3 * m]) < 0.0) q[3 * m] = T(0.0);
     if (val(q[3 * m]) <= P.dry_tol) { q[3 * m + 1] = T(0.0); q[3 * m + 2] = T(0.0); }
+  }
+}
+
+// Transverse Riemann solve (unsplit form): the fluctuation dq (3M, normal-frame order
+// (h, hn, ht) per layer) that an edge sends into one of its cells is split into the waves of
+// the transverse direction, at the state the edge was solved at (Roe velocities unt, utt and
+// depth hbt per layer). The transverse system is the normal one with the roles of the
+// velocities exchanged: acoustic eigenvalues mu_p of the (h, ht) block (the same coupled
+// problem with utt in place of unt), eigenvectors (dh_m, unt_m dh_m, mu_p dh_m) per layer,
+// and a shear wave per layer in hn with speed utt_m. bp gathers mu beta r of the waves with
+// mu > 0 (towards +t), bm those with mu < 0. Coupled edges decompose all layers together
+// (two layers: the closed-form guesses plus Newton steps of the normal solve; more layers:
+// the general branch), otherwise each layer with a wet side alone with speeds
+// utt_m -+ sqrt(g hbt_m); a layer dry on both sides sends nothing.
+template <class T>
+void transverse(const Params& P, const Waves<T>& W, const T* dq, T* bp, T* bm) {
+  const int M = P.M, F = 3 * M;
+  for (int f = 0; f < F; ++f) { bp[f] = T(0.0); bm[f] = T(0.0); }
+  auto send = [&](const T& speed, int f, const T& amount) {
+    const double sv = val(speed);
+    if (sv > 0.0) bp[f] = bp[f] + speed * amount;
+    else if (sv < 0.0) bm[f] = bm[f] + speed * amount;
+  };
+  if (W.coupled) {
+    const int N = 2 * M;
+    T mu[2 * MAXM], dh[2 * MAXM][MAXM], beta[2 * MAXM];
+    if (M == 2 && !P.force_general) {
+      int lost = 0;
+      two_layer_eigen(P, W.utt[0], W.utt[1], W.hbt[0], W.hbt[1], mu, &lost);
+      const T c1 = P.g * W.hbt[0];
+      T A[4][4], rhs[4];
+      for (int p = 0; p < 4; ++p) {
+        dh[p][0] = T(1.0);
+        dh[p][1] = ((mu[p] - W.utt[0]) * (mu[p] - W.utt[0]) - c1) / c1;
+        A[0][p] = dh[p][0]; A[1][p] = mu[p]; A[2][p] = dh[p][1]; A[3][p] = dh[p][1] * mu[p];
+      }
+      rhs[0] = dq[0]; rhs[1] = dq[2]; rhs[2] = dq[3]; rhs[3] = dq[5];
+      solve4(A, rhs, beta);
+    } else {
+      general_eigen(P, W.utt, W.hbt, mu, dh);
+      T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM];
+      for (int p = 0; p < N; ++p)
+        for (int m = 0; m < M; ++m) { R[2 * m][p] = dh[p][m]; R[2 * m + 1][p] = mu[p] * dh[p][m]; }
+      for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[3 * m]; rhs[2 * m + 1] = dq[3 * m + 2]; }
+      solve_n(N, R, rhs, beta);
+    }
+    for (int m = 0; m < M; ++m) {
+      T carried(0.0);  // depth change of layer m carried by the acoustic waves
+      for (int p = 0; p < N; ++p) {
+        const T a = beta[p] * dh[p][m];
+        carried = carried + a;
+        send(mu[p], 3 * m, a);
+        send(mu[p], 3 * m + 1, W.unt[m] * a);
+        send(mu[p], 3 * m + 2, mu[p] * a);
+      }
+      send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * carried);
+    }
+    return;
+  }
+  for (int m = 0; m < M; ++m) {
+    if (!W.active[m]) continue;
+    const T c = sqrt(P.g * W.hbt[m]);
+    const T s1 = W.utt[m] - c, s2 = W.utt[m] + c;
+    const T b1 = (s2 * dq[3 * m] - dq[3 * m + 2]) / (s2 - s1);
+    const T b2 = (dq[3 * m + 2] - s1 * dq[3 * m]) / (s2 - s1);
+    send(s1, 3 * m, b1); send(s1, 3 * m + 1, W.unt[m] * b1); send(s1, 3 * m + 2, s1 * b1);
+    send(s2, 3 * m, b2); send(s2, 3 * m + 1, W.unt[m] * b2); send(s2, 3 * m + 2, s2 * b2);
+    send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * (b1 + b2));
   }
 }
 
@@ -777,6 +877,155 @@ void step_patch_impl(const Params& P, int nx, int ny, double dx, double dy, doub
   if (lost) *lost = lost_x + lost_y;
 }
 
+// Unsplit step on a patch whose ghost ring is filled (wave propagation with transverse
+// Riemann solves, the corner-transport form of the book's Ch. 21): every edge is solved on
+// Q^n; an x edge (i - 1/2, j) sends ap = A+dQ - Ft into cell (i, j) and am = A-dQ + Ft into
+// cell (i - 1, j) (Ft: its limited correction flux, so ap and am are what the cells receive);
+// each is split by the transverse solve, and the parts moving up / down correct the y-edge
+// fluxes above / below the receiving cell by -(dt / 2 dx) B+- (.) ; y edges likewise. Then
+//   Q_ij -= dt/dx (ap_{i-1/2} + am_{i+1/2}) + dt/dy (bp_{j-1/2} + bm_{j+1/2})
+//         + dt/dx (Gx_{i+1/2} - Gx_{i-1/2}) + dt/dy (Gy_{j+1/2} - Gy_{j-1/2})
+// and the positivity fix. Rows j in [-1, ny] and columns i in [-1, nx] are solved, so that
+// the corrections at the patch's own edges are complete.
+template <class T>
+void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double dy, double dt,
+                             T* q, const T* B, double* smax, T* fx, T* fy, int* lost) {
+  const int M = P.M, F = 3 * M;
+  const int PW = nx + 2 * NG, PH = ny + 2 * NG;
+  const size_t plane = (size_t)PW * PH;
+  const double nux = dt / dx, nuy = dt / dy;
+  // x edges i - 1/2, i in [0, nx], rows j in [-1, ny]: am, ap and their transverse parts
+  // (stored in (h, hu, hv) order); row r = j + 1.
+  const size_t XE = (size_t)(ny + 2) * (nx + 1);
+  std::vector<T> xam(XE * F), xap(XE * F), xamU(XE * F), xamD(XE * F), xapU(XE * F), xapD(XE * F);
+  // y edges j - 1/2, j in [0, ny], columns i in [-1, nx]: col c = i + 1
+  const size_t YE = (size_t)(nx + 2) * (ny + 1);
+  std::vector<T> ybm(YE * F), ybp(YE * F), ybmR(YE * F), ybmL(YE * F), ybpR(YE * F), ybpL(YE * F);
+  double sx = 0.0, sy = 0.0;
+  int lost_x = 0, lost_y = 0;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int nlines = dir == 0 ? ny + 2 : nx + 2;  // lines -1 .. n
+    const int n = dir == 0 ? nx : ny;                // cells along a line
+    const double nu = dir == 0 ? nux : nuy;
+    #pragma omp parallel for reduction(max : sx, sy) reduction(+ : lost_x, lost_y) schedule(static)
+    for (int li = 0; li < nlines; ++li) {
+      const int ln = li - 1;
+      std::vector<T> line((n + 4) * F), Bl(n + 4);
+      for (int k = -NG; k < n + NG; ++k) {
+        const size_t o = dir == 0 ? pidx(nx, k, ln) : pidx(nx, ln, k);
+        Bl[k + NG] = B[o];
+        for (int m = 0; m < M; ++m) {
+          line[(k + NG) * F + 3 * m + 0] = q[(3 * m + 0) * plane + o];
+          line[(k + NG) * F + 3 * m + 1] = q[(3 * m + (dir == 0 ? 1 : 2)) * plane + o];
+          line[(k + NG) * F + 3 * m + 2] = q[(3 * m + (dir == 0 ? 2 : 1)) * plane + o];
+        }
+      }
+      std::vector<Waves<T>> W(n + 3);
+      for (int k = 0; k < n + 3; ++k) {
+        const int i = k - 1;
+        riemann(P, &line[(i + 1) * F], &line[(i + 2) * F], Bl[i + 1], Bl[i + 2], W[k]);
+      }
+      const bool interior = ln >= 0 && ln < (dir == 0 ? ny : nx);
+      for (int i = 0; i <= n; ++i) {
+        const int k = i + 1;
+        T amdq[MAXF], apdq[MAXF], ft[MAXF], am[MAXF], ap[MAXF], u[4][MAXF];
+        fluctuations(P, W[k], amdq, apdq);
+        correction(P, W[k], W[k - 1], W[k + 1], nu, ft);
+        for (int f = 0; f < F; ++f) { am[f] = amdq[f] + ft[f]; ap[f] = apdq[f] - ft[f]; }
+        transverse(P, W[k], am, u[0], u[1]);  // am: towards +t, towards -t
+        transverse(P, W[k], ap, u[2], u[3]);
+        if (interior) {
+          double s = 0.0;
+          for (int p = 0; p < W[k].nw; ++p) s = std::max(s, std::fabs(val(W[k].s[p])));
+          if (dir == 0) { sx = std::max(sx, s); lost_x += W[k].hyperbolicity_lost; }
+          else { sy = std::max(sy, s); lost_y += W[k].hyperbolicity_lost; }
+        }
+        // back to (h, hu, hv) order
+        const size_t e = (size_t)li * (n + 1) + i;
+        T* dst[6];
+        if (dir == 0) { dst[0] = &xam[e * F]; dst[1] = &xap[e * F]; dst[2] = &xamU[e * F]; dst[3] = &xamD[e * F];
+                        dst[4] = &xapU[e * F]; dst[5] = &xapD[e * F]; }
+        else { dst[0] = &ybm[e * F]; dst[1] = &ybp[e * F]; dst[2] = &ybmR[e * F]; dst[3] = &ybmL[e * F];
+               dst[4] = &ybpR[e * F]; dst[5] = &ybpL[e * F]; }
+        const T* src[6] = {am, ap, u[0], u[1], u[2], u[3]};
+        for (int v = 0; v < 6; ++v)
+          for (int m = 0; m < M; ++m) {
+            dst[v][3 * m] = src[v][3 * m];
+            dst[v][3 * m + (dir == 0 ? 1 : 2)] = src[v][3 * m + 1];
+            dst[v][3 * m + (dir == 0 ? 2 : 1)] = src[v][3 * m + 2];
+          }
+      }
+    }
+  }
+  // Transverse correction fluxes: Gy at y edges (i, j - 1/2), j in [0, ny], i in [0, nx);
+  // Gx at x edges (i - 1/2, j), i in [0, nx], j in [0, ny).
+  std::vector<T> Gy((size_t)(ny + 1) * nx * F, T(0.0)), Gx((size_t)ny * (nx + 1) * F, T(0.0));
+  const double hx = 0.5 * nux, hy = 0.5 * nuy;
+  auto gy = [&](int i, int jj) -> T* { return &Gy[((size_t)jj * nx + i) * F]; };
+  auto gx = [&](int ii, int j) -> T* { return &Gx[((size_t)j * (nx + 1) + ii) * F]; };
+  for (int j = -1; j <= ny; ++j)
+    for (int i = 0; i <= nx; ++i) {
+      const size_t e = (size_t)(j + 1) * (nx + 1) + i;
+      // ap enters cell (i, j); am enters cell (i - 1, j); up: edge j + 1/2 (index j + 1), down: j - 1/2 (j)
+      for (int side = 0; side < 2; ++side) {
+        const int ci = side == 0 ? i : i - 1;
+        if (ci < 0 || ci >= nx) continue;
+        const T* up = side == 0 ? &xapU[e * F] : &xamU[e * F];
+        const T* dn = side == 0 ? &xapD[e * F] : &xamD[e * F];
+        if (j + 1 <= ny) { T* g = gy(ci, j + 1); for (int f = 0; f < F; ++f) g[f] = g[f] - hx * up[f]; }
+        if (j >= 0) { T* g = gy(ci, j); for (int f = 0; f < F; ++f) g[f] = g[f] - hx * dn[f]; }
+      }
+    }
+  for (int i = -1; i <= nx; ++i)
+    for (int j = 0; j <= ny; ++j) {
+      const size_t e = (size_t)(i + 1) * (ny + 1) + j;
+      // bp enters cell (i, j); bm enters cell (i, j - 1); right: edge i + 1/2, left: i - 1/2
+      for (int side = 0; side < 2; ++side) {
+        const int cj = side == 0 ? j : j - 1;
+        if (cj < 0 || cj >= ny) continue;
+        const T* rt = side == 0 ? &ybpR[e * F] : &ybmR[e * F];
+        const T* lt = side == 0 ? &ybpL[e * F] : &ybmL[e * F];
+        if (i + 1 <= nx) { T* g = gx(i + 1, cj); for (int f = 0; f < F; ++f) g[f] = g[f] - hy * rt[f]; }
+        if (i >= 0) { T* g = gx(i, cj); for (int f = 0; f < F; ++f) g[f] = g[f] - hy * lt[f]; }
+      }
+    }
+  // mass flux of every layer through the interior edges, seen from the lower-index cell:
+  // its normal momentum + (A-dQ + Ft)_h + the transverse correction flux
+  if (fx)
+    for (int m = 0; m < M; ++m)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i <= nx; ++i) {
+          const size_t e = (size_t)(j + 1) * (nx + 1) + i;
+          fx[((size_t)m * ny + j) * (nx + 1) + i] =
+              q[(3 * m + 1) * plane + pidx(nx, i - 1, j)] + xam[e * F + 3 * m] + gx(i, j)[3 * m];
+        }
+  if (fy)
+    for (int m = 0; m < M; ++m)
+      for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          const size_t e = (size_t)(i + 1) * (ny + 1) + j;
+          fy[((size_t)m * (ny + 1) + j) * nx + i] =
+              q[(3 * m + 2) * plane + pidx(nx, i, j - 1)] + ybm[e * F + 3 * m] + gy(i, j)[3 * m];
+        }
+  #pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const size_t exl = (size_t)(j + 1) * (nx + 1) + i, exr = exl + 1;
+      const size_t eyb = (size_t)(i + 1) * (ny + 1) + j, eyt = eyb + 1;
+      T qn[MAXF];
+      for (int f = 0; f < F; ++f) {
+        const size_t o = (size_t)f * plane + pidx(nx, i, j);
+        qn[f] = q[o] - nux * (xap[exl * F + f] + xam[exr * F + f]) - nuy * (ybp[eyb * F + f] + ybm[eyt * F + f])
+                - nux * (gx(i + 1, j)[f] - gx(i, j)[f]) - nuy * (gy(i, j + 1)[f] - gy(i, j)[f]);
+      }
+      positivity(P, qn);
+      // written after every read of this cell's old state (the loops above read q only)
+      for (int f = 0; f < F; ++f) q[(size_t)f * plane + pidx(nx, i, j)] = qn[f];
+    }
+  if (smax) { smax[0] = sx; smax[1] = sy; }
+  if (lost) *lost = lost_x + lost_y;
+}
+
 inline double minmod(double a, double b) {
   // Sec. 2.1: the argument of smaller modulus, zero when the signs differ.
   if (a * b <= 0.0) return 0.0;
@@ -790,6 +1039,7 @@ extern "C" {
 struct or_params {
   int M; double g; double r; double dry_tol; int order; int limiter; int eigen;
   double rho[4];  // layer densities, top first (read for M >= 3 and by the general branch)
+  int unsplit;    // 1: unsplit step with transverse Riemann solves
 };
 
 static Params to_params(const or_params* p) {
@@ -797,6 +1047,7 @@ static Params to_params(const or_params* p) {
   P.M = p->M; P.g = p->g; P.r = p->r; P.dry_tol = p->dry_tol;
   P.order = p->order; P.limiter = p->limiter; P.eigen = p->eigen;
   for (int m = 0; m < MAXM; ++m) P.rho[m] = p->rho[m];
+  P.unsplit = p->unsplit;
   return P;
 }
 
@@ -826,6 +1077,18 @@ void or_riemann_general(const or_params* pp, const double* qL, const double* qR,
   Params P = to_params(pp);
   P.force_general = 1;
   riemann_out(P, qL, qR, BL, BR, Z, s, amdq, apdq, info);
+}
+
+// Transverse split of dq (3M, normal-frame order) at the edge (qL, qR, BL, BR): bp, bm the
+// parts moving towards +t and -t (see transverse above). general: the general coupled branch
+// also for M = 2.
+void or_transverse(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
+                   const double* dq, double* bp, double* bm, int general) {
+  Params P = to_params(pp);
+  P.force_general = general;
+  Waves<double> W;
+  riemann(P, qL, qR, BL, BR, W);
+  transverse(P, W, dq, bp, bm);
 }
 
 void or_eigen(const or_params* pp, double u1, double u2, double hb1, double hb2, double* lam, int* lost) {
@@ -868,7 +1131,8 @@ int or_step_patch(const or_params* pp, int nx, int ny, double dx, double dy, dou
                   double* q, const double* B, double* smax, double* fx, double* fy) {
   const Params P = to_params(pp);
   int lost = 0;
-  step_patch_impl(P, nx, ny, dx, dy, dt, q, B, smax, fx, fy, &lost);
+  if (P.unsplit) step_patch_unsplit_impl(P, nx, ny, dx, dy, dt, q, B, smax, fx, fy, &lost);
+  else step_patch_impl(P, nx, ny, dx, dy, dt, q, B, smax, fx, fy, &lost);
   return lost;
 }
 

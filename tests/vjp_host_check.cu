@@ -23,6 +23,7 @@ struct OrParams {  // layout of the oracle's or_params
   double g, r, dry_tol;
   int order, limiter, eigen;
   double rho[4];
+  int unsplit;
 };
 typedef void (*JacFn)(const OrParams*, const double*, const double*, double, double, double*);
 
@@ -59,7 +60,7 @@ template <int M>
 static double family(JacFn jac, int eigen, double d1, double d2, double spread, double vel, double db,
                      double shear, int trials, unsigned seed) {
   const double g = 9.81, r = M == 2 ? 1025.0 / 1028.0 : 1.0;
-  OrParams op{M, g, r, 1e-6, 1, 2, eigen, {1025.0, 1028.0, 0.0, 0.0}};
+  OrParams op{M, g, r, 1e-6, 1, 2, eigen, {1025.0, 1028.0, 0.0, 0.0}, 0};
   DevParams P{};
   P.M = M;
   P.g = g;
