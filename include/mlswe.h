@@ -88,6 +88,15 @@ typedef struct {
  *               cfl_desired, ceil(dt_parent * rate / cfl_desired) within [1, ratio],
  *               from the wave speeds of the previous step (Sec. 2: a smaller r_t
  *               where the refined region is shallow, as GeoClaw does).
+ *  unsplit      0: dimensional splitting (x sweep, then y sweep on its result);
+ *               1 (M <= 2): the unsplit wave-propagation step of GeoClaw's solver
+ *               family (Sec. 1) in corner-transport form: every edge solved on Q^n, the
+ *               fluctuation each cell receives (correction flux included) split by a
+ *               transverse Riemann solve at the edge state, its parts correcting the
+ *               fluxes of the edges above and below (left and right) the receiving cell
+ *               with weight dt/(2 dx); one update of every cell. It keeps x and y
+ *               symmetric. It allocates 12 * 3M doubles per cell of every level for the
+ *               per-edge arrays. The adjoint and mlswe_step_fixed_noalloc take unsplit = 0.
  */
 typedef struct {
   int M;
@@ -108,6 +117,7 @@ typedef struct {
   int min_side;
   int max_side;
   int dynamic_rt;
+  int unsplit;
 } mlswe_config;
 
 /* Physical extent [x0,x1] x [y0,y1] and coarse (level 0) cell counts of a member. */

@@ -689,16 +689,16 @@ void transverse(const Params& P, const Waves<T>& W, const T* dq, T* bp, T* bm) {
       for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[3 * m]; rhs[2 * m + 1] = dq[3 * m + 2]; }
       solve_n(N, R, rhs, beta);
     }
+    // shear strength: what the acoustic waves leave of hn; they carry the whole depth change
+    // dq_h of every layer (the h rows of the system) and un dq_h of hn
     for (int m = 0; m < M; ++m) {
-      T carried(0.0);  // depth change of layer m carried by the acoustic waves
       for (int p = 0; p < N; ++p) {
         const T a = beta[p] * dh[p][m];
-        carried = carried + a;
         send(mu[p], 3 * m, a);
         send(mu[p], 3 * m + 1, W.unt[m] * a);
         send(mu[p], 3 * m + 2, mu[p] * a);
       }
-      send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * carried);
+      send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * dq[3 * m]);
     }
     return;
   }
@@ -710,7 +710,7 @@ void transverse(const Params& P, const Waves<T>& W, const T* dq, T* bp, T* bm) {
     const T b2 = (dq[3 * m + 2] - s1 * dq[3 * m]) / (s2 - s1);
     send(s1, 3 * m, b1); send(s1, 3 * m + 1, W.unt[m] * b1); send(s1, 3 * m + 2, s1 * b1);
     send(s2, 3 * m, b2); send(s2, 3 * m + 1, W.unt[m] * b2); send(s2, 3 * m + 2, s2 * b2);
-    send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * (b1 + b2));
+    send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * dq[3 * m]);
   }
 }
 

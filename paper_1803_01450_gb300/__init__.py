@@ -39,7 +39,8 @@ class _Config(ctypes.Structure):
                 ("order", ctypes.c_int), ("limiter", ctypes.c_int), ("eigen", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("ratio", ctypes.c_int * 4), ("flag_tol", ctypes.c_double),
                 ("regrid_interval", ctypes.c_int), ("n_buf", ctypes.c_int), ("cluster_eff", ctypes.c_double),
-                ("min_side", ctypes.c_int), ("max_side", ctypes.c_int), ("dynamic_rt", ctypes.c_int)]
+                ("min_side", ctypes.c_int), ("max_side", ctypes.c_int), ("dynamic_rt", ctypes.c_int),
+                ("unsplit", ctypes.c_int)]
 
 
 class _Domain(ctypes.Structure):
@@ -76,6 +77,7 @@ class Config:
     min_side: int = 16
     max_side: int = 64
     dynamic_rt: int = 0
+    unsplit: int = 0
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -91,6 +93,7 @@ class Config:
         c.flag_tol = self.flag_tol; c.regrid_interval = self.regrid_interval; c.n_buf = self.n_buf
         c.cluster_eff = self.cluster_eff; c.min_side = self.min_side; c.max_side = self.max_side
         c.dynamic_rt = int(self.dynamic_rt)
+        c.unsplit = int(self.unsplit)
         return c
 
 
@@ -139,7 +142,7 @@ _SIGS = {
 }
 
 KERNEL_CLASSES = ["sweep_x", "sweep_y", "ghost_fill", "interp_fine", "average", "flags", "reflux", "other",
-                  "adjoint"]
+                  "adjoint", "update"]
 
 
 def build(force: bool = False) -> str:

@@ -471,8 +471,8 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
                                  const double* obs) {
   if (!h || n_steps < 1 || ckpt_every < 1 || n_gauges < 0 || (n_gauges > 0 && (!gauge_ij || !obs)))
     return h ? afail(h, MLSWE_EINVAL, "adjoint_setup: bad argument") : MLSWE_EINVAL;
-  if (h->n_members != 1 || h->L != 1 || h->cfg.order != 1 || h->cfg.M > 2)
-    return afail(h, MLSWE_EINVAL, "adjoint_setup: needs one member, one level, order 1 and M <= 2");
+  if (h->n_members != 1 || h->L != 1 || h->cfg.order != 1 || h->cfg.M > 2 || h->cfg.unsplit)
+    return afail(h, MLSWE_EINVAL, "adjoint_setup: needs one member, one level, order 1, M <= 2 and the split step");
   const Level& V = h->mem[0].lev[0];
   for (int g = 0; g < n_gauges; ++g)
     if (gauge_ij[2 * g] < 0 || gauge_ij[2 * g] >= V.NX || gauge_ij[2 * g + 1] < 0 || gauge_ij[2 * g + 1] >= V.NY)

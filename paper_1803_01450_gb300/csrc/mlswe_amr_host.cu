@@ -143,6 +143,7 @@ static mlswe_status rebuild_masks(Hier* H, int member, int level) {
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   H->wl[level * 2].dirty = H->wl[level * 2 + 1].dirty = true;
   H->wl[(level - 1) * 2].dirty = H->wl[(level - 1) * 2 + 1].dirty = true;
+  H->wu[level].dirty = H->wu[level - 1].dirty = true;
   H->tables_dirty = true;
   return MLSWE_OK;
 }
@@ -318,7 +319,7 @@ static mlswe_status coarse_step(Hier* H) {
   const bool graphs = H->use_graphs && !H->per_patch_launch && !H->timer.on;
   if (!graphs) return enqueue_coarse_step(H);
   for (int l = 0; l < H->L; ++l)
-    for (int dir = 0; dir < 2; ++dir) {
+    for (int dir = 0; dir < (H->cfg.unsplit ? 3 : 2); ++dir) {  // built before the capture (they sync)
       mlswe_status s = ensure_worklist(H, l, dir);
       if (s != MLSWE_OK) return s;
     }
@@ -330,7 +331,11 @@ static mlswe_status coarse_step(Hier* H) {
     CUDA_TRY(H, cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal));
     mlswe_status s = enqueue_coarse_step(H);
     cudaError_t e = cudaStreamEndCapture(H->st, &g);
-    if (s != MLSWE_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (s != MLSWE_OK) {
+      if (g) cudaGraphDestroy(g);
+      H->parity = par0;  // nothing ran
+      return s;
+    }
     if (e != cudaSuccess) return fail(H, MLSWE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     if (H->graph[p]) cudaGraphExecDestroy(H->graph[p]);
     e = cudaGraphInstantiate(&H->graph[p], g, 0);

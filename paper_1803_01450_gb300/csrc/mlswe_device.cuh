@@ -39,6 +39,7 @@ struct DevParams {
   int order;
   int limiter;
   int eigen;
+  int unsplit;     // 1: unsplit step with transverse Riemann solves (M <= 2)
 };
 
 // One (member, level) of the hierarchy: dense arrays over the whole level.
@@ -59,6 +60,14 @@ struct LevelDesc {
                        // null: always active
   int NX, NY, P;
   double inv_dx, inv_dy;
+  // Unsplit step: per-edge arrays of the level, 6 groups of 3M planes for the x edges (plane
+  // size uxp, edge left of cell i on row j at (j + 1) (NX + 1) + i, rows -1 .. NY), then 6
+  // groups for the y edges (plane size uyp, edge below cell j on column i at j (NX + 2) +
+  // i + 1, columns -1 .. NX). Groups: the fluctuation into the lower-index cell (with the
+  // correction flux), into the higher-index cell, and the transverse parts of each towards
+  // +t and -t; fields in (h, hu, hv) order. Null for the split step.
+  double* ue;
+  long long uxp, uyp;
 };
 
 // One tile of a sweep: `nlines` lines of `len` cells, along x (x sweep: rows
@@ -175,13 +184,14 @@ struct EdgeW {
   // What the acoustic waves of layer m sum to: its mass and normal-momentum flux jumps
   // (sum_p Z_p = jump exactly for the f-wave split, up to rounding).
   double t0[M], t1[M];
+  double hbt[M];  // depth whose gravity speed the transverse split of this edge takes
   int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
 };
 
 template <int M>
 struct WRec {  // shared-memory layout of EdgeW: mass of layer m, wave p at A + 2M m + p
   static constexpr int A = 0, S = 2 * M * M, Z = S + 2 * M, US = Z + M, VH = US + M, T0 = VH + M, T1 = T0 + M,
-                       N = T1 + M;
+                       HB = T1 + M, N = HB + M;
 };
 
 // Per-edge record of a coupled two-layer edge that the adjoint's reverse pass reads instead
@@ -439,6 +449,7 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const double
     W.vh[m] = vh[m];
     W.t0[m] = d0[m];
     W.t1[m] = d1[m];
+    W.hbt[m] = hb[m];
   }
 }
 
@@ -462,7 +473,9 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     for (int m = 0; m < M; ++m) W.mass[m][p] = 0.0;
   }
 #pragma unroll
-  for (int m = 0; m < M; ++m) { W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; }
+  for (int m = 0; m < M; ++m) {
+    W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; W.hbt[m] = 0.0;
+  }
   W.wall = 0;
 
   double d0[M], d1[M], d2[M], hb[M];
@@ -606,6 +619,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       W.vh[m] = vh[m];
       W.t0[m] = d0[m];
       W.t1[m] = d1[m];
+      W.hbt[m] = hb[m];
     }
     return;
   }
@@ -632,6 +646,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       const double tc = rsqrt(gh);
       const double ch = gh * tc;
       split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W, 0.5 * tc);
+      W.hbt[m] = hb[m];
     } else if (wl || wr) {
       const double* cw = wl ? cL : cR;
       const double* cd = wl ? cR : cL;
@@ -648,6 +663,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
         const double ch = sqrt(g * hw);
         split_single<M>(m, pa, pb, e0, e1, e2, -ch, ch, utw, 0.0, W);
         W.wall |= 1 << (2 * m + (wl ? 1 : 0));
+        W.hbt[m] = hw;
       } else {
         const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
         const double inv = rcp(sl + sr);
@@ -665,8 +681,143 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
           s2 = fmax(u + c, uh + ch);
         }
         split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], s1, s2, vh, uh, W);
+        W.hbt[m] = hb[m];
       }
     }
+  }
+}
+
+// ---- transverse split of the unsplit step ----
+// The fluctuation dq (normal-frame order (h, hn, ht) per layer) that an edge sends into one
+// of its cells is split into the waves of the transverse direction, at the state the edge
+// was solved at: per layer the depth hb, the normal Roe velocity un and the transverse one
+// ut. The transverse system is the normal one with un and ut exchanged: acoustic eigenvalues
+// mu_p of the (h, ht) block, eigenvectors (dh_m, un_m dh_m, mu_p dh_m), and a shear wave
+// in hn_m with speed ut_m whose strength is what the acoustic waves leave of hn
+// (dq_hn - un dq_h: the acoustic waves carry the whole depth change). up gathers mu beta r
+// of the waves with mu > 0, dn those with mu < 0.
+
+// Eigen data of a coupled two-layer edge in the transverse direction: eigenvalues (closed-form
+// guesses for equal velocities, two Newton steps on the quartic unless hyperbolicity is lost
+// or P.eigen = 1), and what the strengths of any dq need (Lagrange denominators of the
+// eigenvalues, their elementary symmetric sums, the coefficients of a(mu)).
+struct TransEig2 {
+  double mu[4], iden[4], S1, S2, S3, c1, p1, p0, ic1;
+};
+
+__device__ __forceinline__ void trans_eigen2(const DevParams& P, const double* hb, const double* ut, TransEig2& E) {
+  const double g = P.g;
+  const double c1 = g * hb[0], c2 = g * hb[1];
+  double den2[2] = {hb[0] + hb[1], c1}, inv2[2];
+  batched_reciprocal<2>(den2, inv2);
+  const double ubar = (hb[0] * ut[0] + hb[1] * ut[1]) * inv2[0];
+  const double dc = c1 - c2;
+  const double X = dc * dc + 4.0 * P.r * c1 * c2;
+  const double disc = X * rsqrt(X);
+  const double mup = 0.5 * ((c1 + c2) + disc);
+  const double tp = rsqrt(mup);
+  const double sp = mup * tp;
+  const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
+  const double sm = mum * rsqrt(mum);
+  double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
+  const double du = ut[0] - ut[1];
+  const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
+  if (!lst && P.eigen == 0) {
+    const double rc = P.r * c1 * c2;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      double Pl[4], dP[4], q[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const double a1 = lam[p] - ut[0], a2 = lam[p] - ut[1];
+        const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
+        Pl[p] = f1 * f2 - rc;
+        dP[p] = 2.0 * (a1 * f2 + a2 * f1);
+      }
+      batched_reciprocal<4>(dP, q);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) lam[p] -= Pl[p] * q[p];
+    }
+  }
+  const double l01 = lam[0] - lam[1], l02 = lam[0] - lam[2], l03 = lam[0] - lam[3];
+  const double l12 = lam[1] - lam[2], l13 = lam[1] - lam[3], l23 = lam[2] - lam[3];
+  double den[4] = {l01 * l02 * l03, -l01 * l12 * l13, l02 * l12 * l23, -l03 * l13 * l23};
+  batched_reciprocal<4>(den, E.iden);
+  const double s01 = lam[0] + lam[1], s23 = lam[2] + lam[3];
+  const double q0 = lam[0] * lam[1], q1 = lam[2] * lam[3];
+  E.S1 = s01 + s23;
+  E.S2 = q0 + q1 + s01 * s23;
+  E.S3 = q0 * s23 + q1 * s01;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) E.mu[p] = lam[p];
+  E.c1 = c1;
+  E.ic1 = inv2[1];
+  E.p1 = -2.0 * ut[0];
+  E.p0 = ut[0] * ut[0] - c1;
+}
+
+// Adds speed * (v_h, un v_h, speed v_h) to fields f .. f+2 of up (speed > 0) or dn (speed <
+// 0). f is a compile-time constant after unrolling, so up and dn stay in registers.
+__device__ __forceinline__ void trans_send(double speed, double v_h, double un, double* up, double* dn, int f) {
+  const int sc = sign_class(speed);
+  const double a = speed * v_h, b = speed * (un * v_h), c = speed * (speed * v_h);
+  if (sc > 0) { up[f] += a; up[f + 1] += b; up[f + 2] += c; }
+  else if (sc < 0) { dn[f] += a; dn[f + 1] += b; dn[f + 2] += c; }
+}
+
+__device__ __forceinline__ void trans_shear(double ut, double z, double* up, double* dn, int f) {
+  const int sc = sign_class(ut);
+  const double a = ut * z;
+  if (sc > 0) up[f] += a;
+  else if (sc < 0) dn[f] += a;
+}
+
+// Coupled two-layer edge: strengths from the moments of the (h, ht) rows (the normal solve's
+// Vandermonde form with ut in place of un), then the parts towards +t and -t.
+__device__ __forceinline__ void trans_apply2(const TransEig2& E, const double* un, const double* ut,
+                                             const double* dq, double* up, double* dn) {
+#pragma unroll
+  for (int f = 0; f < 6; ++f) { up[f] = 0.0; dn[f] = 0.0; }
+  const double m0 = dq[0], m1 = dq[2];
+  const double m2 = E.c1 * dq[3] - E.p1 * m1 - E.p0 * m0;
+  const double m3 = E.c1 * dq[5] - E.p1 * m2 - E.p0 * m1;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const double mu = E.mu[p];
+    const double k2 = mu - E.S1;
+    const double k1 = E.S2 + mu * k2;
+    const double k0 = mu * k1 - E.S3;
+    const double beta = (m3 + k2 * m2 + k1 * m1 + k0 * m0) * E.iden[p];
+    const double al = mu - ut[0];
+    const double alpha = (al * al - E.c1) * E.ic1;
+    trans_send(mu, beta, un[0], up, dn, 0);
+    trans_send(mu, beta * alpha, un[1], up, dn, 3);
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) trans_shear(ut[m], dq[3 * m + 1] - un[m] * dq[3 * m], up, dn, 3 * m + 1);
+}
+
+// Layers on their own (one layer, or an edge where some layer is dry on a side): speeds
+// ut_m -+ sqrt(g hb_m) for every layer wet on a side (bit m of act).
+template <int M>
+__device__ __forceinline__ void trans_apply_layers(const DevParams& P, int act, const double* hb, const double* un,
+                                                   const double* ut, const double* dq, double* up, double* dn) {
+#pragma unroll
+  for (int f = 0; f < 3 * M; ++f) { up[f] = 0.0; dn[f] = 0.0; }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    if (!((act >> m) & 1)) continue;
+    const double gh = P.g * hb[m];
+    const double tc = rsqrt(gh);
+    const double c = gh * tc;
+    const double inv = 0.5 * tc;  // 1 / (s2 - s1)
+    const double s1 = ut[m] - c, s2 = ut[m] + c;
+    const double dh = dq[3 * m], dht = dq[3 * m + 2];
+    const double b1 = (s2 * dh - dht) * inv;
+    const double b2 = (dht - s1 * dh) * inv;
+    trans_send(s1, b1, un[m], up, dn, 3 * m);
+    trans_send(s2, b2, un[m], up, dn, 3 * m);
+    trans_shear(ut[m], dq[3 * m + 1] - un[m] * dh, up, dn, 3 * m + 1);
   }
 }
 

@@ -123,6 +123,7 @@ static mlswe_status upload_desc(Hier* H) {
       D.active = H->d_active + k;
       D.NX = V.NX; D.NY = V.NY; D.P = V.P;
       D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
+      D.ue = V.ue; D.uxp = V.uxp; D.uyp = V.uyp;
       idx[k] = D.inv_dx; idy[k] = D.inv_dy;
     }
   CUDA_TRY(H, cudaMemcpyAsync(H->d_desc, d.data(), d.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice, H->st));
@@ -161,15 +162,47 @@ long long patch_cells(const Hier* H, int level) {
 static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out, std::vector<int>& patch_off) {
   out.clear();
   patch_off.clear();
-  const TileShape ts = H->shape[level * 2 + dir];
+  const TileShape ts = H->shape[level * 2 + (dir == 2 ? 0 : dir)];
   for (int m = 0; m < H->n_members; ++m) {
     const Level& V = H->mem[m].lev[level];
     const int desc = H->desc_index(m, level);
     for (const Box& b : V.patches) {
       patch_off.push_back((int)out.size());
       int tl, tn;
-      tile_dims(ts, dir == 0 ? b.i1 - b.i0 : b.j1 - b.j0, &tl, &tn);
-      if (dir == 0) {
+      tile_dims(ts, dir != 1 ? b.i1 - b.i0 : b.j1 - b.j0, &tl, &tn);
+      if (dir == 2) {
+        // update tiles of the unsplit step: rows of the patch, cells along x
+        for (int j = b.j0; j < b.j1; j += tn) {
+          const int nl = std::min(tn, b.j1 - j);
+          for (int i = b.i0; i < b.i1; i += tl) {
+            SweepItem it;
+            it.desc = desc; it.i0 = i; it.j0 = j; it.len = std::min(tl, b.i1 - i);
+            it.nlines = nl; it.flags = 1;
+            out.push_back(it);
+          }
+        }
+      } else if (H->cfg.unsplit) {
+        // edge passes of the unsplit step: the patch's lines and one ghost line on each side
+        // (mirrored where it lies beyond the domain)
+        const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;
+        const int a0 = dir == 0 ? b.i0 : b.j0, a1 = dir == 0 ? b.i1 : b.j1;
+        for (int seg = 0; seg < 3; ++seg) {
+          const int s0 = seg == 0 ? lo - 1 : (seg == 1 ? lo : hi);
+          const int s1 = seg == 0 ? lo : (seg == 1 ? hi : hi + 1);
+          for (int x = s0; x < s1; x += tn) {
+            const int nl = std::min(tn, s1 - x);
+            for (int a = a0; a < a1; a += tl) {
+              SweepItem it;
+              it.desc = desc;
+              it.len = std::min(tl, a1 - a);
+              if (dir == 0) { it.i0 = a; it.j0 = x; } else { it.i0 = x; it.j0 = a; }
+              it.nlines = nl;
+              it.flags = (seg == 1 ? 1 : 0) | (a + it.len == a1 ? 2 : 0);
+              out.push_back(it);
+            }
+          }
+        }
+      } else if (dir == 0) {
         // Rows of the patch, plus (refined levels) the two ghost rows on each side that
         // lie in the domain: the y sweep reads Q* there.
         const int g = level > 0 ? kNG : 0;
@@ -207,7 +240,7 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
 }
 
 mlswe_status ensure_worklist(Hier* H, int level, int dir) {
-  Hier::WorkList& W = H->wl[level * 2 + dir];
+  Hier::WorkList& W = dir == 2 ? H->wu[level] : H->wl[level * 2 + dir];
   if (!W.dirty) return MLSWE_OK;
   std::vector<SweepItem> items;
   build_items(H, level, dir, items, W.patch_off);
@@ -247,7 +280,7 @@ mlswe_status ensure_worklist(Hier* H, int level, int dir) {
 // Batched form: one persistent launch per sweep over the tiles of every patch of every
 // member. Per-patch form (comparison only): one launch per patch and sweep.
 mlswe_status enqueue_level_step(Hier* H, int level, int record) {
-  for (int dir = 0; dir < 2; ++dir) {
+  for (int dir = 0; dir < (H->cfg.unsplit ? 3 : 2); ++dir) {
     mlswe_status s = ensure_worklist(H, level, dir);
     if (s != MLSWE_OK) return s;
   }
@@ -273,6 +306,28 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
         timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
         CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p,
                                  std::min(cnt, full), par, record, H->d_smax, H->d_lost, H->st, ctas));
+        timer_end(H, tok);
+      }
+    }
+  }
+  if (H->cfg.unsplit) {
+    // the cell update after both edge passes (memory-bound: 4 CTAs of 256 threads per SM)
+    Hier::WorkList& W = H->wu[level];
+    const int full = 4 * H->num_sms;
+    if (!H->per_patch_launch) {
+      int tok;
+      timer_begin(H, KC_UPDATE, &tok);
+      CUDA_TRY(H, launch_unsplit_update(H->dp, H->d_desc, W.d_items, W.d_count, full, par, record, H->st));
+      timer_end(H, tok);
+    } else {
+      const int np = (int)W.patch_off.size() - 1;
+      for (int p = 0; p < np; ++p) {
+        const int cnt = W.patch_off[p + 1] - W.patch_off[p];
+        if (cnt == 0) continue;
+        int tok;
+        timer_begin(H, KC_UPDATE, &tok);
+        CUDA_TRY(H, launch_unsplit_update(H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p,
+                                          std::min(cnt, full), par, record, H->st));
         timer_end(H, tok);
       }
     }
@@ -308,6 +363,7 @@ void set_level_shape(Hier* H, int level, int dir, int len, int lines, int ctas) 
   H->shape[level * 2 + dir].lines = lines;
   H->shape[level * 2 + dir].ctas = ctas;
   H->wl[level * 2 + dir].dirty = true;
+  if (dir == 0) H->wu[level].dirty = true;  // the update tiles take the x shape
 }
 
 }  // namespace mlswe
@@ -326,6 +382,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
   if (cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->dry_tol >= 0.0) || !(cfg->g > 0.0)) return MLSWE_EINVAL;
   if (cfg->dynamic_rt < 0 || cfg->dynamic_rt > 1) return MLSWE_EINVAL;
+  if (cfg->unsplit < 0 || cfg->unsplit > 1 || (cfg->unsplit && cfg->M > 2)) return MLSWE_EINVAL;
   if (cfg->M >= 2 && !(cfg->rho[0] > 0.0)) return MLSWE_EINVAL;
   for (int m = 0; m + 1 < cfg->M; ++m)  // densities increase downwards (stable stratification)
     if (!(cfg->rho[m] < cfg->rho[m + 1])) return MLSWE_EINVAL;
@@ -352,9 +409,11 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
   for (int m = 0; m < 4; ++m) H->dp.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
+  H->dp.unsplit = cfg->unsplit;
   cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
   H->parity.assign(H->L, 0);
   H->wl.resize(H->L * 2);
+  H->wu.resize(H->L);
   H->shape.resize(H->L * 2);
   for (int l = 0; l < H->L; ++l) {
     // Default tiles: 125-cell rows x 2 (x sweep), 125-cell columns x 2 (y sweep); 256 edges;
@@ -389,6 +448,14 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
       cudaMemsetAsync(V.q[1], 0, plane * F * 8, H->st);
       cudaMemsetAsync(V.qs, 0, plane * F * 8, H->st);
       cudaMemsetAsync(V.B, 0, plane * 8, H->st);
+      if (cfg->unsplit) {
+        V.uxp = (long long)(V.NY + 2) * (V.NX + 1);
+        V.uyp = (long long)(V.NY + 1) * (V.NX + 2);
+        const size_t ub = (size_t)6 * F * (V.uxp + V.uyp) * 8;
+        V.ue = (double*)dev_alloc(H, ub);
+        if (!V.ue) { mlswe_destroy(H); return MLSWE_ENOMEM; }
+        cudaMemsetAsync(V.ue, 0, ub, H->st);
+      }
       if (l == 0) V.patches.push_back(Box{0, 0, nx, ny});
       if (H->L > 1) {
         const int M = cfg->M;

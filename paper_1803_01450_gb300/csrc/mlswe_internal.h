@@ -35,6 +35,8 @@ struct Level {
   double* fyc = nullptr;
   double* fxf = nullptr;
   double* fyf = nullptr;
+  double* ue = nullptr;         // unsplit step: per-edge arrays (see LevelDesc::ue)
+  long long uxp = 0, uyp = 0;
   std::vector<Box> patches;
 };
 
@@ -52,7 +54,8 @@ struct TileShape {
 
 // Kernel classes timed by the optional launch timer.
 enum KernelClass {
-  KC_SWEEP_X = 0, KC_SWEEP_Y, KC_GHOST, KC_INTERP, KC_AVERAGE, KC_FLAGS, KC_REFLUX, KC_OTHER, KC_ADJOINT, KC_COUNT
+  KC_SWEEP_X = 0, KC_SWEEP_Y, KC_GHOST, KC_INTERP, KC_AVERAGE, KC_FLAGS, KC_REFLUX, KC_OTHER, KC_ADJOINT, KC_UPDATE,
+  KC_COUNT
 };
 
 struct LaunchTimer {
@@ -117,6 +120,7 @@ struct Hier {
     int patch_cap = 0;
   };
   std::vector<WorkList> wl;  // [L * 2]
+  std::vector<WorkList> wu;  // [L] cell tiles of the unsplit step's update
   std::vector<TileShape> shape;  // [L * 2]
   int blocks_per_sm = 1;
   int num_sms = 0;
@@ -201,6 +205,8 @@ void* scratch_buffer(Hier* H, size_t bytes);
 void invalidate_graphs(Hier* H);
 
 // Kernel launchers.
+cudaError_t launch_unsplit_update(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                                  const int* n_items_dev, int grid, int parity, int record, cudaStream_t st);
 size_t sweep_smem_bytes(int M);
 cudaError_t launch_average(int nf, int r, const double* fine, int fP, size_t fplane, double* coarse, int cP,
                            size_t cplane, int ci0, int cj0, int ci1, int cj1, const uint8_t* mask, int maskNX,

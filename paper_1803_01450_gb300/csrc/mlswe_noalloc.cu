@@ -79,7 +79,7 @@ using namespace mlswe;
 extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx, int ny, double dx, double dy,
                                                  double dt, const double* q_in, const double* B, double* q_out,
                                                  void* cuda_stream, double* cfl_out) {
-  if (!cfg || !q_in || !B || !q_out || q_in == q_out) return MLSWE_EINVAL;
+  if (!cfg || !q_in || !B || !q_out || q_in == q_out || cfg->unsplit != 0) return MLSWE_EINVAL;
   if (cfg->M < 1 || cfg->M > 2 || cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2 ||
       cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->g > 0.0) || !(cfg->dry_tol >= 0.0))
     return MLSWE_EINVAL;
@@ -112,11 +112,13 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
   D.dt = d_dt;
   D.NX = nx; D.NY = ny; D.P = nx;
   D.inv_dx = 1.0 / dx; D.inv_dy = 1.0 / dy;
+  D.ue = nullptr; D.uxp = 0; D.uyp = 0;
   const int counts[2] = {(int)items[0].size(), (int)items[1].size()};
   DevParams P;
   P.M = cfg->M; P.g = cfg->g; P.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
   for (int m = 0; m < 4; ++m) P.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   P.dry_tol = cfg->dry_tol; P.order = cfg->order; P.limiter = cfg->limiter; P.eigen = cfg->eigen;
+  P.unsplit = 0;
 
   if (cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess) return MLSWE_ECUDA;
   if (cudaMemcpyAsync(d_count, counts, sizeof(counts), cudaMemcpyHostToDevice, st) != cudaSuccess) return MLSWE_ECUDA;

@@ -56,7 +56,11 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* d
 // eplane doubles per field, at the edge's index on the level (x edges: j (NX + 1) + i for
 // the edge left of cell i; y edges: j NX + i for the edge below cell j); the other coupled
 // edges of the tile write to slot eplane - 1, which eplane > (NX + 1) (NY + 1) keeps spare.
-template <int M, int DIR, int MINB, bool STORE>
+// UNSPLIT (M <= 2): the edge pass of the unsplit step. Both directions read Q^n; tiles also
+// cover one ghost line on each side of a patch (mirrored beyond the domain); every edge
+// between the cells of a tile line writes the fluctuations its two cells receive and their
+// transverse splits to the level's edge arrays (LevelDesc::ue) instead of updating cells.
+template <int M, int DIR, int MINB, bool STORE, bool UNSPLIT>
 __global__ void __launch_bounds__(kThreads, MINB)
 sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
              const int* __restrict__ n_items_dev, int parity, int record, unsigned long long* smax_bits,
@@ -78,13 +82,14 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     const int len = item.len, nl = item.nlines;
     const int NX = D.NX, NY = D.NY, Pt = D.P;
     const size_t plane = (size_t)NY * Pt;
-    const double* __restrict__ qin = DIR == 0 ? D.q[parity] : D.qs;
+    const double* __restrict__ qin = (DIR == 0 || UNSPLIT) ? D.q[parity] : D.qs;
     double* __restrict__ qout = DIR == 0 ? D.qs : D.q[parity ^ 1];
     if (D.active != nullptr && *D.active == 0) {
       // This member's level takes no step in this substep (its time ratio is smaller than
       // the substep count of the launch): the y sweep copies the tile's cells from the step's
-      // input to its output (the x sweep's scratch is skipped), nothing is recorded.
-      if (DIR == 0) continue;
+      // input to its output (the x sweep's scratch is skipped), nothing is recorded. (Unsplit:
+      // the update kernel copies.)
+      if (DIR == 0 || UNSPLIT) continue;
       const double* __restrict__ qsrc = D.q[parity];
       const int ncp = nl * len;
       for (int t = threadIdx.x; t < ncp; t += blockDim.x) {
@@ -112,13 +117,21 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       int i, j;
       if (DIR == 0) { i = item.i0 - kNG + k; j = item.j0 + l; }
       else { i = item.i0 + l; j = item.j0 - kNG + k; }
-      double sgn = 1.0;
+      double sgn = 1.0, sgt = 1.0;
       if (DIR == 0) {
         if (i < 0) { i = -1 - i; sgn = -1.0; }
         else if (i >= NX) { i = 2 * NX - 1 - i; sgn = -1.0; }
+        if (UNSPLIT) {  // ghost rows beyond the domain: wall mirror
+          if (j < 0) { j = -1 - j; sgt = -1.0; }
+          else if (j >= NY) { j = 2 * NY - 1 - j; sgt = -1.0; }
+        }
       } else {
         if (j < 0) { j = -1 - j; sgn = -1.0; }
         else if (j >= NY) { j = 2 * NY - 1 - j; sgn = -1.0; }
+        if (UNSPLIT) {
+          if (i < 0) { i = -1 - i; sgt = -1.0; }
+          else if (i >= NX) { i = 2 * NX - 1 - i; sgt = -1.0; }
+        }
       }
       const size_t o = (size_t)j * Pt + i;
       const int c = cslot<DIR>(l, k, len, nl);
@@ -133,7 +146,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const double hu = qin[(3 * m + 1) * plane + o];
         const double hv = qin[(3 * m + 2) * plane + o];
         const double hn = (DIR == 0 ? hu : hv) * sgn;
-        const double ht = DIR == 0 ? hv : hu;
+        const double ht = UNSPLIT ? (DIR == 0 ? hv : hu) * sgt : (DIR == 0 ? hv : hu);
         rec[3 * m] = h; rec[3 * m + 1] = hn; rec[3 * m + 2] = ht;
         // comparisons on bit patterns (integer unit): for a bound b >= +0 and any non-NaN
         // x, x > b exactly when bits(x) > bits(b) as signed 64-bit integers
@@ -196,6 +209,10 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         wav[(WR::T1 + m) * kMaxEdges + es] = W.t1[m];
       }
       wallb[es] = W.wall;
+      if (UNSPLIT) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) wav[(WR::HB + m) * kMaxEdges + es] = W.hbt[m];
+      }
       if (interior && e >= 1 && e <= len + 1) {
         // |s| as bit patterns: non-negative doubles order like unsigned integers (NaN above all)
         unsigned long long sm = __double_as_longlong(smax);
@@ -333,14 +350,63 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         if ((wall >> (2 * m)) & 1) { Lc[3 * m] = 0.0; Lc[3 * m + 1] = 0.0; Lc[3 * m + 2] = 0.0; }
         if ((wall >> (2 * m + 1)) & 1) { Rc[3 * m] = 0.0; Rc[3 * m + 1] = 0.0; Rc[3 * m + 2] = 0.0; }
       }
+      if constexpr (UNSPLIT) {
+        // transverse split of what each cell receives, at this edge's state
+        const int wL = wetb[cslot<DIR>(l, e, len, nl)], wR = wetb[cslot<DIR>(l, e + 1, len, nl)];
+        double hbt[M], un[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          hbt[m] = wav[(WR::HB + m) * kMaxEdges + es];
+          un[m] = wav[(WR::US + m) * kMaxEdges + es];
+        }
+        const int full = (1 << M) - 1;
+        const long long pl = DIR == 0 ? D.uxp : D.uyp;
+        const int line = (DIR == 0 ? item.j0 : item.i0) + l;
+        const int a = (DIR == 0 ? item.i0 : item.j0) + e1;
+        double* __restrict__ base = D.ue + (DIR == 0 ? 0 : 6LL * F * D.uxp) +
+                                    (DIR == 0 ? (long long)(line + 1) * (NX + 1) + a
+                                              : (long long)a * (NX + 2) + (line + 1));
+        // field f of the normal frame -> plane of the (h, hu, hv) order
+        auto put = [&](int grp, const double* v) {
+#pragma unroll
+          for (int m = 0; m < M; ++m) {
+            base[(grp * F + 3 * m) * pl] = v[3 * m];
+            base[(grp * F + 3 * m + (DIR == 0 ? 1 : 2)) * pl] = v[3 * m + 1];
+            base[(grp * F + 3 * m + (DIR == 0 ? 2 : 1)) * pl] = v[3 * m + 2];
+          }
+        };
+        put(0, Lc);
+        put(1, Rc);
+        double up[F], dn[F];
+        if (M == 2 && wL == full && wR == full) {
+          TransEig2 E;
+          trans_eigen2(P, hbt, vh, E);
+          trans_apply2(E, un, vh, Lc, up, dn);
+          put(2, up);
+          put(3, dn);
+          trans_apply2(E, un, vh, Rc, up, dn);
+          put(4, up);
+          put(5, dn);
+        } else {
+          const int act = wL | wR;
+          trans_apply_layers<M>(P, act, hbt, un, vh, Lc, up, dn);
+          put(2, up);
+          put(3, dn);
+          trans_apply_layers<M>(P, act, hbt, un, vh, Rc, up, dn);
+          put(4, up);
+          put(5, dn);
+        }
+      }
     }
     __syncthreads();  // every neighbour read of the waves is done: reuse the space
     if (gl >= 0) {
-      const int g = gslot<DIR>(gl, ge, len, nl);
+      if (!UNSPLIT) {
+        const int g = gslot<DIR>(gl, ge, len, nl);
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        wav[f * kMaxEdges + g] = Lc[f];
-        wav[(F + f) * kMaxEdges + g] = Rc[f];
+        for (int f = 0; f < F; ++f) {
+          wav[f * kMaxEdges + g] = Lc[f];
+          wav[(F + f) * kMaxEdges + g] = Rc[f];
+        }
       }
       // Mass flux of every layer through this edge, seen from the left cell:
       // hn_L + (A-dQ + F)_h. Recorded at coarse/fine interfaces of this level (for the
@@ -371,8 +437,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     }
     __syncthreads();
 
-    // ---- phase 4: update the cells of the tile ----
-    const int nupd = nl * len;
+    // ---- phase 4: update the cells of the tile (the unsplit step updates in its own kernel) ----
+    const int nupd = UNSPLIT ? 0 : nl * len;
     for (int t = threadIdx.x; t < nupd; t += blockDim.x) {
       int l, k;
       if (DIR == 0) { l = t / len; k = t - l * len; }
@@ -410,11 +476,11 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 }
 
 size_t sweep_smem_bytes(int M) {
-  const int rn = 7 * M + 1, wn = 2 * M * M + 7 * M;
+  const int rn = 7 * M + 1, wn = 2 * M * M + 8 * M;
   return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
 }
 
-template <int M, int DIR, int MINB, bool STORE>
+template <int M, int DIR, int MINB, bool STORE, bool UNSPLIT>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                   const int* n_items_dev, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
@@ -422,13 +488,13 @@ static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, co
   const size_t sm = sweep_smem_bytes(M);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE, UNSPLIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sweep_kernel<M, DIR, MINB, STORE><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity, record,
-                                                                smax_bits, lost_count, est, eplane);
+  sweep_kernel<M, DIR, MINB, STORE, UNSPLIT><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity,
+                                                                         record, smax_bits, lost_count, est, eplane);
   return cudaGetLastError();
 }
 
@@ -439,19 +505,24 @@ static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc*
                                   double* est, long long eplane) {
   if constexpr (M == 2) {
     if (est != nullptr)
-      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, true>(P, descs, items, n_items_dev, grid, parity, record,
-                                                          smax_bits, lost_count, st, est, eplane)
-                       : launch_sweep_t<M, DIR, 1, true>(P, descs, items, n_items_dev, grid, parity, record,
-                                                          smax_bits, lost_count, st, est, eplane);
+      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, true, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                 smax_bits, lost_count, st, est, eplane)
+                       : launch_sweep_t<M, DIR, 1, true, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                 smax_bits, lost_count, st, est, eplane);
   }
   if constexpr (M >= 3) {  // three layers fill the register file and shared memory: one CTA per SM
-    return launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
-                                            lost_count, st, nullptr, 0);
+    return launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                                   lost_count, st, nullptr, 0);
   } else {
-    return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false>(P, descs, items, n_items_dev, grid, parity, record,
-                                                         smax_bits, lost_count, st, nullptr, 0)
-                     : launch_sweep_t<M, DIR, 1, false>(P, descs, items, n_items_dev, grid, parity, record,
-                                                         smax_bits, lost_count, st, nullptr, 0);
+    if (P.unsplit)
+      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, true>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                 smax_bits, lost_count, st, nullptr, 0)
+                       : launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                 smax_bits, lost_count, st, nullptr, 0);
+    return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                smax_bits, lost_count, st, nullptr, 0)
+                     : launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, grid, parity, record,
+                                                                smax_bits, lost_count, st, nullptr, 0);
   }
 }
 

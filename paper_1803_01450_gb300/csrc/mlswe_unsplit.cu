@@ -1,0 +1,123 @@
+// Cell update of the unsplit step (wave propagation with transverse Riemann solves, in the
+// corner-transport form of the book's Ch. 21), after the two edge passes of the sweep kernel
+// (UNSPLIT variant) have written, for every x edge and y edge of the level's patches (and of
+// their first ghost lines), the fluctuation each of its two cells receives (correction flux
+// included) and the transverse split of each towards +t and -t. For cell (i, j):
+//   Q -= dt/dx (R_{i-1/2} + L_{i+1/2}) + dt/dy (R_{j-1/2} + L_{j+1/2})
+//        + dt/dx (Gx_{i+1/2} - Gx_{i-1/2}) + dt/dy (Gy_{j+1/2} - Gy_{j-1/2}),
+// with the transverse correction fluxes Gx = -(dt / 2 dy) (parts towards +x received by the
+// cell left of the x edge + parts towards -x received by the cell right of it), Gy likewise
+// with dt / 2 dx; then the positivity fix. At coarse/fine interfaces and refined patch
+// boundaries the transverse part of the mass flux is added to the flux records the edge
+// passes started (one cell owns each edge). Memory-bound: every thread one cell, rows of a
+// tile along x so that neighbouring threads read neighbouring edges.
+#include <cuda_runtime.h>
+#include "mlswe_device.cuh"
+
+namespace mlswe {
+
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
+                      const int* __restrict__ n_items_dev, int parity, int record) {
+  constexpr int F = 3 * M;
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const SweepItem item = items[it];
+    const LevelDesc& D = descs[item.desc];
+    const int NX = D.NX, NY = D.NY, Pt = D.P;
+    const size_t plane = (size_t)NY * Pt;
+    const double* __restrict__ qin = D.q[parity];
+    double* __restrict__ qout = D.q[parity ^ 1];
+    const int len = item.len, ncell = item.nlines * len;
+    if (D.active != nullptr && *D.active == 0) {
+      // no step for this member in this substep: copy the state through
+      for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+        const int l = t / len, k = t - l * len;
+        const size_t o = (size_t)(item.j0 + l) * Pt + (item.i0 + k);
+#pragma unroll
+        for (int f = 0; f < F; ++f) qout[f * plane + o] = qin[f * plane + o];
+      }
+      continue;
+    }
+    const double dt = *D.dt;
+    const double nux = dt * D.inv_dx, nuy = dt * D.inv_dy;
+    const double hxy = 0.5 * nux * nuy;
+    const double* __restrict__ X = D.ue;
+    const double* __restrict__ Y = D.ue + 6LL * F * D.uxp;
+    const long long xp = D.uxp, yp = D.uyp;
+    const long long xr = NX + 1, yr = NX + 2;  // edges per x-edge row, per y-edge row
+    const bool rec = record && (D.covered != nullptr || D.in_patch != nullptr);
+    const long long tol_bits = __double_as_longlong(P.dry_tol);
+    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+      const int l = t / len, k = t - l * len;
+      const int i = item.i0 + k, j = item.j0 + l;
+      const size_t o = (size_t)j * Pt + i;
+      const long long xl = (long long)(j + 1) * xr + i;  // x edge left of the cell
+      const long long yb = (long long)j * yr + (i + 1);   // y edge below the cell
+      // groups: 0 into the lower-index cell, 1 into the higher-index cell, 2/3 the transverse
+      // parts of group 0 towards +t/-t, 4/5 those of group 1
+      auto XG = [&](int g, int f, long long e) { return X[(long long)(g * F + f) * xp + e]; };
+      auto YG = [&](int g, int f, long long e) { return Y[(long long)(g * F + f) * yp + e]; };
+      double qn[F], gxl[M], gxr[M], gyb[M], gyt[M];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        const double dxn = XG(1, f, xl) + XG(0, f, xl + 1);
+        const double dyn = YG(1, f, yb) + YG(0, f, yb + yr);
+        const double sgt = XG(4, f, xl) + XG(2, f, xl + 1) + XG(5, f, xl + xr) + XG(3, f, xl + xr + 1);
+        const double sgb = XG(4, f, xl - xr) + XG(2, f, xl - xr + 1) + XG(5, f, xl) + XG(3, f, xl + 1);
+        const double sgr = YG(4, f, yb) + YG(2, f, yb + yr) + YG(5, f, yb + 1) + YG(3, f, yb + yr + 1);
+        const double sgl = YG(4, f, yb - 1) + YG(2, f, yb + yr - 1) + YG(5, f, yb) + YG(3, f, yb + yr);
+        qn[f] = qin[f * plane + o] - nux * dxn - nuy * dyn + hxy * ((sgr - sgl) + (sgt - sgb));
+        if (f % 3 == 0) {
+          gxl[f / 3] = sgl; gxr[f / 3] = sgr; gyb[f / 3] = sgb; gyt[f / 3] = sgt;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        if (__double_as_longlong(qn[3 * m]) < 0) qn[3 * m] = 0.0;
+        if (__double_as_longlong(qn[3 * m]) <= tol_bits) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) qout[f * plane + o] = qn[f];
+      if (!rec) continue;
+      // Transverse part of the mass flux through this cell's left / bottom edge, and through
+      // its right / top edge when the neighbour there is in no patch of the level (otherwise
+      // that neighbour owns the edge).
+      const double hy = -0.5 * nuy, hx = -0.5 * nux;
+      auto add = [&](bool xdir, int a, int line, const double* s, double h) {
+        const size_t cA = xdir ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
+        const size_t cB = xdir ? cA + 1 : cA + NX;
+        const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
+        const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
+        if (!iface && !bnd) return;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const double gm = h * s[m];
+          const size_t fo = xdir ? ((size_t)m * NY + line) * (NX + 1) + a : ((size_t)m * (NY + 1) + a) * NX + line;
+          if (iface) (xdir ? D.fxc : D.fyc)[fo] += gm;
+          if (bnd) (xdir ? D.fxf : D.fyf)[fo] += dt * gm;
+        }
+      };
+      if (i >= 1) add(true, i, j, gxl, hy);
+      if (i + 1 <= NX - 1 && D.in_patch != nullptr && D.in_patch[(size_t)j * NX + i + 1] == 0) add(true, i + 1, j, gxr, hy);
+      if (j >= 1) add(false, j, i, gyb, hx);
+      if (j + 1 <= NY - 1 && D.in_patch != nullptr && D.in_patch[(size_t)(j + 1) * NX + i] == 0)
+        add(false, j + 1, i, gyt, hx);
+    }
+  }
+}
+
+cudaError_t launch_unsplit_update(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
+                                  const int* n_items_dev, int grid, int parity, int record, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  if (P.M == 1)
+    unsplit_update_kernel<1><<<grid, kThreads, 0, st>>>(P, descs, items, n_items_dev, parity, record);
+  else if (P.M == 2)
+    unsplit_update_kernel<2><<<grid, kThreads, 0, st>>>(P, descs, items, n_items_dev, parity, record);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace mlswe

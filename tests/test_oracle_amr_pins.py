@@ -216,11 +216,14 @@ def test_clustering_tiny_exhaustive():
 
 
 # ------------------------------------------------------------------ composite AMR
-def test_amr_mass_conservation_with_reflux():
+@pytest.mark.parametrize("unsplit", [0, 1])
+def test_amr_mass_conservation_with_reflux(unsplit):
     """Walled, wet, flat-bottom two-layer AMR run: the composite mass of each layer is
-    constant to rounding (the reflux makes the coarse/fine edges conservative)."""
+    constant to rounding (the reflux makes the coarse/fine edges conservative; in the unsplit
+    form the recorded fluxes carry the transverse corrections, and sibling patches compute
+    their shared edges from the same cells)."""
     w = I.small(50)
-    P = O.params(M=2, dry_tol=1e-6)
+    P = O.params(M=2, dry_tol=1e-6, unsplit=unsplit)
     A = OracleAMR(P, (0, 0, 1, 1), 50, 50, 2, [2], -np.ones((100, 100)), min_side=16, max_side=64)
     A.set_state(0, w["q"])
     m0 = A.mass()
@@ -230,12 +233,13 @@ def test_amr_mass_conservation_with_reflux():
     assert np.all(np.abs(m1 - m0) <= 1e-13 * m0)
 
 
-def test_amr_lake_at_rest_on_shelf():
+@pytest.mark.parametrize("unsplit", [0, 1])
+def test_amr_lake_at_rest_on_shelf(unsplit):
     """Three levels over a shelf at rest: surfaces stay flat, momenta stay zero."""
     n0, r = 16, [2, 2]
     nf = n0 * 4
     Bf = I.shelf_B(np.meshgrid(I.centers(0, 1e5, nf), I.centers(0, 1e5, nf))[0])
-    P = O.params(M=2, dry_tol=1e-3)
+    P = O.params(M=2, dry_tol=1e-3, unsplit=unsplit)
     A = OracleAMR(P, (0, 0, 1e5, 1e5), n0, n0, 3, r, Bf, min_side=8, max_side=32)
     q0 = I.layered_state(A.lev[0].B, np.zeros_like(A.lev[0].B), -200.0 * np.ones_like(A.lev[0].B))
     A.set_state(0, q0)
