@@ -49,6 +49,12 @@ M_LAYERS = 2
 FP64_FLOP_PER_CELL_UPDATE = 1293.25
 # The same count for the three-layer version of the workload (inputs.scale3).
 FP64_FLOP_PER_CELL_UPDATE_3 = 4134.82
+# The unsplit step (transverse Riemann solves) on the same workload, per cell update: each edge
+# pass (x edges, y edges) and the transverse correction fluxes plus the update.
+FP64_FLOP_PER_CELL_UPDATE_UNSPLIT = 2456.89
+FP64_FLOP_UNSPLIT_EDGE_PASS = 1143.94
+# HBM copy bandwidth measured on this part (MEASURED_PEAKS.json, STREAM-style copy).
+HBM_PEAK_GBS = 6674.8
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
@@ -407,15 +413,56 @@ def bench_three_layers(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
             "frac_of_fp64_peak": ach / FP64_PEAK_TFLOPS, "tiles": tiles}
 
 
+def bench_unsplit(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
+    """The headline workload with the unsplit step (transverse Riemann solves): throughput,
+    the x edge pass against the FP64 peak, and the update kernel against HBM (it reads the
+    12 x 3M per-edge values, the state, and writes the state: 14 x 3M doubles per cell)."""
+    w = I.scale(n, seed=1000)
+    cfg = pkg.Config(M=2, dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1, unsplit=1)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)], stream=stream.cuda_stream)
+    H.set_bathymetry(0, w["B"])
+    H.set_state(0, 0, w["q"])
+    tiles = H.autotune(0, iters=2)
+    H.set_dt(0, 0.9 * w["dx"] / 205.0)
+    for _ in range(warmup):
+        H.step_level(0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        H.step_level(0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    H.timing(enable=True)
+    for _ in range(steps):
+        H.step_level(0)
+    torch.cuda.synchronize()
+    per_kernel, _ = H.timing(enable=False)
+    H.close()
+    kms = {k: v[0] / v[1] for k, v in per_kernel.items() if v[1]}
+    x_ms = kms["sweep_x"]
+    ach = FP64_FLOP_UNSPLIT_EDGE_PASS * n * n / (x_ms * 1e-3) / 1e12
+    upd_bytes = 14 * 3 * M_LAYERS * 8 * n * n
+    upd_gbs = upd_bytes / (kms["update"] * 1e-3) / 1e9
+    return {"workload": f"{n}^2 shelf, 2 layers, 8 humps, order 2 MC, walls, unsplit step",
+            "lcups": n * n * M_LAYERS * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "kernels_ms_per_launch": kms, "flop_per_cell_update": FP64_FLOP_PER_CELL_UPDATE_UNSPLIT,
+            "x_pass_achieved_tflops": ach, "x_pass_frac_of_fp64_peak": ach / FP64_PEAK_TFLOPS,
+            "update_achieved_gbs": upd_gbs, "update_frac_of_hbm": upd_gbs / HBM_PEAK_GBS,
+            "update_algorithmic_bytes": upd_bytes, "tiles": tiles}
+
+
 def run_only(name):
     import torch
     import paper_1803_01450_gb300 as pkg
     pkg.build()
     stream = torch.cuda.Stream()
     fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint,
-          "three": bench_three_layers, "dynrt": bench_dynamic_rt}[name]
+          "three": bench_three_layers, "dynrt": bench_dynamic_rt, "unsplit": bench_unsplit}[name]
     key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint", "three": "three_layers",
-           "dynrt": "dynamic_time_ratio"}[name]
+           "dynrt": "dynamic_time_ratio", "unsplit": "unsplit"}[name]
     print(json.dumps({key: fn(pkg, torch, stream)}), flush=True)
 
 
@@ -518,6 +565,7 @@ def run_gpu(args):
         line["adjoint"] = bench_adjoint(pkg, torch, stream)
         line["three_layers"] = bench_three_layers(pkg, torch, stream)
         line["dynamic_time_ratio"] = bench_dynamic_rt(pkg, torch, stream)
+        line["unsplit"] = bench_unsplit(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -534,7 +582,7 @@ def main():
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
-    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "dynrt"],
+    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "dynrt", "unsplit"],
                     help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()
     if args.only:

@@ -93,6 +93,8 @@ def lib():
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, _u8p]
         L.or_bathy_average.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.or_count_sweep.argtypes = [_pp, ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.POINTER(ctypes.c_longlong)]
+        L.or_count_unsplit.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, _dp, _dp, ctypes.POINTER(ctypes.c_longlong)]
         L.or_adjoint_step.argtypes = [_pp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, _dp, _dp, _dp, _dp]
     return _lib
@@ -193,6 +195,27 @@ def flops_per_cell_update(P: Params, q, B, dx, dy, dt, rows, cols):
         tot += sum(count_sweep(P, line, Bl, dt / dy)); cells += ny
     # one x sweep and one y sweep per cell update
     return 2.0 * tot / cells
+
+
+def flops_per_cell_update_unsplit(P: Params, q, B, dx, dy, dt, windows):
+    """FP64 operations of the unsplit step per cell update, by phase, counted on n x n
+    windows (i0, j0, n) of a dense state q [3M][ny][nx] with their two-cell rings taken from
+    q (windows away from the walls). The edge passes solve n + 2 lines of n cells (one ghost
+    line per side); their per-line cost is charged to the n interior lines only, so 'x' and
+    'y' are the work of the edges of one cell, 'update' that of the transverse correction
+    fluxes and the cell update. Returns a dict x, y, update, total."""
+    tot = np.zeros(4)
+    cells = 0
+    for (i0, j0, n) in windows:
+        qp = _c(q[:, j0 - NG:j0 + n + NG, i0 - NG:i0 + n + NG])
+        Bp = _c(B[j0 - NG:j0 + n + NG, i0 - NG:i0 + n + NG])
+        out = (ctypes.c_longlong * 16)()
+        lib().or_count_unsplit(ctypes.byref(P), n, n, float(dx), float(dy), float(dt), _d(qp), _d(Bp), out)
+        ph = np.array(out, dtype=float).reshape(4, 4).sum(axis=1)
+        tot += np.array([ph[0] / (n + 2) * n, ph[1] / (n + 2) * n, ph[2], ph[3]])
+        cells += n * n
+    x, y, upd = tot[0] / cells, tot[1] / cells, (tot[2] + tot[3]) / cells
+    return {"x": x, "y": y, "update": upd, "total": x + y + upd}
 
 
 # --------------------------------------------------------------------------- grid level

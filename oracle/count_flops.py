@@ -1,7 +1,8 @@
 """Prints the algorithmic FP64 operation count per cell update of the method (one x sweep
 plus one y sweep, second order with the MC limiter, eigenvalue guesses plus two Newton
 steps), counted by the oracle's counting scalar on interior rows and columns of the
-2048 x 2048 shelf workload (two layers; and its three-layer version). Run:
+2048 x 2048 shelf workload (two layers; its three-layer version; and the unsplit step on
+three 96 x 96 windows of it). Run:
 python -m oracle.count_flops
 
 TEST/MEASUREMENT INFRASTRUCTURE: the constant in bench.py comes from this script."""
@@ -27,6 +28,11 @@ def main():
     f3 = O.flops_per_cell_update(P3, w3["q"], w3["B"], w3["dx"], w3["dy"], dt, rows=[100, 1024, 1900],
                                  cols=[100, 1024, 1900])
     print(f"three layers (scale3 workload), order=2 eigen=0: {f3:.2f} FP64 operations per cell update")
+    Pu = O.params(M=2, dry_tol=1e-3, order=2, unsplit=1)
+    fu = O.flops_per_cell_update_unsplit(Pu, w["q"], w["B"], w["dx"], w["dy"], dt,
+                                         windows=[(100, 100, 96), (976, 976, 96), (1852, 1852, 96)])
+    print(f"unsplit, order=2 eigen=0: {fu['total']:.2f} FP64 operations per cell update "
+          f"(x edges {fu['x']:.2f}, y edges {fu['y']:.2f}, transverse fluxes and update {fu['update']:.2f})")
 
 
 if __name__ == "__main__":

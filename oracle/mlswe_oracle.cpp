@@ -35,6 +35,7 @@
 #include <cstring>
 #include <vector>
 #include <algorithm>
+#include <omp.h>
 
 namespace {
 
@@ -658,47 +659,48 @@ void positivity(const Params& P, T* q) {
 // the general branch), otherwise each layer with a wet side alone with speeds
 // utt_m -+ sqrt(g hbt_m); a layer dry on both sides sends nothing.
 template <class T>
-void transverse(const Params& P, const Waves<T>& W, const T* dq, T* bp, T* bm) {
+void transverse(const Params& P, const Waves<T>& W, int nv, const T* const* dq, T* const* bp, T* const* bm) {
+  // nv fluctuations of the same edge share its eigen-decomposition
   const int M = P.M, F = 3 * M;
-  for (int f = 0; f < F; ++f) { bp[f] = T(0.0); bm[f] = T(0.0); }
-  auto send = [&](const T& speed, int f, const T& amount) {
+  for (int v = 0; v < nv; ++v)
+    for (int f = 0; f < F; ++f) { bp[v][f] = T(0.0); bm[v][f] = T(0.0); }
+  auto send = [&](int v, const T& speed, int f, const T& amount) {
     const double sv = val(speed);
-    if (sv > 0.0) bp[f] = bp[f] + speed * amount;
-    else if (sv < 0.0) bm[f] = bm[f] + speed * amount;
+    if (sv > 0.0) bp[v][f] = bp[v][f] + speed * amount;
+    else if (sv < 0.0) bm[v][f] = bm[v][f] + speed * amount;
   };
   if (W.coupled) {
     const int N = 2 * M;
-    T mu[2 * MAXM], dh[2 * MAXM][MAXM], beta[2 * MAXM];
+    T mu[2 * MAXM], dh[2 * MAXM][MAXM];
     if (M == 2 && !P.force_general) {
       int lost = 0;
       two_layer_eigen(P, W.utt[0], W.utt[1], W.hbt[0], W.hbt[1], mu, &lost);
       const T c1 = P.g * W.hbt[0];
-      T A[4][4], rhs[4];
       for (int p = 0; p < 4; ++p) {
         dh[p][0] = T(1.0);
         dh[p][1] = ((mu[p] - W.utt[0]) * (mu[p] - W.utt[0]) - c1) / c1;
-        A[0][p] = dh[p][0]; A[1][p] = mu[p]; A[2][p] = dh[p][1]; A[3][p] = dh[p][1] * mu[p];
       }
-      rhs[0] = dq[0]; rhs[1] = dq[2]; rhs[2] = dq[3]; rhs[3] = dq[5];
-      solve4(A, rhs, beta);
     } else {
       general_eigen(P, W.utt, W.hbt, mu, dh);
-      T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM];
+    }
+    for (int v = 0; v < nv; ++v) {
+      // strengths from the (h, ht) rows: sum_p beta_p (dh_m, mu_p dh_m) = (dq_h, dq_ht)_m
+      T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM], beta[2 * MAXM];
       for (int p = 0; p < N; ++p)
         for (int m = 0; m < M; ++m) { R[2 * m][p] = dh[p][m]; R[2 * m + 1][p] = mu[p] * dh[p][m]; }
-      for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[3 * m]; rhs[2 * m + 1] = dq[3 * m + 2]; }
+      for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[v][3 * m]; rhs[2 * m + 1] = dq[v][3 * m + 2]; }
       solve_n(N, R, rhs, beta);
-    }
-    // shear strength: what the acoustic waves leave of hn; they carry the whole depth change
-    // dq_h of every layer (the h rows of the system) and un dq_h of hn
-    for (int m = 0; m < M; ++m) {
-      for (int p = 0; p < N; ++p) {
-        const T a = beta[p] * dh[p][m];
-        send(mu[p], 3 * m, a);
-        send(mu[p], 3 * m + 1, W.unt[m] * a);
-        send(mu[p], 3 * m + 2, mu[p] * a);
+      // shear strength: what the acoustic waves leave of hn; they carry the whole depth
+      // change dq_h of every layer (the h rows of the system) and un dq_h of hn
+      for (int m = 0; m < M; ++m) {
+        for (int p = 0; p < N; ++p) {
+          const T a = beta[p] * dh[p][m];
+          send(v, mu[p], 3 * m, a);
+          send(v, mu[p], 3 * m + 1, W.unt[m] * a);
+          send(v, mu[p], 3 * m + 2, mu[p] * a);
+        }
+        send(v, W.utt[m], 3 * m + 1, dq[v][3 * m + 1] - W.unt[m] * dq[v][3 * m]);
       }
-      send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * dq[3 * m]);
     }
     return;
   }
@@ -706,11 +708,13 @@ void transverse(const Params& P, const Waves<T>& W, const T* dq, T* bp, T* bm) {
     if (!W.active[m]) continue;
     const T c = sqrt(P.g * W.hbt[m]);
     const T s1 = W.utt[m] - c, s2 = W.utt[m] + c;
-    const T b1 = (s2 * dq[3 * m] - dq[3 * m + 2]) / (s2 - s1);
-    const T b2 = (dq[3 * m + 2] - s1 * dq[3 * m]) / (s2 - s1);
-    send(s1, 3 * m, b1); send(s1, 3 * m + 1, W.unt[m] * b1); send(s1, 3 * m + 2, s1 * b1);
-    send(s2, 3 * m, b2); send(s2, 3 * m + 1, W.unt[m] * b2); send(s2, 3 * m + 2, s2 * b2);
-    send(W.utt[m], 3 * m + 1, dq[3 * m + 1] - W.unt[m] * dq[3 * m]);
+    for (int v = 0; v < nv; ++v) {
+      const T b1 = (s2 * dq[v][3 * m] - dq[v][3 * m + 2]) / (s2 - s1);
+      const T b2 = (dq[v][3 * m + 2] - s1 * dq[v][3 * m]) / (s2 - s1);
+      send(v, s1, 3 * m, b1); send(v, s1, 3 * m + 1, W.unt[m] * b1); send(v, s1, 3 * m + 2, s1 * b1);
+      send(v, s2, 3 * m, b2); send(v, s2, 3 * m + 1, W.unt[m] * b2); send(v, s2, 3 * m + 2, s2 * b2);
+      send(v, W.utt[m], 3 * m + 1, dq[v][3 * m + 1] - W.unt[m] * dq[v][3 * m]);
+    }
   }
 }
 
@@ -889,7 +893,8 @@ void step_patch_impl(const Params& P, int nx, int ny, double dx, double dy, doub
 // the corrections at the patch's own edges are complete.
 template <class T>
 void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double dy, double dt,
-                             T* q, const T* B, double* smax, T* fx, T* fy, int* lost) {
+                             T* q, const T* B, double* smax, T* fx, T* fy, int* lost,
+                             OpCount* snaps = nullptr /* counting runs: counter after each phase */) {
   const int M = P.M, F = 3 * M;
   const int PW = nx + 2 * NG, PH = ny + 2 * NG;
   const size_t plane = (size_t)PW * PH;
@@ -932,8 +937,12 @@ void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double 
         fluctuations(P, W[k], amdq, apdq);
         correction(P, W[k], W[k - 1], W[k + 1], nu, ft);
         for (int f = 0; f < F; ++f) { am[f] = amdq[f] + ft[f]; ap[f] = apdq[f] - ft[f]; }
-        transverse(P, W[k], am, u[0], u[1]);  // am: towards +t, towards -t
-        transverse(P, W[k], ap, u[2], u[3]);
+        {  // am, ap: their parts towards +t and -t
+          const T* in[2] = {am, ap};
+          T* up[2] = {u[0], u[2]};
+          T* dn[2] = {u[1], u[3]};
+          transverse(P, W[k], 2, in, up, dn);
+        }
         if (interior) {
           double s = 0.0;
           for (int p = 0; p < W[k].nw; ++p) s = std::max(s, std::fabs(val(W[k].s[p])));
@@ -956,6 +965,7 @@ void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double 
           }
       }
     }
+    if (snaps) snaps[dir] = g_ops;
   }
   // Transverse correction fluxes: Gy at y edges (i, j - 1/2), j in [0, ny], i in [0, nx);
   // Gx at x edges (i - 1/2, j), i in [0, nx], j in [0, ny).
@@ -989,6 +999,7 @@ void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double 
         if (i >= 0) { T* g = gx(i, cj); for (int f = 0; f < F; ++f) g[f] = g[f] - hy * lt[f]; }
       }
     }
+  if (snaps) snaps[2] = g_ops;
   // mass flux of every layer through the interior edges, seen from the lower-index cell:
   // its normal momentum + (A-dQ + Ft)_h + the transverse correction flux
   if (fx)
@@ -1022,6 +1033,7 @@ void step_patch_unsplit_impl(const Params& P, int nx, int ny, double dx, double 
       // written after every read of this cell's old state (the loops above read q only)
       for (int f = 0; f < F; ++f) q[(size_t)f * plane + pidx(nx, i, j)] = qn[f];
     }
+  if (snaps) snaps[3] = g_ops;
   if (smax) { smax[0] = sx; smax[1] = sy; }
   if (lost) *lost = lost_x + lost_y;
 }
@@ -1088,7 +1100,10 @@ void or_transverse(const or_params* pp, const double* qL, const double* qR, doub
   P.force_general = general;
   Waves<double> W;
   riemann(P, qL, qR, BL, BR, W);
-  transverse(P, W, dq, bp, bm);
+  const double* in[1] = {dq};
+  double* up[1] = {bp};
+  double* dn[1] = {bm};
+  transverse(P, W, 1, in, up, dn);
 }
 
 void or_eigen(const or_params* pp, double u1, double u2, double hb1, double hb2, double* lam, int* lost) {
@@ -1117,6 +1132,34 @@ void or_count_sweep(const or_params* pp, int n, const double* line, const double
   int lost = 0;
   sweep_line(P, n, l.data(), b.data(), nu, o.data(), (Cnt*)nullptr, &lost);
   out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt;
+}
+
+// Floating-point operations of one unsplit step on a patch array (ghost ring filled),
+// counted with the counting scalar on one thread: out[4k .. 4k+3] = additions, multiplications,
+// divisions, square roots of phase k: 0 the x edges (rows -1 .. ny), 1 the y edges
+// (columns -1 .. nx), 2 the transverse correction fluxes, 3 the update (and mass fluxes).
+void or_count_unsplit(const or_params* pp, int nx, int ny, double dx, double dy, double dt, const double* q,
+                      const double* B, long long* out) {
+  Params P = to_params(pp);
+  P.unsplit = 1;
+  const size_t plane = (size_t)(nx + 2 * NG) * (ny + 2 * NG);
+  std::vector<Cnt> qc(plane * 3 * P.M), bc(plane);
+  for (size_t k = 0; k < qc.size(); ++k) qc[k] = Cnt(q[k]);
+  for (size_t k = 0; k < plane; ++k) bc[k] = Cnt(B[k]);
+  const int threads = omp_get_max_threads();
+  omp_set_num_threads(1);  // one global counter
+  g_ops = OpCount();
+  OpCount snaps[4];
+  int lost = 0;
+  step_patch_unsplit_impl(P, nx, ny, dx, dy, dt, qc.data(), bc.data(), nullptr, (Cnt*)nullptr, (Cnt*)nullptr,
+                          &lost, snaps);
+  omp_set_num_threads(threads);
+  OpCount prev;
+  for (int k = 0; k < 4; ++k) {
+    out[4 * k] = snaps[k].add - prev.add; out[4 * k + 1] = snaps[k].mul - prev.mul;
+    out[4 * k + 2] = snaps[k].div - prev.div; out[4 * k + 3] = snaps[k].sqrt - prev.sqrt;
+    prev = snaps[k];
+  }
 }
 
 void or_fill_walls(int M, int nx, int ny, double* q, double* B, int sides) {

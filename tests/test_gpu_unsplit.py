@@ -127,6 +127,38 @@ def test_exchange_symmetry_on_the_gpu(mlswe_lib):
     assert rel_err(swap(b), a).max() < 1e-12
 
 
+def test_full_size_sampled(mlswe_lib):
+    """2048^2 shelf workload, one unsplit step in the benchmark's launch configuration;
+    sampled output cells checked against the oracle on their 9x9 input windows (a cell's
+    update reads cells within two of it, corners included)."""
+    w = I.scale(2048)
+    q, B = w["q"], w["B"]
+    n = 2048
+    cfg = mlswe_lib.Config(M=2, dry_tol=1e-3, max_levels=1, unsplit=1)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)])
+    H.set_bathymetry(0, B)
+    H.set_state(0, 0, q)
+    dt = 0.9 * w["dx"] / 205.0
+    H.step_level(0, dt=dt)
+    qg = H.get_state(0, 0)
+    H.close()
+    P = O.params(M=2, dry_tol=1e-3, unsplit=1)
+    rs = np.random.default_rng(8)
+    cells = [(int(rs.integers(4, n - 4)), int(rs.integers(4, n - 4))) for _ in range(48)]
+    scale = np.maximum(np.abs(qg).max(axis=(1, 2)), np.abs(q).max(axis=(1, 2)))
+    for (j, i) in cells:
+        sub = np.ascontiguousarray(q[:, j - 4:j + 5, i - 4:i + 5])
+        subB = np.ascontiguousarray(B[j - 4:j + 5, i - 4:i + 5])
+        pert = np.ascontiguousarray(sub * (1.0 + 2.0 ** -52 * rs.choice([-1.0, 1.0], size=sub.shape)))
+        O.step_patch(P, sub, subB, w["dx"], w["dy"], dt)
+        O.step_patch(P, pert, subB, w["dx"], w["dy"], dt)
+        ref = sub[:, 4, 4]
+        err = np.abs(qg[:, j, i] - ref) / np.maximum(scale, 1e-300)
+        sens = np.abs(pert[:, 4, 4] - ref) / np.maximum(scale, 1e-300)
+        assert np.all(err < np.maximum(TOL, 10.0 * sens)), (j, i, err, sens)
+        assert err[[0, 3]].max() < TOL, (j, i, err)
+
+
 def _amr_pair(pkg, levels, ratios, n, min_side, max_side, regrid, dynamic=0, Bf=None):
     nf = n * int(np.prod(ratios))
     if Bf is None:
