@@ -191,7 +191,7 @@ struct EdgeW {
 template <int M>
 struct WRec {  // shared-memory layout of EdgeW: mass of layer m, wave p at A + 2M m + p
   static constexpr int A = 0, S = 2 * M * M, Z = S + 2 * M, US = Z + M, VH = US + M, T0 = VH + M, T1 = T0 + M,
-                       HB = T1 + M, N = HB + M;
+                       N = T1 + M;
 };
 
 // Per-edge record of a coupled two-layer edge that the adjoint's reverse pass reads instead

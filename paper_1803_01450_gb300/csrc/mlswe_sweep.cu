@@ -30,6 +30,13 @@ __device__ __forceinline__ int gslot(int l, int e, int len, int nl) {
   return DIR == 0 ? l * (len + 1) + e : e * nl + l;
 }
 
+// Shared memory of the split layout in doubles: cell records, edge records, wall and wet
+// bytes (rounded up to whole doubles).
+__host__ __device__ constexpr size_t sweep_smem_doubles(int M) {
+  return (size_t)(7 * M + 1) * kMaxCells + (size_t)(2 * M * M + 7 * M) * kMaxEdges +
+         ((size_t)kMaxEdges * 4 + kMaxCells + 7) / 8;
+}
+
 // Largest |s| of a tile, then one atomicMax on the bit pattern. v holds |s| as a bit pattern
 // with the sign cleared, so non-negative doubles order like their unsigned 64-bit patterns
 // and a NaN (exponent all ones, mantissa not zero) lies above +inf: reducing the patterns
@@ -73,6 +80,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
   double* wav = cell + R::N * kMaxCells;                // [WR::N][kMaxEdges], reused for contributions
   int* wallb = reinterpret_cast<int*>(wav + WR::N * kMaxEdges);   // [kMaxEdges]
   unsigned char* wetb = reinterpret_cast<unsigned char*>(wallb + kMaxEdges);  // [kMaxCells]
+  // unsplit only: transverse depth of every edge [M][kMaxEdges], after the split layout
+  double* hbw = reinterpret_cast<double*>(smem) + sweep_smem_doubles(M);
   __shared__ double red[kThreads / 32];
 
   const int n_items = *n_items_dev;
@@ -211,7 +220,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       wallb[es] = W.wall;
       if (UNSPLIT) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) wav[(WR::HB + m) * kMaxEdges + es] = W.hbt[m];
+        for (int m = 0; m < M; ++m) hbw[m * kMaxEdges + es] = W.hbt[m];
       }
       if (interior && e >= 1 && e <= len + 1) {
         // |s| as bit patterns: non-negative doubles order like unsigned integers (NaN above all)
@@ -356,7 +365,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         double hbt[M], un[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          hbt[m] = wav[(WR::HB + m) * kMaxEdges + es];
+          hbt[m] = hbw[m * kMaxEdges + es];
           un[m] = wav[(WR::US + m) * kMaxEdges + es];
         }
         const int full = (1 << M) - 1;
@@ -475,17 +484,14 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
   }
 }
 
-size_t sweep_smem_bytes(int M) {
-  const int rn = 7 * M + 1, wn = 2 * M * M + 8 * M;
-  return (size_t)rn * kMaxCells * 8 + (size_t)wn * kMaxEdges * 8 + kMaxEdges * 4 + kMaxCells;
-}
+size_t sweep_smem_bytes(int M) { return sweep_smem_doubles(M) * 8; }
 
 template <int M, int DIR, int MINB, bool STORE, bool UNSPLIT>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
                                   const int* n_items_dev, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
                                   double* est, long long eplane) {
-  const size_t sm = sweep_smem_bytes(M);
+  const size_t sm = sweep_smem_bytes(M) + (UNSPLIT ? (size_t)M * kMaxEdges * 8 : 0);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE, UNSPLIT>,
