@@ -157,6 +157,16 @@ mlswe_status mlswe_get_bathymetry(mlswe_h h, int member, int level, double* B_ou
 mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q);
 mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out);
 
+/* Asynchronous input for pipelined runs: q (host [3M][ny][nx], page-locked for the copy to
+ * overlap) is copied to a device staging buffer on the library's own copy stream, and
+ * from there into the level's state, in order with the work already enqueued on the
+ * hierarchy's stream (so a step enqueued before reads the old state, one enqueued after
+ * the new one). Returns before the copy ends: q must stay unchanged until the next
+ * mlswe_synchronize or synchronising call. Two staging buffers alternate, so the copy of
+ * the next input overlaps the step in flight. Errors: EINVAL (bad member, level or null
+ * q), ENOMEM (staging allocation), ECUDA. */
+mlswe_status mlswe_set_state_async(mlswe_h h, int member, int level, const double* q);
+
 /* Patch layout of level >= 1: n boxes (host int32 [n][4], level-l indices).
  * Boxes must be disjoint, lie inside the domain, have sides that are
  * multiples of nothing in particular, and nest inside level l-1 patches with
@@ -231,6 +241,14 @@ mlswe_status mlswe_autotune(mlswe_h h, int level, int iters, int* chosen);
 /* Surface elevations eta_m (Eq. (4)) at n points (host [n][2], physical x, y)
  * from the finest level whose patch contains each point; eta_out host [n][M]. */
 mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out);
+
+/* mlswe_read_gauges without waiting: the gauge kernel and the copy into eta_out (host
+ * [n][M], page-locked for an asynchronous copy) are enqueued on the hierarchy's stream;
+ * the values are there after mlswe_synchronize. xy is read before the call returns. */
+mlswe_status mlswe_read_gauges_async(mlswe_h h, int member, int n, const double* xy, double* eta_out);
+
+/* Waits for all work of the hierarchy (its stream and the input copy stream). */
+mlswe_status mlswe_synchronize(mlswe_h h);
 
 /* Run counters (not in the paper; its own report counts cell updates and time,
  * Sec. 3). level_steps[l]: steps taken on level l (subcycles of mlswe_advance

@@ -113,6 +113,9 @@ _SIGS = {
     "mlswe_set_bathymetry": [_H, ctypes.c_int, _dp],
     "mlswe_get_bathymetry": [_H, ctypes.c_int, ctypes.c_int, _dp],
     "mlswe_set_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_set_state_async": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_read_gauges_async": [_H, ctypes.c_int, ctypes.c_int, _dp, _dp],
+    "mlswe_synchronize": [_H],
     "mlswe_get_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
     "mlswe_set_patches": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p],
     "mlswe_get_patches": [_H, ctypes.c_int, ctypes.c_int, _ip, _i32p],
@@ -228,6 +231,7 @@ class Hierarchy:
         or 0, free(pointer)) used instead of torch's caching allocator."""
         self.cfg = cfg
         self.L = lib()
+        self._pending = []  # host arrays of asynchronous copies, kept alive until synchronize()
         doms = (_Domain * len(domains))()
         for k, d in enumerate(domains):
             x0, y0, x1, y1, nx0, ny0 = d
@@ -292,6 +296,29 @@ class Hierarchy:
         ny, nx = self.shape(member, level)
         assert q.shape == (3 * self.M, ny, nx), q.shape
         self._check(self.L.mlswe_set_state(self.h, member, level, _d(q)), "set_state")
+
+    def set_state_async(self, member: int, level: int, q: np.ndarray):
+        """Enqueues q (page-locked for the copy to overlap running work) as the state of
+        (member, level) after the work already enqueued; q is kept alive and must stay
+        unchanged until synchronize()."""
+        ny, nx = self.shape(member, level)
+        if not (q.dtype == np.float64 and q.flags.c_contiguous and q.shape == (3 * self.M, ny, nx)):
+            raise MLSWEError(1, "set_state_async: q must be a C-contiguous float64 [3M][ny][nx] array")
+        self._pending.append(q)
+        self._check(self.L.mlswe_set_state_async(self.h, member, level, _d(q)), "set_state_async")
+
+    def read_gauges_async(self, member: int, xy: np.ndarray, out: np.ndarray):
+        """Enqueues the gauge read into out ([n][M] float64, page-locked for an asynchronous
+        copy); the values are there after synchronize()."""
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        if not (out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (len(xy), self.M)):
+            raise MLSWEError(1, "read_gauges_async: out must be a C-contiguous float64 [n][M] array")
+        self._pending.append(out)
+        self._check(self.L.mlswe_read_gauges_async(self.h, member, len(xy), _d(xy), _d(out)), "read_gauges_async")
+
+    def synchronize(self):
+        self._check(self.L.mlswe_synchronize(self.h), "synchronize")
+        self._pending.clear()
 
     def get_state(self, member: int, level: int) -> np.ndarray:
         ny, nx = self.shape(member, level)

@@ -546,6 +546,14 @@ mlswe_status mlswe_destroy(mlswe_h h) {
   cudaStreamSynchronize(h->st);
   invalidate_graphs(h);
   for (cudaEvent_t e : h->timer.pool) cudaEventDestroy(e);
+  if (h->copy_st) {
+    cudaStreamSynchronize(h->copy_st);
+    cudaStreamDestroy(h->copy_st);
+    for (int s = 0; s < 2; ++s) {
+      if (h->ev_copied[s]) cudaEventDestroy(h->ev_copied[s]);
+      if (h->ev_used[s]) cudaEventDestroy(h->ev_used[s]);
+    }
+  }
   std::vector<void*> all = h->allocations;
   for (void* p : all) dev_free(h, p);
   if (h->own_stream) cudaStreamDestroy(h->st);
@@ -571,6 +579,50 @@ mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q) 
                                   V.NX * 8, V.NY, cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->dt_ready = false;  // the next automatic step starts from this state's wave speeds
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_set_state_async(mlswe_h h, int member, int level, const double* q) {
+  if (!valid_member_level(h, member, level) || !q) return fail(h, MLSWE_EINVAL, "set_state_async: bad argument");
+  Level& V = h->mem[member].lev[level];
+  const int F = 3 * h->cfg.M;
+  const size_t plane = (size_t)V.NY * V.NX, bytes = plane * F * 8;
+  if (!h->copy_st) {
+    CUDA_TRY(h, cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+    for (int s = 0; s < 2; ++s) {
+      CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_copied[s], cudaEventDisableTiming));
+      CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_used[s], cudaEventDisableTiming));
+    }
+  }
+  if (bytes > h->stage_bytes) {
+    CUDA_TRY(h, cudaStreamSynchronize(h->copy_st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (int s = 0; s < 2; ++s) {
+      if (h->stage[s]) dev_free(h, h->stage[s]);
+      h->stage[s] = (double*)dev_alloc(h, bytes);
+      if (!h->stage[s]) { h->stage_bytes = 0; return fail(h, MLSWE_ENOMEM, "staging allocation failed"); }
+    }
+    h->stage_bytes = bytes;
+  }
+  const int s = h->stage_next;
+  h->stage_next ^= 1;
+  // the state copy that last read this staging buffer is done (no-op before its first use)
+  CUDA_TRY(h, cudaStreamWaitEvent(h->copy_st, h->ev_used[s], 0));
+  CUDA_TRY(h, cudaMemcpyAsync(h->stage[s], q, bytes, cudaMemcpyHostToDevice, h->copy_st));
+  CUDA_TRY(h, cudaEventRecord(h->ev_copied[s], h->copy_st));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->st, h->ev_copied[s], 0));
+  double* dst = V.q[h->parity[level]];
+  CUDA_TRY(h, cudaMemcpy2DAsync(dst, V.P * 8, h->stage[s], V.NX * 8, V.NX * 8, (size_t)V.NY * F,
+                                cudaMemcpyDeviceToDevice, h->st));
+  CUDA_TRY(h, cudaEventRecord(h->ev_used[s], h->st));
+  h->dt_ready = false;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_synchronize(mlswe_h h) {
+  if (!h) return MLSWE_EINVAL;
+  if (h->copy_st) CUDA_TRY(h, cudaStreamSynchronize(h->copy_st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
 }
 
@@ -689,7 +741,7 @@ mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long lon
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out) {
+static mlswe_status read_gauges_impl(mlswe_h h, int member, int n, const double* xy, double* eta_out, bool wait) {
   if (!valid_member_level(h, member, 0) || n < 0 || (n > 0 && (!xy || !eta_out)))
     return fail(h, MLSWE_EINVAL, "read_gauges: bad argument");
   if (n == 0) return MLSWE_OK;
@@ -717,9 +769,9 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
     cells[3 * k + 2] = bj;
   }
   const size_t need = cells.size() * 4 + par.size() * 4 + (size_t)n * M * 8 + 64;
+  // (the scratch is only reused by work later on the same stream: no wait needed)
   char* base = (char*)scratch_buffer(h, need);
   if (!base) return fail(h, MLSWE_ENOMEM, "gauge scratch allocation failed");
-  CUDA_TRY(h, cudaStreamSynchronize(h->st));
   double* d_out = (double*)base;
   int* d_cells = (int*)(base + (size_t)n * M * 8);
   int* d_par = d_cells + cells.size();
@@ -730,8 +782,16 @@ mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, d
   CUDA_TRY(h, launch_gauges(M, h->d_desc, d_par, d_cells, n, d_out, h->st));
   timer_end(h, tok);
   CUDA_TRY(h, cudaMemcpyAsync(eta_out, d_out, (size_t)n * M * 8, cudaMemcpyDeviceToHost, h->st));
-  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (wait) CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
+}
+
+mlswe_status mlswe_read_gauges(mlswe_h h, int member, int n, const double* xy, double* eta_out) {
+  return read_gauges_impl(h, member, n, xy, eta_out, true);
+}
+
+mlswe_status mlswe_read_gauges_async(mlswe_h h, int member, int n, const double* xy, double* eta_out) {
+  return read_gauges_impl(h, member, n, xy, eta_out, false);
 }
 
 mlswe_status mlswe_set_bathymetry(mlswe_h h, int member, const double* B_finest) {

@@ -150,6 +150,13 @@ struct Hier {
   LaunchTimer timer;
   long long kernel_launches = 0;   // every kernel this hierarchy launched
   void* scratch = nullptr;         // small per-call device scratch (gauges, flags)
+  // mlswe_set_state_async: copy stream, two staging buffers, events of their copies and of
+  // the state copies that read them
+  cudaStream_t copy_st = nullptr;
+  double* stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  int stage_next = 0;
   size_t scratch_bytes = 0;
   void* adj = nullptr;             // buffers of the fixed-grid adjoint (mlswe_adjoint.cu)
 
