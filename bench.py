@@ -210,12 +210,49 @@ def _time_advance(torch, H, stream, n_steps):
     return e0.elapsed_time(e1)
 
 
+def _amr_transfer_bytes(H, n0, r, M):
+    """Algorithmic bytes of one coarse step's level transfers on a 3-level layout (ratios r, r):
+    ghost fill (A7 with the refinement of A10): per ring cell of a refined patch (two cells
+    wide, once even where rings overlap) its 3M values written and its fine B read, plus the
+    coarse cells under the ring and their face neighbours read at two time levels with B;
+    coarsening (A11): every covered coarse cell reads its r^2 fine cells and writes itself;
+    reflux (A12): every coarse/fine edge reads the coarse and the r fine mass fluxes and
+    updates the uncovered cell's depths. Counts per level step times level steps per coarse
+    step (r on level 1, r^2 on level 2; transfers onto level l once per level-l step)."""
+    import scipy.ndimage as nd
+    F = 3 * M
+    shapes = [n0, n0 * r, n0 * r * r]
+    masks = [np.ones((n0, n0), bool)]
+    for l in (1, 2):
+        m = np.zeros((shapes[l], shapes[l]), bool)
+        for (i0, j0, i1, j1) in H.get_patches(0, l).tolist():
+            m[j0:j1, i0:i1] = True
+        masks.append(m)
+    cross = np.array([[0, 1, 0], [1, 1, 1], [0, 1, 0]], bool)
+    ghost = avg = refl = 0
+    for l in (1, 2):
+        m, nc = masks[l], shapes[l - 1]
+        ring = nd.binary_dilation(m, structure=np.ones((5, 5), bool)) & ~m
+        under = nd.binary_dilation(ring.reshape(nc, r, nc, r).any(axis=(1, 3)), structure=cross)
+        ghost += (int(ring.sum()) * (F + 1) * 8 + int(under.sum()) * (2 * F + 1) * 8) * r ** l
+        cov = m.reshape(nc, r, nc, r).any(axis=(1, 3))
+        avg += int(cov.sum()) * F * (r * r + 1) * 8 * r ** (l - 1)
+        inp = masks[l - 1]
+        ex = (cov[:, 1:] != cov[:, :-1]) & np.where(cov[:, 1:], inp[:, :-1], inp[:, 1:])
+        ey = (cov[1:, :] != cov[:-1, :]) & np.where(cov[1:, :], inp[:-1, :], inp[1:, :])
+        refl += (int(ex.sum()) + int(ey.sum())) * M * (3 + r) * 8 * r ** (l - 1)
+    return {"ghost_fill": ghost, "average": avg, "reflux": refl}
+
+
 def bench_batched_amr(pkg, torch, stream, steps=3):
-    """Three-level AMR over the shore bathymetry, 1000 + 3000 synthetic patches."""
+    """Three-level AMR over the shore bathymetry, 1000 + 3000 synthetic patches; then the level
+    transfers per kernel class and one regrid (flag tolerance 5e-5: the humps' slopes are about
+    1e-4, so the regrid refines around them)."""
     n0, r = 512, 4
     nf = n0 * r * r
     L = 1e5
-    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64)
+    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64,
+                     flag_tol=5e-5)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)], stream=stream.cuda_stream)
     xf = I.centers(0.0, L, nf)
     Bf = np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf)))
@@ -239,6 +276,51 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
     H.set_execution(use_graphs=False, per_patch_launches=True)
     H.advance(1)
     ms_p = _time_advance(torch, H, stream, max(1, steps // 2))
+    H.set_execution(use_graphs=True, per_patch_launches=False)
+    # level transfers of further coarse steps, timed per kernel class (direct launches)
+    H.timing(enable=True)
+    H.advance(steps)
+    torch.cuda.synchronize()
+    per, _ = H.timing(enable=False)
+    tb = _amr_transfer_bytes(H, n0, r, M_LAYERS)
+    transfers = {}
+    for k in ("ghost_fill", "average", "reflux"):
+        ms_k = per[k][0] / steps
+        gbs = tb[k] / (ms_k * 1e-3) / 1e9
+        transfers[k] = {"ms_per_coarse_step": ms_k, "launches_per_coarse_step": per[k][1] / steps,
+                        "algorithmic_bytes_per_coarse_step": tb[k], "achieved_gbs": gbs,
+                        "frac_of_hbm": gbs / HBM_PEAK_GBS}
+    transfers["sweeps_ms_per_coarse_step"] = (per["sweep_x"][0] + per["sweep_y"][0]) / steps
+    # one regrid (A8 flags + clustering, A10 refinement of the new patches)
+    old = [H.get_patches(0, l) for l in (1, 2)]
+    H.timing(enable=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.regrid(0)
+    torch.cuda.synchronize()
+    regrid_s = time.perf_counter() - t0
+    per, _ = H.timing(enable=False)
+    flag_cells = n0 * n0 + (n0 * r) ** 2
+    fb = flag_cells * ((M_LAYERS + 1) * 8 + 1)
+    new_cells = 0
+    for l, o in zip((1, 2), old):
+        nl = n0 * r ** l
+        a_new = np.zeros((nl, nl), bool)
+        a_old = np.zeros((nl, nl), bool)
+        for (i0, j0, i1, j1) in H.get_patches(0, l).tolist():
+            a_new[j0:j1, i0:i1] = True
+        for (i0, j0, i1, j1) in o.tolist():
+            a_old[j0:j1, i0:i1] = True
+        new_cells += int((a_new & ~a_old).sum())
+    ib = new_cells * (3 * M_LAYERS + 1) * 8
+    transfers["regrid"] = {"wall_ms": regrid_s * 1e3, "flags_ms": per["flags"][0],
+                           "flags_algorithmic_bytes": fb,
+                           "flags_achieved_gbs": fb / (per["flags"][0] * 1e-3) / 1e9 if per["flags"][0] else None,
+                           "interp_ms": per["interp_fine"][0], "new_fine_cells": new_cells,
+                           "interp_algorithmic_bytes": ib,
+                           "interp_achieved_gbs": ib / (per["interp_fine"][0] * 1e-3) / 1e9
+                           if per["interp_fine"][0] else None,
+                           "patches_after": [len(H.get_patches(0, l)) for l in (1, 2)]}
     H.close()
     lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
     lp = upd * M_LAYERS * max(1, steps // 2) / (ms_p * 1e-3)
@@ -247,7 +329,7 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
             "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
             "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
             "ms_per_coarse_step_batched": ms_b / steps, "ms_per_coarse_step_per_patch": ms_p / max(1, steps // 2),
-            "autotuned_tiles": chosen}
+            "autotuned_tiles": chosen, "level_transfers": transfers}
 
 
 def bench_dynamic_rt(pkg, torch, stream, steps=6):

@@ -45,15 +45,12 @@ __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* 
   B = C.B[o];
 }
 
-// mode 0: write every cell of the item box; mode 1: only in-domain cells outside every
-// patch of the fine level (ghost cells). substep >= 0 (ghost fill inside a coarse step): the
-// coarse state is taken at alpha = substep / rt of the fine level's member, and items of
-// members whose fine level is not active in this substep are skipped; substep < 0: alpha.
+// Every fine cell of the item boxes (new patches) from the coarse state at alpha; the ghost
+// rings use ghost_cells_kernel below.
 template <int M>
 __global__ void __launch_bounds__(256)
 interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha_in, int mode,
-              int substep) {
+              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha) {
   constexpr int F = 3 * M;
   const int n_items = *n_items_dev;
   const double inv_r = 1.0 / (double)r;
@@ -61,11 +58,6 @@ interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem
     const InterpItem item = items[it];
     const LevelDesc& C = descs[item.desc_c];
     const LevelDesc& Fd = descs[item.desc_f];
-    double alpha = alpha_in;
-    if (substep >= 0) {
-      if (Fd.active != nullptr && *Fd.active == 0) continue;
-      alpha = (double)substep / (double)(*Fd.rt);
-    }
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
     const int total = w * h;
     const double* qo = C.q[par_c ^ 1];
@@ -76,7 +68,6 @@ interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem
       const int I = item.i0 + t % w, J = item.j0 + t / w;
       if (I < 0 || J < 0 || I >= Fd.NX || J >= Fd.NY) continue;
       const size_t fo = (size_t)J * Fd.P + I;
-      if (mode == 1 && Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
       const int ic = I / r, jc = J / r, a = I - ic * r, b = J - jc * r;
       const double offx = (a + 0.5) * inv_r - 0.5, offy = (b + 0.5) * inv_r - 0.5;
       // coarse cell k and its face neighbours: 0 = k, 1 = west, 2 = east, 3 = south, 4 = north
@@ -139,14 +130,126 @@ interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem
 }
 
 cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
-                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
-                          cudaStream_t st, int substep) {
+                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha,
+                          cudaStream_t st) {
   if (M == 1)
-    interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+    interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
   else if (M == 3)
-    interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+    interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
   else
-    interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha, mode, substep);
+    interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
+  return cudaGetLastError();
+}
+
+// Ghost fill (mode 1 of the refinement above) organised per coarse cell: the thread of a
+// coarse cell under a ghost strip loads it and its four face neighbours once, forms the
+// wet flags, surfaces and minmod slopes of every layer once, and then reconstructs each of
+// its r x r fine cells that lies in the strip and in no patch of the fine level (the
+// per-fine-cell form recomputes all of that for every fine cell). Same formulas per fine
+// cell as interp_kernel.
+template <int M>
+__global__ void __launch_bounds__(256)
+ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const GhostCell* __restrict__ cells,
+                   const int* __restrict__ n_dev, int r, int par_c, int par_f, double alpha_in, int substep) {
+  constexpr int F = 3 * M;
+  const int n = *n_dev;
+  const double inv_r = 1.0 / (double)r;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const GhostCell g = cells[e];
+    const LevelDesc& C = descs[g.desc_c];
+    const LevelDesc& Fd = descs[g.desc_f];
+    double alpha = alpha_in;
+    if (substep >= 0) {
+      if (Fd.active != nullptr && *Fd.active == 0) continue;
+      alpha = (double)substep / (double)(*Fd.rt);
+    }
+    const double* qo = C.q[par_c ^ 1];
+    const double* qn = C.q[par_c];
+    double* qf = Fd.q[par_f];
+    const size_t fplane = (size_t)Fd.NY * Fd.P;
+    double q[5][F], Bc[5];
+    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc, q[0], Bc[0]);
+    coarse_cell<M>(C, qo, qn, alpha, g.ic - 1, g.jc, q[1], Bc[1]);
+    coarse_cell<M>(C, qo, qn, alpha, g.ic + 1, g.jc, q[2], Bc[2]);
+    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc - 1, q[3], Bc[3]);
+    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc + 1, q[4], Bc[4]);
+    // per layer: wet in the coarse cell, its surface and slopes, its momenta and their slopes
+    bool wet0[M];
+    double eta0[M], se[M][2], c0[M][2], sm[M][2][2];
+#pragma unroll
+    for (int m = M - 1; m >= 0; --m) {
+      bool wet[5];
+      double eta[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        bool wt = true;
+#pragma unroll
+        for (int n2 = 0; n2 <= m; ++n2) wt = wt && (q[c][3 * n2] > P.dry_tol);
+        wet[c] = wt;
+        double ev = Bc[c];
+#pragma unroll
+        for (int n2 = M - 1; n2 >= m; --n2) ev = ev + q[c][3 * n2];
+        eta[c] = ev;
+      }
+      wet0[m] = wet[0];
+      eta0[m] = eta[0];
+      se[m][0] = minmod_d(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
+      se[m][1] = minmod_d(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int f = 3 * m + 1 + k;
+        const double cv = q[0][f];
+        c0[m][k] = cv;
+        sm[m][k][0] = minmod_d(wet[1] ? cv - q[1][f] : 0.0, wet[2] ? q[2][f] - cv : 0.0);
+        sm[m][k][1] = minmod_d(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
+      }
+    }
+    for (int b = 0; b < r; ++b) {
+      const int J = g.jc * r + b;
+      if (J < g.j0 || J >= g.j1) continue;
+      for (int a = 0; a < r; ++a) {
+        const int I = g.ic * r + a;
+        if (I < g.i0 || I >= g.i1) continue;
+        if (Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
+        const size_t fo = (size_t)J * Fd.P + I;
+        const double offx = (a + 0.5) * inv_r - 0.5, offy = (b + 0.5) * inv_r - 0.5;
+        const double Bf = Fd.B[fo];
+        double hf[M], out[F];
+#pragma unroll
+        for (int m = M - 1; m >= 0; --m) {
+          double hv = 0.0, huv = 0.0, hvv = 0.0;
+          if (wet0[m]) {
+            const double ef = eta0[m] + se[m][0] * offx + se[m][1] * offy;
+            double bh = Bf;
+#pragma unroll
+            for (int n2 = M - 1; n2 > m; --n2) bh = bh + hf[n2];
+            hv = fmax(0.0, ef - bh);
+            if (hv > P.dry_tol) {
+              huv = c0[m][0] + sm[m][0][0] * offx + sm[m][0][1] * offy;
+              hvv = c0[m][1] + sm[m][1][0] * offx + sm[m][1][1] * offy;
+            }
+          }
+          hf[m] = hv;
+          out[3 * m] = hv;
+          out[3 * m + 1] = huv;
+          out[3 * m + 2] = hvv;
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) qf[f * fplane + fo] = out[f];
+      }
+    }
+  }
+}
+
+cudaError_t launch_ghost_cells(int M, const DevParams& P, const LevelDesc* descs, const GhostCell* cells,
+                               const int* n_dev, int grid, int r, int par_c, int par_f, double alpha, int substep,
+                               cudaStream_t st) {
+  if (M == 1)
+    ghost_cells_kernel<1><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+  else if (M == 3)
+    ghost_cells_kernel<3><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+  else
+    ghost_cells_kernel<2><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   return cudaGetLastError();
 }
 
@@ -295,94 +398,94 @@ cudaError_t launch_mask_boxes(uint8_t* mask, int NX, const int* boxes, int n, in
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(256)
-reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-              const int* __restrict__ n_items_dev, int r, int par_c) {
-  const int n_items = *n_items_dev;
+reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ cells,
+              const int* __restrict__ n_dev, int r, int par_c) {
+  // One thread per coarse cell of a patch of the coarse level that is not covered and has a
+  // covered face neighbour (the host lists them); it corrects its depths for all such edges.
+  const int n = *n_dev;
   const double inv_r = 1.0 / (double)r;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const InterpItem item = items[it];
-    const LevelDesc& C = descs[item.desc_c];
-    const LevelDesc& Fd = descs[item.desc_f];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const InterpItem cell = cells[e];
+    const LevelDesc& C = descs[cell.desc_c];
+    const LevelDesc& Fd = descs[cell.desc_f];
     if (C.active != nullptr && *C.active == 0) continue;  // no coarse step taken: nothing to correct
-    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const int total = w * h;
+    const int i = cell.i0, j = cell.j0;
     double* qc = C.q[par_c];
     const size_t cplane = (size_t)C.NY * C.P;
     const double dt_c = *C.dt;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int i = item.i0 + t % w, j = item.j0 + t / w;
-      const size_t c = (size_t)j * C.NX + i;
-      if (C.covered[c]) continue;
-      if (C.in_patch && !C.in_patch[c]) continue;
-      double dh[M];
+    const size_t c = (size_t)j * C.NX + i;
+    double dh[M];
 #pragma unroll
-      for (int m = 0; m < M; ++m) dh[m] = 0.0;
-      // west edge (i - 1/2): neighbour i-1 covered, this cell on the right: h -= corr
-      if (i > 0 && C.covered[c - 1]) {
+    for (int m = 0; m < M; ++m) dh[m] = 0.0;
+    // west edge (i - 1/2): neighbour i-1 covered, this cell on the right: h -= corr
+    if (i > 0 && C.covered[c - 1]) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          double fine = 0.0;
-          for (int k = 0; k < r; ++k) {
-            const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)i * r;
-            fine += Fd.fxf[fo];
-            Fd.fxf[fo] = 0.0;
-          }
-          const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i];
-          dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dx;
+      for (int m = 0; m < M; ++m) {
+        double fine = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < r; ++k) {
+          const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)i * r;
+          fine += Fd.fxf[fo];
+          Fd.fxf[fo] = 0.0;
         }
+        const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i];
+        dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dx;
       }
-      // east edge (i + 1/2): neighbour i+1 covered, this cell on the left: h += corr
-      if (i + 1 < C.NX && C.covered[c + 1]) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          double fine = 0.0;
-          for (int k = 0; k < r; ++k) {
-            const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)(i + 1) * r;
-            fine += Fd.fxf[fo];
-            Fd.fxf[fo] = 0.0;
-          }
-          const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i + 1];
-          dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dx;
-        }
-      }
-      if (j > 0 && C.covered[c - C.NX]) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          double fine = 0.0;
-          for (int k = 0; k < r; ++k) {
-            const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)j * r) * Fd.NX + (size_t)i * r + k;
-            fine += Fd.fyf[fo];
-            Fd.fyf[fo] = 0.0;
-          }
-          const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j) * C.NX + i];
-          dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dy;
-        }
-      }
-      if (j + 1 < C.NY && C.covered[c + C.NX]) {
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-          double fine = 0.0;
-          for (int k = 0; k < r; ++k) {
-            const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)(j + 1) * r) * Fd.NX + (size_t)i * r + k;
-            fine += Fd.fyf[fo];
-            Fd.fyf[fo] = 0.0;
-          }
-          const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j + 1) * C.NX + i];
-          dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dy;
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < M; ++m)
-        if (dh[m] != 0.0) qc[(3 * m) * cplane + (size_t)j * C.P + i] += dh[m];
     }
+    // east edge (i + 1/2): neighbour i+1 covered, this cell on the left: h += corr
+    if (i + 1 < C.NX && C.covered[c + 1]) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        double fine = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < r; ++k) {
+          const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)(i + 1) * r;
+          fine += Fd.fxf[fo];
+          Fd.fxf[fo] = 0.0;
+        }
+        const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i + 1];
+        dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dx;
+      }
+    }
+    if (j > 0 && C.covered[c - C.NX]) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        double fine = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < r; ++k) {
+          const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)j * r) * Fd.NX + (size_t)i * r + k;
+          fine += Fd.fyf[fo];
+          Fd.fyf[fo] = 0.0;
+        }
+        const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j) * C.NX + i];
+        dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dy;
+      }
+    }
+    if (j + 1 < C.NY && C.covered[c + C.NX]) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        double fine = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < r; ++k) {
+          const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)(j + 1) * r) * Fd.NX + (size_t)i * r + k;
+          fine += Fd.fyf[fo];
+          Fd.fyf[fo] = 0.0;
+        }
+        const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j + 1) * C.NX + i];
+        dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dy;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+      if (dh[m] != 0.0) qc[(3 * m) * cplane + (size_t)j * C.P + i] += dh[m];
   }
 }
 
-cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev, int grid,
+cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* cells, const int* n_dev, int grid,
                           int r, int par_c, cudaStream_t st) {
-  if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
-  else if (M == 3) reflux_kernel<3><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
-  else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, items, n_items_dev, r, par_c);
+  if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
+  else if (M == 3) reflux_kernel<3><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
+  else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
   return cudaGetLastError();
 }
 

@@ -9,16 +9,19 @@
 namespace mlswe {
 
 cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
-                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha, int mode,
-                          cudaStream_t st, int substep = -1);
+                          const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha,
+                          cudaStream_t st);
 cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
                                  int grid, int r, int par_c, int par_f, cudaStream_t st);
 cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long long cells, double dry_tol,
                          double inv_dx, double inv_dy, double tol2, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_mask_boxes(uint8_t* mask, int NX, const int* boxes, int n, int div, long long max_cells,
                               cudaStream_t st);
-cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev, int grid,
+cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* cells, const int* n_dev, int grid,
                           int r, int par_c, cudaStream_t st);
+cudaError_t launch_ghost_cells(int M, const DevParams& P, const LevelDesc* descs, const GhostCell* cells,
+                               const int* n_dev, int grid, int r, int par_c, int par_f, double alpha, int substep,
+                               cudaStream_t st);
 cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
                          const int* n_items_dev, int grid, const int* par_of_desc, unsigned long long* out,
                          cudaStream_t st);
@@ -43,6 +46,9 @@ static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
   } while (0)
 
 static int grid_full(Hier* H) { return 2 * H->num_sms; }
+// Flat transfer lists (one thread per entry): enough CTAs to keep the loads of several
+// entries in flight per SM.
+static int grid_flat(Hier* H) { return 8 * H->num_sms; }
 
 // Appends the chunks (sides <= kChunk) of box b as items.
 static void push_chunks(std::vector<InterpItem>& v, int dc, int df, Box b) {
@@ -51,11 +57,12 @@ static void push_chunks(std::vector<InterpItem>& v, int dc, int df, Box b) {
       v.push_back(InterpItem{dc, df, i, j, std::min(i + kChunk, b.i1), std::min(j + kChunk, b.j1)});
 }
 
-static mlswe_status upload_table(Hier* H, DevTable<InterpItem>& T, const std::vector<InterpItem>& v) {
+template <class T_>
+static mlswe_status upload_table(Hier* H, DevTable<T_>& T, const std::vector<T_>& v) {
   if ((int)v.size() > T.cap || !T.d) {
     if (T.d) dev_free(H, T.d);
     T.cap = std::max<int>(256, (int)v.size() * 3 / 2);
-    T.d = (InterpItem*)dev_alloc(H, T.cap * sizeof(InterpItem));
+    T.d = (T_*)dev_alloc(H, T.cap * sizeof(T_));
     if (!T.d) return fail(H, MLSWE_ENOMEM, "item table allocation failed");
     invalidate_graphs(H);
   }
@@ -65,7 +72,7 @@ static mlswe_status upload_table(Hier* H, DevTable<InterpItem>& T, const std::ve
   }
   T.count = (int)v.size();
   if (!v.empty())
-    CUDA_TRY(H, cudaMemcpyAsync(T.d, v.data(), v.size() * sizeof(InterpItem), cudaMemcpyHostToDevice, H->st));
+    CUDA_TRY(H, cudaMemcpyAsync(T.d, v.data(), v.size() * sizeof(T_), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaMemcpyAsync(T.d_count, &T.count, sizeof(int), cudaMemcpyHostToDevice, H->st));
   return MLSWE_OK;
 }
@@ -78,7 +85,8 @@ static mlswe_status build_tables(Hier* H) {
   std::vector<long long> cells(H->n_members * H->L, 0);
   std::vector<InterpItem> speed;
   for (int l = 0; l < H->L; ++l) {
-    std::vector<InterpItem> ghost, avg, refl;
+    std::vector<InterpItem> avg, refl;
+    std::vector<GhostCell> gcell;
     for (int m = 0; m < H->n_members; ++m) {
       const Level& V = H->mem[m].lev[l];
       const int d = H->desc_index(m, l);
@@ -96,14 +104,42 @@ static mlswe_status build_tables(Hier* H) {
                                  Box{gi0, b.j0, b.i0, b.j1},
                                  Box{b.i1, b.j0, gi1, b.j1}};
           for (const Box& s : strips)
-            if (s.i1 > s.i0 && s.j1 > s.j0) push_chunks(ghost, dc, d, s);
+            if (s.i1 > s.i0 && s.j1 > s.j0) {
+              for (int jc = s.j0 / r; jc <= (s.j1 - 1) / r; ++jc)
+                for (int ic = s.i0 / r; ic <= (s.i1 - 1) / r; ++ic)
+                  gcell.push_back(GhostCell{dc, d, ic, jc, s.i0, s.j0, s.i1, s.j1});
+            }
           push_chunks(avg, dc, d, Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
         }
       }
-      if (l + 1 < H->L && !H->mem[m].lev[l + 1].patches.empty())
-        for (const Box& b : V.patches) push_chunks(refl, d, H->desc_index(m, l + 1), b);
+      if (l + 1 < H->L && !H->mem[m].lev[l + 1].patches.empty()) {
+        // reflux cells: cells of a patch of this level, not covered by the next level, with a
+        // covered face neighbour (found around the coarsened boxes of the finer patches)
+        const int r = H->cfg.ratio[l], df = H->desc_index(m, l + 1);
+        std::vector<uint8_t> cov((size_t)V.NX * V.NY, 0), inp, seen((size_t)V.NX * V.NY, 0);
+        for (const Box& b : H->mem[m].lev[l + 1].patches)
+          for (int j = b.j0 / r; j < b.j1 / r; ++j)
+            std::memset(&cov[(size_t)j * V.NX + b.i0 / r], 1, b.i1 / r - b.i0 / r);
+        if (l > 0) {
+          inp.assign((size_t)V.NX * V.NY, 0);
+          for (const Box& b : V.patches)
+            for (int j = b.j0; j < b.j1; ++j) std::memset(&inp[(size_t)j * V.NX + b.i0], 1, b.i1 - b.i0);
+        }
+        auto visit = [&](int i, int j) {
+          if (i < 0 || j < 0 || i >= V.NX || j >= V.NY) return;
+          const size_t c = (size_t)j * V.NX + i;
+          if (seen[c] || cov[c] || (l > 0 && !inp[c])) return;
+          seen[c] = 1;
+          refl.push_back(InterpItem{d, df, i, j, i + 1, j + 1});
+        };
+        for (const Box& b : H->mem[m].lev[l + 1].patches) {
+          const int ci0 = b.i0 / r, cj0 = b.j0 / r, ci1 = b.i1 / r, cj1 = b.j1 / r;
+          for (int j = cj0; j < cj1; ++j) { visit(ci0 - 1, j); visit(ci1, j); }
+          for (int i = ci0; i < ci1; ++i) { visit(i, cj0 - 1); visit(i, cj1); }
+        }
+      }
     }
-    mlswe_status s = upload_table(H, H->t_ghost[l], ghost);
+    mlswe_status s = upload_table(H, H->t_gcell[l], gcell);
     if (s == MLSWE_OK) s = upload_table(H, H->t_avg[l], avg);
     if (s == MLSWE_OK) s = upload_table(H, H->t_reflux[l], refl);
     if (s != MLSWE_OK) return s;
@@ -189,7 +225,7 @@ static mlswe_status set_patches_internal(Hier* H, int member, int level, const s
 
 // ---- one-shot (synchronous) level transfers used by the API and by regridding ----
 static mlswe_status run_items(Hier* H, int kc, const std::vector<InterpItem>& items, int kind, int r, int par_c,
-                              int par_f, double alpha, int mode) {
+                              int par_f, double alpha) {
   if (items.empty()) return MLSWE_OK;
   const size_t bytes = items.size() * sizeof(InterpItem) + 64;
   char* base = (char*)scratch_buffer(H, bytes);
@@ -203,7 +239,7 @@ static mlswe_status run_items(Hier* H, int kc, const std::vector<InterpItem>& it
   int tok;
   timer_begin(H, kc, &tok);
   if (kind == 0)
-    CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, d_items, d_count, grid_full(H), r, par_c, par_f, alpha, mode,
+    CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, d_items, d_count, grid_full(H), r, par_c, par_f, alpha,
                               H->st));
   else
     CUDA_TRY(H, launch_average_items(3 * H->cfg.M, H->d_desc, d_items, d_count, grid_full(H), r, par_c, par_f, H->st));
@@ -219,7 +255,7 @@ static mlswe_status interp_boxes(Hier* H, int member, int coarse_level, const st
   for (const Box& b : boxes)
     push_chunks(items, H->desc_index(member, coarse_level), H->desc_index(member, coarse_level + 1), b);
   return run_items(H, KC_INTERP, items, 0, H->cfg.ratio[coarse_level], H->parity[coarse_level],
-                   H->parity[coarse_level + 1], 1.0, 0);
+                   H->parity[coarse_level + 1], 1.0);
 }
 
 // ---- the subcycled coarse step (graph-capturable: no host syncs, tables on device) ----
@@ -234,9 +270,9 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
     CUDA_TRY(H, launch_set_active(H->L, H->n_members, level, substep, H->d_rt, H->d_active, H->st));
     timer_end(H, tok);
     timer_begin(H, KC_GHOST, &tok);
-    CUDA_TRY(H, launch_interp(H->cfg.M, H->dp, H->d_desc, H->t_ghost[level].d, H->t_ghost[level].d_count, grid_full(H),
-                              H->cfg.ratio[level - 1], H->parity[level - 1], H->parity[level], 0.0, 1, H->st,
-                              substep));
+    CUDA_TRY(H, launch_ghost_cells(H->cfg.M, H->dp, H->d_desc, H->t_gcell[level].d, H->t_gcell[level].d_count,
+                                   grid_flat(H), H->cfg.ratio[level - 1], H->parity[level - 1], H->parity[level], 0.0,
+                                   substep, H->st));
     timer_end(H, tok);
   }
   mlswe_status s = enqueue_level_step(H, level, 1);
@@ -252,7 +288,7 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
                                      grid_full(H), rt, H->parity[level], H->parity[level + 1], H->st));
     timer_end(H, tok);
     timer_begin(H, KC_REFLUX, &tok);
-    CUDA_TRY(H, launch_reflux(H->cfg.M, H->d_desc, H->t_reflux[level].d, H->t_reflux[level].d_count, grid_full(H), rt,
+    CUDA_TRY(H, launch_reflux(H->cfg.M, H->d_desc, H->t_reflux[level].d, H->t_reflux[level].d_count, grid_flat(H), rt,
                               H->parity[level], H->st));
     timer_end(H, tok);
   }
@@ -482,8 +518,9 @@ mlswe_status mlswe_fill_ghosts(mlswe_h h, int level, double alpha) {
   }
   int tok;
   timer_begin(h, KC_GHOST, &tok);
-  CUDA_TRY(h, launch_interp(h->cfg.M, h->dp, h->d_desc, h->t_ghost[level].d, h->t_ghost[level].d_count, grid_full(h),
-                            h->cfg.ratio[level - 1], h->parity[level - 1], h->parity[level], alpha, 1, h->st));
+  CUDA_TRY(h, launch_ghost_cells(h->cfg.M, h->dp, h->d_desc, h->t_gcell[level].d, h->t_gcell[level].d_count,
+                                 grid_flat(h), h->cfg.ratio[level - 1], h->parity[level - 1], h->parity[level], alpha,
+                                 -1, h->st));
   timer_end(h, tok);
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
@@ -505,7 +542,7 @@ mlswe_status mlswe_average_coarse(mlswe_h h, int fine_level, int member) {
     push_chunks(items, h->desc_index(member, fine_level - 1), h->desc_index(member, fine_level),
                 Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
   h->dt_ready = false;
-  return run_items(h, KC_AVERAGE, items, 1, r, h->parity[fine_level - 1], h->parity[fine_level], 1.0, 0);
+  return run_items(h, KC_AVERAGE, items, 1, r, h->parity[fine_level - 1], h->parity[fine_level], 1.0);
 }
 
 mlswe_status mlswe_get_flags(mlswe_h h, int member, int level, uint8_t* flags) {

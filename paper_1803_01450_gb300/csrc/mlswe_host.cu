@@ -423,9 +423,9 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
     H->shape[l * 2] = TileShape{125, 2, ctas};
     H->shape[l * 2 + 1] = TileShape{125, 2, ctas};
   }
-  H->t_ghost.resize(H->L);
   H->t_avg.resize(H->L);
   H->t_reflux.resize(H->L);
+  H->t_gcell.resize(H->L);
   H->mem.resize(n_members);
   const int F = 3 * cfg->M;
   for (int m = 0; m < n_members; ++m) {

@@ -23,6 +23,14 @@ struct InterpItem {
   int i0, j0, i1, j1;
 };
 
+// Work entry of the ghost fill: one coarse cell (ic, jc) of level l-1 under a ghost strip
+// (fine cells [i0, i1) x [j0, j1) of level l, in the domain) of a level-l patch.
+struct GhostCell {
+  int desc_c, desc_f;
+  int ic, jc;
+  int i0, j0, i1, j1;
+};
+
 struct Level {
   int NX = 0, NY = 0, P = 0;
   double dx = 0, dy = 0;
@@ -128,7 +136,8 @@ struct Hier {
   bool use_graphs = true;
   // Level-transfer tables per level (ghost strips of level l, coarsening of l onto l-1,
   // reflux scan of l, wave-speed boxes of all levels).
-  std::vector<DevTable<InterpItem>> t_ghost, t_avg, t_reflux;
+  std::vector<DevTable<InterpItem>> t_avg, t_reflux;  // reflux: single interface cells
+  std::vector<DevTable<GhostCell>> t_gcell;                     // ghost fill: coarse cells of the rings
   DevTable<InterpItem> t_speed;
   bool tables_dirty = true;
   bool dt_ready = false;           // device dt holds the next coarse step
