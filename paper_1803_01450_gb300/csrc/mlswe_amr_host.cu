@@ -188,17 +188,25 @@ static mlswe_status check_layout(Hier* H, int member, int level, const std::vect
   const Level& V = H->mem[member].lev[level];
   const Level& C = H->mem[member].lev[level - 1];
   const int r = H->cfg.ratio[level - 1];
+  // overlaps: sweep over the boxes in order of i0; only boxes starting before b ends in x
+  // can overlap it
+  std::vector<int> ord(boxes.size());
+  for (size_t a = 0; a < boxes.size(); ++a) ord[a] = (int)a;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return boxes[x].i0 < boxes[y].i0; });
+  for (size_t a = 0; a < ord.size(); ++a) {
+    const Box& b = boxes[ord[a]];
+    for (size_t c = a + 1; c < ord.size() && boxes[ord[c]].i0 < b.i1; ++c) {
+      const Box& o = boxes[ord[c]];
+      if (std::max(b.j0, o.j0) < std::min(b.j1, o.j1) && std::max(b.i0, o.i0) < std::min(b.i1, o.i1))
+        return fail(H, MLSWE_ENESTING, "patches overlap");
+    }
+  }
   for (size_t a = 0; a < boxes.size(); ++a) {
     const Box& b = boxes[a];
     if (b.i0 < 0 || b.j0 < 0 || b.i1 > V.NX || b.j1 > V.NY || b.i1 <= b.i0 || b.j1 <= b.j0)
       return fail(H, MLSWE_ENESTING, "patch outside the domain or empty");
     if (b.i0 % r || b.j0 % r || b.i1 % r || b.j1 % r)
       return fail(H, MLSWE_ENESTING, "patch not aligned to coarse cells");
-    for (size_t c = a + 1; c < boxes.size(); ++c) {
-      const Box& o = boxes[c];
-      if (std::max(b.i0, o.i0) < std::min(b.i1, o.i1) && std::max(b.j0, o.j0) < std::min(b.j1, o.j1))
-        return fail(H, MLSWE_ENESTING, "patches overlap");
-    }
     if (level - 1 > 0) {
       // proper nesting: the patch, grown by kNest coarse cells (not across the domain
       // boundary), lies inside the union of the coarse level's patches.

@@ -180,8 +180,11 @@ std::vector<Box> cluster_flags(const uint8_t* flags, int nx, int ny, int level, 
 // Rectangles of `a` not covered by any box of `sub` (disjoint, deterministic order).
 std::vector<Box> box_difference(const Box& a, const std::vector<Box>& sub) {
   std::vector<Box> cur{a};
+  std::vector<Box> nxt;
   for (const Box& s : sub) {
-    std::vector<Box> nxt;
+    // a box that misses `a` misses every fragment of it (most of them, on a regrid)
+    if (s.i1 <= a.i0 || s.i0 >= a.i1 || s.j1 <= a.j0 || s.j0 >= a.j1) continue;
+    nxt.clear();
     for (const Box& c : cur) {
       const int i0 = std::max(c.i0, s.i0), j0 = std::max(c.j0, s.j0), i1 = std::min(c.i1, s.i1), j1 = std::min(c.j1, s.j1);
       if (i0 >= i1 || j0 >= j1) { nxt.push_back(c); continue; }
