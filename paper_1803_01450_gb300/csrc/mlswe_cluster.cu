@@ -23,26 +23,35 @@
 namespace mlswe {
 
 void dilate_flags(const uint8_t* in, int nx, int ny, int n, std::vector<uint8_t>& out) {
-  // Separable max filter: rows, then columns.
+  // Separable max filter with sliding-window counts (a cell is set when its window of
+  // 2n + 1 holds a flag): along each row, then down the columns one row at a time, so both
+  // passes read memory in row order.
   std::vector<uint8_t> tmp((size_t)nx * ny, 0);
   out.assign((size_t)nx * ny, 0);
   for (int j = 0; j < ny; ++j) {
     const uint8_t* row = in + (size_t)j * nx;
-    int last = -1000000;  // last flagged index seen
-    std::vector<int> nextf(nx + 1, 1000000);
-    for (int i = nx - 1; i >= 0; --i) nextf[i] = row[i] ? i : nextf[i + 1];
+    uint8_t* t = &tmp[(size_t)j * nx];
+    int c = 0;
+    for (int i = 0; i <= std::min(n, nx - 1); ++i) c += row[i];
     for (int i = 0; i < nx; ++i) {
-      if (row[i]) last = i;
-      tmp[(size_t)j * nx + i] = (i - last <= n || nextf[i] - i <= n) ? 1 : 0;
+      t[i] = c > 0;
+      if (i + n + 1 < nx) c += row[i + n + 1];
+      if (i - n >= 0) c -= row[i - n];
     }
   }
-  for (int i = 0; i < nx; ++i) {
-    int last = -1000000;
-    std::vector<int> nextf(ny + 1, 1000000);
-    for (int j = ny - 1; j >= 0; --j) nextf[j] = tmp[(size_t)j * nx + i] ? j : nextf[j + 1];
-    for (int j = 0; j < ny; ++j) {
-      if (tmp[(size_t)j * nx + i]) last = j;
-      out[(size_t)j * nx + i] = (j - last <= n || nextf[j] - j <= n) ? 1 : 0;
+  std::vector<int> cnt(nx, 0);
+  for (int k = 0; k <= std::min(n, ny - 1); ++k)
+    for (int i = 0; i < nx; ++i) cnt[i] += tmp[(size_t)k * nx + i];
+  for (int j = 0; j < ny; ++j) {
+    uint8_t* o = &out[(size_t)j * nx];
+    for (int i = 0; i < nx; ++i) o[i] = cnt[i] > 0;
+    if (j + n + 1 < ny) {
+      const uint8_t* a = &tmp[(size_t)(j + n + 1) * nx];
+      for (int i = 0; i < nx; ++i) cnt[i] += a[i];
+    }
+    if (j - n >= 0) {
+      const uint8_t* b = &tmp[(size_t)(j - n) * nx];
+      for (int i = 0; i < nx; ++i) cnt[i] -= b[i];
     }
   }
 }
