@@ -321,6 +321,22 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
                            "interp_achieved_gbs": ib / (per["interp_fine"][0] * 1e-3) / 1e9
                            if per["interp_fine"][0] else None,
                            "patches_after": [len(H.get_patches(0, l)) for l in (1, 2)]}
+    # the whole AMR cycle: 8 coarse steps with a regrid before every 4th (as the workload's
+    # regrid interval), cell updates from the device counters, regrids inside the timed region
+    H.advance(1)
+    torch.cuda.synchronize()
+    s0 = H.get_stats()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        H.regrid(0)
+        H.advance(4)
+    torch.cuda.synchronize()
+    cyc_s = time.perf_counter() - t0
+    s1 = H.get_stats()
+    cyc_upd = sum(s1["cell_updates"]) - sum(s0["cell_updates"])
+    transfers["cycle_with_regrids"] = {"coarse_steps": 8, "regrids": 2, "wall_ms": cyc_s * 1e3,
+                                       "cell_updates": cyc_upd, "lcups": cyc_upd * M_LAYERS / cyc_s,
+                                       "patches": [len(H.get_patches(0, l)) for l in (1, 2)]}
     H.close()
     lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
     lp = upd * M_LAYERS * max(1, steps // 2) / (ms_p * 1e-3)
