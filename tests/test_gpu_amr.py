@@ -318,3 +318,36 @@ def test_empty_refined_level_changes_nothing(mlswe_lib):
     assert np.array_equal(H1.get_state(0, 0), H2.get_state(0, 0))
     H1.close()
     H2.close()
+
+
+def test_refinement_worked_examples_gpu(mlswe_lib):
+    """The hand-worked refinement examples of tests/golden on the GPU (interp_fine of one
+    coarse column, data constant in y)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "refinement_worked_examples.json")) as f:
+        examples = json.load(f)["examples"]
+    for ex in examples:
+        c = ex["coarse"]
+        cfg = mlswe_lib.Config(M=2, dry_tol=1e-6, max_levels=2, ratio=[2], regrid_interval=0, min_side=2, max_side=8)
+        H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 4.0, 4.0, 4, 4)])
+        cols = [0, 1, 2, 2]  # coarse columns k-1, k, k+1, and a copy of k+1
+        Bf = np.zeros((8, 8))
+        for ci, k in enumerate(cols):
+            Bf[:, 2 * ci:2 * ci + 2] = c["B"][k]
+        Bf[:, 2:4] = ex["fine_B"]
+        H.set_bathymetry(0, Bf)
+        q = np.zeros((6, 4, 4))
+        for ci, k in enumerate(cols):
+            q[0, :, ci], q[1, :, ci] = c["h1"][k], c["hu1"][k]
+            q[3, :, ci], q[4, :, ci] = c["h2"][k], c["hu2"][k]
+        H.set_state(0, 0, q)
+        H.set_patches(0, 1, np.array([[2, 0, 4, 8]]))
+        H.interp_fine(0, 0)
+        qf = H.get_state(0, 1)
+        H.close()
+        f = ex["fine"]
+        for name, field in (("h1", 0), ("hu1", 1), ("h2", 3), ("hu2", 4)):
+            got = qf[field, :, 2:4]
+            assert np.allclose(got, np.array(f[name])[None, :], rtol=1e-14, atol=1e-14), (ex["name"], name, got)
+        assert not qf[[2, 5]][:, :, 2:4].any()

@@ -349,3 +349,31 @@ def test_dynamic_time_ratio_conserves_mass_and_rest():
     R.interp_into(0, R.lev[0].q, R.lev[1].in_patch_mask())
     R.advance(6)
     assert np.abs(R.lev[0].q[[1, 2, 4, 5]]).max() <= 1e-13
+
+
+def _golden_refinement():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "refinement_worked_examples.json")) as f:
+        return json.load(f)
+
+
+def test_refinement_worked_examples():
+    """The hand-worked refinement examples of tests/golden (Sec. 2.1 Eqs. (4), (5), (10), the
+    bottom-up layer loop and the clipping at zero depth) reproduced by the oracle."""
+    P = O.params(M=2, dry_tol=1e-6)
+    for ex in _golden_refinement()["examples"]:
+        c = ex["coarse"]
+        q = np.zeros((6, 1, 3))
+        q[0, 0], q[1, 0] = c["h1"], c["hu1"]
+        q[3, 0], q[4, 0] = c["h2"], c["hu2"]
+        B = np.array([c["B"]], float)
+        qp, Bp = O.pad(q, B)
+        O.fill_walls(2, qp, Bp)
+        Bf = np.array([ex["fine_B"], ex["fine_B"]], float)
+        out = O.interp_fine(P, 2, qp, Bp, (1, 0, 2, 1), Bf)
+        f = ex["fine"]
+        for name, field in (("h1", 0), ("hu1", 1), ("h2", 3), ("hu2", 4)):
+            for row in range(2):
+                assert np.allclose(out[field, row], f[name], rtol=1e-14, atol=1e-14), (ex["name"], name, out[field])
+        assert not out[[2, 5]].any()
