@@ -185,6 +185,7 @@ struct EdgeW {
   // (sum_p Z_p = jump exactly for the f-wave split, up to rounding).
   double t0[M], t1[M];
   double hbt[M];  // depth whose gravity speed the transverse split of this edge takes
+  double muk[M];  // M >= 3, coupled edges: eigenvalues of the coupling matrix G (velocity-free)
   int wall;  // bit 2m: layer m reflects into the left cell (left is dry), bit 2m+1: right
 };
 
@@ -344,6 +345,82 @@ __device__ __forceinline__ void gauss_solve(double A[N][N], double b[N], double 
 // A(l) dh = 0 (Cramer); momenta l dh; strengths from the 6 x 6 system of the flux jumps.
 // Loss of hyperbolicity: some adjacent pair with (u_m - u_{m+1})^2 >= (1 - rho_m/rho_{m+1})
 // g (hbar_m + hbar_{m+1}); the guesses are used then (and for P.eigen = 1).
+// Eigenvalues lam (guess order: external -, ..., external +) and eigenvector depths dh (dh_1
+// = 1) of the coupled three-layer system with velocities u, mean depths hb and coupling G,
+// from mu_k (the eigenvalues of G): the guesses, the loss-of-hyperbolicity test (returned),
+// two Newton steps and Cramer's rule, as described above.
+template <int M>
+__device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M][M], const double* u,
+                                            const double* hb, const double* mu, double* lam, double dh[][M]) {
+  static_assert(M == 3, "general coupled branch written for three layers");
+  constexpr int N = 2 * M;
+  const double g = P.g;
+  double hs = 0.0, hus = 0.0;
+#pragma unroll
+  for (int m = 0; m < M; ++m) { hs += hb[m]; hus = fma(hb[m], u[m], hus); }
+  const double ubar = hus * rcp(hs);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const double sq = sqrt(mu[k]);
+    lam[k] = ubar - sq;
+    lam[N - 1 - k] = ubar + sq;
+  }
+  bool lst = false;
+#pragma unroll
+  for (int m = 0; m + 1 < M; ++m) {
+    const double du = u[m] - u[m + 1];
+    lst = lst || (du * du >= (1.0 - P.rho[m] * rcp(P.rho[m + 1])) * g * (hb[m] + hb[m + 1]));
+  }
+  auto build_A = [&](double l, double A[M][M]) {
+#pragma unroll
+    for (int m = 0; m < M; ++m)
+#pragma unroll
+      for (int n = 0; n < M; ++n) {
+        const double am = l - u[m];
+        A[m][n] = (m == n ? am * am : 0.0) - G[m][n];
+      }
+  };
+  if (!lst && P.eigen == 0) {
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      double Pl[N], dP[N], idP[N];
+#pragma unroll
+      for (int p = 0; p < N; ++p) {
+        double A[M][M];
+        build_A(lam[p], A);
+        const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+        const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+        const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+        Pl[p] = A[0][0] * c00 - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+        dP[p] = 2.0 * ((lam[p] - u[0]) * c00 + (lam[p] - u[1]) * c11 + (lam[p] - u[2]) * c22);
+      }
+      batched_reciprocal<N>(dP, idP);
+#pragma unroll
+      for (int p = 0; p < N; ++p) lam[p] -= Pl[p] * idP[p];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    double A[M][M];
+    build_A(lam[p], A);
+    const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    const double id2 = rcp(det2);
+    dh[p][0] = 1.0;
+    dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
+    dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
+  }
+  return lst;
+}
+
+template <int M>
+__device__ __forceinline__ void coupling_matrix(const DevParams& P, const double* hb, double G[M][M]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int n = 0; n < M; ++n) G[m][n] = P.g * hb[m] * (n >= m ? 1.0 : density_ratio<M>(P, n, m));
+}
+
 template <int M>
 __device__ __forceinline__ void coupled_general(const DevParams& P, const double* cL, const double* cR,
                                                 const double* hb, const double* d0, const double* d1,
@@ -361,78 +438,23 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const double
     vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
     wq[m] = sqrt(g * hb[m] * rcp(P.rho[m]));
   }
+  coupling_matrix<M>(P, hb, G);
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int n = 0; n < M; ++n) {
-      G[m][n] = g * hb[m] * (n >= m ? 1.0 : density_ratio<M>(P, n, m));
-      K[m][n] = wq[m] * wq[n] * fmin(P.rho[m], P.rho[n]);
-    }
+    for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * fmin(P.rho[m], P.rho[n]);
   jacobi_eigenvalues<M>(K, mu);
-  double hs = 0.0, hus = 0.0;
+  double lam[N], dh[N][M];
+  lost += general_eig<M>(P, G, uh, hb, mu, lam, dh) ? 1 : 0;
+  // the strengths
+  double Rm[N][N], rhs[N], beta[N];
 #pragma unroll
-  for (int m = 0; m < M; ++m) { hs += hb[m]; hus = fma(hb[m], uh[m], hus); }
-  const double ubar = hus * rcp(hs);
-  double lam[N];
-#pragma unroll
-  for (int k = 0; k < M; ++k) {
-    const double sq = sqrt(mu[k]);
-    lam[k] = ubar - sq;
-    lam[N - 1 - k] = ubar + sq;
-  }
-  bool lst = false;
-#pragma unroll
-  for (int m = 0; m + 1 < M; ++m) {
-    const double du = uh[m] - uh[m + 1];
-    lst = lst || (du * du >= (1.0 - P.rho[m] * rcp(P.rho[m + 1])) * g * (hb[m] + hb[m + 1]));
-  }
-  lost += lst ? 1 : 0;
-  auto build_A = [&](double l, double A[M][M]) {
-#pragma unroll
-    for (int m = 0; m < M; ++m)
-#pragma unroll
-      for (int n = 0; n < M; ++n) {
-        const double am = l - uh[m];
-        A[m][n] = (m == n ? am * am : 0.0) - G[m][n];
-      }
-  };
-  if (!lst && P.eigen == 0) {
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      double Pl[N], dP[N], idP[N];
-#pragma unroll
-      for (int p = 0; p < N; ++p) {
-        double A[M][M];
-        build_A(lam[p], A);
-        const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
-        const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
-        const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-        Pl[p] = A[0][0] * c00 - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-        dP[p] = 2.0 * ((lam[p] - uh[0]) * c00 + (lam[p] - uh[1]) * c11 + (lam[p] - uh[2]) * c22);
-      }
-      batched_reciprocal<N>(dP, idP);
-#pragma unroll
-      for (int p = 0; p < N; ++p) lam[p] -= Pl[p] * idP[p];
-    }
-  }
-  // eigenvectors (dh_1 = 1) and the strengths
-  double Rm[N][N], rhs[N], beta[N], dh[N][M];
-#pragma unroll
-  for (int p = 0; p < N; ++p) {
-    double A[M][M];
-    build_A(lam[p], A);
-    const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-    const double id2 = rcp(det2);
-    dh[p][0] = 1.0;
-    dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
-    dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
+  for (int p = 0; p < N; ++p)
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       Rm[2 * m][p] = dh[p][m];
       Rm[2 * m + 1][p] = lam[p] * dh[p][m];
     }
-  }
 #pragma unroll
   for (int m = 0; m < M; ++m) { rhs[2 * m] = d0[m]; rhs[2 * m + 1] = d1[m]; }
   gauss_solve<N>(Rm, rhs, beta);
@@ -450,6 +472,7 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const double
     W.t0[m] = d0[m];
     W.t1[m] = d1[m];
     W.hbt[m] = hb[m];
+    W.muk[m] = mu[m];
   }
 }
 
@@ -474,7 +497,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
   }
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; W.hbt[m] = 0.0;
+    W.z[m] = 0.0; W.us[m] = 0.0; W.vh[m] = 0.0; W.t0[m] = 0.0; W.t1[m] = 0.0; W.hbt[m] = 0.0; W.muk[m] = 0.0;
   }
   W.wall = 0;
 
@@ -818,6 +841,46 @@ __device__ __forceinline__ void trans_apply_layers(const DevParams& P, int act, 
     trans_send(s1, b1, un[m], up, dn, 3 * m);
     trans_send(s2, b2, un[m], up, dn, 3 * m);
     trans_shear(ut[m], dq[3 * m + 1] - un[m] * dh, up, dn, 3 * m + 1);
+  }
+}
+
+// Coupled edge of M >= 3 layers: the transverse eigenvalues are the roots of
+// det(diag((mu - ut_m)^2) - G) with the same G as the normal solve, so the guesses reuse its
+// eigenvalues mu_k of G around the transverse mean velocity; then general_eig's Newton steps
+// and eigenvectors, and the 2M x 2M elimination for the strengths of each fluctuation.
+template <int M>
+__device__ __forceinline__ void trans_apply_general(const DevParams& P, const double* hb, const double* un,
+                                                    const double* ut, const double* muk, const double* dqa,
+                                                    const double* dqb, double* upa, double* dna, double* upb,
+                                                    double* dnb) {
+  constexpr int N = 2 * M;
+  double G[M][M], lam[N], dh[N][M];
+  coupling_matrix<M>(P, hb, G);
+  general_eig<M>(P, G, ut, hb, muk, lam, dh);
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    const double* dq = v == 0 ? dqa : dqb;
+    double* up = v == 0 ? upa : upb;
+    double* dn = v == 0 ? dna : dnb;
+#pragma unroll
+    for (int f = 0; f < 3 * M; ++f) { up[f] = 0.0; dn[f] = 0.0; }
+    double Rm[N][N], rhs[N], beta[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        Rm[2 * m][p] = dh[p][m];
+        Rm[2 * m + 1][p] = lam[p] * dh[p][m];
+      }
+#pragma unroll
+    for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[3 * m]; rhs[2 * m + 1] = dq[3 * m + 2]; }
+    gauss_solve<N>(Rm, rhs, beta);
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int m = 0; m < M; ++m) trans_send(lam[p], beta[p] * dh[p][m], un[m], up, dn, 3 * m);
+#pragma unroll
+    for (int m = 0; m < M; ++m) trans_shear(ut[m], dq[3 * m + 1] - un[m] * dq[3 * m], up, dn, 3 * m + 1);
   }
 }
 

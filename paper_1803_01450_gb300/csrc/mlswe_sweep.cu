@@ -80,8 +80,10 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
   double* wav = cell + R::N * kMaxCells;                // [WR::N][kMaxEdges], reused for contributions
   int* wallb = reinterpret_cast<int*>(wav + WR::N * kMaxEdges);   // [kMaxEdges]
   unsigned char* wetb = reinterpret_cast<unsigned char*>(wallb + kMaxEdges);  // [kMaxCells]
-  // unsplit only: transverse depth of every edge [M][kMaxEdges], after the split layout
+  // unsplit only: transverse depth of every edge [M][kMaxEdges], after the split layout, and
+  // (M >= 3) the eigenvalues of the coupling matrix [M][kMaxEdges]
   double* hbw = reinterpret_cast<double*>(smem) + sweep_smem_doubles(M);
+  double* muw = hbw + M * kMaxEdges;
   __shared__ double red[kThreads / 32];
 
   const int n_items = *n_items_dev;
@@ -220,7 +222,10 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       wallb[es] = W.wall;
       if (UNSPLIT) {
 #pragma unroll
-        for (int m = 0; m < M; ++m) hbw[m * kMaxEdges + es] = W.hbt[m];
+        for (int m = 0; m < M; ++m) {
+          hbw[m * kMaxEdges + es] = W.hbt[m];
+          if (M >= 3) muw[m * kMaxEdges + es] = W.muk[m];
+        }
       }
       if (interior && e >= 1 && e <= len + 1) {
         // |s| as bit patterns: non-negative doubles order like unsigned integers (NaN above all)
@@ -387,6 +392,18 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         put(0, Lc);
         put(1, Rc);
         double up[F], dn[F];
+        if constexpr (M >= 3) {
+          if (wL == full && wR == full) {
+            double muk[M], up2[F], dn2[F];
+#pragma unroll
+            for (int m = 0; m < M; ++m) muk[m] = muw[m * kMaxEdges + es];
+            trans_apply_general<M>(P, hbt, un, vh, muk, Lc, Rc, up, dn, up2, dn2);
+            put(2, up);
+            put(3, dn);
+            put(4, up2);
+            put(5, dn2);
+          }
+        }
         if (M == 2 && wL == full && wR == full) {
           TransEig2 E;
           trans_eigen2(P, hbt, vh, E);
@@ -396,7 +413,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
           trans_apply2(E, un, vh, Rc, up, dn);
           put(4, up);
           put(5, dn);
-        } else {
+        } else if (M == 1 || wL != full || wR != full) {
           const int act = wL | wR;
           trans_apply_layers<M>(P, act, hbt, un, vh, Lc, up, dn);
           put(2, up);
@@ -491,7 +508,7 @@ static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, co
                                   const int* n_items_dev, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
                                   double* est, long long eplane) {
-  const size_t sm = sweep_smem_bytes(M) + (UNSPLIT ? (size_t)M * kMaxEdges * 8 : 0);
+  const size_t sm = sweep_smem_bytes(M) + (UNSPLIT ? (size_t)(M >= 3 ? 2 * M : M) * kMaxEdges * 8 : 0);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE, UNSPLIT>,
@@ -517,6 +534,9 @@ static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc*
                                                                  smax_bits, lost_count, st, est, eplane);
   }
   if constexpr (M >= 3) {  // three layers fill the register file and shared memory: one CTA per SM
+    if (P.unsplit)
+      return launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                                                    lost_count, st, nullptr, 0);
     return launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
                                                    lost_count, st, nullptr, 0);
   } else {

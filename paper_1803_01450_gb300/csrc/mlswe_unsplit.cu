@@ -9,8 +9,9 @@
 // cell left of the x edge + parts towards -x received by the cell right of it), Gy likewise
 // with dt / 2 dx; then the positivity fix. At coarse/fine interfaces and refined patch
 // boundaries the transverse part of the mass flux is added to the flux records the edge
-// passes started (one cell owns each edge). Memory-bound: every thread one cell, rows of a
-// tile along x so that neighbouring threads read neighbouring edges.
+// passes started (one cell owns each edge). Every thread one cell, rows of a tile along x so
+// that neighbouring threads read neighbouring edges; each transverse flux sum is formed for
+// both cells beside it, so the FP64 work rather than the reads sets the time.
 #include <cuda_runtime.h>
 #include "mlswe_device.cuh"
 
@@ -115,6 +116,8 @@ cudaError_t launch_unsplit_update(const DevParams& P, const LevelDesc* descs, co
     unsplit_update_kernel<1><<<grid, kThreads, 0, st>>>(P, descs, items, n_items_dev, parity, record);
   else if (P.M == 2)
     unsplit_update_kernel<2><<<grid, kThreads, 0, st>>>(P, descs, items, n_items_dev, parity, record);
+  else if (P.M == 3)
+    unsplit_update_kernel<3><<<grid, kThreads, 0, st>>>(P, descs, items, n_items_dev, parity, record);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

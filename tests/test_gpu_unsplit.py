@@ -3,7 +3,7 @@ the oracle's unsplit step: fixed walled grids (one and two layers, orders 1 and 
 that span several tiles with a ragged last one), a shore with dry cells, lake at rest, the
 reported Courant number, x/y exchange symmetry on the GPU itself, subcycled AMR runs with
 regrids (two and three levels), the dynamic time ratio (members passing substeps through the
-update kernel), and the options the unsplit step does not take. Tolerance: 1e-11 relative
+update kernel), three layers, and the options the unsplit step does not take. Tolerance: 1e-11 relative
 per field, as for the split step (reciprocals, closed-form strengths and fused
 multiply-adds against plainly rounded oracle arithmetic)."""
 import numpy as np
@@ -247,11 +247,67 @@ def test_amr_dynamic_time_ratio(mlswe_lib):
     H.close()
 
 
+RHO3 = (1000.0, 1020.0, 1030.0)
+
+
+def _run_three(pkg, q, B, dx, dy, dts, order=2, dry_tol=1e-6):
+    ny, nx = B.shape
+    cfg = pkg.Config(M=3, rho=RHO3, order=order, dry_tol=dry_tol, max_levels=1, unsplit=1)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, nx * dx, ny * dy, nx, ny)])
+    H.set_bathymetry(0, B)
+    H.set_state(0, 0, q)
+    P = O.params(M=3, rho=RHO3, dry_tol=dry_tol, order=order, unsplit=1)
+    qo = q.copy()
+    for dt in dts:
+        H.step_level(0, dt=dt)
+        qo, _, _ = O.step_walled(P, qo, B, dx, dy, dt)
+    qg = H.get_state(0, 0)
+    H.close()
+    return qg, qo, P
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("shape", [(17, 23), (40, 130)])
+def test_three_layer_random_wet_states(mlswe_lib, order, shape):
+    """Three layers: the coupled transverse split reuses the normal solve's eigenvalues of the
+    coupling matrix around the transverse mean velocity."""
+    ny, nx = shape
+    q, B = I.gaussian_random_state(51 + nx + ny, 3, nx, ny, depth=(0.5, 0.4, 0.6))
+    dx, dy = 1.0 / nx, 1.3 / ny
+    qg, qo, _ = _run_three(mlswe_lib, q, B, dx, dy, [0.25 * min(dx, dy) / 4.0] * 5, order=order)
+    err = rel_err(qg, qo)
+    assert err.max() < TOL, err
+
+
+def test_three_layer_shore_and_rest(mlswe_lib):
+    w = I.shore3(96, seed=3002)
+    dts = [0.5 * w["dx"] / 210.0] * 20
+    qg, qo, P = _run_three(mlswe_lib, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
+    rng = np.random.default_rng(2)
+    a, b = w["q"].copy(), w["q"] * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=w["q"].shape))
+    for dt in dts:
+        a, _, _ = O.step_walled(P, a, w["B"], w["dx"], w["dy"], dt)
+        b, _, _ = O.step_walled(P, b, w["B"], w["dx"], w["dy"], dt)
+    sens = rel_err(b, a)
+    err = rel_err(qg, qo)
+    assert np.all(err < np.maximum(TOL, 10.0 * sens)), (err, sens)
+    assert err[[0, 3, 6]].max() < TOL
+    n = 64
+    B = I.shore_bathymetry(n, n)
+    q = I.stacked_state(B, (np.zeros_like(B), -50.0 + 0.0 * B, -200.0 + 0.0 * B))
+    cfg = mlswe_lib.Config(M=3, rho=RHO3, max_levels=1, unsplit=1)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)])
+    H.set_bathymetry(0, B)
+    H.set_state(0, 0, q)
+    for _ in range(20):
+        H.step_level(0, dt=2.0)
+    qg = H.get_state(0, 0)
+    H.close()
+    assert np.abs(qg[[1, 2, 4, 5, 7, 8]]).max() <= 1e-13 * 4000
+
+
 def test_options_the_unsplit_step_does_not_take(mlswe_lib):
-    with pytest.raises(mlswe_lib.MLSWEError) as e:
-        mlswe_lib.Hierarchy(mlswe_lib.Config(M=3, rho=(1000.0, 1020.0, 1030.0), unsplit=1),
-                            [(0.0, 0.0, 1.0, 1.0, 16, 16)])
-    assert e.value.status == 1
+    """The adjoint differentiates the split step only."""
     cfg = mlswe_lib.Config(M=2, dry_tol=1e-6, max_levels=1, order=1, unsplit=1)
     H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, 40, 40)])
     q, B = I.gaussian_random_state(3, 2, 40, 40)
