@@ -53,6 +53,7 @@ FP64_FLOP_PER_CELL_UPDATE_3 = 4134.82
 # pass (x edges, y edges) and the transverse correction fluxes plus the update.
 FP64_FLOP_PER_CELL_UPDATE_UNSPLIT = 2456.89
 FP64_FLOP_UNSPLIT_EDGE_PASS = 1143.94
+FP64_FLOP_PER_CELL_UPDATE_UNSPLIT_3 = 6816.15  # three layers (inputs.scale3)
 # HBM copy bandwidth measured on this part (MEASURED_PEAKS.json, STREAM-style copy).
 HBM_PEAK_GBS = 6674.8
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
@@ -544,7 +545,27 @@ def bench_unsplit(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
     ach = FP64_FLOP_UNSPLIT_EDGE_PASS * n * n / (x_ms * 1e-3) / 1e12
     upd_bytes = 14 * 3 * M_LAYERS * 8 * n * n
     upd_gbs = upd_bytes / (kms["update"] * 1e-3) / 1e9
+    # three layers (the scale3 workload) with the unsplit step
+    w3 = I.scale3(n, seed=1000)
+    cfg3 = pkg.Config(M=3, rho=(1000.0, 1020.0, 1030.0), dry_tol=w3["dry_tol"], order=2, limiter=2, max_levels=1,
+                      unsplit=1)
+    H3 = pkg.Hierarchy(cfg3, [(0.0, 0.0, 1e5, 1e5, n, n)], stream=stream.cuda_stream)
+    H3.set_bathymetry(0, w3["B"])
+    H3.set_state(0, 0, w3["q"])
+    H3.set_dt(0, 0.9 * w3["dx"] / 205.0)
+    for _ in range(warmup):
+        H3.step_level(0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        H3.step_level(0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms3 = e0.elapsed_time(e1)
+    H3.close()
     return {"workload": f"{n}^2 shelf, 2 layers, 8 humps, order 2 MC, walls, unsplit step",
+            "three_layers_lcups": n * n * 3 * steps / (ms3 * 1e-3), "three_layers_ms_per_step": ms3 / steps,
+            "three_layers_step_tflops": FP64_FLOP_PER_CELL_UPDATE_UNSPLIT_3 * n * n / (ms3 / steps * 1e-3) / 1e12,
             "lcups": n * n * M_LAYERS * steps / (ms * 1e-3), "ms_per_step": ms / steps,
             "kernels_ms_per_launch": kms, "flop_per_cell_update": FP64_FLOP_PER_CELL_UPDATE_UNSPLIT,
             "x_pass_achieved_tflops": ach, "x_pass_frac_of_fp64_peak": ach / FP64_PEAK_TFLOPS,

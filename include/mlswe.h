@@ -89,7 +89,7 @@ typedef struct {
  *               from the wave speeds of the previous step (Sec. 2: a smaller r_t
  *               where the refined region is shallow, as GeoClaw does).
  *  unsplit      0: dimensional splitting (x sweep, then y sweep on its result);
- *               1 (M <= 2): the unsplit wave-propagation step of GeoClaw's solver
+ *               1: the unsplit wave-propagation step of GeoClaw's solver
  *               family (Sec. 1) in corner-transport form: every edge solved on Q^n, the
  *               fluctuation each cell receives (correction flux included) split by a
  *               transverse Riemann solve at the edge state, its parts correcting the

@@ -33,6 +33,11 @@ def main():
                                          windows=[(100, 100, 96), (976, 976, 96), (1852, 1852, 96)])
     print(f"unsplit, order=2 eigen=0: {fu['total']:.2f} FP64 operations per cell update "
           f"(x edges {fu['x']:.2f}, y edges {fu['y']:.2f}, transverse fluxes and update {fu['update']:.2f})")
+    P3u = O.params(M=3, dry_tol=1e-3, order=2, rho=(1000.0, 1020.0, 1030.0), unsplit=1)
+    f3u = O.flops_per_cell_update_unsplit(P3u, w3["q"], w3["B"], w3["dx"], w3["dy"], dt,
+                                          windows=[(100, 100, 96), (976, 976, 96), (1852, 1852, 96)])
+    print(f"unsplit, three layers (scale3 workload): {f3u['total']:.2f} FP64 operations per cell update "
+          f"(x edges {f3u['x']:.2f}, y edges {f3u['y']:.2f}, transverse fluxes and update {f3u['update']:.2f})")
 
 
 if __name__ == "__main__":

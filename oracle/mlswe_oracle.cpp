@@ -142,6 +142,7 @@ struct Waves {
   // gravity speed it takes, the normal and the transverse velocity; whether the layers were
   // solved together, and which layers had a wet side.
   T hbt[MAXM], unt[MAXM], utt[MAXM];
+  T muk[MAXM];  // coupled edges of M >= 3 layers: the eigenvalues of the coupling matrix G
   int coupled;
   int active[MAXM];
 };
@@ -333,20 +334,24 @@ void jacobi_eigenvalues(int n, T K[MAXM][MAXM], T mu[MAXM]) {
 // Eigenvalues lam[0 .. 2M-1] (ascending guesses order) and eigenvector depths dh[p][m]
 // (dh_1 = 1) of the coupled M-layer system with velocities uh and mean depths hbar, as
 // described above; returns 1 when hyperbolicity is lost (the guesses are kept).
+// mu: the eigenvalues of G (they depend on hbar and the densities only); mu_known = false
+// computes them here (and returns them in mu), true takes them as given.
 template <class T>
 int general_eigen(const Params& P, const T uh[MAXM], const T hbar[MAXM], T lam[2 * MAXM],
-                  T dh[2 * MAXM][MAXM]) {
+                  T dh[2 * MAXM][MAXM], T mu[MAXM], bool mu_known) {
   const int M = P.M, N = 2 * M;
   const double g = P.g;
   T G[MAXM][MAXM];
   for (int m = 0; m < M; ++m)
     for (int n = 0; n < M; ++n) G[m][n] = g * hbar[m] * (n >= m ? 1.0 : density_ratio(P, n, m));
   // guesses
-  T K[MAXM][MAXM], mu[MAXM], wq[MAXM];
-  for (int m = 0; m < M; ++m) wq[m] = sqrt(g * hbar[m] / P.rho[m]);
-  for (int m = 0; m < M; ++m)
-    for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * std::min(P.rho[m], P.rho[n]);
-  jacobi_eigenvalues(M, K, mu);
+  if (!mu_known) {
+    T K[MAXM][MAXM], wq[MAXM];
+    for (int m = 0; m < M; ++m) wq[m] = sqrt(g * hbar[m] / P.rho[m]);
+    for (int m = 0; m < M; ++m)
+      for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * std::min(P.rho[m], P.rho[n]);
+    jacobi_eigenvalues(M, K, mu);
+  }
   T hsum = T(0.0), husum = T(0.0);
   for (int m = 0; m < M; ++m) { hsum = hsum + hbar[m]; husum = husum + hbar[m] * uh[m]; }
   const T ubar = husum / hsum;
@@ -404,7 +409,7 @@ void coupled_waves_general(const Params& P, T h[2][MAXM], T hn[2][MAXM], T un[2]
     vh[m] = (sl * ut[0][m] + sr * ut[1][m]) / (sl + sr);
   }
   T lam[2 * MAXM], dh[2 * MAXM][MAXM];
-  W.hyperbolicity_lost = general_eigen(P, uh, hbar, lam, dh);
+  W.hyperbolicity_lost = general_eigen(P, uh, hbar, lam, dh, W.muk, false);
   // the strengths
   T R[2 * MAXM][2 * MAXM], rhs[2 * MAXM], beta[2 * MAXM];
   for (int p = 0; p < N; ++p)
@@ -443,7 +448,7 @@ void riemann(const Params& P, const T* qL, const T* qR, const T& BL, const T& BR
   }
   for (int m = 0; m < MAXM; ++m) {
     W.wall_into[m] = -1;
-    W.hbt[m] = T(0.0); W.unt[m] = T(0.0); W.utt[m] = T(0.0);
+    W.hbt[m] = T(0.0); W.unt[m] = T(0.0); W.utt[m] = T(0.0); W.muk[m] = T(0.0);
     W.active[m] = 0;
   }
   W.coupled = 0;
@@ -681,7 +686,10 @@ void transverse(const Params& P, const Waves<T>& W, int nv, const T* const* dq, 
         dh[p][1] = ((mu[p] - W.utt[0]) * (mu[p] - W.utt[0]) - c1) / c1;
       }
     } else {
-      general_eigen(P, W.utt, W.hbt, mu, dh);
+      // G and so its eigenvalues are the normal solve's: only the velocities differ
+      T muk[MAXM];
+      for (int m = 0; m < M; ++m) muk[m] = W.muk[m];
+      general_eigen(P, W.utt, W.hbt, mu, dh, muk, true);
     }
     for (int v = 0; v < nv; ++v) {
       // strengths from the (h, ht) rows: sum_p beta_p (dh_m, mu_p dh_m) = (dq_h, dq_ht)_m
