@@ -292,41 +292,50 @@ __device__ __forceinline__ void jacobi_eigenvalues(double K[M][M], double mu[M])
     }
 }
 
-// Solve A x = b (N x N) by Gaussian elimination with partial pivoting; every index is a
-// compile-time constant (row exchanges are selects), so A stays in registers.
-template <int N>
-__device__ __forceinline__ void gauss_solve(double A[N][N], double b[N], double x[N]) {
+// One elimination step (pivot column K, a compile-time index, so every access below is to a
+// fixed register): partial pivoting (ties: lowest row), the row exchange as selects, then
+// the elimination of column K below the pivot; recurses to K + 1.
+template <int N, int K>
+__device__ __forceinline__ void gauss_step(double (&A)[N][N], double (&b)[N]) {
+  if constexpr (K < N) {
+    int piv = K;
+    unsigned long long best = abs_bits(A[K][K]);
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    int piv = k;
-    unsigned long long best = abs_bits(A[k][k]);
-#pragma unroll
-    for (int i = k + 1; i < N; ++i) {
-      const unsigned long long v = abs_bits(A[i][k]);
+    for (int i = K + 1; i < N; ++i) {
+      const unsigned long long v = abs_bits(A[i][K]);
       if (v > best) { best = v; piv = i; }
     }
 #pragma unroll
-    for (int i = k + 1; i < N; ++i) {
+    for (int i = K + 1; i < N; ++i) {
       const bool sw = i == piv;
 #pragma unroll
-      for (int j = k; j < N; ++j) {
-        const double t = A[k][j];
-        A[k][j] = sw ? A[i][j] : t;
+      for (int j = K; j < N; ++j) {
+        const double t = A[K][j];
+        A[K][j] = sw ? A[i][j] : t;
         A[i][j] = sw ? t : A[i][j];
       }
-      const double tb = b[k];
-      b[k] = sw ? b[i] : tb;
+      const double tb = b[K];
+      b[K] = sw ? b[i] : tb;
       b[i] = sw ? tb : b[i];
     }
-    const double ip = rcp(A[k][k]);
+    const double ip = rcp(A[K][K]);
 #pragma unroll
-    for (int i = k + 1; i < N; ++i) {
-      const double f = A[i][k] * ip;
+    for (int i = K + 1; i < N; ++i) {
+      const double f = A[i][K] * ip;
 #pragma unroll
-      for (int j = k + 1; j < N; ++j) A[i][j] = fma(-f, A[k][j], A[i][j]);
-      b[i] = fma(-f, b[k], b[i]);
+      for (int j = K + 1; j < N; ++j) A[i][j] = fma(-f, A[K][j], A[i][j]);
+      b[i] = fma(-f, b[K], b[i]);
     }
+    gauss_step<N, K + 1>(A, b);
   }
+}
+
+// Solve A x = b (N x N) by Gaussian elimination with partial pivoting. The steps are
+// instantiated per pivot column, so every index is a compile-time constant and A stays in
+// registers (a loop over the pivot column left A in local memory for N = 6).
+template <int N>
+__device__ __forceinline__ void gauss_solve(double (&A)[N][N], double (&b)[N], double (&x)[N]) {
+  gauss_step<N, 0>(A, b);
 #pragma unroll
   for (int k = N - 1; k >= 0; --k) {
     double sum = b[k];
