@@ -551,7 +551,6 @@ __global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const u
                                 int* init_flag, double* dt) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const bool initial = *init_flag != 0;
-  __syncthreads();
   if (m < A.n_members) {
     double best = INFINITY, fac = 1.0;
     double rate[4] = {0.0, 0.0, 0.0, 0.0};
@@ -624,9 +623,8 @@ __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, c
 
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
                             int* init_flag, double* dt, cudaStream_t st) {
-  // a single CTA reads the flag, then its thread 0 clears it after everyone has read it
-  if (A.n_members > 1024) return cudaErrorInvalidValue;
-  dt_begin_kernel<<<1, ((A.n_members + 31) / 32) * 32, 0, st>>>(A, smax_bits, init_bits, init_flag, dt);
+  // one thread per member; the flag is cleared after the kernel, in stream order
+  dt_begin_kernel<<<(A.n_members + 255) / 256, 256, 0, st>>>(A, smax_bits, init_bits, init_flag, dt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return cudaMemsetAsync(init_flag, 0, sizeof(int), st);

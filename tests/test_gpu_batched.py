@@ -116,3 +116,33 @@ def test_autotune_keeps_state_and_results(mlswe_lib):
         assert np.array_equal(H1.get_state(k, 1), H2.get_state(k, 1))
     H1.close()
     H2.close()
+
+
+def test_more_members_than_one_cta(mlswe_lib):
+    """1100 one-level members (the time-step kernel spans several CTAs): every member keeps
+    its own time step; a sample of members matches its own oracle run."""
+    n, nm = 8, 1100
+    depths = 1.0 + 0.001 * np.arange(nm)
+    cfg = mlswe_lib.Config(M=1, dry_tol=1e-6, max_levels=1, regrid_interval=0)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, n, n)] * nm)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    states = []
+    for k in range(nm):
+        B = -depths[k] * np.ones((n, n))
+        q = np.zeros((3, n, n))
+        q[0] = depths[k] + 0.01 * np.exp(-((X - 0.5) ** 2 + (Y - 0.4) ** 2) / 0.02)
+        H.set_bathymetry(k, B)
+        H.set_state(k, 0, q)
+        states.append((B, q))
+    H.advance(2)
+    t, _ = H.get_time()
+    assert len(set(np.round(t, 15))) == nm  # deeper members take shorter steps
+    for k in (0, 517, 1024, 1099):
+        B, q = states[k]
+        A = OracleAMR(O.params(M=1, dry_tol=1e-6), (0, 0, 1, 1), n, n, 1, [], B)
+        A.set_state(0, q)
+        A.advance(2)
+        assert abs(t[k] - A.t) <= 1e-12 * A.t
+        assert rel_err(H.get_state(k, 0), A.lev[0].q).max() < 1e-11
+    H.close()
