@@ -636,11 +636,14 @@ def run_gpu(args):
     # ---- end to end through the public API with pinned host buffers ----
     # Every step copies its input state from pinned host memory and reads its gauges back.
     # Pipelined: the input of step k + 1 is enqueued (copy stream, double-buffered staging)
-    # before waiting for step k, so its host-to-device copy overlaps step k's compute.
+    # right after step k, so its host-to-device copy overlaps step k's compute, and the host
+    # waits for step k - 1's gauges (an event on the stream) while step k runs.
     qh = torch.empty(w["q"].shape, dtype=torch.float64, pin_memory=True).numpy()
     qh[...] = w["q"]
     xy = np.stack([np.linspace(1e4, 9e4, 32), np.linspace(2e4, 8e4, 32)], axis=1)
-    gout = torch.empty((32, M_LAYERS), dtype=torch.float64, pin_memory=True).numpy()
+    gout = [torch.empty((32, M_LAYERS), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    results = []
     e2e_steps = max(3, min(args.steps, 10))
     H.set_state(0, 0, qh)
     H.step_level(0)
@@ -649,11 +652,18 @@ def run_gpu(args):
     H.set_state_async(0, 0, qh)
     for k in range(e2e_steps):
         H.step_level(0)
-        H.read_gauges_async(0, xy, gout)
+        H.read_gauges_async(0, xy, gout[k % 2])
+        done[k % 2].record(stream)
         if k + 1 < e2e_steps:
             H.set_state_async(0, 0, qh)
-        H.synchronize()
+        if k >= 1:
+            done[(k - 1) % 2].synchronize()
+            results.append(gout[(k - 1) % 2].copy())
+    done[(e2e_steps - 1) % 2].synchronize()
+    results.append(gout[(e2e_steps - 1) % 2].copy())
+    H.synchronize()
     e2e_s = time.perf_counter() - t0
+    assert len(results) == e2e_steps and all(np.isfinite(g).all() for g in results)
     H.close()
 
     lcu_per_step = N_CELLS * N_CELLS * M_LAYERS

@@ -612,8 +612,11 @@ mlswe_status mlswe_set_state_async(mlswe_h h, int member, int level, const doubl
   CUDA_TRY(h, cudaEventRecord(h->ev_copied[s], h->copy_st));
   CUDA_TRY(h, cudaStreamWaitEvent(h->st, h->ev_copied[s], 0));
   double* dst = V.q[h->parity[level]];
-  CUDA_TRY(h, cudaMemcpy2DAsync(dst, V.P * 8, h->stage[s], V.NX * 8, V.NX * 8, (size_t)V.NY * F,
-                                cudaMemcpyDeviceToDevice, h->st));
+  if (V.P == V.NX)  // unpadded rows: one contiguous copy
+    CUDA_TRY(h, cudaMemcpyAsync(dst, h->stage[s], bytes, cudaMemcpyDeviceToDevice, h->st));
+  else
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, V.P * 8, h->stage[s], V.NX * 8, V.NX * 8, (size_t)V.NY * F,
+                                  cudaMemcpyDeviceToDevice, h->st));
   CUDA_TRY(h, cudaEventRecord(h->ev_used[s], h->st));
   h->dt_ready = false;
   return MLSWE_OK;
