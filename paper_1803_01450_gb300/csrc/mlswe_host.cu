@@ -574,9 +574,11 @@ mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q) 
   Level& V = h->mem[member].lev[level];
   const int F = 3 * h->cfg.M;
   double* dst = V.q[h->parity[level]];
-  for (int f = 0; f < F; ++f)
-    CUDA_TRY(h, cudaMemcpy2DAsync(dst + (size_t)f * V.NY * V.P, V.P * 8, q + (size_t)f * V.NY * V.NX, V.NX * 8,
-                                  V.NX * 8, V.NY, cudaMemcpyHostToDevice, h->st));
+  if (V.P == V.NX)  // unpadded rows: one contiguous copy
+    CUDA_TRY(h, cudaMemcpyAsync(dst, q, (size_t)F * V.NY * V.NX * 8, cudaMemcpyHostToDevice, h->st));
+  else
+    CUDA_TRY(h, cudaMemcpy2DAsync(dst, V.P * 8, q, V.NX * 8, V.NX * 8, (size_t)V.NY * F, cudaMemcpyHostToDevice,
+                                  h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->dt_ready = false;  // the next automatic step starts from this state's wave speeds
   return MLSWE_OK;
@@ -634,9 +636,11 @@ mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out) {
   Level& V = h->mem[member].lev[level];
   const int F = 3 * h->cfg.M;
   const double* src = V.q[h->parity[level]];
-  for (int f = 0; f < F; ++f)
-    CUDA_TRY(h, cudaMemcpy2DAsync(q_out + (size_t)f * V.NY * V.NX, V.NX * 8, src + (size_t)f * V.NY * V.P, V.P * 8,
-                                  V.NX * 8, V.NY, cudaMemcpyDeviceToHost, h->st));
+  if (V.P == V.NX)
+    CUDA_TRY(h, cudaMemcpyAsync(q_out, src, (size_t)F * V.NY * V.NX * 8, cudaMemcpyDeviceToHost, h->st));
+  else
+    CUDA_TRY(h, cudaMemcpy2DAsync(q_out, V.NX * 8, src, V.P * 8, V.NX * 8, (size_t)V.NY * F, cudaMemcpyDeviceToHost,
+                                  h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return MLSWE_OK;
 }
