@@ -458,8 +458,9 @@ static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
     const int ctas = H->shape[dir].ctas;
     int tok;
     timer_begin(H, KC_ADJOINT, &tok);
-    ACUDA(H, launch_sweep(dir, H->dp, A->descs + a, W.d_items, W.d_count, ctas * H->num_sms, 0, 0, H->d_smax,
-                          nullptr, H->st, ctas, adj_edge_records(A, a, dir), A->eplane));
+    ACUDA(H, launch_sweep(dir, H->dp, A->descs + a, W.d_items, W.d_count, W.packed ? W.d_tile_off : nullptr,
+                          ctas * H->num_sms, 0, 0, H->d_smax, nullptr, H->st, ctas, adj_edge_records(A, a, dir),
+                          A->eplane));
     timer_end(H, tok);
   }
   return MLSWE_OK;

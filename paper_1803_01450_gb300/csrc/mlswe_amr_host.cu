@@ -463,12 +463,13 @@ static mlswe_status autotune_level(Hier* H, int level, int iters, int* chosen) {
         if (W.count == 0) continue;
         const int par = H->parity[level];
         const int full = ctas * H->num_sms;
-        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr,
-                                 H->st, ctas));
+        const int* toff = W.packed ? W.d_tile_off : nullptr;
+        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, toff, full, par, 0, H->d_smax,
+                                 nullptr, H->st, ctas));
         CUDA_TRY(H, cudaEventRecord(e0, H->st));
         for (int k = 0; k < iters; ++k)
-          CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, 0, H->d_smax, nullptr,
-                                   H->st, ctas));
+          CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, toff, full, par, 0, H->d_smax,
+                                   nullptr, H->st, ctas));
         CUDA_TRY(H, cudaEventRecord(e1, H->st));
         CUDA_TRY(H, cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -660,6 +661,8 @@ mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out) {
 mlswe_status mlswe_set_execution(mlswe_h h, int use_graphs, int per_patch_launches) {
   if (!h) return MLSWE_EINVAL;
   h->use_graphs = use_graphs != 0;
+  if (h->per_patch_launch != (per_patch_launches != 0))
+    for (auto& W : h->wl) W.dirty = true;  // packed tiles (batched) or tiles per patch
   h->per_patch_launch = per_patch_launches != 0;
   invalidate_graphs(h);
   return MLSWE_OK;

@@ -29,6 +29,7 @@ constexpr int kNG = 2;          // ghost cells per side
 constexpr int kMaxEdges = 256;  // edges per tile (one thread each)
 constexpr int kMaxCells = 288;  // cells per tile (edges + lines, lines <= 32)
 constexpr int kThreads = 256;
+constexpr int kMaxGroups = 4;   // groups of lines (runs of patch lines) packed into one sweep tile
 
 struct DevParams {
   int M;

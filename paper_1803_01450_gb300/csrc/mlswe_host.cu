@@ -239,11 +239,92 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
   patch_off.push_back((int)out.size());
 }
 
+// Runs of patch lines for the packed (batched) form: for every patch and every part of its
+// lines (the tile length of tile_dims), one item holding all consecutive lines with the same
+// flags; pack_tiles then cuts and packs them into tiles.
+static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& out) {
+  out.clear();
+  const TileShape ts = H->shape[level * 2 + dir];
+  for (int m = 0; m < H->n_members; ++m) {
+    const Level& V = H->mem[m].lev[level];
+    const int desc = H->desc_index(m, level);
+    for (const Box& b : V.patches) {
+      const int a0 = dir == 0 ? b.i0 : b.j0, a1 = dir == 0 ? b.i1 : b.j1;  // along the lines
+      const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;  // across
+      int tl, tn;
+      tile_dims(ts, a1 - a0, &tl, &tn);
+      // runs of lines: ghost lines before the patch, its own lines, ghost lines after
+      int g0 = 0, g1 = 0;
+      if (H->cfg.unsplit) { g0 = lo - 1; g1 = hi + 1; }
+      else if (dir == 0 && level > 0) { g0 = std::max(0, lo - kNG); g1 = std::min(V.NY, hi + kNG); }
+      else { g0 = lo; g1 = hi; }
+      const int rs[3][3] = {{g0, lo, 0}, {lo, hi, 1}, {hi, g1, 0}};
+      for (const auto& run : rs) {
+        if (run[1] <= run[0]) continue;
+        for (int a = a0; a < a1; a += tl) {
+          SweepItem it;
+          it.desc = desc;
+          it.len = std::min(tl, a1 - a);
+          if (dir == 0) { it.i0 = a; it.j0 = run[0]; } else { it.i0 = run[0]; it.j0 = a; }
+          it.nlines = run[1] - run[0];
+          it.flags = run[2] | (a + it.len == a1 ? 2 : 0);
+          out.push_back(it);
+        }
+      }
+    }
+  }
+}
+
+// Greedy packing of the runs, in order, into tiles of at most kMaxEdges edges, kMaxCells
+// cells and kMaxGroups groups of lines (at most 32 lines each) of one (member, level): a run
+// that does not fit is cut, its remaining lines start the next tile.
+static void pack_tiles(const std::vector<SweepItem>& segs, int dir, std::vector<SweepItem>& items,
+                       std::vector<int>& toff) {
+  items.clear();
+  toff.assign(1, 0);
+  int used_e = 0, used_c = 0, ng = 0, desc = -1;
+  auto close = [&]() {
+    if (ng > 0) toff.push_back((int)items.size());
+    used_e = used_c = ng = 0;
+    desc = -1;
+  };
+  for (const SweepItem& sgm : segs) {
+    int left = sgm.nlines, first = 0;
+    while (left > 0) {
+      const int room = std::min((kMaxEdges - used_e) / (sgm.len + 3), (kMaxCells - used_c) / (sgm.len + 4));
+      const int take = std::min(std::min(left, room), 32);
+      if (take < 1 || ng == kMaxGroups || (ng > 0 && sgm.desc != desc)) {
+        close();
+        continue;
+      }
+      SweepItem g = sgm;
+      if (dir == 0) g.j0 = sgm.j0 + first; else g.i0 = sgm.i0 + first;
+      g.nlines = take;
+      items.push_back(g);
+      ++ng;
+      desc = sgm.desc;
+      used_e += take * (sgm.len + 3);
+      used_c += take * (sgm.len + 4);
+      left -= take;
+      first += take;
+    }
+  }
+  close();
+}
+
 mlswe_status ensure_worklist(Hier* H, int level, int dir) {
   Hier::WorkList& W = dir == 2 ? H->wu[level] : H->wl[level * 2 + dir];
   if (!W.dirty) return MLSWE_OK;
   std::vector<SweepItem> items;
   build_items(H, level, dir, items, W.patch_off);
+  // batched form: groups of lines packed into tiles (the per-patch form keeps a tile per item)
+  std::vector<int> toff;
+  W.packed = dir != 2 && !H->per_patch_launch;
+  if (W.packed) {
+    std::vector<SweepItem> segs;
+    build_segments(H, level, dir, segs);
+    pack_tiles(segs, dir, items, toff);
+  }
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   if ((int)items.size() > W.capacity) {
     if (W.d_items) dev_free(H, W.d_items);
@@ -264,12 +345,22 @@ mlswe_status ensure_worklist(Hier* H, int level, int dir) {
     W.d_count = (int*)dev_alloc(H, sizeof(int));
     if (!W.d_count) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
   }
+  if (W.packed && (int)toff.size() > W.tile_cap) {
+    if (W.d_tile_off) dev_free(H, W.d_tile_off);
+    W.tile_cap = std::max<int>(1024, (int)toff.size() * 3 / 2);
+    W.d_tile_off = (int*)dev_alloc(H, W.tile_cap * sizeof(int));
+    if (!W.d_tile_off) return fail(H, MLSWE_ENOMEM, "work list allocation failed");
+    invalidate_graphs(H);
+  }
   std::vector<int> pc(std::max(np, 1), 0);
   for (int p = 0; p < np; ++p) pc[p] = W.patch_off[p + 1] - W.patch_off[p];
   W.count = (int)items.size();
+  W.ntiles = W.packed ? (int)toff.size() - 1 : W.count;
   if (!items.empty())
     CUDA_TRY(H, cudaMemcpyAsync(W.d_items, items.data(), items.size() * sizeof(SweepItem), cudaMemcpyHostToDevice, H->st));
-  CUDA_TRY(H, cudaMemcpyAsync(W.d_count, &W.count, sizeof(int), cudaMemcpyHostToDevice, H->st));
+  if (W.packed)
+    CUDA_TRY(H, cudaMemcpyAsync(W.d_tile_off, toff.data(), toff.size() * sizeof(int), cudaMemcpyHostToDevice, H->st));
+  CUDA_TRY(H, cudaMemcpyAsync(W.d_count, &W.ntiles, sizeof(int), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaMemcpyAsync(W.d_patch_count, pc.data(), pc.size() * sizeof(int), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   W.dirty = false;
@@ -294,8 +385,8 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
       // when a later regrid fills the work list.
       int tok;
       timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
-      CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, full, par, record, H->d_smax,
-                               H->d_lost, H->st, ctas));
+      CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items, W.d_count, W.packed ? W.d_tile_off : nullptr,
+                               full, par, record, H->d_smax, H->d_lost, H->st, ctas));
       timer_end(H, tok);
     } else {
       const int np = (int)W.patch_off.size() - 1;
@@ -304,7 +395,7 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
         if (cnt == 0) continue;
         int tok;
         timer_begin(H, dir == 0 ? KC_SWEEP_X : KC_SWEEP_Y, &tok);
-        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p,
+        CUDA_TRY(H, launch_sweep(dir, H->dp, H->d_desc, W.d_items + W.patch_off[p], W.d_patch_count + p, nullptr,
                                  std::min(cnt, full), par, record, H->d_smax, H->d_lost, H->st, ctas));
         timer_end(H, tok);
       }

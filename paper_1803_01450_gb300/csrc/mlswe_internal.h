@@ -126,6 +126,12 @@ struct Hier {
     std::vector<int> patch_off;     // item offset of every (member, patch)
     int* d_patch_count = nullptr;   // item count of every (member, patch)
     int patch_cap = 0;
+    // Batched form (not per-patch launches): the items are groups of lines packed into tiles
+    // of at most kMaxEdges edges, tile t = items [tile_off[t], tile_off[t + 1]).
+    bool packed = false;
+    int* d_tile_off = nullptr;
+    int tile_cap = 0;
+    int ntiles = 0;
   };
   std::vector<WorkList> wl;  // [L * 2]
   std::vector<WorkList> wu;  // [L] cell tiles of the unsplit step's update
@@ -230,9 +236,9 @@ cudaError_t launch_average(int nf, int r, const double* fine, int fP, size_t fpl
 cudaError_t launch_gauges(int M, const LevelDesc* descs, const int* parity_of_desc, const int* cells, int n,
                           double* out, cudaStream_t st);
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                         const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm = 1, double* est = nullptr,
-                         long long eplane = 0);
+                         const int* n_items_dev, const int* tile_off, int grid, int parity, int record,
+                         unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st, int ctas_per_sm = 1,
+                         double* est = nullptr, long long eplane = 0);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
 void adjoint_release(Hier* H);

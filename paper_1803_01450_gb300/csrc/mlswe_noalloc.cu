@@ -133,7 +133,8 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MLSWE_ECUDA;
   for (int dir = 0; dir < 2; ++dir)
-    if (launch_sweep(dir, P, d_desc, d_items[dir], d_count + dir, sms, 0, 1, d_smax, nullptr, st) != cudaSuccess)
+    if (launch_sweep(dir, P, d_desc, d_items[dir], d_count + dir, nullptr, sms, 0, 1, d_smax, nullptr, st) !=
+        cudaSuccess)
       return MLSWE_ECUDA;
   if (cfl_out) {
     unsigned long long bits[2];

@@ -70,8 +70,8 @@ __device__ __forceinline__ void block_max_atomic(double v, unsigned long long* d
 template <int M, int DIR, int MINB, bool STORE, bool UNSPLIT>
 __global__ void __launch_bounds__(kThreads, MINB)
 sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
-             const int* __restrict__ n_items_dev, int parity, int record, unsigned long long* smax_bits,
-             unsigned int* lost_count, double* __restrict__ est, long long eplane) {
+             const int* __restrict__ n_tiles_dev, const int* __restrict__ tile_off, int parity, int record,
+             unsigned long long* smax_bits, unsigned int* lost_count, double* __restrict__ est, long long eplane) {
   using R = Rec<M>;
   using WR = WRec<M>;
   constexpr int F = 3 * M;
@@ -85,12 +85,39 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
   double* hbw = reinterpret_cast<double*>(smem) + sweep_smem_doubles(M);
   double* muw = hbw + M * kMaxEdges;
   __shared__ double red[kThreads / 32];
+  // The tile's groups (items tile_off[it] .. tile_off[it + 1], or item it alone), all of one
+  // (member, level), and their running counts of cells, edges, cell contributions and updates.
+  __shared__ SweepItem sg[kMaxGroups];
+  __shared__ int sb[4][kMaxGroups + 1];
+  __shared__ int sng, s_rec;
 
-  const int n_items = *n_items_dev;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const SweepItem item = items[it];
-    const LevelDesc& D = descs[item.desc];
-    const int len = item.len, nl = item.nlines;
+  const int n_tiles = *n_tiles_dev;
+  for (int it = blockIdx.x; it < n_tiles; it += gridDim.x) {
+    if (threadIdx.x == 0) {
+      const int g0 = tile_off ? tile_off[it] : it, g1 = tile_off ? tile_off[it + 1] : it + 1;
+      int c = 0, e = 0, gc = 0, u = 0, rc = 0;
+      for (int g = 0; g < g1 - g0; ++g) {
+        const SweepItem x = items[g0 + g];
+        sg[g] = x;
+        sb[0][g] = c; sb[1][g] = e; sb[2][g] = gc; sb[3][g] = u;
+        c += x.nlines * (x.len + 4); e += x.nlines * (x.len + 3); gc += x.nlines * (x.len + 1);
+        u += x.nlines * x.len;
+        rc |= x.flags & 1;
+      }
+      sng = g1 - g0;
+      sb[0][g1 - g0] = c; sb[1][g1 - g0] = e; sb[2][g1 - g0] = gc; sb[3][g1 - g0] = u;
+      s_rec = rc;
+    }
+    __syncthreads();
+    const int ngrp = sng;
+    // group of flat index t in the running counts k (0 cells, 1 edges, 2 contributions, 3 updates)
+    auto group_of = [&](int k, int t) {
+      int g = 0;
+#pragma unroll
+      for (int h = 1; h < kMaxGroups; ++h) g += (h < ngrp && t >= sb[k][h]) ? 1 : 0;
+      return g;
+    };
+    const LevelDesc& D = descs[sg[0].desc];
     const int NX = D.NX, NY = D.NY, Pt = D.P;
     const size_t plane = (size_t)NY * Pt;
     const double* __restrict__ qin = (DIR == 0 || UNSPLIT) ? D.q[parity] : D.qs;
@@ -100,31 +127,39 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       // the substep count of the launch): the y sweep copies the tile's cells from the step's
       // input to its output (the x sweep's scratch is skipped), nothing is recorded. (Unsplit:
       // the update kernel copies.)
-      if (DIR == 0 || UNSPLIT) continue;
+      if (DIR == 0 || UNSPLIT) {
+        __syncthreads();  // the group table is rewritten for the next tile
+        continue;
+      }
       const double* __restrict__ qsrc = D.q[parity];
-      const int ncp = nl * len;
+      const int ncp = sb[3][ngrp];
       for (int t = threadIdx.x; t < ncp; t += blockDim.x) {
+        const int g = group_of(3, t);
+        const SweepItem& item = sg[g];
+        const int len = item.len, nl = item.nlines, tt = t - sb[3][g];
         int l, k;
-        if (DIR == 0) { l = t / len; k = t - l * len; }
-        else { k = t / nl; l = t - k * nl; }
+        if (DIR == 0) { l = tt / len; k = tt - l * len; }
+        else { k = tt / nl; l = tt - k * nl; }
         const size_t o = DIR == 0 ? (size_t)(item.j0 + l) * Pt + (item.i0 + k) : (size_t)(item.j0 + k) * Pt + (item.i0 + l);
 #pragma unroll
         for (int f = 0; f < F; ++f) qout[f * plane + o] = qsrc[f * plane + o];
       }
+      __syncthreads();
       continue;
     }
     const double dt = *D.dt;
     const double nu = dt * (DIR == 0 ? D.inv_dx : D.inv_dy);
     const long long tol_bits = __double_as_longlong(P.dry_tol);
-    // interior lines of a recorded step count toward the CFL reduction and the reflux fluxes
-    const bool interior = (item.flags & 1) && record;
 
     // ---- phase 1: load cells (mirror at walls) and compute the per-cell record ----
-    const int ncell = nl * (len + 4);
+    const int ncell = sb[0][ngrp];
     for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+      const int g = group_of(0, t);
+      const SweepItem& item = sg[g];
+      const int len = item.len, nl = item.nlines, tt = t - sb[0][g];
       int l, k;
-      if (DIR == 0) { l = t / (len + 4); k = t - l * (len + 4); }
-      else { k = t / nl; l = t - k * nl; }
+      if (DIR == 0) { l = tt / (len + 4); k = tt - l * (len + 4); }
+      else { k = tt / nl; l = tt - k * nl; }
       int i, j;
       if (DIR == 0) { i = item.i0 - kNG + k; j = item.j0 + l; }
       else { i = item.i0 + l; j = item.j0 - kNG + k; }
@@ -145,7 +180,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         }
       }
       const size_t o = (size_t)j * Pt + i;
-      const int c = cslot<DIR>(l, k, len, nl);
+      const int c = sb[0][g] + cslot<DIR>(l, k, len, nl);
       double rec[R::N];
       const double Bv = D.B[o];
       rec[R::BB] = Bv;
@@ -182,14 +217,19 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     __syncthreads();
 
     // ---- phase 2: Riemann solve at every edge of the tile ----
-    const int nedge = nl * (len + 3);
+    const int nedge = sb[1][ngrp];
     double smax = 0.0;
     int lost = 0;
     for (int t = threadIdx.x; t < nedge; t += blockDim.x) {
+      const int g = group_of(1, t);
+      const SweepItem& item = sg[g];
+      const int len = item.len, nl = item.nlines, tt = t - sb[1][g];
+      // interior lines of a recorded step count toward the CFL reduction and the reflux fluxes
+      const bool interior = (item.flags & 1) && record;
       int l, e;
-      if (DIR == 0) { l = t / (len + 3); e = t - l * (len + 3); }
-      else { e = t / nl; l = t - e * nl; }
-      const int cl = cslot<DIR>(l, e, len, nl), cr = cslot<DIR>(l, e + 1, len, nl);
+      if (DIR == 0) { l = tt / (len + 3); e = tt - l * (len + 3); }
+      else { e = tt / nl; l = tt - e * nl; }
+      const int cl = sb[0][g] + cslot<DIR>(l, e, len, nl), cr = sb[0][g] + cslot<DIR>(l, e + 1, len, nl);
       double cL[R::N], cR[R::N];
 #pragma unroll
       for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
@@ -204,7 +244,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
                         : est + (size_t)(item.j0 - 1 + e) * NX + (item.i0 + l);
       }
       solve_edge<M, STORE>(P, cL, cR, wetb[cl], wetb[cr], W, lst, st, eplane);
-      const int es = eslot<DIR>(l, e, len, nl);
+      const int es = sb[1][g] + eslot<DIR>(l, e, len, nl);
 #pragma unroll
       for (int p = 0; p < 2 * M; ++p) {
 #pragma unroll
@@ -243,18 +283,21 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     __syncthreads();
 
     // ---- phase 3: fluctuations + limited correction -> left/right cell contributions ----
-    const int ng = nl * (len + 1);
+    const int ng = sb[2][ngrp];
     double Lc[F], Rc[F];
-    int gl = -1, ge = -1;
+    int gl = -1, ge = -1, gg = 0;
     if (threadIdx.x < ng) {
       const int t = threadIdx.x;
+      const int g = group_of(2, t);
+      const SweepItem& item = sg[g];
+      const int len = item.len, nl = item.nlines, tt = t - sb[2][g];
       int l, e1;
-      if (DIR == 0) { l = t / (len + 1); e1 = t - l * (len + 1); }
-      else { e1 = t / nl; l = t - e1 * nl; }
-      gl = l; ge = e1;
+      if (DIR == 0) { l = tt / (len + 1); e1 = tt - l * (len + 1); }
+      else { e1 = tt / nl; l = tt - e1 * nl; }
+      gl = l; ge = e1; gg = g;
       const int e = e1 + 1;
-      const int es = eslot<DIR>(l, e, len, nl);
-      const int esl = eslot<DIR>(l, e - 1, len, nl), esr = eslot<DIR>(l, e + 1, len, nl);
+      const int es = sb[1][g] + eslot<DIR>(l, e, len, nl);
+      const int esl = sb[1][g] + eslot<DIR>(l, e - 1, len, nl), esr = sb[1][g] + eslot<DIR>(l, e + 1, len, nl);
       const int wall = wallb[es];
       double vh[M];
 #pragma unroll
@@ -366,7 +409,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       }
       if constexpr (UNSPLIT) {
         // transverse split of what each cell receives, at this edge's state
-        const int wL = wetb[cslot<DIR>(l, e, len, nl)], wR = wetb[cslot<DIR>(l, e + 1, len, nl)];
+        const int wL = wetb[sb[0][g] + cslot<DIR>(l, e, len, nl)], wR = wetb[sb[0][g] + cslot<DIR>(l, e + 1, len, nl)];
         double hbt[M], un[M];
 #pragma unroll
         for (int m = 0; m < M; ++m) {
@@ -426,8 +469,11 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     }
     __syncthreads();  // every neighbour read of the waves is done: reuse the space
     if (gl >= 0) {
+      const SweepItem& item = sg[gg];
+      const int len = item.len, nl = item.nlines;
+      const bool interior = (item.flags & 1) && record;
       if (!UNSPLIT) {
-        const int g = gslot<DIR>(gl, ge, len, nl);
+        const int g = sb[2][gg] + gslot<DIR>(gl, ge, len, nl);
 #pragma unroll
         for (int f = 0; f < F; ++f) {
           wav[f * kMaxEdges + g] = Lc[f];
@@ -445,7 +491,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         if (a >= 1 && a <= NA - 1) {
           const size_t cA = DIR == 0 ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
           const size_t cB = DIR == 0 ? cA + 1 : cA + NX;
-          const int clft = cslot<DIR>(gl, ge + 1, len, nl);
+          const int clft = sb[0][gg] + cslot<DIR>(gl, ge + 1, len, nl);
           const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
           const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
           if (iface || bnd) {
@@ -464,13 +510,16 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
     __syncthreads();
 
     // ---- phase 4: update the cells of the tile (the unsplit step updates in its own kernel) ----
-    const int nupd = UNSPLIT ? 0 : nl * len;
+    const int nupd = UNSPLIT ? 0 : sb[3][ngrp];
     for (int t = threadIdx.x; t < nupd; t += blockDim.x) {
+      const int g = group_of(3, t);
+      const SweepItem& item = sg[g];
+      const int len = item.len, nl = item.nlines, tt = t - sb[3][g];
       int l, k;
-      if (DIR == 0) { l = t / len; k = t - l * len; }
-      else { k = t / nl; l = t - k * nl; }
-      const int c = cslot<DIR>(l, k + 2, len, nl);
-      const int gL = gslot<DIR>(l, k, len, nl), gR = gslot<DIR>(l, k + 1, len, nl);
+      if (DIR == 0) { l = tt / len; k = tt - l * len; }
+      else { k = tt / nl; l = tt - k * nl; }
+      const int c = sb[0][g] + cslot<DIR>(l, k + 2, len, nl);
+      const int gL = sb[2][g] + gslot<DIR>(l, k, len, nl), gR = sb[2][g] + gslot<DIR>(l, k + 1, len, nl);
       double qn[F];
 #pragma unroll
       for (int f = 0; f < F; ++f)
@@ -492,7 +541,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         qout[(3 * m + 2) * plane + o] = DIR == 0 ? qn[3 * m + 2] : qn[3 * m + 1];
       }
     }
-    if (interior) block_max_atomic(smax, &smax_bits[item.desc * 2 + DIR], red);
+    if (record && s_rec) block_max_atomic(smax, &smax_bits[sg[0].desc * 2 + DIR], red);
     if (lost_count) {
       for (int o = 16; o > 0; o >>= 1) lost += __shfl_xor_sync(0xffffffffu, lost, o);
       if ((threadIdx.x & 31) == 0 && lost) atomicAdd(lost_count, (unsigned)lost);
@@ -505,7 +554,7 @@ size_t sweep_smem_bytes(int M) { return sweep_smem_doubles(M) * 8; }
 
 template <int M, int DIR, int MINB, bool STORE, bool UNSPLIT>
 static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                                  const int* n_items_dev, int grid, int parity, int record,
+                                  const int* n_items_dev, const int* tile_off, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
                                   double* est, long long eplane) {
   const size_t sm = sweep_smem_bytes(M) + (UNSPLIT ? (size_t)(M >= 3 ? 2 * M : M) * kMaxEdges * 8 : 0);
@@ -516,60 +565,62 @@ static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, co
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  sweep_kernel<M, DIR, MINB, STORE, UNSPLIT><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, parity,
-                                                                         record, smax_bits, lost_count, est, eplane);
+  sweep_kernel<M, DIR, MINB, STORE, UNSPLIT><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, tile_off,
+                                                                         parity, record, smax_bits, lost_count, est,
+                                                                         eplane);
   return cudaGetLastError();
 }
 
 template <int M, int DIR>
 static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                                  const int* n_items_dev, int grid, int parity, int record,
+                                  const int* n_items_dev, const int* tile_off, int grid, int parity, int record,
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
                                   double* est, long long eplane) {
   if constexpr (M == 2) {
     if (est != nullptr)
-      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, true, false>(P, descs, items, n_items_dev, grid, parity, record,
+      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, true, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                  smax_bits, lost_count, st, est, eplane)
-                       : launch_sweep_t<M, DIR, 1, true, false>(P, descs, items, n_items_dev, grid, parity, record,
+                       : launch_sweep_t<M, DIR, 1, true, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                  smax_bits, lost_count, st, est, eplane);
   }
   if constexpr (M >= 3) {  // three layers fill the register file and shared memory: one CTA per SM
     if (P.unsplit)
-      return launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+      return launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                                     lost_count, st, nullptr, 0);
-    return launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+    return launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                                    lost_count, st, nullptr, 0);
   } else {
     if (P.unsplit)
-      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, true>(P, descs, items, n_items_dev, grid, parity, record,
+      return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, true>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                  smax_bits, lost_count, st, nullptr, 0)
-                       : launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, grid, parity, record,
+                       : launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                  smax_bits, lost_count, st, nullptr, 0);
-    return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, false>(P, descs, items, n_items_dev, grid, parity, record,
+    return ctas >= 2 ? launch_sweep_t<M, DIR, 2, false, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                 smax_bits, lost_count, st, nullptr, 0)
-                     : launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, grid, parity, record,
+                     : launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
                                                                 smax_bits, lost_count, st, nullptr, 0);
   }
 }
 
 cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, const SweepItem* items,
-                         const int* n_items_dev, int grid, int parity, int record, unsigned long long* smax_bits,
-                         unsigned int* lost_count, cudaStream_t st, int ctas_per_sm, double* est, long long eplane) {
+                         const int* n_items_dev, const int* tile_off, int grid, int parity, int record,
+                         unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st, int ctas_per_sm,
+                         double* est, long long eplane) {
   if (grid <= 0) return cudaSuccess;
   const int c = ctas_per_sm;
   if (P.M == 1)
-    return dir == 0 ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+    return dir == 0 ? launch_sweep_m<1, 0>(c, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0)
-                    : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                    : launch_sweep_m<1, 1>(c, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0);
   if (P.M == 3)
-    return dir == 0 ? launch_sweep_m<3, 0>(1, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+    return dir == 0 ? launch_sweep_m<3, 0>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0)
-                    : launch_sweep_m<3, 1>(1, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                    : launch_sweep_m<3, 1>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0);
-  return dir == 0 ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+  return dir == 0 ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                          lost_count, st, est, eplane)
-                  : launch_sweep_m<2, 1>(c, P, descs, items, n_items_dev, grid, parity, record, smax_bits,
+                  : launch_sweep_m<2, 1>(c, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                          lost_count, st, est, eplane);
 }
 
