@@ -59,7 +59,7 @@ HBM_PEAK_GBS = 6674.8
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/).
-SWEEP_X_DRAM_BYTES = 399.6e6
+SWEEP_X_DRAM_BYTES = 408.6e6
 
 
 class ClockSampler:
