@@ -240,8 +240,8 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
 }
 
 // Runs of patch lines for the packed (batched) form: for every patch and every part of its
-// lines (the tile length of tile_dims), one item holding all consecutive lines with the same
-// flags; pack_tiles then cuts and packs them into tiles.
+// lines (the tile length of tile_dims), one item holding all consecutive lines of one kind;
+// pack_tiles then cuts and packs them into tiles.
 static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& out) {
   out.clear();
   const TileShape ts = H->shape[level * 2 + dir];
@@ -249,67 +249,15 @@ static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& 
     const Level& V = H->mem[m].lev[level];
     const int desc = H->desc_index(m, level);
     for (const Box& b : V.patches) {
-      const int a0 = dir == 0 ? b.i0 : b.j0, a1 = dir == 0 ? b.i1 : b.j1;  // along the lines
-      const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;  // across
+      const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;
       int tl, tn;
-      tile_dims(ts, a1 - a0, &tl, &tn);
-      // runs of lines: ghost lines before the patch, its own lines, ghost lines after
-      int g0 = 0, g1 = 0;
+      tile_dims(ts, dir == 0 ? b.w() : b.h(), &tl, &tn);
+      int g0 = lo, g1 = hi;  // lines processed: the patch's, ghost lines on each side
       if (H->cfg.unsplit) { g0 = lo - 1; g1 = hi + 1; }
       else if (dir == 0 && level > 0) { g0 = std::max(0, lo - kNG); g1 = std::min(V.NY, hi + kNG); }
-      else { g0 = lo; g1 = hi; }
-      const int rs[3][3] = {{g0, lo, 0}, {lo, hi, 1}, {hi, g1, 0}};
-      for (const auto& run : rs) {
-        if (run[1] <= run[0]) continue;
-        for (int a = a0; a < a1; a += tl) {
-          SweepItem it;
-          it.desc = desc;
-          it.len = std::min(tl, a1 - a);
-          if (dir == 0) { it.i0 = a; it.j0 = run[0]; } else { it.i0 = run[0]; it.j0 = a; }
-          it.nlines = run[1] - run[0];
-          it.flags = run[2] | (a + it.len == a1 ? 2 : 0);
-          out.push_back(it);
-        }
-      }
+      patch_segments(b, dir, tl, g0, g1, desc, out);
     }
   }
-}
-
-// Greedy packing of the runs, in order, into tiles of at most kMaxEdges edges, kMaxCells
-// cells and kMaxGroups groups of lines (at most 32 lines each) of one (member, level): a run
-// that does not fit is cut, its remaining lines start the next tile.
-static void pack_tiles(const std::vector<SweepItem>& segs, int dir, std::vector<SweepItem>& items,
-                       std::vector<int>& toff) {
-  items.clear();
-  toff.assign(1, 0);
-  int used_e = 0, used_c = 0, ng = 0, desc = -1;
-  auto close = [&]() {
-    if (ng > 0) toff.push_back((int)items.size());
-    used_e = used_c = ng = 0;
-    desc = -1;
-  };
-  for (const SweepItem& sgm : segs) {
-    int left = sgm.nlines, first = 0;
-    while (left > 0) {
-      const int room = std::min((kMaxEdges - used_e) / (sgm.len + 3), (kMaxCells - used_c) / (sgm.len + 4));
-      const int take = std::min(std::min(left, room), 32);
-      if (take < 1 || ng == kMaxGroups || (ng > 0 && sgm.desc != desc)) {
-        close();
-        continue;
-      }
-      SweepItem g = sgm;
-      if (dir == 0) g.j0 = sgm.j0 + first; else g.i0 = sgm.i0 + first;
-      g.nlines = take;
-      items.push_back(g);
-      ++ng;
-      desc = sgm.desc;
-      used_e += take * (sgm.len + 3);
-      used_c += take * (sgm.len + 4);
-      left -= take;
-      first += take;
-    }
-  }
-  close();
 }
 
 mlswe_status ensure_worklist(Hier* H, int level, int dir) {
@@ -323,7 +271,7 @@ mlswe_status ensure_worklist(Hier* H, int level, int dir) {
   if (W.packed) {
     std::vector<SweepItem> segs;
     build_segments(H, level, dir, segs);
-    pack_tiles(segs, dir, items, toff);
+    if (!pack_tiles(segs, dir, items, toff)) return fail(H, MLSWE_EINVAL, "sweep tiles: line longer than a tile");
   }
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   if ((int)items.size() > W.capacity) {

@@ -241,6 +241,16 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
                          double* est = nullptr, long long eplane = 0);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
+
+// Packed sweep tiles (mlswe_pack.cu). patch_segments appends the runs of lines of patch b
+// for a sweep along dir (0: x, lines are rows; 1: y, lines are columns): lines [g0, g1)
+// across (the patch's own lines [lo, hi) flagged interior, the others ghost lines), parts of
+// at most tile_len cells along. pack_tiles packs runs in order into tiles of at most
+// kMaxEdges edges, kMaxCells cells and kMaxGroups groups (runs or their pieces) of one
+// desc, cutting a run where it does not fit: tile t is items [toff[t], toff[t + 1]); false
+// (nothing usable) when a run's line is longer than a tile holds.
+void patch_segments(const Box& b, int dir, int tile_len, int g0, int g1, int desc, std::vector<SweepItem>& out);
+bool pack_tiles(const std::vector<SweepItem>& segs, int dir, std::vector<SweepItem>& items, std::vector<int>& toff);
 void adjoint_release(Hier* H);
 mlswe_status ensure_worklist(Hier* H, int level, int dir);
 
