@@ -107,13 +107,31 @@ __device__ __forceinline__ double pos_min(double a, double b) {  // both > 0
   return __longlong_as_double(x < y ? x : y);
 }
 
-// Same values as limiter_phi: theta <= 0 gives 0; the minima of positive numbers are taken
-// on their bit patterns.
-__device__ __forceinline__ double limiter_phi_fast(int kind, double th) {
-  if (kind == 0) return 1.0;
-  if (__double_as_longlong(th) <= 0) return 0.0;  // th <= +0 or negative
-  if (kind == 1) return pos_min(1.0, th);
-  return pos_min(pos_min(fma(0.5, th, 0.5), 2.0), th + th);
+// Share of a wave of speed s that goes to the left cell, second-order correction included:
+//   c = (1 if s < 0, 0 if s > 0, 1/2 if s = 0) + sign(s) (1 - nu |s|) phi(theta) / 2
+// (the correction only where act). For the MC limiter phi / 2 = min((1 + theta) / 4, 1,
+// theta) exactly (scalings by powers of two), so its factor 2 goes into the weight
+// sign(s) (1 - nu |s|) and the correction costs one FMA for the weight, one for the
+// limiter and one to add it. theta = num * iden; limiters: 0 none (phi = 1), 1 minmod, 2 MC;
+// the minima of positive numbers are taken on their bit patterns.
+__device__ __forceinline__ double left_share(int kind, int sc, bool act, double num, double iden, double s,
+                                             double nu) {
+  const double base = sc < 0 ? 1.0 : (sc > 0 ? 0.0 : 0.5);
+  if (!act) return base;
+  const double th = num * iden;
+  if (kind == 2) {
+    if (__double_as_longlong(th) <= 0) return base;  // phi = 0
+    const double ph = pos_min(pos_min(fma(0.25, th, 0.25), 1.0), th);
+    const double w = sc > 0 ? fma(-nu, fabs(s), 1.0) : fma(nu, fabs(s), -1.0);
+    return fma(w, ph, base);
+  }
+  double ph = 1.0;
+  if (kind == 1) {
+    if (__double_as_longlong(th) <= 0) return base;
+    ph = pos_min(1.0, th);
+  }
+  const double w = sc > 0 ? fma(-0.5 * nu, fabs(s), 0.5) : fma(0.5 * nu, fabs(s), -0.5);
+  return fma(w, ph, base);
 }
 
 // |x| in [2^-160, 2^160), read from the exponent field (integer unit, not the FP64 pipe).

@@ -306,8 +306,6 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       // R = T - L, since the waves of a layer sum to its flux jump T (mass, normal momentum)
       // and the transverse row to vh T_mass + z.
       double Lm[M], Lsm[M];
-#pragma unroll
-      for (int m = 0; m < M; ++m) { Lm[m] = 0.0; Lsm[m] = 0.0; }
       // Wave limiter: theta_p = zu_p / zz_p for the acoustic waves and zu_m / z_m for the shear
       // waves ((z_up z)/(z z) with z != 0), with one reciprocal for all of them.
       constexpr int NA = 2 * M, NR = 2 * M + M;
@@ -368,17 +366,13 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
         const double s = wav[(WR::S + p) * kMaxEdges + es];
-        double corr = 0.0;
-        if (act[p]) {
-          const double phi = limiter_phi_fast(P.limiter, num[p] * iden[p]);
-          corr = (sc[p] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(s), 1.0) * phi;
-        }
-        const double cl = (sc[p] < 0 ? 1.0 : (sc[p] > 0 ? 0.0 : 0.5)) + corr;
+        const double cl = left_share(P.limiter, sc[p], act[p], num[p], iden[p], s, nu);
+        const double cs = cl * s;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const double cm = cl * wav[(WR::A + NA * m + p) * kMaxEdges + es];
-          Lm[m] += cm;
-          Lsm[m] += cm * s;
+          const double a = wav[(WR::A + NA * m + p) * kMaxEdges + es];
+          if (p == 0) { Lm[m] = cl * a; Lsm[m] = cs * a; }
+          else { Lm[m] = fma(cl, a, Lm[m]); Lsm[m] = fma(cs, a, Lsm[m]); }
         }
       }
       double Lz[M], Rz[M];
@@ -387,12 +381,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const int q = NA + m;
         const double z = wav[(WR::Z + m) * kMaxEdges + es];
         const double us = wav[(WR::US + m) * kMaxEdges + es];
-        double corr = 0.0;
-        if (act[q]) {
-          const double phi = limiter_phi_fast(P.limiter, num[q] * iden[q]);
-          corr = (sc[q] > 0 ? 0.5 : -0.5) * fma(-nu, fabs(us), 1.0) * phi;
-        }
-        const double cl = (sc[q] < 0 ? 1.0 : (sc[q] > 0 ? 0.0 : 0.5)) + corr;
+        const double cl = left_share(P.limiter, sc[q], act[q], num[q], iden[q], us, nu);
         Lz[m] = cl * z;
         Rz[m] = z - Lz[m];
       }
