@@ -36,6 +36,8 @@ struct DevParams {
   double g;
   double r;        // rho_1 / rho_2 (M = 2)
   double rho[4];   // layer densities, top (lightest) first
+  double rr[4][4];  // rho_n / rho_m at [n][m], computed on the host
+  double irho[4];   // 1 / rho_m
   double dry_tol;
   int order;
   int limiter;
@@ -140,6 +142,59 @@ __device__ __forceinline__ bool moderate(double x) {
   return e - 863u <= 320u;
 }
 
+// Reciprocal and reciprocal square root by iteration (Newton-Raphson family; see Muller et
+// al., Handbook of Floating-Point Arithmetic, ch. 5 on iterations for division and square
+// root), cheaper on the FP64 pipe than the correctly rounded functions. The seed is the FP32
+// reciprocal (square root) of the leading 20 significand bits, scaled by integer arithmetic
+// on the exponent field: relative error eta below 2^-19. One third-order (Householder) step
+// follows; its truncation error is O(eta^3) < 2^-56, so the result is within about one unit
+// in the last place of the exact value (not always the correctly rounded one).
+//
+// 1/x for a normal x with |x| < 2^1022: with e = 1 - x y, y' = y + y (e + e^2).
+__device__ __forceinline__ double rcp_iter(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int ex = (int)((hi >> 20) & 0x7ffu);                          // biased exponent of x
+  const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3));  // significand in [1, 2)
+  const unsigned r = __float_as_uint(__frcp_rn(m));                    // 1/m in (1/2, 1]
+  const int re = (int)(r >> 23) - 127;                                  // its exponent: 0 or -1
+  // 1/x = sign(x) (1/m) 2^(1023 - ex): biased exponent 2046 - ex + re
+  const unsigned long long yb = (b & 0x8000000000000000ull) | ((unsigned long long)(2046 - ex + re) << 52) |
+                                ((unsigned long long)(r & 0x7fffffu) << 29);
+  const double y = __longlong_as_double((long long)yb);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+// 1/sqrt(x) for x > 0 with exponent in [-1000, 1000]: x = s 2^(2k) with s in [1, 4) (the
+// significand, doubled when the exponent is odd); with e = 1 - x y^2,
+// y' = y + y e (1/2 + 3 e / 8).
+__device__ __forceinline__ double rsqrt_iter(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int E = (int)(hi >> 20) - 1023;  // unbiased exponent (x > 0: no sign bit)
+  const int odd = E & 1;
+  const float s = __uint_as_float((odd ? 0x40000000u : 0x3f800000u) | ((hi & 0xfffffu) << 3));
+  const unsigned r = __float_as_uint(rsqrtf(s));  // in (1/2, 1]
+  const int re = (int)(r >> 23) - 127;            // 0 or -1
+  const int k = (E - odd) / 2;                     // exact: E - odd is even
+  const unsigned long long yb = ((unsigned long long)(1023 + re - k) << 52) | ((unsigned long long)(r & 0x7fffffu) << 29);
+  const double y = __longlong_as_double((long long)yb);
+  const double xy = x * y;
+  const double e = fma(-xy, y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
+}
+
+// The iterations where |x| lies in [2^-160, 2^160) (x > 0 for the square root), the
+// library functions elsewhere (zero, subnormal, huge, infinite, NaN or negative arguments).
+__device__ __forceinline__ double rcp_fast(double x) { return moderate(x) ? rcp_iter(x) : rcp(x); }
+__device__ __forceinline__ double rsqrt_fast(double x) {
+  return __double_as_longlong(x) >= 0 && moderate(x) ? rsqrt_iter(x) : rsqrt(x);
+}
+__device__ __forceinline__ double sqrt_fast(double x) {
+  return __double_as_longlong(x) >= 0 && moderate(x) ? x * rsqrt_iter(x) : sqrt(x);
+}
+
 // Reciprocals of N <= 6 nonzero numbers with one division:
 // 1/x_p = (1/prod x) * prod_{q != p} x_q, used when every |x_p| lies in [2^-160, 2^160) (so
 // every partial product stays a normal FP64 number); otherwise one division each.
@@ -157,7 +212,7 @@ __device__ __forceinline__ void batched_reciprocal(const double* x, double* inv)
     suf[N - 1] = 1.0;
 #pragma unroll
     for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
-    const double ip = rcp(pre[N - 1] * x[N - 1]);
+    const double ip = rcp_iter(pre[N - 1] * x[N - 1]);  // |product| in [2^-960, 2^966)
 #pragma unroll
     for (int p = 0; p < N; ++p) inv[p] = ip * (pre[p] * suf[p]);
   } else {
@@ -237,7 +292,7 @@ __device__ __forceinline__ int layer_of_slot(int p) {
 template <int M>
 __device__ __forceinline__ double density_ratio(const DevParams& P, int n, int m) {
   if constexpr (M == 2) return P.r;
-  return P.rho[n] * rcp(P.rho[m]);
+  return P.rr[n][m];
 }
 
 // Single-layer f-wave split of (d0, d1, d2) with speeds s1 < s2 (inv_ds: 1/(s2 - s1) when
@@ -246,7 +301,7 @@ template <int M>
 __device__ __forceinline__ void split_single(int m, int pa, int pb, double d0, double d1, double d2,
                                              double s1, double s2, double vh, double us, EdgeW<M>& W,
                                              double inv_ds = 0.0) {
-  const double inv = inv_ds != 0.0 ? inv_ds : rcp(s2 - s1);
+  const double inv = inv_ds != 0.0 ? inv_ds : rcp_fast(s2 - s1);
   const double b1 = (s2 * d0 - d1) * inv;
   const double b2 = (d1 - s1 * d0) * inv;
   W.mass[m][pa] = b1;
@@ -282,9 +337,9 @@ __device__ __forceinline__ void jacobi_eigenvalues(double K[M][M], double mu[M])
       for (int q = p + 1; q < M; ++q) {
         const double kpq = K[p][q];
         if (kpq == 0.0) continue;
-        const double theta = (K[q][q] - K[p][p]) * (0.5 * rcp(kpq));
-        const double t = copysign(rcp(fabs(theta) + sqrt(fma(theta, theta, 1.0))), theta);
-        const double c = rsqrt(fma(t, t, 1.0)), sn = t * c;
+        const double theta = (K[q][q] - K[p][p]) * (0.5 * rcp_fast(kpq));
+        const double t = copysign(rcp_fast(fabs(theta) + sqrt_fast(fma(theta, theta, 1.0))), theta);
+        const double c = rsqrt_fast(fma(t, t, 1.0)), sn = t * c;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           const double kp = K[k][p], kq = K[k][q];
@@ -337,7 +392,7 @@ __device__ __forceinline__ void gauss_step(double (&A)[N][N], double (&b)[N]) {
       b[K] = sw ? b[i] : tb;
       b[i] = sw ? tb : b[i];
     }
-    const double ip = rcp(A[K][K]);
+    const double ip = rcp_fast(A[K][K]);
 #pragma unroll
     for (int i = K + 1; i < N; ++i) {
       const double f = A[i][K] * ip;
@@ -360,7 +415,7 @@ __device__ __forceinline__ void gauss_solve(double (&A)[N][N], double (&b)[N], d
     double sum = b[k];
 #pragma unroll
     for (int j = k + 1; j < N; ++j) sum = fma(-A[k][j], x[j], sum);
-    x[k] = sum * rcp(A[k][k]);
+    x[k] = sum * rcp_fast(A[k][k]);
   }
 }
 
@@ -386,10 +441,10 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
   double hs = 0.0, hus = 0.0;
 #pragma unroll
   for (int m = 0; m < M; ++m) { hs += hb[m]; hus = fma(hb[m], u[m], hus); }
-  const double ubar = hus * rcp(hs);
+  const double ubar = hus * rcp_fast(hs);
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const double sq = sqrt(mu[k]);
+    const double sq = sqrt_fast(mu[k]);
     lam[k] = ubar - sq;
     lam[N - 1 - k] = ubar + sq;
   }
@@ -397,7 +452,7 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
 #pragma unroll
   for (int m = 0; m + 1 < M; ++m) {
     const double du = u[m] - u[m + 1];
-    lst = lst || (du * du >= (1.0 - P.rho[m] * rcp(P.rho[m + 1])) * g * (hb[m] + hb[m + 1]));
+    lst = lst || (du * du >= (1.0 - P.rr[m][m + 1]) * g * (hb[m] + hb[m + 1]));
   }
   auto build_A = [&](double l, double A[M][M]) {
 #pragma unroll
@@ -433,7 +488,7 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
     double A[M][M];
     build_A(lam[p], A);
     const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-    const double id2 = rcp(det2);
+    const double id2 = rcp_fast(det2);
     dh[p][0] = 1.0;
     dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
     dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
@@ -461,16 +516,16 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const double
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-    const double inv = rcp(sl + sr);
+    const double inv = rcp_fast(sl + sr);
     uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
     vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
-    wq[m] = sqrt(g * hb[m] * rcp(P.rho[m]));
+    wq[m] = sqrt_fast(g * hb[m] * P.irho[m]);
   }
   coupling_matrix<M>(P, hb, G);
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * fmin(P.rho[m], P.rho[n]);
+    for (int n = 0; n < M; ++n) K[m][n] = wq[m] * wq[n] * P.rho[m < n ? m : n];  // densities increase downwards
   jacobi_eigenvalues<M>(K, mu);
   double lam[N], dh[N][M];
   lost += general_eig<M>(P, G, uh, hb, mu, lam, dh) ? 1 : 0;
@@ -562,6 +617,10 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     }
     const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * inv4[2];
     const double dc = c1 - c2;
+    // The library rsqrt here (not rsqrt_fast): with the iteration's range branches at these
+    // three calls, the recording form of the kernel (STORE) and the plain one no longer
+    // round the surrounding arithmetic the same way, and recorded steps must equal plain
+    // steps bit for bit.
     const double X = dc * dc + 4.0 * P.r * c1 * c2;
     const double rX = rsqrt(X);
     const double disc = X * rX;
@@ -602,7 +661,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
         }
         // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
         const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
-        const double inv = 0.5 * rcp(p01 * p23);
+        const double inv = 0.5 * rcp_fast(p01 * p23);
         const double i01 = inv * p23, i23 = inv * p01;
         const double q[4] = {i01 * dP[1], i01 * dP[0], i23 * dP[3], i23 * dP[2]};  // 1/P'(lambda_p)
 #pragma unroll
@@ -637,7 +696,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     den[2] = l02 * l12 * l23;
     den[3] = -l03 * l13 * l23;
     const double q01 = den[0] * den[1], q23 = den[2] * den[3];
-    const double iall = rcp(q01 * q23);
+    const double iall = rcp_fast(q01 * q23);
     double iden[4];
     iden[0] = iall * q23 * den[1];
     iden[1] = iall * q23 * den[0];
@@ -689,12 +748,12 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     const double hL = cL[3 * m], hR = cR[3 * m];
     if (wl && wr) {
       const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-      const double inv = rcp(sl + sr);
+      const double inv = rcp_fast(sl + sr);
       const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
       const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
       // one reciprocal square root gives c = sqrt(g hbar) and 1/(s2 - s1) = 1/(2c)
       const double gh = g * hb[m];
-      const double tc = rsqrt(gh);
+      const double tc = rsqrt_fast(gh);
       const double ch = gh * tc;
       split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W, 0.5 * tc);
       W.hbt[m] = hb[m];
@@ -717,7 +776,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
         W.hbt[m] = hw;
       } else {
         const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-        const double inv = rcp(sl + sr);
+        const double inv = rcp_fast(sl + sr);
         const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
         const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
         const double ch = sqrt(g * hb[m]);
@@ -764,12 +823,12 @@ __device__ __forceinline__ void trans_eigen2(const DevParams& P, const double* h
   const double ubar = (hb[0] * ut[0] + hb[1] * ut[1]) * inv2[0];
   const double dc = c1 - c2;
   const double X = dc * dc + 4.0 * P.r * c1 * c2;
-  const double disc = X * rsqrt(X);
+  const double disc = X * rsqrt_fast(X);
   const double mup = 0.5 * ((c1 + c2) + disc);
-  const double tp = rsqrt(mup);
+  const double tp = rsqrt_fast(mup);
   const double sp = mup * tp;
   const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
-  const double sm = mum * rsqrt(mum);
+  const double sm = mum * rsqrt_fast(mum);
   double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
   const double du = ut[0] - ut[1];
   const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
@@ -859,7 +918,7 @@ __device__ __forceinline__ void trans_apply_layers(const DevParams& P, int act, 
   for (int m = 0; m < M; ++m) {
     if (!((act >> m) & 1)) continue;
     const double gh = P.g * hb[m];
-    const double tc = rsqrt(gh);
+    const double tc = rsqrt_fast(gh);
     const double c = gh * tc;
     const double inv = 0.5 * tc;  // 1 / (s2 - s1)
     const double s1 = ut[m] - c, s2 = ut[m] + c;

@@ -447,6 +447,10 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
   H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
   for (int m = 0; m < 4; ++m) H->dp.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
+  for (int m = 0; m < 4; ++m) {
+    H->dp.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
+    for (int n = 0; n < 4; ++n) H->dp.rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
+  }
   H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
   H->dp.unsplit = cfg->unsplit;
   cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);

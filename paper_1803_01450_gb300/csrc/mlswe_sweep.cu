@@ -201,7 +201,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         above = w;
         wet |= w ? (1 << m) : 0;
         // one reciprocal square root gives both sqrt(h) = h t and 1/h = t t
-        const double t = hbits > 0 ? rsqrt(h) : 0.0;
+        const double t = hbits > 0 ? rsqrt_fast(h) : 0.0;
         double un = 0.0, ut = 0.0;
         if (w) { const double ih = t * t; un = hn * ih; ut = ht * ih; }
         rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;

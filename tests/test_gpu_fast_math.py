@@ -1,0 +1,107 @@
+"""The sweep kernel's reciprocal, reciprocal square root and square root by iteration (FP32
+seed and one third-order Newton-Raphson step where |x| lies in [2^-160, 2^160), the library
+functions elsewhere) against an exact reference (50-digit decimal arithmetic, correctly
+rounded back to FP64) and against CUDA's own functions: at most one unit in the last place
+from the correctly rounded value, and the library's values where the iteration does not run
+(zero, subnormals, huge and non-finite arguments, negative square roots)."""
+import ctypes
+import decimal
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def mc(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    so = str(tmp_path_factory.mktemp("mc") / "libmc.so")
+    subprocess.run([nvcc, "-std=c++17", "-O3", "-shared", "-Xcompiler", "-fPIC",
+                    "-gencode", "arch=compute_103a,code=sm_103a", "-o", so, os.path.join(HERE, "math_check.cu")],
+                   check=True, capture_output=True)
+    L = ctypes.CDLL(so)
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.mc_run.argtypes = [dp, ctypes.c_int, dp]
+    L.mc_run.restype = ctypes.c_int
+    return L
+
+
+def run(mc, x):
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.zeros((6, len(x)))
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert mc.mc_run(x.ctypes.data_as(dp), len(x), out.ctypes.data_as(dp)) == 0
+    return out
+
+
+def ulps(a, b):
+    """Distance in units in the last place between doubles of the same sign."""
+    ia, ib = a.view(np.int64), b.view(np.int64)
+    return np.abs(ia - ib)
+
+
+def exact(x, kind):
+    decimal.getcontext().prec = 50
+    out = np.empty_like(x)
+    for k, v in enumerate(x):
+        d = decimal.Decimal(float(v))
+        if kind == "rcp":
+            r = 1 / d
+        elif kind == "rsqrt":
+            r = 1 / d.sqrt()
+        else:
+            r = d.sqrt()
+        out[k] = float(r)  # correctly rounded
+    return out
+
+
+def moderate_inputs(rng, n, positive):
+    e = rng.uniform(-159.5, 159.5, n)
+    x = np.exp2(e) * rng.uniform(1.0, 2.0, n)
+    x = np.concatenate([x, 1.0 + np.arange(64) * 2.0 ** -20, [1.0, 2.0, 4.0, 0.5, 3.0, 1.5, 2.0 ** 159, 2.0 ** -160]])
+    if not positive:
+        x = x * np.where(rng.random(len(x)) < 0.5, -1.0, 1.0)
+    return x
+
+
+def test_reciprocal_within_one_ulp(mc):
+    rng = np.random.default_rng(11)
+    x = moderate_inputs(rng, 200000, positive=False)
+    out = run(mc, x)
+    assert (ulps(out[0], out[1]) <= 1).all()  # CUDA's __drcp_rn is correctly rounded
+    s = x[:3000]
+    assert (ulps(out[0][:3000], exact(s, "rcp")) <= 1).all()
+
+
+def test_reciprocal_square_root_and_square_root_within_one_ulp(mc):
+    rng = np.random.default_rng(12)
+    x = moderate_inputs(rng, 200000, positive=True)
+    out = run(mc, x)
+    s = x[:3000]
+    assert (ulps(out[2][:3000], exact(s, "rsqrt")) <= 1).all()
+    assert (ulps(out[4][:3000], exact(s, "sqrt")) <= 2).all()  # x times an rsqrt within one ulp
+    # against CUDA's rsqrt (itself within one ulp) and correctly rounded sqrt, on all inputs
+    assert (ulps(out[2], out[3]) <= 2).all()
+    assert (ulps(out[4], out[5]) <= 2).all()
+
+
+def test_outside_the_range_the_library_functions_answer(mc):
+    tiny = np.nextafter(0.0, 1.0)
+    x = np.array([0.0, -0.0, tiny, 1e-300, 2.0 ** -161, 2.0 ** 161, 1e300, np.inf, -np.inf, np.nan, -1.0, -4.0,
+                  -2.0 ** -170, 2.0 ** -170])
+    out = run(mc, x)
+    for fast, ref in ((0, 1), (2, 3), (4, 5)):
+        a, b = out[fast], out[ref]
+        for k, v in enumerate(x):
+            if fast == 0 and 2.0 ** -160 <= abs(v) < 2.0 ** 161:
+                continue  # -1, -4 are in range for the reciprocal
+            assert (np.isnan(a[k]) and np.isnan(b[k])) or a[k].view(np.int64) == b[k].view(np.int64), (fast, v)
+    inr = np.abs(x) >= 2.0 ** -160
+    inr &= np.abs(x) < 2.0 ** 161
+    assert (ulps(out[0][inr], out[1][inr]) <= 1).all()
