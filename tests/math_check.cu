@@ -1,6 +1,6 @@
 // Device wrapper around the sweep kernel's iterative reciprocal and reciprocal square root
-// (compiled by the test for the GPU) so that they can be compared with the library
-// functions and with an exact reference.
+// and its left share of a limited wave (compiled by the test for the GPU) so that they can
+// be compared with the library functions, an exact reference and the textbook formula.
 #include <cuda_runtime.h>
 #include "../paper_1803_01450_gb300/csrc/mlswe_device.cuh"
 
@@ -16,7 +16,37 @@ __global__ void math_kernel(const double* __restrict__ x, int n, double* __restr
   out[4 * (size_t)n + i] = mlswe::sqrt_fast(v);
   out[5 * (size_t)n + i] = sqrt(v);
 }
+__global__ void share_kernel(const double* __restrict__ in, const int* __restrict__ flags, int n,
+                             double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int* f = flags + 3 * i;
+  out[i] = mlswe::left_share(f[0], f[1], f[2] != 0, in[4 * i], in[4 * i + 1], in[4 * i + 2], in[4 * i + 3]);
+}
 }  // namespace
+
+// Left share of a wave (the sweep's left_share): in = (num, iden, s, nu) per case, flags =
+// (limiter kind, sign class of s, active) per case.
+extern "C" int mc_left_share(const double* in_host, const int* flags_host, int n, double* out_host) {
+  if (n <= 0) return 0;
+  double *din = nullptr, *dout = nullptr;
+  int* dfl = nullptr;
+  int rc = 0;
+  if (cudaMalloc(&din, sizeof(double) * 4 * (size_t)n) != cudaSuccess) return 1;
+  if (cudaMalloc(&dout, sizeof(double) * n) != cudaSuccess) rc = 1;
+  if (!rc && cudaMalloc(&dfl, sizeof(int) * 3 * (size_t)n) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(din, in_host, sizeof(double) * 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc && cudaMemcpy(dfl, flags_host, sizeof(int) * 3 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess) rc = 1;
+  if (!rc) {
+    share_kernel<<<(n + 255) / 256, 256>>>(din, dfl, n, dout);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = 1;
+  }
+  if (!rc && cudaMemcpy(out_host, dout, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess) rc = 1;
+  cudaFree(din);
+  cudaFree(dout);
+  cudaFree(dfl);
+  return rc;
+}
 
 extern "C" int mc_run(const double* x_host, int n, double* out_host) {
   if (n <= 0) return 0;

@@ -3,7 +3,10 @@ seed and one third-order Newton-Raphson step where |x| lies in [2^-160, 2^160), 
 functions elsewhere) against an exact reference (50-digit decimal arithmetic, correctly
 rounded back to FP64) and against CUDA's own functions: at most one unit in the last place
 from the correctly rounded value, and the library's values where the iteration does not run
-(zero, subnormals, huge and non-finite arguments, negative square roots)."""
+(zero, subnormals, huge and non-finite arguments, negative square roots). And the share of a
+limited wave that goes to the left cell, whose weight carries the MC limiter's factor 2,
+against the second-order correction written out as in the wave-propagation method:
+base + sign(s) (1 - nu |s|) phi(theta) / 2."""
 import ctypes
 import decimal
 import os
@@ -29,6 +32,8 @@ def mc(tmp_path_factory):
     dp = ctypes.POINTER(ctypes.c_double)
     L.mc_run.argtypes = [dp, ctypes.c_int, dp]
     L.mc_run.restype = ctypes.c_int
+    L.mc_left_share.argtypes = [dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, dp]
+    L.mc_left_share.restype = ctypes.c_int
     return L
 
 
@@ -105,3 +110,43 @@ def test_outside_the_range_the_library_functions_answer(mc):
     inr = np.abs(x) >= 2.0 ** -160
     inr &= np.abs(x) < 2.0 ** 161
     assert (ulps(out[0][inr], out[1][inr]) <= 1).all()
+
+
+def _phi(kind, th):
+    if kind == 0:
+        return 1.0
+    if th <= 0.0:
+        return 0.0
+    if kind == 1:
+        return min(1.0, th)
+    return max(0.0, min(0.5 * (1.0 + th), 2.0, 2.0 * th))
+
+
+def test_left_share_matches_the_written_out_correction(mc):
+    rng = np.random.default_rng(13)
+    n = 60000
+    kind = rng.integers(0, 3, n)
+    sc = rng.choice([-1, 0, 1], n, p=[0.45, 0.1, 0.45])
+    act = (rng.random(n) < 0.9) & (sc != 0)
+    s = sc * np.exp2(rng.uniform(-8, 4, n))
+    nu = rng.uniform(0.0, 0.9, n) / np.maximum(np.abs(s), 1e-300)
+    nu = np.where(sc == 0, rng.uniform(0.0, 1.0, n), nu)
+    # theta spanning the limiter's kinks (0, 1/3, 1, 3) and both signs
+    th = np.concatenate([rng.uniform(-2, 6, n // 2), rng.choice([0.0, 1 / 3, 1.0, 3.0, -0.0], n - n // 2)])
+    th = th * (1.0 + rng.uniform(-1e-12, 1e-12, n))
+    num = th * np.exp2(rng.integers(-20, 20, n))
+    iden = np.where(th == 0, 1.0, th / np.where(num == 0, 1.0, num))
+    inp = np.ascontiguousarray(np.stack([num, iden, s, nu], axis=1))
+    fl = np.ascontiguousarray(np.stack([kind, sc, act.astype(int)], axis=1).astype(np.int32))
+    out = np.zeros(n)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert mc.mc_left_share(inp.ctypes.data_as(dp), fl.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n,
+                            out.ctypes.data_as(dp)) == 0
+    for k in range(n):
+        base = 1.0 if sc[k] < 0 else (0.0 if sc[k] > 0 else 0.5)
+        ref = base
+        if act[k]:
+            t = num[k] * iden[k]  # theta as the kernel forms it
+            ref = base + (0.5 if sc[k] > 0 else -0.5) * (1.0 - nu[k] * abs(s[k])) * _phi(kind[k], t)
+        # a few roundings apart (the kernel fuses; the written-out form rounds each step)
+        assert abs(out[k] - ref) <= 1e-15 * max(1.0, abs(ref)), (k, kind[k], sc[k], act[k], out[k], ref)
