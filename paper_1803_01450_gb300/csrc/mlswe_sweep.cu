@@ -163,22 +163,26 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       int i, j;
       if (DIR == 0) { i = item.i0 - kNG + k; j = item.j0 + l; }
       else { i = item.i0 + l; j = item.j0 - kNG + k; }
-      double sgn = 1.0, sgt = 1.0;
+      // wall mirror: the momentum normal to the wall changes sign (sign-bit masks, applied on
+      // the integer unit)
+      long long sgn = 0, sgt = 0;
+      constexpr long long kSign = (long long)0x8000000000000000ull;
       if (DIR == 0) {
-        if (i < 0) { i = -1 - i; sgn = -1.0; }
-        else if (i >= NX) { i = 2 * NX - 1 - i; sgn = -1.0; }
+        if (i < 0) { i = -1 - i; sgn = kSign; }
+        else if (i >= NX) { i = 2 * NX - 1 - i; sgn = kSign; }
         if (UNSPLIT) {  // ghost rows beyond the domain: wall mirror
-          if (j < 0) { j = -1 - j; sgt = -1.0; }
-          else if (j >= NY) { j = 2 * NY - 1 - j; sgt = -1.0; }
+          if (j < 0) { j = -1 - j; sgt = kSign; }
+          else if (j >= NY) { j = 2 * NY - 1 - j; sgt = kSign; }
         }
       } else {
-        if (j < 0) { j = -1 - j; sgn = -1.0; }
-        else if (j >= NY) { j = 2 * NY - 1 - j; sgn = -1.0; }
+        if (j < 0) { j = -1 - j; sgn = kSign; }
+        else if (j >= NY) { j = 2 * NY - 1 - j; sgn = kSign; }
         if (UNSPLIT) {
-          if (i < 0) { i = -1 - i; sgt = -1.0; }
-          else if (i >= NX) { i = 2 * NX - 1 - i; sgt = -1.0; }
+          if (i < 0) { i = -1 - i; sgt = kSign; }
+          else if (i >= NX) { i = 2 * NX - 1 - i; sgt = kSign; }
         }
       }
+      auto flip = [](double v, long long mask) { return __longlong_as_double(__double_as_longlong(v) ^ mask); };
       const size_t o = (size_t)j * Pt + i;
       const int c = sb[0][g] + cslot<DIR>(l, k, len, nl);
       double rec[R::N];
@@ -191,8 +195,8 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const double h = qin[(3 * m) * plane + o];
         const double hu = qin[(3 * m + 1) * plane + o];
         const double hv = qin[(3 * m + 2) * plane + o];
-        const double hn = (DIR == 0 ? hu : hv) * sgn;
-        const double ht = UNSPLIT ? (DIR == 0 ? hv : hu) * sgt : (DIR == 0 ? hv : hu);
+        const double hn = flip(DIR == 0 ? hu : hv, sgn);
+        const double ht = UNSPLIT ? flip(DIR == 0 ? hv : hu, sgt) : (DIR == 0 ? hv : hu);
         rec[3 * m] = h; rec[3 * m + 1] = hn; rec[3 * m + 2] = ht;
         // comparisons on bit patterns (integer unit): for a bound b >= +0 and any non-NaN
         // x, x > b exactly when bits(x) > bits(b) as signed 64-bit integers
