@@ -30,6 +30,7 @@ constexpr int kMaxEdges = 256;  // edges per tile (one thread each)
 constexpr int kMaxCells = 288;  // cells per tile (edges + lines, lines <= 32)
 constexpr int kThreads = 256;
 constexpr int kMaxGroups = 4;   // groups of lines (runs of patch lines) packed into one sweep tile
+constexpr int kUpdLen = 31, kUpdRows = 8;  // cell tiles of the unsplit step's update (one warp per row)
 
 struct DevParams {
   int M;

@@ -171,7 +171,11 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
       int tl, tn;
       tile_dims(ts, dir != 1 ? b.i1 - b.i0 : b.j1 - b.j0, &tl, &tn);
       if (dir == 2) {
-        // update tiles of the unsplit step: rows of the patch, cells along x
+        // update tiles of the unsplit step: up to kUpdRows rows of the patch, the row split
+        // into equal parts of at most kUpdLen cells
+        const int parts = (b.w() + kUpdLen - 1) / kUpdLen;
+        tl = (b.w() + parts - 1) / parts;
+        tn = kUpdRows;
         for (int j = b.j0; j < b.j1; j += tn) {
           const int nl = std::min(tn, b.j1 - j);
           for (int i = b.i0; i < b.i1; i += tl) {
@@ -350,7 +354,7 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record) {
     }
   }
   if (H->cfg.unsplit) {
-    // the cell update after both edge passes (memory-bound: 4 CTAs of 256 threads per SM)
+    // the cell update after both edge passes (4 CTAs of 256 threads per SM)
     Hier::WorkList& W = H->wu[level];
     const int full = 4 * H->num_sms;
     if (!H->per_patch_launch) {
@@ -402,7 +406,6 @@ void set_level_shape(Hier* H, int level, int dir, int len, int lines, int ctas) 
   H->shape[level * 2 + dir].lines = lines;
   H->shape[level * 2 + dir].ctas = ctas;
   H->wl[level * 2 + dir].dirty = true;
-  if (dir == 0) H->wu[level].dirty = true;  // the update tiles take the x shape
 }
 
 }  // namespace mlswe

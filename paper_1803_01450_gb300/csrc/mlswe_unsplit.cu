@@ -9,19 +9,30 @@
 // cell left of the x edge + parts towards -x received by the cell right of it), Gy likewise
 // with dt / 2 dx; then the positivity fix. At coarse/fine interfaces and refined patch
 // boundaries the transverse part of the mass flux is added to the flux records the edge
-// passes started (one cell owns each edge). Every thread one cell, rows of a tile along x so
-// that neighbouring threads read neighbouring edges; each transverse flux sum is formed for
-// both cells beside it, so the FP64 work rather than the reads sets the time.
+// passes started (one cell owns each edge).
+//
+// Each transverse sum belongs to an edge, and two cells use it: tiles of at most
+// kUpdLen x kUpdRows cells, one warp per row. Lane k forms the sum of the x edge left of its
+// cell (lane len the one right of the last cell) and takes its right one from lane k + 1 by
+// a shuffle; each warp forms the sums of the y edges below its row into shared memory (the
+// last row's warp also those above it). Every sum is formed once (plus one edge per row and
+// one row of edges per tile) instead of twice, with the same operands in the same order, so
+// the values are those of forming them per cell. All global reads of a tile are issued
+// before its one barrier; the reads of the edge records (36 doubles per edge for two layers)
+// set the time.
 #include <cuda_runtime.h>
 #include "mlswe_device.cuh"
 
 namespace mlswe {
 
 template <int M>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
                       const int* __restrict__ n_items_dev, int parity, int record) {
+  static_assert(kUpdRows * 32 == kThreads && kUpdLen < 32, "one warp per row, one spare lane");
   constexpr int F = 3 * M;
+  __shared__ double gys[F][kUpdRows + 1][32];  // sums of the y edges below rows 0 .. nl (row nl: above nl - 1)
+  const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
   const int n_items = *n_items_dev;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const SweepItem item = items[it];
@@ -30,16 +41,17 @@ unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Sw
     const size_t plane = (size_t)NY * Pt;
     const double* __restrict__ qin = D.q[parity];
     double* __restrict__ qout = D.q[parity ^ 1];
-    const int len = item.len, ncell = item.nlines * len;
+    const int len = item.len, nl = item.nlines;  // len <= kUpdLen, nl <= kUpdRows
+    const int i = item.i0 + lane, j = item.j0 + l;
+    const bool row = l < nl, cell = row && lane < len;
     if (D.active != nullptr && *D.active == 0) {
       // no step for this member in this substep: copy the state through
-      for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-        const int l = t / len, k = t - l * len;
-        const size_t o = (size_t)(item.j0 + l) * Pt + (item.i0 + k);
+      if (cell) {
+        const size_t o = (size_t)j * Pt + i;
 #pragma unroll
         for (int f = 0; f < F; ++f) qout[f * plane + o] = qin[f * plane + o];
       }
-      continue;
+      continue;  // the same for every thread of the block; no shared memory used
     }
     const double dt = *D.dt;
     const double nux = dt * D.inv_dx, nuy = dt * D.inv_dy;
@@ -48,64 +60,97 @@ unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Sw
     const double* __restrict__ Y = D.ue + 6LL * F * D.uxp;
     const long long xp = D.uxp, yp = D.uyp;
     const long long xr = NX + 1, yr = NX + 2;  // edges per x-edge row, per y-edge row
-    const bool rec = record && (D.covered != nullptr || D.in_patch != nullptr);
-    const long long tol_bits = __double_as_longlong(P.dry_tol);
-    for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
-      const int l = t / len, k = t - l * len;
-      const int i = item.i0 + k, j = item.j0 + l;
-      const size_t o = (size_t)j * Pt + i;
-      const long long xl = (long long)(j + 1) * xr + i;  // x edge left of the cell
-      const long long yb = (long long)j * yr + (i + 1);   // y edge below the cell
-      // groups: 0 into the lower-index cell, 1 into the higher-index cell, 2/3 the transverse
-      // parts of group 0 towards +t/-t, 4/5 those of group 1
-      auto XG = [&](int g, int f, long long e) { return X[(long long)(g * F + f) * xp + e]; };
-      auto YG = [&](int g, int f, long long e) { return Y[(long long)(g * F + f) * yp + e]; };
+    // groups: 0 into the lower-index cell, 1 into the higher-index cell, 2/3 the transverse
+    // parts of group 0 towards +t/-t, 4/5 those of group 1
+    auto XG = [&](int g, int f, long long e) { return X[(long long)(g * F + f) * xp + e]; };
+    auto YG = [&](int g, int f, long long e) { return Y[(long long)(g * F + f) * yp + e]; };
+    // transverse sum of the y edge above the cell whose left x edge is x
+    auto ysum = [&](int f, long long x) {
+      return XG(4, f, x) + XG(2, f, x + 1) + XG(5, f, x + xr) + XG(3, f, x + xr + 1);
+    };
+    // transverse sum of the x edge right of the cell whose bottom y edge is y
+    auto xsum = [&](int f, long long y) {
+      return YG(4, f, y) + YG(2, f, y + yr) + YG(5, f, y + 1) + YG(3, f, y + yr + 1);
+    };
+    const long long xl = (long long)(j + 1) * xr + i;  // x edge left of the cell
+    const long long yb = (long long)j * yr + (i + 1);   // y edge below the cell
+    // every global read of the tile before the barrier (no exchange needs them earlier):
+    // the y-edge sums into shared memory, the x-edge sums, fluctuations and Q^n in registers
+    const bool edge = row && lane <= len;  // lanes 0 .. len form the x edges of the row
+    double sgl[F], dxn[F], dyn[F], q0[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) { sgl[f] = 0.0; dxn[f] = 0.0; dyn[f] = 0.0; q0[f] = 0.0; }
+    if (cell) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) gys[f][l][lane] = ysum(f, xl - xr);
+      if (l == nl - 1) {
+#pragma unroll
+        for (int f = 0; f < F; ++f) gys[f][nl][lane] = ysum(f, xl);
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        dxn[f] = XG(1, f, xl) + XG(0, f, xl + 1);
+        dyn[f] = YG(1, f, yb) + YG(0, f, yb + yr);
+        q0[f] = qin[f * plane + (size_t)j * Pt + i];
+      }
+    }
+    if (edge) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) sgl[f] = xsum(f, yb - 1);
+    }
+    __syncthreads();
+    if (row) {  // whole warps
       double qn[F], gxl[M], gxr[M], gyb[M], gyt[M];
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        const double dxn = XG(1, f, xl) + XG(0, f, xl + 1);
-        const double dyn = YG(1, f, yb) + YG(0, f, yb + yr);
-        const double sgt = XG(4, f, xl) + XG(2, f, xl + 1) + XG(5, f, xl + xr) + XG(3, f, xl + xr + 1);
-        const double sgb = XG(4, f, xl - xr) + XG(2, f, xl - xr + 1) + XG(5, f, xl) + XG(3, f, xl + 1);
-        const double sgr = YG(4, f, yb) + YG(2, f, yb + yr) + YG(5, f, yb + 1) + YG(3, f, yb + yr + 1);
-        const double sgl = YG(4, f, yb - 1) + YG(2, f, yb + yr - 1) + YG(5, f, yb) + YG(3, f, yb + yr);
-        qn[f] = qin[f * plane + o] - nux * dxn - nuy * dyn + hxy * ((sgr - sgl) + (sgt - sgb));
-        if (f % 3 == 0) {
-          gxl[f / 3] = sgl; gxr[f / 3] = sgr; gyb[f / 3] = sgb; gyt[f / 3] = sgt;
+        const double sgr = __shfl_down_sync(0xffffffffu, sgl[f], 1);
+        qn[f] = 0.0;
+        if (cell) {
+          const double sgb = gys[f][l][lane], sgt = gys[f][l + 1][lane];
+          qn[f] = q0[f] - nux * dxn[f] - nuy * dyn[f] + hxy * ((sgr - sgl[f]) + (sgt - sgb));
+          if (f % 3 == 0) {
+            gxl[f / 3] = sgl[f]; gxr[f / 3] = sgr; gyb[f / 3] = sgb; gyt[f / 3] = sgt;
+          }
         }
       }
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        if (__double_as_longlong(qn[3 * m]) < 0) qn[3 * m] = 0.0;
-        if (__double_as_longlong(qn[3 * m]) <= tol_bits) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
-      }
-#pragma unroll
-      for (int f = 0; f < F; ++f) qout[f * plane + o] = qn[f];
-      if (!rec) continue;
-      // Transverse part of the mass flux through this cell's left / bottom edge, and through
-      // its right / top edge when the neighbour there is in no patch of the level (otherwise
-      // that neighbour owns the edge).
-      const double hy = -0.5 * nuy, hx = -0.5 * nux;
-      auto add = [&](bool xdir, int a, int line, const double* s, double h) {
-        const size_t cA = xdir ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
-        const size_t cB = xdir ? cA + 1 : cA + NX;
-        const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
-        const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
-        if (!iface && !bnd) return;
+      if (cell) {
+        const long long tol_bits = __double_as_longlong(P.dry_tol);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-          const double gm = h * s[m];
-          const size_t fo = xdir ? ((size_t)m * NY + line) * (NX + 1) + a : ((size_t)m * (NY + 1) + a) * NX + line;
-          if (iface) (xdir ? D.fxc : D.fyc)[fo] += gm;
-          if (bnd) (xdir ? D.fxf : D.fyf)[fo] += dt * gm;
+          if (__double_as_longlong(qn[3 * m]) < 0) qn[3 * m] = 0.0;
+          if (__double_as_longlong(qn[3 * m]) <= tol_bits) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
         }
-      };
-      if (i >= 1) add(true, i, j, gxl, hy);
-      if (i + 1 <= NX - 1 && D.in_patch != nullptr && D.in_patch[(size_t)j * NX + i + 1] == 0) add(true, i + 1, j, gxr, hy);
-      if (j >= 1) add(false, j, i, gyb, hx);
-      if (j + 1 <= NY - 1 && D.in_patch != nullptr && D.in_patch[(size_t)(j + 1) * NX + i] == 0)
-        add(false, j + 1, i, gyt, hx);
+        const size_t o = (size_t)j * Pt + i;
+#pragma unroll
+        for (int f = 0; f < F; ++f) qout[f * plane + o] = qn[f];
+        if (record && (D.covered != nullptr || D.in_patch != nullptr)) {
+          // Transverse part of the mass flux through this cell's left / bottom edge, and
+          // through its right / top edge when the neighbour there is in no patch of the level
+          // (otherwise that neighbour owns the edge).
+          const double hy = -0.5 * nuy, hx = -0.5 * nux;
+          auto add = [&](bool xdir, int a, int line, const double* sv, double h) {
+            const size_t cA = xdir ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
+            const size_t cB = xdir ? cA + 1 : cA + NX;
+            const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
+            const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
+            if (!iface && !bnd) return;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+              const double gm = h * sv[m];
+              const size_t fo = xdir ? ((size_t)m * NY + line) * (NX + 1) + a : ((size_t)m * (NY + 1) + a) * NX + line;
+              if (iface) (xdir ? D.fxc : D.fyc)[fo] += gm;
+              if (bnd) (xdir ? D.fxf : D.fyf)[fo] += dt * gm;
+            }
+          };
+          if (i >= 1) add(true, i, j, gxl, hy);
+          if (i + 1 <= NX - 1 && D.in_patch != nullptr && D.in_patch[(size_t)j * NX + i + 1] == 0) add(true, i + 1, j, gxr, hy);
+          if (j >= 1) add(false, j, i, gyb, hx);
+          if (j + 1 <= NY - 1 && D.in_patch != nullptr && D.in_patch[(size_t)(j + 1) * NX + i] == 0)
+            add(false, j + 1, i, gyt, hx);
+        }
+      }
     }
+    __syncthreads();  // the y-edge sums are rewritten for the next tile
   }
 }
 
