@@ -25,8 +25,11 @@
 
 namespace mlswe {
 
+// Resident CTAs: the kernel waits on its reads, so more warps help even at the cost of some
+// spilling (M <= 2: 4 CTAs of 64 registers, 0.96 ms against 1.03 ms with 2 CTAs of 128 on the
+// 2048^2 two-layer workload); three layers keep 2 CTAs of 128 registers.
 template <int M>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, M >= 3 ? 2 : 4)
 unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* __restrict__ items,
                       const int* __restrict__ n_items_dev, int parity, int record) {
   static_assert(kUpdRows * 32 == kThreads && kUpdLen < 32, "one warp per row, one spare lane");
