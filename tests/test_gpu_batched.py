@@ -61,6 +61,41 @@ def test_graph_direct_and_per_patch_are_bit_identical(mlswe_lib):
             assert np.array_equal(outs[0][k][1], outs[mode][k][1])
 
 
+@pytest.mark.parametrize("M,unsplit", [(1, 0), (3, 0), (2, 1)])
+def test_packed_and_per_patch_tiles_bit_identical(mlswe_lib, M, unsplit):
+    """The batched form packs runs of patch lines of several patches into one sweep tile;
+    the per-patch form keeps one rectangle of one patch per tile. One layer, three layers and
+    the unsplit step over two members of different sizes, regridding: identical layouts and
+    bit-identical states."""
+    r = 2
+    sizes = [(40, 40), (56, 48)]
+    rho = {1: (1000.0,), 2: (1000.0, 1025.0), 3: (1000.0, 1020.0, 1030.0)}[M]
+    surfaces = [-0.4, -0.8][: M - 1]
+    outs = []
+    for per_patch in (False, True):
+        cfg = mlswe_lib.Config(M=M, rho=rho, dry_tol=1e-6, max_levels=2, ratio=[r], flag_tol=1e-3,
+                               regrid_interval=4, n_buf=2, cluster_eff=0.7, min_side=8, max_side=32,
+                               unsplit=unsplit)
+        H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, nx, ny) for nx, ny in sizes])
+        for k, (nx, ny) in enumerate(sizes):
+            xf, yf = (np.arange(nx * r) + 0.5) / (nx * r), (np.arange(ny * r) + 0.5) / (ny * r)
+            Xf, _ = np.meshgrid(xf, yf)
+            H.set_bathymetry(k, -1.5 + 0.2 * Xf)
+            B0 = H.get_bathymetry(k, 0)
+            X, Y = np.meshgrid((np.arange(nx) + 0.5) / nx, (np.arange(ny) + 0.5) / ny)
+            eta1 = 0.02 * np.exp(-((X - 0.3 - 0.2 * k) ** 2 + (Y - 0.5) ** 2) / 0.005)
+            H.set_state(k, 0, I.stacked_state(B0, [eta1] + [s + 0.0 * X for s in surfaces]))
+        if per_patch:
+            H.set_execution(use_graphs=False, per_patch_launches=True)
+        H.advance(8)
+        outs.append([(H.get_patches(k, 1), H.get_state(k, 0), H.get_state(k, 1)) for k in range(len(sizes))])
+        H.close()
+    for k in range(len(sizes)):
+        assert len(outs[0][k][0]) > 0
+        for a, b in zip(outs[0][k], outs[1][k]):
+            assert np.array_equal(a, b)
+
+
 def test_graph_replay_is_deterministic(mlswe_lib):
     members = _members(range(2))
     res = []
