@@ -36,6 +36,7 @@ struct DevParams {
   int M;
   double g;
   double r;        // rho_1 / rho_2 (M = 2)
+  double omr, four_r, omr_g;  // 1 - r, 4 r, (1 - r) g (M = 2), computed on the host
   double rho[4];   // layer densities, top (lightest) first
   double rr[4][4];  // rho_n / rho_m at [n][m], computed on the host
   double irho[4];   // 1 / rho_m
@@ -189,6 +190,12 @@ __device__ __forceinline__ double rsqrt_iter(double x) {
 // The iterations where |x| lies in [2^-160, 2^160) (x > 0 for the square root), the
 // library functions elsewhere (zero, subnormal, huge, infinite, NaN or negative arguments).
 __device__ __forceinline__ double rcp_fast(double x) { return moderate(x) ? rcp_iter(x) : rcp(x); }
+// 0.5 / x: the iteration's result with its exponent field lowered by one (exact: the result
+// of a moderate argument is a normal number far from the subnormal range).
+__device__ __forceinline__ double half_rcp_fast(double x) {
+  if (moderate(x)) return __longlong_as_double(__double_as_longlong(rcp_iter(x)) - (1ll << 52));
+  return 0.5 * rcp(x);
+}
 __device__ __forceinline__ double rsqrt_fast(double x) {
   return __double_as_longlong(x) >= 0 && moderate(x) ? rsqrt_iter(x) : rsqrt(x);
 }
@@ -622,7 +629,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     // three calls, the recording form of the kernel (STORE) and the plain one no longer
     // round the surrounding arithmetic the same way, and recorded steps must equal plain
     // steps bit for bit.
-    const double X = dc * dc + 4.0 * P.r * c1 * c2;
+    const double c12 = c1 * c2;
+    const double X = dc * dc + P.four_r * c12;
     const double rX = rsqrt(X);
     const double disc = X * rX;
     const double csum = c1 + c2;
@@ -630,7 +638,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     const double mup = 0.5 * (csum + disc);
     const double tp = rsqrt(mup);
     const double sp = mup * tp;
-    const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
+    const double mum = (P.omr * c12) * (tp * tp);
     const double rmum = rsqrt(mum);
     const double sm = mum * rmum;
     double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
@@ -640,12 +648,12 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
 #pragma unroll
     for (int p = 0; p < 4; ++p) put(FwdRec::LAM0 + p, lam[p]);
     const double du = uh[0] - uh[1];
-    const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
+    const bool lst = du * du >= P.omr_g * (hb[0] + hb[1]);
     lost += lst ? 1 : 0;
     const bool newton = !lst && P.eigen == 0;
     put(FwdRec::NEWTON, newton ? 1.0 : 0.0);
     if (newton) {
-      const double rc = P.r * c1 * c2;
+      const double rc = P.r * c12;
 #pragma unroll
       for (int it = 0; it < 2; ++it) {
         if (it == 1) {
@@ -662,7 +670,7 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
         }
         // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
         const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
-        const double inv = 0.5 * rcp_fast(p01 * p23);
+        const double inv = half_rcp_fast(p01 * p23);
         const double i01 = inv * p23, i23 = inv * p01;
         const double q[4] = {i01 * dP[1], i01 * dP[0], i23 * dP[3], i23 * dP[2]};  // 1/P'(lambda_p)
 #pragma unroll
@@ -823,18 +831,19 @@ __device__ __forceinline__ void trans_eigen2(const DevParams& P, const double* h
   batched_reciprocal<2>(den2, inv2);
   const double ubar = (hb[0] * ut[0] + hb[1] * ut[1]) * inv2[0];
   const double dc = c1 - c2;
-  const double X = dc * dc + 4.0 * P.r * c1 * c2;
+  const double c12 = c1 * c2;
+  const double X = dc * dc + P.four_r * c12;
   const double disc = X * rsqrt_fast(X);
   const double mup = 0.5 * ((c1 + c2) + disc);
   const double tp = rsqrt_fast(mup);
   const double sp = mup * tp;
-  const double mum = ((1.0 - P.r) * c1 * c2) * (tp * tp);
+  const double mum = (P.omr * c12) * (tp * tp);
   const double sm = mum * rsqrt_fast(mum);
   double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
   const double du = ut[0] - ut[1];
-  const bool lst = du * du >= (1.0 - P.r) * g * (hb[0] + hb[1]);
+  const bool lst = du * du >= P.omr_g * (hb[0] + hb[1]);
   if (!lst && P.eigen == 0) {
-    const double rc = P.r * c1 * c2;
+    const double rc = P.r * c12;
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
       double Pl[4], dP[4], q[4];

@@ -449,6 +449,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   }
   if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
   H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  H->dp.omr = 1.0 - H->dp.r; H->dp.four_r = 4.0 * H->dp.r; H->dp.omr_g = (1.0 - H->dp.r) * cfg->g;
   for (int m = 0; m < 4; ++m) H->dp.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   for (int m = 0; m < 4; ++m) {
     H->dp.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;

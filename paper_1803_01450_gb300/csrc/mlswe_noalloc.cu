@@ -116,6 +116,7 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
   const int counts[2] = {(int)items[0].size(), (int)items[1].size()};
   DevParams P;
   P.M = cfg->M; P.g = cfg->g; P.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  P.omr = 1.0 - P.r; P.four_r = 4.0 * P.r; P.omr_g = (1.0 - P.r) * cfg->g;
   for (int m = 0; m < 4; ++m) P.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
   for (int m = 0; m < 4; ++m) {
     P.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
