@@ -40,6 +40,7 @@ struct DevParams {
   double rho[4];   // layer densities, top (lightest) first
   double rr[4][4];  // rho_n / rho_m at [n][m], computed on the host
   double irho[4];   // 1 / rho_m
+  double gap_g[4];  // (1 - rho_m / rho_{m+1}) g: reduced gravity between layers m and m + 1
   double dry_tol;
   int order;
   int limiter;
@@ -460,7 +461,7 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
 #pragma unroll
   for (int m = 0; m + 1 < M; ++m) {
     const double du = u[m] - u[m + 1];
-    lst = lst || (du * du >= (1.0 - P.rr[m][m + 1]) * g * (hb[m] + hb[m + 1]));
+    lst = lst || (du * du >= P.gap_g[m] * (hb[m] + hb[m + 1]));
   }
   auto build_A = [&](double l, double A[M][M]) {
 #pragma unroll

@@ -454,6 +454,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   for (int m = 0; m < 4; ++m) {
     H->dp.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
     for (int n = 0; n < 4; ++n) H->dp.rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
+    H->dp.gap_g[m] = m + 1 < cfg->M ? (1.0 - cfg->rho[m] / cfg->rho[m + 1]) * cfg->g : 0.0;
   }
   H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
   H->dp.unsplit = cfg->unsplit;

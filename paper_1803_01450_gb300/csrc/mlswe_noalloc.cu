@@ -121,6 +121,7 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
   for (int m = 0; m < 4; ++m) {
     P.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
     for (int n = 0; n < 4; ++n) P.rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
+    P.gap_g[m] = m + 1 < cfg->M ? (1.0 - cfg->rho[m] / cfg->rho[m + 1]) * cfg->g : 0.0;
   }
   P.dry_tol = cfg->dry_tol; P.order = cfg->order; P.limiter = cfg->limiter; P.eigen = cfg->eigen;
   P.unsplit = 0;
