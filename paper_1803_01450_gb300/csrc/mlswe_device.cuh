@@ -153,13 +153,26 @@ __device__ __forceinline__ bool moderate(double x) {
 // follows; its truncation error is O(eta^3) < 2^-56, so the result is within about one unit
 // in the last place of the exact value (not always the correctly rounded one).
 //
+// FP32 seeds: the hardware approximations (relative error about 2^-23), arguments in [1, 4)
+// (never subnormal, so flushing them to zero changes nothing).
+__device__ __forceinline__ float seed_rcp(float m) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));
+  return r;
+}
+__device__ __forceinline__ float seed_rsqrt(float m) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(m));
+  return r;
+}
+
 // 1/x for a normal x with |x| < 2^1022: with e = 1 - x y, y' = y + y (e + e^2).
 __device__ __forceinline__ double rcp_iter(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32);
   const int ex = (int)((hi >> 20) & 0x7ffu);                          // biased exponent of x
   const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3));  // significand in [1, 2)
-  const unsigned r = __float_as_uint(__frcp_rn(m));                    // 1/m in (1/2, 1]
+  const unsigned r = __float_as_uint(seed_rcp(m));                     // 1/m in (1/2, 1]
   const int re = (int)(r >> 23) - 127;                                  // its exponent: 0 or -1
   // 1/x = sign(x) (1/m) 2^(1023 - ex): biased exponent 2046 - ex + re
   const unsigned long long yb = (b & 0x8000000000000000ull) | ((unsigned long long)(2046 - ex + re) << 52) |
@@ -178,7 +191,7 @@ __device__ __forceinline__ double rsqrt_iter(double x) {
   const int E = (int)(hi >> 20) - 1023;  // unbiased exponent (x > 0: no sign bit)
   const int odd = E & 1;
   const float s = __uint_as_float((odd ? 0x40000000u : 0x3f800000u) | ((hi & 0xfffffu) << 3));
-  const unsigned r = __float_as_uint(rsqrtf(s));  // in (1/2, 1]
+  const unsigned r = __float_as_uint(seed_rsqrt(s));  // in (1/2, 1]
   const int re = (int)(r >> 23) - 127;            // 0 or -1
   const int k = (E - odd) / 2;                     // exact: E - odd is even
   const unsigned long long yb = ((unsigned long long)(1023 + re - k) << 52) | ((unsigned long long)(r & 0x7fffffu) << 29);
