@@ -182,7 +182,7 @@ __device__ __forceinline__ double rcp_iter(double x) {
   return fma(y, fma(e, e, e), y);
 }
 
-// 1/sqrt(x) for x > 0 with exponent in [-1000, 1000]: x = s 2^(2k) with s in [1, 4) (the
+// 1/sqrt(x) for any positive normal x: x = s 2^(2k) with s in [1, 4) (the
 // significand, doubled when the exponent is odd); with e = 1 - x y^2,
 // y' = y + y e (1/2 + 3 e / 8).
 __device__ __forceinline__ double rsqrt_iter(double x) {
@@ -639,21 +639,21 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
     }
     const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * inv4[2];
     const double dc = c1 - c2;
-    // The library rsqrt here (not rsqrt_fast): with the iteration's range branches at these
-    // three calls, the recording form of the kernel (STORE) and the plain one no longer
-    // round the surrounding arithmetic the same way, and recorded steps must equal plain
-    // steps bit for bit.
+    // X, mu_+ and mu_- are positive normal numbers here (both layers wet: c1, c2 > 0), where
+    // the iteration holds for any exponent: no range branch. (A branch at these three calls
+    // made the recording form of the kernel (STORE) round the surrounding arithmetic
+    // differently from the plain one; recorded steps must equal plain steps bit for bit.)
     const double c12 = c1 * c2;
     const double X = dc * dc + P.four_r * c12;
-    const double rX = rsqrt(X);
+    const double rX = rsqrt_iter(X);
     const double disc = X * rX;
     const double csum = c1 + c2;
     // mu_+ mu_- = (1 - r) c1 c2: mu_- without the cancellation of (csum - disc)/2
     const double mup = 0.5 * (csum + disc);
-    const double tp = rsqrt(mup);
+    const double tp = rsqrt_iter(mup);
     const double sp = mup * tp;
     const double mum = (P.omr * c12) * (tp * tp);
-    const double rmum = rsqrt(mum);
+    const double rmum = rsqrt_iter(mum);
     const double sm = mum * rmum;
     double lam[4] = {ubar - sp, ubar - sm, ubar + sm, ubar + sp};
     put(FwdRec::IDISC, rX);
