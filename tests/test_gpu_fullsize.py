@@ -1,0 +1,97 @@
+"""The batched-AMR workload at full size, in the launch configuration the benchmark times
+(512^2 coarse, ratios 4, 4, 1000 + 3000 seeded patches over the shore bathymetry,
+autotuned tiles, one persistent launch per level step, graph replay), checked where the
+oracle can follow it: a level-2 step of sampled patches (the most active and some at
+random) against the oracle's patch step on the same ghost-filled input, and the whole
+level-0 step against the oracle's walled step, within 1e-11 of each field's level-wide
+scale (near-rest momenta: within 10x the oracle's own one-ulp sensitivity)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1803_01450_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+NG = 2
+
+
+@pytest.fixture(scope="module")
+def amr_full(mlswe_lib):
+    n0, r, L = 512, 4, 1e5
+    nf = n0 * r * r
+    cfg = mlswe_lib.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16,
+                           max_side=64, flag_tol=5e-5)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)])
+    xf = I.centers(0.0, L, nf)
+    H.set_bathymetry(0, np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf))))
+    B0 = H.get_bathymetry(0, 0)
+    x0 = I.centers(0.0, L, n0)
+    X, Y = np.meshgrid(x0, x0)
+    eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
+    H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
+    l1 = I.random_layout(3100, n0 * r, n0 * r, 1000, r)
+    l2 = I.random_layout(3200, nf, nf, 3000, r, parents=l1, margin=2)
+    H.set_patches(0, 1, l1)
+    H.interp_fine(0, 0)
+    H.set_patches(0, 2, l2)
+    H.interp_fine(1, 0)
+    for lev in range(3):
+        H.autotune(lev, iters=2)
+    H.advance(1)
+    yield H, dict(n0=n0, r=r, L=L, nf=nf)
+    H.close()
+
+
+def _scale(q):
+    return np.maximum(np.abs(q).max(axis=(1, 2)), 1e-300)
+
+
+def test_level2_sampled_patches_match_oracle_patch_step(amr_full):
+    H, w = amr_full
+    nf, L = w["nf"], w["L"]
+    dx = L / nf
+    dt = 0.03  # Courant number about 0.5 at the deepest water on this level
+    boxes = H.get_patches(0, 2)
+    assert len(boxes) == 3000
+    H.fill_ghosts(2, 1.0)
+    q0 = H.get_state(0, 2)
+    B2 = H.get_bathymetry(0, 2)
+    H.step_level(2, dt=dt)
+    q1 = H.get_state(0, 2)
+    rng = np.random.default_rng(77)
+    inner = [b for b in boxes.tolist() if b[0] >= NG and b[1] >= NG and b[2] <= nf - NG and b[3] <= nf - NG]
+    # the three patches with the strongest flow and three at random
+    act = [np.abs(q0[[1, 2, 4, 5], b[1]:b[3], b[0]:b[2]]).max() for b in inner]
+    picks = list(np.argsort(act)[-3:]) + list(rng.choice(len(inner), 3, replace=False))
+    # level-wide per-field scale; momenta near rest are rounding noise of eta - B, so their
+    # bound is the larger of 1e-11 and 10x the oracle's own change under a one-ulp
+    # perturbation of its input
+    scale = np.maximum(np.abs(q0).max(axis=(1, 2)), np.abs(q1).max(axis=(1, 2)))
+    P = O.params(M=2, dry_tol=1e-3)
+    for k in picks:
+        i0, j0, i1, j1 = inner[k]
+        qp = np.ascontiguousarray(q0[:, j0 - NG:j1 + NG, i0 - NG:i1 + NG])
+        Bp = np.ascontiguousarray(B2[j0 - NG:j1 + NG, i0 - NG:i1 + NG])
+        pert = np.ascontiguousarray(qp * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=qp.shape)))
+        O.step_patch(P, qp, Bp, dx, dx, dt)
+        O.step_patch(P, pert, Bp, dx, dx, dt)
+        want = qp[:, NG:-NG, NG:-NG]
+        err = np.abs(q1[:, j0:j1, i0:i1] - want).max(axis=(1, 2)) / scale
+        sens = np.abs(pert[:, NG:-NG, NG:-NG] - want).max(axis=(1, 2)) / scale
+        assert err[[0, 3]].max() <= TOL, (inner[k], err)
+        assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (inner[k], err, sens)
+
+
+def test_level0_step_matches_oracle_walled_step(amr_full):
+    H, w = amr_full
+    n0, L = w["n0"], w["L"]
+    dx = L / n0
+    dt = 0.4
+    q0 = H.get_state(0, 0)
+    B0 = H.get_bathymetry(0, 0)
+    H.step_level(0, dt=dt)
+    q1 = H.get_state(0, 0)
+    want, _, _ = O.step_walled(O.params(M=2, dry_tol=1e-3), q0, B0, dx, dx, dt)
+    err = np.abs(q1 - want).max(axis=(1, 2)) / np.maximum(_scale(want), _scale(q0))
+    assert err.max() <= TOL, err
