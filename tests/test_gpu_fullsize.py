@@ -3,8 +3,9 @@
 autotuned tiles, one persistent launch per level step, graph replay), checked where the
 oracle can follow it: a level-2 step of sampled patches (the most active and some at
 random) against the oracle's patch step on the same ghost-filled input, and the whole
-level-0 step against the oracle's walled step, within 1e-11 of each field's level-wide
-scale (near-rest momenta: within 10x the oracle's own one-ulp sensitivity)."""
+level-0 step against the oracle's walled step; and the ensemble workload (256 members) on
+sampled members and patches. Within 1e-11 of each field's level-wide scale (near-rest
+momenta in deep water: within 10x the oracle's own one-ulp sensitivity)."""
 import numpy as np
 import pytest
 
@@ -45,6 +46,20 @@ def amr_full(mlswe_lib):
 
 def _scale(q):
     return np.maximum(np.abs(q).max(axis=(1, 2)), 1e-300)
+
+
+def _check_walled_step(P, q0, B, dx, dt, got, rng, where):
+    """got against the oracle's walled step of q0: depths within 1e-11 of their scale,
+    momenta within the larger of 1e-11 and 10x the oracle's own change under a one-ulp
+    perturbation of its input (deep water makes near-rest momentum rounding noise)."""
+    want, _, _ = O.step_walled(P, q0, B, dx, dx, dt)
+    pert = np.ascontiguousarray(q0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=q0.shape)))
+    wp, _, _ = O.step_walled(P, pert, B, dx, dx, dt)
+    scale = np.maximum(_scale(want), _scale(q0))
+    err = np.abs(got - want).max(axis=(1, 2)) / scale
+    sens = np.abs(wp - want).max(axis=(1, 2)) / scale
+    assert err[[0, 3]].max() <= TOL, (where, err)
+    assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (where, err, sens)
 
 
 def test_level2_sampled_patches_match_oracle_patch_step(amr_full):
@@ -92,6 +107,78 @@ def test_level0_step_matches_oracle_walled_step(amr_full):
     B0 = H.get_bathymetry(0, 0)
     H.step_level(0, dt=dt)
     q1 = H.get_state(0, 0)
-    want, _, _ = O.step_walled(O.params(M=2, dry_tol=1e-3), q0, B0, dx, dx, dt)
-    err = np.abs(q1 - want).max(axis=(1, 2)) / np.maximum(_scale(want), _scale(q0))
-    assert err.max() <= TOL, err
+    _check_walled_step(O.params(M=2, dry_tol=1e-3), q0, B0, dx, dt, q1, np.random.default_rng(79), "level 0")
+
+
+@pytest.fixture(scope="module")
+def ensemble_full(mlswe_lib):
+    """The ensemble workload as the benchmark builds it: 256 members, coarse U{128..512}^2,
+    seeded shelves and humps, one refined level (ratio 4, seeded patches)."""
+    r = 4
+    members = [I.ensemble_member(k) for k in range(256)]
+    cfg = mlswe_lib.Config(M=2, dry_tol=1e-3, max_levels=2, ratio=[r], regrid_interval=0, min_side=16,
+                           max_side=64)
+    H = mlswe_lib.Hierarchy(cfg, [(0.0, 0.0, m["L"], m["L"], m["n"], m["n"]) for m in members])
+    for k, m in enumerate(members):
+        nf = m["n"] * r
+        xf = I.centers(0.0, m["L"], nf)
+        H.set_bathymetry(k, np.ascontiguousarray(np.broadcast_to(
+            I.shelf_B(xf, depth=m["depth"], shelf_x=m["shelf_x"])[None, :], (nf, nf))))
+        B0 = H.get_bathymetry(k, 0)
+        x0 = I.centers(0.0, m["L"], m["n"])
+        X, Y = np.meshgrid(x0, x0)
+        H.set_state(k, 0, I.layered_state(B0, I.hump_field(X, Y, *m["humps"]), -200.0 * np.ones_like(B0)))
+        H.set_patches(k, 1, I.random_layout(5100 + k, m["n"] * r, m["n"] * r, max(4, m["n"] // 16), r))
+        H.interp_fine(0, k)
+    for lev in range(2):
+        H.autotune(lev, iters=2)
+    H.advance(1)
+    yield H, members, r
+    H.close()
+
+
+def test_ensemble_sampled_members_match_oracle(ensemble_full):
+    """One step of every member's level 0 (each with its own dt, one launch) and then of
+    every member's refined level: sampled members' level 0 against the oracle's walled step,
+    sampled patches of two members against the oracle's patch step."""
+    H, members, r = ensemble_full
+    dx0 = np.array([m["L"] / m["n"] for m in members])
+    c = np.sqrt(9.81 * np.array([m["depth"] for m in members]))
+    dt0 = 0.45 * dx0 / c
+    P = O.params(M=2, dry_tol=1e-3)
+    ns = [m["n"] for m in members]
+    sample = [int(np.argmin(ns)), int(np.argmax(ns)), 97]
+    q0 = {k: H.get_state(k, 0) for k in sample}
+    H.step_level(0, dt=dt0)
+    rng0 = np.random.default_rng(80)
+    for k in sample:
+        _check_walled_step(P, q0[k], H.get_bathymetry(k, 0), dx0[k], dt0[k], H.get_state(k, 0), rng0, k)
+    # the refined level, from rings filled at the level-0 state just reached
+    H.fill_ghosts(1, 1.0)
+    rng = np.random.default_rng(78)
+    before = {}
+    for k in (sample[1], 5):
+        nf = members[k]["n"] * r
+        qa = H.get_state(k, 1)
+        boxes = [b for b in H.get_patches(k, 1).tolist()
+                 if b[0] >= NG and b[1] >= NG and b[2] <= nf - NG and b[3] <= nf - NG]
+        picks = rng.choice(len(boxes), min(2, len(boxes)), replace=False)
+        before[k] = (qa, [(boxes[i], np.ascontiguousarray(qa[:, boxes[i][1] - NG:boxes[i][3] + NG,
+                                                             boxes[i][0] - NG:boxes[i][2] + NG])) for i in picks])
+    H.step_level(1, dt=dt0 / r)
+    for k, (qa, inputs) in before.items():
+        nf = members[k]["n"] * r
+        qb = H.get_state(k, 1)
+        Bf = H.get_bathymetry(k, 1)
+        scale = np.maximum(np.abs(qa).max(axis=(1, 2)), np.abs(qb).max(axis=(1, 2)))
+        dxf = members[k]["L"] / nf
+        for (i0, j0, i1, j1), qp in inputs:
+            Bp = np.ascontiguousarray(Bf[j0 - NG:j1 + NG, i0 - NG:i1 + NG])
+            pert = np.ascontiguousarray(qp * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=qp.shape)))
+            O.step_patch(P, qp, Bp, dxf, dxf, dt0[k] / r)
+            O.step_patch(P, pert, Bp, dxf, dxf, dt0[k] / r)
+            want = qp[:, NG:-NG, NG:-NG]
+            err = np.abs(qb[:, j0:j1, i0:i1] - want).max(axis=(1, 2)) / scale
+            sens = np.abs(pert[:, NG:-NG, NG:-NG] - want).max(axis=(1, 2)) / scale
+            assert err[[0, 3]].max() <= TOL, (k, (i0, j0, i1, j1), err)
+            assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (k, (i0, j0, i1, j1), err, sens)
