@@ -5,7 +5,8 @@ oracle can follow it: a level-2 step of sampled patches (the most active and som
 random) against the oracle's patch step on the same ghost-filled input, and the whole
 level-0 step against the oracle's walled step; and the ensemble workload (256 members) on
 sampled members and patches. Within 1e-11 of each field's level-wide scale (near-rest
-momenta in deep water: within 10x the oracle's own one-ulp sensitivity)."""
+momenta in deep water: within 10x the oracle's own one-ulp sensitivity). The adjoint
+workload at full size: its gradient against central differences of the GPU forward."""
 import numpy as np
 import pytest
 
@@ -182,3 +183,38 @@ def test_ensemble_sampled_members_match_oracle(ensemble_full):
             sens = np.abs(pert[:, NG:-NG, NG:-NG] - want).max(axis=(1, 2)) / scale
             assert err[[0, 3]].max() <= TOL, (k, (i0, j0, i1, j1), err)
             assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (k, (i0, j0, i1, j1), err, sens)
+
+
+def test_adjoint_full_size_gradient_matches_central_fd(mlswe_lib):
+    """The adjoint workload as the benchmark runs it (512^2, 200 first-order steps, 32
+    gauges, checkpoints every 20, per-edge forward records kept): the gradient with respect
+    to eta_1 and B along six seeded directions mixing both controls against central
+    differences of the GPU forward loss."""
+    import torch
+    from paper_1803_01450_gb300.adjoint import FixedGridProblem, gauge_misfit
+    n, steps, ckpt, n_g, L = 512, 200, 20, 32, 1e5
+    B = I.adjoint_bathymetry(n, L)
+    eta1 = I.adjoint_eta1(n, seed=4000, L=L)
+    gauges = I.gauge_cells(n, n_g, seed=4100)
+    dt = 0.5 * (L / n) / 205.0
+    prob = FixedGridProblem(n, n, L, dt, steps, ckpt, gauges, np.zeros((steps, n_g)))
+    dev = torch.device("cuda", 0)
+    e = torch.tensor(eta1, dtype=torch.float64, device=dev, requires_grad=True)
+    Bt = torch.tensor(B, dtype=torch.float64, device=dev, requires_grad=True)
+    loss = gauge_misfit(e, Bt, prob)
+    loss.backward()
+    ge, gB = e.grad.cpu().numpy(), Bt.grad.cpu().numpy()
+    assert np.abs(ge).max() > 0 and np.abs(gB).max() > 0
+    rng = np.random.default_rng(10)
+    x_norm = np.sqrt(np.sum(eta1 ** 2) + np.sum(B ** 2))
+    for _ in range(6):
+        de = rng.standard_normal(ge.shape)
+        dB = rng.standard_normal(gB.shape)
+        d_norm = np.sqrt(np.sum(de ** 2) + np.sum(dB ** 2))
+        eps = 1e-6 * x_norm / d_norm
+        Jp = prob.forward(eta1 + eps * de, B + eps * dB)
+        Jm = prob.forward(eta1 - eps * de, B - eps * dB)
+        fd = (Jp - Jm) / (2 * eps)
+        ad = float(np.sum(ge * de) + np.sum(gB * dB))
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
+    prob.close()
