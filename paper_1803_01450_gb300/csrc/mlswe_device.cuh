@@ -526,8 +526,8 @@ __device__ __forceinline__ void coupling_matrix(const DevParams& P, const double
     for (int n = 0; n < M; ++n) G[m][n] = P.g * hb[m] * (n >= m ? 1.0 : density_ratio<M>(P, n, m));
 }
 
-template <int M>
-__device__ __forceinline__ void coupled_general(const DevParams& P, const double* cL, const double* cR,
+template <int M, class CRec>
+__device__ __forceinline__ void coupled_general(const DevParams& P, const CRec cL, const CRec cR,
                                                 const double* hb, const double* d0, const double* d1,
                                                 const double* d2, EdgeW<M>& W, int& lost) {
   static_assert(M == 3, "general coupled branch written for three layers");
@@ -581,12 +581,21 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const double
   }
 }
 
-// Riemann solve at one edge. cL, cR: cell records; wL, wR: wet bits (bit m = layer m).
+// A cell record read in place from the tile's shared-memory records (field f at
+// p[f * kMaxCells]): fields are loaded where the solver uses them instead of all up front,
+// which keeps fewer values live in registers.
+struct SmemRec {
+  const double* p;
+  __device__ __forceinline__ double operator[](int f) const { return p[f * kMaxCells]; }
+};
+
+// Riemann solve at one edge. cL, cR: cell records (arrays or SmemRec views); wL, wR: wet
+// bits (bit m = layer m).
 // STORE: a coupled two-layer edge also writes its FwdRec record to st (field k at
 // st[k * sstride]). The stores are unconditional (st must be valid), so the arithmetic is
 // compiled in the same basic blocks, and therefore rounds the same, as without STORE.
-template <int M, bool STORE = false>
-__device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL, const double* cR,
+template <int M, bool STORE = false, class CRec = const double*>
+__device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, const CRec cR,
                                            int wL, int wR, EdgeW<M>& W, int& lost, double* st = nullptr,
                                            long long sstride = 0) {
   auto put = [&](int k, double v) {
@@ -781,8 +790,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const double* cL,
       split_single<M>(m, pa, pb, d0[m], d1[m], d2[m], uh - ch, uh + ch, vh, uh, W, 0.5 * tc);
       W.hbt[m] = hb[m];
     } else if (wl || wr) {
-      const double* cw = wl ? cL : cR;
-      const double* cd = wl ? cR : cL;
+      const CRec cw = wl ? cL : cR;
+      const CRec cd = wl ? cR : cL;
       const double bhat_d = (m == M - 1) ? cd[R::BB] : cd[R::ETA + m + 1];
       if (cw[R::ETA + m] < bhat_d) {
         // Wall for this layer: mirror of the wet side, coupling dropped.

@@ -234,9 +234,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       if (DIR == 0) { l = tt / (len + 3); e = tt - l * (len + 3); }
       else { e = tt / nl; l = tt - e * nl; }
       const int cl = sb[0][g] + cslot<DIR>(l, e, len, nl), cr = sb[0][g] + cslot<DIR>(l, e + 1, len, nl);
-      double cL[R::N], cR[R::N];
-#pragma unroll
-      for (int f = 0; f < R::N; ++f) { cL[f] = cell[f * kMaxCells + cl]; cR[f] = cell[f * kMaxCells + cr]; }
+      const SmemRec cL{cell + cl}, cR{cell + cr};
       EdgeW<M> W;
       int lst = 0;
       // halo edges write their record to the spare last slot of each plane
@@ -247,7 +245,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
           st = DIR == 0 ? est + (size_t)(item.j0 + l) * (NX + 1) + (item.i0 - 1 + e)
                         : est + (size_t)(item.j0 - 1 + e) * NX + (item.i0 + l);
       }
-      solve_edge<M, STORE>(P, cL, cR, wetb[cl], wetb[cr], W, lst, st, eplane);
+      solve_edge<M, STORE, SmemRec>(P, cL, cR, wetb[cl], wetb[cr], W, lst, st, eplane);
       const int es = sb[1][g] + eslot<DIR>(l, e, len, nl);
 #pragma unroll
       for (int p = 0; p < 2 * M; ++p) {
