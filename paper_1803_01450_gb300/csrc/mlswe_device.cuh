@@ -441,6 +441,64 @@ __device__ __forceinline__ void gauss_solve(double (&A)[N][N], double (&b)[N], d
   }
 }
 
+// The same elimination for R right-hand sides at once (rows b[r]): the pivots depend on A
+// only, so each right-hand side goes through exactly the operations of gauss_solve alone,
+// while A is eliminated once.
+template <int N, int R, int K>
+__device__ __forceinline__ void gauss_step_multi(double (&A)[N][N], double (&b)[R][N]) {
+  if constexpr (K < N) {
+    int piv = K;
+    unsigned long long best = abs_bits(A[K][K]);
+#pragma unroll
+    for (int i = K + 1; i < N; ++i) {
+      const unsigned long long v = abs_bits(A[i][K]);
+      if (v > best) { best = v; piv = i; }
+    }
+#pragma unroll
+    for (int i = K + 1; i < N; ++i) {
+      const bool sw = i == piv;
+#pragma unroll
+      for (int j = K; j < N; ++j) {
+        const double t = A[K][j];
+        A[K][j] = sw ? A[i][j] : t;
+        A[i][j] = sw ? t : A[i][j];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const double tb = b[r][K];
+        b[r][K] = sw ? b[r][i] : tb;
+        b[r][i] = sw ? tb : b[r][i];
+      }
+    }
+    const double ip = rcp_fast(A[K][K]);
+#pragma unroll
+    for (int i = K + 1; i < N; ++i) {
+      const double f = A[i][K] * ip;
+#pragma unroll
+      for (int j = K + 1; j < N; ++j) A[i][j] = fma(-f, A[K][j], A[i][j]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) b[r][i] = fma(-f, b[r][K], b[r][i]);
+    }
+    gauss_step_multi<N, R, K + 1>(A, b);
+  }
+}
+
+template <int N, int R>
+__device__ __forceinline__ void gauss_solve_multi(double (&A)[N][N], double (&b)[R][N], double (&x)[R][N]) {
+  gauss_step_multi<N, R, 0>(A, b);
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    const double id = rcp_fast(A[k][k]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      double sum = b[r][k];
+#pragma unroll
+      for (int j = k + 1; j < N; ++j) sum = fma(-A[k][j], x[r][j], sum);
+      x[r][k] = sum * id;
+    }
+  }
+}
+
 // Coupled branch for M = 3 layers. The eigenvalues of the normal system at the Roe state are
 // the roots of P(l) = det(A(l)), A(l) = diag((l - u_m)^2) - G, G_mn = g hbar_m C_mn with
 // C_mn = 1 for n >= m and rho_n / rho_m for the lighter layers n < m. Guesses: the roots for
@@ -977,6 +1035,21 @@ __device__ __forceinline__ void trans_apply_general(const DevParams& P, const do
   double G[M][M], lam[N], dh[N][M];
   coupling_matrix<M>(P, hb, G);
   general_eig<M>(P, G, ut, hb, muk, lam, dh);
+  // one elimination of the eigenvector matrix for the strengths of both fluctuations
+  double Rm[N][N], rhs[2][N], beta[2][N];
+#pragma unroll
+  for (int p = 0; p < N; ++p)
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      Rm[2 * m][p] = dh[p][m];
+      Rm[2 * m + 1][p] = lam[p] * dh[p][m];
+    }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    rhs[0][2 * m] = dqa[3 * m]; rhs[0][2 * m + 1] = dqa[3 * m + 2];
+    rhs[1][2 * m] = dqb[3 * m]; rhs[1][2 * m + 1] = dqb[3 * m + 2];
+  }
+  gauss_solve_multi<N, 2>(Rm, rhs, beta);
 #pragma unroll
   for (int v = 0; v < 2; ++v) {
     const double* dq = v == 0 ? dqa : dqb;
@@ -984,30 +1057,13 @@ __device__ __forceinline__ void trans_apply_general(const DevParams& P, const do
     double* dn = v == 0 ? dna : dnb;
 #pragma unroll
     for (int f = 0; f < 3 * M; ++f) { up[f] = 0.0; dn[f] = 0.0; }
-    double Rm[N][N], rhs[N], beta[N];
 #pragma unroll
     for (int p = 0; p < N; ++p)
 #pragma unroll
-      for (int m = 0; m < M; ++m) {
-        Rm[2 * m][p] = dh[p][m];
-        Rm[2 * m + 1][p] = lam[p] * dh[p][m];
-      }
-#pragma unroll
-    for (int m = 0; m < M; ++m) { rhs[2 * m] = dq[3 * m]; rhs[2 * m + 1] = dq[3 * m + 2]; }
-    gauss_solve<N>(Rm, rhs, beta);
-#pragma unroll
-    for (int p = 0; p < N; ++p)
-#pragma unroll
-      for (int m = 0; m < M; ++m) trans_send(lam[p], beta[p] * dh[p][m], un[m], up, dn, 3 * m);
+      for (int m = 0; m < M; ++m) trans_send(lam[p], beta[v][p] * dh[p][m], un[m], up, dn, 3 * m);
 #pragma unroll
     for (int m = 0; m < M; ++m) trans_shear(ut[m], dq[3 * m + 1] - un[m] * dq[3 * m], up, dn, 3 * m + 1);
   }
-}
-
-__device__ __forceinline__ double limiter_phi(int kind, double th) {
-  if (kind == 0) return 1.0;
-  if (kind == 1) return fmax(0.0, fmin(1.0, th));
-  return fmax(0.0, fmin(fmin(0.5 * (1.0 + th), 2.0), 2.0 * th));
 }
 
 }  // namespace mlswe
