@@ -34,6 +34,8 @@ def mc(tmp_path_factory):
     L.mc_run.restype = ctypes.c_int
     L.mc_left_share.argtypes = [dp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, dp]
     L.mc_left_share.restype = ctypes.c_int
+    L.mc_solve.argtypes = [dp, ctypes.c_int, dp]
+    L.mc_solve.restype = ctypes.c_int
     return L
 
 
@@ -150,3 +152,26 @@ def test_left_share_matches_the_written_out_correction(mc):
             ref = base + (0.5 if sc[k] > 0 else -0.5) * (1.0 - nu[k] * abs(s[k])) * _phi(kind[k], t)
         # a few roundings apart (the kernel fuses; the written-out form rounds each step)
         assert abs(out[k] - ref) <= 1e-15 * max(1.0, abs(ref)), (k, kind[k], sc[k], act[k], out[k], ref)
+
+
+def test_elimination_for_two_right_hand_sides_equals_two_solves(mc):
+    """The transverse solve of three layers eliminates the eigenvector matrix once for both
+    fluctuations: the same pivots and operations per right-hand side as two separate solves,
+    so the same bits; and the solution solves the system (against numpy)."""
+    rng = np.random.default_rng(14)
+    n = 4000
+    A = rng.standard_normal((n, 6, 6))
+    A[: n // 4] *= np.exp2(rng.integers(-20, 20, (n // 4, 6, 1)))  # badly scaled rows: pivoting
+    A[n // 4: n // 2, :, 0] *= 1e-9  # small leading column: row exchanges
+    b = rng.standard_normal((n, 2, 6))
+    inp = np.ascontiguousarray(np.concatenate([A.reshape(n, 36), b.reshape(n, 12)], axis=1))
+    out = np.zeros((n, 24))
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert mc.mc_solve(inp.ctypes.data_as(dp), n, out.ctypes.data_as(dp)) == 0
+    single, multi = out[:, :12], out[:, 12:]
+    assert np.array_equal(single.view(np.int64), multi.view(np.int64))
+    x = np.linalg.solve(A, b.transpose(0, 2, 1)).transpose(0, 2, 1).reshape(n, 12)
+    cond = np.linalg.cond(A)
+    ok = cond < 1e8
+    err = np.abs(single - x).max(axis=1) / np.maximum(np.abs(x).max(axis=1), 1e-300)
+    assert (err[ok] <= 1e-15 * cond[ok] * 100).all()
