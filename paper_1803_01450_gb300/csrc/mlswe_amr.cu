@@ -141,12 +141,12 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
   return cudaGetLastError();
 }
 
-// Ghost fill (mode 1 of the refinement above) organised per coarse cell: the thread of a
-// coarse cell under a ghost strip loads it and its four face neighbours once, forms the
-// wet flags, surfaces and minmod slopes of every layer once, and then reconstructs each of
-// its r x r fine cells that lies in the strip and in no patch of the fine level (the
-// per-fine-cell form recomputes all of that for every fine cell). Same formulas per fine
-// cell as interp_kernel.
+// Ghost fill (the refinement above applied to the ring cells of the patches) organised per
+// coarse cell: the thread of a coarse cell under a ghost strip loads it and its four face
+// neighbours once, forms the wet flags, surfaces and minmod slopes of every layer once, and
+// then reconstructs each of its r x r fine cells that lies in the strip and in no patch of
+// the fine level (the per-fine-cell form recomputes all of that for every fine cell). Same
+// formulas per fine cell as interp_kernel.
 template <int M>
 __global__ void __launch_bounds__(256)
 ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const GhostCell* __restrict__ cells,
