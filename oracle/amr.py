@@ -120,6 +120,13 @@ class OracleAMR:
         m = fine_mask[box[1] * r:box[3] * r, box[0] * r:box[2] * r]
         sub[:, m] = vals[:, m]
 
+    def coarse_state_at(self, l, alpha):
+        """State of level l at fraction alpha in [0, 1] of its last step: linear in time
+        between the states before (q_old) and after (q) that step, the coarse values the
+        ghost cells of the finer level refine from at each of its substeps."""
+        V = self.lev[l]
+        return (1.0 - alpha) * V.q_old + alpha * V.q
+
     def patch_array(self, l, box, alpha):
         """Patch array [F][h+4][w+4] of level l with its ghost ring: patch and sibling cells
         from the level, other in-domain cells by refinement of the coarse state interpolated
@@ -134,8 +141,7 @@ class OracleAMR:
         if l > 0:
             inside = V.in_patch_mask()[sj0:sj1, si0:si1]
             if not inside.all():
-                Cl = self.lev[l - 1]
-                qc = (1.0 - alpha) * Cl.q_old + alpha * Cl.q
+                qc = self.coarse_state_at(l - 1, alpha)
                 r = self.r[l - 1]
                 box_c = (si0 // r, sj0 // r, -(-si1 // r), -(-sj1 // r))
                 vals = self.interp_box(l - 1, qc, box_c)
@@ -268,13 +274,18 @@ class OracleAMR:
         need = math.ceil((dt_parent * self.rates[l]) / self.cfl)
         return min(r, max(1, need))
 
+    def substep_fraction(self, l, s, rt):
+        """Time of the start of substep s of level l as a fraction of its parent's step,
+        when the parent step is taken in rt equal substeps (Sec. 2, time refinement)."""
+        return s / rt
+
     def advance_level(self, l, dt, alpha):
         self.step_level(l, dt, alpha)
         self.level_steps[l] += 1
         if l + 1 < self.L and self.lev[l + 1].patches:
             rt = self.time_ratio(l + 1, dt)
             for s in range(rt):
-                self.advance_level(l + 1, dt / rt, s / rt)
+                self.advance_level(l + 1, dt / rt, self.substep_fraction(l + 1, s, rt))
             self.average_down(l)
             self.reflux(l, dt)
 
