@@ -621,7 +621,7 @@ def run_gpu(args):
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, N_CELLS, N_CELLS)], stream=stream.cuda_stream)
     H.set_bathymetry(0, w["B"])
     H.set_state(0, 0, w["q"])
-    tiles = H.autotune(0, iters=3)
+    tiles = "default 125 x 2, 2 CTAs per SM" if args.no_autotune else H.autotune(0, iters=3)
     dt = 0.9 * w["dx"] / 205.0
     H.set_dt(0, dt)
     for _ in range(args.warmup):
@@ -732,6 +732,8 @@ def main():
     ap.add_argument("--impl", default="mlswe", choices=["mlswe", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="headline sweeps with the default tiles (no tile trials before the timed steps)")
     ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "dynrt", "unsplit"],
                     help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()

@@ -55,7 +55,7 @@ class Level:
 
 class OracleAMR:
     def __init__(self, P, domain, nx0, ny0, max_levels, ratios, B_finest, flag_tol=1e-3, n_buf=2,
-                 cluster_eff=0.7, min_side=16, max_side=64, cfl=0.9, n_nest=2, dynamic_rt=False):
+                 cluster_eff=0.7, min_side=16, max_side=64, cfl=0.9, n_nest=2, dynamic_rt=False, cfl_max=1.0):
         self.P = P
         self.dynamic_rt = dynamic_rt
         self.M = P.M
@@ -65,6 +65,7 @@ class OracleAMR:
         self.r = list(ratios)
         self.flag_tol, self.n_buf, self.eff = flag_tol, n_buf, cluster_eff
         self.min_side, self.max_side, self.cfl, self.n_nest = min_side, max_side, cfl, n_nest
+        self.cfl_max = cfl_max
         self.lev = []
         nx, ny = nx0, ny0
         for l in range(max_levels):
@@ -85,6 +86,11 @@ class OracleAMR:
         self.rates = [0.0] * max_levels   # largest speed / cell size per level, for the next step
         self.fresh = False                # this coarse step follows a regrid: fixed ratios
         self.level_steps = [0] * max_levels
+        self.level_dt = [0.0] * max_levels  # step of each level in the last coarse step
+        self.rejected = 0                     # coarse-step attempts rejected (Courant > cfl_max)
+        self.rejected_smax = None             # wave speeds measured by the last rejected attempt
+        self.history = []                     # (Courant number, kept) of every automatic attempt
+        self.cfl_failed = False               # a member gave up after the retry budget
 
     # ------------------------------------------------------------------ helpers
     def set_state(self, level, q):
@@ -282,6 +288,7 @@ class OracleAMR:
     def advance_level(self, l, dt, alpha):
         self.step_level(l, dt, alpha)
         self.level_steps[l] += 1
+        self.level_dt[l] = dt
         if l + 1 < self.L and self.lev[l + 1].patches:
             rt = self.time_ratio(l + 1, dt)
             for s in range(rt):
@@ -330,18 +337,51 @@ class OracleAMR:
                 best = min(best, fac / rate)
         return self.cfl * best
 
+    def courant(self):
+        """Courant number of the last coarse step: the largest over the levels of the level's
+        step times its largest wave speed per cell size, max(sx * (1/dx), sy * (1/dy))."""
+        c = 0.0
+        for l, V in enumerate(self.lev):
+            c = max(c, self.level_dt[l] * max(self.smax[l][0] * (1.0 / V.dx), self.smax[l][1] * (1.0 / V.dy)))
+        return c
+
     def advance(self, n_coarse_steps, regrid_interval=0, dt=None):
+        """n accepted coarse steps. With automatic time steps (dt None) an attempt whose
+        Courant number exceeds cfl_max is rejected: every level returns to its state before
+        the attempt and the step is retaken in the next round with the time step the usual
+        rule gives from the wave speeds that attempt measured (dt * cfl / Courant number for
+        the level that bounds it). Regrids happen at the start of rounds k < n with
+        k % regrid_interval == 0; the rounds after the first n (retakes only) never regrid.
+        After n + 8 extra rounds the run gives up (cfl_failed)."""
         self._alloc_flux()
-        for k in range(n_coarse_steps):
-            if regrid_interval and k % regrid_interval == 0 and self.L > 1:
+        done, k = 0, 0
+        while done < n_coarse_steps:
+            if k >= 2 * n_coarse_steps + 8:
+                self.cfl_failed = True
+                return
+            if k < n_coarse_steps and regrid_interval and k % regrid_interval == 0 and self.L > 1:
                 self.regrid(0)
                 self.fresh = True  # the last speeds were measured on the old patches
             step_dt = dt if dt is not None else (self.initial_dt() if self.dt is None else self.next_dt())
             self.smax = [np.zeros(2) for _ in range(self.L)]
+            self.level_dt = [0.0] * self.L
+            saved = [V.q.copy() for V in self.lev] if dt is None else None
             self.advance_level(0, step_dt, 0.0)
             self.fresh = False
             self.dt = step_dt
+            k += 1
+            if dt is None:
+                c = self.courant()
+                kept = not (c > self.cfl_max)
+                self.history.append((c, kept))
+                if not kept:
+                    for V, q in zip(self.lev, saved):
+                        V.q = q
+                    self.rejected += 1
+                    self.rejected_smax = [s.copy() for s in self.smax]
+                    continue
             self.t += step_dt
+            done += 1
 
     # ------------------------------------------------------------------ regrid
     def flags(self, l):
