@@ -46,7 +46,8 @@ typedef enum {
   MLSWE_EINVAL = 1,     /* bad argument (sizes, indices, null pointers, unsupported option) */
   MLSWE_ENOMEM = 2,     /* device or host allocation failed */
   MLSWE_ECUDA = 3,      /* a CUDA call failed; text in mlswe_last_error */
-  MLSWE_ECFL = 4,       /* a step ran with Courant number above cfl_max (the step is kept) */
+  MLSWE_ECFL = 4,       /* Courant number above cfl_max: mlswe_step_level undid the level step;
+                           mlswe_advance spent its retake budget (see there) */
   MLSWE_ENEGDEPTH = 5,  /* a non-finite value was met in the wave-speed reduction */
   MLSWE_ENESTING = 6,   /* a patch layout violates nesting or overlaps */
   MLSWE_ETIMEOUT = 7,   /* reserved: a bounded device wait gave up */
@@ -72,7 +73,8 @@ typedef struct {
  *  g            gravity; dry_tol: layer m is wet where h_m > dry_tol and every
  *               layer above is wet (top-down rule, Sec. 2.1).
  *  cfl_desired  target Courant number for the automatic time step;
- *  cfl_max      steps above it report MLSWE_ECFL.
+ *  cfl_max      a coarse step of mlswe_advance above it is rejected and retaken; a level
+ *               step of mlswe_step_level above it (with a Courant report) is undone.
  *  order        1 or 2 (second-order wave correction); limiter 0 none,
  *               1 minmod, 2 MC; eigen 0: eigenvalue guesses + 2 Newton steps,
  *               1: guesses only.
@@ -186,7 +188,10 @@ mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt);
  * every member with the time step set by mlswe_set_dt (or, if dt is not
  * NULL, with dt host [n_members]). Ghost cells of patches on level >= 1 must
  * have been filled (mlswe_fill_ghosts). cfl_out (host [n_members], may be
- * NULL) receives the Courant number of the step: dt * max(sx/dx, sy/dy). */
+ * NULL) receives the Courant number of the step: dt * max(sx/dx, sy/dy); when
+ * some member's exceeds cfl_max the step is undone for every member (the level's
+ * state is the one before the call) and MLSWE_ECFL is returned, so the caller can
+ * retry with a smaller dt. Without cfl_out nothing is checked. */
 mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cfl_out);
 
 /* Fills the ghost ring (2 cells) of every patch of `level` >= 1 that is not
@@ -216,7 +221,20 @@ mlswe_status mlswe_regrid(mlswe_h h, int base_level);
 /* Advances every member by n_coarse_steps level-0 steps of the subcycled
  * Berger-Oliger scheme (r_t = ratio), with automatic time steps (cfl_desired),
  * averaging and mass reflux at coarse/fine interfaces, and a regrid every
- * regrid_interval coarse steps. */
+ * regrid_interval coarse steps.
+ * Courant control (Sec. 2 keeps every level's Courant number below one through
+ * r_t): the Courant number of a coarse-step attempt is the largest over the levels
+ * of dt_l * max(sx/dx_l, sy/dy_l). An attempt above cfl_max is rejected: every level
+ * of that member returns to its state before the attempt (the refined levels' patch
+ * cells are copied aside before each attempt, in one buffer per refined level and
+ * member allocated at the first call) and its time does not advance; the next round
+ * retakes the step with the time step the usual rule gives from the wave speeds the
+ * rejected attempt measured (dt * cfl_desired / Courant number for the bounding
+ * level). The call runs n_coarse_steps rounds (regrids at the rounds the interval
+ * selects), then retake rounds without regrids, in which only members short of
+ * n_coarse_steps kept steps take a step, until every member has them; after
+ * n_coarse_steps + 8 retake rounds it returns MLSWE_ECFL (the members keep their
+ * last kept state). Rejections are counted in mlswe_stats.cfl_exceeded. */
 mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps);
 
 /* Simulated time of every member (t_out, host [n_members]) and the level-0 time
@@ -256,8 +274,11 @@ mlswe_status mlswe_synchronize(mlswe_h h);
  * level l times those steps, summed over members (multiply by M for
  * layer-cell updates); patches[l]: current patch count of level l over
  * members; regrids: regrids run; coarse_steps: coarse steps of mlswe_advance;
- * cfl_exceeded: member coarse steps whose Courant number exceeded cfl_max;
- * last_cfl: largest Courant number of the last coarse step over the members.
+ * cfl_exceeded: member coarse-step attempts rejected because their Courant number
+ * exceeded cfl_max (each was retaken); last_cfl: largest Courant number of the last
+ * coarse-step attempt over the members. level_steps and cell_updates include the
+ * steps of rejected attempts (work the GPU did); coarse_steps counts the rounds of
+ * mlswe_advance that can regrid (not the retake rounds).
  * Levels beyond max_levels read 0. Synchronises the stream. */
 typedef struct {
   long long coarse_steps;

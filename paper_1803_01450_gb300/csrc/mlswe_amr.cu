@@ -551,7 +551,9 @@ __global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const u
                                 int* init_flag, double* dt) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   const bool initial = *init_flag != 0;
-  if (m < A.n_members) {
+  // A member that sits the round out (its coarse steps are all kept) keeps its time step,
+  // wave speeds and counters untouched.
+  if (m < A.n_members && A.active[m * A.L] != 0) {
     double best = INFINITY, fac = 1.0;
     double rate[4] = {0.0, 0.0, 0.0, 0.0};
     for (int l = 0; l < A.L; ++l) {
@@ -595,12 +597,23 @@ __global__ void dt_begin_kernel(DtArgs A, unsigned long long* smax_bits, const u
   }
 }
 
-// End of a coarse step: Courant number reached by every member (status bit 0 when
-// above cfl_max, bit 1 when a wave speed was not finite) and the member's time.
+// End of a coarse-step attempt: Courant number reached by every member, the largest over
+// its levels of dt_l max(sx/dx_l, sy/dy_l). Above cfl_max the attempt is rejected (Sec. 2:
+// the time refinement exists to keep each level's Courant number below one): redo is set,
+// the member's time does not advance, and the snapshot kernel that follows restores its
+// state; the next round retakes the step with the time step dt_begin derives from the speeds
+// this attempt measured. Status bit 1 when a wave speed was not finite.
 __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, const double* dt, double* t_member,
                                 double* cfl_reached, unsigned int* status, unsigned long long* cfl_count) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m == 0) *A.fresh = 0;
   if (m >= A.n_members) return;
+  const bool took = A.active[m * A.L] != 0;
+  for (int l = 1; l < A.L; ++l) A.active[m * A.L + l] = 1;  // steps outside advance take every level
+  if (!took) {
+    A.redo[m] = 0;
+    return;
+  }
   double reached = 0.0;
   bool bad = false;
   for (int l = 0; l < A.L; ++l) {
@@ -611,14 +624,51 @@ __global__ void step_end_kernel(DtArgs A, const unsigned long long* smax_bits, c
     reached = fmax(reached, dt[d] * fmax(sx * A.inv_dx[d], sy * A.inv_dy[d]));
   }
   cfl_reached[m] = reached;
-  if (reached > A.cfl_max) {
-    atomicOr(status, 1u);
-    atomicAdd(cfl_count, 1ull);
-  }
   if (bad) atomicOr(status, 2u);
+  if (reached > A.cfl_max) {
+    A.redo[m] = 1;
+    atomicAdd(cfl_count, 1ull);
+    return;
+  }
+  A.redo[m] = 0;
+  A.done[m] += 1;
   t_member[m] += dt[m * A.L];
-  for (int l = 1; l < A.L; ++l) A.active[m * A.L + l] = 1;  // steps outside advance take every level
-  if (m == 0) *A.fresh = 0;
+}
+
+// Courant control (see launch_snapshot): one block per patch chunk, F fields of its cells.
+__global__ void __launch_bounds__(256)
+snapshot_kernel(int F, int L, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+                const int* __restrict__ n_items_dev, int mode, ParSet par, const int* __restrict__ redo) {
+  const int n_items = *n_items_dev;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const InterpItem item = items[it];
+    const int d = item.desc_c, l = d % L, m = d / L;
+    const LevelDesc& D = descs[d];
+    const double* __restrict__ src;
+    double* __restrict__ dst;
+    if (mode == 0) {
+      if (l == 0) continue;  // level 0 keeps its state before the step in its other buffer
+      src = D.q[par.start[l]];
+      dst = D.snap;
+    } else {
+      if (redo[m] == 0) continue;
+      src = l == 0 ? D.q[par.start[0]] : D.snap;
+      dst = D.q[par.next[l]];
+    }
+    const int w = item.i1 - item.i0, n = w * (item.j1 - item.j0);
+    const size_t plane = (size_t)D.NY * D.P;
+    for (int t = threadIdx.x; t < n * F; t += blockDim.x) {
+      const int f = t / n, c = t - f * n, j = c / w, i = c - j * w;
+      const size_t o = (size_t)f * plane + (size_t)(item.j0 + j) * D.P + (item.i0 + i);
+      dst[o] = src[o];
+    }
+  }
+}
+
+cudaError_t launch_snapshot(int F, int L, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
+                            int grid, int mode, const ParSet& par, const int* redo, cudaStream_t st) {
+  snapshot_kernel<<<grid, 256, 0, st>>>(F, L, descs, items, n_items_dev, mode, par, redo);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,

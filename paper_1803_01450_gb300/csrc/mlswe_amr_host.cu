@@ -320,19 +320,37 @@ static DtArgs dt_args(Hier* H) {
   A.cells = H->d_cells;
   A.steps_acc = H->d_steps_acc;
   A.cells_acc = H->d_cells_acc;
+  A.redo = H->d_redo;
+  A.done = H->d_done;
   return A;
 }
 
-// One coarse step: time step on the device, the level tree, the Courant check.
+// One coarse-step attempt: time step on the device, a snapshot of the refined levels' patch
+// cells, the level tree, the Courant check, and the restore of the members whose attempt
+// was rejected (their next round retakes the step).
 static mlswe_status enqueue_coarse_step(Hier* H) {
   int tok;
+  ParSet ps{};
+  for (int l = 0; l < H->L; ++l) ps.start[l] = H->parity[l];
   timer_begin(H, KC_OTHER, &tok);
   CUDA_TRY(H, launch_dt_begin(dt_args(H), H->d_smax, H->d_init, H->d_init_flag, H->d_dt, H->st));
   timer_end(H, tok);
+  const int F = 3 * H->cfg.M;
+  if (H->L > 1) {
+    timer_begin(H, KC_OTHER, &tok);
+    CUDA_TRY(H, launch_snapshot(F, H->L, H->d_desc, H->t_speed.d, H->t_speed.d_count, grid_full(H), 0, ps,
+                                H->d_redo, H->st));
+    timer_end(H, tok);
+  }
   mlswe_status s = enqueue_level_tree(H, 0, 0);
   if (s != MLSWE_OK) return s;
+  for (int l = 0; l < H->L; ++l) ps.next[l] = H->parity[l];
   timer_begin(H, KC_OTHER, &tok);
   CUDA_TRY(H, launch_step_end(dt_args(H), H->d_smax, H->d_dt, H->d_t, H->d_cfl, H->d_status, H->d_cfl_count,
+                              H->st));
+  timer_end(H, tok);
+  timer_begin(H, KC_OTHER, &tok);
+  CUDA_TRY(H, launch_snapshot(F, H->L, H->d_desc, H->t_speed.d, H->t_speed.d_count, grid_full(H), 1, ps, H->d_redo,
                               H->st));
   timer_end(H, tok);
   return MLSWE_OK;
@@ -581,12 +599,32 @@ mlswe_status mlswe_regrid(mlswe_h h, int base_level) {
   return MLSWE_OK;
 }
 
+// Kept coarse steps of every member (host copy of the device counters).
+static mlswe_status read_done(Hier* H, std::vector<long long>& done) {
+  done.resize(H->n_members);
+  CUDA_TRY(H, cudaMemcpyAsync(done.data(), H->d_done, H->n_members * 8, cudaMemcpyDeviceToHost, H->st));
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  return MLSWE_OK;
+}
+
+// Level-0 activity of every member (a member that sits a round out takes no step on any level).
+static mlswe_status set_member_active(Hier* H, const std::vector<int>& act) {
+  CUDA_TRY(H, cudaMemcpy2DAsync(H->d_active, (size_t)H->L * sizeof(int), act.data(), sizeof(int), sizeof(int),
+                                H->n_members, cudaMemcpyHostToDevice, H->st));
+  return MLSWE_OK;
+}
+
 mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
   if (!h || n_coarse_steps < 0) return fail(h, MLSWE_EINVAL, "advance: bad argument");
   NvtxRange range("mlswe_advance");
   CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, 4, h->st));
+  mlswe_status s = ensure_snapshots(h);
+  if (s != MLSWE_OK) return s;
+  std::vector<long long> target;
+  s = read_done(h, target);
+  if (s != MLSWE_OK) return s;
+  for (long long& t : target) t += n_coarse_steps;
   for (int k = 0; k < n_coarse_steps; ++k) {
-    mlswe_status s;
     if (h->cfg.regrid_interval > 0 && h->L > 1 && h->coarse_steps % h->cfg.regrid_interval == 0) {
       s = regrid_internal(h, 0);
       if (s != MLSWE_OK) return s;
@@ -608,11 +646,37 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
     if (s != MLSWE_OK) return s;
     h->coarse_steps++;  // level steps and cell updates are counted on the device (dt_begin)
   }
+  // Retake rounds (no regrid): members whose rejected attempts left them short of n kept
+  // steps step again, the others sit the rounds out.
+  bool masked = false;
+  bool gave_up = false;
+  for (int extra = 0;; ++extra) {
+    std::vector<long long> done;
+    s = read_done(h, done);
+    if (s != MLSWE_OK) return s;
+    std::vector<int> act(h->n_members, 0);
+    bool any = false;
+    for (int m = 0; m < h->n_members; ++m)
+      if (done[m] < target[m]) { act[m] = 1; any = true; }
+    if (!any) break;
+    if (extra >= n_coarse_steps + 8) { gave_up = true; break; }
+    s = set_member_active(h, act);
+    if (s != MLSWE_OK) return s;
+    masked = true;
+    NvtxRange step_range("mlswe_coarse_step_retake");
+    s = coarse_step(h);
+    if (s != MLSWE_OK) return s;
+  }
+  if (masked) {
+    s = set_member_active(h, std::vector<int>(h->n_members, 1));
+    if (s != MLSWE_OK) return s;
+  }
   unsigned int status = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   if (status & 2u) return fail(h, MLSWE_ENEGDEPTH, "non-finite wave speed in a step");
-  if (status & 1u) return fail(h, MLSWE_ECFL, "Courant number above cfl_max in a step");
+  if (gave_up)
+    return fail(h, MLSWE_ECFL, "Courant number above cfl_max in every retake of a step (retake budget spent)");
   return MLSWE_OK;
 }
 

@@ -74,6 +74,9 @@ struct LevelDesc {
   // +t and -t; fields in (h, hu, hv) order. Null for the split step.
   double* ue;
   long long uxp, uyp;
+  // Copy of the patch cells of this level (level >= 1) taken before a coarse-step attempt of
+  // mlswe_advance, layout of q; a rejected attempt restores it. Null until advance needs it.
+  double* snap;
 };
 
 // One tile of a sweep: `nlines` lines of `len` cells, along x (x sweep: rows

@@ -124,12 +124,32 @@ static mlswe_status upload_desc(Hier* H) {
       D.NX = V.NX; D.NY = V.NY; D.P = V.P;
       D.inv_dx = 1.0 / V.dx; D.inv_dy = 1.0 / V.dy;
       D.ue = V.ue; D.uxp = V.uxp; D.uyp = V.uyp;
+      D.snap = V.snap;
       idx[k] = D.inv_dx; idy[k] = D.inv_dy;
     }
   CUDA_TRY(H, cudaMemcpyAsync(H->d_desc, d.data(), d.size() * sizeof(LevelDesc), cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaMemcpyAsync(H->d_invdx, idx.data(), nd * 8, cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaMemcpyAsync(H->d_invdy, idy.data(), nd * 8, cudaMemcpyHostToDevice, H->st));
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  return MLSWE_OK;
+}
+
+// Snapshot buffers of levels >= 1 for the Courant control of mlswe_advance (one state array
+// per level and member, allocated at the first advance of a multi-level hierarchy).
+mlswe_status ensure_snapshots(Hier* H) {
+  if (H->snaps_ready || H->L < 2) return MLSWE_OK;
+  const int F = 3 * H->cfg.M;
+  for (int m = 0; m < H->n_members; ++m)
+    for (int l = 1; l < H->L; ++l) {
+      Level& V = H->mem[m].lev[l];
+      if (V.snap) continue;
+      V.snap = (double*)dev_alloc(H, (size_t)V.NY * V.P * F * 8);
+      if (!V.snap) return fail(H, MLSWE_ENOMEM, "advance: snapshot allocation failed");
+    }
+  mlswe_status s = upload_desc(H);
+  if (s != MLSWE_OK) return s;
+  invalidate_graphs(H);
+  H->snaps_ready = true;
   return MLSWE_OK;
 }
 
@@ -551,6 +571,12 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
   H->d_cells = (long long*)dev_alloc(H, nd * 8);
   H->d_steps_acc = (long long*)dev_alloc(H, nd * 8);
   H->d_cells_acc = (long long*)dev_alloc(H, nd * 8);
+  H->d_redo = (int*)dev_alloc(H, n_members * 4);
+  H->d_done = (long long*)dev_alloc(H, n_members * 8);
+  if (!H->d_redo || !H->d_done) {
+    mlswe_destroy(H);
+    return MLSWE_ENOMEM;
+  }
   if (!H->d_desc || !H->d_dt || !H->d_smax || !H->d_init || !H->d_lost || !H->d_status || !H->d_t || !H->d_cfl ||
       !H->d_has || !H->d_invdx || !H->d_invdy || !H->d_par || !H->d_init_flag || !H->d_cfl_count || !H->d_rt ||
       !H->d_active || !H->d_cells || !H->d_steps_acc || !H->d_cells_acc || !H->d_fresh) {
@@ -579,6 +605,8 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
     cudaMemsetAsync(H->d_fresh, 0, 8, H->st);
     cudaMemsetAsync(H->d_steps_acc, 0, nd * 8, H->st);
     cudaMemsetAsync(H->d_cells_acc, 0, nd * 8, H->st);
+    cudaMemsetAsync(H->d_redo, 0, n_members * 4, H->st);
+    cudaMemsetAsync(H->d_done, 0, n_members * 8, H->st);
     cudaStreamSynchronize(H->st);
   }
   H->level_steps.assign(H->L, 0);
@@ -724,7 +752,14 @@ mlswe_status mlswe_step_level(mlswe_h h, int level, const double* dt, double* cf
     if (s != MLSWE_OK) return s;
     if (nan_seen) return fail(h, MLSWE_ENEGDEPTH, "non-finite wave speed in step");
     for (int m = 0; m < h->n_members; ++m)
-      if (cfl_out[m] > h->cfg.cfl_max) return fail(h, MLSWE_ECFL, "Courant number above cfl_max");
+      if (cfl_out[m] > h->cfg.cfl_max) {
+        // Undo the level step for every member (they share its launches): the buffer that
+        // held the state before the step becomes current again.
+        h->parity[level] ^= 1;
+        h->level_steps[level] -= 1;
+        h->cell_updates[level] -= patch_cells(h, level);
+        return fail(h, MLSWE_ECFL, "Courant number above cfl_max: the level step was undone");
+      }
   }
   return MLSWE_OK;
 }

@@ -45,6 +45,7 @@ struct Level {
   double* fyf = nullptr;
   double* ue = nullptr;         // unsplit step: per-edge arrays (see LevelDesc::ue)
   long long uxp = 0, uyp = 0;
+  double* snap = nullptr;       // level >= 1: patch cells before a coarse-step attempt
   std::vector<Box> patches;
 };
 
@@ -159,6 +160,9 @@ struct Hier {
   int* d_rt = nullptr;                 // [n_members * L] time ratio of each level (this step)
   int* d_active = nullptr;             // [n_members * L] the level's current substep is taken
   int* d_fresh = nullptr;              // [1] the next coarse step follows a regrid
+  int* d_redo = nullptr;               // [n_members] the last attempt was rejected (Courant > cfl_max)
+  long long* d_done = nullptr;         // [n_members] coarse steps kept by mlswe_advance
+  bool snaps_ready = false;            // every level >= 1 has its snapshot buffer
   long long* d_cells = nullptr;        // [n_members * L] cells inside the patches
   long long* d_steps_acc = nullptr;    // [n_members * L] level steps of mlswe_advance
   long long* d_cells_acc = nullptr;    // [n_members * L] cell updates of mlswe_advance
@@ -195,6 +199,8 @@ struct DtArgs {
   const long long* cells;   // [member * L + l] cells inside the level's patches
   long long* steps_acc;     // [member * L + l] level steps taken (accumulated)
   long long* cells_acc;     // [member * L + l] cell updates taken (accumulated)
+  int* redo;                // [member] 1: the attempt just taken was rejected
+  long long* done;          // [member] coarse steps kept
 };
 cudaError_t launch_dt_begin(const DtArgs& A, unsigned long long* smax_bits, const unsigned long long* init_bits,
                             int* init_flag, double* dt, cudaStream_t st);
@@ -203,6 +209,18 @@ cudaError_t launch_set_active(int L, int n_members, int level, int k, const int*
 cudaError_t launch_step_end(const DtArgs& A, const unsigned long long* smax_bits, const double* dt, double* t_member,
                             double* cfl_reached, unsigned int* status, unsigned long long* cfl_count,
                             cudaStream_t st);
+
+// Parities of every level at the start of a coarse step and after it.
+struct ParSet {
+  int start[4];
+  int next[4];
+};
+// Courant control of mlswe_advance over the patch boxes of every level (the wave-speed work
+// list): mode 0 copies the patch cells of levels >= 1 into their snapshots; mode 1, for the
+// members whose attempt was rejected, copies level 0's state before the step into its new
+// buffer and the snapshots into the new buffers of levels >= 1.
+cudaError_t launch_snapshot(int F, int L, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
+                            int grid, int mode, const ParSet& par, const int* redo, cudaStream_t st);
 
 // Cells inside the patches of `level`, summed over the members.
 long long patch_cells(const Hier* H, int level);
@@ -225,6 +243,7 @@ void* dev_alloc(Hier* H, size_t bytes);
 void dev_free(Hier* H, void* p);
 void* scratch_buffer(Hier* H, size_t bytes);
 void invalidate_graphs(Hier* H);
+mlswe_status ensure_snapshots(Hier* H);
 
 // Kernel launchers.
 cudaError_t launch_unsplit_update(const DevParams& P, const LevelDesc* descs, const SweepItem* items,

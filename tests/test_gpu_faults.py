@@ -48,20 +48,26 @@ def test_non_finite_state_is_reported(mlswe_lib):
 
 
 def test_courant_number_above_limit_is_reported(mlswe_lib):
+    """A level step above cfl_max (with a Courant report) is undone and reported; automatic
+    steps aimed above cfl_max are rejected in every retake and the call gives up with the
+    state of the last kept step."""
     w = I.small(50)
     H = _small(mlswe_lib)
     H.set_state(0, 0, w["q"])
     dt_ok = 0.9 * w["dx"] / 3.2
     cfl = H.step_level(0, dt=dt_ok, want_cfl=True)
     assert 0 < cfl[0] < 1.0
+    q1 = H.get_state(0, 0)
     _raises(mlswe_lib, ECFL, H.step_level, 0, dt=10 * dt_ok, want_cfl=True)
+    assert np.array_equal(H.get_state(0, 0), q1)  # undone
     H.close()
-    # automatic time steps aimed above cfl_max
+    # automatic time steps aimed above cfl_max: 2 rounds + 2 + 8 retake rounds, all rejected
     H = _small(mlswe_lib, cfl_desired=1.5, cfl_max=1.0)
     H.set_state(0, 0, w["q"])
     _raises(mlswe_lib, ECFL, H.advance, 2)
     st = H.get_stats()
-    assert st["cfl_exceeded"] >= 1 and st["last_cfl"] > 1.0
+    assert st["cfl_exceeded"] == 12 and st["last_cfl"] > 1.0
+    assert np.array_equal(H.get_state(0, 0), w["q"]) and H.get_time()[0][0] == 0.0
     H.close()
 
 
