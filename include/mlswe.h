@@ -349,22 +349,46 @@ mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_g
  * device whose FP64 rate bounds the adjoint). */
 mlswe_status mlswe_adjoint_keep_edge_data(mlswe_h h, int enable);
 
-/* Runs n_steps first-order steps from the current level-0 state (advancing it)
- * and returns J in *loss (host). */
-mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss);
+/* The controls of the gauge-misfit problem (Sec. 2.1, Eqs. (4)-(5) with the fluid at
+ * rest): eta1_0, the initial top surface eta_1, and B, the bathymetry, both device
+ * [ny][nx] (caller-owned, read before the call returns). The library writes B into the
+ * level and builds the initial state on the device: for two layers with the interface
+ * at rest at eta2, h_2 = eta2 - B and h_1 = eta1_0 - eta2; for one layer h_1 = eta1_0 - B
+ * (eta2 unused); momenta 0. Needs one member and one level (EINVAL otherwise, and for
+ * pointers that are not device memory). Synchronises the stream. */
+mlswe_status mlswe_fixed_set_controls(mlswe_h h, const double* eta1_0, const double* B, double eta2);
 
-/* Gradient of J of the last mlswe_fixed_forward: dL_dq0 receives dJ/dQ^0
- * (device, dense [3M][ny][nx], caller-owned) and dL_dB receives dJ/dB (device,
- * dense [ny][nx]; B enters every step's flux jumps and every gauge's eta_1). */
-mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB);
+/* mlswe_fixed_set_controls, then n_steps first-order steps from that state (advancing
+ * it); returns J in *loss (host). Call mlswe_adjoint_setup once before (after a first
+ * mlswe_fixed_set_controls, so that its tile timing sees a representative state). */
+mlswe_status mlswe_fixed_forward(mlswe_h h, const double* eta1_0, const double* B, double eta2, double* loss);
+
+/* Runs n_steps first-order steps from the current level-0 state, however it was set
+ * (advancing it), and returns J in *loss (host). */
+mlswe_status mlswe_fixed_forward_state(mlswe_h h, double* loss);
+
+/* Gradient of J of the last forward pass with respect to the controls of
+ * mlswe_fixed_forward: dL_deta1_0 and dL_dB, device [ny][nx] (caller-owned). B enters
+ * the initial depth of the bottom layer, every step's flux jumps (Eq. (4) surfaces)
+ * and every gauge's eta_1, so dL_dB = (dJ/dB at fixed Q^0) - dJ/dh_M(0); dL_deta1_0 =
+ * dJ/dh_1(0). Computed on the device. EINVAL for pointers that are not device memory,
+ * a missing forward pass, or an edge whose layers were not wet on both sides. */
+mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_deta1_0, double* dL_dB);
+
+/* Gradient of J of the last forward pass with respect to the initial state and, at fixed
+ * initial state, the bathymetry: dL_dq0 device dense [3M][ny][nx], dL_dB device [ny][nx]
+ * (caller-owned). The state-level form of mlswe_fixed_backward, for callers that set the
+ * initial state themselves (mlswe_set_state + mlswe_fixed_forward_state). */
+mlswe_status mlswe_fixed_backward_state(mlswe_h h, double* dL_dq0, double* dL_dB);
 
 /* One dimensionally split step of a single grid with walls on all sides that
  * allocates no memory. The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory while they step the model
  * (for example a solver run inside a callback of a framework that owns the
  * device memory pool, or a service under a no-allocation-after-start-up rule).
- * The caller passes its own device buffers: q_in and q_out [3M][ny][nx]
- * (distinct), B [ny][nx]. The solver's working memory (state after the x sweep,
+ * The caller passes its own device buffers: q_in and q_out [3M][ny][nx], B
+ * [ny][nx]; q_out may share no byte with q_in or B, and all three must be device (or
+ * managed) memory (MLSWE_EINVAL otherwise, checked before any GPU work). The solver's working memory (state after the x sweep,
  * tile lists, descriptor, time step, wave-speed slots) lives in one static
  * device array of about 16 MB that every GPU loading the library holds until
  * the process exits; grids up to nx * ny <= 512 * 512 cells (nx, ny >= 4) fit,

@@ -137,8 +137,11 @@ _SIGS = {
     "mlswe_get_clock": [_H, _dp, ctypes.c_int],
     "mlswe_get_stats": [_H, ctypes.c_void_p],
     "mlswe_set_clock": [_H, _dp, ctypes.c_int],
-    "mlswe_fixed_forward": [_H, _dp],
+    "mlswe_fixed_set_controls": [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double],
+    "mlswe_fixed_forward": [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, _dp],
+    "mlswe_fixed_forward_state": [_H, _dp],
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
+    "mlswe_fixed_backward_state": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
     "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
                      ctypes.POINTER(ctypes.c_longlong)],
@@ -434,15 +437,34 @@ class Hierarchy:
         the transposed sweeps; takes effect at the next adjoint_setup."""
         self._check(self.L.mlswe_adjoint_keep_edge_data(self.h, 1 if enable else 0), "adjoint_keep_edge_data")
 
-    def fixed_forward(self) -> float:
+    def fixed_set_controls(self, eta1_ptr: int, B_ptr: int, eta2: float):
+        """Initial state of the gauge-misfit problem from the device controls eta_1(0), B."""
+        self._check(self.L.mlswe_fixed_set_controls(self.h, ctypes.c_void_p(eta1_ptr), ctypes.c_void_p(B_ptr),
+                                                    float(eta2)), "fixed_set_controls")
+
+    def fixed_forward(self, eta1_ptr: int, B_ptr: int, eta2: float) -> float:
+        """Loss of the forward pass from the device controls eta_1(0), B ([ny][nx] each)."""
         loss = ctypes.c_double(0.0)
-        self._check(self.L.mlswe_fixed_forward(self.h, ctypes.byref(loss)), "fixed_forward")
+        self._check(self.L.mlswe_fixed_forward(self.h, ctypes.c_void_p(eta1_ptr), ctypes.c_void_p(B_ptr),
+                                               float(eta2), ctypes.byref(loss)), "fixed_forward")
         return loss.value
 
-    def fixed_backward(self, dq0_ptr: int, dB_ptr: int):
-        """Writes dJ/dQ^0 ([3M][ny][nx]) and dJ/dB ([ny][nx]) into caller-owned device buffers."""
-        self._check(self.L.mlswe_fixed_backward(self.h, ctypes.c_void_p(dq0_ptr), ctypes.c_void_p(dB_ptr)),
+    def fixed_forward_state(self) -> float:
+        """Loss of the forward pass from the current state."""
+        loss = ctypes.c_double(0.0)
+        self._check(self.L.mlswe_fixed_forward_state(self.h, ctypes.byref(loss)), "fixed_forward_state")
+        return loss.value
+
+    def fixed_backward(self, d_eta1_ptr: int, dB_ptr: int):
+        """Writes dJ/d eta_1(0) and dJ/dB ([ny][nx] each) into caller-owned device buffers."""
+        self._check(self.L.mlswe_fixed_backward(self.h, ctypes.c_void_p(d_eta1_ptr), ctypes.c_void_p(dB_ptr)),
                     "fixed_backward")
+
+    def fixed_backward_state(self, dq0_ptr: int, dB_ptr: int):
+        """Writes dJ/dQ^0 ([3M][ny][nx]) and dJ/dB at fixed Q^0 ([ny][nx]) into caller-owned
+        device buffers."""
+        self._check(self.L.mlswe_fixed_backward_state(self.h, ctypes.c_void_p(dq0_ptr), ctypes.c_void_p(dB_ptr)),
+                    "fixed_backward_state")
 
     def timing(self, enable: bool = True):
         """Per-kernel-class device time (ms) and launches since the last call; resets them."""

@@ -224,13 +224,9 @@ static cudaError_t launch_adjoint_t(const DevParams& P, const LevelDesc* descs, 
                                     int grid, const double* state, const double* lam_out, double* lam_in, double* gB,
                                     unsigned int* status, cudaStream_t st, const double* est, long long eplane) {
   const size_t sm = adjoint_smem_bytes(M);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_sweep_kernel<M, DIR, LOADED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = set_smem_limit_once(attr_set, adjoint_sweep_kernel<M, DIR, LOADED>, (int)sm);
+  if (e != cudaSuccess) return e;
   adjoint_sweep_kernel<M, DIR, LOADED><<<grid, kAdjThreads, sm, st>>>(P, descs, items, n, state, lam_out, lam_in,
                                                                        gB, status, est, eplane);
   return cudaGetLastError();
@@ -466,6 +462,61 @@ static mlswe_status adj_forward_step(Hier* H, Adjoint* A, int a) {
   return MLSWE_OK;
 }
 
+// Controls of the gauge-misfit problem to its initial state (a fluid at rest, Eqs. (4)-(5)):
+// the surface eta_1(0) and the bathymetry B (dense [NY][NX]) give, for two layers with the
+// interface at rest at eta_2, h_2 = eta_2 - B and h_1 = eta_1 - eta_2; for one layer
+// h_1 = eta_1 - B; momenta 0. B is also written into the level's bathymetry.
+__global__ void controls_to_state_kernel(int M, int NX, int NY, int P, const double* __restrict__ eta1,
+                                         const double* __restrict__ Bc, double eta2, double* __restrict__ q,
+                                         double* __restrict__ B) {
+  const size_t plane = (size_t)NY * P;
+  const long long n = (long long)NX * NY;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / NX), i = (int)(k - (long long)j * NX);
+    const size_t o = (size_t)j * P + i;
+    const double b = Bc[k], e1 = eta1[k];
+    B[o] = b;
+    if (M == 2) {
+      q[o] = e1 - eta2;
+      q[3 * plane + o] = eta2 - b;
+      q[4 * plane + o] = 0.0;
+      q[5 * plane + o] = 0.0;
+    } else {
+      q[o] = e1 - b;
+    }
+    q[plane + o] = 0.0;
+    q[2 * plane + o] = 0.0;
+  }
+}
+
+// Gradients of J with respect to the state Q^0 (lam, pitched) and to B at fixed Q^0 (gB)
+// to the gradients with respect to the controls, by the chain rule of the map above:
+// dJ/deta_1 = dJ/dh_1, dJ/dB = gB - dJ/dh_M (h_M = eta_M - B is the only depth B enters).
+__global__ void state_grad_to_controls_kernel(int M, int NX, int NY, int P, const double* __restrict__ lam,
+                                              const double* __restrict__ gB, double* __restrict__ d_eta1,
+                                              double* __restrict__ d_B) {
+  const size_t plane = (size_t)NY * P;
+  const long long n = (long long)NX * NY;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(k / NX), i = (int)(k - (long long)j * NX);
+    const size_t o = (size_t)j * P + i;
+    d_eta1[k] = lam[o];
+    d_B[k] = gB[o] - lam[(size_t)3 * (M - 1) * plane + o];
+  }
+}
+
+// Device (or managed) memory that kernels can dereference.
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static mlswe_status fixed_backward_core(mlswe_h h);
+
 extern "C" {
 
 mlswe_status mlswe_adjoint_setup(mlswe_h h, int n_steps, int ckpt_every, int n_gauges, const int32_t* gauge_ij,
@@ -537,7 +588,30 @@ mlswe_status mlswe_adjoint_keep_edge_data(mlswe_h h, int enable) {
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss) {
+mlswe_status mlswe_fixed_set_controls(mlswe_h h, const double* eta1_0, const double* B, double eta2) {
+  if (!h) return MLSWE_EINVAL;
+  if (!eta1_0 || !B) return afail(h, MLSWE_EINVAL, "fixed_set_controls: null pointer");
+  if (h->n_members != 1 || h->L != 1 || h->cfg.M > 2)
+    return afail(h, MLSWE_EINVAL, "fixed_set_controls: needs one member, one level and M <= 2");
+  if (!is_device_ptr(eta1_0) || !is_device_ptr(B))
+    return afail(h, MLSWE_EINVAL, "fixed_set_controls: eta1_0 and B must be device pointers");
+  Level& V = h->mem[0].lev[0];
+  controls_to_state_kernel<<<2 * h->num_sms, 256, 0, h->st>>>(h->cfg.M, V.NX, V.NY, V.P, eta1_0, B, eta2,
+                                                               V.q[h->parity[0]], V.B);
+  h->kernel_launches++;
+  ACUDA(h, cudaGetLastError());
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  h->dt_ready = false;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_fixed_forward(mlswe_h h, const double* eta1_0, const double* B, double eta2, double* loss) {
+  mlswe_status s = mlswe_fixed_set_controls(h, eta1_0, B, eta2);
+  if (s != MLSWE_OK) return s;
+  return mlswe_fixed_forward_state(h, loss);
+}
+
+mlswe_status mlswe_fixed_forward_state(mlswe_h h, double* loss) {
   if (!h) return MLSWE_EINVAL;
   Adjoint* A = adj_of(h, false);
   if (!A || A->n_steps < 1) return afail(h, MLSWE_EINVAL, "fixed_forward: call mlswe_adjoint_setup first");
@@ -584,8 +658,42 @@ mlswe_status mlswe_fixed_forward(mlswe_h h, double* loss) {
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
-  if (!h || !dL_dq0 || !dL_dB) return h ? afail(h, MLSWE_EINVAL, "fixed_backward: bad argument") : MLSWE_EINVAL;
+mlswe_status mlswe_fixed_backward_state(mlswe_h h, double* dL_dq0, double* dL_dB) {
+  if (!h || !dL_dq0 || !dL_dB) return h ? afail(h, MLSWE_EINVAL, "fixed_backward_state: bad argument") : MLSWE_EINVAL;
+  if (!is_device_ptr(dL_dq0) || !is_device_ptr(dL_dB))
+    return afail(h, MLSWE_EINVAL, "fixed_backward_state: outputs must be device pointers");
+  mlswe_status s = fixed_backward_core(h);
+  if (s != MLSWE_OK) return s;
+  Adjoint* A = adj_of(h, false);
+  const Level& V = h->mem[0].lev[0];
+  const int F = 3 * h->cfg.M;
+  ACUDA(h, cudaMemcpy2DAsync(dL_dq0, V.NX * 8, A->lam, V.P * 8, V.NX * 8, (size_t)F * V.NY, cudaMemcpyDeviceToDevice,
+                             h->st));
+  ACUDA(h, cudaMemcpy2DAsync(dL_dB, V.NX * 8, A->gB, V.P * 8, V.NX * 8, V.NY, cudaMemcpyDeviceToDevice, h->st));
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_deta1_0, double* dL_dB) {
+  if (!h || !dL_deta1_0 || !dL_dB) return h ? afail(h, MLSWE_EINVAL, "fixed_backward: bad argument") : MLSWE_EINVAL;
+  if (!is_device_ptr(dL_deta1_0) || !is_device_ptr(dL_dB))
+    return afail(h, MLSWE_EINVAL, "fixed_backward: outputs must be device pointers");
+  mlswe_status s = fixed_backward_core(h);
+  if (s != MLSWE_OK) return s;
+  Adjoint* A = adj_of(h, false);
+  const Level& V = h->mem[0].lev[0];
+  state_grad_to_controls_kernel<<<2 * h->num_sms, 256, 0, h->st>>>(h->cfg.M, V.NX, V.NY, V.P, A->lam, A->gB,
+                                                                    dL_deta1_0, dL_dB);
+  h->kernel_launches++;
+  ACUDA(h, cudaGetLastError());
+  ACUDA(h, cudaStreamSynchronize(h->st));
+  return MLSWE_OK;
+}
+
+}  // extern "C"
+
+// The backward pass: lam = dJ/dQ^0 and gB = dJ/dB at fixed Q^0, in the adjoint's buffers.
+static mlswe_status fixed_backward_core(mlswe_h h) {
   Adjoint* A = adj_of(h, false);
   if (!A || !A->forward_done) return afail(h, MLSWE_EINVAL, "fixed_backward: run mlswe_fixed_forward first");
   NvtxRange range("mlswe_fixed_backward");
@@ -630,14 +738,9 @@ mlswe_status mlswe_fixed_backward(mlswe_h h, double* dL_dq0, double* dL_dB) {
       timer_end(h, tok);
     }
   }
-  ACUDA(h, cudaMemcpy2DAsync(dL_dq0, V.NX * 8, A->lam, V.P * 8, V.NX * 8, (size_t)F * V.NY, cudaMemcpyDeviceToDevice,
-                             h->st));
-  ACUDA(h, cudaMemcpy2DAsync(dL_dB, V.NX * 8, A->gB, V.P * 8, V.NX * 8, V.NY, cudaMemcpyDeviceToDevice, h->st));
   unsigned int status = 0;
   ACUDA(h, cudaMemcpyAsync(&status, h->d_status, 4, cudaMemcpyDeviceToHost, h->st));
   ACUDA(h, cudaStreamSynchronize(h->st));
   if (status & 4u) return afail(h, MLSWE_EINVAL, "fixed_backward: a layer was not wet on both sides of an edge");
   return MLSWE_OK;
 }
-
-}  // extern "C"
