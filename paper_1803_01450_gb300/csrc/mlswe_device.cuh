@@ -21,6 +21,7 @@
 // are reciprocal-and-multiply, and the 4x4 wave-strength system is solved in
 // closed form through its Vandermonde structure instead of by elimination.
 #pragma once
+#include <atomic>
 #include <cstdint>
 
 namespace mlswe {
@@ -89,6 +90,22 @@ struct SweepItem {
   int flags;  // bit 0: interior lines (count CFL, record interface fluxes); bit 1: the tile
               // ends its patch line (its last edge is the patch boundary)
 };
+
+// Raises a kernel's dynamic shared-memory limit once per device: the attribute belongs
+// to the device that is current when it is set, so a process that launches on several
+// devices sets it on each (bit d of `flags` marks device d; devices past 63 set it on
+// every launch). Safe to call from several host threads: setting it twice is harmless.
+template <class K>
+cudaError_t set_smem_limit_once(std::atomic<unsigned long long>& flags, K* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (flags.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) flags.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 

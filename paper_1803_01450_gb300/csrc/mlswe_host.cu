@@ -106,6 +106,19 @@ static void timer_collect(Hier* H) {
   T.next = 0;
 }
 
+void fill_dev_params(const mlswe_config* cfg, DevParams* P) {
+  P->M = cfg->M; P->g = cfg->g; P->r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
+  P->omr = 1.0 - P->r; P->four_r = 4.0 * P->r; P->omr_g = (1.0 - P->r) * cfg->g;
+  for (int m = 0; m < 4; ++m) P->rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
+  for (int m = 0; m < 4; ++m) {
+    P->irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
+    for (int n = 0; n < 4; ++n) P->rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
+    P->gap_g[m] = m + 1 < cfg->M ? (1.0 - cfg->rho[m] / cfg->rho[m + 1]) * cfg->g : 0.0;
+  }
+  P->dry_tol = cfg->dry_tol; P->order = cfg->order; P->limiter = cfg->limiter; P->eigen = cfg->eigen;
+  P->unsplit = cfg->unsplit;
+}
+
 static mlswe_status upload_desc(Hier* H) {
   const int nd = H->n_members * H->L;
   std::vector<LevelDesc> d(nd);
@@ -468,16 +481,7 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
     H->own_stream = true;
   }
   if (alloc && alloc->alloc && alloc->free) { H->alloc = *alloc; H->own_alloc = false; }
-  H->dp.M = cfg->M; H->dp.g = cfg->g; H->dp.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
-  H->dp.omr = 1.0 - H->dp.r; H->dp.four_r = 4.0 * H->dp.r; H->dp.omr_g = (1.0 - H->dp.r) * cfg->g;
-  for (int m = 0; m < 4; ++m) H->dp.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
-  for (int m = 0; m < 4; ++m) {
-    H->dp.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
-    for (int n = 0; n < 4; ++n) H->dp.rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
-    H->dp.gap_g[m] = m + 1 < cfg->M ? (1.0 - cfg->rho[m] / cfg->rho[m + 1]) * cfg->g : 0.0;
-  }
-  H->dp.dry_tol = cfg->dry_tol; H->dp.order = cfg->order; H->dp.limiter = cfg->limiter; H->dp.eigen = cfg->eigen;
-  H->dp.unsplit = cfg->unsplit;
+  fill_dev_params(cfg, &H->dp);
   cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev);
   H->parity.assign(H->L, 0);
   H->wl.resize(H->L * 2);

@@ -243,6 +243,9 @@ void* dev_alloc(Hier* H, size_t bytes);
 void dev_free(Hier* H, void* p);
 void* scratch_buffer(Hier* H, size_t bytes);
 void invalidate_graphs(Hier* H);
+// Solver constants of a configuration, the host-side ones (density ratios, reciprocals,
+// reduced gravities) computed here once for every path that launches the sweeps.
+void fill_dev_params(const mlswe_config* cfg, DevParams* P);
 mlswe_status ensure_snapshots(Hier* H);
 
 // Kernel launchers.

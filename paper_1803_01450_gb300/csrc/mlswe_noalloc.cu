@@ -72,6 +72,23 @@ static void noalloc_items(int nx, int ny, int dir, std::vector<SweepItem>& out) 
   }
 }
 
+// True when p is memory a kernel can dereference (device or managed). Querying the
+// pointer allocates nothing.
+static bool noalloc_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unregistered host pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Byte ranges [a, a + na) and [b, b + nb) share at least one byte.
+static bool noalloc_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
 }  // namespace mlswe
 
 using namespace mlswe;
@@ -79,13 +96,20 @@ using namespace mlswe;
 extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx, int ny, double dx, double dy,
                                                  double dt, const double* q_in, const double* B, double* q_out,
                                                  void* cuda_stream, double* cfl_out) {
-  if (!cfg || !q_in || !B || !q_out || q_in == q_out || cfg->unsplit != 0) return MLSWE_EINVAL;
+  if (!cfg || !q_in || !B || !q_out || cfg->unsplit != 0) return MLSWE_EINVAL;
   if (cfg->M < 1 || cfg->M > 2 || cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2 ||
       cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->g > 0.0) || !(cfg->dry_tol >= 0.0))
     return MLSWE_EINVAL;
   if (cfg->M == 2 && !(cfg->rho[0] > 0.0 && cfg->rho[0] < cfg->rho[1])) return MLSWE_EINVAL;
   if (nx < 4 || ny < 4 || !(dx > 0.0) || !(dy > 0.0) || !(dt >= 0.0)) return MLSWE_EINVAL;
   if ((long long)nx * ny > kNoAllocMaxCells) return MLSWE_EINVAL;  // grid larger than the scratch array
+  // The buffers: device memory the kernels can read and write, and an output that shares
+  // no byte with either input (the sweeps read q_in and B while they write q_out).
+  const size_t state_bytes = (size_t)3 * cfg->M * nx * ny * sizeof(double);
+  const size_t bath_bytes = (size_t)nx * ny * sizeof(double);
+  if (!noalloc_device_ptr(q_in) || !noalloc_device_ptr(B) || !noalloc_device_ptr(q_out)) return MLSWE_EINVAL;
+  if (noalloc_overlap(q_in, state_bytes, q_out, state_bytes) || noalloc_overlap(B, bath_bytes, q_out, state_bytes))
+    return MLSWE_EINVAL;
   std::vector<SweepItem> items[2];
   for (int dir = 0; dir < 2; ++dir) {
     noalloc_items(nx, ny, dir, items[dir]);
@@ -115,16 +139,7 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
   D.ue = nullptr; D.uxp = 0; D.uyp = 0;
   const int counts[2] = {(int)items[0].size(), (int)items[1].size()};
   DevParams P;
-  P.M = cfg->M; P.g = cfg->g; P.r = cfg->M == 2 ? cfg->rho[0] / cfg->rho[1] : 1.0;
-  P.omr = 1.0 - P.r; P.four_r = 4.0 * P.r; P.omr_g = (1.0 - P.r) * cfg->g;
-  for (int m = 0; m < 4; ++m) P.rho[m] = m < cfg->M ? cfg->rho[m] : 0.0;
-  for (int m = 0; m < 4; ++m) {
-    P.irho[m] = m < cfg->M ? 1.0 / cfg->rho[m] : 0.0;
-    for (int n = 0; n < 4; ++n) P.rr[n][m] = n < cfg->M && m < cfg->M ? cfg->rho[n] / cfg->rho[m] : 0.0;
-    P.gap_g[m] = m + 1 < cfg->M ? (1.0 - cfg->rho[m] / cfg->rho[m + 1]) * cfg->g : 0.0;
-  }
-  P.dry_tol = cfg->dry_tol; P.order = cfg->order; P.limiter = cfg->limiter; P.eigen = cfg->eigen;
-  P.unsplit = 0;
+  fill_dev_params(cfg, &P);  // unsplit is 0 (checked above)
 
   if (cudaMemcpyAsync(d_desc, &D, sizeof(D), cudaMemcpyHostToDevice, st) != cudaSuccess) return MLSWE_ECUDA;
   if (cudaMemcpyAsync(d_count, counts, sizeof(counts), cudaMemcpyHostToDevice, st) != cudaSuccess) return MLSWE_ECUDA;

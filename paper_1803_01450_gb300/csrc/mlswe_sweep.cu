@@ -549,13 +549,9 @@ static cudaError_t launch_sweep_t(const DevParams& P, const LevelDesc* descs, co
                                   unsigned long long* smax_bits, unsigned int* lost_count, cudaStream_t st,
                                   double* est, long long eplane) {
   const size_t sm = sweep_smem_bytes(M) + (UNSPLIT ? (size_t)(M >= 3 ? 2 * M : M) * kMaxEdges * 8 : 0);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<M, DIR, MINB, STORE, UNSPLIT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_set{0};
+  cudaError_t e = set_smem_limit_once(attr_set, sweep_kernel<M, DIR, MINB, STORE, UNSPLIT>, (int)sm);
+  if (e != cudaSuccess) return e;
   sweep_kernel<M, DIR, MINB, STORE, UNSPLIT><<<grid, kThreads, sm, st>>>(P, descs, items, n_items_dev, tile_off,
                                                                          parity, record, smax_bits, lost_count, est,
                                                                          eplane);
