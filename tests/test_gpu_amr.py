@@ -12,7 +12,7 @@ import pytest
 import oracle as O
 from oracle.amr import OracleAMR
 from paper_1803_01450_gb300 import inputs as I
-from conftest import rel_err
+from conftest import rel_err, report
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -200,9 +200,11 @@ def test_amr_run_parity_small(mlswe_lib):
     t, dt = H.get_time()
     assert abs(t[0] - A.t) <= 1e-12 * A.t
     q0 = H.get_state(0, 0)
+    report("amr_small_100coarse_level0", rel_err(q0, A.lev[0].q))
     assert rel_err(q0, A.lev[0].q).max() < TOL
     m = A.lev[1].in_patch_mask()
     q1 = H.get_state(0, 1)
+    report("amr_small_100coarse_level1", rel_err(q1[:, m], A.lev[1].q[:, m]))
     assert rel_err(q1[:, m], A.lev[1].q[:, m]).max() < TOL
     m_gpu = gpu_mass()
     assert np.all(np.abs(m_gpu - A.mass()) <= 1e-12 * A.mass())

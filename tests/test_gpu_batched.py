@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from oracle.amr import OracleAMR
 from paper_1803_01450_gb300 import inputs as I
-from conftest import rel_err
+from conftest import rel_err, report, state_err, state_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -122,16 +122,10 @@ def test_ensemble_members_match_oracle(mlswe_lib):
         A.advance(8, regrid_interval=4)
         assert [tuple(b) for b in H.get_patches(k, 1).tolist()] == [tuple(b) for b in A.lev[1].patches]
         assert abs(t[k] - A.t) <= 1e-12 * A.t
-        # Deep water: momentum near rest is rounding noise of eta - B, so the bound is the
-        # larger of 1e-11 and 10x the oracle's own change under a one-ulp input perturbation.
-        A2 = OracleAMR(P, (0, 0, m["L"], m["L"]), m["n"], m["n"], 2, [4], Bf, flag_tol=2e-5, min_side=16, max_side=64)
-        rng = np.random.default_rng(k)
-        A2.set_state(0, q0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=q0.shape)))
-        A2.advance(8, regrid_interval=4)
-        sens = rel_err(A2.lev[0].q, A.lev[0].q)
-        err = rel_err(H.get_state(k, 0), A.lev[0].q)
-        assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (k, err, sens)
-        assert err[[0, 3]].max() <= TOL
+        # momenta against at least h_max sqrt(g h_max) of their layer (state_scale)
+        err = state_err(H.get_state(k, 0), A.lev[0].q, 2)
+        report(f"ensemble3_member{k}_level0", err)
+        assert err.max() <= TOL, (k, err)
     assert len(set(np.round(dt, 12))) == len(members)  # per-member time steps differ
     H.close()
 

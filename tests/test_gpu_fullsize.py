@@ -4,14 +4,15 @@ autotuned tiles, one persistent launch per level step, graph replay), checked wh
 oracle can follow it: a level-2 step of sampled patches (the most active and some at
 random) against the oracle's patch step on the same ghost-filled input, and the whole
 level-0 step against the oracle's walled step; and the ensemble workload (256 members) on
-sampled members and patches. Within 1e-11 of each field's level-wide scale (near-rest
-momenta in deep water: within 10x the oracle's own one-ulp sensitivity). The adjoint
+sampled members and patches. Within 1e-11 of each field's level-wide scale (state_scale:
+a momentum's scale is at least h_max sqrt(g h_max) of its layer). The adjoint
 workload at full size: its gradient against central differences of the GPU forward."""
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_1803_01450_gb300 import inputs as I
+from conftest import report, state_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -50,17 +51,13 @@ def _scale(q):
 
 
 def _check_walled_step(P, q0, B, dx, dt, got, rng, where):
-    """got against the oracle's walled step of q0: depths within 1e-11 of their scale,
-    momenta within the larger of 1e-11 and 10x the oracle's own change under a one-ulp
-    perturbation of its input (deep water makes near-rest momentum rounding noise)."""
+    """got against the oracle's walled step of q0, every field within 1e-11 of its scale
+    (state_scale of the states before and after: momenta at least h_max sqrt(g h_max))."""
     want, _, _ = O.step_walled(P, q0, B, dx, dx, dt)
-    pert = np.ascontiguousarray(q0 * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=q0.shape)))
-    wp, _, _ = O.step_walled(P, pert, B, dx, dx, dt)
-    scale = np.maximum(_scale(want), _scale(q0))
+    scale = np.maximum(state_scale(want, P.M), state_scale(q0, P.M))
     err = np.abs(got - want).max(axis=(1, 2)) / scale
-    sens = np.abs(wp - want).max(axis=(1, 2)) / scale
-    assert err[[0, 3]].max() <= TOL, (where, err)
-    assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (where, err, sens)
+    report(f"walled_step_{where}", err)
+    assert err.max() <= TOL, (where, err)
 
 
 def test_level2_sampled_patches_match_oracle_patch_step(amr_full):
@@ -80,23 +77,20 @@ def test_level2_sampled_patches_match_oracle_patch_step(amr_full):
     # the three patches with the strongest flow and three at random
     act = [np.abs(q0[[1, 2, 4, 5], b[1]:b[3], b[0]:b[2]]).max() for b in inner]
     picks = list(np.argsort(act)[-3:]) + list(rng.choice(len(inner), 3, replace=False))
-    # level-wide per-field scale; momenta near rest are rounding noise of eta - B, so their
-    # bound is the larger of 1e-11 and 10x the oracle's own change under a one-ulp
-    # perturbation of its input
-    scale = np.maximum(np.abs(q0).max(axis=(1, 2)), np.abs(q1).max(axis=(1, 2)))
+    # level-wide per-field scale (momenta at least h_max sqrt(g h_max) of their layer)
+    scale = np.maximum(state_scale(q0, 2), state_scale(q1, 2))
     P = O.params(M=2, dry_tol=1e-3)
+    worst = np.zeros(6)
     for k in picks:
         i0, j0, i1, j1 = inner[k]
         qp = np.ascontiguousarray(q0[:, j0 - NG:j1 + NG, i0 - NG:i1 + NG])
         Bp = np.ascontiguousarray(B2[j0 - NG:j1 + NG, i0 - NG:i1 + NG])
-        pert = np.ascontiguousarray(qp * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=qp.shape)))
         O.step_patch(P, qp, Bp, dx, dx, dt)
-        O.step_patch(P, pert, Bp, dx, dx, dt)
         want = qp[:, NG:-NG, NG:-NG]
         err = np.abs(q1[:, j0:j1, i0:i1] - want).max(axis=(1, 2)) / scale
-        sens = np.abs(pert[:, NG:-NG, NG:-NG] - want).max(axis=(1, 2)) / scale
-        assert err[[0, 3]].max() <= TOL, (inner[k], err)
-        assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (inner[k], err, sens)
+        worst = np.maximum(worst, err)
+        assert err.max() <= TOL, (inner[k], err)
+    report("amr_level2_patches", worst)
 
 
 def test_level0_step_matches_oracle_walled_step(amr_full):
@@ -171,18 +165,17 @@ def test_ensemble_sampled_members_match_oracle(ensemble_full):
         nf = members[k]["n"] * r
         qb = H.get_state(k, 1)
         Bf = H.get_bathymetry(k, 1)
-        scale = np.maximum(np.abs(qa).max(axis=(1, 2)), np.abs(qb).max(axis=(1, 2)))
+        scale = np.maximum(state_scale(qa, 2), state_scale(qb, 2))
         dxf = members[k]["L"] / nf
+        worst = np.zeros(6)
         for (i0, j0, i1, j1), qp in inputs:
             Bp = np.ascontiguousarray(Bf[j0 - NG:j1 + NG, i0 - NG:i1 + NG])
-            pert = np.ascontiguousarray(qp * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=qp.shape)))
             O.step_patch(P, qp, Bp, dxf, dxf, dt0[k] / r)
-            O.step_patch(P, pert, Bp, dxf, dxf, dt0[k] / r)
             want = qp[:, NG:-NG, NG:-NG]
             err = np.abs(qb[:, j0:j1, i0:i1] - want).max(axis=(1, 2)) / scale
-            sens = np.abs(pert[:, NG:-NG, NG:-NG] - want).max(axis=(1, 2)) / scale
-            assert err[[0, 3]].max() <= TOL, (k, (i0, j0, i1, j1), err)
-            assert np.all(err <= np.maximum(TOL, 10.0 * sens)), (k, (i0, j0, i1, j1), err, sens)
+            worst = np.maximum(worst, err)
+            assert err.max() <= TOL, (k, (i0, j0, i1, j1), err)
+        report(f"ensemble_member{k}_refined_patches", worst)
 
 
 def test_adjoint_full_size_gradient_matches_central_fd(mlswe_lib):

@@ -2,14 +2,13 @@
 wet states (both orders, odd shapes), a shore where the lower layers meet dry ground (the
 per-layer branch and its walls), the lake at rest, the count of edges that lost
 hyperbolicity, and a subcycled AMR run (refinement, coarsening and reflux with three layers).
-Tolerance: 1e-11 relative per field (the oracle's one-ulp sensitivity where deep water makes
-near-rest momentum rounding noise, as in the two-layer tests)."""
+Tolerance: 1e-11 relative per field; on the deep shore a momentum's scale is at least
+h_max sqrt(g h_max) of its layer (state_scale), as in the two-layer tests."""
 import numpy as np
 import pytest
 
 from paper_1803_01450_gb300 import inputs as I
-from conftest import rel_err
-from test_gpu_step import oracle_sensitivity
+from conftest import rel_err, report, state_err, state_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -78,10 +77,9 @@ def test_three_layer_shore(mlswe_lib, orc):
     w = I.shore3(96, seed=3002)
     dts = [0.5 * w["dx"] / 210.0] * 20
     qg, qo, _, _, P = _run_both(mlswe_lib, orc, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
-    err = rel_err(qg, qo)
-    sens = oracle_sensitivity(orc, w["q"], w["B"], w["dx"], w["dy"], dts, P)
-    assert np.all(err < np.maximum(TOL, 10.0 * sens)), (err, sens)
-    assert err[[0, 3, 6]].max() < TOL  # depths: plain bound
+    err = state_err(qg, qo, 3)
+    report("three_layer_shore_96_20steps", err)
+    assert err.max() < TOL, err
 
 
 def test_three_layer_lake_at_rest(mlswe_lib):

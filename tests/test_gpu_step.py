@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_1803_01450_gb300 import inputs as I
-from conftest import rel_err
+from conftest import rel_err, report, state_err, state_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -40,6 +40,7 @@ def test_small_config_100_steps(mlswe_lib, orc):
     dts = [0.9 * w["dx"] / 3.2] * 100
     qg, qo = _run_both(mlswe_lib, orc, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
     err = rel_err(qg, qo)
+    report("small_50_100steps", err)
     assert err.max() < TOL, err
 
 
@@ -52,6 +53,7 @@ def test_random_wet_states(mlswe_lib, orc, M, order, limiter, shape):
     dts = [0.2 * min(dx, dy) / 4.0] * 5
     qg, qo = _run_both(mlswe_lib, orc, q, B, dx, dy, dts, M=M, order=order, limiter=limiter, dry_tol=1e-6)
     err = rel_err(qg, qo)
+    report(f"random_M{M}_o{order}_l{limiter}_{ny}x{nx}", err)
     assert err.max() < TOL, err
 
 
@@ -62,30 +64,17 @@ def test_eigen_guess_only_variant(mlswe_lib, orc):
     assert rel_err(qg, qo).max() < TOL
 
 
-def oracle_sensitivity(orc, q, B, dx, dy, dts, P, seed=1):
-    """Per-field change of the oracle's own result when its input is perturbed by about one
-    ulp (relative 2^-52, random signs): the floor below which no two FP64 implementations
-    of this step can be asked to agree."""
-    rng = np.random.default_rng(seed)
-    a, b = q.copy(), q * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=q.shape))
-    for dt in dts:
-        a, _, _ = orc.step_walled(P, a, B, dx, dy, dt)
-        b, _, _ = orc.step_walled(P, b, B, dx, dy, dt)
-    return rel_err(b, a)
-
-
 def test_shore_wet_dry(mlswe_lib, orc):
-    """Shelf + shore with both layers meeting dry land. Deep water (B down to -4000 m) on a
-    1 km grid makes the momentum of the near-rest region rounding noise of the well-balanced
-    eta - B reconstruction, so the bound is the larger of 1e-11 and 10x the oracle's own
-    one-ulp sensitivity."""
+    """Shelf + shore with both layers meeting dry land, 20 steps. Deep water (B down to
+    -4000 m) makes the momentum of the near-rest region rounding noise of the well-balanced
+    eta - B reconstruction; momenta are measured against the physical scale
+    h_max sqrt(g h_max) of their layer (state_scale)."""
     w = I.shore(96, seed=3001)
     dts = [0.5 * w["dx"] / 210.0] * 20
     qg, qo = _run_both(mlswe_lib, orc, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
-    err = rel_err(qg, qo)
-    sens = oracle_sensitivity(orc, w["q"], w["B"], w["dx"], w["dy"], dts, orc.params(M=2, dry_tol=w["dry_tol"]))
-    assert np.all(err < np.maximum(TOL, 10.0 * sens)), (err, sens)
-    assert err[[0, 3]].max() < TOL  # depths: plain bound
+    err = state_err(qg, qo, 2)
+    report("shore_96_20steps", err)
+    assert err.max() < TOL, err
 
 
 def test_lake_at_rest_gpu(mlswe_lib):
@@ -135,21 +124,19 @@ def test_full_size_sampled(mlswe_lib, orc):
     P = orc.params(M=2, dry_tol=1e-3)
     rs = np.random.default_rng(7)
     cells = [(int(rs.integers(4, n - 4)), int(rs.integers(4, n - 4))) for _ in range(48)]
-    # per-field scale of the state after the step (momenta start at zero); deep water makes
-    # near-rest momentum rounding noise of eta - B, so each cell's bound is the larger of
-    # 1e-11 and 10x the oracle's own change under a one-ulp perturbation of its window
-    scale = np.maximum(np.abs(qg).max(axis=(1, 2)), np.abs(q).max(axis=(1, 2)))
+    # per-field scale of the whole state before and after the step (momenta start at zero,
+    # so they take the physical scale h_max sqrt(g h_max) of their layer, state_scale)
+    scale = np.maximum(state_scale(qg, 2), state_scale(q, 2))
+    worst = np.zeros(6)
     for (j, i) in cells:
         sub = np.ascontiguousarray(q[:, j - 4:j + 5, i - 4:i + 5])
         subB = np.ascontiguousarray(B[j - 4:j + 5, i - 4:i + 5])
-        pert = np.ascontiguousarray(sub * (1.0 + 2.0 ** -52 * rs.choice([-1.0, 1.0], size=sub.shape)))
         orc.step_patch(P, sub, subB, w["dx"], w["dy"], dt)
-        orc.step_patch(P, pert, subB, w["dx"], w["dy"], dt)
         ref = sub[:, 4, 4]
-        err = np.abs(qg[:, j, i] - ref) / np.maximum(scale, 1e-300)
-        sens = np.abs(pert[:, 4, 4] - ref) / np.maximum(scale, 1e-300)
-        assert np.all(err < np.maximum(TOL, 10.0 * sens)), (j, i, err, sens)
-        assert err[[0, 3]].max() < TOL, (j, i, err)
+        err = np.abs(qg[:, j, i] - ref) / scale
+        worst = np.maximum(worst, err)
+        assert err.max() < TOL, (j, i, err)
+    report("scale_2048_sampled", worst)
 
 
 def test_hyperbolicity_loss_branch(mlswe_lib, orc):

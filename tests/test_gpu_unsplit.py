@@ -12,7 +12,7 @@ import pytest
 import oracle as O
 from oracle.amr import OracleAMR
 from paper_1803_01450_gb300 import inputs as I
-from conftest import rel_err
+from conftest import rel_err, report, state_err, state_scale
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -67,21 +67,14 @@ def test_small_workload_100_steps(mlswe_lib):
 
 def test_shore_wet_dry(mlswe_lib):
     """Both layers meeting dry land (the per-layer transverse split, walls for a layer):
-    depths to 1e-11; momenta to the larger of 1e-11 and 10x the oracle's own change under a
-    one-ulp perturbation (deep water makes near-rest momentum rounding noise)."""
+    every field to 1e-11 of its scale (state_scale: a momentum's scale is at least h_max
+    sqrt(g h_max) of its layer, since deep water makes near-rest momentum rounding noise)."""
     w = I.shore(96, seed=3001)
     dts = [0.5 * w["dx"] / 210.0] * 20
     qg, qo, _ = _run_both(mlswe_lib, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
-    P = O.params(M=2, dry_tol=w["dry_tol"], unsplit=1)
-    rng = np.random.default_rng(1)
-    a, b = w["q"].copy(), w["q"] * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=w["q"].shape))
-    for dt in dts:
-        a, _, _ = O.step_walled(P, a, w["B"], w["dx"], w["dy"], dt)
-        b, _, _ = O.step_walled(P, b, w["B"], w["dx"], w["dy"], dt)
-    sens = rel_err(b, a)
-    err = rel_err(qg, qo)
-    assert np.all(err < np.maximum(TOL, 10.0 * sens)), (err, sens)
-    assert err[[0, 3]].max() < TOL
+    err = state_err(qg, qo, 2)
+    report("unsplit_shore_96_20steps", err)
+    assert err.max() < TOL, err
 
 
 def test_lake_at_rest(mlswe_lib):
@@ -145,18 +138,17 @@ def test_full_size_sampled(mlswe_lib):
     P = O.params(M=2, dry_tol=1e-3, unsplit=1)
     rs = np.random.default_rng(8)
     cells = [(int(rs.integers(4, n - 4)), int(rs.integers(4, n - 4))) for _ in range(48)]
-    scale = np.maximum(np.abs(qg).max(axis=(1, 2)), np.abs(q).max(axis=(1, 2)))
+    scale = np.maximum(state_scale(qg, 2), state_scale(q, 2))
+    worst = np.zeros(6)
     for (j, i) in cells:
         sub = np.ascontiguousarray(q[:, j - 4:j + 5, i - 4:i + 5])
         subB = np.ascontiguousarray(B[j - 4:j + 5, i - 4:i + 5])
-        pert = np.ascontiguousarray(sub * (1.0 + 2.0 ** -52 * rs.choice([-1.0, 1.0], size=sub.shape)))
         O.step_patch(P, sub, subB, w["dx"], w["dy"], dt)
-        O.step_patch(P, pert, subB, w["dx"], w["dy"], dt)
         ref = sub[:, 4, 4]
-        err = np.abs(qg[:, j, i] - ref) / np.maximum(scale, 1e-300)
-        sens = np.abs(pert[:, 4, 4] - ref) / np.maximum(scale, 1e-300)
-        assert np.all(err < np.maximum(TOL, 10.0 * sens)), (j, i, err, sens)
-        assert err[[0, 3]].max() < TOL, (j, i, err)
+        err = np.abs(qg[:, j, i] - ref) / scale
+        worst = np.maximum(worst, err)
+        assert err.max() < TOL, (j, i, err)
+    report("unsplit_scale_2048_sampled", worst)
 
 
 def _amr_pair(pkg, levels, ratios, n, min_side, max_side, regrid, dynamic=0, Bf=None):
@@ -283,15 +275,9 @@ def test_three_layer_shore_and_rest(mlswe_lib):
     w = I.shore3(96, seed=3002)
     dts = [0.5 * w["dx"] / 210.0] * 20
     qg, qo, P = _run_three(mlswe_lib, w["q"], w["B"], w["dx"], w["dy"], dts, dry_tol=w["dry_tol"])
-    rng = np.random.default_rng(2)
-    a, b = w["q"].copy(), w["q"] * (1.0 + 2.0 ** -52 * rng.choice([-1.0, 1.0], size=w["q"].shape))
-    for dt in dts:
-        a, _, _ = O.step_walled(P, a, w["B"], w["dx"], w["dy"], dt)
-        b, _, _ = O.step_walled(P, b, w["B"], w["dx"], w["dy"], dt)
-    sens = rel_err(b, a)
-    err = rel_err(qg, qo)
-    assert np.all(err < np.maximum(TOL, 10.0 * sens)), (err, sens)
-    assert err[[0, 3, 6]].max() < TOL
+    err = state_err(qg, qo, 3)
+    report("unsplit_three_layer_shore_96_20steps", err)
+    assert err.max() < TOL, err
     n = 64
     B = I.shore_bathymetry(n, n)
     q = I.stacked_state(B, (np.zeros_like(B), -50.0 + 0.0 * B, -200.0 + 0.0 * B))
