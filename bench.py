@@ -54,8 +54,17 @@ FP64_FLOP_PER_CELL_UPDATE_3 = 4134.82
 FP64_FLOP_PER_CELL_UPDATE_UNSPLIT = 2456.89
 FP64_FLOP_UNSPLIT_EDGE_PASS = 1143.94
 FP64_FLOP_PER_CELL_UPDATE_UNSPLIT_3 = 6816.15  # three layers (inputs.scale3)
-# HBM copy bandwidth measured on this part (MEASURED_PEAKS.json, STREAM-style copy).
-HBM_PEAK_GBS = 6674.8
+def _measured_hbm_gbs(default=6674.8):
+    """HBM copy bandwidth measured on the GB300s (STREAM-style copy), from the peaks
+    file the machine provides; the earlier measurement when the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return default
+
+
+HBM_PEAK_GBS = _measured_hbm_gbs()
 # FP64 peak derived from the unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/); None
@@ -143,6 +152,7 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    oracle.use_timing_build()
     oracle.build()
     w = I.scale(N_CELLS)
     P = oracle.params(M=2, dry_tol=w["dry_tol"])
@@ -154,7 +164,7 @@ def run_reference(args):
     for _ in range(args.steps):
         q, _, _ = oracle.step_walled(P, q, B, w["dx"], w["dy"], dt)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     v = N_CELLS * N_CELLS * M_LAYERS * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
@@ -162,15 +172,38 @@ def run_reference(args):
             "config": {"workload": _workload_name(), "cells": N_CELLS * N_CELLS, "layers": M_LAYERS},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full time steps of the 2048^2 workload after "
-                                       f"{args.warmup} warm-up steps"},
+                                       f"{args.warmup} warm-up steps, oracle built -O3 (Neoverse V2 tuning on "
+                                       f"Arm hosts), OpenMP over rows",
+                             "host_cores": _host_cores()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds_budget=12.0):
-    """Oracle throughput on the host cores over a bounded sample of the headline workload: whole
-    time steps until about seconds_budget of CPU work has run."""
+def _host_cores():
+    """Logical CPUs, those this process may run on, and physical cores (distinct (package,
+    core) pairs in sysfs; None where the topology is not readable)."""
+    phys = set()
+    base = "/sys/devices/system/cpu"
+    try:
+        for d in os.listdir(base):
+            if d.startswith("cpu") and d[3:].isdigit():
+                t = os.path.join(base, d, "topology")
+                with open(os.path.join(t, "core_id")) as f:
+                    core = f.read().strip()
+                with open(os.path.join(t, "physical_package_id")) as f:
+                    pkg = f.read().strip()
+                phys.add((pkg, core))
+    except OSError:
+        phys = set()
+    return {"logical": os.cpu_count(), "affinity": len(os.sched_getaffinity(0)),
+            "physical": len(phys) or None}
+
+
+def _oracle_rate(seconds_budget, max_steps):
+    """LCU/s of the oracle's timing build over whole headline time steps (about seconds_budget
+    of work, at least one step), and the OpenMP threads it ran with."""
     import oracle
+    oracle.use_timing_build()
     oracle.build()
     w = I.scale(N_CELLS)
     P = oracle.params(M=2, dry_tol=w["dry_tol"])
@@ -181,12 +214,34 @@ def cpu_baseline(seconds_budget=12.0):
     while True:
         q, _, _ = oracle.step_walled(P, q, B, w["dx"], w["dy"], dt)
         n += 1
-        if time.perf_counter() - t0 > seconds_budget or n >= 400:
+        if time.perf_counter() - t0 > seconds_budget or n >= max_steps:
             break
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": N_CELLS * N_CELLS * M_LAYERS * n / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n} full time steps of the 2048^2 headline workload ({el:.1f} s)"}
+    return N_CELLS * N_CELLS * M_LAYERS * n / el, n, el, oracle.threads()
+
+
+def cpu_baseline(seconds_budget=12.0):
+    """Oracle throughput on the host cores over a bounded sample of the headline workload
+    (whole time steps, about seconds_budget of work), with every core the process may use and
+    with one thread (a child process with OMP_NUM_THREADS=1, about 8 s)."""
+    v, n, el, threads = _oracle_rate(seconds_budget, 400)
+    one = None
+    try:
+        code = ("import json, bench; r = bench._oracle_rate(8.0, 3); "
+                "print(json.dumps({'value': r[0], 'steps': r[1], 's': r[2], 'threads': r[3]}))")
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=300)
+        if out.returncode == 0:
+            one = json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        one = None
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} full time steps of the 2048^2 headline workload ({el:.1f} s), oracle built -O3 "
+                      f"(Neoverse V2 tuning on Arm hosts), OpenMP over rows",
+            "host_cores": _host_cores(),
+            "one_core": None if one is None else {"value": one["value"], "threads": one["threads"],
+                                                  "sample": f"{one['steps']} full time steps ({one['s']:.1f} s)"}}
 
 
 def _interior_updates(H, member_count, levels, ratios):
@@ -589,6 +644,29 @@ def bench_unsplit(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
             "update_algorithmic_bytes": upd_bytes, "tiles": tiles}
 
 
+def _summary(line):
+    """The secondary figures in a few numbers, last on the line (readers that keep only the
+    end of the output still see them)."""
+    out = {"headline_lcups": line["value"], "e2e_lcups": line["e2e"]["value"],
+           "sweep_frac_of_fp64_peak": line["roofline"]["frac"]}
+    amr = line.get("batched_amr")
+    if amr:
+        out["batched_amr"] = {"batched_lcups": amr.get("lcups_batched"), "per_patch_lcups": amr.get("lcups_per_patch"),
+                              "ratio": amr.get("batched_over_per_patch")}
+    ens = line.get("ensemble")
+    if ens:
+        out["ensemble"] = {"batched_lcups": ens.get("lcups_batched"), "per_patch_lcups": ens.get("lcups_per_patch"),
+                           "ratio": ens.get("batched_over_per_patch")}
+    adj = line.get("adjoint")
+    if adj:
+        out["adjoint_over_forward"] = adj.get("adjoint_over_forward")
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        out["cpu_oracle_lcups"] = cpu["value"]
+        out["cpu_oracle_one_core_lcups"] = (cpu.get("one_core") or {}).get("value")
+    return out
+
+
 def run_only(name):
     import torch
     import paper_1803_01450_gb300 as pkg
@@ -720,6 +798,7 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
+        line["summary"] = _summary(line)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -1403,6 +1403,9 @@ void adjoint_sweep_line(const Params& P, int n, const double* line, const double
 
 // Jacobian of the first-order fluctuations of one edge, J[12][14]: rows A-dQ (6), A+dQ (6);
 // columns qL (6), qR (6), BL, BR (dual numbers).
+// OpenMP threads the oracle's parallel loops use (for reporting the CPU baseline).
+extern "C" int or_threads() { return omp_get_max_threads(); }
+
 extern "C" void or_edge_jacobian(const or_params* pp, const double* qL, const double* qR, double BL, double BR,
                                  double* J) {
   const Params P = to_params(pp);
