@@ -172,7 +172,7 @@ def run_reference(args):
             "config": {"workload": _workload_name(), "cells": N_CELLS * N_CELLS, "layers": M_LAYERS},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full time steps of the 2048^2 workload after "
-                                       f"{args.warmup} warm-up steps, oracle built -O3 (Neoverse V2 tuning on "
+                                       f"{args.warmup} warm-up steps, oracle built -O3 (scheduled for Neoverse V2 on "
                                        f"Arm hosts), OpenMP over rows",
                              "host_cores": _host_cores()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -238,7 +238,7 @@ def cpu_baseline(seconds_budget=12.0):
         one = None
     return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{n} full time steps of the 2048^2 headline workload ({el:.1f} s), oracle built -O3 "
-                      f"(Neoverse V2 tuning on Arm hosts), OpenMP over rows",
+                      f"(scheduled for Neoverse V2 on Arm hosts), OpenMP over rows",
             "host_cores": _host_cores(),
             "one_core": None if one is None else {"value": one["value"], "threads": one["threads"],
                                                   "sample": f"{one['steps']} full time steps ({one['s']:.1f} s)"}}
@@ -457,13 +457,13 @@ def bench_dynamic_rt(pkg, torch, stream, steps=6):
     return out
 
 
-def bench_ensemble(pkg, torch, stream, n_members=256, steps=3):
-    """Ensemble of independent members, U{128..512}^2 coarse grids, one refined level."""
-    r = 4
-    members = [I.ensemble_member(k) for k in range(n_members)]
+def _ensemble_hierarchy(pkg, stream, ids, r=4):
+    """The ensemble workload's members `ids` (seeded shelves, humps and refined layouts) in one
+    hierarchy, autotuned; returns (hierarchy, chosen tiles)."""
+    members = [I.ensemble_member(k) for k in ids]
     cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=2, ratio=[r], regrid_interval=0, min_side=16, max_side=64)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, m["L"], m["L"], m["n"], m["n"]) for m in members], stream=stream.cuda_stream)
-    for k, m in enumerate(members):
+    for k, (mid, m) in enumerate(zip(ids, members)):
         nf = m["n"] * r
         xf = I.centers(0.0, m["L"], nf)
         Bf = np.ascontiguousarray(np.broadcast_to(I.shelf_B(xf, depth=m["depth"], shelf_x=m["shelf_x"])[None, :],
@@ -473,10 +473,84 @@ def bench_ensemble(pkg, torch, stream, n_members=256, steps=3):
         x0 = I.centers(0.0, m["L"], m["n"])
         X, Y = np.meshgrid(x0, x0)
         H.set_state(k, 0, I.layered_state(B0, I.hump_field(X, Y, *m["humps"]), -200.0 * np.ones_like(B0)))
-        lay = I.random_layout(5100 + k, m["n"] * r, m["n"] * r, max(4, m["n"] // 16), r)
-        H.set_patches(k, 1, lay)
+        H.set_patches(k, 1, I.random_layout(5100 + mid, m["n"] * r, m["n"] * r, max(4, m["n"] // 16), r))
         H.interp_fine(0, k)
     chosen = [H.autotune(l, iters=2) for l in range(2)]
+    return H, chosen
+
+
+def bench_ensemble_partitioned(pkg, torch, stream, rank, ws, n_members=256, steps=3):
+    """The ensemble workload with its members partitioned over the ranks (largest first to the
+    least-loaded rank, by level-0 cells); each rank advances its members in its own batched
+    launches; the job's cell updates are summed and its time is the slowest rank's."""
+    import torch.distributed as dist
+    from paper_1803_01450_gb300 import sharding as S
+    costs = [I.ensemble_member(k)["n"] ** 2 for k in range(n_members)]
+    ids = S.partition_members(costs, ws)[rank]
+    H, _ = _ensemble_hierarchy(pkg, stream, ids)
+    upd = _interior_updates(H, len(ids), 2, [4])
+    H.advance(1)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = _time_advance(torch, H, stream, steps)
+    H.close()
+    tmax = S.max_all(ms, dist, torch.device("cuda", torch.cuda.current_device()))
+    total = S.sum_all(upd * M_LAYERS * steps, dist, torch.device("cuda", torch.cuda.current_device()))
+    return {"workload": f"{n_members} ensemble members partitioned over {ws} ranks", "ranks": ws,
+            "lcups": total / (tmax * 1e-3), "ms_slowest_rank": tmax, "members_per_rank": len(ids)}
+
+
+def bench_slabs(pkg, torch, stream, rank, ws, n=N_CELLS, steps=10, warmup=3):
+    """The headline grid split into slabs of rows over the ranks, two halo rows swapped by
+    NCCL point-to-point sends before every step; owned layer-cell updates of all ranks over the
+    slowest rank's time (strong scaling of one grid)."""
+    import torch.distributed as dist
+    from paper_1803_01450_gb300 import sharding as S
+    w = I.scale(n, seed=1000)
+    sl = S.slab_of(n, ws, rank)
+    dy = 1e5 / n
+    cfg = pkg.Config(M=2, dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, sl.rows * dy, n, sl.rows)], stream=stream.cuda_stream)
+    H.set_bathymetry(0, np.ascontiguousarray(w["B"][sl.lo:sl.hi]))
+    H.set_state(0, 0, np.ascontiguousarray(w["q"][:, sl.lo:sl.hi]))
+    H.set_dt(0, 0.9 * w["dx"] / 205.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def get_rows(r0, k):
+        t = torch.empty((3 * M_LAYERS, k, n), dtype=torch.float64, device=dev)
+        H.get_rows_device(0, 0, r0, k, t.data_ptr())
+        return t
+
+    def set_rows(r0, k, t):
+        H.set_rows_device(0, 0, r0, k, t.data_ptr())
+
+    def step():
+        with torch.cuda.stream(stream):
+            S.halo_exchange(sl, rank, ws, get_rows, set_rows, dist)
+        H.step_level(0)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    H.close()
+    tmax = S.max_all(ms, dist, dev)
+    total = S.sum_all((sl.j1 - sl.j0) * n * M_LAYERS * steps, dist, dev)
+    return {"workload": f"{n}x{n} shelf grid in {ws} slabs of rows, 2 halo rows per shared edge", "ranks": ws,
+            "lcups": total / (tmax * 1e-3), "ms_per_step_slowest_rank": tmax / steps}
+
+
+def bench_ensemble(pkg, torch, stream, n_members=256, steps=3):
+    """Ensemble of independent members, U{128..512}^2 coarse grids, one refined level."""
+    r = 4
+    H, chosen = _ensemble_hierarchy(pkg, stream, list(range(n_members)), r)
     upd = _interior_updates(H, n_members, 2, [r])
     H.advance(1)
     ms_b = _time_advance(torch, H, stream, steps)
@@ -660,6 +734,9 @@ def _summary(line):
     adj = line.get("adjoint")
     if adj:
         out["adjoint_over_forward"] = adj.get("adjoint_over_forward")
+    for key in ("ensemble_partitioned", "slabs"):
+        if key in line:
+            out[key + "_lcups"] = line[key]["lcups"]
     cpu = line.get("cpu_baseline")
     if cpu:
         out["cpu_oracle_lcups"] = cpu["value"]
@@ -788,6 +865,13 @@ def run_gpu(args):
         "e2e": {"value": lcu_per_step * e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(w["q"].nbytes + xy.nbytes), "d2h_bytes_per_step": 32 * M_LAYERS * 8},
     }
+    if ws > 1 and not args.no_amr:
+        # work split over the ranks (every rank takes part): members partitioned, one grid in slabs
+        part = bench_ensemble_partitioned(pkg, torch, stream, rank, ws)
+        slabs = bench_slabs(pkg, torch, stream, rank, ws)
+        if rank == 0:
+            line["ensemble_partitioned"] = part
+            line["slabs"] = slabs
     if rank == 0 and not args.no_amr:
         line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
         line["ensemble"] = bench_ensemble(pkg, torch, stream)

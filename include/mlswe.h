@@ -159,6 +159,15 @@ mlswe_status mlswe_get_bathymetry(mlswe_h h, int member, int level, double* B_ou
 mlswe_status mlswe_set_state(mlswe_h h, int member, int level, const double* q);
 mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out);
 
+/* Rows [j0, j0 + n) of every field of the current state of one level, device to device:
+ * get copies them into dst, set copies src into them; the buffer is device [3M][n][nx]
+ * (caller-owned). Ordered on the hierarchy's stream, no synchronisation (the copy is done
+ * when later work on that stream runs). For the halo rows of a grid split into slabs of
+ * rows across GPUs (not in the paper; the paper's runs share memory, Sec. 3). EINVAL for
+ * rows outside the level or a buffer that is not device memory. */
+mlswe_status mlswe_get_rows_device(mlswe_h h, int member, int level, int j0, int n, double* dst);
+mlswe_status mlswe_set_rows_device(mlswe_h h, int member, int level, int j0, int n, const double* src);
+
 /* Asynchronous input for pipelined runs: q (host [3M][ny][nx], page-locked for the copy to
  * overlap) is copied to a device staging buffer on the library's own copy stream, and
  * from there into the level's state, in order with the work already enqueued on the

@@ -42,14 +42,16 @@ def _compile(out, flags):
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (g++, OpenMP, no FP contraction): the parity build
-    (-O2) and the build the CPU baseline is timed with (-O3, and on Arm hosts tuned for the
-    Grace CPU's Neoverse V2 cores; same arithmetic: no contraction, no reassociation)."""
+    (-O2) and the build the CPU baseline is timed with (-O3, and on Arm hosts scheduled for
+    the Grace CPU's Neoverse V2 cores; same arithmetic: no contraction, no reassociation)."""
     import concurrent.futures as cf
     os.makedirs(_BUILD, exist_ok=True)
     stale = lambda p: force or not os.path.exists(p) or os.path.getmtime(p) < os.path.getmtime(_SRC)
 
     def timing():
-        tuned = ["-O3", "-mcpu=neoverse-v2"] if platform.machine() in ("aarch64", "arm64") else ["-O3"]
+        # scheduling tuned for the Grace CPU's Neoverse V2 cores, no instruction-set extension
+        # (SVE instructions stopped a run with SIGILL on a host that does not enable them)
+        tuned = ["-O3", "-mtune=neoverse-v2"] if platform.machine() in ("aarch64", "arm64") else ["-O3"]
         try:
             _compile(_TIMING_LIB_PATH, tuned)
         except subprocess.CalledProcessError:

@@ -114,6 +114,8 @@ _SIGS = {
     "mlswe_get_bathymetry": [_H, ctypes.c_int, ctypes.c_int, _dp],
     "mlswe_set_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
     "mlswe_set_state_async": [_H, ctypes.c_int, ctypes.c_int, _dp],
+    "mlswe_get_rows_device": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "mlswe_set_rows_device": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "mlswe_read_gauges_async": [_H, ctypes.c_int, ctypes.c_int, _dp, _dp],
     "mlswe_synchronize": [_H],
     "mlswe_get_state": [_H, ctypes.c_int, ctypes.c_int, _dp],
@@ -436,6 +438,16 @@ class Hierarchy:
         """Keep per-edge forward records of the recomputed steps (default) or rebuild them in
         the transposed sweeps; takes effect at the next adjoint_setup."""
         self._check(self.L.mlswe_adjoint_keep_edge_data(self.h, 1 if enable else 0), "adjoint_keep_edge_data")
+
+    def get_rows_device(self, member: int, level: int, j0: int, n: int, dst_ptr: int):
+        """Rows [j0, j0 + n) of the level's state into a device buffer [3M][n][nx] (stream-ordered)."""
+        self._check(self.L.mlswe_get_rows_device(self.h, member, level, j0, n, ctypes.c_void_p(dst_ptr)),
+                    "get_rows_device")
+
+    def set_rows_device(self, member: int, level: int, j0: int, n: int, src_ptr: int):
+        """A device buffer [3M][n][nx] into rows [j0, j0 + n) of the level's state (stream-ordered)."""
+        self._check(self.L.mlswe_set_rows_device(self.h, member, level, j0, n, ctypes.c_void_p(src_ptr)),
+                    "set_rows_device")
 
     def fixed_set_controls(self, eta1_ptr: int, B_ptr: int, eta2: float):
         """Initial state of the gauge-misfit problem from the device controls eta_1(0), B."""

@@ -725,6 +725,44 @@ mlswe_status mlswe_get_state(mlswe_h h, int member, int level, double* q_out) {
   return MLSWE_OK;
 }
 
+// Rows [j0, j0 + n) of every field of the current state, device to device (no host copy,
+// no synchronisation: ordered on the hierarchy's stream).
+static mlswe_status rows_device(mlswe_h h, int member, int level, int j0, int n, double* other, bool to_other,
+                                const char* what) {
+  if (!valid_member_level(h, member, level) || !other || n < 0)
+    return fail(h, MLSWE_EINVAL, std::string(what) + ": bad argument");
+  Level& V = h->mem[member].lev[level];
+  if (j0 < 0 || j0 + n > V.NY) return fail(h, MLSWE_EINVAL, std::string(what) + ": rows outside the level");
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, other) != cudaSuccess ||
+      (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    return fail(h, MLSWE_EINVAL, std::string(what) + ": the buffer must be device memory");
+  }
+  const int F = 3 * h->cfg.M;
+  double* q = V.q[h->parity[level]];
+  const size_t plane = (size_t)V.NY * V.P;
+  for (int f = 0; f < F; ++f) {
+    double* lvl = q + f * plane + (size_t)j0 * V.P;
+    double* buf = other + (size_t)f * n * V.NX;
+    if (to_other)
+      CUDA_TRY(h, cudaMemcpy2DAsync(buf, V.NX * 8, lvl, V.P * 8, V.NX * 8, n, cudaMemcpyDeviceToDevice, h->st));
+    else
+      CUDA_TRY(h, cudaMemcpy2DAsync(lvl, V.P * 8, buf, V.NX * 8, V.NX * 8, n, cudaMemcpyDeviceToDevice, h->st));
+  }
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_get_rows_device(mlswe_h h, int member, int level, int j0, int n, double* dst) {
+  return rows_device(h, member, level, j0, n, dst, true, "get_rows_device");
+}
+
+mlswe_status mlswe_set_rows_device(mlswe_h h, int member, int level, int j0, int n, const double* src) {
+  mlswe_status s = rows_device(h, member, level, j0, n, const_cast<double*>(src), false, "set_rows_device");
+  if (s == MLSWE_OK) h->dt_ready = false;
+  return s;
+}
+
 mlswe_status mlswe_set_dt(mlswe_h h, int level, const double* dt) {
   if (!h || level < 0 || level >= h->L || !dt) return fail(h, MLSWE_EINVAL, "set_dt: bad argument");
   for (int m = 0; m < h->n_members; ++m) {

@@ -1,0 +1,115 @@
+"""Work split across GPUs (one process per GPU, torch.distributed): host-side bookkeeping only.
+
+Two splits of the method's work, both without changing a single arithmetic operation of a
+member's step:
+
+* Ensemble members are independent problems. partition_members assigns whole members to
+  ranks, largest first to the least-loaded rank (by cells per coarse step); a rank builds one
+  hierarchy over its members and advances them in its own batched launches. Only scalars
+  cross ranks (cell updates, times), through all-reduces.
+* One grid split into slabs of rows. A rank holds its rows plus two halo rows on each side
+  that faces another slab (at the domain's own walls the slab keeps the wall). Before every
+  step the ranks swap the two rows next to each shared slab edge; the x sweep then runs over
+  every local row (halo rows included: their rows are complete in x) and the y sweep updates
+  the owned rows from cells at most two rows away, all of them local and current. The rows a
+  rank owns therefore come out exactly as in the undivided grid. The rows beyond a halo (the
+  local array's end, which the solver treats as a wall) only ever feed the halo rows, which
+  the next swap overwrites. A time step common to all slabs is the minimum over the ranks
+  (min_all).
+
+Data moves only by point-to-point sends into local buffers and by scalar all-reduces
+(NCCL on GPUs, gloo on CPUs); the stepping itself is a callable the caller supplies (the
+CUDA library's level step).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+HALO = 2  # rows each side of a shared slab edge: the second-order stencil reaches two cells
+
+
+def partition_members(costs, world_size):
+    """Member indices per rank: members in decreasing cost (ties: lower index first), each to
+    the rank with the least cost so far (ties: lower rank); each rank's list in index order."""
+    order = sorted(range(len(costs)), key=lambda k: (-costs[k], k))
+    load = [0] * world_size
+    out = [[] for _ in range(world_size)]
+    for k in order:
+        r = min(range(world_size), key=lambda j: (load[j], j))
+        out[r].append(k)
+        load[r] += costs[k]
+    return [sorted(v) for v in out]
+
+
+@dataclass(frozen=True)
+class Slab:
+    """Rows [j0, j1) of an ny-row grid owned by a rank; local rows [lo, hi) held (halos)."""
+    j0: int
+    j1: int
+    lo: int
+    hi: int
+
+    @property
+    def rows(self) -> int:
+        return self.hi - self.lo
+
+    @property
+    def own(self) -> slice:
+        """The owned rows as a slice of the local array."""
+        return slice(self.j0 - self.lo, self.j1 - self.lo)
+
+
+def slab_of(ny, world_size, rank):
+    """Even split of ny rows (the first ny % world_size ranks take one more); each slab must
+    own at least HALO rows so that its neighbour's halo lies in it."""
+    base, extra = divmod(ny, world_size)
+    if base < HALO:
+        raise ValueError(f"{ny} rows cannot be split into {world_size} slabs of at least {HALO} rows")
+    j0 = rank * base + min(rank, extra)
+    j1 = j0 + base + (1 if rank < extra else 0)
+    lo = j0 - HALO if rank > 0 else 0
+    hi = j1 + HALO if rank < world_size - 1 else ny
+    return Slab(j0, j1, lo, hi)
+
+
+def halo_exchange(slab: Slab, rank, world_size, get_rows, set_rows, dist, group=None):
+    """Swaps the HALO rows next to every shared slab edge with the neighbouring ranks.
+
+    get_rows(r0, n) returns the local rows [r0, r0 + n) as a contiguous tensor (every field);
+    set_rows(r0, n, t) writes such a tensor back. Sends go out and receives come in as one
+    batch of point-to-point operations, so neither neighbour waits for the other to finish."""
+    ops, recv = [], []
+    if rank > 0:
+        send_lo = get_rows(slab.j0 - slab.lo, HALO)
+        buf_lo = send_lo.new_empty(send_lo.shape)
+        ops += [dist.P2POp(dist.isend, send_lo, rank - 1, group), dist.P2POp(dist.irecv, buf_lo, rank - 1, group)]
+        recv.append((0, buf_lo))
+    if rank < world_size - 1:
+        send_hi = get_rows(slab.j1 - slab.lo - HALO, HALO)
+        buf_hi = send_hi.new_empty(send_hi.shape)
+        ops += [dist.P2POp(dist.isend, send_hi, rank + 1, group), dist.P2POp(dist.irecv, buf_hi, rank + 1, group)]
+        recv.append((slab.j1 - slab.lo, buf_hi))
+    if ops:
+        for req in dist.batch_isend_irecv(ops):
+            req.wait()
+    for r0, buf in recv:
+        set_rows(r0, HALO, buf)
+
+
+def _reduce(value, op, dist, device):
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def sum_all(value, dist, device=None):
+    return _reduce(value, dist.ReduceOp.SUM, dist, device)
+
+
+def max_all(value, dist, device=None):
+    return _reduce(value, dist.ReduceOp.MAX, dist, device)
+
+
+def min_all(value, dist, device=None):
+    return _reduce(value, dist.ReduceOp.MIN, dist, device)
