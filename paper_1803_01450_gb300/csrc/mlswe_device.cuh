@@ -237,26 +237,19 @@ __device__ __forceinline__ double sqrt_fast(double x) {
   return __double_as_longlong(x) >= 0 && moderate(x) ? x * rsqrt_iter(x) : sqrt(x);
 }
 
-// Reciprocals of N <= 6 nonzero numbers with one division:
-// 1/x_p = (1/prod x) * prod_{q != p} x_q, used when every |x_p| lies in [2^-160, 2^160) (so
-// every partial product stays a normal FP64 number); otherwise one division each.
+// Reciprocals of N <= 6 nonzero numbers: when every |x_p| lies in [2^-160, 2^160), each by
+// the seeded iteration (3 FP64 instructions; an earlier form shared one reciprocal of the
+// product among the N values, which costs about 4N + 1); otherwise one division each. One
+// range test for the group keeps the branch structure of the caller simple.
 template <int N>
 __device__ __forceinline__ void batched_reciprocal(const double* x, double* inv) {
-  static_assert(N <= 6, "partial products must stay in range");
+  static_assert(N <= 6, "groups of at most six");
   bool safe = true;
 #pragma unroll
   for (int p = 0; p < N; ++p) safe = safe && moderate(x[p]);
   if (safe) {
-    double pre[N], suf[N];
-    pre[0] = 1.0;
 #pragma unroll
-    for (int p = 1; p < N; ++p) pre[p] = pre[p - 1] * x[p - 1];
-    suf[N - 1] = 1.0;
-#pragma unroll
-    for (int p = N - 2; p >= 0; --p) suf[p] = suf[p + 1] * x[p + 1];
-    const double ip = rcp_iter(pre[N - 1] * x[N - 1]);  // |product| in [2^-960, 2^966)
-#pragma unroll
-    for (int p = 0; p < N; ++p) inv[p] = ip * (pre[p] * suf[p]);
+    for (int p = 0; p < N; ++p) inv[p] = rcp_iter(x[p]);
   } else {
 #pragma unroll
     for (int p = 0; p < N; ++p) inv[p] = rcp(x[p]);
@@ -805,13 +798,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
     den[1] = -l01 * l12 * l13;
     den[2] = l02 * l12 * l23;
     den[3] = -l03 * l13 * l23;
-    const double q01 = den[0] * den[1], q23 = den[2] * den[3];
-    const double iall = rcp_fast(q01 * q23);
     double iden[4];
-    iden[0] = iall * q23 * den[1];
-    iden[1] = iall * q23 * den[0];
-    iden[2] = iall * q01 * den[3];
-    iden[3] = iall * q01 * den[2];
+    batched_reciprocal<4>(den, iden);
     // Numerators: prod_{q != p}(x - l_q) = Q(x)/(x - l_p), Q(x) = x^4 - S1 x^3 + S2 x^2 - S3 x + S4,
     // by synthetic division: coefficients 1, l_p - S1, S2 + l_p (l_p - S1), l_p (...) - S3.
     const double s01 = lam[0] + lam[1], s23 = lam[2] + lam[3];
