@@ -221,6 +221,57 @@ __device__ __forceinline__ double rsqrt_iter(double x) {
   return fma(y, e * fma(0.375, e, 0.5), y);
 }
 
+// 1/x to about 2^-44 relative for a normal x with |x| < 2^1022: the FP32 seed of the leading
+// 23 significand bits (relative error below 2^-22) and one second-order Newton-Raphson step,
+// y' = y + y e with e = 1 - x y (error e^2), 2 FP64 instructions. Only for factors whose own
+// error is multiplied by a small quantity: the Newton corrections of the eigenvalues (their
+// error is the correction times 2^-44, below the rounding of the eigenvalue) and the
+// limiter ratios (an error of 2^-44 in theta moves the limited correction by as little).
+__device__ __forceinline__ double rcp2_iter(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int ex = (int)((hi >> 20) & 0x7ffu);
+  const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));  // in [1, 2)
+  const unsigned r = __float_as_uint(seed_rcp(m));
+  const int re = (int)(r >> 23) - 127;
+  const unsigned long long yb = (b & 0x8000000000000000ull) | ((unsigned long long)(2046 - ex + re) << 52) |
+                                ((unsigned long long)(r & 0x7fffffu) << 29);
+  const double y = __longlong_as_double((long long)yb);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
+// rcp2_iter of N numbers when every |x_p| lies in [2^-160, 2^160) (one range test for the
+// group), one division each otherwise.
+template <int N>
+__device__ __forceinline__ void reciprocal2_group(const double* x, double* inv) {
+  bool safe = true;
+#pragma unroll
+  for (int p = 0; p < N; ++p) safe = safe && moderate(x[p]);
+  if (safe) {
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = rcp2_iter(x[p]);
+  } else {
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = rcp(x[p]);
+  }
+}
+
+// 0.5 / x_p the same way; the factor 1/2 lowers the exponent field of the iterate (exact: for
+// |x_p| in [2^-160, 2^160) the result is a normal number far from the subnormal range).
+template <int N>
+__device__ __forceinline__ void half_reciprocal2_group(const double* x, double* inv) {
+  bool safe = true;
+#pragma unroll
+  for (int p = 0; p < N; ++p) safe = safe && moderate(x[p]);
+  if (safe) {
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = __longlong_as_double(__double_as_longlong(rcp2_iter(x[p])) - (1ll << 52));
+  } else {
+#pragma unroll
+    for (int p = 0; p < N; ++p) inv[p] = 0.5 * rcp(x[p]);
+  }
+}
+
 // The iterations where |x| lies in [2^-160, 2^160) (x > 0 for the square root), the
 // library functions elsewhere (zero, subnormal, huge, infinite, NaN or negative arguments).
 __device__ __forceinline__ double rcp_fast(double x) { return moderate(x) ? rcp_iter(x) : rcp(x); }
@@ -762,11 +813,10 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
           Pl[p] = f1 * f2 - rc;
           dP[p] = a1 * f2 + a2 * f1;  // P'(l) / 2
         }
-        // One reciprocal for the four Newton quotients (the factor 1/2 of P' folded in).
-        const double p01 = dP[0] * dP[1], p23 = dP[2] * dP[3];
-        const double inv = half_rcp_fast(p01 * p23);
-        const double i01 = inv * p23, i23 = inv * p01;
-        const double q[4] = {i01 * dP[1], i01 * dP[0], i23 * dP[3], i23 * dP[2]};  // 1/P'(lambda_p)
+        // The four Newton quotients 1/P'(lambda_p) = (1/2) / dP_p by second-order reciprocals
+        // (the quotient multiplies the correction P / P').
+        double q[4];
+        half_reciprocal2_group<4>(dP, q);
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           lam[p] -= Pl[p] * q[p];
@@ -941,9 +991,9 @@ __device__ __forceinline__ void trans_eigen2(const DevParams& P, const double* h
         const double a1 = lam[p] - ut[0], a2 = lam[p] - ut[1];
         const double f1 = a1 * a1 - c1, f2 = a2 * a2 - c2;
         Pl[p] = f1 * f2 - rc;
-        dP[p] = 2.0 * (a1 * f2 + a2 * f1);
+        dP[p] = a1 * f2 + a2 * f1;  // P'(l) / 2
       }
-      batched_reciprocal<4>(dP, q);
+      half_reciprocal2_group<4>(dP, q);  // 1/P': its error only scales the correction
 #pragma unroll
       for (int p = 0; p < 4; ++p) lam[p] -= Pl[p] * q[p];
     }

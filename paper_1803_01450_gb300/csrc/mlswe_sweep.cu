@@ -364,7 +364,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         }
       }
       double iden[NR];
-      batched_reciprocal_groups<NR>(den, iden);
+      reciprocal2_group<NR>(den, iden);  // limiter ratios: second-order reciprocals suffice
 #pragma unroll
       for (int p = 0; p < NA; ++p) {
         const double s = wav[(WR::S + p) * kMaxEdges + es];
