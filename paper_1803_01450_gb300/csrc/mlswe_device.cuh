@@ -346,7 +346,8 @@ __device__ __forceinline__ void batched_reciprocal_groups(const double* x, doubl
 template <int M>
 struct Rec {
   static constexpr int H = 0;             // h_m at 3m, hn_m at 3m+1, ht_m at 3m+2
-  static constexpr int UN = 3 * M;        // un_m at UN + 2m, ut_m at UN + 2m + 1
+  static constexpr int UN = 3 * M;        // sqrt(h_m) un_m at UN + 2m, sqrt(h_m) ut_m at UN + 2m + 1
+                                          // (0 where not wet): the Roe-average numerators
   static constexpr int SQ = 5 * M;        // sqrt(h_m)
   static constexpr int ETA = 6 * M;       // eta_m
   static constexpr int BB = 7 * M;        // B
@@ -681,8 +682,8 @@ __device__ __forceinline__ void coupled_general(const DevParams& P, const CRec c
   for (int m = 0; m < M; ++m) {
     const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
     const double inv = rcp_fast(sl + sr);
-    uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-    vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+    uh[m] = (cL[R::UN + 2 * m] + cR[R::UN + 2 * m]) * inv;
+    vh[m] = (cL[R::UN + 2 * m + 1] + cR[R::UN + 2 * m + 1]) * inv;
     wq[m] = sqrt_fast(g * hb[m] * P.irho[m]);
   }
   coupling_matrix<M>(P, hb, G);
@@ -767,8 +768,10 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
 #pragma unroll
     for (int n = 0; n < m; ++n) coup += density_ratio<M>(P, n, m) * (cR[3 * n] - cL[3 * n]);
     d0[m] = hnR - hnL;
-    d1[m] = (hnR * cR[R::UN + 2 * m] - hnL * cL[R::UN + 2 * m]) + g * hb[m] * coup;
-    d2[m] = hnR * cR[R::UN + 2 * m + 1] - hnL * cL[R::UN + 2 * m + 1];
+    // hn u = (sqrt(h) u)^2 and hn v = (sqrt(h) u)(sqrt(h) v) from the records
+    const double wL = cL[R::UN + 2 * m], wR = cR[R::UN + 2 * m];
+    d1[m] = (wR * wR - wL * wL) + g * hb[m] * coup;
+    d2[m] = wR * cR[R::UN + 2 * m + 1] - wL * cL[R::UN + 2 * m + 1];
   }
   const int full = (1 << M) - 1;
   if constexpr (M == 2) if (wL == full && wR == full) {
@@ -784,9 +787,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
     double uh[2], vh[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-      const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
-      uh[m] = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv4[m];
-      vh[m] = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv4[m];
+      uh[m] = (cL[R::UN + 2 * m] + cR[R::UN + 2 * m]) * inv4[m];
+      vh[m] = (cL[R::UN + 2 * m + 1] + cR[R::UN + 2 * m + 1]) * inv4[m];
     }
     const double ubar = (hb[0] * uh[0] + hb[1] * uh[1]) * inv4[2];
     const double dc = c1 - c2;
@@ -917,8 +919,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
     if (wl && wr) {
       const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
       const double inv = rcp_fast(sl + sr);
-      const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-      const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+      const double uh = (cL[R::UN + 2 * m] + cR[R::UN + 2 * m]) * inv;
+      const double vh = (cL[R::UN + 2 * m + 1] + cR[R::UN + 2 * m + 1]) * inv;
       // one reciprocal square root gives c = sqrt(g hbar) and 1/(s2 - s1) = 1/(2c)
       const double gh = g * hb[m];
       const double tc = rsqrt_fast(gh);
@@ -932,7 +934,8 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
       if (cw[R::ETA + m] < bhat_d) {
         // Wall for this layer: mirror of the wet side, coupling dropped.
         const double hw = cw[3 * m], hnw = cw[3 * m + 1];
-        const double unw = cw[R::UN + 2 * m], utw = cw[R::UN + 2 * m + 1];
+        const double isw = rcp_fast(cw[R::SQ + m]);  // wet side: u = (sqrt(h) u) / sqrt(h)
+        const double unw = cw[R::UN + 2 * m] * isw, utw = cw[R::UN + 2 * m + 1] * isw;
         // Oriented left -> right: wet left gives (hn, -hn), wet right gives (-hn, hn).
         const double sgn = wl ? 1.0 : -1.0;
         const double e0 = -2.0 * sgn * hnw;
@@ -945,16 +948,16 @@ __device__ __forceinline__ void solve_edge(const DevParams& P, const CRec cL, co
       } else {
         const double sl = cL[R::SQ + m], sr = cR[R::SQ + m];
         const double inv = rcp_fast(sl + sr);
-        const double uh = (sl * cL[R::UN + 2 * m] + sr * cR[R::UN + 2 * m]) * inv;
-        const double vh = (sl * cL[R::UN + 2 * m + 1] + sr * cR[R::UN + 2 * m + 1]) * inv;
+        const double uh = (cL[R::UN + 2 * m] + cR[R::UN + 2 * m]) * inv;
+        const double vh = (cL[R::UN + 2 * m + 1] + cR[R::UN + 2 * m + 1]) * inv;
         const double ch = sqrt(g * hb[m]);
         double s1, s2;
         if (wl) {
-          const double c = sqrt(g * hL), u = cL[R::UN + 2 * m];
+          const double c = sqrt(g * hL), u = cL[R::UN + 2 * m] * rcp_fast(cL[R::SQ + m]);
           s1 = fmin(u - c, uh - ch);
           s2 = u + 2.0 * c;
         } else {
-          const double c = sqrt(g * hR), u = cR[R::UN + 2 * m];
+          const double c = sqrt(g * hR), u = cR[R::UN + 2 * m] * rcp_fast(cR[R::SQ + m]);
           s1 = u - 2.0 * c;
           s2 = fmax(u + c, uh + ch);
         }

@@ -204,10 +204,10 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         const bool w = above && (hbits > tol_bits);
         above = w;
         wet |= w ? (1 << m) : 0;
-        // one reciprocal square root gives both sqrt(h) = h t and 1/h = t t
+        // one reciprocal square root gives sqrt(h) = h t and sqrt(h) u = hn t, sqrt(h) v = ht t
         const double t = hbits > 0 ? rsqrt_fast(h) : 0.0;
         double un = 0.0, ut = 0.0;
-        if (w) { const double ih = t * t; un = hn * ih; ut = ht * ih; }
+        if (w) { un = hn * t; ut = ht * t; }
         rec[R::UN + 2 * m] = un; rec[R::UN + 2 * m + 1] = ut;
         rec[R::SQ + m] = h * t;
       }
