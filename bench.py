@@ -49,6 +49,8 @@ M_LAYERS = 2
 FP64_FLOP_PER_CELL_UPDATE = 1293.25
 # The same count for the three-layer version of the workload (inputs.scale3).
 FP64_FLOP_PER_CELL_UPDATE_3 = 4134.82
+# ... and for the four-layer version (inputs.scale4).
+FP64_FLOP_PER_CELL_UPDATE_4 = 10523.35
 # The unsplit step (transverse Riemann solves) on the same workload, per cell update: each edge
 # pass (x edges, y edges) and the transverse correction fluxes plus the update.
 FP64_FLOP_PER_CELL_UPDATE_UNSPLIT = 2456.89
@@ -302,11 +304,12 @@ def _amr_transfer_bytes(H, n0, r, M):
     return {"ghost_fill": ghost, "average": avg, "reflux": refl}
 
 
-def bench_batched_amr(pkg, torch, stream, steps=3):
-    """Three-level AMR over the shore bathymetry, 1000 + 3000 synthetic patches; then the level
-    transfers per kernel class and one regrid (flag tolerance 5e-5: the humps' slopes are about
-    1e-4, so the regrid refines around them)."""
-    n0, r = 512, 4
+def bench_batched_amr(pkg, torch, stream, steps=3, n0=512, patches=(1000, 3000)):
+    """Three-level AMR over the shore bathymetry, 1000 + 3000 synthetic patches (the figure;
+    smaller coarse grids and patch counts give short cases of the same kernels for profiling);
+    then the level transfers per kernel class and one regrid (flag tolerance 5e-5: the humps'
+    slopes are about 1e-4, so the regrid refines around them)."""
+    r = 4
     nf = n0 * r * r
     L = 1e5
     cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64,
@@ -321,8 +324,8 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
     X, Y = np.meshgrid(x0, x0)
     eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
     H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
-    l1 = I.random_layout(3100, n0 * r, n0 * r, 1000, r)
-    l2 = I.random_layout(3200, nf, nf, 3000, r, parents=l1, margin=2)
+    l1 = I.random_layout(3100, n0 * r, n0 * r, patches[0], r)
+    l2 = I.random_layout(3200, nf, nf, patches[1], r, parents=l1, margin=2)
     H.set_patches(0, 1, l1)
     H.interp_fine(0, 0)
     H.set_patches(0, 2, l2)
@@ -398,7 +401,7 @@ def bench_batched_amr(pkg, torch, stream, steps=3):
     H.close()
     lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
     lp = upd * M_LAYERS * max(1, steps // 2) / (ms_p * 1e-3)
-    return {"workload": "3 levels, 512^2 coarse, ratios 4,4, shore bathymetry, 8 humps; seeded layout of "
+    return {"workload": f"3 levels, {n0}^2 coarse, ratios 4,4, shore bathymetry, 8 humps; seeded layout of "
                         f"{len(l1)} level-1 and {len(l2)} level-2 patches (sides 16..64)",
             "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
             "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
@@ -623,12 +626,15 @@ def bench_adjoint(pkg, torch, stream, n=512, steps=200, ckpt=20, n_g=32):
             "forward_lcups": n * n * M_LAYERS * steps / (fwd * 1e-3), "loss": loss}
 
 
-def bench_three_layers(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
+def bench_three_layers(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3, M=3):
     """The headline workload with three layers (surfaces humps / -100 m / -600 m over the same
-    shelf, densities 1000 / 1020 / 1030): the general M-layer coupled branch in deep water, the
-    per-layer branch on the shelf where the bottom layer ends."""
-    w = I.scale3(n, seed=1000)
-    cfg = pkg.Config(M=3, rho=(1000.0, 1020.0, 1030.0), dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
+    shelf, densities 1000 / 1020 / 1030), or four (humps / -100 / -300 / -600 m, densities
+    1000 / 1020 / 1030 / 1040): the general M-layer coupled branch in deep water, the
+    per-layer branch on the shelf where the lower layers end."""
+    w = I.scale3(n, seed=1000) if M == 3 else I.scale4(n, seed=1000)
+    rho = (1000.0, 1020.0, 1030.0, 1040.0)[:M]
+    flop = FP64_FLOP_PER_CELL_UPDATE_3 if M == 3 else FP64_FLOP_PER_CELL_UPDATE_4
+    cfg = pkg.Config(M=M, rho=rho, dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1)
     H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)], stream=stream.cuda_stream)
     H.set_bathymetry(0, w["B"])
     H.set_state(0, 0, w["q"])
@@ -650,10 +656,11 @@ def bench_three_layers(pkg, torch, stream, n=N_CELLS, steps=10, warmup=3):
     H.close()
     sx_ms, sx_n = per_kernel["sweep_x"]
     x_ms = sx_ms / max(1, sx_n)
-    ach = 0.5 * FP64_FLOP_PER_CELL_UPDATE_3 * n * n / (x_ms * 1e-3) / 1e12
-    return {"workload": f"{n}^2 shelf, 3 layers (humps / -100 m / -600 m), order 2 MC, walls",
-            "lcups": n * n * 3 * steps / (ms * 1e-3), "ms_per_step": ms / steps, "sweep_x_ms": x_ms,
-            "flop_per_cell_update": FP64_FLOP_PER_CELL_UPDATE_3, "achieved_tflops": ach,
+    ach = 0.5 * flop * n * n / (x_ms * 1e-3) / 1e12
+    surf = "-100 m / -600 m" if M == 3 else "-100 m / -300 m / -600 m"
+    return {"workload": f"{n}^2 shelf, {M} layers (humps / {surf}), order 2 MC, walls",
+            "lcups": n * n * M * steps / (ms * 1e-3), "ms_per_step": ms / steps, "sweep_x_ms": x_ms,
+            "flop_per_cell_update": flop, "achieved_tflops": ach,
             "frac_of_fp64_peak": ach / FP64_PEAK_TFLOPS, "tiles": tiles}
 
 
@@ -744,14 +751,20 @@ def _summary(line):
     return out
 
 
-def run_only(name):
+def run_only(name, args=None):
+    import functools
     import torch
     import paper_1803_01450_gb300 as pkg
     pkg.build()
     stream = torch.cuda.Stream()
-    fn = {"amr": bench_batched_amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint_forms,
-          "three": bench_three_layers, "dynrt": bench_dynamic_rt, "unsplit": bench_unsplit}[name]
+    amr = bench_batched_amr
+    if args is not None and args.amr_coarse:
+        a, b = (int(v) for v in args.amr_patches.split(","))
+        amr = functools.partial(bench_batched_amr, n0=args.amr_coarse, patches=(a, b))
+    fn = {"amr": amr, "ensemble": bench_ensemble, "adjoint": bench_adjoint_forms,
+          "three": bench_three_layers, "four": functools.partial(bench_three_layers, M=4), "dynrt": bench_dynamic_rt, "unsplit": bench_unsplit}[name]
     key = {"amr": "batched_amr", "ensemble": "ensemble", "adjoint": "adjoint", "three": "three_layers",
+           "four": "four_layers",
            "dynrt": "dynamic_time_ratio", "unsplit": "unsplit"}[name]
     print(json.dumps({key: fn(pkg, torch, stream)}), flush=True)
 
@@ -877,6 +890,7 @@ def run_gpu(args):
         line["ensemble"] = bench_ensemble(pkg, torch, stream)
         line["adjoint"] = bench_adjoint_forms(pkg, torch, stream)
         line["three_layers"] = bench_three_layers(pkg, torch, stream)
+        line["four_layers"] = bench_three_layers(pkg, torch, stream, M=4)
         line["dynamic_time_ratio"] = bench_dynamic_rt(pkg, torch, stream)
         line["unsplit"] = bench_unsplit(pkg, torch, stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -898,11 +912,14 @@ def main():
     ap.add_argument("--no-amr", action="store_true", help="skip the batched-AMR, ensemble and adjoint figures")
     ap.add_argument("--no-autotune", action="store_true",
                     help="headline sweeps with the default tiles (no tile trials before the timed steps)")
-    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "dynrt", "unsplit"],
+    ap.add_argument("--amr-coarse", type=int, default=0,
+                    help="with --only amr: coarse grid side of a smaller case (default: the 512 figure)")
+    ap.add_argument("--amr-patches", default="1000,3000", help="with --amr-coarse: level-1,level-2 patch counts")
+    ap.add_argument("--only", choices=["amr", "ensemble", "adjoint", "three", "four", "dynrt", "unsplit"],
                     help="print only that secondary figure (a short command for profiling its kernels)")
     args = ap.parse_args()
     if args.only:
-        run_only(args.only)
+        run_only(args.only, args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -1,7 +1,7 @@
 """Prints the algorithmic FP64 operation count per cell update of the method (one x sweep
 plus one y sweep, second order with the MC limiter, eigenvalue guesses plus two Newton
 steps), counted by the oracle's counting scalar on interior rows and columns of the
-2048 x 2048 shelf workload (two layers; its three-layer version; and the unsplit step on
+2048 x 2048 shelf workload (two layers; its three- and four-layer versions; and the unsplit step on
 three 96 x 96 windows of it). Run:
 python -m oracle.count_flops
 
@@ -28,6 +28,11 @@ def main():
     f3 = O.flops_per_cell_update(P3, w3["q"], w3["B"], w3["dx"], w3["dy"], dt, rows=[100, 1024, 1900],
                                  cols=[100, 1024, 1900])
     print(f"three layers (scale3 workload), order=2 eigen=0: {f3:.2f} FP64 operations per cell update")
+    w4 = I.scale4(2048)
+    P4 = O.params(M=4, dry_tol=1e-3, order=2, rho=(1000.0, 1020.0, 1030.0, 1040.0))
+    f4 = O.flops_per_cell_update(P4, w4["q"], w4["B"], w4["dx"], w4["dy"], dt, rows=[100, 1024, 1900],
+                                 cols=[100, 1024, 1900])
+    print(f"four layers (scale4 workload), order=2 eigen=0: {f4:.2f} FP64 operations per cell update")
     Pu = O.params(M=2, dry_tol=1e-3, order=2, unsplit=1)
     fu = O.flops_per_cell_update_unsplit(Pu, w["q"], w["B"], w["dx"], w["dy"], dt,
                                          windows=[(100, 100, 96), (976, 976, 96), (1852, 1852, 96)])

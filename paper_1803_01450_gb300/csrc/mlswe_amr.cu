@@ -30,18 +30,39 @@ __device__ __forceinline__ double minmod_d(double a, double b) {
   return fabs(a) <= fabs(b) ? a : b;
 }
 
+// minmod on the bit patterns (integer unit): 0 when a and b differ in sign or either is zero,
+// else the one of smaller magnitude (a on ties). Equal to minmod_d except where a b
+// underflows to zero for same-signed |a|, |b| below about 1e-154 (minmod_d then gives 0).
+__device__ __forceinline__ double minmod_bits(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  const unsigned long long ax = (unsigned long long)x & 0x7fffffffffffffffull;
+  const unsigned long long ay = (unsigned long long)y & 0x7fffffffffffffffull;
+  if ((x ^ y) < 0 || ax == 0 || ay == 0) return 0.0;
+  return ax <= ay ? a : b;
+}
+
 template <int M>
 __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* qn, double alpha, int i, int j,
                             double* q /*[3M]*/, double& B) {
-  double sx = 1.0, sy = 1.0;
-  if (i < 0) { i = -1 - i; sx = -1.0; } else if (i >= C.NX) { i = 2 * C.NX - 1 - i; sx = -1.0; }
-  if (j < 0) { j = -1 - j; sy = -1.0; } else if (j >= C.NY) { j = 2 * C.NY - 1 - j; sy = -1.0; }
+  // wall mirror: the normal momentum changes sign (on the sign bit)
+  long long sx = 0, sy = 0;
+  constexpr long long kSign = (long long)0x8000000000000000ull;
+  if (i < 0) { i = -1 - i; sx = kSign; } else if (i >= C.NX) { i = 2 * C.NX - 1 - i; sx = kSign; }
+  if (j < 0) { j = -1 - j; sy = kSign; } else if (j >= C.NY) { j = 2 * C.NY - 1 - j; sy = kSign; }
   const size_t o = (size_t)j * C.P + i, plane = (size_t)C.NY * C.P;
-  const double a1 = 1.0 - alpha;
+  if (alpha == 0.0) {  // (1 - 0) q_old + 0 q = q_old
 #pragma unroll
-  for (int f = 0; f < 3 * M; ++f) q[f] = a1 * qo[f * plane + o] + alpha * qn[f * plane + o];
+    for (int f = 0; f < 3 * M; ++f) q[f] = qo[f * plane + o];
+  } else {
+    const double a1 = 1.0 - alpha;
 #pragma unroll
-  for (int m = 0; m < M; ++m) { q[3 * m + 1] *= sx; q[3 * m + 2] *= sy; }
+    for (int f = 0; f < 3 * M; ++f) q[f] = a1 * qo[f * plane + o] + alpha * qn[f * plane + o];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    q[3 * m + 1] = __longlong_as_double(__double_as_longlong(q[3 * m + 1]) ^ sx);
+    q[3 * m + 2] = __longlong_as_double(__double_as_longlong(q[3 * m + 2]) ^ sy);
+  }
   B = C.B[o];
 }
 
@@ -136,6 +157,8 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
     interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
   else if (M == 3)
     interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
+  else if (M == 4)
+    interp_kernel<4><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
   else
     interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
   return cudaGetLastError();
@@ -174,6 +197,9 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
     coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc - 1, q[3], Bc[3]);
     coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc + 1, q[4], Bc[4]);
     // per layer: wet in the coarse cell, its surface and slopes, its momenta and their slopes
+    // (wet tests and minmod on bit patterns: depths are >= 0 and dry_tol >= 0, so h > dry_tol
+    // exactly when bits(h) > bits(dry_tol) as signed integers)
+    const long long tol_bits = __double_as_longlong(P.dry_tol);
     bool wet0[M];
     double eta0[M], se[M][2], c0[M][2], sm[M][2][2];
 #pragma unroll
@@ -184,7 +210,7 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
       for (int c = 0; c < 5; ++c) {
         bool wt = true;
 #pragma unroll
-        for (int n2 = 0; n2 <= m; ++n2) wt = wt && (q[c][3 * n2] > P.dry_tol);
+        for (int n2 = 0; n2 <= m; ++n2) wt = wt && (__double_as_longlong(q[c][3 * n2]) > tol_bits);
         wet[c] = wt;
         double ev = Bc[c];
 #pragma unroll
@@ -193,40 +219,50 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
       }
       wet0[m] = wet[0];
       eta0[m] = eta[0];
-      se[m][0] = minmod_d(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
-      se[m][1] = minmod_d(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
+      se[m][0] = minmod_bits(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
+      se[m][1] = minmod_bits(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int f = 3 * m + 1 + k;
         const double cv = q[0][f];
         c0[m][k] = cv;
-        sm[m][k][0] = minmod_d(wet[1] ? cv - q[1][f] : 0.0, wet[2] ? q[2][f] - cv : 0.0);
-        sm[m][k][1] = minmod_d(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
+        sm[m][k][0] = minmod_bits(wet[1] ? cv - q[1][f] : 0.0, wet[2] ? q[2][f] - cv : 0.0);
+        sm[m][k][1] = minmod_bits(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
       }
     }
-    for (int b = 0; b < r; ++b) {
-      const int J = g.jc * r + b;
-      if (J < g.j0 || J >= g.j1) continue;
-      for (int a = 0; a < r; ++a) {
-        const int I = g.ic * r + a;
-        if (I < g.i0 || I >= g.i1) continue;
+    // fine columns a outer: the x parts eta + sx offx (and the momenta's) once per column
+    for (int a = 0; a < r; ++a) {
+      const int I = g.ic * r + a;
+      if (I < g.i0 || I >= g.i1) continue;
+      const double offx = (a + 0.5) * inv_r - 0.5;
+      double ex[M], mx[M][2];
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        ex[m] = fma(se[m][0], offx, eta0[m]);
+        mx[m][0] = fma(sm[m][0][0], offx, c0[m][0]);
+        mx[m][1] = fma(sm[m][1][0], offx, c0[m][1]);
+      }
+      for (int b = 0; b < r; ++b) {
+        const int J = g.jc * r + b;
+        if (J < g.j0 || J >= g.j1) continue;
         if (Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
         const size_t fo = (size_t)J * Fd.P + I;
-        const double offx = (a + 0.5) * inv_r - 0.5, offy = (b + 0.5) * inv_r - 0.5;
+        const double offy = (b + 0.5) * inv_r - 0.5;
         const double Bf = Fd.B[fo];
         double hf[M], out[F];
 #pragma unroll
         for (int m = M - 1; m >= 0; --m) {
           double hv = 0.0, huv = 0.0, hvv = 0.0;
           if (wet0[m]) {
-            const double ef = eta0[m] + se[m][0] * offx + se[m][1] * offy;
+            const double ef = fma(se[m][1], offy, ex[m]);
             double bh = Bf;
 #pragma unroll
             for (int n2 = M - 1; n2 > m; --n2) bh = bh + hf[n2];
-            hv = fmax(0.0, ef - bh);
-            if (hv > P.dry_tol) {
-              huv = c0[m][0] + sm[m][0][0] * offx + sm[m][0][1] * offy;
-              hvv = c0[m][1] + sm[m][1][0] * offx + sm[m][1][1] * offy;
+            const double d = ef - bh;
+            hv = __double_as_longlong(d) < 0 ? 0.0 : d;  // max(0, d); -0 gives +0
+            if (__double_as_longlong(hv) > tol_bits) {
+              huv = fma(sm[m][0][1], offy, mx[m][0]);
+              hvv = fma(sm[m][1][1], offy, mx[m][1]);
             }
           }
           hf[m] = hv;
@@ -248,6 +284,8 @@ cudaError_t launch_ghost_cells(int M, const DevParams& P, const LevelDesc* descs
     ghost_cells_kernel<1><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   else if (M == 3)
     ghost_cells_kernel<3><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+  else if (M == 4)
+    ghost_cells_kernel<4><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   else
     ghost_cells_kernel<2><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   return cudaGetLastError();
@@ -361,6 +399,7 @@ cudaError_t launch_flags(int M, const LevelDesc* descs, int desc, int par, long 
   const int grid = (int)std::max<long long>(1, std::min<long long>((cells + 255) / 256, 4096));
   if (M == 1) flags_kernel<1><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
   else if (M == 3) flags_kernel<3><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
+  else if (M == 4) flags_kernel<4><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
   else flags_kernel<2><<<grid, 256, 0, st>>>(descs, desc, par, dry_tol, inv_dx, inv_dy, tol2, flags);
   return cudaGetLastError();
 }
@@ -402,6 +441,10 @@ reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict_
               const int* __restrict__ n_dev, int r, int par_c) {
   // One thread per coarse cell of a patch of the coarse level that is not covered and has a
   // covered face neighbour (the host lists them); it corrects its depths for all such edges.
+  // Every read of a thread (coverage of the four neighbours, the coarse fluxes, the r fine
+  // fluxes of each covered edge and layer) is issued before any store, so a thread waits for
+  // memory about once instead of once per read-then-clear pair; the fine accumulators are
+  // cleared afterwards.
   const int n = *n_dev;
   const double inv_r = 1.0 / (double)r;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -410,74 +453,70 @@ reflux_kernel(const LevelDesc* __restrict__ descs, const InterpItem* __restrict_
     const LevelDesc& Fd = descs[cell.desc_f];
     if (C.active != nullptr && *C.active == 0) continue;  // no coarse step taken: nothing to correct
     const int i = cell.i0, j = cell.j0;
-    double* qc = C.q[par_c];
-    const size_t cplane = (size_t)C.NY * C.P;
-    const double dt_c = *C.dt;
     const size_t c = (size_t)j * C.NX + i;
+    // covered face neighbours: west, east, south, north
+    const bool cov[4] = {i > 0 && C.covered[c - 1] != 0, i + 1 < C.NX && C.covered[c + 1] != 0,
+                         j > 0 && C.covered[c - C.NX] != 0, j + 1 < C.NY && C.covered[c + C.NX] != 0};
+    const double dt_c = *C.dt;
+    // first fine flux of each edge (x edges: column I, rows J .. J + r - 1, stride NX_f + 1;
+    // y edges: row J, columns I .. I + r - 1, stride 1) and the coarse flux, per layer
+    double* fbase[4];
+    size_t fstride[4];
+    const double* cflux[4];
+    size_t cstride[4];
+    fbase[0] = Fd.fxf + (size_t)j * r * (Fd.NX + 1) + (size_t)i * r;
+    fbase[1] = Fd.fxf + (size_t)j * r * (Fd.NX + 1) + (size_t)(i + 1) * r;
+    fbase[2] = Fd.fyf + (size_t)j * r * Fd.NX + (size_t)i * r;
+    fbase[3] = Fd.fyf + (size_t)(j + 1) * r * Fd.NX + (size_t)i * r;
+    fstride[0] = fstride[1] = (size_t)Fd.NX + 1;
+    fstride[2] = fstride[3] = 1;
+    const size_t fxplane = (size_t)Fd.NY * (Fd.NX + 1), fyplane = (size_t)(Fd.NY + 1) * Fd.NX;
+    cflux[0] = C.fxc + (size_t)j * (C.NX + 1) + i;
+    cflux[1] = C.fxc + (size_t)j * (C.NX + 1) + i + 1;
+    cflux[2] = C.fyc + (size_t)j * C.NX + i;
+    cflux[3] = C.fyc + (size_t)(j + 1) * C.NX + i;
+    cstride[0] = cstride[1] = (size_t)C.NY * (C.NX + 1);
+    cstride[2] = cstride[3] = (size_t)(C.NY + 1) * C.NX;
+    double fine[4][M], coarse[4][M];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        fine[d][m] = 0.0;
+        coarse[d][m] = 0.0;
+        if (cov[d]) {
+          const double* fp = fbase[d] + (size_t)m * (d < 2 ? fxplane : fyplane);
+          double sum = 0.0;
+#pragma unroll 4
+          for (int k = 0; k < r; ++k) sum += fp[k * fstride[d]];
+          fine[d][m] = sum;
+          coarse[d][m] = cflux[d][m * cstride[d]];
+        }
+      }
     double dh[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) dh[m] = 0.0;
-    // west edge (i - 1/2): neighbour i-1 covered, this cell on the right: h -= corr
-    if (i > 0 && C.covered[c - 1]) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        double fine = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < r; ++k) {
-          const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)i * r;
-          fine += Fd.fxf[fo];
-          Fd.fxf[fo] = 0.0;
-        }
-        const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i];
-        dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dx;
-      }
+    for (int m = 0; m < M; ++m) {
+      // west / south: this cell on the right of the edge, h -= corr; east / north: h += corr
+      dh[m] = 0.0;
+      if (cov[0]) dh[m] -= (dt_c * coarse[0][m] - fine[0][m] * inv_r) * C.inv_dx;
+      if (cov[1]) dh[m] += (dt_c * coarse[1][m] - fine[1][m] * inv_r) * C.inv_dx;
+      if (cov[2]) dh[m] -= (dt_c * coarse[2][m] - fine[2][m] * inv_r) * C.inv_dy;
+      if (cov[3]) dh[m] += (dt_c * coarse[3][m] - fine[3][m] * inv_r) * C.inv_dy;
     }
-    // east edge (i + 1/2): neighbour i+1 covered, this cell on the left: h += corr
-    if (i + 1 < C.NX && C.covered[c + 1]) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        double fine = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < r; ++k) {
-          const size_t fo = ((size_t)m * Fd.NY + (size_t)j * r + k) * (Fd.NX + 1) + (size_t)(i + 1) * r;
-          fine += Fd.fxf[fo];
-          Fd.fxf[fo] = 0.0;
-        }
-        const double Fc = C.fxc[((size_t)m * C.NY + j) * (C.NX + 1) + i + 1];
-        dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dx;
-      }
-    }
-    if (j > 0 && C.covered[c - C.NX]) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        double fine = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < r; ++k) {
-          const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)j * r) * Fd.NX + (size_t)i * r + k;
-          fine += Fd.fyf[fo];
-          Fd.fyf[fo] = 0.0;
-        }
-        const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j) * C.NX + i];
-        dh[m] -= (dt_c * Fc - fine * inv_r) * C.inv_dy;
-      }
-    }
-    if (j + 1 < C.NY && C.covered[c + C.NX]) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        double fine = 0.0;
-#pragma unroll 4
-        for (int k = 0; k < r; ++k) {
-          const size_t fo = ((size_t)m * (Fd.NY + 1) + (size_t)(j + 1) * r) * Fd.NX + (size_t)i * r + k;
-          fine += Fd.fyf[fo];
-          Fd.fyf[fo] = 0.0;
-        }
-        const double Fc = C.fyc[((size_t)m * (C.NY + 1) + j + 1) * C.NX + i];
-        dh[m] += (dt_c * Fc - fine * inv_r) * C.inv_dy;
-      }
-    }
+    double* qc = C.q[par_c];
+    const size_t cplane = (size_t)C.NY * C.P;
 #pragma unroll
     for (int m = 0; m < M; ++m)
       if (dh[m] != 0.0) qc[(3 * m) * cplane + (size_t)j * C.P + i] += dh[m];
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+      if (cov[d])
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          double* fp = fbase[d] + (size_t)m * (d < 2 ? fxplane : fyplane);
+#pragma unroll 4
+          for (int k = 0; k < r; ++k) fp[k * fstride[d]] = 0.0;
+        }
   }
 }
 
@@ -485,6 +524,7 @@ cudaError_t launch_reflux(int M, const LevelDesc* descs, const InterpItem* cells
                           int r, int par_c, cudaStream_t st) {
   if (M == 1) reflux_kernel<1><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
   else if (M == 3) reflux_kernel<3><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
+  else if (M == 4) reflux_kernel<4><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
   else reflux_kernel<2><<<grid, 256, 0, st>>>(descs, cells, n_dev, r, par_c);
   return cudaGetLastError();
 }
@@ -533,6 +573,7 @@ cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, cons
                          cudaStream_t st) {
   if (M == 1) speed_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
   else if (M == 3) speed_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
+  else if (M == 4) speed_kernel<4><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
   else speed_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_of_desc, out);
   return cudaGetLastError();
 }

@@ -597,10 +597,24 @@ __device__ __forceinline__ void gauss_solve_multi(double (&A)[N][N], double (&b)
 // = 1) of the coupled three-layer system with velocities u, mean depths hb and coupling G,
 // from mu_k (the eigenvalues of G): the guesses, the loss-of-hyperbolicity test (returned),
 // two Newton steps and Cramer's rule, as described above.
+__device__ __forceinline__ double det3(double a00, double a01, double a02, double a10, double a11, double a12,
+                                      double a20, double a21, double a22) {
+  return a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+}
+
+// Determinant of the 3 x 3 matrix of A without row r and column c (4 x 4 A; r, c compile-time
+// constants after unrolling).
+template <int R, int C>
+__device__ __forceinline__ double minor4(const double A[4][4]) {
+  constexpr int r0 = R == 0 ? 1 : 0, r1 = R <= 1 ? 2 : 1, r2 = R <= 2 ? 3 : 2;
+  constexpr int c0 = C == 0 ? 1 : 0, c1 = C <= 1 ? 2 : 1, c2 = C <= 2 ? 3 : 2;
+  return det3(A[r0][c0], A[r0][c1], A[r0][c2], A[r1][c0], A[r1][c1], A[r1][c2], A[r2][c0], A[r2][c1], A[r2][c2]);
+}
+
 template <int M>
 __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M][M], const double* u,
                                             const double* hb, const double* mu, double* lam, double dh[][M]) {
-  static_assert(M == 3, "general coupled branch written for three layers");
+  static_assert(M == 3 || M == 4, "general coupled branch written for three and four layers");
   constexpr int N = 2 * M;
   const double g = P.g;
   double hs = 0.0, hus = 0.0;
@@ -636,14 +650,22 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
       for (int p = 0; p < N; ++p) {
         double A[M][M];
         build_A(lam[p], A);
-        const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
-        const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
-        const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-        Pl[p] = A[0][0] * c00 - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-        dP[p] = 2.0 * ((lam[p] - u[0]) * c00 + (lam[p] - u[1]) * c11 + (lam[p] - u[2]) * c22);
+        if constexpr (M == 3) {
+          const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+          const double c11 = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+          const double c22 = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+          Pl[p] = A[0][0] * c00 - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                  A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+          dP[p] = 2.0 * ((lam[p] - u[0]) * c00 + (lam[p] - u[1]) * c11 + (lam[p] - u[2]) * c22);
+        } else {
+          // det A by the first row; P' = sum_m 2 (l - u_m) cof_mm (d/dl of the diagonal)
+          const double c00 = minor4<0, 0>(A), c11 = minor4<1, 1>(A), c22 = minor4<2, 2>(A), c33 = minor4<3, 3>(A);
+          Pl[p] = A[0][0] * c00 - A[0][1] * minor4<0, 1>(A) + A[0][2] * minor4<0, 2>(A) - A[0][3] * minor4<0, 3>(A);
+          dP[p] = 2.0 * ((lam[p] - u[0]) * c00 + (lam[p] - u[1]) * c11 + (lam[p] - u[2]) * c22 +
+                         (lam[p] - u[3]) * c33);
+        }
       }
-      batched_reciprocal<N>(dP, idP);
+      batched_reciprocal_groups<N>(dP, idP);
 #pragma unroll
       for (int p = 0; p < N; ++p) lam[p] -= Pl[p] * idP[p];
     }
@@ -652,11 +674,19 @@ __device__ __forceinline__ bool general_eig(const DevParams& P, const double G[M
   for (int p = 0; p < N; ++p) {
     double A[M][M];
     build_A(lam[p], A);
-    const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-    const double id2 = rcp_fast(det2);
     dh[p][0] = 1.0;
-    dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
-    dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
+    if constexpr (M == 3) {
+      const double det2 = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+      const double id2 = rcp_fast(det2);
+      dh[p][1] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id2;
+      dh[p][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id2;
+    } else {
+      // rows 0..2 of A dh = 0 with dh_1 = 1: sum_{c >= 1} A[r][c] dh_c = -A[r][0], by Cramer
+      const double id = rcp_fast(det3(A[0][1], A[0][2], A[0][3], A[1][1], A[1][2], A[1][3], A[2][1], A[2][2], A[2][3]));
+      dh[p][1] = -det3(A[0][0], A[0][2], A[0][3], A[1][0], A[1][2], A[1][3], A[2][0], A[2][2], A[2][3]) * id;
+      dh[p][2] = -det3(A[0][1], A[0][0], A[0][3], A[1][1], A[1][0], A[1][3], A[2][1], A[2][0], A[2][3]) * id;
+      dh[p][3] = -det3(A[0][1], A[0][2], A[0][0], A[1][1], A[1][2], A[1][0], A[2][1], A[2][2], A[2][0]) * id;
+    }
   }
   return lst;
 }
@@ -673,7 +703,7 @@ template <int M, class CRec>
 __device__ __forceinline__ void coupled_general(const DevParams& P, const CRec cL, const CRec cR,
                                                 const double* hb, const double* d0, const double* d1,
                                                 const double* d2, EdgeW<M>& W, int& lost) {
-  static_assert(M == 3, "general coupled branch written for three layers");
+  static_assert(M == 3 || M == 4, "general coupled branch written for three and four layers");
   using R = Rec<M>;
   constexpr int N = 2 * M;
   const double g = P.g;

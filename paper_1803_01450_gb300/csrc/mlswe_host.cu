@@ -453,11 +453,12 @@ mlswe_status mlswe_create_hierarchy(const mlswe_config* cfg, int n_members, cons
                                     const mlswe_allocator* alloc, void* cuda_stream, mlswe_h* out) {
   if (!cfg || !doms || !out || n_members <= 0) return MLSWE_EINVAL;
   *out = nullptr;
-  if (cfg->M < 1 || cfg->M > 3 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
+  if (cfg->M < 1 || cfg->M > 4 || cfg->max_levels < 1 || cfg->max_levels > 4) return MLSWE_EINVAL;
   if (cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2) return MLSWE_EINVAL;
   if (cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->dry_tol >= 0.0) || !(cfg->g > 0.0)) return MLSWE_EINVAL;
   if (cfg->dynamic_rt < 0 || cfg->dynamic_rt > 1) return MLSWE_EINVAL;
   if (cfg->unsplit < 0 || cfg->unsplit > 1) return MLSWE_EINVAL;
+  if (cfg->unsplit && cfg->M > 3) return MLSWE_EINVAL;  // the transverse solves take at most three layers
   if (cfg->M >= 2 && !(cfg->rho[0] > 0.0)) return MLSWE_EINVAL;
   for (int m = 0; m + 1 < cfg->M; ++m)  // densities increase downwards (stable stratification)
     if (!(cfg->rho[m] < cfg->rho[m + 1])) return MLSWE_EINVAL;

@@ -571,9 +571,11 @@ static cudaError_t launch_sweep_m(int ctas, const DevParams& P, const LevelDesc*
                                                                  smax_bits, lost_count, st, est, eplane);
   }
   if constexpr (M >= 3) {  // three layers fill the register file and shared memory: one CTA per SM
-    if (P.unsplit)
-      return launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
-                                                    lost_count, st, nullptr, 0);
+    if constexpr (M == 3) {
+      if (P.unsplit)
+        return launch_sweep_t<M, DIR, 1, false, true>(P, descs, items, n_items_dev, tile_off, grid, parity, record,
+                                                      smax_bits, lost_count, st, nullptr, 0);
+    }
     return launch_sweep_t<M, DIR, 1, false, false>(P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                                    lost_count, st, nullptr, 0);
   } else {
@@ -604,6 +606,11 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
     return dir == 0 ? launch_sweep_m<3, 0>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0)
                     : launch_sweep_m<3, 1>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0);
+  if (P.M == 4)  // split step only (the host refuses the unsplit step for four layers)
+    return dir == 0 ? launch_sweep_m<4, 0>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
+                                           lost_count, st, nullptr, 0)
+                    : launch_sweep_m<4, 1>(1, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                            lost_count, st, nullptr, 0);
   return dir == 0 ? launch_sweep_m<2, 0>(c, P, descs, items, n_items_dev, tile_off, grid, parity, record, smax_bits,
                                          lost_count, st, est, eplane)

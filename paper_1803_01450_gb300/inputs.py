@@ -108,6 +108,30 @@ def shore3(n: int, seed: int = 3000, L: float = 1e5, n_humps: int = 8):
     return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
 
 
+def shore4(n: int, seed: int = 3000, L: float = 1e5, n_humps: int = 8):
+    """Four-layer shore workload on an n x n grid: surfaces humps / -50 m / -120 m / -250 m
+    over the shore bathymetry, so the lower layers meet the rising ground one after another."""
+    x = centers(0.0, L, n)
+    X, Y = np.meshgrid(x, x)
+    B = shore_B(X)
+    A, w, xc, yc = humps(seed, n_humps, L)
+    eta1 = hump_field(X, Y, A, w, xc, yc)
+    q = stacked_state(B, (eta1, -50.0 + 0.0 * X, -120.0 + 0.0 * X, -250.0 + 0.0 * X))
+    return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
+
+
+def scale4(n: int = 2048, seed: int = 1000, L: float = 1e5):
+    """Four-layer version of the scale workload: the same shelf and humps, surfaces
+    humps / -100 m / -300 m / -600 m (the lower layers end where the shelf rises above them)."""
+    x = centers(0.0, L, n)
+    X, Y = np.meshgrid(x, x)
+    B = shelf_B(X)
+    A, w, xc, yc = humps(seed, 8, L)
+    eta1 = hump_field(X, Y, A, w, xc, yc)
+    q = stacked_state(B, (eta1, -100.0 + 0.0 * X, -300.0 + 0.0 * X, -600.0 + 0.0 * X))
+    return dict(q=q, B=B, dx=L / n, dy=L / n, domain=(0.0, 0.0, L, L), dry_tol=1e-3)
+
+
 def small(n: int = 50):
     x = centers(0.0, 1.0, n)
     X, Y = np.meshgrid(x, x)
