@@ -4,7 +4,7 @@
  * Paper: A. Schwarzschild and K. Mandli, "An Implementation of Adaptive Mesh
  * Refinement for Shallow Water Equations", arXiv:1803.01450.
  *
- * The library advances an M-layer (M = 1, 2 or 3) shallow-water model on a
+ * The library advances an M-layer (M = 1 to 4) shallow-water model on a
  * hierarchy of refinement levels (Sec. 2, Eqs. (1)-(2): dx^{l+1} = dx^l / r^l)
  * for one or more independent ensemble members, in FP64 on one GPU. Layer 1 is
  * the top layer (Sec. 2.1). The conserved fields of a cell are, per layer m,
@@ -65,11 +65,11 @@ typedef struct {
 } mlswe_allocator;
 
 /* Model and AMR configuration.
- *  M            layers (1, 2 or 3); rho[0..M-1] densities, increasing downwards
- *               (rho[0] < rho[1] < rho[2]). M = 3 couples the layers through the
+ *  M            layers (1 to 4); rho[0..M-1] densities, increasing downwards
+ *               (rho[0] < rho[1] < ...). M = 3 and 4 couple the layers through the
  *               general M-layer eigenproblem (the paper's Eqs. (4)-(5) hold for any
- *               M) and runs one CTA per SM; mlswe_step_fixed_noalloc and the
- *               adjoint take M <= 2.
+ *               M) and run one CTA per SM; mlswe_step_fixed_noalloc and the
+ *               adjoint take M <= 2, the unsplit step M <= 3.
  *  g            gravity; dry_tol: layer m is wet where h_m > dry_tol and every
  *               layer above is wet (top-down rule, Sec. 2.1).
  *  cfl_desired  target Courant number for the automatic time step;
