@@ -164,6 +164,9 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
   return cudaGetLastError();
 }
 
+// Launched in blocks of 64 threads (four times the blocks of the flat grid): a level's list
+// of ring cells often fills only a fraction of the GPU, and small blocks spread it over every
+// SM instead of giving some SMs two large blocks and others none.
 // Ghost fill (the refinement above applied to the ring cells of the patches) organised per
 // coarse cell: the thread of a coarse cell under a ghost strip loads it and its four face
 // neighbours once, forms the wet flags, surfaces and minmod slopes of every layer once, and
@@ -281,13 +284,13 @@ cudaError_t launch_ghost_cells(int M, const DevParams& P, const LevelDesc* descs
                                const int* n_dev, int grid, int r, int par_c, int par_f, double alpha, int substep,
                                cudaStream_t st) {
   if (M == 1)
-    ghost_cells_kernel<1><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+    ghost_cells_kernel<1><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   else if (M == 3)
-    ghost_cells_kernel<3><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+    ghost_cells_kernel<3><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   else if (M == 4)
-    ghost_cells_kernel<4><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+    ghost_cells_kernel<4><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   else
-    ghost_cells_kernel<2><<<grid, 256, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+    ghost_cells_kernel<2><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
   return cudaGetLastError();
 }
 
