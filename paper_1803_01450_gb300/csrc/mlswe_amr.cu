@@ -315,9 +315,13 @@ cudaError_t launch_set_active(int L, int n_members, int level, int k, const int*
 // mean of their r x r fine cells (row-major sum, then times 1/(r r)), every component.
 // Items: (desc_c, desc_f, coarse box).
 // ---------------------------------------------------------------------------
+// RC: the ratio as a compile-time constant (2 or 4; 0: the runtime r), so that the r x r loads
+// of a field are unrolled and in flight together; the sum keeps the row-major order.
+template <int RC>
 __global__ void __launch_bounds__(256)
 average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-                     const int* __restrict__ n_items_dev, int r, int par_c, int par_f) {
+                     const int* __restrict__ n_items_dev, int r_rt, int par_c, int par_f) {
+  const int r = RC > 0 ? RC : r_rt;
   const double inv = 1.0 / (double)(r * r);
   const int n_items = *n_items_dev;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -327,15 +331,26 @@ average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpIte
     if (C.active != nullptr && *C.active == 0) continue;  // the coarse level copied its state through
     const int w = item.i1 - item.i0, h = item.j1 - item.j0;
     const int total = w * h;
-    const double* qf = Fd.q[par_f];
-    double* qc = C.q[par_c];
+    const double* __restrict__ qf = Fd.q[par_f];
+    double* __restrict__ qc = C.q[par_c];
     const size_t fplane = (size_t)Fd.NY * Fd.P, cplane = (size_t)C.NY * C.P;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int i = item.i0 + t % w, j = item.j0 + t / w;
       for (int f = 0; f < F; ++f) {
+        const double* __restrict__ src = qf + f * fplane + (size_t)(j * r) * Fd.P + (size_t)i * r;
         double s = 0.0;
-        for (int b = 0; b < r; ++b)
-          for (int a = 0; a < r; ++a) s += qf[f * fplane + (size_t)(j * r + b) * Fd.P + (i * r + a)];
+        if constexpr (RC > 0) {
+          double v[RC * RC];
+#pragma unroll
+          for (int b = 0; b < RC; ++b)
+#pragma unroll
+            for (int a = 0; a < RC; ++a) v[b * RC + a] = src[(size_t)b * Fd.P + a];
+#pragma unroll
+          for (int k = 0; k < RC * RC; ++k) s += v[k];
+        } else {
+          for (int b = 0; b < r; ++b)
+            for (int a = 0; a < r; ++a) s += src[(size_t)b * Fd.P + a];
+        }
         qc[f * cplane + (size_t)j * C.P + i] = s * inv;
       }
     }
@@ -344,7 +359,9 @@ average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpIte
 
 cudaError_t launch_average_items(int F, const LevelDesc* descs, const InterpItem* items, const int* n_items_dev,
                                  int grid, int r, int par_c, int par_f, cudaStream_t st) {
-  average_items_kernel<<<grid, 256, 0, st>>>(F, descs, items, n_items_dev, r, par_c, par_f);
+  if (r == 4) average_items_kernel<4><<<grid, 256, 0, st>>>(F, descs, items, n_items_dev, r, par_c, par_f);
+  else if (r == 2) average_items_kernel<2><<<grid, 256, 0, st>>>(F, descs, items, n_items_dev, r, par_c, par_f);
+  else average_items_kernel<0><<<grid, 256, 0, st>>>(F, descs, items, n_items_dev, r, par_c, par_f);
   return cudaGetLastError();
 }
 
