@@ -400,10 +400,10 @@ mlswe_status mlswe_fixed_backward_state(mlswe_h h, double* dL_dq0, double* dL_dB
  * managed) memory (MLSWE_EINVAL otherwise, checked before any GPU work). The solver's working memory (state after the x sweep,
  * tile lists, descriptor, time step, wave-speed slots) lives in one static
  * device array of about 16 MB that every GPU loading the library holds until
- * the process exits; grids up to nx * ny <= 512 * 512 cells (nx, ny >= 4) fit,
- * larger ones return MLSWE_EINVAL. The first call on a device looks up that
- * array's device address (a runtime query, not stream work), so make that first
- * call before any stream capture. All calls
+ * the process exits; grids of M * nx * ny <= 2 * 512 * 512 layer cells (nx, ny >= 4;
+ * 512 x 512 cells for one or two layers) fit, larger ones return MLSWE_EINVAL. M is
+ * 1 to 4, densities strictly increasing downwards. The first call on a device looks up that
+ * array's device address (a runtime query, not stream work). All calls
  * share the array: calls that overlap on the GPU race and must be serialised
  * by the caller. Uses the model settings of cfg (M, rho, g, dry_tol, order,
  * limiter, eigen); work is issued on cuda_stream. cfl_out (host, may be NULL)

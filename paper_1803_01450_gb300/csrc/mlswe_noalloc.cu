@@ -24,11 +24,12 @@
 
 namespace mlswe {
 
-// Largest grid the scratch array holds: nx * ny <= 512 * 512 cells (the state after
-// the x sweep of up to two layers, 12.6 MB) and up to 65536 tiles per sweep.
-constexpr long long kNoAllocMaxCells = 512LL * 512LL;
+// Largest grid the scratch array holds: the state after the x sweep of M * nx * ny <=
+// 2 * 512 * 512 layer cells (12.6 MB: 512 x 512 cells for one or two layers, fewer cells for
+// three or four) and up to 65536 tiles per sweep.
+constexpr long long kNoAllocMaxLayerCells = 2LL * 512LL * 512LL;
 constexpr int kNoAllocMaxItems = 65536;
-constexpr size_t kNoAllocQsBytes = (size_t)6 * kNoAllocMaxCells * sizeof(double);
+constexpr size_t kNoAllocQsBytes = (size_t)3 * kNoAllocMaxLayerCells * sizeof(double);
 constexpr size_t kNoAllocItemBytes = (size_t)kNoAllocMaxItems * sizeof(SweepItem);
 constexpr size_t kNoAllocHeadBytes = 1024;  // descriptor, item counts, dt, wave-speed slots
 constexpr size_t kNoAllocBytes = kNoAllocHeadBytes + 2 * kNoAllocItemBytes + kNoAllocQsBytes;
@@ -97,12 +98,14 @@ extern "C" mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx
                                                  double dt, const double* q_in, const double* B, double* q_out,
                                                  void* cuda_stream, double* cfl_out) {
   if (!cfg || !q_in || !B || !q_out || cfg->unsplit != 0) return MLSWE_EINVAL;
-  if (cfg->M < 1 || cfg->M > 2 || cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2 ||
+  if (cfg->M < 1 || cfg->M > 4 || cfg->order < 1 || cfg->order > 2 || cfg->limiter < 0 || cfg->limiter > 2 ||
       cfg->eigen < 0 || cfg->eigen > 1 || !(cfg->g > 0.0) || !(cfg->dry_tol >= 0.0))
     return MLSWE_EINVAL;
-  if (cfg->M == 2 && !(cfg->rho[0] > 0.0 && cfg->rho[0] < cfg->rho[1])) return MLSWE_EINVAL;
+  if (cfg->M >= 2 && !(cfg->rho[0] > 0.0)) return MLSWE_EINVAL;
+  for (int m = 0; m + 1 < cfg->M; ++m)  // densities increase downwards (stable stratification)
+    if (!(cfg->rho[m] < cfg->rho[m + 1])) return MLSWE_EINVAL;
   if (nx < 4 || ny < 4 || !(dx > 0.0) || !(dy > 0.0) || !(dt >= 0.0)) return MLSWE_EINVAL;
-  if ((long long)nx * ny > kNoAllocMaxCells) return MLSWE_EINVAL;  // grid larger than the scratch array
+  if ((long long)cfg->M * nx * ny > kNoAllocMaxLayerCells) return MLSWE_EINVAL;  // larger than the scratch array
   // The buffers: device memory the kernels can read and write, and an output that shares
   // no byte with either input (the sweeps read q_in and B while they write q_out).
   const size_t state_bytes = (size_t)3 * cfg->M * nx * ny * sizeof(double);

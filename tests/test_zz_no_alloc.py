@@ -92,6 +92,48 @@ def test_noalloc_step_matches_hierarchy_two_calls(mlswe_lib):
     assert st == EINVAL
 
 
+RHO = {1: (1000.0,), 3: (1000.0, 1020.0, 1030.0), 4: (1000.0, 1020.0, 1030.0, 1040.0)}
+
+
+@pytest.mark.parametrize("M", [1, 3, 4])
+def test_noalloc_step_matches_oracle_other_layer_counts(mlswe_lib, M):
+    """One, three and four layers (Eqs. (4)-(5) for any M): three calls in a row against the
+    oracle's walled step, each field within 1e-11 of its scale; the size limit is by layer
+    cells (M nx ny <= 2 x 512 x 512)."""
+    import torch
+    from conftest import report, state_err
+
+    pkg = mlswe_lib
+    fn = _entry(pkg)
+    ny, nx = 57, 90
+    depth = {1: (0.5,), 3: (0.4, 0.3, 0.6), 4: (0.4, 0.3, 0.35, 0.6)}[M]
+    q0, B = I.gaussian_random_state(60 + M, M, nx, ny, depth=depth, vel=0.01)
+    dx, dy = 1.0 / nx, 1.2 / ny
+    dt = 0.2 * min(dx, dy) / 4.0
+    ccfg = pkg.Config(M=M, rho=RHO[M], dry_tol=1e-6, order=2, limiter=2, max_levels=1).to_c()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    a = torch.tensor(q0, dtype=torch.float64, device=dev).contiguous()
+    b = torch.empty_like(a)
+    Bt = torch.tensor(B, dtype=torch.float64, device=dev).contiguous()
+    P = O.params(M=M, rho=RHO[M], dry_tol=1e-6, order=2, limiter=2)
+    qo = q0.copy()
+    for k in range(3):
+        src, dst = (a, b) if k % 2 == 0 else (b, a)
+        assert fn(ctypes.byref(ccfg), nx, ny, dx, dy, dt, src.data_ptr(), Bt.data_ptr(), dst.data_ptr(), stream,
+                  None) == 0
+        qo, _, _ = O.step_walled(P, qo, B, dx, dy, dt)
+    torch.cuda.synchronize()
+    err = state_err(b.cpu().numpy(), qo, M)
+    report(f"noalloc_M{M}_{ny}x{nx}_3steps", err)
+    assert err.max() < TOL, err
+    side = int((2 * 512 * 512 // M) ** 0.5)
+    rows = 2 * 512 * 512 // (M * side) + 1  # one row more than the array holds
+    assert M * side * (rows - 1) <= 2 * 512 * 512 < M * side * rows
+    assert fn(ctypes.byref(ccfg), side, rows, dx, dy, dt, a.data_ptr(), Bt.data_ptr(), b.data_ptr(), stream,
+              None) == EINVAL
+
+
 def test_noalloc_rejects_host_and_overlapping_buffers(mlswe_lib):
     """Host arrays (which a kernel would fault on) and an output that overlaps an input are
     refused with EINVAL before any launch; the outputs stay untouched."""
