@@ -68,8 +68,8 @@ typedef struct {
  *  M            layers (1 to 4); rho[0..M-1] densities, increasing downwards
  *               (rho[0] < rho[1] < ...). M = 3 and 4 couple the layers through the
  *               general M-layer eigenproblem (the paper's Eqs. (4)-(5) hold for any
- *               M) and run one CTA per SM; mlswe_step_fixed_noalloc and the
- *               adjoint take M <= 2, the unsplit step M <= 3.
+ *               M) and run one CTA per SM; the adjoint takes M <= 2, the
+ *               unsplit step M <= 3.
  *  g            gravity; dry_tol: layer m is wet where h_m > dry_tol and every
  *               layer above is wet (top-down rule, Sec. 2.1).
  *  cfl_desired  target Courant number for the automatic time step;

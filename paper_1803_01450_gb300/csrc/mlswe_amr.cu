@@ -173,13 +173,13 @@ cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, con
 // then reconstructs each of its r x r fine cells that lies in the strip and in no patch of
 // the fine level (the per-fine-cell form recomputes all of that for every fine cell). Same
 // formulas per fine cell as interp_kernel.
-template <int M>
+template <int M, int R>
 __global__ void __launch_bounds__(256)
 ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const GhostCell* __restrict__ cells,
-                   const int* __restrict__ n_dev, int r, int par_c, int par_f, double alpha_in, int substep) {
+                   const int* __restrict__ n_dev, int par_c, int par_f, double alpha_in, int substep) {
   constexpr int F = 3 * M;
   const int n = *n_dev;
-  const double inv_r = 1.0 / (double)r;
+  const double inv_r = 1.0 / (double)R;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const GhostCell g = cells[e];
     const LevelDesc& C = descs[g.desc_c];
@@ -233,10 +233,29 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
         sm[m][k][1] = minmod_bits(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
       }
     }
+    // Which of the R x R fine cells take a value: inside the strip and in no patch of the fine
+    // level. All R x R mask bytes are loaded before any is used (independent loads in flight
+    // together instead of one round trip per fine cell).
+    unsigned need = 0;
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int J = g.jc * R + b;
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const int I = g.ic * R + a;
+        const bool strip = I >= g.i0 && I < g.i1 && J >= g.j0 && J < g.j1;
+        const uint8_t cov = strip ? Fd.in_patch[(size_t)J * Fd.NX + I] : (uint8_t)1;
+        need |= (cov == 0 ? 1u : 0u) << (b * R + a);
+      }
+    }
     // fine columns a outer: the x parts eta + sx offx (and the momenta's) once per column
-    for (int a = 0; a < r; ++a) {
-      const int I = g.ic * r + a;
-      if (I < g.i0 || I >= g.i1) continue;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      unsigned col = 0;
+#pragma unroll
+      for (int b = 0; b < R; ++b) col |= ((need >> (b * R + a)) & 1u) << b;
+      if (col == 0) continue;
+      const int I = g.ic * R + a;
       const double offx = (a + 0.5) * inv_r - 0.5;
       double ex[M], mx[M][2];
 #pragma unroll
@@ -245,20 +264,23 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
         mx[m][0] = fma(sm[m][0][0], offx, c0[m][0]);
         mx[m][1] = fma(sm[m][1][0], offx, c0[m][1]);
       }
-      for (int b = 0; b < r; ++b) {
-        const int J = g.jc * r + b;
-        if (J < g.j0 || J >= g.j1) continue;
-        if (Fd.in_patch[(size_t)J * Fd.NX + I]) continue;
-        const size_t fo = (size_t)J * Fd.P + I;
+      // the column's fine bathymetry, all loads issued before the first use
+      double Bcol[R];
+#pragma unroll
+      for (int b = 0; b < R; ++b)
+        Bcol[b] = ((col >> b) & 1u) ? Fd.B[(size_t)(g.jc * R + b) * Fd.P + I] : 0.0;
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        if (((col >> b) & 1u) == 0) continue;
+        const size_t fo = (size_t)(g.jc * R + b) * Fd.P + I;
         const double offy = (b + 0.5) * inv_r - 0.5;
-        const double Bf = Fd.B[fo];
         double hf[M], out[F];
 #pragma unroll
         for (int m = M - 1; m >= 0; --m) {
           double hv = 0.0, huv = 0.0, hvv = 0.0;
           if (wet0[m]) {
             const double ef = fma(se[m][1], offy, ex[m]);
-            double bh = Bf;
+            double bh = Bcol[b];
 #pragma unroll
             for (int n2 = M - 1; n2 > m; --n2) bh = bh + hf[n2];
             const double d = ef - bh;
@@ -280,17 +302,25 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
   }
 }
 
+template <int M>
+static void launch_ghost_cells_m(const DevParams& P, const LevelDesc* descs, const GhostCell* cells,
+                                 const int* n_dev, int grid, int r, int par_c, int par_f, double alpha,
+                                 int substep, cudaStream_t st) {
+  if (r == 2)
+    ghost_cells_kernel<M, 2><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, par_c, par_f, alpha, substep);
+  else
+    ghost_cells_kernel<M, 4><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, par_c, par_f, alpha, substep);
+}
+
+// r: the level's refinement ratio, 2 or 4 (the only ratios a hierarchy accepts).
 cudaError_t launch_ghost_cells(int M, const DevParams& P, const LevelDesc* descs, const GhostCell* cells,
                                const int* n_dev, int grid, int r, int par_c, int par_f, double alpha, int substep,
                                cudaStream_t st) {
-  if (M == 1)
-    ghost_cells_kernel<1><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
-  else if (M == 3)
-    ghost_cells_kernel<3><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
-  else if (M == 4)
-    ghost_cells_kernel<4><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
-  else
-    ghost_cells_kernel<2><<<4 * grid, 64, 0, st>>>(P, descs, cells, n_dev, r, par_c, par_f, alpha, substep);
+  if (r != 2 && r != 4) return cudaErrorInvalidValue;
+  if (M == 1) launch_ghost_cells_m<1>(P, descs, cells, n_dev, grid, r, par_c, par_f, alpha, substep, st);
+  else if (M == 3) launch_ghost_cells_m<3>(P, descs, cells, n_dev, grid, r, par_c, par_f, alpha, substep, st);
+  else if (M == 4) launch_ghost_cells_m<4>(P, descs, cells, n_dev, grid, r, par_c, par_f, alpha, substep, st);
+  else launch_ghost_cells_m<2>(P, descs, cells, n_dev, grid, r, par_c, par_f, alpha, substep, st);
   return cudaGetLastError();
 }
 
