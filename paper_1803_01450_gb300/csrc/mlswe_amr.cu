@@ -25,14 +25,10 @@ namespace mlswe {
 // variables and are zero where h_{m,f} <= dry_tol. A layer not wet in k (top-down
 // rule) gives zero depth and momentum. The coarse state is (1-alpha) Q^n + alpha Q^{n+1}.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double minmod_d(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
-  return fabs(a) <= fabs(b) ? a : b;
-}
-
 // minmod on the bit patterns (integer unit): 0 when a and b differ in sign or either is zero,
-// else the one of smaller magnitude (a on ties). Equal to minmod_d except where a b
-// underflows to zero for same-signed |a|, |b| below about 1e-154 (minmod_d then gives 0).
+// else the one of smaller magnitude (a on ties). The same as the product test (a b <= 0 gives
+// 0) except where a b underflows to zero for same-signed |a|, |b| below about 1e-154, where
+// the product test gives 0.
 __device__ __forceinline__ double minmod_bits(double a, double b) {
   const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
   const unsigned long long ax = (unsigned long long)x & 0x7fffffffffffffffull;
@@ -66,120 +62,190 @@ __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* 
   B = C.B[o];
 }
 
-// Every fine cell of the item boxes (new patches) from the coarse state at alpha; the ghost
-// rings use ghost_cells_kernel below.
+// Refinement organised per coarse cell (used by the new-patch fill and the ghost fill): the
+// coarse cell's state and its four face neighbours' at alpha are loaded once, the wet flags,
+// surfaces and minmod slopes of every layer formed once, and then each of its R x R fine
+// cells that is wanted is reconstructed from them (the per-fine-cell form recomputes all of
+// that for every fine cell). Wet tests and minmod work on bit patterns: depths are >= 0 and
+// dry_tol >= 0, so h > dry_tol exactly when bits(h) > bits(dry_tol) as signed integers.
 template <int M>
-__global__ void __launch_bounds__(256)
-interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
-              const int* __restrict__ n_items_dev, int r, int par_c, int par_f, double alpha) {
+struct CoarsePrep {
+  bool wet0[M];          // layer wet in the coarse cell (top-down rule)
+  double eta0[M];        // its surface (Eq. (4))
+  double se[M][2];       // limited surface differences in x and y (Eq. (10) times dx)
+  double c0[M][2];       // its momenta
+  double sm[M][2][2];    // limited momentum differences [component][direction]
+};
+
+template <int M>
+__device__ __forceinline__ void coarse_prep(const LevelDesc& C, const double* qo, const double* qn, double alpha,
+                                            int ic, int jc, long long tol_bits, CoarsePrep<M>& S) {
   constexpr int F = 3 * M;
-  const int n_items = *n_items_dev;
-  const double inv_r = 1.0 / (double)r;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const InterpItem item = items[it];
-    const LevelDesc& C = descs[item.desc_c];
-    const LevelDesc& Fd = descs[item.desc_f];
-    const int w = item.i1 - item.i0, h = item.j1 - item.j0;
-    const int total = w * h;
-    const double* qo = C.q[par_c ^ 1];
-    const double* qn = C.q[par_c];
-    double* qf = Fd.q[par_f];
-    const size_t fplane = (size_t)Fd.NY * Fd.P;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int I = item.i0 + t % w, J = item.j0 + t / w;
-      if (I < 0 || J < 0 || I >= Fd.NX || J >= Fd.NY) continue;
-      const size_t fo = (size_t)J * Fd.P + I;
-      const int ic = I / r, jc = J / r, a = I - ic * r, b = J - jc * r;
-      const double offx = (a + 0.5) * inv_r - 0.5, offy = (b + 0.5) * inv_r - 0.5;
-      // coarse cell k and its face neighbours: 0 = k, 1 = west, 2 = east, 3 = south, 4 = north
-      double q[5][F], Bc[5];
-      coarse_cell<M>(C, qo, qn, alpha, ic, jc, q[0], Bc[0]);
-      coarse_cell<M>(C, qo, qn, alpha, ic - 1, jc, q[1], Bc[1]);
-      coarse_cell<M>(C, qo, qn, alpha, ic + 1, jc, q[2], Bc[2]);
-      coarse_cell<M>(C, qo, qn, alpha, ic, jc - 1, q[3], Bc[3]);
-      coarse_cell<M>(C, qo, qn, alpha, ic, jc + 1, q[4], Bc[4]);
-      const double Bf = Fd.B[fo];
-      double hf[M];
-      double out[F];
+  // coarse cell k and its face neighbours: 0 = k, 1 = west, 2 = east, 3 = south, 4 = north
+  double q[5][F], Bc[5];
+  coarse_cell<M>(C, qo, qn, alpha, ic, jc, q[0], Bc[0]);
+  coarse_cell<M>(C, qo, qn, alpha, ic - 1, jc, q[1], Bc[1]);
+  coarse_cell<M>(C, qo, qn, alpha, ic + 1, jc, q[2], Bc[2]);
+  coarse_cell<M>(C, qo, qn, alpha, ic, jc - 1, q[3], Bc[3]);
+  coarse_cell<M>(C, qo, qn, alpha, ic, jc + 1, q[4], Bc[4]);
 #pragma unroll
-      for (int m = M - 1; m >= 0; --m) {
-        bool wet[5];
-        double eta[5];
+  for (int m = M - 1; m >= 0; --m) {
+    bool wet[5];
+    double eta[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) {
-          bool wt = true;
+    for (int c = 0; c < 5; ++c) {
+      bool wt = true;
 #pragma unroll
-          for (int n = 0; n <= m; ++n) wt = wt && (q[c][3 * n] > P.dry_tol);
-          wet[c] = wt;
-          double e = Bc[c];
+      for (int n2 = 0; n2 <= m; ++n2) wt = wt && (__double_as_longlong(q[c][3 * n2]) > tol_bits);
+      wet[c] = wt;
+      double ev = Bc[c];
 #pragma unroll
-          for (int n = M - 1; n >= m; --n) e = e + q[c][3 * n];
-          eta[c] = e;
-        }
-        double hv = 0.0, huv = 0.0, hvv = 0.0;
-        if (wet[0]) {
-          const double sx = minmod_d(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
-          const double sy = minmod_d(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
-          const double ef = eta[0] + sx * offx + sy * offy;
-          double bh = Bf;
+      for (int n2 = M - 1; n2 >= m; --n2) ev = ev + q[c][3 * n2];
+      eta[c] = ev;
+    }
+    S.wet0[m] = wet[0];
+    S.eta0[m] = eta[0];
+    S.se[m][0] = minmod_bits(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
+    S.se[m][1] = minmod_bits(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
 #pragma unroll
-          for (int n = M - 1; n > m; --n) bh = bh + hf[n];
-          hv = fmax(0.0, ef - bh);
-          if (hv > P.dry_tol) {
-            double mom[2];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              const int f = 3 * m + 1 + k;
-              const double c0 = q[0][f];
-              const double mx = minmod_d(wet[1] ? c0 - q[1][f] : 0.0, wet[2] ? q[2][f] - c0 : 0.0);
-              const double my = minmod_d(wet[3] ? c0 - q[3][f] : 0.0, wet[4] ? q[4][f] - c0 : 0.0);
-              mom[k] = c0 + mx * offx + my * offy;
-            }
-            huv = mom[0];
-            hvv = mom[1];
-          }
-        }
-        hf[m] = hv;
-        out[3 * m] = hv;
-        out[3 * m + 1] = huv;
-        out[3 * m + 2] = hvv;
-      }
-#pragma unroll
-      for (int f = 0; f < F; ++f) qf[f * fplane + fo] = out[f];
+    for (int k = 0; k < 2; ++k) {
+      const int f = 3 * m + 1 + k;
+      const double cv = q[0][f];
+      S.c0[m][k] = cv;
+      S.sm[m][k][0] = minmod_bits(wet[1] ? cv - q[1][f] : 0.0, wet[2] ? q[2][f] - cv : 0.0);
+      S.sm[m][k][1] = minmod_bits(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
     }
   }
 }
 
+// The x parts of fine column a (offset offx from the coarse centre, in coarse cells): the
+// surface eta + sx offx and the momenta c + mx offx, once per column.
+template <int M>
+__device__ __forceinline__ void fine_column(const CoarsePrep<M>& S, double offx, double (&ex)[M],
+                                            double (&mx)[M][2]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    ex[m] = fma(S.se[m][0], offx, S.eta0[m]);
+    mx[m][0] = fma(S.sm[m][0][0], offx, S.c0[m][0]);
+    mx[m][1] = fma(S.sm[m][1][0], offx, S.c0[m][1]);
+  }
+}
+
+// One fine cell of that column (offset offy), bottom layer first: eta_f, Bhat_f = B_f plus the
+// fine layers below (Eq. (5)), h = max(0, eta_f - Bhat_f), momenta where h > dry_tol; written
+// to the 3M planes of qf at fo.
+template <int M>
+__device__ __forceinline__ void fine_cell(const CoarsePrep<M>& S, const double (&ex)[M], const double (&mx)[M][2],
+                                          double offy, double Bf, long long tol_bits, double* __restrict__ qf,
+                                          size_t fplane, size_t fo) {
+  constexpr int F = 3 * M;
+  double hf[M], out[F];
+#pragma unroll
+  for (int m = M - 1; m >= 0; --m) {
+    double hv = 0.0, huv = 0.0, hvv = 0.0;
+    if (S.wet0[m]) {
+      const double ef = fma(S.se[m][1], offy, ex[m]);
+      double bh = Bf;
+#pragma unroll
+      for (int n2 = M - 1; n2 > m; --n2) bh = bh + hf[n2];
+      const double d = ef - bh;
+      hv = __double_as_longlong(d) < 0 ? 0.0 : d;  // max(0, d); -0 gives +0
+      if (__double_as_longlong(hv) > tol_bits) {
+        huv = fma(S.sm[m][0][1], offy, mx[m][0]);
+        hvv = fma(S.sm[m][1][1], offy, mx[m][1]);
+      }
+    }
+    hf[m] = hv;
+    out[3 * m] = hv;
+    out[3 * m + 1] = huv;
+    out[3 * m + 2] = hvv;
+  }
+#pragma unroll
+  for (int f = 0; f < F; ++f) qf[f * fplane + fo] = out[f];
+}
+
+// Every fine cell of the item boxes (new patches: fine-index boxes, clipped to the level) from
+// the coarse state at alpha, one thread per coarse cell under the box.
+template <int M, int R>
+__global__ void __launch_bounds__(256)
+interp_kernel(DevParams P, const LevelDesc* __restrict__ descs, const InterpItem* __restrict__ items,
+              const int* __restrict__ n_items_dev, int par_c, int par_f, double alpha) {
+  constexpr double inv_r = 1.0 / (double)R;
+  const int n_items = *n_items_dev;
+  const long long tol_bits = __double_as_longlong(P.dry_tol);
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const InterpItem item = items[it];
+    const LevelDesc& C = descs[item.desc_c];
+    const LevelDesc& Fd = descs[item.desc_f];
+    const int i0 = max(item.i0, 0), j0 = max(item.j0, 0);
+    const int i1 = min(item.i1, Fd.NX), j1 = min(item.j1, Fd.NY);
+    if (i0 >= i1 || j0 >= j1) continue;
+    const int ic0 = i0 / R, jc0 = j0 / R;
+    const int cw = (i1 + R - 1) / R - ic0, ch = (j1 + R - 1) / R - jc0;
+    const double* qo = C.q[par_c ^ 1];
+    const double* qn = C.q[par_c];
+    double* qf = Fd.q[par_f];
+    const size_t fplane = (size_t)Fd.NY * Fd.P;
+    for (int t = threadIdx.x; t < cw * ch; t += blockDim.x) {
+      const int ic = ic0 + t % cw, jc = jc0 + t / cw;
+      CoarsePrep<M> S;
+      coarse_prep<M>(C, qo, qn, alpha, ic, jc, tol_bits, S);
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const int I = ic * R + a;
+        if (I < i0 || I >= i1) continue;
+        double ex[M], mx[M][2];
+        fine_column<M>(S, (a + 0.5) * inv_r - 0.5, ex, mx);
+        double Bcol[R];
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          const int J = jc * R + b;
+          Bcol[b] = (J >= j0 && J < j1) ? Fd.B[(size_t)J * Fd.P + I] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          const int J = jc * R + b;
+          if (J < j0 || J >= j1) continue;
+          fine_cell<M>(S, ex, mx, (b + 0.5) * inv_r - 0.5, Bcol[b], tol_bits, qf, fplane, (size_t)J * Fd.P + I);
+        }
+      }
+    }
+  }
+}
+
+template <int M>
+static void launch_interp_m(const DevParams& P, const LevelDesc* descs, const InterpItem* items,
+                            const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha,
+                            cudaStream_t st) {
+  if (r == 2) interp_kernel<M, 2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_c, par_f, alpha);
+  else interp_kernel<M, 4><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, par_c, par_f, alpha);
+}
+
+// r: the refinement ratio, 2 or 4 (the only ratios a hierarchy accepts).
 cudaError_t launch_interp(int M, const DevParams& P, const LevelDesc* descs, const InterpItem* items,
                           const int* n_items_dev, int grid, int r, int par_c, int par_f, double alpha,
                           cudaStream_t st) {
-  if (M == 1)
-    interp_kernel<1><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
-  else if (M == 3)
-    interp_kernel<3><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
-  else if (M == 4)
-    interp_kernel<4><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
-  else
-    interp_kernel<2><<<grid, 256, 0, st>>>(P, descs, items, n_items_dev, r, par_c, par_f, alpha);
+  if (r != 2 && r != 4) return cudaErrorInvalidValue;
+  if (M == 1) launch_interp_m<1>(P, descs, items, n_items_dev, grid, r, par_c, par_f, alpha, st);
+  else if (M == 3) launch_interp_m<3>(P, descs, items, n_items_dev, grid, r, par_c, par_f, alpha, st);
+  else if (M == 4) launch_interp_m<4>(P, descs, items, n_items_dev, grid, r, par_c, par_f, alpha, st);
+  else launch_interp_m<2>(P, descs, items, n_items_dev, grid, r, par_c, par_f, alpha, st);
   return cudaGetLastError();
 }
 
-// Launched in blocks of 64 threads (four times the blocks of the flat grid): a level's list
-// of ring cells often fills only a fraction of the GPU, and small blocks spread it over every
-// SM instead of giving some SMs two large blocks and others none.
-// Ghost fill (the refinement above applied to the ring cells of the patches) organised per
-// coarse cell: the thread of a coarse cell under a ghost strip loads it and its four face
-// neighbours once, forms the wet flags, surfaces and minmod slopes of every layer once, and
-// then reconstructs each of its r x r fine cells that lies in the strip and in no patch of
-// the fine level (the per-fine-cell form recomputes all of that for every fine cell). Same
-// formulas per fine cell as interp_kernel.
+// Ghost fill: the refinement above applied to the ring cells of the patches, one thread per
+// coarse cell under a ghost strip; it reconstructs each of its R x R fine cells that lies in
+// the strip and in no patch of the fine level. Launched in blocks of 64 threads (four times
+// the blocks of the flat grid): a level's list of ring cells often fills only a fraction of
+// the GPU, and small blocks spread it over every SM instead of giving some SMs two large
+// blocks and others none.
 template <int M, int R>
 __global__ void __launch_bounds__(256)
 ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const GhostCell* __restrict__ cells,
                    const int* __restrict__ n_dev, int par_c, int par_f, double alpha_in, int substep) {
-  constexpr int F = 3 * M;
+  constexpr double inv_r = 1.0 / (double)R;
   const int n = *n_dev;
-  const double inv_r = 1.0 / (double)R;
+  const long long tol_bits = __double_as_longlong(P.dry_tol);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const GhostCell g = cells[e];
     const LevelDesc& C = descs[g.desc_c];
@@ -193,46 +259,8 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
     const double* qn = C.q[par_c];
     double* qf = Fd.q[par_f];
     const size_t fplane = (size_t)Fd.NY * Fd.P;
-    double q[5][F], Bc[5];
-    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc, q[0], Bc[0]);
-    coarse_cell<M>(C, qo, qn, alpha, g.ic - 1, g.jc, q[1], Bc[1]);
-    coarse_cell<M>(C, qo, qn, alpha, g.ic + 1, g.jc, q[2], Bc[2]);
-    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc - 1, q[3], Bc[3]);
-    coarse_cell<M>(C, qo, qn, alpha, g.ic, g.jc + 1, q[4], Bc[4]);
-    // per layer: wet in the coarse cell, its surface and slopes, its momenta and their slopes
-    // (wet tests and minmod on bit patterns: depths are >= 0 and dry_tol >= 0, so h > dry_tol
-    // exactly when bits(h) > bits(dry_tol) as signed integers)
-    const long long tol_bits = __double_as_longlong(P.dry_tol);
-    bool wet0[M];
-    double eta0[M], se[M][2], c0[M][2], sm[M][2][2];
-#pragma unroll
-    for (int m = M - 1; m >= 0; --m) {
-      bool wet[5];
-      double eta[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        bool wt = true;
-#pragma unroll
-        for (int n2 = 0; n2 <= m; ++n2) wt = wt && (__double_as_longlong(q[c][3 * n2]) > tol_bits);
-        wet[c] = wt;
-        double ev = Bc[c];
-#pragma unroll
-        for (int n2 = M - 1; n2 >= m; --n2) ev = ev + q[c][3 * n2];
-        eta[c] = ev;
-      }
-      wet0[m] = wet[0];
-      eta0[m] = eta[0];
-      se[m][0] = minmod_bits(wet[1] ? eta[0] - eta[1] : 0.0, wet[2] ? eta[2] - eta[0] : 0.0);
-      se[m][1] = minmod_bits(wet[3] ? eta[0] - eta[3] : 0.0, wet[4] ? eta[4] - eta[0] : 0.0);
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int f = 3 * m + 1 + k;
-        const double cv = q[0][f];
-        c0[m][k] = cv;
-        sm[m][k][0] = minmod_bits(wet[1] ? cv - q[1][f] : 0.0, wet[2] ? q[2][f] - cv : 0.0);
-        sm[m][k][1] = minmod_bits(wet[3] ? cv - q[3][f] : 0.0, wet[4] ? q[4][f] - cv : 0.0);
-      }
-    }
+    CoarsePrep<M> S;
+    coarse_prep<M>(C, qo, qn, alpha, g.ic, g.jc, tol_bits, S);
     // Which of the R x R fine cells take a value: inside the strip and in no patch of the fine
     // level. All R x R mask bytes are loaded before any is used (independent loads in flight
     // together instead of one round trip per fine cell).
@@ -248,7 +276,7 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
         need |= (cov == 0 ? 1u : 0u) << (b * R + a);
       }
     }
-    // fine columns a outer: the x parts eta + sx offx (and the momenta's) once per column
+    // fine columns a outer: the x parts once per column
 #pragma unroll
     for (int a = 0; a < R; ++a) {
       unsigned col = 0;
@@ -256,14 +284,8 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
       for (int b = 0; b < R; ++b) col |= ((need >> (b * R + a)) & 1u) << b;
       if (col == 0) continue;
       const int I = g.ic * R + a;
-      const double offx = (a + 0.5) * inv_r - 0.5;
       double ex[M], mx[M][2];
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        ex[m] = fma(se[m][0], offx, eta0[m]);
-        mx[m][0] = fma(sm[m][0][0], offx, c0[m][0]);
-        mx[m][1] = fma(sm[m][1][0], offx, c0[m][1]);
-      }
+      fine_column<M>(S, (a + 0.5) * inv_r - 0.5, ex, mx);
       // the column's fine bathymetry, all loads issued before the first use
       double Bcol[R];
 #pragma unroll
@@ -272,31 +294,8 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
 #pragma unroll
       for (int b = 0; b < R; ++b) {
         if (((col >> b) & 1u) == 0) continue;
-        const size_t fo = (size_t)(g.jc * R + b) * Fd.P + I;
-        const double offy = (b + 0.5) * inv_r - 0.5;
-        double hf[M], out[F];
-#pragma unroll
-        for (int m = M - 1; m >= 0; --m) {
-          double hv = 0.0, huv = 0.0, hvv = 0.0;
-          if (wet0[m]) {
-            const double ef = fma(se[m][1], offy, ex[m]);
-            double bh = Bcol[b];
-#pragma unroll
-            for (int n2 = M - 1; n2 > m; --n2) bh = bh + hf[n2];
-            const double d = ef - bh;
-            hv = __double_as_longlong(d) < 0 ? 0.0 : d;  // max(0, d); -0 gives +0
-            if (__double_as_longlong(hv) > tol_bits) {
-              huv = fma(sm[m][0][1], offy, mx[m][0]);
-              hvv = fma(sm[m][1][1], offy, mx[m][1]);
-            }
-          }
-          hf[m] = hv;
-          out[3 * m] = hv;
-          out[3 * m + 1] = huv;
-          out[3 * m + 2] = hvv;
-        }
-#pragma unroll
-        for (int f = 0; f < F; ++f) qf[f * fplane + fo] = out[f];
+        fine_cell<M>(S, ex, mx, (b + 0.5) * inv_r - 0.5, Bcol[b], tol_bits, qf, fplane,
+                     (size_t)(g.jc * R + b) * Fd.P + I);
       }
     }
   }
