@@ -310,28 +310,8 @@ def bench_batched_amr(pkg, torch, stream, steps=3, n0=512, patches=(1000, 3000))
     then the level transfers per kernel class and one regrid (flag tolerance 5e-5: the humps'
     slopes are about 1e-4, so the regrid refines around them)."""
     r = 4
-    nf = n0 * r * r
-    L = 1e5
-    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64,
-                     flag_tol=5e-5)
-    H = pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)], stream=stream.cuda_stream)
-    xf = I.centers(0.0, L, nf)
-    Bf = np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf)))
-    H.set_bathymetry(0, Bf)
-    del Bf
-    B0 = H.get_bathymetry(0, 0)
-    x0 = I.centers(0.0, L, n0)
-    X, Y = np.meshgrid(x0, x0)
-    eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
-    H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
-    l1 = I.random_layout(3100, n0 * r, n0 * r, patches[0], r)
-    l2 = I.random_layout(3200, nf, nf, patches[1], r, parents=l1, margin=2)
-    H.set_patches(0, 1, l1)
-    H.interp_fine(0, 0)
-    H.set_patches(0, 2, l2)
-    H.interp_fine(1, 0)
-    chosen = [H.autotune(l, iters=2) for l in range(3)]
-    upd = _interior_updates(H, 1, 3, [r, r])
+    H, chosen, upd = _batched_amr_hierarchy(pkg, stream, n0, patches)
+    n_patches = [len(H.get_patches(0, l)) for l in (1, 2)]
     H.advance(1)
     ms_b = _time_advance(torch, H, stream, steps)
     H.set_execution(use_graphs=False, per_patch_launches=True)
@@ -398,15 +378,97 @@ def bench_batched_amr(pkg, torch, stream, steps=3, n0=512, patches=(1000, 3000))
     transfers["cycle_with_regrids"] = {"coarse_steps": 8, "regrids": 2, "wall_ms": cyc_s * 1e3,
                                        "cell_updates": cyc_upd, "lcups": cyc_upd * M_LAYERS / cyc_s,
                                        "patches": [len(H.get_patches(0, l)) for l in (1, 2)]}
+    transfers["partition_exchange"] = _partition_pack_times(torch, H, stream)
     H.close()
     lb = upd * M_LAYERS * steps / (ms_b * 1e-3)
     lp = upd * M_LAYERS * max(1, steps // 2) / (ms_p * 1e-3)
     return {"workload": f"3 levels, {n0}^2 coarse, ratios 4,4, shore bathymetry, 8 humps; seeded layout of "
-                        f"{len(l1)} level-1 and {len(l2)} level-2 patches (sides 16..64)",
+                        f"{n_patches[0]} level-1 and {n_patches[1]} level-2 patches (sides 16..64)",
             "cell_updates_per_coarse_step": upd, "coarse_steps": steps,
             "lcups_batched": lb, "lcups_per_patch": lp, "batched_over_per_patch": lb / lp,
             "ms_per_coarse_step_batched": ms_b / steps, "ms_per_coarse_step_per_patch": ms_p / max(1, steps // 2),
             "autotuned_tiles": chosen, "level_transfers": transfers}
+
+
+def _partition_pack_times(torch, H, stream, ws=2, reps=5):
+    """Kernel side of the patch-partition exchange on one GPU: the hierarchy split over ws
+    ranks (no hook; this process plays rank 0), then per refined level the doubles every rank
+    sends per level step and the pack and unpack times of rank 0's and rank 1's buffers (CUDA
+    events; read + write bytes of the copies over the time)."""
+    H.set_partition(0, ws)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"ranks": ws}
+    for level in (1, 2):
+        sizes = H.partition_sizes(level)
+        buf = torch.empty(max(sizes), dtype=torch.float64, device=dev)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(reps):
+            H.partition_pack(level, buf.data_ptr())
+        e[1].record(stream)
+        for _ in range(reps):
+            H.partition_unpack(level, 1, buf.data_ptr())
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        pack_ms, unpack_ms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+        out[f"level{level}"] = {"doubles_per_rank": sizes, "job_bytes_per_level_step": 8 * sum(sizes),
+                                "pack_ms": pack_ms, "pack_gbs": 16 * sizes[0] / (pack_ms * 1e-3) / 1e9,
+                                "unpack_ms": unpack_ms, "unpack_gbs": 16 * sizes[1] / (unpack_ms * 1e-3) / 1e9}
+    H.set_partition(0, 1)
+    return out
+
+
+def bench_amr_partitioned(pkg, torch, stream, rank, ws, steps=3, n0=512, patches=(1000, 3000)):
+    """The batched AMR workload with the patches of its refined levels split over the ranks
+    (space-filling curve, balanced cells): every rank holds the whole hierarchy and sweeps its
+    own patches; after each refined level step the ranks all-gather their packed patch values
+    and take the largest wave speeds over NCCL (sharding.PatchPartition). Layer-cell updates of
+    the job (every rank's hierarchy is the whole job) over the slowest rank's time."""
+    import torch.distributed as dist
+    from paper_1803_01450_gb300 import sharding as S
+    H, _, upd = _batched_amr_hierarchy(pkg, stream, n0, patches)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    S.PatchPartition(H, rank, ws, dist, dev)
+    H.advance(1)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = _time_advance(torch, H, stream, steps)
+    H.close()
+    tmax = S.max_all(ms, dist, dev)
+    return {"workload": f"3 levels, {n0}^2 coarse, {patches[0]} + {patches[1]} patches split over {ws} ranks",
+            "ranks": ws, "lcups": upd * M_LAYERS * steps / (tmax * 1e-3),
+            "ms_per_coarse_step_slowest_rank": tmax / steps}
+
+
+def _batched_amr_hierarchy(pkg, stream, n0, patches, autotune=True):
+    """The three-level hierarchy of the batched AMR workload (shore bathymetry, 8 humps, seeded
+    synthetic layouts of patches[0] level-1 and patches[1] level-2 patches), its autotuned
+    tiles and its interior cell updates per coarse step."""
+    r = 4
+    nf = n0 * r * r
+    L = 1e5
+    cfg = pkg.Config(M=2, dry_tol=1e-3, max_levels=3, ratio=[r, r], regrid_interval=0, min_side=16, max_side=64,
+                     flag_tol=5e-5)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, L, L, n0, n0)], stream=stream.cuda_stream)
+    xf = I.centers(0.0, L, nf)
+    Bf = np.ascontiguousarray(np.broadcast_to(I.shore_B(xf)[None, :], (nf, nf)))
+    H.set_bathymetry(0, Bf)
+    del Bf
+    B0 = H.get_bathymetry(0, 0)
+    x0 = I.centers(0.0, L, n0)
+    X, Y = np.meshgrid(x0, x0)
+    eta1 = I.hump_field(X, Y, *I.humps(3000, 8))
+    H.set_state(0, 0, I.layered_state(B0, eta1, -200.0 * np.ones_like(B0)))
+    l1 = I.random_layout(3100, n0 * r, n0 * r, patches[0], r)
+    l2 = I.random_layout(3200, nf, nf, patches[1], r, parents=l1, margin=2)
+    H.set_patches(0, 1, l1)
+    H.interp_fine(0, 0)
+    H.set_patches(0, 2, l2)
+    H.interp_fine(1, 0)
+    chosen = [H.autotune(l, iters=2) for l in range(3)] if autotune else None
+    return H, chosen, _interior_updates(H, 1, 3, [r, r])
+
 
 
 def bench_dynamic_rt(pkg, torch, stream, steps=6):
@@ -741,7 +803,7 @@ def _summary(line):
     adj = line.get("adjoint")
     if adj:
         out["adjoint_over_forward"] = adj.get("adjoint_over_forward")
-    for key in ("ensemble_partitioned", "slabs"):
+    for key in ("ensemble_partitioned", "slabs", "amr_partitioned"):
         if key in line:
             out[key + "_lcups"] = line[key]["lcups"]
     cpu = line.get("cpu_baseline")
@@ -882,9 +944,11 @@ def run_gpu(args):
         # work split over the ranks (every rank takes part): members partitioned, one grid in slabs
         part = bench_ensemble_partitioned(pkg, torch, stream, rank, ws)
         slabs = bench_slabs(pkg, torch, stream, rank, ws)
+        amr_part = bench_amr_partitioned(pkg, torch, stream, rank, ws)
         if rank == 0:
             line["ensemble_partitioned"] = part
             line["slabs"] = slabs
+            line["amr_partitioned"] = amr_part
     if rank == 0 and not args.no_amr:
         line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
         line["ensemble"] = bench_ensemble(pkg, torch, stream)

@@ -424,6 +424,66 @@ mlswe_status mlswe_step_fixed_noalloc(const mlswe_config* cfg, int nx, int ny, d
 mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long long* launches_out,
                           long long* total_launches);
 
+/* ---- Patch partition across ranks (not in the paper; its conclusion names parallel and
+ * GPU work as the next step). One process per GPU holds the whole hierarchy; the work of
+ * the refined levels is split by patches:
+ *  - the patches of every level >= 1 are ordered by member, then by the Morton
+ *    (Z-order) key of their centre (bits of the integer cell indices (i0 + i1) / 2 and
+ *    (j0 + j1) / 2 interleaved, x in the even bits), then by patch index; with T the
+ *    level's patch cells over all members and c_p the cells before patch p in that order,
+ *    patch p goes to rank min(n - 1, floor((2 c_p + cells_p) n / (2 T))) (the rank whose
+ *    share of the cells holds the patch's middle cell), so each rank's cells differ from
+ *    T / n by at most the largest patch;
+ *  - a rank sweeps only its own patches of levels >= 1; level 0, the ghost fill, the
+ *    coarsening, the reflux, the time step and the regrids run on every rank, on state
+ *    that every rank holds in full after each exchange;
+ *  - after every step of a level >= 1 inside mlswe_advance, the library calls the
+ *    exchange hook, which must give every rank the other ranks' patch values
+ *    (mlswe_partition_pack / mlswe_partition_unpack, through an all-gather) and the
+ *    maximum over the ranks of the wave-speed slots (mlswe_wave_speed_slots). Then the
+ *    ranks' hierarchies equal the undivided hierarchy's after every step.
+ * The orders and the split are the same on every rank (host integer arithmetic on the
+ * same layouts), so no owner table is sent. */
+
+/* Exchange hook: called by mlswe_advance on the calling thread after the kernels of
+ * one step of `level` (>= 1) are enqueued on the hierarchy's stream; work it enqueues
+ * on that stream runs before the rest of the coarse step. Returns 0, or non-zero to
+ * stop mlswe_advance with MLSWE_EINVAL. */
+typedef int (*mlswe_exchange_hook)(void* ctx, int level);
+
+/* Partition the refined levels' patches over world_size ranks (rank: this process's).
+ * world_size 1 undoes it. The split step only (unsplit: MLSWE_EINVAL) and the batched
+ * launch form (mlswe_set_execution per_patch_launches = 1 is refused while partitioned);
+ * mlswe_advance launches directly (no graph capture) while a hook is set. hook may be
+ * NULL for callers that step levels themselves (mlswe_step_level steps only this rank's
+ * patches of a level >= 1; the caller exchanges). */
+mlswe_status mlswe_set_partition(mlswe_h h, int rank, int world_size, mlswe_exchange_hook hook, void* ctx);
+
+/* Owner rank of every patch of (member, level): owner_out host [n patches]. */
+mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner_out);
+
+/* Doubles in each rank's packed buffer of `level` (host [world_size]). A packed buffer holds,
+ * for every patch the rank owns in the order of the split above, the 3M state fields of the
+ * patch cells (current buffer; field, then row, then column), the boundary mass-flux
+ * accumulators of its rows' left and right edges and of its columns' bottom and top edges
+ * ([M][rows][2], [M][columns][2]), and, on levels with a finer level, the interface mass
+ * fluxes of every x edge and y edge of the patch box including its sides
+ * ([M][rows][columns + 1], [M][rows + 1][columns]). */
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, long long* doubles_per_rank);
+
+/* This rank's packed buffer of `level` into dst (device, mlswe_partition_sizes doubles),
+ * enqueued on the hierarchy's stream. */
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, double* dst);
+
+/* Writes the patches rank `from` owns on `level` from its packed buffer src (device),
+ * enqueued on the hierarchy's stream. */
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int from, const double* src);
+
+/* Device address and length of the wave-speed slots (n doubles: the largest wave speed of
+ * every member, level and sweep direction in the current coarse step, non-negative). An
+ * exchange hook replaces them by their maximum over the ranks. */
+mlswe_status mlswe_wave_speed_slots(mlswe_h h, double** dev, int* n);
+
 #ifdef __cplusplus
 }
 #endif

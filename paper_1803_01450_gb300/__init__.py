@@ -104,6 +104,9 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _H = ctypes.c_void_p
 
+# int (*)(void* ctx, int level): the exchange hook of a partitioned hierarchy
+_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int)
+
 # name -> argtypes (restype is mlswe_status unless stated)
 _SIGS = {
     "mlswe_create_hierarchy": [ctypes.POINTER(_Config), ctypes.c_int, ctypes.POINTER(_Domain),
@@ -145,6 +148,12 @@ _SIGS = {
     "mlswe_fixed_backward": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_fixed_backward_state": [_H, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
+    "mlswe_set_partition": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "mlswe_partition_owners": [_H, ctypes.c_int, ctypes.c_int, _ip],
+    "mlswe_partition_sizes": [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
+    "mlswe_partition_pack": [_H, ctypes.c_int, ctypes.c_void_p],
+    "mlswe_partition_unpack": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "mlswe_wave_speed_slots": [_H, ctypes.POINTER(ctypes.c_void_p), _ip],
     "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
                      ctypes.POINTER(ctypes.c_longlong)],
 }
@@ -377,7 +386,59 @@ class Hierarchy:
         self._check(self.L.mlswe_regrid(self.h, base_level), "regrid")
 
     def advance(self, n_coarse_steps: int, allow=(MLSWE_OK,)):
-        return self._check(self.L.mlswe_advance(self.h, n_coarse_steps), "advance", allow)
+        st = self.L.mlswe_advance(self.h, n_coarse_steps)
+        err = getattr(self, "_hook_error", None)
+        if err is not None:
+            self._hook_error = None
+            raise MLSWEError(st, f"advance: the exchange hook raised {err!r}") from err
+        return self._check(st, "advance", allow)
+
+    # ---- patch partition across ranks (mlswe_set_partition and the exchange calls) ----
+    def set_partition(self, rank: int, world_size: int, hook=None):
+        """Sweep only this rank's patches of the refined levels; hook(level), if given, is
+        called by advance after every refined level step and must exchange (see sharding)."""
+        cb = None
+        if hook is not None:
+            def _cb(ctx, level):
+                try:
+                    hook(level)
+                    return 0
+                except BaseException as e:  # reported by advance
+                    self._hook_error = e
+                    return 1
+            cb = _HOOK(_cb)
+        self._hook_ref = cb  # the C side keeps only the function pointer
+        self._hook_error = None
+        fp = ctypes.cast(cb, ctypes.c_void_p) if cb is not None else None
+        self._check(self.L.mlswe_set_partition(self.h, rank, world_size, fp, None), "set_partition")
+        self.part_rank, self.part_size = rank, world_size
+
+    def partition_owners(self, member: int, level: int) -> np.ndarray:
+        out = np.zeros(len(self.get_patches(member, level)), dtype=np.int32)
+        self._check(self.L.mlswe_partition_owners(self.h, member, level,
+                                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int))),
+                    "partition_owners")
+        return out
+
+    def partition_sizes(self, level: int):
+        """Doubles in every rank's packed buffer of `level`."""
+        n = getattr(self, "part_size", 1)
+        out = (ctypes.c_longlong * n)()
+        self._check(self.L.mlswe_partition_sizes(self.h, level, out), "partition_sizes")
+        return [int(v) for v in out]
+
+    def partition_pack(self, level: int, dst_ptr: int):
+        self._check(self.L.mlswe_partition_pack(self.h, level, ctypes.c_void_p(dst_ptr)), "partition_pack")
+
+    def partition_unpack(self, level: int, rank: int, src_ptr: int):
+        self._check(self.L.mlswe_partition_unpack(self.h, level, rank, ctypes.c_void_p(src_ptr)),
+                    "partition_unpack")
+
+    def wave_speed_slots(self):
+        """(device address, count) of the wave-speed slots (float64, non-negative)."""
+        p, n = ctypes.c_void_p(), ctypes.c_int()
+        self._check(self.L.mlswe_wave_speed_slots(self.h, ctypes.byref(p), ctypes.byref(n)), "wave_speed_slots")
+        return int(p.value), int(n.value)
 
     def get_time(self):
         """(simulated time per member, next level-0 time step per member)."""

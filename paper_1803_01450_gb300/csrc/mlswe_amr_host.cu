@@ -181,6 +181,7 @@ static mlswe_status rebuild_masks(Hier* H, int member, int level) {
   H->wl[(level - 1) * 2].dirty = H->wl[(level - 1) * 2 + 1].dirty = true;
   H->wu[level].dirty = H->wu[level - 1].dirty = true;
   H->tables_dirty = true;
+  H->part_dirty = true;
   return MLSWE_OK;
 }
 
@@ -285,6 +286,8 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
   }
   mlswe_status s = enqueue_level_step(H, level, 1);
   if (s != MLSWE_OK) return s;
+  s = run_exchange_hook(H, level);  // partitioned: the other ranks' patches of this level
+  if (s != MLSWE_OK) return s;
   if (level + 1 < H->L) {
     const int rt = H->cfg.ratio[level];  // the most substeps any member takes
     for (int k = 0; k < rt; ++k) {
@@ -378,7 +381,7 @@ static mlswe_status initial_dt(Hier* H) {
 // One coarse step: replay of the captured graph for the current level-0 parity, or
 // direct launches (per-patch form, timing on, or graphs disabled).
 static mlswe_status coarse_step(Hier* H) {
-  const bool graphs = H->use_graphs && !H->per_patch_launch && !H->timer.on;
+  const bool graphs = H->use_graphs && !H->per_patch_launch && !H->timer.on && H->part_hook == nullptr;
   if (!graphs) return enqueue_coarse_step(H);
   for (int l = 0; l < H->L; ++l)
     for (int dir = 0; dir < (H->cfg.unsplit ? 3 : 2); ++dir) {  // built before the capture (they sync)
@@ -724,6 +727,7 @@ mlswe_status mlswe_get_time(mlswe_h h, double* t_out, double* dt_out) {
 
 mlswe_status mlswe_set_execution(mlswe_h h, int use_graphs, int per_patch_launches) {
   if (!h) return MLSWE_EINVAL;
+  if (per_patch_launches && h->part_size > 1) return fail(h, MLSWE_EINVAL, "set_execution: partitioned hierarchy");
   h->use_graphs = use_graphs != 0;
   if (h->per_patch_launch != (per_patch_launches != 0))
     for (auto& W : h->wl) W.dirty = true;  // packed tiles (batched) or tiles per patch

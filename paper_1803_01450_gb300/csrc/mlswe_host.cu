@@ -285,7 +285,9 @@ static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& 
   for (int m = 0; m < H->n_members; ++m) {
     const Level& V = H->mem[m].lev[level];
     const int desc = H->desc_index(m, level);
-    for (const Box& b : V.patches) {
+    for (int p = 0; p < (int)V.patches.size(); ++p) {
+      if (!patch_owned(H, m, level, p)) continue;  // another rank sweeps it
+      const Box& b = V.patches[p];
       const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;
       int tl, tn;
       tile_dims(ts, dir == 0 ? b.w() : b.h(), &tl, &tn);
@@ -300,6 +302,10 @@ static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& 
 mlswe_status ensure_worklist(Hier* H, int level, int dir) {
   Hier::WorkList& W = dir == 2 ? H->wu[level] : H->wl[level * 2 + dir];
   if (!W.dirty) return MLSWE_OK;
+  if (H->part_size > 1) {
+    mlswe_status s = ensure_partition(H);
+    if (s != MLSWE_OK) return s;
+  }
   std::vector<SweepItem> items;
   build_items(H, level, dir, items, W.patch_off);
   // batched form: groups of lines packed into tiles (the per-patch form keeps a tile per item)

@@ -54,6 +54,14 @@ struct Member {
   std::vector<Level> lev;
 };
 
+// Work entry of the partition exchange: one patch (box of level cells of desc) and where its
+// values start in its owner's packed buffer (see mlswe_partition.cu for the layout).
+struct PackItem {
+  int desc;
+  int i0, j0, i1, j1;
+  long long off;
+};
+
 // Tile shape of one sweep direction: `len` cells along the sweep, `lines` lines per tile.
 struct TileShape {
   int len = 61;
@@ -178,6 +186,19 @@ struct Hier {
   int stage_next = 0;
   size_t scratch_bytes = 0;
   void* adj = nullptr;             // buffers of the fixed-grid adjoint (mlswe_adjoint.cu)
+  // Patch partition across ranks (mlswe_partition.cu): this rank sweeps only the patches of
+  // levels >= 1 it owns; everything else runs on every rank.
+  int part_rank = 0, part_size = 1;
+  mlswe_exchange_hook part_hook = nullptr;
+  void* part_ctx = nullptr;
+  bool part_dirty = true;
+  std::vector<std::vector<std::vector<int>>> owner;  // [member][level][patch] rank
+  struct PartLevel {
+    DevTable<PackItem> items;      // every patch of the level, grouped by owner
+    std::vector<int> first;        // [part_size + 1] item range of each owner
+    std::vector<long long> size;   // [part_size] doubles in each owner's packed buffer
+  };
+  std::vector<PartLevel> part;     // [L]
 
   int desc_index(int member, int level) const { return member * L + level; }
 };
@@ -263,6 +284,13 @@ cudaError_t launch_sweep(int dir, const DevParams& P, const LevelDesc* descs, co
                          double* est = nullptr, long long eplane = 0);
 
 mlswe_status enqueue_level_step(Hier* H, int level, int record);
+
+// Patch partition (mlswe_partition.cu): owners and exchange tables rebuilt after a layout
+// change; whether this rank sweeps patch p of (member, level) (always on level 0 and when the
+// hierarchy is not partitioned); the exchange hook after a level step.
+mlswe_status ensure_partition(Hier* H);
+bool patch_owned(const Hier* H, int member, int level, int p);
+mlswe_status run_exchange_hook(Hier* H, int level);
 
 // Packed sweep tiles (mlswe_pack.cu). patch_segments appends the runs of lines of patch b
 // for a sweep along dir (0: x, lines are rows; 1: y, lines are columns): lines [g0, g1)

@@ -1,0 +1,276 @@
+// Patch partition across ranks: the owner of every patch of the refined levels (a
+// space-filling-curve split with balanced cells), the packed exchange buffers of a level
+// (state of the owned patch cells and the mass fluxes the reflux reads) and their pack and
+// unpack kernels, and the exchange hook that mlswe_advance calls after each refined level
+// step. No collective is called here: the caller's hook moves the buffers (for example an
+// NCCL all-gather through torch.distributed).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include "mlswe_internal.h"
+
+namespace mlswe {
+
+static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
+  if (H) H->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(H, call)                                                               \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((H), MLSWE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Morton (Z-order) key of a cell index pair: bit b of i at bit 2b, bit b of j at bit 2b + 1,
+// for the low 21 bits of each.
+static unsigned long long morton(int i, int j) {
+  unsigned long long key = 0;
+  for (int b = 0; b < 21; ++b) {
+    key |= (unsigned long long)((i >> b) & 1) << (2 * b);
+    key |= (unsigned long long)((j >> b) & 1) << (2 * b + 1);
+  }
+  return key;
+}
+
+// Doubles of one patch in a packed buffer (layout in mlswe_partition_sizes' description).
+static long long pack_doubles(int M, const Box& b, bool fine_level_below) {
+  const long long w = b.w(), h = b.h();
+  long long n = 3LL * M * w * h + 2LL * M * h + 2LL * M * w;
+  if (fine_level_below) n += (long long)M * h * (w + 1) + (long long)M * (h + 1) * w;
+  return n;
+}
+
+static bool partitioned(const Hier* H) { return H->part_size > 1; }
+
+bool patch_owned(const Hier* H, int member, int level, int p) {
+  if (!partitioned(H) || level == 0) return true;
+  return H->owner[member][level][p] == H->part_rank;
+}
+
+static mlswe_status upload_items(Hier* H, DevTable<PackItem>& T, const std::vector<PackItem>& v) {
+  if ((int)v.size() > T.cap || !T.d) {
+    if (T.d) dev_free(H, T.d);
+    T.cap = std::max<int>(64, (int)v.size() * 3 / 2);
+    T.d = (PackItem*)dev_alloc(H, T.cap * sizeof(PackItem));
+    if (!T.d) return fail(H, MLSWE_ENOMEM, "partition table allocation failed");
+  }
+  T.count = (int)v.size();
+  if (!v.empty())
+    CUDA_TRY(H, cudaMemcpyAsync(T.d, v.data(), v.size() * sizeof(PackItem), cudaMemcpyHostToDevice, H->st));
+  return MLSWE_OK;
+}
+
+mlswe_status ensure_partition(Hier* H) {
+  if (!H->part_dirty) return MLSWE_OK;
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));  // no pack or unpack still reads the old table
+  const int n = std::max(1, H->part_size);
+  H->owner.assign(H->n_members, std::vector<std::vector<int>>(H->L));
+  H->part.resize(H->L);
+  for (int l = 0; l < H->L; ++l) {
+    struct Entry { int m, p; unsigned long long key; long long cells; };
+    std::vector<Entry> e;
+    long long total = 0;
+    for (int m = 0; m < H->n_members; ++m) {
+      const std::vector<Box>& P = H->mem[m].lev[l].patches;
+      H->owner[m][l].assign(P.size(), 0);
+      for (int p = 0; p < (int)P.size(); ++p) {
+        const Box& b = P[p];
+        const long long c = (long long)b.w() * b.h();
+        e.push_back(Entry{m, p, morton((b.i0 + b.i1) / 2, (b.j0 + b.j1) / 2), c});
+        total += c;
+      }
+    }
+    std::stable_sort(e.begin(), e.end(), [](const Entry& a, const Entry& b) {
+      if (a.m != b.m) return a.m < b.m;
+      if (a.key != b.key) return a.key < b.key;
+      return a.p < b.p;
+    });
+    // owner: the rank whose share of the cells holds the patch's middle cell
+    long long before = 0;
+    std::vector<std::vector<PackItem>> per(n);
+    Hier::PartLevel& PL = H->part[l];
+    PL.size.assign(n, 0);
+    for (const Entry& x : e) {
+      int r = 0;
+      if (l > 0 && total > 0) r = (int)std::min<long long>(n - 1, (2 * before + x.cells) * n / (2 * total));
+      before += x.cells;
+      H->owner[x.m][l][x.p] = r;
+      const Box& b = H->mem[x.m].lev[l].patches[x.p];
+      per[r].push_back(PackItem{H->desc_index(x.m, l), b.i0, b.j0, b.i1, b.j1, PL.size[r]});
+      PL.size[r] += pack_doubles(H->cfg.M, b, l + 1 < H->L);
+    }
+    std::vector<PackItem> all;
+    PL.first.assign(n + 1, 0);
+    for (int r = 0; r < n; ++r) {
+      PL.first[r] = (int)all.size();
+      all.insert(all.end(), per[r].begin(), per[r].end());
+    }
+    PL.first[n] = (int)all.size();
+    mlswe_status s = upload_items(H, PL.items, all);
+    if (s != MLSWE_OK) return s;
+  }
+  CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  H->part_dirty = false;
+  return MLSWE_OK;
+}
+
+// Copies between the level arrays and a packed buffer, one block per patch: unpack = 1 writes
+// the level arrays from buf, 0 writes buf. items [first, last) all belong to one owner.
+template <int M>
+__global__ void __launch_bounds__(256)
+part_copy_kernel(const LevelDesc* __restrict__ descs, const PackItem* __restrict__ items, int first, int last,
+                 int par, double* buf, int unpack) {
+  for (int k = first + blockIdx.x; k < last; k += gridDim.x) {
+    const PackItem it = items[k];
+    const LevelDesc& D = descs[it.desc];
+    const int w = it.i1 - it.i0, h = it.j1 - it.j0;
+    const int NX = D.NX, NY = D.NY;
+    double* b = buf + it.off;
+    auto mv = [&](double* level_value, long long t) {
+      if (unpack) *level_value = b[t];
+      else b[t] = *level_value;
+    };
+    // state of the patch cells, field by field
+    const long long ncell = (long long)w * h;
+    const size_t plane = (size_t)NY * D.P;
+    for (long long t = threadIdx.x; t < 3LL * M * ncell; t += blockDim.x) {
+      const int f = (int)(t / ncell);
+      const int c = (int)(t - (long long)f * ncell);
+      const int j = it.j0 + c / w, i = it.i0 + c % w;
+      mv(D.q[par] + f * plane + (size_t)j * D.P + i, t);
+    }
+    b += 3LL * M * ncell;
+    // boundary accumulators: x edges at i0 and i1 of every row, y edges at j0 and j1 of
+    // every column
+    for (int t = threadIdx.x; t < 2 * M * h; t += blockDim.x) {
+      const int m = t / (2 * h), rr = t - m * 2 * h, j = it.j0 + (rr >> 1), a = (rr & 1) ? it.i1 : it.i0;
+      mv(D.fxf + ((size_t)m * NY + j) * (NX + 1) + a, t);
+    }
+    b += 2LL * M * h;
+    for (int t = threadIdx.x; t < 2 * M * w; t += blockDim.x) {
+      const int m = t / (2 * w), rr = t - m * 2 * w, i = it.i0 + (rr >> 1), a = (rr & 1) ? it.j1 : it.j0;
+      mv(D.fyf + ((size_t)m * (NY + 1) + a) * NX + i, t);
+    }
+    b += 2LL * M * w;
+    if (D.fxc != nullptr) {
+      // interface fluxes of every edge of the box, sides included
+      const int wx = w + 1;
+      for (int t = threadIdx.x; t < M * h * wx; t += blockDim.x) {
+        const int m = t / (h * wx), rr = t - m * h * wx, j = it.j0 + rr / wx, a = it.i0 + rr % wx;
+        mv(D.fxc + ((size_t)m * NY + j) * (NX + 1) + a, t);
+      }
+      b += (long long)M * h * wx;
+      const int hy = h + 1;
+      for (int t = threadIdx.x; t < M * hy * w; t += blockDim.x) {
+        const int m = t / (hy * w), rr = t - m * hy * w, a = it.j0 + rr / w, i = it.i0 + rr % w;
+        mv(D.fyc + ((size_t)m * (NY + 1) + a) * NX + i, t);
+      }
+    }
+  }
+}
+
+static cudaError_t launch_part_copy(int M, const LevelDesc* descs, const PackItem* items, int first, int last,
+                                    int par, double* buf, int unpack, int grid, cudaStream_t st) {
+  if (last <= first) return cudaSuccess;
+  const int g = std::min(grid, last - first);
+  if (M == 1) part_copy_kernel<1><<<g, 256, 0, st>>>(descs, items, first, last, par, buf, unpack);
+  else if (M == 3) part_copy_kernel<3><<<g, 256, 0, st>>>(descs, items, first, last, par, buf, unpack);
+  else if (M == 4) part_copy_kernel<4><<<g, 256, 0, st>>>(descs, items, first, last, par, buf, unpack);
+  else part_copy_kernel<2><<<g, 256, 0, st>>>(descs, items, first, last, par, buf, unpack);
+  return cudaGetLastError();
+}
+
+mlswe_status run_exchange_hook(Hier* H, int level) {
+  if (!partitioned(H) || level == 0 || !H->part_hook) return MLSWE_OK;
+  if (H->part_hook(H->part_ctx, level) != 0) return fail(H, MLSWE_EINVAL, "partition exchange hook failed");
+  return MLSWE_OK;
+}
+
+// Argument checks shared by the exchange calls; builds the tables when a layout changed.
+static mlswe_status part_level_ready(Hier* H, int level) {
+  if (level < 1 || level >= H->L) return fail(H, MLSWE_EINVAL, "partition: level must be a refined level");
+  return ensure_partition(H);
+}
+
+static bool device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace mlswe
+
+using namespace mlswe;
+
+extern "C" {
+
+mlswe_status mlswe_set_partition(mlswe_h h, int rank, int world_size, mlswe_exchange_hook hook, void* ctx) {
+  if (!h || world_size < 1 || rank < 0 || rank >= world_size) return fail(h, MLSWE_EINVAL, "partition: bad rank");
+  if (world_size > 1 && (h->cfg.unsplit || h->per_patch_launch))
+    return fail(h, MLSWE_EINVAL, "partition: split step in the batched form only");
+  h->part_rank = world_size > 1 ? rank : 0;
+  h->part_size = world_size;
+  h->part_hook = world_size > 1 ? hook : nullptr;
+  h->part_ctx = ctx;
+  h->part_dirty = true;
+  for (auto& W : h->wl) W.dirty = true;  // the sweeps take this rank's patches
+  invalidate_graphs(h);
+  return ensure_partition(h);
+}
+
+mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner_out) {
+  if (!h || !owner_out || member < 0 || member >= h->n_members || level < 0 || level >= h->L)
+    return fail(h, MLSWE_EINVAL, "partition_owners: bad argument");
+  mlswe_status s = ensure_partition(h);
+  if (s != MLSWE_OK) return s;
+  const std::vector<int>& o = h->owner[member][level];
+  std::copy(o.begin(), o.end(), owner_out);
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, long long* doubles_per_rank) {
+  if (!h || !doubles_per_rank) return fail(h, MLSWE_EINVAL, "partition_sizes: bad argument");
+  mlswe_status s = part_level_ready(h, level);
+  if (s != MLSWE_OK) return s;
+  for (int r = 0; r < h->part_size; ++r) doubles_per_rank[r] = h->part[level].size[r];
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, double* dst) {
+  if (!h || !dst) return fail(h, MLSWE_EINVAL, "partition_pack: bad argument");
+  mlswe_status s = part_level_ready(h, level);
+  if (s != MLSWE_OK) return s;
+  if (!device_pointer(dst)) return fail(h, MLSWE_EINVAL, "partition_pack: dst is not device memory");
+  const Hier::PartLevel& PL = h->part[level];
+  const int r = h->part_rank;
+  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[r], PL.first[r + 1], h->parity[level], dst, 0,
+                               2 * h->num_sms, h->st));
+  h->kernel_launches += PL.first[r + 1] > PL.first[r] ? 1 : 0;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int from, const double* src) {
+  if (!h || !src || from < 0 || from >= h->part_size) return fail(h, MLSWE_EINVAL, "partition_unpack: bad argument");
+  mlswe_status s = part_level_ready(h, level);
+  if (s != MLSWE_OK) return s;
+  if (!device_pointer(src)) return fail(h, MLSWE_EINVAL, "partition_unpack: src is not device memory");
+  const Hier::PartLevel& PL = h->part[level];
+  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[from], PL.first[from + 1], h->parity[level],
+                               const_cast<double*>(src), 1, 2 * h->num_sms, h->st));
+  h->kernel_launches += PL.first[from + 1] > PL.first[from] ? 1 : 0;
+  return MLSWE_OK;
+}
+
+mlswe_status mlswe_wave_speed_slots(mlswe_h h, double** dev, int* n) {
+  if (!h || !dev || !n) return fail(h, MLSWE_EINVAL, "wave_speed_slots: bad argument");
+  *dev = reinterpret_cast<double*>(h->d_smax);
+  *n = 2 * h->n_members * h->L;
+  return MLSWE_OK;
+}
+
+}  // extern "C"

@@ -17,9 +17,17 @@ member's step:
   the next swap overwrites. A time step common to all slabs is the minimum over the ranks
   (min_all).
 
-Data moves only by point-to-point sends into local buffers and by scalar all-reduces
-(NCCL on GPUs, gloo on CPUs); the stepping itself is a callable the caller supplies (the
-CUDA library's level step).
+* The patches of an AMR hierarchy's refined levels split over the ranks. Every rank holds
+  the whole hierarchy; the library sweeps only the rank's own patches of the levels >= 1
+  (owners by a space-filling curve, partition_patches restates the rule) and calls a hook
+  after every refined level step, in which the ranks all-gather their packed patch values
+  and take the maximum of the wave-speed slots (exchange_level; PatchPartition wires it to
+  a Hierarchy). Level 0, ghost fill, coarsening, reflux, time steps and regrids run on
+  every rank on the full state, so every rank's hierarchy equals the undivided one.
+
+Data moves only by point-to-point sends or all-gathers into local buffers and by
+all-reduces (NCCL on GPUs, gloo on CPUs); the stepping itself is a callable the caller
+supplies (the CUDA library's level step) or the library's own driver.
 """
 from __future__ import annotations
 
@@ -113,3 +121,83 @@ def max_all(value, dist, device=None):
 
 def min_all(value, dist, device=None):
     return _reduce(value, dist.ReduceOp.MIN, dist, device)
+
+
+# ---------------------------------------------------------------------- patch partition
+def morton(i: int, j: int) -> int:
+    """Z-order key of a cell index pair: the low 21 bits of i in the even bits, of j in the
+    odd bits."""
+    key = 0
+    for b in range(21):
+        key |= ((i >> b) & 1) << (2 * b)
+        key |= ((j >> b) & 1) << (2 * b + 1)
+    return key
+
+
+def partition_patches(layouts, world_size):
+    """Owner rank of every patch of one refined level over all members (layouts: per member an
+    (n, 4) array of boxes i0, j0, i1, j1). Patches in order of member, then Morton key of the
+    integer centre ((i0 + i1) // 2, (j0 + j1) // 2), then index; with T the cells of all of
+    them and c the cells before a patch, the patch goes to min(n - 1, (2 c + cells) n // (2 T)):
+    the rank whose share of the cells holds the patch's middle cell."""
+    entries = []
+    for m, boxes in enumerate(layouts):
+        for p, (i0, j0, i1, j1) in enumerate(boxes):
+            entries.append((m, morton((i0 + i1) // 2, (j0 + j1) // 2), p, (i1 - i0) * (j1 - j0)))
+    entries.sort()
+    total = sum(e[3] for e in entries)
+    owners = [[0] * len(b) for b in layouts]
+    before = 0
+    for m, _, p, cells in entries:
+        r = min(world_size - 1, (2 * before + cells) * world_size // (2 * total)) if total > 0 else 0
+        owners[m][p] = r
+        before += cells
+    return owners
+
+
+def exchange_level(rank, world_size, sizes, pack, unpack, speeds, dist, new_buffer):
+    """The exchange after a refined level step: every rank packs its patches into a buffer of
+    max(sizes) values (pack(buf)), the buffers are all-gathered, each rank writes the other
+    ranks' patches (unpack(q, buf_q) for q != rank with sizes[q] > 0), and the wave-speed
+    slots become their maximum over the ranks (speeds: a float64 tensor, or None)."""
+    n = max(sizes) if sizes else 0
+    if n > 0:
+        send = new_buffer(n)
+        pack(send)
+        recv = [new_buffer(n) for _ in range(world_size)]
+        dist.all_gather(recv, send)
+        for q in range(world_size):
+            if q != rank and sizes[q] > 0:
+                unpack(q, recv[q])
+    if speeds is not None:
+        dist.all_reduce(speeds, op=dist.ReduceOp.MAX)
+
+
+class _DeviceArray:
+    """A float64 device array the library owns, seen by torch without a copy."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f8", "data": (ptr, False), "version": 2}
+
+
+class PatchPartition:
+    """Partition of a Hierarchy's refined-level patches over the ranks of a process group
+    (NCCL): sets the hierarchy's partition and the exchange hook that mlswe_advance calls.
+    The collectives run on the hierarchy's stream, ordered with its kernels."""
+
+    def __init__(self, H, rank, world_size, dist, device):
+        self.H, self.rank, self.ws, self.dist, self.device = H, rank, world_size, dist, device
+        H.set_partition(rank, world_size, self._exchange)
+
+    def _exchange(self, level):
+        import torch
+        H = self.H
+        stream = torch.cuda.ExternalStream(H.stream, device=self.device)
+        with torch.cuda.stream(stream):
+            ptr, n = H.wave_speed_slots()
+            speeds = torch.as_tensor(_DeviceArray(ptr, n), device=self.device)
+            exchange_level(self.rank, self.ws, H.partition_sizes(level),
+                           lambda buf: H.partition_pack(level, buf.data_ptr()),
+                           lambda q, buf: H.partition_unpack(level, q, buf.data_ptr()),
+                           speeds, self.dist,
+                           lambda k: torch.empty(k, dtype=torch.float64, device=self.device))

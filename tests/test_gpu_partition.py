@@ -1,0 +1,220 @@
+"""Patches of the refined levels split over ranks (mlswe_set_partition), emulated on one GPU in
+one process: each rank is a hierarchy advanced by its own host thread on its own stream, and
+the exchange hook moves the packed patch values and the wave-speed slots between the
+hierarchies through device copies, with host barriers between the phases (no kernel waits on
+another). After the runs every rank's hierarchy must equal the undivided one bit for bit:
+every level's patch cells, the layouts the regrids chose, the times.
+
+* three levels (ratios 2, 2) with regrids, two and three ranks;
+* two members with ratios 4, 4 and the dynamic time ratio, two ranks;
+* the library's owners equal the restated rule (sharding.partition_patches);
+* refusals: a bad rank, the per-patch launch form while partitioned.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1803_01450_gb300 import inputs as I
+from paper_1803_01450_gb300 import sharding as S
+
+pytestmark = pytest.mark.gpu
+
+
+class _Group:
+    def __init__(self, ws):
+        self.ws = ws
+        self.barrier = threading.Barrier(ws, timeout=300)
+        self.bufs = [None] * ws
+        self.speeds = [None] * ws
+        self.calls = [0] * ws
+
+
+def _hook(H, r, grp, dev):
+    import torch
+
+    def hook(level):
+        stream = torch.cuda.ExternalStream(H.stream, device=dev)
+        sizes = H.partition_sizes(level)
+        with torch.cuda.stream(stream):
+            buf = torch.empty(max(max(sizes), 1), dtype=torch.float64, device=dev)
+            if sizes[r] > 0:
+                H.partition_pack(level, buf.data_ptr())
+            ptr, n = H.wave_speed_slots()
+            sp = torch.as_tensor(S._DeviceArray(ptr, n), device=dev)
+            snap = sp.clone()
+        stream.synchronize()
+        grp.bufs[r], grp.speeds[r] = buf, snap
+        grp.calls[r] += 1
+        grp.barrier.wait()
+        with torch.cuda.stream(stream):
+            for q in range(grp.ws):
+                if q != r and sizes[q] > 0:
+                    H.partition_unpack(level, q, grp.bufs[q].data_ptr())
+            sp.copy_(torch.stack(grp.speeds).amax(dim=0))
+        stream.synchronize()
+        grp.barrier.wait()
+
+    return hook
+
+
+def _make(pkg, cfg, members, stream=None):
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, n, n) for n, _, _ in members], stream=stream)
+    for k, (n, q, B) in enumerate(members):
+        H.set_bathymetry(k, B)
+        H.set_state(k, 0, q)
+    return H
+
+
+def _snapshot(H, n_members, L):
+    out = []
+    for k in range(n_members):
+        levels = []
+        for l in range(L):
+            boxes = H.get_patches(k, l)
+            q = H.get_state(k, l)
+            if l == 0:
+                levels.append((boxes, q))
+            else:
+                m = np.zeros(q.shape[1:], bool)
+                for (i0, j0, i1, j1) in boxes.tolist():
+                    m[j0:j1, i0:i1] = True
+                levels.append((boxes, q[:, m]))
+        out.append(levels)
+    return out, H.get_time()[0]
+
+
+def _run_partitioned(pkg, cfg, members, ws, steps, L):
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grp = _Group(ws)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(ws)]
+    hs = [_make(pkg, cfg, members, stream=streams[r].cuda_stream) for r in range(ws)]
+    for r, H in enumerate(hs):
+        H.set_partition(r, ws, _hook(H, r, grp, dev))
+    errors = [None] * ws
+
+    def run(r):
+        try:
+            hs[r].advance(steps)
+        except BaseException as e:  # reported below
+            errors[r] = e
+            grp.barrier.abort()
+
+    threads = [threading.Thread(target=run, args=(r,)) for r in range(ws)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for e in errors:
+        if e is not None:
+            raise e
+    owners = [[H.partition_owners(k, l) for l in range(1, L) for k in range(len(members))] for H in hs]
+    snaps = [_snapshot(H, len(members), L) for H in hs]
+    layouts = [[H.get_patches(k, l) for k in range(len(members))] for l in range(1, L) for H in hs[:1]]
+    for H in hs:
+        H.close()
+    return snaps, owners, layouts, grp.calls
+
+
+def _assert_equal(snap, want):
+    (levels_got, t_got), (levels_want, t_want) = snap, want
+    assert np.array_equal(t_got, t_want)
+    for mg, mw in zip(levels_got, levels_want):
+        for (bg, qg), (bw, qw) in zip(mg, mw):
+            assert np.array_equal(bg, bw)
+            assert np.array_equal(qg, qw)
+
+
+def _three_level_case():
+    n = 40
+    w = I.small(n)
+    return [(n, w["q"], -np.ones((4 * n, 4 * n)))]
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_three_levels_partitioned_equal_undivided(mlswe_lib, ws):
+    pkg = mlswe_lib
+    cfg = pkg.Config(M=2, dry_tol=1e-6, max_levels=3, ratio=[2, 2], flag_tol=1e-3, regrid_interval=3,
+                     min_side=8, max_side=16)
+    members = _three_level_case()
+    H = _make(pkg, cfg, members)
+    H.regrid(0)
+    H.advance(7)
+    want = _snapshot(H, 1, 3)
+    H.close()
+    assert len(want[0][0][2][0]) > 1  # several level-2 patches to split
+
+    # the partitioned runs start from the same regridded layout
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grp = _Group(ws)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(ws)]
+    hs = [_make(pkg, cfg, members, stream=streams[r].cuda_stream) for r in range(ws)]
+    for r, Hr in enumerate(hs):
+        Hr.regrid(0)
+        Hr.set_partition(r, ws, _hook(Hr, r, grp, dev))
+    errors = [None] * ws
+
+    def run(r):
+        try:
+            hs[r].advance(7)
+        except BaseException as e:
+            errors[r] = e
+            grp.barrier.abort()
+
+    threads = [threading.Thread(target=run, args=(r,)) for r in range(ws)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for e in errors:
+        if e is not None:
+            raise e
+    for l in (1, 2):
+        own = hs[0].partition_owners(0, l)
+        assert own.tolist() == S.partition_patches([hs[0].get_patches(0, l).tolist()], ws)[0]
+        assert set(own.tolist()) == set(range(ws))  # every rank sweeps something
+    snaps = [_snapshot(Hr, 1, 3) for Hr in hs]
+    for Hr in hs:
+        Hr.close()
+    assert min(grp.calls) > 0 and len(set(grp.calls)) == 1
+    for snap in snaps:
+        _assert_equal(snap, want)
+
+
+def test_two_members_dynamic_ratio_partitioned_equal_undivided(mlswe_lib):
+    pkg = mlswe_lib
+    cfg = pkg.Config(M=2, dry_tol=1e-6, max_levels=3, ratio=[4, 4], flag_tol=1e-3, regrid_interval=2,
+                     min_side=8, max_side=24, dynamic_rt=1)
+    members = []
+    for k, n in enumerate((24, 32)):
+        w = I.small(n)
+        members.append((n, w["q"], -np.ones((16 * n, 16 * n))))
+    H = _make(pkg, cfg, members)
+    H.advance(5)
+    want = _snapshot(H, 2, 3)
+    H.close()
+    snaps, owners, _, calls = _run_partitioned(pkg, cfg, members, 2, 5, 3)
+    assert min(calls) > 0
+    for snap in snaps:
+        _assert_equal(snap, want)
+    assert all(np.array_equal(a, b) for a, b in zip(owners[0], owners[1]))
+
+
+def test_partition_refusals(mlswe_lib):
+    pkg = mlswe_lib
+    cfg = pkg.Config(M=2, dry_tol=1e-6, max_levels=2, ratio=[2])
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, 16, 16)])
+    for rank, ws in ((2, 2), (-1, 2), (0, 0)):
+        with pytest.raises(pkg.MLSWEError) as e:
+            H.set_partition(rank, ws)
+        assert e.value.status == 1
+    H.set_partition(1, 2)
+    with pytest.raises(pkg.MLSWEError):
+        H.set_execution(use_graphs=True, per_patch_launches=True)
+    with pytest.raises(pkg.MLSWEError):
+        H.partition_sizes(0)  # level 0 is not partitioned
+    H.set_partition(0, 1)
+    H.set_execution(use_graphs=True, per_patch_launches=True)
+    H.close()

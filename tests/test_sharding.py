@@ -58,6 +58,52 @@ def test_slabs_cover_rows_with_halos():
         S.slab_of(5, 4, 0)
 
 
+def _boxes(seed=5, n=40, nx=96, ny=80):
+    """Disjoint boxes of sides 4..16 on an nx x ny grid (seeded, placed by rejection), some of
+    them touching: a refined level's patches."""
+    rng = np.random.default_rng(seed)
+    occ = np.zeros((ny, nx), bool)
+    out = []
+    while len(out) < n:
+        w, h = (int(v) for v in rng.integers(4, 17, 2))
+        i0, j0 = int(rng.integers(0, nx - w + 1)), int(rng.integers(0, ny - h + 1))
+        if not occ[j0:j0 + h, i0:i0 + w].any():
+            occ[j0:j0 + h, i0:i0 + w] = True
+            out.append((i0, j0, i0 + w, j0 + h))
+    return out
+
+
+def test_morton_key_interleaves_bits():
+    assert S.morton(0, 0) == 0 and S.morton(1, 0) == 1 and S.morton(0, 1) == 2 and S.morton(3, 5) == 39
+    assert S.morton(2 ** 20, 0) == 2 ** 40 and S.morton(0, 2 ** 20) == 2 ** 41
+    # Z order: the four quadrants of a 2^k square come one after another
+    keys = {(i, j): S.morton(i, j) for i in range(8) for j in range(8)}
+    quad = lambda i, j: (j // 4) * 2 + i // 4  # noqa: E731
+    order = sorted(keys, key=keys.get)
+    assert [quad(i, j) for i, j in order] == sorted(quad(i, j) for i, j in order)
+
+
+def test_partition_patches_covers_balances_and_follows_the_curve():
+    layouts = [_boxes(5), _boxes(6, n=25), []]
+    cells = [[(b[2] - b[0]) * (b[3] - b[1]) for b in L] for L in layouts]
+    biggest = max(c for cs in cells for c in cs)
+    total = sum(sum(cs) for cs in cells)
+    for ws in (1, 2, 3, 7):
+        owners = S.partition_patches(layouts, ws)
+        assert owners == S.partition_patches(layouts, ws)
+        assert [len(o) for o in owners] == [len(L) for L in layouts]
+        load = [0] * ws
+        seq = []
+        for m, L in enumerate(layouts):
+            for p, b in sorted(enumerate(L), key=lambda e: (S.morton((e[1][0] + e[1][2]) // 2,
+                                                                     (e[1][1] + e[1][3]) // 2), e[0])):
+                load[owners[m][p]] += cells[m][p]
+                seq.append(owners[m][p])
+        assert seq == sorted(seq)  # contiguous runs of the curve, in rank order
+        assert all(abs(x - total / ws) <= biggest for x in load)
+    assert S.partition_patches([[]], 4) == [[]]
+
+
 # ---------------------------------------------------------------------- gloo ranks
 def _members():
     from paper_1803_01450_gb300 import inputs as I
@@ -136,6 +182,78 @@ def _single_slab_run(steps=12):
     return q, t
 
 
+def _patch_case():
+    rng = np.random.default_rng(17)
+    ny, nx = 80, 96
+    return rng.standard_normal((ny, nx)), _boxes(7, n=30, nx=nx, ny=ny)
+
+
+def _patch_step(Q, boxes):
+    """New values of the cells of the given boxes from Q (all from the old Q): a 5-point
+    average reading the ring cells around each box (edges clamped), and the largest |value|."""
+    P = np.pad(Q, 1, mode="edge")
+    new, smax = [], 0.0
+    for (i0, j0, i1, j1) in boxes:
+        c = P[j0 + 1:j1 + 1, i0 + 1:i1 + 1]
+        v = 0.5 * c + 0.125 * (P[j0:j1, i0 + 1:i1 + 1] + P[j0 + 2:j1 + 2, i0 + 1:i1 + 1]
+                               + P[j0 + 1:j1 + 1, i0:i1] + P[j0 + 1:j1 + 1, i0 + 2:i1 + 2])
+        new.append(v)
+        smax = max(smax, float(np.abs(v).max()))
+    return new, smax
+
+
+def _patch_run_single(steps=6):
+    Q, boxes = _patch_case()
+    speeds = []
+    for _ in range(steps):
+        new, smax = _patch_step(Q, boxes)
+        for (i0, j0, i1, j1), v in zip(boxes, new):
+            Q[j0:j1, i0:i1] = v
+        speeds.append(smax)
+    return Q, speeds
+
+
+def _patch_run_rank(rank, ws, dist, steps=6, exchange=True):
+    """Each rank steps only its own boxes, then exchange_level gives it the others' cells and
+    the largest |value| over the ranks."""
+    import torch
+    Q, boxes = _patch_case()
+    owner = S.partition_patches([boxes], ws)[0]
+    mine = [k for k in range(len(boxes)) if owner[k] == rank]
+    cells = lambda k: (boxes[k][2] - boxes[k][0]) * (boxes[k][3] - boxes[k][1])  # noqa: E731
+    sizes = [sum(cells(k) for k in range(len(boxes)) if owner[k] == r) for r in range(ws)]
+    speeds = []
+    for _ in range(steps):
+        new, smax = _patch_step(Q, [boxes[k] for k in mine])
+        for k, v in zip(mine, new):
+            i0, j0, i1, j1 = boxes[k]
+            Q[j0:j1, i0:i1] = v
+        sp = torch.tensor([smax], dtype=torch.float64)
+
+        def pack(buf):
+            flat = np.concatenate([Q[boxes[k][1]:boxes[k][3], boxes[k][0]:boxes[k][2]].ravel() for k in mine]
+                                  or [np.zeros(0)])
+            buf[:flat.size] = torch.from_numpy(flat)
+
+        def unpack(q, buf):
+            o = 0
+            b = buf.numpy()
+            for k in range(len(boxes)):
+                if owner[k] != q:
+                    continue
+                i0, j0, i1, j1 = boxes[k]
+                Q[j0:j1, i0:i1] = b[o:o + cells(k)].reshape(j1 - j0, i1 - i0)
+                o += cells(k)
+
+        if exchange:
+            S.exchange_level(rank, ws, sizes, pack, unpack, sp, dist,
+                             lambda n: torch.zeros(n, dtype=torch.float64))
+        else:
+            dist.all_reduce(sp, op=dist.ReduceOp.MAX)
+        speeds.append(float(sp[0]))
+    return Q, speeds
+
+
 def _worker(rank, ws, port, out_dir, what):
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
@@ -155,6 +273,12 @@ def _worker(rank, ws, port, out_dir, what):
                     allres.update(g)
                 np.save(os.path.join(out_dir, "members.npy"), np.array([allres, total, parts], dtype=object),
                         allow_pickle=True)
+        elif what in ("patches", "patches_no_exchange"):
+            Q, speeds = _patch_run_rank(rank, ws, dist, exchange=(what == "patches"))
+            gathered = [None] * ws
+            dist.all_gather_object(gathered, (rank, Q, speeds))
+            if rank == 0:
+                np.save(os.path.join(out_dir, "patches.npy"), np.array(gathered, dtype=object), allow_pickle=True)
         else:
             if what == "slabs_halo1":
                 S.HALO = 1  # planted: one halo row where the stencil reaches two
@@ -205,3 +329,24 @@ def test_planted_one_row_halo_fails(tmp_path):
     want, _ = _single_slab_run()
     got = np.concatenate([g[1] for g in gathered], axis=1)
     assert got.shape == want.shape and not np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_patches_partitioned_with_exchange_equal_undivided(tmp_path, ws):
+    """Every rank steps its own boxes of a refined level (owners by partition_patches), then
+    all-gathers the packed cells and takes the largest speed (exchange_level): every rank's
+    whole array equals the undivided run's, step after step, and so do the speeds."""
+    _spawn(ws, tmp_path, "patches")
+    gathered = np.load(tmp_path / "patches.npy", allow_pickle=True)
+    want, speeds = _patch_run_single()
+    for _, Q, sp in gathered:
+        assert np.array_equal(Q, want)
+        assert sp == speeds
+
+
+def test_planted_missing_exchange_fails(tmp_path):
+    """Without the all-gather each rank's ring cells from the other ranks' boxes go stale."""
+    _spawn(2, tmp_path, "patches_no_exchange")
+    gathered = np.load(tmp_path / "patches.npy", allow_pickle=True)
+    want, _ = _patch_run_single()
+    assert not all(np.array_equal(Q, want) for _, Q, _ in gathered)
