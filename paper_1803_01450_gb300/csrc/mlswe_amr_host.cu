@@ -27,7 +27,7 @@ cudaError_t launch_speed(int M, const DevParams& P, const LevelDesc* descs, cons
                          cudaStream_t st);
 std::vector<Box> cluster_flags(const uint8_t* flags, int nx, int ny, int level, const std::vector<Box>& patches,
                                int r, int n_buf, double eff, int min_side, int max_side, int n_nest);
-std::vector<Box> box_difference(const Box& a, const std::vector<Box>& sub);
+std::vector<Box> fresh_cells(const std::vector<Box>& boxes, const std::vector<Box>& old);
 void set_level_shape(Hier* H, int level, int dir, int len, int lines, int ctas);
 
 constexpr int kNest = 2;    // nesting margin in coarse cells
@@ -450,12 +450,7 @@ static mlswe_status regrid_internal(Hier* H, int base) {
       const std::vector<Box> old = Fl.patches;
       mlswe_status s = set_patches_internal(H, m, l + 1, boxes);
       if (s != MLSWE_OK) return s;
-      std::vector<Box> fresh;
-      for (const Box& b : boxes) {
-        std::vector<Box> d = box_difference(b, old);
-        fresh.insert(fresh.end(), d.begin(), d.end());
-      }
-      s = interp_boxes(H, m, l, fresh);
+      s = interp_boxes(H, m, l, fresh_cells(boxes, old));
       if (s != MLSWE_OK) return s;
     }
   }

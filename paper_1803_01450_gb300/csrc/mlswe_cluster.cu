@@ -23,36 +23,27 @@
 namespace mlswe {
 
 void dilate_flags(const uint8_t* in, int nx, int ny, int n, std::vector<uint8_t>& out) {
-  // Separable max filter with sliding-window counts (a cell is set when its window of
-  // 2n + 1 holds a flag): along each row, then down the columns one row at a time, so both
-  // passes read memory in row order.
+  // Separable max filter (a cell is set when its (2n + 1) x (2n + 1) window holds a flag):
+  // along each row, the OR of the row shifted by -n .. n, then down the columns, the OR of
+  // rows j - n .. j + n; every inner loop is a straight byte OR over a row (vectorised), and
+  // both passes read memory in row order.
   std::vector<uint8_t> tmp((size_t)nx * ny, 0);
   out.assign((size_t)nx * ny, 0);
   for (int j = 0; j < ny; ++j) {
     const uint8_t* row = in + (size_t)j * nx;
     uint8_t* t = &tmp[(size_t)j * nx];
-    int c = 0;
-    for (int i = 0; i <= std::min(n, nx - 1); ++i) c += row[i];
-    for (int i = 0; i < nx; ++i) {
-      t[i] = c > 0;
-      if (i + n + 1 < nx) c += row[i + n + 1];
-      if (i - n >= 0) c -= row[i - n];
+    for (int k = -n; k <= n; ++k) {
+      const int i0 = std::max(0, -k), i1 = std::min(nx, nx - k);
+      for (int i = i0; i < i1; ++i) t[i] |= row[i + k];
     }
   }
-  std::vector<int> cnt(nx, 0);
-  for (int k = 0; k <= std::min(n, ny - 1); ++k)
-    for (int i = 0; i < nx; ++i) cnt[i] += tmp[(size_t)k * nx + i];
   for (int j = 0; j < ny; ++j) {
     uint8_t* o = &out[(size_t)j * nx];
-    for (int i = 0; i < nx; ++i) o[i] = cnt[i] > 0;
-    if (j + n + 1 < ny) {
-      const uint8_t* a = &tmp[(size_t)(j + n + 1) * nx];
-      for (int i = 0; i < nx; ++i) cnt[i] += a[i];
+    for (int k = std::max(0, j - n); k <= std::min(ny - 1, j + n); ++k) {
+      const uint8_t* a = &tmp[(size_t)k * nx];
+      for (int i = 0; i < nx; ++i) o[i] |= a[i];
     }
-    if (j - n >= 0) {
-      const uint8_t* b = &tmp[(size_t)(j - n) * nx];
-      for (int i = 0; i < nx; ++i) cnt[i] -= b[i];
-    }
+    for (int i = 0; i < nx; ++i) o[i] = o[i] != 0;
   }
 }
 
@@ -205,6 +196,41 @@ std::vector<Box> box_difference(const Box& a, const std::vector<Box>& sub) {
     cur.swap(nxt);
   }
   return cur;
+}
+
+// The cells of `boxes` outside every box of `old`, as boxes: box_difference of each new box
+// against the old boxes that can touch it, found through buckets of kBucket x kBucket cells
+// (each old box is listed in every bucket it overlaps; candidates keep their order in `old`).
+std::vector<Box> fresh_cells(const std::vector<Box>& boxes, const std::vector<Box>& old) {
+  constexpr int kBucket = 64;
+  int ni = 1, nj = 1;
+  for (const Box& b : old) {
+    ni = std::max(ni, (b.i1 + kBucket - 1) / kBucket);
+    nj = std::max(nj, (b.j1 + kBucket - 1) / kBucket);
+  }
+  std::vector<std::vector<int>> bucket((size_t)ni * nj);
+  for (int k = 0; k < (int)old.size(); ++k) {
+    const Box& b = old[k];
+    for (int bj = b.j0 / kBucket; bj <= (b.j1 - 1) / kBucket; ++bj)
+      for (int bi = b.i0 / kBucket; bi <= (b.i1 - 1) / kBucket; ++bi) bucket[(size_t)bj * ni + bi].push_back(k);
+  }
+  std::vector<Box> out, cand;
+  std::vector<int> idx;
+  std::vector<char> seen(old.size(), 0);
+  for (const Box& a : boxes) {
+    idx.clear();
+    const int bj1 = std::min(nj - 1, (a.j1 - 1) / kBucket), bi1 = std::min(ni - 1, (a.i1 - 1) / kBucket);
+    for (int bj = a.j0 / kBucket; bj <= bj1; ++bj)
+      for (int bi = a.i0 / kBucket; bi <= bi1; ++bi)
+        for (int k : bucket[(size_t)bj * ni + bi])
+          if (!seen[k]) { seen[k] = 1; idx.push_back(k); }
+    std::sort(idx.begin(), idx.end());
+    cand.clear();
+    for (int k : idx) { cand.push_back(old[k]); seen[k] = 0; }
+    const std::vector<Box> d = box_difference(a, cand);
+    out.insert(out.end(), d.begin(), d.end());
+  }
+  return out;
 }
 
 }  // namespace mlswe

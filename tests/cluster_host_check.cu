@@ -8,6 +8,7 @@ namespace mlswe {
 void dilate_flags(const uint8_t* in, int nx, int ny, int n, std::vector<uint8_t>& out);
 std::vector<Box> cluster_flags(const uint8_t* flags, int nx, int ny, int level, const std::vector<Box>& patches,
                                int r, int n_buf, double eff, int min_side, int max_side, int n_nest);
+std::vector<Box> fresh_cells(const std::vector<Box>& boxes, const std::vector<Box>& old);
 }
 
 extern "C" {
@@ -29,6 +30,20 @@ int hc_cluster(const uint8_t* flags, int nx, int ny, int level, const int* patch
     out[4 * k] = b[k].i0; out[4 * k + 1] = b[k].j0; out[4 * k + 2] = b[k].i1; out[4 * k + 3] = b[k].j1;
   }
   return (int)b.size();
+}
+
+
+// Boxes of the cells of `boxes` outside every box of `old` (the regrid's new cells); returns
+// the count, writes at most cap boxes.
+int hc_fresh(const int* boxes, int nb, const int* old, int no, int* out, int cap) {
+  std::vector<mlswe::Box> B, O;
+  for (int k = 0; k < nb; ++k) B.push_back(mlswe::Box{boxes[4 * k], boxes[4 * k + 1], boxes[4 * k + 2], boxes[4 * k + 3]});
+  for (int k = 0; k < no; ++k) O.push_back(mlswe::Box{old[4 * k], old[4 * k + 1], old[4 * k + 2], old[4 * k + 3]});
+  std::vector<mlswe::Box> f = mlswe::fresh_cells(B, O);
+  for (int k = 0; k < (int)f.size() && k < cap; ++k) {
+    out[4 * k] = f[k].i0; out[4 * k + 1] = f[k].j0; out[4 * k + 2] = f[k].i1; out[4 * k + 3] = f[k].j1;
+  }
+  return (int)f.size();
 }
 
 }

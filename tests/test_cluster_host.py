@@ -33,6 +33,8 @@ def hc(tmp_path_factory):
     L.hc_cluster.argtypes = [u8, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int,
                              ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int]
     L.hc_cluster.restype = ctypes.c_int
+    L.hc_fresh.argtypes = [ip, ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_int]
+    L.hc_fresh.restype = ctypes.c_int
     return L
 
 
@@ -88,3 +90,44 @@ def test_clustering_matches_oracle(hc, seed):
     n = hc.hc_cluster(_u8(f), nx, ny, level, pa.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(patches), r, 2,
                       0.7, min_side, max_side, 2, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), cap)
     assert [tuple(b) for b in out[:n].tolist()] == [tuple(b) for b in want]
+
+
+def _disjoint_boxes(rng, n, nx, ny, lo, hi):
+    occ = np.zeros((ny, nx), bool)
+    out = []
+    for _ in range(20 * n):
+        if len(out) == n:
+            break
+        w, h = (int(v) for v in rng.integers(lo, hi + 1, 2))
+        i0, j0 = int(rng.integers(0, nx - w + 1)), int(rng.integers(0, ny - h + 1))
+        if not occ[j0:j0 + h, i0:i0 + w].any():
+            occ[j0:j0 + h, i0:i0 + w] = True
+            out.append((i0, j0, i0 + w, j0 + h))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_fresh_cells_are_new_minus_old(hc, seed):
+    """The regrid fills the cells of the new layout that no old patch held: the boxes the
+    library returns are disjoint and cover exactly those cells (boxes spanning several
+    64-cell buckets and none at all included)."""
+    rng = np.random.default_rng(700 + seed)
+    nx, ny = 300, 260
+    new = _disjoint_boxes(rng, int(rng.integers(0, 60)), nx, ny, 4, 90)
+    old = _disjoint_boxes(rng, int(rng.integers(0, 60)), nx, ny, 4, 90)
+    ip = ctypes.POINTER(ctypes.c_int)
+    a = np.ascontiguousarray(np.array(new, dtype=np.int32).reshape(-1, 4))
+    b = np.ascontiguousarray(np.array(old, dtype=np.int32).reshape(-1, 4))
+    cap = 100000
+    out = np.zeros((cap, 4), np.int32)
+    n = hc.hc_fresh(a.ctypes.data_as(ip), len(new), b.ctypes.data_as(ip), len(old), out.ctypes.data_as(ip), cap)
+    cnt = np.zeros((ny, nx), np.int32)
+    for (i0, j0, i1, j1) in out[:n].tolist():
+        assert i0 < i1 and j0 < j1
+        cnt[j0:j1, i0:i1] += 1
+    want = np.zeros((ny, nx), bool)
+    for (i0, j0, i1, j1) in new:
+        want[j0:j1, i0:i1] = True
+    for (i0, j0, i1, j1) in old:
+        want[j0:j1, i0:i1] = False
+    assert cnt.max() <= 1 and np.array_equal(cnt.astype(bool), want)
