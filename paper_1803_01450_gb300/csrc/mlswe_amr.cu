@@ -363,9 +363,11 @@ average_items_kernel(int F, const LevelDesc* __restrict__ descs, const InterpIte
     const double* __restrict__ qf = Fd.q[par_f];
     double* __restrict__ qc = C.q[par_c];
     const size_t fplane = (size_t)Fd.NY * Fd.P, cplane = (size_t)C.NY * C.P;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int i = item.i0 + t % w, j = item.j0 + t / w;
-      for (int f = 0; f < F; ++f) {
+    // one thread per (field, coarse cell): small items still fill the block
+    for (int t = threadIdx.x; t < F * total; t += blockDim.x) {
+      const int f = t / total, c = t - f * total;
+      const int i = item.i0 + c % w, j = item.j0 + c / w;
+      {
         const double* __restrict__ src = qf + f * fplane + (size_t)(j * r) * Fd.P + (size_t)i * r;
         double s = 0.0;
         if constexpr (RC > 0) {

@@ -132,14 +132,36 @@ part_copy_kernel(const LevelDesc* __restrict__ descs, const PackItem* __restrict
       if (unpack) *level_value = b[t];
       else b[t] = *level_value;
     };
-    // state of the patch cells, field by field
+    // state of the patch cells, field by field: a warp per row (3M h rows), its lanes along
+    // the row (coalesced, no division per value)
     const long long ncell = (long long)w * h;
     const size_t plane = (size_t)NY * D.P;
-    for (long long t = threadIdx.x; t < 3LL * M * ncell; t += blockDim.x) {
-      const int f = (int)(t / ncell);
-      const int c = (int)(t - (long long)f * ncell);
-      const int j = it.j0 + c / w, i = it.i0 + c % w;
-      mv(D.q[par] + f * plane + (size_t)j * D.P + i, t);
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int nrow = 3 * M * h;
+    for (int row0 = (threadIdx.x >> 5) * 4; row0 < nrow; row0 += nwarp * 4) {
+      // four rows per warp at a time: their loads are issued before their stores
+      for (int i = lane; i < w; i += 32) {
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int row = row0 + k;
+          if (row < nrow) {
+            const int f = row / h, j = it.j0 + (row - f * h);
+            double* lv = D.q[par] + f * plane + (size_t)j * D.P + it.i0 + i;
+            v[k] = unpack ? b[(long long)row * w + i] : *lv;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int row = row0 + k;
+          if (row < nrow) {
+            const int f = row / h, j = it.j0 + (row - f * h);
+            double* lv = D.q[par] + f * plane + (size_t)j * D.P + it.i0 + i;
+            if (unpack) *lv = v[k];
+            else b[(long long)row * w + i] = v[k];
+          }
+        }
+      }
     }
     b += 3LL * M * ncell;
     // boundary accumulators: x edges at i0 and i1 of every row, y edges at j0 and j1 of
@@ -249,7 +271,7 @@ mlswe_status mlswe_partition_pack(mlswe_h h, int level, double* dst) {
   const Hier::PartLevel& PL = h->part[level];
   const int r = h->part_rank;
   CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[r], PL.first[r + 1], h->parity[level], dst, 0,
-                               2 * h->num_sms, h->st));
+                               8 * h->num_sms, h->st));
   h->kernel_launches += PL.first[r + 1] > PL.first[r] ? 1 : 0;
   return MLSWE_OK;
 }
@@ -261,7 +283,7 @@ mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int from, const double
   if (!device_pointer(src)) return fail(h, MLSWE_EINVAL, "partition_unpack: src is not device memory");
   const Hier::PartLevel& PL = h->part[level];
   CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[from], PL.first[from + 1], h->parity[level],
-                               const_cast<double*>(src), 1, 2 * h->num_sms, h->st));
+                               const_cast<double*>(src), 1, 8 * h->num_sms, h->st));
   h->kernel_launches += PL.first[from + 1] > PL.first[from] ? 1 : 0;
   return MLSWE_OK;
 }
