@@ -62,6 +62,23 @@ __device__ void coarse_cell(const LevelDesc& C, const double* qo, const double* 
   B = C.B[o];
 }
 
+// k / rt for the substeps of a level (0 <= k < rt <= 4 with the ratios 2 and 4): the quotients
+// folded at compile time (correctly rounded, as the division is), so the ghost fill does not
+// divide per ring cell; other values divide.
+__device__ __forceinline__ double substep_fraction(int k, int rt) {
+  if (k < 0 || k >= rt || rt > 4) return (double)k / (double)rt;
+  switch (rt * 4 + k) {
+    case 4: case 8: case 12: case 16: return 0.0;
+    case 9: return 1.0 / 2.0;
+    case 13: return 1.0 / 3.0;
+    case 14: return 2.0 / 3.0;
+    case 17: return 1.0 / 4.0;
+    case 18: return 2.0 / 4.0;
+    case 19: return 3.0 / 4.0;
+    default: return (double)k / (double)rt;
+  }
+}
+
 // Refinement organised per coarse cell (used by the new-patch fill and the ghost fill): the
 // coarse cell's state and its four face neighbours' at alpha are loaded once, the wet flags,
 // surfaces and minmod slopes of every layer formed once, and then each of its R x R fine
@@ -253,7 +270,7 @@ ghost_cells_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Ghost
     double alpha = alpha_in;
     if (substep >= 0) {
       if (Fd.active != nullptr && *Fd.active == 0) continue;
-      alpha = (double)substep / (double)(*Fd.rt);
+      alpha = substep_fraction(substep, *Fd.rt);
     }
     const double* qo = C.q[par_c ^ 1];
     const double* qn = C.q[par_c];
