@@ -7,6 +7,7 @@ every level's patch cells, the layouts the regrids chose, the times.
 
 * three levels (ratios 2, 2) with regrids, two and three ranks;
 * two members with ratios 4, 4 and the dynamic time ratio, two ranks;
+* four ranks for two patches (ranks with nothing to sweep or send);
 * the library's owners equal the restated rule (sharding.partition_patches);
 * refusals: a bad rank, the per-patch launch form while partitioned.
 """
@@ -200,6 +201,62 @@ def test_two_members_dynamic_ratio_partitioned_equal_undivided(mlswe_lib):
     for snap in snaps:
         _assert_equal(snap, want)
     assert all(np.array_equal(a, b) for a, b in zip(owners[0], owners[1]))
+
+
+def test_more_ranks_than_patches(mlswe_lib):
+    """Four ranks, two level-1 patches set by hand (no regrid): two ranks own no patch (empty
+    sweeps and packed buffers), the run still equals the undivided one."""
+    import torch
+    pkg = mlswe_lib
+    n = 32
+    w = I.small(n)
+    cfg = pkg.Config(M=2, dry_tol=1e-6, max_levels=2, ratio=[2], regrid_interval=0, min_side=8, max_side=32)
+    boxes = np.array([[8, 8, 32, 40], [32, 8, 56, 24]], dtype=np.int32)
+
+    def make(stream=None):
+        H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1.0, 1.0, n, n)], stream=stream)
+        H.set_bathymetry(0, -np.ones((2 * n, 2 * n)))
+        H.set_state(0, 0, w["q"])
+        H.set_patches(0, 1, boxes)
+        H.interp_fine(0, 0)
+        return H
+
+    H = make()
+    H.advance(4)
+    want = _snapshot(H, 1, 2)
+    H.close()
+    ws = 4
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grp = _Group(ws)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(ws)]
+    hs = [make(streams[r].cuda_stream) for r in range(ws)]
+    for r, Hr in enumerate(hs):
+        Hr.set_partition(r, ws, _hook(Hr, r, grp, dev))
+    owners = hs[0].partition_owners(0, 1).tolist()
+    assert len(set(owners)) == 2 and owners == S.partition_patches([boxes.tolist()], ws)[0]
+    assert sum(1 for x in hs[0].partition_sizes(1) if x == 0) == 2
+    errors = [None] * ws
+
+    def run(r):
+        try:
+            hs[r].advance(4)
+        except BaseException as e:
+            errors[r] = e
+            grp.barrier.abort()
+
+    threads = [threading.Thread(target=run, args=(r,)) for r in range(ws)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for e in errors:
+        if e is not None:
+            raise e
+    snaps = [_snapshot(Hr, 1, 2) for Hr in hs]
+    for Hr in hs:
+        Hr.close()
+    for snap in snaps:
+        _assert_equal(snap, want)
 
 
 def test_partition_refusals(mlswe_lib):
