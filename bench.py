@@ -949,7 +949,9 @@ def run_gpu(args):
             line["ensemble_partitioned"] = part
             line["slabs"] = slabs
             line["amr_partitioned"] = amr_part
-    if rank == 0 and not args.no_amr:
+    if rank == 0 and ws == 1 and not args.no_amr:
+        # single-GPU figures (with N > 1 GPUs they would hold every GPU while rank 0 repeats
+        # the N = 1 run's numbers)
         line["batched_amr"] = bench_batched_amr(pkg, torch, stream)
         line["ensemble"] = bench_ensemble(pkg, torch, stream)
         line["adjoint"] = bench_adjoint_forms(pkg, torch, stream)
