@@ -915,6 +915,7 @@ def run_gpu(args):
     lcu_per_step = N_CELLS * N_CELLS * M_LAYERS
     tmax = max_over_ranks(ms, ws, dev)
     value = job_value(lcu_per_step, args.steps, ws, tmax)
+    e2e_value = job_value(lcu_per_step, e2e_steps, ws, max_over_ranks(e2e_s * 1e3, ws, dev))
 
     sx_ms, sx_n = per_kernel["sweep_x"]
     sy_ms, sy_n = per_kernel["sweep_y"]
@@ -937,8 +938,8 @@ def run_gpu(args):
         "gpu_launches": total_launches,
         "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in per_kernel.items() if v[1]},
         "roofline": roof,
-        "e2e": {"value": lcu_per_step * e2e_steps / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(w["q"].nbytes + xy.nbytes), "d2h_bytes_per_step": 32 * M_LAYERS * 8},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(w["q"].nbytes + xy.nbytes) * ws, "d2h_bytes_per_step": 32 * M_LAYERS * 8 * ws},
     }
     if ws > 1 and not args.no_amr:
         # work split over the ranks (every rank takes part): members partitioned, one grid in slabs
