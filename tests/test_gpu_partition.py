@@ -8,6 +8,7 @@ every level's patch cells, the layouts the regrids chose, the times.
 * three levels (ratios 2, 2) with regrids, two and three ranks;
 * two members with ratios 4, 4 and the dynamic time ratio, two ranks;
 * four ranks for two patches (ranks with nothing to sweep or send);
+* a coarse step forced above cfl_max, rejected and retaken alike on every rank;
 * the library's owners equal the restated rule (sharding.partition_patches);
 * refusals: a bad rank, the per-patch launch form while partitioned.
 """
@@ -255,6 +256,70 @@ def test_more_ranks_than_patches(mlswe_lib):
     snaps = [_snapshot(Hr, 1, 2) for Hr in hs]
     for Hr in hs:
         Hr.close()
+    for snap in snaps:
+        _assert_equal(snap, want)
+
+
+def _scale_speeds(H, scale):
+    """The wave speeds the next time step comes from, times scale (through the clock record):
+    a scale below one makes the next attempt exceed cfl_max."""
+    c = H.get_clock()
+    n, L = H.n_members, H.cfg.max_levels
+    c[n:n + 2 * n * L] *= scale
+    H.set_clock(c)
+
+
+def test_courant_retakes_partitioned_equal_undivided(mlswe_lib):
+    """A coarse step forced above cfl_max (speeds scaled to 40 % before it) is rejected and
+    retaken on every rank alike: the ranks' Courant decisions come from the max-reduced speeds,
+    the restores and retakes run on their own hierarchies, and they end equal to the undivided
+    run, with the same rejection count."""
+    import torch
+    pkg = mlswe_lib
+    cfg = pkg.Config(M=2, dry_tol=1e-6, max_levels=3, ratio=[2, 2], flag_tol=1e-3, regrid_interval=3,
+                     min_side=8, max_side=16)
+    members = _three_level_case()
+    H = _make(pkg, cfg, members)
+    H.advance(2)
+    _scale_speeds(H, 0.4)
+    H.advance(3)
+    want = _snapshot(H, 1, 3)
+    rejected = H.get_stats()["cfl_exceeded"]
+    H.close()
+    assert rejected > 0
+    ws = 2
+    dev = torch.device("cuda", torch.cuda.current_device())
+    grp = _Group(ws)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(ws)]
+    hs = [_make(pkg, cfg, members, stream=streams[r].cuda_stream) for r in range(ws)]
+    for r, Hr in enumerate(hs):
+        Hr.set_partition(r, ws, _hook(Hr, r, grp, dev))
+    errors = [None] * ws
+
+    def run(r, k):
+        try:
+            hs[r].advance(k)
+        except BaseException as e:
+            errors[r] = e
+            grp.barrier.abort()
+
+    for k, scale in ((2, 0.4), (3, None)):
+        threads = [threading.Thread(target=run, args=(r, k)) for r in range(ws)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        for e in errors:
+            if e is not None:
+                raise e
+        if scale is not None:
+            for Hr in hs:
+                _scale_speeds(Hr, scale)
+    snaps = [_snapshot(Hr, 1, 3) for Hr in hs]
+    counts = [Hr.get_stats()["cfl_exceeded"] for Hr in hs]
+    for Hr in hs:
+        Hr.close()
+    assert counts == [rejected] * ws
     for snap in snaps:
         _assert_equal(snap, want)
 
