@@ -2,8 +2,9 @@
 figures) at full size: one step in the benchmark's launch configuration (autotuned tiles, one
 CTA per SM), and sampled output cells checked against the oracle on their 9 x 9 input windows
 (the split second-order step reaches four cells), within 1e-11 of each field's scale
-(state_scale). The samples include shelf cells where the lower layers end (the per-layer
-branch of the edge solve) besides the deep water of the coupled M-layer branch."""
+(state_scale); the three-layer workload also through the unsplit step. The samples include
+shelf cells where the lower layers end (the per-layer branch of the edge solve) besides the
+deep water of the coupled M-layer branch."""
 import numpy as np
 import pytest
 
@@ -47,3 +48,35 @@ def test_multilayer_full_size_sampled(mlswe_lib, orc, M):
         worst = np.maximum(worst, err)
         assert err.max() < TOL, (j, i, err)
     report(f"scale_2048_M{M}_sampled", worst)
+
+
+def test_three_layer_unsplit_full_size_sampled(mlswe_lib, orc):
+    """The same three-layer workload through the unsplit step (transverse Riemann solves),
+    sampled the same way (a cell's unsplit update reads cells within two of it, corners
+    included)."""
+    pkg = mlswe_lib
+    n, M = 2048, 3
+    w = I.scale3(n, seed=1000)
+    q, B = w["q"], w["B"]
+    cfg = pkg.Config(M=M, rho=RHO[M], dry_tol=w["dry_tol"], order=2, limiter=2, max_levels=1, unsplit=1)
+    H = pkg.Hierarchy(cfg, [(0.0, 0.0, 1e5, 1e5, n, n)])
+    H.set_bathymetry(0, B)
+    H.set_state(0, 0, q)
+    dt = 0.9 * w["dx"] / 205.0
+    H.step_level(0, dt=dt)
+    qg = H.get_state(0, 0)
+    H.close()
+    P = orc.params(M=M, rho=RHO[M], dry_tol=w["dry_tol"], order=2, limiter=2, unsplit=1)
+    rs = np.random.default_rng(23)
+    cells = [(int(rs.integers(4, n - 4)), int(rs.integers(4, n - 4))) for _ in range(32)]
+    cells += [(int(rs.integers(4, n - 4)), int(rs.integers(int(0.62 * n), n - 4))) for _ in range(8)]
+    scale = np.maximum(state_scale(qg, M), state_scale(q, M))
+    worst = np.zeros(3 * M)
+    for (j, i) in cells:
+        sub = np.ascontiguousarray(q[:, j - 4:j + 5, i - 4:i + 5])
+        subB = np.ascontiguousarray(B[j - 4:j + 5, i - 4:i + 5])
+        orc.step_patch(P, sub, subB, w["dx"], w["dy"], dt)
+        err = np.abs(qg[:, j, i] - sub[:, 4, 4]) / scale
+        worst = np.maximum(worst, err)
+        assert err.max() < TOL, (j, i, err)
+    report("unsplit_scale_2048_M3_sampled", worst)
