@@ -37,23 +37,16 @@ __host__ __device__ constexpr size_t sweep_smem_doubles(int M) {
          ((size_t)kMaxEdges * 4 + kMaxCells + 7) / 8;
 }
 
-// Largest |s| of a tile, then one atomicMax on the bit pattern. v holds |s| as a bit pattern
-// with the sign cleared, so non-negative doubles order like their unsigned 64-bit patterns
-// and a NaN (exponent all ones, mantissa not zero) lies above +inf: reducing the patterns
-// with an integer max keeps a non-finite speed visible to the host (fmax would drop it).
-__device__ __forceinline__ void block_max_atomic(double v, unsigned long long* dst, double* red) {
+// Largest |s| of a warp folded into the tile's shared maximum (no barrier of its own: the
+// phase barrier that follows orders it before thread 0 reads the tile's maximum). v holds |s|
+// as a bit pattern with the sign cleared, so non-negative doubles order like their unsigned
+// 64-bit patterns and a NaN (exponent all ones, mantissa not zero) lies above +inf: reducing
+// the patterns with an integer max keeps a non-finite speed visible to the host (fmax would
+// drop it).
+__device__ __forceinline__ void warp_max_to_shared(double v, unsigned long long* tile_max) {
   unsigned long long b = (unsigned long long)__double_as_longlong(v);
   for (int o = 16; o > 0; o >>= 1) b = umax64(b, __shfl_xor_sync(0xffffffffu, b, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = __longlong_as_double((long long)b);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long m = (unsigned long long)__double_as_longlong(red[0]);
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-      m = umax64(m, (unsigned long long)__double_as_longlong(red[k]));
-    atomicMax(dst, m);
-  }
-  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicMax(tile_max, b);
 }
 
 // MINB: CTAs resident per SM the build targets (1: up to 255 registers per thread; 2: at
@@ -84,7 +77,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
   // (M >= 3) the eigenvalues of the coupling matrix [M][kMaxEdges]
   double* hbw = reinterpret_cast<double*>(smem) + sweep_smem_doubles(M);
   double* muw = hbw + M * kMaxEdges;
-  __shared__ double red[kThreads / 32];
+  __shared__ unsigned long long s_smax;  // largest |s| of the tile (bit pattern)
   // The tile's groups (items tile_off[it] .. tile_off[it + 1], or item it alone), all of one
   // (member, level), and their running counts of cells, edges, cell contributions and updates.
   __shared__ SweepItem sg[kMaxGroups];
@@ -107,6 +100,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
       sng = g1 - g0;
       sb[0][g1 - g0] = c; sb[1][g1 - g0] = e; sb[2][g1 - g0] = gc; sb[3][g1 - g0] = u;
       s_rec = rc;
+      s_smax = 0ull;
     }
     __syncthreads();
     const int ngrp = sng;
@@ -282,6 +276,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         if (e <= len || (item.flags & 2)) lost += lst;
       }
     }
+    if (record && s_rec) warp_max_to_shared(smax, &s_smax);
     __syncthreads();
 
     // ---- phase 3: fluctuations + limited correction -> left/right cell contributions ----
@@ -532,7 +527,7 @@ sweep_kernel(DevParams P, const LevelDesc* __restrict__ descs, const SweepItem* 
         qout[(3 * m + 2) * plane + o] = DIR == 0 ? qn[3 * m + 2] : qn[3 * m + 1];
       }
     }
-    if (record && s_rec) block_max_atomic(smax, &smax_bits[sg[0].desc * 2 + DIR], red);
+    if (record && s_rec && threadIdx.x == 0) atomicMax(&smax_bits[sg[0].desc * 2 + DIR], s_smax);
     if (lost_count) {
       for (int o = 16; o > 0; o >>= 1) lost += __shfl_xor_sync(0xffffffffu, lost, o);
       if ((threadIdx.x & 31) == 0 && lost) atomicAdd(lost_count, (unsigned)lost);
