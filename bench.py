@@ -71,7 +71,7 @@ HBM_PEAK_GBS = _measured_hbm_gbs()
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per launch of the x sweep on the headline workload (ncu, see profiles/); None
 # while the kernel has changed since the last capture.
-SWEEP_X_DRAM_BYTES = 402.3e6
+SWEEP_X_DRAM_BYTES = 401.5e6
 
 
 class ClockSampler:
