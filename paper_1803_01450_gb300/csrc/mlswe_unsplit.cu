@@ -34,7 +34,7 @@ unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Sw
                       const int* __restrict__ n_items_dev, int parity, int record) {
   static_assert(kUpdRows * 32 == kThreads && kUpdLen < 32, "one warp per row, one spare lane");
   constexpr int F = 3 * M;
-  __shared__ double gys[F][kUpdRows + 1][32];  // sums of the y edges below rows 0 .. nl (row nl: above nl - 1)
+  __shared__ double gys[3][kUpdRows + 1][32];  // one layer's sums of the y edges below rows 0 .. nl (row nl: above nl - 1)
   const int lane = threadIdx.x & 31, l = threadIdx.x >> 5;
   const int n_items = *n_items_dev;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -77,83 +77,84 @@ unsplit_update_kernel(DevParams P, const LevelDesc* __restrict__ descs, const Sw
     };
     const long long xl = (long long)(j + 1) * xr + i;  // x edge left of the cell
     const long long yb = (long long)j * yr + (i + 1);   // y edge below the cell
-    // every global read of the tile before the barrier (no exchange needs them earlier):
-    // the y-edge sums into shared memory, the x-edge sums, fluctuations and Q^n in registers
     const bool edge = row && lane <= len;  // lanes 0 .. len form the x edges of the row
-    double sgl[F], dxn[F], dyn[F], q0[F];
+    // One layer at a time (the update and the positivity fix of a layer use only its own
+    // three fields): its global reads before the barrier (the y-edge sums into shared memory,
+    // the x-edge sums, fluctuations and Q^n in registers), then its update. Three fields at a
+    // time keep the two-layer kernel within 64 registers with few spills (the loop is kept a
+    // loop there; unrolled, the compiler draws later layers' reads forward and spills more);
+    // three layers, at 128 registers, unroll it without spilling.
+#pragma unroll(M >= 3 ? M : 1)
+    for (int m = 0; m < M; ++m) {
+      double sgl[3], dxn[3], dyn[3], q0[3];
 #pragma unroll
-    for (int f = 0; f < F; ++f) { sgl[f] = 0.0; dxn[f] = 0.0; dyn[f] = 0.0; q0[f] = 0.0; }
-    if (cell) {
+      for (int k = 0; k < 3; ++k) { sgl[k] = 0.0; dxn[k] = 0.0; dyn[k] = 0.0; q0[k] = 0.0; }
+      if (cell) {
 #pragma unroll
-      for (int f = 0; f < F; ++f) gys[f][l][lane] = ysum(f, xl - xr);
-      if (l == nl - 1) {
+        for (int k = 0; k < 3; ++k) gys[k][l][lane] = ysum(3 * m + k, xl - xr);
+        if (l == nl - 1) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) gys[f][nl][lane] = ysum(f, xl);
+          for (int k = 0; k < 3; ++k) gys[k][nl][lane] = ysum(3 * m + k, xl);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int f = 3 * m + k;
+          dxn[k] = XG(1, f, xl) + XG(0, f, xl + 1);
+          dyn[k] = YG(1, f, yb) + YG(0, f, yb + yr);
+          q0[k] = qin[f * plane + (size_t)j * Pt + i];
+        }
       }
+      if (edge) {
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        dxn[f] = XG(1, f, xl) + XG(0, f, xl + 1);
-        dyn[f] = YG(1, f, yb) + YG(0, f, yb + yr);
-        q0[f] = qin[f * plane + (size_t)j * Pt + i];
+        for (int k = 0; k < 3; ++k) sgl[k] = xsum(3 * m + k, yb - 1);
       }
-    }
-    if (edge) {
+      __syncthreads();
+      if (row) {  // whole warps
+        double qn[3], gxl = 0.0, gxr = 0.0, gyb = 0.0, gyt = 0.0;
 #pragma unroll
-      for (int f = 0; f < F; ++f) sgl[f] = xsum(f, yb - 1);
-    }
-    __syncthreads();
-    if (row) {  // whole warps
-      double qn[F], gxl[M], gxr[M], gyb[M], gyt[M];
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-        const double sgr = __shfl_down_sync(0xffffffffu, sgl[f], 1);
-        qn[f] = 0.0;
-        if (cell) {
-          const double sgb = gys[f][l][lane], sgt = gys[f][l + 1][lane];
-          qn[f] = q0[f] - nux * dxn[f] - nuy * dyn[f] + hxy * ((sgr - sgl[f]) + (sgt - sgb));
-          if (f % 3 == 0) {
-            gxl[f / 3] = sgl[f]; gxr[f / 3] = sgr; gyb[f / 3] = sgb; gyt[f / 3] = sgt;
+        for (int k = 0; k < 3; ++k) {
+          const double sgr = __shfl_down_sync(0xffffffffu, sgl[k], 1);
+          qn[k] = 0.0;
+          if (cell) {
+            const double sgb = gys[k][l][lane], sgt = gys[k][l + 1][lane];
+            qn[k] = q0[k] - nux * dxn[k] - nuy * dyn[k] + hxy * ((sgr - sgl[k]) + (sgt - sgb));
+            if (k == 0) { gxl = sgl[0]; gxr = sgr; gyb = sgb; gyt = sgt; }
           }
         }
-      }
-      if (cell) {
-        const long long tol_bits = __double_as_longlong(P.dry_tol);
+        if (cell) {
+          const long long tol_bits = __double_as_longlong(P.dry_tol);
+          if (__double_as_longlong(qn[0]) < 0) qn[0] = 0.0;
+          if (__double_as_longlong(qn[0]) <= tol_bits) { qn[1] = 0.0; qn[2] = 0.0; }
+          const size_t o = (size_t)j * Pt + i;
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-          if (__double_as_longlong(qn[3 * m]) < 0) qn[3 * m] = 0.0;
-          if (__double_as_longlong(qn[3 * m]) <= tol_bits) { qn[3 * m + 1] = 0.0; qn[3 * m + 2] = 0.0; }
-        }
-        const size_t o = (size_t)j * Pt + i;
-#pragma unroll
-        for (int f = 0; f < F; ++f) qout[f * plane + o] = qn[f];
-        if (record && (D.covered != nullptr || D.in_patch != nullptr)) {
-          // Transverse part of the mass flux through this cell's left / bottom edge, and
-          // through its right / top edge when the neighbour there is in no patch of the level
-          // (otherwise that neighbour owns the edge).
-          const double hy = -0.5 * nuy, hx = -0.5 * nux;
-          auto add = [&](bool xdir, int a, int line, const double* sv, double h) {
-            const size_t cA = xdir ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
-            const size_t cB = xdir ? cA + 1 : cA + NX;
-            const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
-            const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
-            if (!iface && !bnd) return;
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-              const double gm = h * sv[m];
+          for (int k = 0; k < 3; ++k) qout[(3 * m + k) * plane + o] = qn[k];
+          if (record && (D.covered != nullptr || D.in_patch != nullptr)) {
+            // Transverse part of layer m's mass flux through this cell's left / bottom edge,
+            // and through its right / top edge when the neighbour there is in no patch of the
+            // level (otherwise that neighbour owns the edge).
+            const double hy = -0.5 * nuy, hx = -0.5 * nux;
+            auto add = [&](bool xdir, int a, int line, double sv, double h) {
+              const size_t cA = xdir ? (size_t)line * NX + (a - 1) : (size_t)(a - 1) * NX + line;
+              const size_t cB = xdir ? cA + 1 : cA + NX;
+              const bool iface = D.covered != nullptr && D.covered[cA] != D.covered[cB];
+              const bool bnd = D.in_patch != nullptr && D.in_patch[cA] != D.in_patch[cB];
+              if (!iface && !bnd) return;
+              const double gm = h * sv;
               const size_t fo = xdir ? ((size_t)m * NY + line) * (NX + 1) + a : ((size_t)m * (NY + 1) + a) * NX + line;
               if (iface) (xdir ? D.fxc : D.fyc)[fo] += gm;
               if (bnd) (xdir ? D.fxf : D.fyf)[fo] += dt * gm;
-            }
-          };
-          if (i >= 1) add(true, i, j, gxl, hy);
-          if (i + 1 <= NX - 1 && D.in_patch != nullptr && D.in_patch[(size_t)j * NX + i + 1] == 0) add(true, i + 1, j, gxr, hy);
-          if (j >= 1) add(false, j, i, gyb, hx);
-          if (j + 1 <= NY - 1 && D.in_patch != nullptr && D.in_patch[(size_t)(j + 1) * NX + i] == 0)
-            add(false, j + 1, i, gyt, hx);
+            };
+            if (i >= 1) add(true, i, j, gxl, hy);
+            if (i + 1 <= NX - 1 && D.in_patch != nullptr && D.in_patch[(size_t)j * NX + i + 1] == 0)
+              add(true, i + 1, j, gxr, hy);
+            if (j >= 1) add(false, j, i, gyb, hx);
+            if (j + 1 <= NY - 1 && D.in_patch != nullptr && D.in_patch[(size_t)(j + 1) * NX + i] == 0)
+              add(false, j + 1, i, gyt, hx);
+          }
         }
       }
+      __syncthreads();  // the y-edge sums are rewritten for the next layer or tile
     }
-    __syncthreads();  // the y-edge sums are rewritten for the next tile
   }
 }
 
