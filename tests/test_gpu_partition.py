@@ -7,6 +7,7 @@ every level's patch cells, the layouts the regrids chose, the times.
 
 * three levels (ratios 2, 2) with regrids, two and three ranks;
 * two members with ratios 4, 4 and the dynamic time ratio, two ranks;
+* three layers, ratio 4, three ranks;
 * four ranks for two patches (ranks with nothing to sweep or send);
 * a coarse step forced above cfl_max, rejected and retaken alike on every rank;
 * the library's owners equal the restated rule (sharding.partition_patches);
@@ -202,6 +203,33 @@ def test_two_members_dynamic_ratio_partitioned_equal_undivided(mlswe_lib):
     for snap in snaps:
         _assert_equal(snap, want)
     assert all(np.array_equal(a, b) for a, b in zip(owners[0], owners[1]))
+
+
+def test_three_layers_partitioned_equal_undivided(mlswe_lib):
+    """Three layers (the general M-layer branch and the pack layout of 9 fields), two levels
+    with ratio 4 and regrids, three ranks."""
+    pkg = mlswe_lib
+    n = 32
+    rho = (1000.0, 1020.0, 1030.0)
+    cfg = pkg.Config(M=3, rho=rho, dry_tol=1e-6, max_levels=2, ratio=[4], flag_tol=1e-3, regrid_interval=2,
+                     min_side=8, max_side=32)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    eta = 0.02 * np.exp(-((X - 0.45) ** 2 + (Y - 0.5) ** 2) / 0.006)
+    q = np.zeros((9, n, n))
+    q[6] = 0.4       # bottom layer: -1 .. -0.6
+    q[3] = 0.3       # middle layer: -0.6 .. -0.3
+    q[0] = 0.3 + eta  # top layer: -0.3 .. eta
+    members = [(n, q, -np.ones((4 * n, 4 * n)))]
+    H = _make(pkg, cfg, members)
+    H.advance(5)
+    want = _snapshot(H, 1, 2)
+    H.close()
+    assert len(want[0][0][1][0]) > 2
+    snaps, _, _, calls = _run_partitioned(pkg, cfg, members, 3, 5, 2)
+    assert min(calls) > 0
+    for snap in snaps:
+        _assert_equal(snap, want)
 
 
 def test_more_ranks_than_patches(mlswe_lib):
