@@ -6,7 +6,9 @@
  *
  * The library advances an M-layer (M = 1 to 4) shallow-water model on a
  * hierarchy of refinement levels (Sec. 2, Eqs. (1)-(2): dx^{l+1} = dx^l / r^l)
- * for one or more independent ensemble members, in FP64 on one GPU. Layer 1 is
+ * for one or more independent ensemble members, in FP64 on one GPU (several
+ * processes, one per GPU, can split a hierarchy's refined patches: see the patch
+ * partition entry points near the end). Layer 1 is
  * the top layer (Sec. 2.1). The conserved fields of a cell are, per layer m,
  * (h_m, h_m u_m, h_m v_m); arrays of a level are stored field-major
  * [3M][ny][nx] (row-major, x fastest) in the order
