@@ -443,15 +443,24 @@ mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long lon
  *    exchange hook, which must give every rank the other ranks' patch values
  *    (mlswe_partition_pack / mlswe_partition_unpack, through an all-gather) and the
  *    maximum over the ranks of the wave-speed slots (mlswe_wave_speed_slots). Then the
- *    ranks' hierarchies equal the undivided hierarchy's after every step.
+ *    ranks' hierarchies equal the undivided hierarchy's after every step;
+ *  - halo exchanges: after the substeps of the finest level other than the last of a
+ *    parent step, nothing but that level's own next substep reads its patches (the
+ *    coarsening and the reflux come after the last one, and no finer level exists),
+ *    and a substep of a patch reads other patches only within two cells of it. The
+ *    hook is then called with halo_only = 1 and moves, of every patch, only the cells
+ *    within two cells (corners included) of another rank's patch of the same member;
+ *    the other ranks' patches are stale on a rank between those substeps and current
+ *    again after the full exchange of the last one.
  * The orders and the split are the same on every rank (host integer arithmetic on the
  * same layouts), so no owner table is sent. */
 
 /* Exchange hook: called by mlswe_advance on the calling thread after the kernels of
  * one step of `level` (>= 1) are enqueued on the hierarchy's stream; work it enqueues
- * on that stream runs before the rest of the coarse step. Returns 0, or non-zero to
- * stop mlswe_advance with MLSWE_EINVAL. */
-typedef int (*mlswe_exchange_hook)(void* ctx, int level);
+ * on that stream runs before the rest of the coarse step. halo_only: 1 for a halo
+ * exchange, 0 for a full one (pass it on to the sizes, pack and unpack calls). Returns 0,
+ * or non-zero to stop mlswe_advance with MLSWE_EINVAL. */
+typedef int (*mlswe_exchange_hook)(void* ctx, int level, int halo_only);
 
 /* Partition the refined levels' patches over world_size ranks (rank: this process's).
  * world_size 1 undoes it. The split step only (unsplit: MLSWE_EINVAL) and the batched
@@ -464,22 +473,24 @@ mlswe_status mlswe_set_partition(mlswe_h h, int rank, int world_size, mlswe_exch
 /* Owner rank of every patch of (member, level): owner_out host [n patches]. */
 mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner_out);
 
-/* Doubles in each rank's packed buffer of `level` (host [world_size]). A packed buffer holds,
- * for every patch the rank owns in the order of the split above, the 3M state fields of the
- * patch cells (current buffer; field, then row, then column), the boundary mass-flux
- * accumulators of its rows' left and right edges and of its columns' bottom and top edges
- * ([M][rows][2], [M][columns][2]), and, on levels with a finer level, the interface mass
- * fluxes of every x edge and y edge of the patch box including its sides
- * ([M][rows][columns + 1], [M][rows + 1][columns]). */
-mlswe_status mlswe_partition_sizes(mlswe_h h, int level, long long* doubles_per_rank);
+/* Doubles in each rank's packed buffer of `level` (host [world_size]). A full buffer
+ * (halo_only = 0) holds, for every patch the rank owns in the order of the split above, the
+ * 3M state fields of the patch cells (current buffer; field, then row, then column), the
+ * boundary mass-flux accumulators of its rows' left and right edges and of its columns'
+ * bottom and top edges ([M][rows][2], [M][columns][2]), and, on levels with a finer level,
+ * the interface mass fluxes of every x edge and y edge of the patch box including its sides
+ * ([M][rows][columns + 1], [M][rows + 1][columns]). A halo buffer (halo_only = 1) holds,
+ * for every pair of a patch P the rank owns and a patch Q of another rank (same member),
+ * the 3M state fields of the box where Q grown by two cells meets P. */
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int halo_only, long long* doubles_per_rank);
 
 /* This rank's packed buffer of `level` into dst (device, mlswe_partition_sizes doubles),
  * enqueued on the hierarchy's stream. */
-mlswe_status mlswe_partition_pack(mlswe_h h, int level, double* dst);
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, int halo_only, double* dst);
 
-/* Writes the patches rank `from` owns on `level` from its packed buffer src (device),
+/* Writes the cells rank `from` packed for `level` from its packed buffer src (device),
  * enqueued on the hierarchy's stream. */
-mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int from, const double* src);
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int halo_only, int from, const double* src);
 
 /* Device address and length of the wave-speed slots (n doubles: the largest wave speed of
  * every member, level and sweep direction in the current coarse step, non-negative). An

@@ -105,7 +105,7 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 _H = ctypes.c_void_p
 
 # int (*)(void* ctx, int level): the exchange hook of a partitioned hierarchy
-_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int)
+_HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
 
 # name -> argtypes (restype is mlswe_status unless stated)
 _SIGS = {
@@ -150,9 +150,9 @@ _SIGS = {
     "mlswe_autotune": [_H, ctypes.c_int, ctypes.c_int, _ip],
     "mlswe_set_partition": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "mlswe_partition_owners": [_H, ctypes.c_int, ctypes.c_int, _ip],
-    "mlswe_partition_sizes": [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
-    "mlswe_partition_pack": [_H, ctypes.c_int, ctypes.c_void_p],
-    "mlswe_partition_unpack": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "mlswe_partition_sizes": [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
+    "mlswe_partition_pack": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
+    "mlswe_partition_unpack": [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p],
     "mlswe_wave_speed_slots": [_H, ctypes.POINTER(ctypes.c_void_p), _ip],
     "mlswe_timing": [_H, ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_longlong),
                      ctypes.POINTER(ctypes.c_longlong)],
@@ -395,13 +395,14 @@ class Hierarchy:
 
     # ---- patch partition across ranks (mlswe_set_partition and the exchange calls) ----
     def set_partition(self, rank: int, world_size: int, hook=None):
-        """Sweep only this rank's patches of the refined levels; hook(level), if given, is
-        called by advance after every refined level step and must exchange (see sharding)."""
+        """Sweep only this rank's patches of the refined levels; hook(level, halo_only), if
+        given, is called by advance after every refined level step and must exchange (see
+        sharding)."""
         cb = None
         if hook is not None:
-            def _cb(ctx, level):
+            def _cb(ctx, level, halo_only):
                 try:
-                    hook(level)
+                    hook(level, halo_only)
                     return 0
                 except BaseException as e:  # reported by advance
                     self._hook_error = e
@@ -420,18 +421,19 @@ class Hierarchy:
                     "partition_owners")
         return out
 
-    def partition_sizes(self, level: int):
-        """Doubles in every rank's packed buffer of `level`."""
+    def partition_sizes(self, level: int, halo_only: int = 0):
+        """Doubles in every rank's packed buffer of `level` (full, or halo cells only)."""
         n = getattr(self, "part_size", 1)
         out = (ctypes.c_longlong * n)()
-        self._check(self.L.mlswe_partition_sizes(self.h, level, out), "partition_sizes")
+        self._check(self.L.mlswe_partition_sizes(self.h, level, int(halo_only), out), "partition_sizes")
         return [int(v) for v in out]
 
-    def partition_pack(self, level: int, dst_ptr: int):
-        self._check(self.L.mlswe_partition_pack(self.h, level, ctypes.c_void_p(dst_ptr)), "partition_pack")
+    def partition_pack(self, level: int, dst_ptr: int, halo_only: int = 0):
+        self._check(self.L.mlswe_partition_pack(self.h, level, int(halo_only), ctypes.c_void_p(dst_ptr)),
+                    "partition_pack")
 
-    def partition_unpack(self, level: int, rank: int, src_ptr: int):
-        self._check(self.L.mlswe_partition_unpack(self.h, level, rank, ctypes.c_void_p(src_ptr)),
+    def partition_unpack(self, level: int, rank: int, src_ptr: int, halo_only: int = 0):
+        self._check(self.L.mlswe_partition_unpack(self.h, level, int(halo_only), rank, ctypes.c_void_p(src_ptr)),
                     "partition_unpack")
 
     def wave_speed_slots(self):

@@ -286,7 +286,11 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
   }
   mlswe_status s = enqueue_level_step(H, level, 1);
   if (s != MLSWE_OK) return s;
-  s = run_exchange_hook(H, level);  // partitioned: the other ranks' patches of this level
+  // Partitioned: the other ranks' patches of this level; between the substeps of the finest
+  // level only their cells within two of this rank's patches (the next substep reads no
+  // more), everything after the last substep of the parent step.
+  const bool halo = level == H->L - 1 && level > 0 && substep < H->cfg.ratio[level - 1] - 1;
+  s = run_exchange_hook(H, level, halo ? 1 : 0);
   if (s != MLSWE_OK) return s;
   if (level + 1 < H->L) {
     const int rt = H->cfg.ratio[level];  // the most substeps any member takes

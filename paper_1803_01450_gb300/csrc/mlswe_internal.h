@@ -59,6 +59,7 @@ struct Member {
 struct PackItem {
   int desc;
   int i0, j0, i1, j1;
+  int state_only;  // 1: the state fields of the box only (halo exchange)
   long long off;
 };
 
@@ -193,10 +194,14 @@ struct Hier {
   void* part_ctx = nullptr;
   bool part_dirty = true;
   std::vector<std::vector<std::vector<int>>> owner;  // [member][level][patch] rank
-  struct PartLevel {
-    DevTable<PackItem> items;      // every patch of the level, grouped by owner
+  struct PartTable {
+    DevTable<PackItem> items;      // grouped by owner
     std::vector<int> first;        // [part_size + 1] item range of each owner
     std::vector<long long> size;   // [part_size] doubles in each owner's packed buffer
+  };
+  struct PartLevel {
+    PartTable full;                // every patch of the level
+    PartTable halo;                // the boxes of own patches within two cells of another rank's
   };
   std::vector<PartLevel> part;     // [L]
 
@@ -290,7 +295,7 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record);
 // hierarchy is not partitioned); the exchange hook after a level step.
 mlswe_status ensure_partition(Hier* H);
 bool patch_owned(const Hier* H, int member, int level, int p);
-mlswe_status run_exchange_hook(Hier* H, int level);
+mlswe_status run_exchange_hook(Hier* H, int level, int halo_only);
 
 // Packed sweep tiles (mlswe_pack.cu). patch_segments appends the runs of lines of patch b
 // for a sweep along dir (0: x, lines are rows; 1: y, lines are columns): lines [g0, g1)

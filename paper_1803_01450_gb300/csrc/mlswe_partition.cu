@@ -62,6 +62,44 @@ static mlswe_status upload_items(Hier* H, DevTable<PackItem>& T, const std::vect
   return MLSWE_OK;
 }
 
+// For every patch, the indices of the other patches whose box grown by g cells meets it
+// (in increasing order), found through buckets of 64 x 64 cells.
+static std::vector<std::vector<int>> patches_near(const std::vector<Box>& P, int g) {
+  constexpr int kBucket = 64;
+  std::vector<std::vector<int>> out(P.size());
+  if (P.empty()) return out;
+  int ni = 1, nj = 1;
+  for (const Box& b : P) {
+    ni = std::max(ni, (b.i1 + g + kBucket - 1) / kBucket);
+    nj = std::max(nj, (b.j1 + g + kBucket - 1) / kBucket);
+  }
+  std::vector<std::vector<int>> bucket((size_t)ni * nj);
+  for (int k = 0; k < (int)P.size(); ++k) {
+    const Box& b = P[k];
+    for (int bj = std::max(0, b.j0 - g) / kBucket; bj <= (b.j1 + g - 1) / kBucket; ++bj)
+      for (int bi = std::max(0, b.i0 - g) / kBucket; bi <= (b.i1 + g - 1) / kBucket; ++bi)
+        bucket[(size_t)bj * ni + bi].push_back(k);
+  }
+  std::vector<char> seen(P.size(), 0);
+  for (int p = 0; p < (int)P.size(); ++p) {
+    const Box& a = P[p];
+    std::vector<int>& v = out[p];
+    for (int bj = a.j0 / kBucket; bj <= std::min(nj - 1, (a.j1 - 1) / kBucket); ++bj)
+      for (int bi = a.i0 / kBucket; bi <= std::min(ni - 1, (a.i1 - 1) / kBucket); ++bi)
+        for (int q : bucket[(size_t)bj * ni + bi]) {
+          if (q == p || seen[q]) continue;
+          const Box& b = P[q];
+          if (b.i0 - g < a.i1 && a.i0 < b.i1 + g && b.j0 - g < a.j1 && a.j0 < b.j1 + g) {
+            seen[q] = 1;
+            v.push_back(q);
+          }
+        }
+    for (int q : v) seen[q] = 0;
+    std::sort(v.begin(), v.end());
+  }
+  return out;
+}
+
 mlswe_status ensure_partition(Hier* H) {
   if (!H->part_dirty) return MLSWE_OK;
   CUDA_TRY(H, cudaStreamSynchronize(H->st));  // no pack or unpack still reads the old table
@@ -89,27 +127,55 @@ mlswe_status ensure_partition(Hier* H) {
     });
     // owner: the rank whose share of the cells holds the patch's middle cell
     long long before = 0;
-    std::vector<std::vector<PackItem>> per(n);
+    std::vector<std::vector<PackItem>> per(n), per_h(n);
     Hier::PartLevel& PL = H->part[l];
-    PL.size.assign(n, 0);
+    PL.full.size.assign(n, 0);
+    PL.halo.size.assign(n, 0);
     for (const Entry& x : e) {
       int r = 0;
       if (l > 0 && total > 0) r = (int)std::min<long long>(n - 1, (2 * before + x.cells) * n / (2 * total));
       before += x.cells;
       H->owner[x.m][l][x.p] = r;
+    }
+    for (const Entry& x : e) {
+      const int r = H->owner[x.m][l][x.p];
       const Box& b = H->mem[x.m].lev[l].patches[x.p];
-      per[r].push_back(PackItem{H->desc_index(x.m, l), b.i0, b.j0, b.i1, b.j1, PL.size[r]});
-      PL.size[r] += pack_doubles(H->cfg.M, b, l + 1 < H->L);
+      per[r].push_back(PackItem{H->desc_index(x.m, l), b.i0, b.j0, b.i1, b.j1, 0, PL.full.size[r]});
+      PL.full.size[r] += pack_doubles(H->cfg.M, b, l + 1 < H->L);
     }
-    std::vector<PackItem> all;
-    PL.first.assign(n + 1, 0);
-    for (int r = 0; r < n; ++r) {
-      PL.first[r] = (int)all.size();
-      all.insert(all.end(), per[r].begin(), per[r].end());
+    // halo boxes: where another rank's patch of the member, grown by two cells, meets an
+    // own patch (in the order of the own patches, then of the others)
+    if (l > 0 && n > 1) {
+      for (int m = 0; m < H->n_members; ++m) {
+        const std::vector<Box>& P = H->mem[m].lev[l].patches;
+        const std::vector<std::vector<int>> near = patches_near(P, kNG);
+        for (int p = 0; p < (int)P.size(); ++p) {
+          const int r = H->owner[m][l][p];
+          for (int q : near[p]) {
+            if (H->owner[m][l][q] == r) continue;
+            const Box& Q = P[q];
+            const Box c{std::max(P[p].i0, Q.i0 - kNG), std::max(P[p].j0, Q.j0 - kNG), std::min(P[p].i1, Q.i1 + kNG),
+                        std::min(P[p].j1, Q.j1 + kNG)};
+            if (c.i0 >= c.i1 || c.j0 >= c.j1) continue;
+            per_h[r].push_back(PackItem{H->desc_index(m, l), c.i0, c.j0, c.i1, c.j1, 1, PL.halo.size[r]});
+            PL.halo.size[r] += 3LL * H->cfg.M * c.w() * c.h();
+          }
+        }
+      }
     }
-    PL.first[n] = (int)all.size();
-    mlswe_status s = upload_items(H, PL.items, all);
-    if (s != MLSWE_OK) return s;
+    for (int half = 0; half < 2; ++half) {
+      Hier::PartTable& T = half ? PL.halo : PL.full;
+      std::vector<std::vector<PackItem>>& src = half ? per_h : per;
+      std::vector<PackItem> all;
+      T.first.assign(n + 1, 0);
+      for (int r = 0; r < n; ++r) {
+        T.first[r] = (int)all.size();
+        all.insert(all.end(), src[r].begin(), src[r].end());
+      }
+      T.first[n] = (int)all.size();
+      mlswe_status s = upload_items(H, T.items, all);
+      if (s != MLSWE_OK) return s;
+    }
   }
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
   H->part_dirty = false;
@@ -163,6 +229,7 @@ part_copy_kernel(const LevelDesc* __restrict__ descs, const PackItem* __restrict
         }
       }
     }
+    if (it.state_only) continue;  // a halo box: its state only
     b += 3LL * M * ncell;
     // boundary accumulators: x edges at i0 and i1 of every row, y edges at j0 and j1 of
     // every column
@@ -204,9 +271,9 @@ static cudaError_t launch_part_copy(int M, const LevelDesc* descs, const PackIte
   return cudaGetLastError();
 }
 
-mlswe_status run_exchange_hook(Hier* H, int level) {
+mlswe_status run_exchange_hook(Hier* H, int level, int halo_only) {
   if (!partitioned(H) || level == 0 || !H->part_hook) return MLSWE_OK;
-  if (H->part_hook(H->part_ctx, level) != 0) return fail(H, MLSWE_EINVAL, "partition exchange hook failed");
+  if (H->part_hook(H->part_ctx, level, halo_only) != 0) return fail(H, MLSWE_EINVAL, "partition exchange hook failed");
   return MLSWE_OK;
 }
 
@@ -255,36 +322,39 @@ mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_sizes(mlswe_h h, int level, long long* doubles_per_rank) {
-  if (!h || !doubles_per_rank) return fail(h, MLSWE_EINVAL, "partition_sizes: bad argument");
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int halo_only, long long* doubles_per_rank) {
+  if (!h || !doubles_per_rank || (halo_only != 0 && halo_only != 1))
+    return fail(h, MLSWE_EINVAL, "partition_sizes: bad argument");
   mlswe_status s = part_level_ready(h, level);
   if (s != MLSWE_OK) return s;
-  for (int r = 0; r < h->part_size; ++r) doubles_per_rank[r] = h->part[level].size[r];
+  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
+  for (int r = 0; r < h->part_size; ++r) doubles_per_rank[r] = T.size[r];
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_pack(mlswe_h h, int level, double* dst) {
-  if (!h || !dst) return fail(h, MLSWE_EINVAL, "partition_pack: bad argument");
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, int halo_only, double* dst) {
+  if (!h || !dst || (halo_only != 0 && halo_only != 1)) return fail(h, MLSWE_EINVAL, "partition_pack: bad argument");
   mlswe_status s = part_level_ready(h, level);
   if (s != MLSWE_OK) return s;
   if (!device_pointer(dst)) return fail(h, MLSWE_EINVAL, "partition_pack: dst is not device memory");
-  const Hier::PartLevel& PL = h->part[level];
+  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
   const int r = h->part_rank;
-  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[r], PL.first[r + 1], h->parity[level], dst, 0,
+  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, T.items.d, T.first[r], T.first[r + 1], h->parity[level], dst, 0,
                                8 * h->num_sms, h->st));
-  h->kernel_launches += PL.first[r + 1] > PL.first[r] ? 1 : 0;
+  h->kernel_launches += T.first[r + 1] > T.first[r] ? 1 : 0;
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int from, const double* src) {
-  if (!h || !src || from < 0 || from >= h->part_size) return fail(h, MLSWE_EINVAL, "partition_unpack: bad argument");
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int halo_only, int from, const double* src) {
+  if (!h || !src || from < 0 || from >= h->part_size || (halo_only != 0 && halo_only != 1))
+    return fail(h, MLSWE_EINVAL, "partition_unpack: bad argument");
   mlswe_status s = part_level_ready(h, level);
   if (s != MLSWE_OK) return s;
   if (!device_pointer(src)) return fail(h, MLSWE_EINVAL, "partition_unpack: src is not device memory");
-  const Hier::PartLevel& PL = h->part[level];
-  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, PL.items.d, PL.first[from], PL.first[from + 1], h->parity[level],
+  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
+  CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, T.items.d, T.first[from], T.first[from + 1], h->parity[level],
                                const_cast<double*>(src), 1, 8 * h->num_sms, h->st));
-  h->kernel_launches += PL.first[from + 1] > PL.first[from] ? 1 : 0;
+  h->kernel_launches += T.first[from + 1] > T.first[from] ? 1 : 0;
   return MLSWE_OK;
 }
 

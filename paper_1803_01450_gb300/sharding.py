@@ -23,7 +23,9 @@ member's step:
   after every refined level step, in which the ranks all-gather their packed patch values
   and take the maximum of the wave-speed slots (exchange_level; PatchPartition wires it to
   a Hierarchy). Level 0, ghost fill, coarsening, reflux, time steps and regrids run on
-  every rank on the full state, so every rank's hierarchy equals the undivided one.
+  every rank on the full state, so every rank's hierarchy equals the undivided one. Between
+  the finest level's substeps of one parent step only the halo cells move (the cells of a
+  rank's patches within two cells of another rank's patch), the full state after the last.
 
 Data moves only by point-to-point sends or all-gathers into local buffers and by
 all-reduces (NCCL on GPUs, gloo on CPUs); the stepping itself is a callable the caller
@@ -189,15 +191,15 @@ class PatchPartition:
         self.H, self.rank, self.ws, self.dist, self.device = H, rank, world_size, dist, device
         H.set_partition(rank, world_size, self._exchange)
 
-    def _exchange(self, level):
+    def _exchange(self, level, halo_only):
         import torch
         H = self.H
         stream = torch.cuda.ExternalStream(H.stream, device=self.device)
         with torch.cuda.stream(stream):
             ptr, n = H.wave_speed_slots()
             speeds = torch.as_tensor(_DeviceArray(ptr, n), device=self.device)
-            exchange_level(self.rank, self.ws, H.partition_sizes(level),
-                           lambda buf: H.partition_pack(level, buf.data_ptr()),
-                           lambda q, buf: H.partition_unpack(level, q, buf.data_ptr()),
+            exchange_level(self.rank, self.ws, H.partition_sizes(level, halo_only),
+                           lambda buf: H.partition_pack(level, buf.data_ptr(), halo_only),
+                           lambda q, buf: H.partition_unpack(level, q, buf.data_ptr(), halo_only),
                            speeds, self.dist,
                            lambda k: torch.empty(k, dtype=torch.float64, device=self.device))

@@ -3,7 +3,9 @@ one process: each rank is a hierarchy advanced by its own host thread on its own
 the exchange hook moves the packed patch values and the wave-speed slots between the
 hierarchies through device copies, with host barriers between the phases (no kernel waits on
 another). After the runs every rank's hierarchy must equal the undivided one bit for bit:
-every level's patch cells, the layouts the regrids chose, the times.
+every level's patch cells, the layouts the regrids chose, the times. Between the finest
+level's substeps the library asks for halo exchanges only (cells within two of another
+rank's patch); the bit-for-bit equality checks that nothing else is read there.
 
 * three levels (ratios 2, 2) with regrids, two and three ranks;
 * two members with ratios 4, 4 and the dynamic time ratio, two ranks;
@@ -31,18 +33,20 @@ class _Group:
         self.bufs = [None] * ws
         self.speeds = [None] * ws
         self.calls = [0] * ws
+        self.modes = [0, 0]  # rank 0's full and halo exchanges
 
 
 def _hook(H, r, grp, dev):
     import torch
 
-    def hook(level):
+    def hook(level, halo_only):
         stream = torch.cuda.ExternalStream(H.stream, device=dev)
-        sizes = H.partition_sizes(level)
+        sizes = H.partition_sizes(level, halo_only)
+        grp.modes[halo_only] += 1 if r == 0 else 0
         with torch.cuda.stream(stream):
             buf = torch.empty(max(max(sizes), 1), dtype=torch.float64, device=dev)
             if sizes[r] > 0:
-                H.partition_pack(level, buf.data_ptr())
+                H.partition_pack(level, buf.data_ptr(), halo_only)
             ptr, n = H.wave_speed_slots()
             sp = torch.as_tensor(S._DeviceArray(ptr, n), device=dev)
             snap = sp.clone()
@@ -53,7 +57,7 @@ def _hook(H, r, grp, dev):
         with torch.cuda.stream(stream):
             for q in range(grp.ws):
                 if q != r and sizes[q] > 0:
-                    H.partition_unpack(level, q, grp.bufs[q].data_ptr())
+                    H.partition_unpack(level, q, grp.bufs[q].data_ptr(), halo_only)
             sp.copy_(torch.stack(grp.speeds).amax(dim=0))
         stream.synchronize()
         grp.barrier.wait()
@@ -182,6 +186,7 @@ def test_three_levels_partitioned_equal_undivided(mlswe_lib, ws):
     for Hr in hs:
         Hr.close()
     assert min(grp.calls) > 0 and len(set(grp.calls)) == 1
+    assert grp.modes[0] > 0 and grp.modes[1] > 0  # full and halo exchanges both ran
     for snap in snaps:
         _assert_equal(snap, want)
 
