@@ -393,9 +393,9 @@ def bench_batched_amr(pkg, torch, stream, steps=3, n0=512, patches=(1000, 3000))
 def _partition_pack_times(torch, H, stream, ws=2, reps=5):
     """Kernel side of the patch-partition exchange on one GPU: the hierarchy split over ws
     ranks (no hook; this process plays rank 0), then per refined level the doubles every rank
-    sends in a full exchange, the bytes of a halo exchange, and the pack and unpack times of
-    rank 0's and rank 1's full buffers (CUDA events; read + write bytes of the copies over the
-    time)."""
+    sends in a full exchange, the job's bytes of the other kinds of exchange (halo, last,
+    averaged), and the pack and unpack times of rank 0's and rank 1's full buffers (CUDA
+    events; read + write bytes of the copies over the time)."""
     H.set_partition(0, ws)
     dev = torch.device("cuda", torch.cuda.current_device())
     out = {"ranks": ws}
@@ -413,9 +413,11 @@ def _partition_pack_times(torch, H, stream, ws=2, reps=5):
         e[2].record(stream)
         torch.cuda.synchronize()
         pack_ms, unpack_ms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
-        halo = H.partition_sizes(level, 1)
+        kinds = {k: 8 * sum(H.partition_sizes(level, i)) for i, k in ((1, "halo"), (2, "last"))}
+        if level == 1:
+            kinds["averaged_into_level1"] = 8 * sum(H.partition_sizes(1, 3))
         out[f"level{level}"] = {"doubles_per_rank": sizes, "job_bytes_per_level_step": 8 * sum(sizes),
-                                "halo_job_bytes": 8 * sum(halo),
+                                "job_bytes_of_other_kinds": kinds,
                                 "pack_ms": pack_ms, "pack_gbs": 16 * sizes[0] / (pack_ms * 1e-3) / 1e9,
                                 "unpack_ms": unpack_ms, "unpack_gbs": 16 * sizes[1] / (unpack_ms * 1e-3) / 1e9}
     H.set_partition(0, 1)

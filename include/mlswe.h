@@ -436,31 +436,41 @@ mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long lon
  *    patch p goes to rank min(n - 1, floor((2 c_p + cells_p) n / (2 T))) (the rank whose
  *    share of the cells holds the patch's middle cell), so each rank's cells differ from
  *    T / n by at most the largest patch;
- *  - a rank sweeps only its own patches of levels >= 1; level 0, the ghost fill, the
- *    coarsening, the reflux, the time step and the regrids run on every rank, on state
- *    that every rank holds in full after each exchange;
- *  - after every step of a level >= 1 inside mlswe_advance, the library calls the
- *    exchange hook, which must give every rank the other ranks' patch values
- *    (mlswe_partition_pack / mlswe_partition_unpack, through an all-gather) and the
- *    maximum over the ranks of the wave-speed slots (mlswe_wave_speed_slots). Then the
- *    ranks' hierarchies equal the undivided hierarchy's after every step;
- *  - halo exchanges: after the substeps of the finest level other than the last of a
- *    parent step, nothing but that level's own next substep reads its patches (the
- *    coarsening and the reflux come after the last one, and no finer level exists),
- *    and a substep of a patch reads other patches only within two cells of it. The
- *    hook is then called with halo_only = 1 and moves, of every patch, only the cells
- *    within two cells (corners included) of another rank's patch of the same member;
- *    the other ranks' patches are stale on a rank between those substeps and current
- *    again after the full exchange of the last one.
+ *  - a rank sweeps only its own patches of levels >= 1, and coarsens only its own patches
+ *    of the finest level; level 0, the ghost fill, the other coarsenings, the reflux,
+ *    the time step and the regrids run on every rank;
+ *  - inside mlswe_advance the library calls the exchange hook at fixed points with a
+ *    kind, and the hook must give every rank the other ranks' packed values of that kind
+ *    (mlswe_partition_pack / mlswe_partition_unpack, through an all-gather), and, for
+ *    kinds 0 to 2, the maximum over the ranks of the wave-speed slots
+ *    (mlswe_wave_speed_slots):
+ *      MLSWE_XCHG_FULL (0): every patch of the level: after each step of a refined
+ *        level other than the finest, before every regrid and at the end of
+ *        mlswe_advance (for the finest level);
+ *      MLSWE_XCHG_HALO (1): after the finest level's substeps other than the last of a
+ *        parent step, only the cells of each patch within two cells (corners included)
+ *        of another rank's patch of the same member: nothing but the next substep reads
+ *        the level then, and a substep of a patch reads other patches only that close;
+ *      MLSWE_XCHG_LAST (2): after the last substep, the halo cells and every patch's
+ *        boundary mass-flux accumulators (which the parent's reflux reads);
+ *      MLSWE_XCHG_AVERAGED (3): after the finest level is coarsened onto its parent
+ *        (`level` is the parent), the parent cells under every patch of the finest level
+ *        (the only parent cells that coarsening wrote);
+ *    so between the exchanges of the finest level the other ranks' patches of that level
+ *    are stale on a rank, and every reader of them (the regrid, the end of the call) is
+ *    preceded by a full exchange. Then after mlswe_advance the ranks' hierarchies equal
+ *    the undivided hierarchy's.
  * The orders and the split are the same on every rank (host integer arithmetic on the
  * same layouts), so no owner table is sent. */
 
-/* Exchange hook: called by mlswe_advance on the calling thread after the kernels of
- * one step of `level` (>= 1) are enqueued on the hierarchy's stream; work it enqueues
- * on that stream runs before the rest of the coarse step. halo_only: 1 for a halo
- * exchange, 0 for a full one (pass it on to the sizes, pack and unpack calls). Returns 0,
- * or non-zero to stop mlswe_advance with MLSWE_EINVAL. */
-typedef int (*mlswe_exchange_hook)(void* ctx, int level, int halo_only);
+enum { MLSWE_XCHG_FULL = 0, MLSWE_XCHG_HALO = 1, MLSWE_XCHG_LAST = 2, MLSWE_XCHG_AVERAGED = 3 };
+
+/* Exchange hook: called by mlswe_advance (and mlswe_regrid) on the calling thread at the
+ * points above, with the kernels before it enqueued on the hierarchy's stream; work it
+ * enqueues on that stream runs before the rest of the call. kind: an MLSWE_XCHG_ value, to
+ * pass on to the sizes, pack and unpack calls. Returns 0, or non-zero to stop the call
+ * with MLSWE_EINVAL. */
+typedef int (*mlswe_exchange_hook)(void* ctx, int level, int kind);
 
 /* Partition the refined levels' patches over world_size ranks (rank: this process's).
  * world_size 1 undoes it. The split step only (unsplit: MLSWE_EINVAL) and the batched
@@ -473,24 +483,27 @@ mlswe_status mlswe_set_partition(mlswe_h h, int rank, int world_size, mlswe_exch
 /* Owner rank of every patch of (member, level): owner_out host [n patches]. */
 mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner_out);
 
-/* Doubles in each rank's packed buffer of `level` (host [world_size]). A full buffer
- * (halo_only = 0) holds, for every patch the rank owns in the order of the split above, the
- * 3M state fields of the patch cells (current buffer; field, then row, then column), the
- * boundary mass-flux accumulators of its rows' left and right edges and of its columns'
- * bottom and top edges ([M][rows][2], [M][columns][2]), and, on levels with a finer level,
- * the interface mass fluxes of every x edge and y edge of the patch box including its sides
- * ([M][rows][columns + 1], [M][rows + 1][columns]). A halo buffer (halo_only = 1) holds,
- * for every pair of a patch P the rank owns and a patch Q of another rank (same member),
- * the 3M state fields of the box where Q grown by two cells meets P. */
-mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int halo_only, long long* doubles_per_rank);
+/* Doubles in each rank's packed buffer of `level` and `kind` (host [world_size]). Every
+ * buffer is a list of boxes in a fixed order, each with some of: the 3M state fields of its
+ * cells (current buffer; field, then row, then column), the boundary mass-flux accumulators
+ * of its rows' left and right edges and of its columns' bottom and top edges ([M][rows][2],
+ * [M][columns][2]), the interface mass fluxes of every x edge and y edge of the box
+ * including its sides ([M][rows][columns + 1], [M][rows + 1][columns]). FULL: every patch
+ * the rank owns (in the order of the split above) with its state, accumulators and, on
+ * levels with a finer level, interface fluxes. HALO: for every pair of a patch P the rank
+ * owns and a patch Q of another rank (same member), the state of the box where Q grown by
+ * two cells meets P. LAST: the HALO boxes, then every owned patch's accumulators. AVERAGED
+ * (level = the finest level's parent): for every finest-level patch the rank owns, the
+ * state of the parent cells under it. */
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int kind, long long* doubles_per_rank);
 
-/* This rank's packed buffer of `level` into dst (device, mlswe_partition_sizes doubles),
- * enqueued on the hierarchy's stream. */
-mlswe_status mlswe_partition_pack(mlswe_h h, int level, int halo_only, double* dst);
+/* This rank's packed buffer of `level` and `kind` into dst (device, mlswe_partition_sizes
+ * doubles), enqueued on the hierarchy's stream. */
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, int kind, double* dst);
 
-/* Writes the cells rank `from` packed for `level` from its packed buffer src (device),
- * enqueued on the hierarchy's stream. */
-mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int halo_only, int from, const double* src);
+/* Writes the values rank `from` packed for `level` and `kind` from its packed buffer src
+ * (device), enqueued on the hierarchy's stream. */
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int kind, int from, const double* src);
 
 /* Device address and length of the wave-speed slots (n doubles: the largest wave speed of
  * every member, level and sweep direction in the current coarse step, non-negative). An

@@ -104,8 +104,10 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 _H = ctypes.c_void_p
 
-# int (*)(void* ctx, int level): the exchange hook of a partitioned hierarchy
+# int (*)(void* ctx, int level, int kind): the exchange hook of a partitioned hierarchy
 _HOOK = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
+# exchange kinds (MLSWE_XCHG_*)
+XCHG_FULL, XCHG_HALO, XCHG_LAST, XCHG_AVERAGED = 0, 1, 2, 3
 
 # name -> argtypes (restype is mlswe_status unless stated)
 _SIGS = {
@@ -395,14 +397,14 @@ class Hierarchy:
 
     # ---- patch partition across ranks (mlswe_set_partition and the exchange calls) ----
     def set_partition(self, rank: int, world_size: int, hook=None):
-        """Sweep only this rank's patches of the refined levels; hook(level, halo_only), if
-        given, is called by advance after every refined level step and must exchange (see
-        sharding)."""
+        """Sweep only this rank's patches of the refined levels; hook(level, kind), if given,
+        is called by advance at the exchange points (kind: XCHG_FULL, XCHG_HALO, XCHG_LAST,
+        XCHG_AVERAGED) and must exchange (see sharding)."""
         cb = None
         if hook is not None:
-            def _cb(ctx, level, halo_only):
+            def _cb(ctx, level, kind):
                 try:
-                    hook(level, halo_only)
+                    hook(level, kind)
                     return 0
                 except BaseException as e:  # reported by advance
                     self._hook_error = e
@@ -421,19 +423,19 @@ class Hierarchy:
                     "partition_owners")
         return out
 
-    def partition_sizes(self, level: int, halo_only: int = 0):
-        """Doubles in every rank's packed buffer of `level` (full, or halo cells only)."""
+    def partition_sizes(self, level: int, kind: int = 0):
+        """Doubles in every rank's packed buffer of `level` and exchange `kind`."""
         n = getattr(self, "part_size", 1)
         out = (ctypes.c_longlong * n)()
-        self._check(self.L.mlswe_partition_sizes(self.h, level, int(halo_only), out), "partition_sizes")
+        self._check(self.L.mlswe_partition_sizes(self.h, level, int(kind), out), "partition_sizes")
         return [int(v) for v in out]
 
-    def partition_pack(self, level: int, dst_ptr: int, halo_only: int = 0):
-        self._check(self.L.mlswe_partition_pack(self.h, level, int(halo_only), ctypes.c_void_p(dst_ptr)),
+    def partition_pack(self, level: int, dst_ptr: int, kind: int = 0):
+        self._check(self.L.mlswe_partition_pack(self.h, level, int(kind), ctypes.c_void_p(dst_ptr)),
                     "partition_pack")
 
-    def partition_unpack(self, level: int, rank: int, src_ptr: int, halo_only: int = 0):
-        self._check(self.L.mlswe_partition_unpack(self.h, level, int(halo_only), rank, ctypes.c_void_p(src_ptr)),
+    def partition_unpack(self, level: int, rank: int, src_ptr: int, kind: int = 0):
+        self._check(self.L.mlswe_partition_unpack(self.h, level, int(kind), rank, ctypes.c_void_p(src_ptr)),
                     "partition_unpack")
 
     def wave_speed_slots(self):

@@ -81,6 +81,10 @@ static mlswe_status upload_table(Hier* H, DevTable<T_>& T, const std::vector<T_>
 // synchronous). Graphs stay valid unless a table had to grow.
 static mlswe_status build_tables(Hier* H) {
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
+  if (H->part_size > 1) {  // the finest level's coarsening takes this rank's patches only
+    mlswe_status s = ensure_partition(H);
+    if (s != MLSWE_OK) return s;
+  }
   std::vector<int> has(H->n_members * H->L, 0);
   std::vector<long long> cells(H->n_members * H->L, 0);
   std::vector<InterpItem> speed;
@@ -96,7 +100,8 @@ static mlswe_status build_tables(Hier* H) {
       if (l > 0) {
         const int dc = H->desc_index(m, l - 1);
         const int r = H->cfg.ratio[l - 1];
-        for (const Box& b : V.patches) {
+        for (int p = 0; p < (int)V.patches.size(); ++p) {
+          const Box& b = V.patches[p];
           // ghost ring as four strips, clipped to the domain
           const int gi0 = std::max(0, b.i0 - kNG), gi1 = std::min(V.NX, b.i1 + kNG);
           const Box strips[4] = {Box{gi0, std::max(0, b.j0 - kNG), gi1, b.j0},
@@ -109,7 +114,7 @@ static mlswe_status build_tables(Hier* H) {
                 for (int ic = s.i0 / r; ic <= (s.i1 - 1) / r; ++ic)
                   gcell.push_back(GhostCell{dc, d, ic, jc, s.i0, s.j0, s.i1, s.j1});
             }
-          push_chunks(avg, dc, d, Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
+          if (coarsens_patch(H, m, l, p)) push_chunks(avg, dc, d, Box{b.i0 / r, b.j0 / r, b.i1 / r, b.j1 / r});
         }
       }
       if (l + 1 < H->L && !H->mem[m].lev[l + 1].patches.empty()) {
@@ -286,11 +291,13 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
   }
   mlswe_status s = enqueue_level_step(H, level, 1);
   if (s != MLSWE_OK) return s;
-  // Partitioned: the other ranks' patches of this level; between the substeps of the finest
-  // level only their cells within two of this rank's patches (the next substep reads no
-  // more), everything after the last substep of the parent step.
-  const bool halo = level == H->L - 1 && level > 0 && substep < H->cfg.ratio[level - 1] - 1;
-  s = run_exchange_hook(H, level, halo ? 1 : 0);
+  // Partitioned: the other ranks' patches of this level, all of them for a level with a finer
+  // one; for the finest level only their cells within two of this rank's patches (the next
+  // substep reads no more), after the last substep with the accumulators the reflux reads.
+  int kind = MLSWE_XCHG_FULL;
+  if (level == H->L - 1 && level > 0)
+    kind = substep < H->cfg.ratio[level - 1] - 1 ? MLSWE_XCHG_HALO : MLSWE_XCHG_LAST;
+  s = run_exchange_hook(H, level, kind);
   if (s != MLSWE_OK) return s;
   if (level + 1 < H->L) {
     const int rt = H->cfg.ratio[level];  // the most substeps any member takes
@@ -302,6 +309,10 @@ static mlswe_status enqueue_level_tree(Hier* H, int level, int substep) {
     CUDA_TRY(H, launch_average_items(3 * H->cfg.M, H->d_desc, H->t_avg[level + 1].d, H->t_avg[level + 1].d_count,
                                      grid_full(H), rt, H->parity[level], H->parity[level + 1], H->st));
     timer_end(H, tok);
+    if (level + 1 == H->L - 1) {  // partitioned: each rank coarsened its own finest patches
+      s = run_exchange_hook(H, level, MLSWE_XCHG_AVERAGED);
+      if (s != MLSWE_OK) return s;
+    }
     timer_begin(H, KC_REFLUX, &tok);
     CUDA_TRY(H, launch_reflux(H->cfg.M, H->d_desc, H->t_reflux[level].d, H->t_reflux[level].d_count, grid_flat(H), rt,
                               H->parity[level], H->st));
@@ -428,6 +439,10 @@ static mlswe_status coarse_step(Hier* H) {
 
 static mlswe_status regrid_internal(Hier* H, int base) {
   NvtxRange range("mlswe_regrid");
+  if (H->L > 1) {  // partitioned: the flags and the kept patch cells need the whole finest level
+    mlswe_status s = run_exchange_hook(H, H->L - 1, MLSWE_XCHG_FULL);
+    if (s != MLSWE_OK) return s;
+  }
   H->regrids++;
   for (int m = 0; m < H->n_members; ++m) {
     for (int l = base; l + 1 < H->L; ++l) {
@@ -671,6 +686,10 @@ mlswe_status mlswe_advance(mlswe_h h, int n_coarse_steps) {
   }
   if (masked) {
     s = set_member_active(h, std::vector<int>(h->n_members, 1));
+    if (s != MLSWE_OK) return s;
+  }
+  if (h->L > 1) {  // partitioned: every rank's finest level whole again for the caller
+    s = run_exchange_hook(h, h->L - 1, MLSWE_XCHG_FULL);
     if (s != MLSWE_OK) return s;
   }
   unsigned int status = 0;

@@ -59,9 +59,10 @@ struct Member {
 struct PackItem {
   int desc;
   int i0, j0, i1, j1;
-  int state_only;  // 1: the state fields of the box only (halo exchange)
+  int parts;  // bit 0: state fields, 1: boundary mass-flux accumulators, 2: interface fluxes
   long long off;
 };
+constexpr int kPackState = 1, kPackAccum = 2, kPackIface = 4;
 
 // Tile shape of one sweep direction: `len` cells along the sweep, `lines` lines per tile.
 struct TileShape {
@@ -200,8 +201,8 @@ struct Hier {
     std::vector<long long> size;   // [part_size] doubles in each owner's packed buffer
   };
   struct PartLevel {
-    PartTable full;                // every patch of the level
-    PartTable halo;                // the boxes of own patches within two cells of another rank's
+    PartTable kind[4];             // exchange tables by MLSWE_XCHG_ kind (full, halo, last,
+                                   // averaged: parent cells under the finest level's patches)
   };
   std::vector<PartLevel> part;     // [L]
 
@@ -295,7 +296,10 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record);
 // hierarchy is not partitioned); the exchange hook after a level step.
 mlswe_status ensure_partition(Hier* H);
 bool patch_owned(const Hier* H, int member, int level, int p);
-mlswe_status run_exchange_hook(Hier* H, int level, int halo_only);
+mlswe_status run_exchange_hook(Hier* H, int level, int kind);
+// This rank coarsens finest-level patch p of member m (the others are coarsened by their
+// owners): always when the hierarchy is not partitioned.
+bool coarsens_patch(const Hier* H, int member, int level, int p);
 
 // Packed sweep tiles (mlswe_pack.cu). patch_segments appends the runs of lines of patch b
 // for a sweep along dir (0: x, lines are rows; 1: y, lines are columns): lines [g0, g1)

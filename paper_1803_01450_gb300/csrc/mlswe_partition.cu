@@ -23,6 +23,8 @@ static mlswe_status fail(Hier* H, mlswe_status s, const std::string& msg) {
       return fail((H), MLSWE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+static bool partitioned(const Hier* H) { return H->part_size > 1; }
+
 // Morton (Z-order) key of a cell index pair: bit b of i at bit 2b, bit b of j at bit 2b + 1,
 // for the low 21 bits of each.
 static unsigned long long morton(int i, int j) {
@@ -34,15 +36,21 @@ static unsigned long long morton(int i, int j) {
   return key;
 }
 
-// Doubles of one patch in a packed buffer (layout in mlswe_partition_sizes' description).
-static long long pack_doubles(int M, const Box& b, bool fine_level_below) {
+// Doubles of one box in a packed buffer with the given parts (layout in
+// mlswe_partition_sizes' description; the interface fluxes only on levels with a finer level).
+static long long pack_doubles(int M, const Box& b, int parts, bool fine_level_below) {
   const long long w = b.w(), h = b.h();
-  long long n = 3LL * M * w * h + 2LL * M * h + 2LL * M * w;
-  if (fine_level_below) n += (long long)M * h * (w + 1) + (long long)M * (h + 1) * w;
+  long long n = 0;
+  if (parts & kPackState) n += 3LL * M * w * h;
+  if (parts & kPackAccum) n += 2LL * M * h + 2LL * M * w;
+  if ((parts & kPackIface) && fine_level_below) n += (long long)M * h * (w + 1) + (long long)M * (h + 1) * w;
   return n;
 }
 
-static bool partitioned(const Hier* H) { return H->part_size > 1; }
+bool coarsens_patch(const Hier* H, int member, int level, int p) {
+  if (!partitioned(H) || level != H->L - 1 || level == 0) return true;
+  return H->owner[member][level][p] == H->part_rank;
+}
 
 bool patch_owned(const Hier* H, int member, int level, int p) {
   if (!partitioned(H) || level == 0) return true;
@@ -106,8 +114,8 @@ mlswe_status ensure_partition(Hier* H) {
   const int n = std::max(1, H->part_size);
   H->owner.assign(H->n_members, std::vector<std::vector<int>>(H->L));
   H->part.resize(H->L);
+  struct Entry { int m, p; unsigned long long key; long long cells; };
   for (int l = 0; l < H->L; ++l) {
-    struct Entry { int m, p; unsigned long long key; long long cells; };
     std::vector<Entry> e;
     long long total = 0;
     for (int m = 0; m < H->n_members; ++m) {
@@ -127,26 +135,49 @@ mlswe_status ensure_partition(Hier* H) {
     });
     // owner: the rank whose share of the cells holds the patch's middle cell
     long long before = 0;
-    std::vector<std::vector<PackItem>> per(n), per_h(n);
-    Hier::PartLevel& PL = H->part[l];
-    PL.full.size.assign(n, 0);
-    PL.halo.size.assign(n, 0);
     for (const Entry& x : e) {
       int r = 0;
       if (l > 0 && total > 0) r = (int)std::min<long long>(n - 1, (2 * before + x.cells) * n / (2 * total));
       before += x.cells;
       H->owner[x.m][l][x.p] = r;
     }
-    for (const Entry& x : e) {
-      const int r = H->owner[x.m][l][x.p];
-      const Box& b = H->mem[x.m].lev[l].patches[x.p];
-      per[r].push_back(PackItem{H->desc_index(x.m, l), b.i0, b.j0, b.i1, b.j1, 0, PL.full.size[r]});
-      PL.full.size[r] += pack_doubles(H->cfg.M, b, l + 1 < H->L);
+  }
+  // exchange tables per level and kind, each grouped by the rank that packs it
+  const int M = H->cfg.M, fin = H->L - 1;
+  for (int l = 0; l < H->L; ++l) {
+    std::vector<std::vector<PackItem>> per[4];
+    long long* sz[4];
+    for (int k = 0; k < 4; ++k) {
+      per[k].assign(n, {});
+      H->part[l].kind[k].size.assign(n, 0);
+      sz[k] = H->part[l].kind[k].size.data();
     }
-    // halo boxes: where another rank's patch of the member, grown by two cells, meets an
-    // own patch (in the order of the own patches, then of the others)
-    if (l > 0 && n > 1) {
-      for (int m = 0; m < H->n_members; ++m) {
+    auto add = [&](int k, int r, int desc, const Box& b, int parts, bool below) {
+      per[k][r].push_back(PackItem{desc, b.i0, b.j0, b.i1, b.j1, parts, sz[k][r]});
+      sz[k][r] += pack_doubles(M, b, parts, below);
+    };
+    if (l > 0) {
+      std::vector<Entry> order;  // the split's order, for the full buffers
+      for (int m = 0; m < H->n_members; ++m)
+        for (int p = 0; p < (int)H->mem[m].lev[l].patches.size(); ++p) {
+          const Box& b = H->mem[m].lev[l].patches[p];
+          order.push_back(Entry{m, p, morton((b.i0 + b.i1) / 2, (b.j0 + b.j1) / 2), 0});
+        }
+      std::stable_sort(order.begin(), order.end(), [](const Entry& a, const Entry& b) {
+        if (a.m != b.m) return a.m < b.m;
+        if (a.key != b.key) return a.key < b.key;
+        return a.p < b.p;
+      });
+      const bool below = l + 1 < H->L;
+      for (const Entry& x : order) {
+        const int r = H->owner[x.m][l][x.p];
+        add(MLSWE_XCHG_FULL, r, H->desc_index(x.m, l), H->mem[x.m].lev[l].patches[x.p],
+            kPackState | kPackAccum | kPackIface, below);
+      }
+      // halo boxes: where another rank's patch of the member, grown by two cells, meets an
+      // own patch (in the order of the own patches, then of the others); LAST adds every
+      // owned patch's accumulators after them
+      for (int m = 0; m < H->n_members && n > 1; ++m) {
         const std::vector<Box>& P = H->mem[m].lev[l].patches;
         const std::vector<std::vector<int>> near = patches_near(P, kNG);
         for (int p = 0; p < (int)P.size(); ++p) {
@@ -157,24 +188,36 @@ mlswe_status ensure_partition(Hier* H) {
             const Box c{std::max(P[p].i0, Q.i0 - kNG), std::max(P[p].j0, Q.j0 - kNG), std::min(P[p].i1, Q.i1 + kNG),
                         std::min(P[p].j1, Q.j1 + kNG)};
             if (c.i0 >= c.i1 || c.j0 >= c.j1) continue;
-            per_h[r].push_back(PackItem{H->desc_index(m, l), c.i0, c.j0, c.i1, c.j1, 1, PL.halo.size[r]});
-            PL.halo.size[r] += 3LL * H->cfg.M * c.w() * c.h();
+            add(MLSWE_XCHG_HALO, r, H->desc_index(m, l), c, kPackState, below);
+            add(MLSWE_XCHG_LAST, r, H->desc_index(m, l), c, kPackState, below);
           }
         }
       }
+      for (const Entry& x : order)
+        add(MLSWE_XCHG_LAST, H->owner[x.m][l][x.p], H->desc_index(x.m, l), H->mem[x.m].lev[l].patches[x.p],
+            kPackAccum, below);
     }
-    for (int half = 0; half < 2; ++half) {
-      Hier::PartTable& T = half ? PL.halo : PL.full;
-      std::vector<std::vector<PackItem>>& src = half ? per_h : per;
+    if (l + 1 == fin) {
+      // the parent cells under every finest-level patch, packed by that patch's owner
+      const int r_f = H->cfg.ratio[l];
+      for (int m = 0; m < H->n_members; ++m) {
+        const std::vector<Box>& P = H->mem[m].lev[fin].patches;
+        for (int p = 0; p < (int)P.size(); ++p)
+          add(MLSWE_XCHG_AVERAGED, H->owner[m][fin][p], H->desc_index(m, l),
+              Box{P[p].i0 / r_f, P[p].j0 / r_f, P[p].i1 / r_f, P[p].j1 / r_f}, kPackState, false);
+      }
+    }
+    for (int k = 0; k < 4; ++k) {
+      Hier::PartTable& T = H->part[l].kind[k];
       std::vector<PackItem> all;
       T.first.assign(n + 1, 0);
       for (int r = 0; r < n; ++r) {
         T.first[r] = (int)all.size();
-        all.insert(all.end(), src[r].begin(), src[r].end());
+        all.insert(all.end(), per[k][r].begin(), per[k][r].end());
       }
       T.first[n] = (int)all.size();
-      mlswe_status s = upload_items(H, T.items, all);
-      if (s != MLSWE_OK) return s;
+      mlswe_status st = upload_items(H, T.items, all);
+      if (st != MLSWE_OK) return st;
     }
   }
   CUDA_TRY(H, cudaStreamSynchronize(H->st));
@@ -203,7 +246,7 @@ part_copy_kernel(const LevelDesc* __restrict__ descs, const PackItem* __restrict
     const long long ncell = (long long)w * h;
     const size_t plane = (size_t)NY * D.P;
     const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    const int nrow = 3 * M * h;
+    const int nrow = (it.parts & kPackState) ? 3 * M * h : 0;
     for (int row0 = (threadIdx.x >> 5) * 4; row0 < nrow; row0 += nwarp * 4) {
       // four rows per warp at a time: their loads are issued before their stores
       for (int i = lane; i < w; i += 32) {
@@ -229,21 +272,22 @@ part_copy_kernel(const LevelDesc* __restrict__ descs, const PackItem* __restrict
         }
       }
     }
-    if (it.state_only) continue;  // a halo box: its state only
-    b += 3LL * M * ncell;
-    // boundary accumulators: x edges at i0 and i1 of every row, y edges at j0 and j1 of
-    // every column
-    for (int t = threadIdx.x; t < 2 * M * h; t += blockDim.x) {
-      const int m = t / (2 * h), rr = t - m * 2 * h, j = it.j0 + (rr >> 1), a = (rr & 1) ? it.i1 : it.i0;
-      mv(D.fxf + ((size_t)m * NY + j) * (NX + 1) + a, t);
+    if (it.parts & kPackState) b += 3LL * M * ncell;
+    if (it.parts & kPackAccum) {
+      // boundary accumulators: x edges at i0 and i1 of every row, y edges at j0 and j1 of
+      // every column
+      for (int t = threadIdx.x; t < 2 * M * h; t += blockDim.x) {
+        const int m = t / (2 * h), rr = t - m * 2 * h, j = it.j0 + (rr >> 1), a = (rr & 1) ? it.i1 : it.i0;
+        mv(D.fxf + ((size_t)m * NY + j) * (NX + 1) + a, t);
+      }
+      b += 2LL * M * h;
+      for (int t = threadIdx.x; t < 2 * M * w; t += blockDim.x) {
+        const int m = t / (2 * w), rr = t - m * 2 * w, i = it.i0 + (rr >> 1), a = (rr & 1) ? it.j1 : it.j0;
+        mv(D.fyf + ((size_t)m * (NY + 1) + a) * NX + i, t);
+      }
+      b += 2LL * M * w;
     }
-    b += 2LL * M * h;
-    for (int t = threadIdx.x; t < 2 * M * w; t += blockDim.x) {
-      const int m = t / (2 * w), rr = t - m * 2 * w, i = it.i0 + (rr >> 1), a = (rr & 1) ? it.j1 : it.j0;
-      mv(D.fyf + ((size_t)m * (NY + 1) + a) * NX + i, t);
-    }
-    b += 2LL * M * w;
-    if (D.fxc != nullptr) {
+    if ((it.parts & kPackIface) && D.fxc != nullptr) {
       // interface fluxes of every edge of the box, sides included
       const int wx = w + 1;
       for (int t = threadIdx.x; t < M * h * wx; t += blockDim.x) {
@@ -271,15 +315,20 @@ static cudaError_t launch_part_copy(int M, const LevelDesc* descs, const PackIte
   return cudaGetLastError();
 }
 
-mlswe_status run_exchange_hook(Hier* H, int level, int halo_only) {
-  if (!partitioned(H) || level == 0 || !H->part_hook) return MLSWE_OK;
-  if (H->part_hook(H->part_ctx, level, halo_only) != 0) return fail(H, MLSWE_EINVAL, "partition exchange hook failed");
+mlswe_status run_exchange_hook(Hier* H, int level, int kind) {
+  if (!partitioned(H) || !H->part_hook) return MLSWE_OK;
+  if (kind != MLSWE_XCHG_AVERAGED && level == 0) return MLSWE_OK;
+  mlswe_status s = ensure_partition(H);
+  if (s != MLSWE_OK) return s;
+  if (H->part_hook(H->part_ctx, level, kind) != 0) return fail(H, MLSWE_EINVAL, "partition exchange hook failed");
   return MLSWE_OK;
 }
 
 // Argument checks shared by the exchange calls; builds the tables when a layout changed.
-static mlswe_status part_level_ready(Hier* H, int level) {
-  if (level < 1 || level >= H->L) return fail(H, MLSWE_EINVAL, "partition: level must be a refined level");
+static mlswe_status part_level_ready(Hier* H, int level, int kind) {
+  if (kind < MLSWE_XCHG_FULL || kind > MLSWE_XCHG_AVERAGED) return fail(H, MLSWE_EINVAL, "partition: bad kind");
+  if (kind == MLSWE_XCHG_AVERAGED ? (level != H->L - 2) : (level < 1 || level >= H->L))
+    return fail(H, MLSWE_EINVAL, "partition: no exchange of this kind on this level");
   return ensure_partition(H);
 }
 
@@ -307,6 +356,7 @@ mlswe_status mlswe_set_partition(mlswe_h h, int rank, int world_size, mlswe_exch
   h->part_hook = world_size > 1 ? hook : nullptr;
   h->part_ctx = ctx;
   h->part_dirty = true;
+  h->tables_dirty = true;               // the finest level's coarsening takes this rank's patches
   for (auto& W : h->wl) W.dirty = true;  // the sweeps take this rank's patches
   invalidate_graphs(h);
   return ensure_partition(h);
@@ -322,22 +372,21 @@ mlswe_status mlswe_partition_owners(mlswe_h h, int member, int level, int* owner
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int halo_only, long long* doubles_per_rank) {
-  if (!h || !doubles_per_rank || (halo_only != 0 && halo_only != 1))
-    return fail(h, MLSWE_EINVAL, "partition_sizes: bad argument");
-  mlswe_status s = part_level_ready(h, level);
+mlswe_status mlswe_partition_sizes(mlswe_h h, int level, int kind, long long* doubles_per_rank) {
+  if (!h || !doubles_per_rank) return fail(h, MLSWE_EINVAL, "partition_sizes: bad argument");
+  mlswe_status s = part_level_ready(h, level, kind);
   if (s != MLSWE_OK) return s;
-  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
+  const Hier::PartTable& T = h->part[level].kind[kind];
   for (int r = 0; r < h->part_size; ++r) doubles_per_rank[r] = T.size[r];
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_pack(mlswe_h h, int level, int halo_only, double* dst) {
-  if (!h || !dst || (halo_only != 0 && halo_only != 1)) return fail(h, MLSWE_EINVAL, "partition_pack: bad argument");
-  mlswe_status s = part_level_ready(h, level);
+mlswe_status mlswe_partition_pack(mlswe_h h, int level, int kind, double* dst) {
+  if (!h || !dst) return fail(h, MLSWE_EINVAL, "partition_pack: bad argument");
+  mlswe_status s = part_level_ready(h, level, kind);
   if (s != MLSWE_OK) return s;
   if (!device_pointer(dst)) return fail(h, MLSWE_EINVAL, "partition_pack: dst is not device memory");
-  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
+  const Hier::PartTable& T = h->part[level].kind[kind];
   const int r = h->part_rank;
   CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, T.items.d, T.first[r], T.first[r + 1], h->parity[level], dst, 0,
                                8 * h->num_sms, h->st));
@@ -345,13 +394,12 @@ mlswe_status mlswe_partition_pack(mlswe_h h, int level, int halo_only, double* d
   return MLSWE_OK;
 }
 
-mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int halo_only, int from, const double* src) {
-  if (!h || !src || from < 0 || from >= h->part_size || (halo_only != 0 && halo_only != 1))
-    return fail(h, MLSWE_EINVAL, "partition_unpack: bad argument");
-  mlswe_status s = part_level_ready(h, level);
+mlswe_status mlswe_partition_unpack(mlswe_h h, int level, int kind, int from, const double* src) {
+  if (!h || !src || from < 0 || from >= h->part_size) return fail(h, MLSWE_EINVAL, "partition_unpack: bad argument");
+  mlswe_status s = part_level_ready(h, level, kind);
   if (s != MLSWE_OK) return s;
   if (!device_pointer(src)) return fail(h, MLSWE_EINVAL, "partition_unpack: src is not device memory");
-  const Hier::PartTable& T = halo_only ? h->part[level].halo : h->part[level].full;
+  const Hier::PartTable& T = h->part[level].kind[kind];
   CUDA_TRY(h, launch_part_copy(h->cfg.M, h->d_desc, T.items.d, T.first[from], T.first[from + 1], h->parity[level],
                                const_cast<double*>(src), 1, 8 * h->num_sms, h->st));
   h->kernel_launches += T.first[from + 1] > T.first[from] ? 1 : 0;

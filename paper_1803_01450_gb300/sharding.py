@@ -23,9 +23,11 @@ member's step:
   after every refined level step, in which the ranks all-gather their packed patch values
   and take the maximum of the wave-speed slots (exchange_level; PatchPartition wires it to
   a Hierarchy). Level 0, ghost fill, coarsening, reflux, time steps and regrids run on
-  every rank on the full state, so every rank's hierarchy equals the undivided one. Between
-  the finest level's substeps of one parent step only the halo cells move (the cells of a
-  rank's patches within two cells of another rank's patch), the full state after the last.
+  every rank, so every rank's hierarchy equals the undivided one. The finest level moves
+  less: between its substeps only the halo cells (the cells of a rank's patches within two
+  cells of another rank's patch), after the last one the halo cells and the reflux
+  accumulators; each rank coarsens its own finest patches and sends the parent cells under
+  them; the whole finest level moves only before a regrid and at the end of an advance.
 
 Data moves only by point-to-point sends or all-gathers into local buffers and by
 all-reduces (NCCL on GPUs, gloo on CPUs); the stepping itself is a callable the caller
@@ -191,15 +193,16 @@ class PatchPartition:
         self.H, self.rank, self.ws, self.dist, self.device = H, rank, world_size, dist, device
         H.set_partition(rank, world_size, self._exchange)
 
-    def _exchange(self, level, halo_only):
+    def _exchange(self, level, kind):
         import torch
         H = self.H
         stream = torch.cuda.ExternalStream(H.stream, device=self.device)
         with torch.cuda.stream(stream):
             ptr, n = H.wave_speed_slots()
+            # the speeds' maximum is idempotent: taken at every kind of exchange
             speeds = torch.as_tensor(_DeviceArray(ptr, n), device=self.device)
-            exchange_level(self.rank, self.ws, H.partition_sizes(level, halo_only),
-                           lambda buf: H.partition_pack(level, buf.data_ptr(), halo_only),
-                           lambda q, buf: H.partition_unpack(level, q, buf.data_ptr(), halo_only),
+            exchange_level(self.rank, self.ws, H.partition_sizes(level, kind),
+                           lambda buf: H.partition_pack(level, buf.data_ptr(), kind),
+                           lambda q, buf: H.partition_unpack(level, q, buf.data_ptr(), kind),
                            speeds, self.dist,
                            lambda k: torch.empty(k, dtype=torch.float64, device=self.device))
