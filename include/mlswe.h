@@ -436,9 +436,10 @@ mlswe_status mlswe_timing(mlswe_h h, int enable, int n, double* ms_out, long lon
  *    patch p goes to rank min(n - 1, floor((2 c_p + cells_p) n / (2 T))) (the rank whose
  *    share of the cells holds the patch's middle cell), so each rank's cells differ from
  *    T / n by at most the largest patch;
- *  - a rank sweeps only its own patches of levels >= 1, and coarsens only its own patches
- *    of the finest level; level 0, the ghost fill, the other coarsenings, the reflux,
- *    the time step and the regrids run on every rank;
+ *  - a rank sweeps and ghost-fills only its own patches of levels >= 1 (a patch's ghost
+ *    ring is read by its own sweeps only; cells outside every patch may therefore differ
+ *    between ranks), and coarsens only its own patches of the finest level; level 0, the
+ *    other coarsenings, the reflux, the time step and the regrids run on every rank;
  *  - inside mlswe_advance the library calls the exchange hook at fixed points with a
  *    kind, and the hook must give every rank the other ranks' packed values of that kind
  *    (mlswe_partition_pack / mlswe_partition_unpack, through an all-gather), and, for

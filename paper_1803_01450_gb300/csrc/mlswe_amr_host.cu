@@ -108,8 +108,10 @@ static mlswe_status build_tables(Hier* H) {
                                  Box{gi0, b.j1, gi1, std::min(V.NY, b.j1 + kNG)},
                                  Box{gi0, b.j0, b.i0, b.j1},
                                  Box{b.i1, b.j0, gi1, b.j1}};
+          // partitioned: only the owner's sweeps read a patch's ring, so the owner fills it
+          const bool own = patch_owned(H, m, l, p);
           for (const Box& s : strips)
-            if (s.i1 > s.i0 && s.j1 > s.j0) {
+            if (own && s.i1 > s.i0 && s.j1 > s.j0) {
               for (int jc = s.j0 / r; jc <= (s.j1 - 1) / r; ++jc)
                 for (int ic = s.i0 / r; ic <= (s.i1 - 1) / r; ++ic)
                   gcell.push_back(GhostCell{dc, d, ic, jc, s.i0, s.j0, s.i1, s.j1});
