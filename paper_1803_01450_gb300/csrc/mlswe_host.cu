@@ -279,22 +279,70 @@ static void build_items(Hier* H, int level, int dir, std::vector<SweepItem>& out
 // Runs of patch lines for the packed (batched) form: for every patch and every part of its
 // lines (the tile length of tile_dims), one item holding all consecutive lines of one kind;
 // pack_tiles then cuts and packs them into tiles.
+// The x sweep of a refined level also sweeps the two rows above and below each patch (the y
+// sweep reads its result there). Where such a row runs through another patch swept here, that
+// patch's own x sweep already writes the same values (an x-sweep value depends on its row
+// only), so those columns are left out: the parts of ghost row r of patch p that no patch q
+// (swept by this rank) with q.j0 <= r < q.j1 covers.
+static void ghost_row_parts(const std::vector<Box>& P, const std::vector<int>& near, const Box& b, int r,
+                            const std::vector<char>& swept, std::vector<std::pair<int, int>>& parts) {
+  parts.assign(1, {b.i0, b.i1});
+  for (int q : near) {
+    const Box& Q = P[q];
+    if (!swept[q] || r < Q.j0 || r >= Q.j1) continue;
+    std::vector<std::pair<int, int>> next;
+    for (const auto& iv : parts) {
+      if (Q.i1 <= iv.first || Q.i0 >= iv.second) { next.push_back(iv); continue; }
+      if (iv.first < Q.i0) next.push_back({iv.first, Q.i0});
+      if (Q.i1 < iv.second) next.push_back({Q.i1, iv.second});
+    }
+    parts.swap(next);
+  }
+}
+
 static void build_segments(Hier* H, int level, int dir, std::vector<SweepItem>& out) {
   out.clear();
   const TileShape ts = H->shape[level * 2 + dir];
+  const bool ghost_rows = !H->cfg.unsplit && dir == 0 && level > 0;
   for (int m = 0; m < H->n_members; ++m) {
     const Level& V = H->mem[m].lev[level];
     const int desc = H->desc_index(m, level);
+    std::vector<std::vector<int>> near;
+    std::vector<char> swept(V.patches.size(), 0);
+    for (int p = 0; p < (int)V.patches.size(); ++p) swept[p] = patch_owned(H, m, level, p) ? 1 : 0;
+    if (ghost_rows) near = patches_near(V.patches, kNG);
+    std::vector<std::pair<int, int>> pa, pb;
     for (int p = 0; p < (int)V.patches.size(); ++p) {
-      if (!patch_owned(H, m, level, p)) continue;  // another rank sweeps it
+      if (!swept[p]) continue;  // another rank sweeps it
       const Box& b = V.patches[p];
       const int lo = dir == 0 ? b.j0 : b.i0, hi = dir == 0 ? b.j1 : b.i1;
       int tl, tn;
       tile_dims(ts, dir == 0 ? b.w() : b.h(), &tl, &tn);
-      int g0 = lo, g1 = hi;  // lines processed: the patch's, ghost lines on each side
-      if (H->cfg.unsplit) { g0 = lo - 1; g1 = hi + 1; }
-      else if (dir == 0 && level > 0) { g0 = std::max(0, lo - kNG); g1 = std::min(V.NY, hi + kNG); }
-      patch_segments(b, dir, tl, g0, g1, desc, out);
+      if (!ghost_rows) {
+        int g0 = lo, g1 = hi;  // lines processed: the patch's (unsplit: one ghost line each side)
+        if (H->cfg.unsplit) { g0 = lo - 1; g1 = hi + 1; }
+        patch_segments(b, dir, tl, g0, g1, desc, out);
+        continue;
+      }
+      // ghost rows below, the patch's rows, ghost rows above; consecutive ghost rows with the
+      // same parts form one run
+      auto ghost = [&](int r0, int r1) {
+        int r = r0;
+        while (r < r1) {
+          ghost_row_parts(V.patches, near[p], b, r, swept, pa);
+          int e = r + 1;
+          while (e < r1) {
+            ghost_row_parts(V.patches, near[p], b, e, swept, pb);
+            if (pb != pa) break;
+            ++e;
+          }
+          for (const auto& iv : pa) patch_segments(Box{iv.first, r, iv.second, r}, dir, tl, r, e, desc, out);
+          r = e;
+        }
+      };
+      ghost(std::max(0, lo - kNG), lo);
+      patch_segments(b, dir, tl, lo, hi, desc, out);
+      ghost(hi, std::min(V.NY, hi + kNG));
     }
   }
 }

@@ -295,6 +295,8 @@ mlswe_status enqueue_level_step(Hier* H, int level, int record);
 // change; whether this rank sweeps patch p of (member, level) (always on level 0 and when the
 // hierarchy is not partitioned); the exchange hook after a level step.
 mlswe_status ensure_partition(Hier* H);
+// For every patch, the other patches whose box grown by g cells meets it (ascending).
+std::vector<std::vector<int>> patches_near(const std::vector<Box>& P, int g);
 bool patch_owned(const Hier* H, int member, int level, int p);
 mlswe_status run_exchange_hook(Hier* H, int level, int kind);
 // This rank coarsens finest-level patch p of member m (the others are coarsened by their

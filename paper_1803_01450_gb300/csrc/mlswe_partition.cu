@@ -72,7 +72,7 @@ static mlswe_status upload_items(Hier* H, DevTable<PackItem>& T, const std::vect
 
 // For every patch, the indices of the other patches whose box grown by g cells meets it
 // (in increasing order), found through buckets of 64 x 64 cells.
-static std::vector<std::vector<int>> patches_near(const std::vector<Box>& P, int g) {
+std::vector<std::vector<int>> patches_near(const std::vector<Box>& P, int g) {
   constexpr int kBucket = 64;
   std::vector<std::vector<int>> out(P.size());
   if (P.empty()) return out;
